@@ -1,0 +1,127 @@
+"""Seeded synthetic inputs shared by the CUDA path and the oracle.
+
+This module holds initial conditions only (density and velocity fields, or
+random populations for identity checks); it contains none of the lattice
+method's arithmetic and imports nothing else from this package, so both the
+CUDA-path tests and the oracle may use it.
+
+Fields are FP64 numpy arrays: ``rho[nz, ny, nx]`` and ``u[3, nz, ny, nx]``,
+x fastest, lattice units.
+"""
+from __future__ import annotations
+
+import math
+from typing import Optional, Tuple
+
+import numpy as np
+
+THETA_LATTICE = 1.0 / 3.0  # c_s^2 of the D3Q19/D3Q27 lattices (Sec. 7 / App. F)
+
+
+def tgv_fields(n: int, u0: float = 0.05, rho0: float = 1.0,
+               shape: Optional[Tuple[int, int, int]] = None) -> Tuple[np.ndarray, np.ndarray]:
+    """Taylor-Green vortex initial state (Sec. 7.1).
+
+    u_x = u0 sin X cos Y cos Z, u_y = -u0 cos X sin Y cos Z, u_z = 0 with
+    X = 2 pi x / L_box (node positions x = 0..n-1).  The pressure fluctuation
+    p = rho0 u0^2/16 (cos 2X + cos 2Y)(cos 2Z + 2) enters as rho = rho0 + p/theta.
+    """
+    nx, ny, nz = shape if shape is not None else (n, n, n)
+    X = 2.0 * math.pi * np.arange(nx) / nx
+    Y = 2.0 * math.pi * np.arange(ny) / ny
+    Z = 2.0 * math.pi * np.arange(nz) / nz
+    Zg, Yg, Xg = np.meshgrid(Z, Y, X, indexing="ij")
+    u = np.zeros((3, nz, ny, nx), dtype=np.float64)
+    u[0] = u0 * np.sin(Xg) * np.cos(Yg) * np.cos(Zg)
+    u[1] = -u0 * np.cos(Xg) * np.sin(Yg) * np.cos(Zg)
+    p = rho0 * u0 * u0 / 16.0 * (np.cos(2 * Xg) + np.cos(2 * Yg)) * (np.cos(2 * Zg) + 2.0)
+    rho = rho0 + p / THETA_LATTICE
+    return rho, u
+
+
+def tgv2d_fields(n: int, u0: float = 0.01, nz: int = 4) -> Tuple[np.ndarray, np.ndarray]:
+    """Two-dimensional Taylor-Green vortex, uniform in z (an exact Navier-Stokes
+    solution whose kinetic energy decays as exp(-2 nu |k|^2 t), |k|^2 = 2 (2 pi/n)^2).
+    rho carries the exact pressure p = -rho0 u0^2/4 (cos 2X + cos 2Y)."""
+    X = 2.0 * math.pi * np.arange(n) / n
+    Yg, Xg = np.meshgrid(X, X, indexing="ij")
+    u = np.zeros((3, nz, n, n), dtype=np.float64)
+    u[0] = (u0 * np.sin(Xg) * np.cos(Yg))[None]
+    u[1] = (-u0 * np.cos(Xg) * np.sin(Yg))[None]
+    p = -u0 * u0 / 4.0 * (np.cos(2 * Xg) + np.cos(2 * Yg))
+    rho = np.broadcast_to(1.0 + p / THETA_LATTICE, (nz, n, n)).copy()
+    return rho, u
+
+
+def shear_wave_fields(n: int, amp: float = 1e-3, nxy: int = 4) -> Tuple[np.ndarray, np.ndarray]:
+    """u_x = amp sin(2 pi z / n), uniform in x and y, rho = 1 (decays as exp(-nu k^2 t))."""
+    z = np.arange(n)
+    u = np.zeros((3, n, nxy, nxy), dtype=np.float64)
+    u[0] = (amp * np.sin(2.0 * math.pi * z / n))[:, None, None]
+    rho = np.ones((n, nxy, nxy), dtype=np.float64)
+    return rho, u
+
+
+def hit_fields(n: int, k0: float = 4.0, urms: float = 0.04, seed: int = 0,
+               shape: Optional[Tuple[int, int, int]] = None,
+               dtype=np.float64) -> Tuple[np.ndarray, np.ndarray]:
+    """Decaying homogeneous isotropic turbulence initial velocity.
+
+    Random-phase solenoidal field with energy spectrum E(k) ~ k^4 exp(-2 (k/k0)^2),
+    k in units of 2 pi / L.  Recipe: complex Gaussian noise from a seeded PCG64
+    generator on the rfft half-spectrum, times the amplitude
+    sqrt(E(k) / (4 pi k^2)), projected onto the plane normal to k
+    (u <- u - k (k.u)/k^2), zero mean, inverse real FFT, then rescaled so that
+    the per-component rms sqrt(<u_a^2>) averaged over the three components
+    equals ``urms``.  rho = 1.
+    """
+    import scipy.fft as sfft
+
+    nx, ny, nz = shape if shape is not None else (n, n, n)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    kx = np.fft.rfftfreq(nx, d=1.0 / nx)
+    ky = np.fft.fftfreq(ny, d=1.0 / ny)
+    kz = np.fft.fftfreq(nz, d=1.0 / nz)
+    KZ, KY, KX = np.meshgrid(kz, ky, kx, indexing="ij")
+    k2 = KX * KX + KY * KY + KZ * KZ
+    k = np.sqrt(k2)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        amp = np.where(k > 0, np.sqrt(k ** 4 * np.exp(-2.0 * (k / k0) ** 2) / (4.0 * math.pi * k2)), 0.0)
+    spec = np.empty((3,) + k.shape, dtype=np.complex128)
+    for a in range(3):
+        spec[a] = (rng.standard_normal(k.shape) + 1j * rng.standard_normal(k.shape)) * amp
+    with np.errstate(divide="ignore", invalid="ignore"):
+        kdotu = (KX * spec[0] + KY * spec[1] + KZ * spec[2]) / np.where(k2 > 0, k2, 1.0)
+    spec[0] -= KX * kdotu
+    spec[1] -= KY * kdotu
+    spec[2] -= KZ * kdotu
+    spec[:, 0, 0, 0] = 0.0
+    u = np.empty((3, nz, ny, nx), dtype=np.float64)
+    for a in range(3):
+        u[a] = sfft.irfftn(spec[a], s=(nz, ny, nx), workers=-1)
+    del spec
+    u -= u.reshape(3, -1).mean(axis=1)[:, None, None, None]
+    rms = math.sqrt(float(np.mean(u * u)))
+    u *= urms / rms
+    rho = np.ones((nz, ny, nx), dtype=np.float64)
+    return rho.astype(dtype, copy=False), u.astype(dtype, copy=False)
+
+
+def random_populations(q: int, shape: Tuple[int, int, int], seed: int = 0, amp: float = 0.05,
+                       weights: Optional[np.ndarray] = None) -> np.ndarray:
+    """Random positive populations f[q, nz, ny, nx] = w_i (1 + amp * N(0,1)).
+
+    ``weights`` are the lattice weights (passed in by the caller so that this
+    module carries no lattice table); when None every population is scaled by 1/q.
+    """
+    nx, ny, nz = shape
+    rng = np.random.Generator(np.random.PCG64(seed))
+    w = np.full(q, 1.0 / q) if weights is None else np.asarray(weights, dtype=np.float64)
+    noise = rng.standard_normal((q, nz, ny, nx))
+    return w[:, None, None, None] * (1.0 + amp * noise)
+
+
+def ensemble_viscosities(nbox: int, seed: int = 0, lo: float = 5e-5, hi: float = 5e-4) -> np.ndarray:
+    """Per-box viscosities uniform in [lo, hi] from a seeded PCG64 generator."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return lo + (hi - lo) * rng.random(nbox)

@@ -193,7 +193,8 @@ def init_equilibrium(q: int, rho: Optional[np.ndarray], u: np.ndarray) -> np.nda
 
 
 def fields(f: np.ndarray, F: Sequence[float] = (0.0, 0.0, 0.0)):
-    """rho[nz,ny,nx], u[3,nz,ny,nx] of a population array (App. F.1 step 1)."""
+    """rho[nz,ny,nx], u[3,nz,ny,nx] of a stored (post-collision) population array
+    (App. F.1 step 1); with a body force the reported velocity is (sum f c - F/2)/rho."""
     lib = _load()
     q, nz, ny, nx = f.shape
     ff = np.ascontiguousarray(f, dtype=np.float64)

@@ -659,18 +659,22 @@ int orc_init_equilibrium(int q, int nx, int ny, int nz, const double* rho, const
     return 0;
 }
 
-/* Macroscopic fields of a population array (App. F.1 step 1), with the
- * half-force shift when F is given. */
+/* Macroscopic fields of a stored (post-collision) population array, App. F.1
+ * step 1.  With Guo forcing the collision adds the full impulse F to sum f c,
+ * so the velocity of time n is (sum f c - F/2)/rho: the moments are taken
+ * with the force -F. */
 int orc_fields(int q, int nx, int ny, int nz, const double* F, const double* f, double* rho, double* u)
 {
     orc_lattice L;
     if (orc_lattice_init(q, &L)) return -1;
-    const double Z[3] = {0.0, 0.0, 0.0};
+    double mF[3] = {0.0, 0.0, 0.0};
+    if (F)
+        for (int a = 0; a < 3; ++a) mF[a] = -F[a];
     size_t N = (size_t)nx * ny * nz;
     for (size_t c = 0; c < N; ++c) {
         double fc[27], r, uu[3];
         for (int i = 0; i < q; ++i) fc[i] = f[(size_t)i * N + c];
-        orc_moments_L(&L, fc, F ? F : Z, &r, uu);
+        orc_moments_L(&L, fc, mF, &r, uu);
         rho[c] = r;
         for (int a = 0; a < 3; ++a) u[(size_t)a * N + c] = uu[a];
     }

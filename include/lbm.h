@@ -1,0 +1,186 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) kinetic-closure LES lattice-Boltzmann
+ * library (liblbm.so).
+ *
+ * The library advances a three-dimensional lattice-Boltzmann large-eddy
+ * simulation whose collision carries the collision-side subgrid closure of
+ * Marson & Malaspinas, "Kinetic closure of turbulence: collision-side modeling
+ * beyond the filtered Boltzmann equation" (arXiv 2605.19796):
+ *
+ *   f_post_i = f_i - omega_hat (f_i - f0_i - f_sgs_i) - omega_sgs f_sgs_i      (App. F.1, Eq. operational_two_rate_update)
+ *   f_i(x + c_i, t + 1) = f_post_i(x, t)                                     (Eq. streaming)
+ *
+ * with the shifted rates omega_hat = (nu/theta + 1/2)^-1 and
+ * omega_sgs = min(omega_hat, (C_nu Delta sqrt(k_sgs)/theta + 1/2)^-1),
+ * k_sgs = |tr m_sgs| / 2 (Eq. omega_sgs_operational), and the SGS carrier f_sgs
+ * of the selected closure (KC-MP, App. F.3; KC-RB, App. F.2; KC-RR, App. F.4).
+ * Each time step is ONE fused CUDA kernel: pull streaming, moments,
+ * equilibrium (Eq. discrete_equilibrium), finite-difference strain
+ * (Eqs. fd, strain_rate_discrete, fd_boundary_lower/upper), closure, rate and
+ * relaxation, and the store.
+ *
+ * Conventions
+ *  - Lattice units (dx = dt = 1, theta = 1/3).
+ *  - Canonical population order: D3Q27 index i = 9*(cz+1) + 3*(cy+1) + (cx+1)
+ *    for c in {-1,0,1}^3; D3Q19 is the same enumeration without the eight
+ *    corners (|c|^2 = 3).
+ *  - Fields are x-fastest: rho[box][z][y][x], u[3][box][z][y][x] (the velocity
+ *    component is the slowest index), populations [box][q][z][y][x].
+ *  - The state held by a handle is the post-collision population array; after
+ *    n steps its moments are the fields at time n.
+ *  - All entry points return 0 on success or a negative LBM_ERR_* code; the
+ *    message of the last failure on the calling thread is lbm_last_error().
+ *  - Host arrays are owned by the caller and only accessed during the call.
+ *    Device memory allocated by lbm_create is owned by the handle and freed by
+ *    lbm_destroy.
+ *  - Work is enqueued on the handle's CUDA stream (cfg.cuda_stream, NULL = the
+ *    legacy default stream).  lbm_step returns after enqueueing; calls that
+ *    return data to host memory synchronise the stream.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_ABI_VERSION 1
+
+/* error codes */
+#define LBM_OK 0
+#define LBM_ERR_ARG (-1)         /* invalid argument or configuration          */
+#define LBM_ERR_OOM (-2)         /* device or host allocation failed           */
+#define LBM_ERR_CUDA (-3)        /* a CUDA runtime call failed                 */
+#define LBM_ERR_NONFINITE (-4)   /* a NaN/Inf density or velocity was detected */
+#define LBM_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up         */
+#define LBM_ERR_UNSUPPORTED (-6) /* combination not supported (e.g. KC-RR on D3Q19) */
+#define LBM_ERR_IO (-7)          /* file I/O failed or the file does not match  */
+
+/* lattice (App. F "Velocity space discretization"; D3Q19 as an extension) */
+#define LBM_D3Q19 19
+#define LBM_D3Q27 27
+
+/* collision closure (Sec. 6 and App. F) */
+#define LBM_BGK 0          /* resolved BGK: omega_sgs = omega_hat (Sec. 5.1 resolved-BGK limit) */
+#define LBM_KCMP 1         /* moment-projected closure, App. F.3 (default, C_nu = 0.035)    */
+#define LBM_KCRB_HERMITE 2 /* residual-based closure, Hermite f1, Eq. kcrb_operational_fone  */
+#define LBM_KCRB_RAW 3     /* residual-based closure, raw c c : S f1, Eq. kcrb_operational_raw_fone */
+#define LBM_KCRR 4         /* recursive kinetic closure, App. F.4 (D3Q27 only)               */
+
+/* population storage */
+#define LBM_FP64 0          /* double storage, double arithmetic (parity mode)               */
+#define LBM_FP32 1          /* float storage, float arithmetic                               */
+#define LBM_FP16_SHIFTED 2  /* half storage of f_i - w_i, float arithmetic                   */
+#define LBM_BF16_SHIFTED 3  /* bfloat16 storage of f_i - w_i, float arithmetic               */
+
+/* boundary condition per axis (both faces) */
+#define LBM_PERIODIC 0
+#define LBM_BOUNCEBACK 1 /* halfway bounce-back walls; supported on the y axis only */
+
+typedef struct lbm_handle lbm_handle;
+
+typedef struct {
+    int lattice;        /* LBM_D3Q19 or LBM_D3Q27                                   */
+    int nx, ny, nz;     /* cells per box, each >= 1 (>= 3 along a bounce-back axis)  */
+    int nbatch;         /* number of independent boxes (ensemble), >= 1             */
+    const double* nu;   /* host array [nbatch]: kinematic viscosity per box, > 0;
+                           tau_hat = nu/theta + 1/2 (Eq. omega_t_discrete)          */
+    int closure;        /* LBM_BGK .. LBM_KCRR                                      */
+    double c_nu;        /* C_nu of Eq. nu_t_sharp_closure (paper: 0.035 KC-MP,
+                           0.02 KC-RB and KC-RR)                                    */
+    double delta;       /* filter width Delta in lattice units (paper: 1)            */
+    int storage;        /* LBM_FP64 .. LBM_BF16_SHIFTED                              */
+    int bc[3];          /* per axis x, y, z: LBM_PERIODIC or LBM_BOUNCEBACK          */
+    double force[3];    /* uniform body force density (Guo forcing); zero for none   */
+    void* cuda_stream;  /* cudaStream_t to enqueue on; NULL = legacy default stream  */
+    int tile_y;         /* tuning: rows per CTA tile (0 = library default)           */
+    int zchunk;         /* tuning: z-planes per CTA march (0 = library default)      */
+} lbm_config;
+
+/* Fills cfg with defaults: D3Q27, 32^3, one box, KC-MP, C_nu 0.035, Delta 1,
+ * FP32 storage, periodic, no force.  cfg->nu must still be set. */
+void lbm_config_default(lbm_config* cfg);
+
+/* Creates a solver.  Allocates two population buffers (ping-pong) of
+ * nbatch*q*nx*ny*nz elements each plus small control buffers on the current
+ * CUDA device.  On failure *out is NULL and nothing is leaked. */
+int lbm_create(const lbm_config* cfg, lbm_handle** out);
+
+/* Frees everything the handle owns; NULL is ignored. */
+void lbm_destroy(lbm_handle* h);
+
+/* Sets every population to the equilibrium f0(rho, u) (Eq. discrete_equilibrium).
+ * rho: host [nbatch*nz*ny*nx] or NULL for rho = 1; u: host [3][nbatch*nz*ny*nx].
+ * Synchronises the stream before returning. */
+int lbm_init_velocity(lbm_handle* h, const double* rho, const double* u);
+
+/* As lbm_init_velocity with device pointers (FP64, same layouts); enqueue only. */
+int lbm_init_velocity_device(lbm_handle* h, const double* rho_dev, const double* u_dev);
+
+/* Advances every box by nsteps time steps (one fused kernel launch per step).
+ * Enqueue only; errors detected on the device (non-finite fields) are reported
+ * by the next lbm_moments / lbm_diagnostics / lbm_synchronize. */
+int lbm_step(lbm_handle* h, int nsteps);
+
+/* Density and velocity of the current state (App. F.1 step 1, with the
+ * half-force shift when a body force is set) into host arrays rho
+ * [nbatch*N] and u [3][nbatch*N] (either may be NULL).  Synchronises. */
+int lbm_moments(lbm_handle* h, double* rho, double* u);
+
+/* As lbm_moments into device FP64 arrays; enqueue only. */
+int lbm_moments_device(lbm_handle* h, double* rho_dev, double* u_dev);
+
+/* FP64 global diagnostics of box `box` (Sec. 7.1, Eq. tgv_energy_enstrophy):
+ * out[0] mass sum, out[1..3] momentum sums, out[4] E_k = <rho|u|^2/2>,
+ * out[5] enstrophy <|curl u|^2/2> with the sixth-order centred curl (second-order
+ * stencils along bounce-back axes), out[6] number of non-finite cells,
+ * out[7] max |u|.  Synchronises; returns LBM_ERR_NONFINITE if out[6] > 0. */
+int lbm_diagnostics(lbm_handle* h, int box, double out[8]);
+
+/* Copies the populations, converted to FP64 (shifted storage un-shifted), to
+ * host [nbatch][q][nz][ny][nx].  Synchronises. */
+int lbm_get_populations(lbm_handle* h, double* f);
+
+/* Sets the populations from host FP64 [nbatch][q][nz][ny][nx].  Synchronises. */
+int lbm_set_populations(lbm_handle* h, const double* f);
+
+/* Gathers the populations (FP64, un-shifted) of ncells cells of box `box`:
+ * xyz is host int [ncells][3] (x, y, z, each wrapped periodically into the
+ * box), out is host double [ncells][q] in canonical order.  Synchronises.
+ * Lets callers check sampled cells of lattices too large to copy back. */
+int lbm_probe(lbm_handle* h, int box, const int* xyz, int ncells, double* out);
+
+/* Device address and element size (bytes) of the current population buffer
+ * (read-only view, valid until the next lbm_step). */
+int lbm_population_buffer(lbm_handle* h, const void** ptr, int* elem_bytes);
+
+/* Waits for the handle's stream; returns LBM_ERR_NONFINITE if a step saw a
+ * non-finite density or velocity since the last check (the flag is cleared). */
+int lbm_synchronize(lbm_handle* h);
+
+/* Writes / reads the state (header + raw populations in storage format).
+ * lbm_load requires a file written for the same lattice, sizes, nbatch and
+ * storage (LBM_ERR_IO otherwise).  Both synchronise. */
+int lbm_save(lbm_handle* h, const char* path);
+int lbm_load(lbm_handle* h, const char* path);
+
+/* Steps taken since creation (or since the state in the last lbm_load). */
+int64_t lbm_step_count(const lbm_handle* h);
+
+/* Number of CUDA kernels this handle has launched since creation. */
+int64_t lbm_kernel_launches(const lbm_handle* h);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* lbm_last_error(void);
+
+/* LBM_ABI_VERSION of the loaded library. */
+int lbm_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,411 @@
+// Auxiliary kernels of liblbm: equilibrium initialisation, moments, storage
+// conversions and the FP64 diagnostics reduction.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "lbm_internal.h"
+#include "lbm_lattice.cuh"
+#include "lbm_step.cuh"
+
+namespace lbmk {
+
+namespace {
+
+// storage value <-> FP64 population f (un-shifted)
+template <typename S>
+__device__ __forceinline__ double to_f(S v, double w);
+template <>
+__device__ __forceinline__ double to_f<double>(double v, double)
+{
+    return v;
+}
+template <>
+__device__ __forceinline__ double to_f<float>(float v, double)
+{
+    return (double)v;
+}
+template <>
+__device__ __forceinline__ double to_f<__half>(__half v, double w)
+{
+    return w + (double)__half2float(v);
+}
+template <>
+__device__ __forceinline__ double to_f<__nv_bfloat16>(__nv_bfloat16 v, double w)
+{
+    return w + (double)__bfloat162float(v);
+}
+
+template <typename S>
+__device__ __forceinline__ S from_f(double f, double w);
+template <>
+__device__ __forceinline__ double from_f<double>(double f, double)
+{
+    return f;
+}
+template <>
+__device__ __forceinline__ float from_f<float>(double f, double)
+{
+    return (float)f;
+}
+template <>
+__device__ __forceinline__ __half from_f<__half>(double f, double w)
+{
+    return __float2half_rn((float)(f - w));
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(double f, double w)
+{
+    return __float2bfloat16_rn((float)(f - w));
+}
+
+// f0 - w in FP64 from Eq. (discrete_equilibrium) (D3Q27) or the second-order
+// Hermite form (D3Q19)
+template <int Q>
+__device__ __forceinline__ void equilibrium_g(double rho, double ux, double uy, double uz, double (&geq)[Q])
+{
+    const double a1 = 1.0 / kTheta, a2 = (1.0 - kTheta) / (2.0 * kTheta * kTheta), a0 = -kTheta / (2.0 * kTheta * kTheta);
+    static_for<Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
+        constexpr double w = weight_of(Q, i);
+        if constexpr (Q == 27) {
+            const double px = cx == 0 ? 1.0 + a0 * ux * ux : 1.0 + cx * a1 * ux + a2 * ux * ux;
+            const double py = cy == 0 ? 1.0 + a0 * uy * uy : 1.0 + cy * a1 * uy + a2 * uy * uy;
+            const double pz = cz == 0 ? 1.0 + a0 * uz * uz : 1.0 + cz * a1 * uz + a2 * uz * uz;
+            geq[i] = w * (rho * px * py * pz - 1.0);
+        } else {
+            const double cu = cx * ux + cy * uy + cz * uz;
+            const double usq = ux * ux + uy * uy + uz * uz;
+            geq[i] = w * ((rho - 1.0) + rho * (a1 * cu + 0.5 * a1 * a1 * cu * cu - 0.5 * a1 * usq));
+        }
+    });
+}
+
+template <int Q, typename S>
+__global__ void init_kernel(S* f, const double* rho, const double* u, long long ncell, int nbatch, long long ps,
+                            long long bs)
+{
+    const long long total = ncell * nbatch;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+        const long long box = t / ncell, c = t - box * ncell;
+        const double r = rho ? rho[t] : 1.0;
+        double geq[Q];
+        equilibrium_g<Q>(r, u[t], u[total + t], u[2 * total + t], geq);
+        S* fb = f + box * bs + c;
+        static_for<Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr double w = weight_of(Q, i);
+            fb[i * ps] = from_f<S>(w + geq[i], w);
+        });
+    }
+}
+
+// rho = sum f, u = (sum f c - F/2)/rho: the post-collision array carries the
+// momentum of time n plus the full force impulse, so the half-force shift is
+// subtracted to report the time-n velocity of Guo forcing.
+template <int Q, typename S>
+__global__ void moments_kernel(const S* f, double* rho, double* u, long long ncell, int nbatch, long long ps,
+                               long long bs, double Fx, double Fy, double Fz)
+{
+    const long long total = ncell * nbatch;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+        const long long box = t / ncell, c = t - box * ncell;
+        const S* fb = f + box * bs + c;
+        double d = 0, jx = 0, jy = 0, jz = 0;
+        static_for<Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
+            constexpr double w = weight_of(Q, i);
+            const double g = to_f<S>(fb[i * ps], w) - w;
+            d += g;
+            jx += cx * g;
+            jy += cy * g;
+            jz += cz * g;
+        });
+        const double r = 1.0 + d;
+        if (rho) rho[t] = r;
+        if (u) {
+            u[t] = (jx - 0.5 * Fx) / r;
+            u[total + t] = (jy - 0.5 * Fy) / r;
+            u[2 * total + t] = (jz - 0.5 * Fz) / r;
+        }
+    }
+}
+
+template <int Q, typename S>
+__global__ void to_f64_kernel(const S* f, double* out, long long ncell, int nbatch, long long ps, long long bs)
+{
+    const long long total = ncell * nbatch;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+        const long long box = t / ncell, c = t - box * ncell;
+        static_for<Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            const long long k = box * bs + i * ps + c;
+            out[k] = to_f<S>(f[k], weight_of(Q, i));
+        });
+    }
+}
+
+template <int Q, typename S>
+__global__ void from_f64_kernel(S* f, const double* in, long long ncell, int nbatch, long long ps, long long bs)
+{
+    const long long total = ncell * nbatch;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+        const long long box = t / ncell, c = t - box * ncell;
+        static_for<Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            const long long k = box * bs + i * ps + c;
+            f[k] = from_f<S>(in[k], weight_of(Q, i));
+        });
+    }
+}
+
+template <int Q, typename S>
+__global__ void probe_kernel(const S* f, const int* xyz, int ncells, int nx, int ny, int nz, long long ps, double* out)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ncells) return;
+    const int x = wrapi(xyz[3 * t], nx), y = wrapi(xyz[3 * t + 1], ny), z = wrapi(xyz[3 * t + 2], nz);
+    const long long c = ((long long)z * ny + y) * nx + x;
+    static_for<Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        out[(long long)t * Q + i] = to_f<S>(f[i * ps + c], weight_of(Q, i));
+    });
+}
+
+int grid_for(long long n, int block)
+{
+    long long g = (n + block - 1) / block;
+    if (g > 152LL * 32) g = 152LL * 32;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+template <typename F>
+cudaError_t dispatch_storage(int storage, F&& f)
+{
+    switch (storage) {
+    case ST_F64: return f((double*)nullptr);
+    case ST_F32: return f((float*)nullptr);
+    case ST_F16S: return f((__half*)nullptr);
+    case ST_BF16S: return f((__nv_bfloat16*)nullptr);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// ------------------------------------------------------------------ diagnostics
+
+constexpr int kDiagBlock = 256;
+constexpr int kDiagVals = 8;
+
+__device__ __forceinline__ double u_at(const double* u, long long N, int comp, int x, int y, int z, int nx, int ny)
+{
+    return u[comp * N + ((long long)z * ny + y) * nx + x];
+}
+
+// d u_comp / d axis at (x,y,z): sixth-order centred on periodic axes
+// (coefficients 3/4, -3/20, 1/60), second-order central / one-sided on wall axes
+__device__ double deriv(const double* u, long long N, int comp, int axis, int x, int y, int z, int nx, int ny, int nz,
+                        const int* bcs)
+{
+    const int n = axis == 0 ? nx : (axis == 1 ? ny : nz);
+    const int p = axis == 0 ? x : (axis == 1 ? y : z);
+    auto at = [&](int k) {
+        int xx = x, yy = y, zz = z;
+        if (axis == 0) xx = k;
+        if (axis == 1) yy = k;
+        if (axis == 2) zz = k;
+        return u_at(u, N, comp, xx, yy, zz, nx, ny);
+    };
+    if (bcs[axis] == 0) {
+        const double c1 = 0.75, c2 = -0.15, c3 = 1.0 / 60.0;
+        return c1 * (at(wrapi(p + 1, n)) - at(wrapi(p - 1, n))) + c2 * (at(wrapi(p + 2, n)) - at(wrapi(p - 2, n))) +
+               c3 * (at(wrapi(p + 3, n)) - at(wrapi(p - 3, n)));
+    }
+    if (p > 0 && p < n - 1) return 0.5 * (at(p + 1) - at(p - 1));
+    if (p == 0) return 0.5 * (-3.0 * at(0) + 4.0 * at(1) - at(2));
+    return 0.5 * (3.0 * at(n - 1) - 4.0 * at(n - 2) + at(n - 3));
+}
+
+struct DiagBC {
+    int b[3];
+};
+
+__global__ void __launch_bounds__(kDiagBlock) diag_kernel(const double* rho, const double* u, int nx, int ny, int nz,
+                                                          DiagBC bc, double* partials)
+{
+    const long long N = (long long)nx * ny * nz;
+    double acc[kDiagVals] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(c % nx);
+        const int y = (int)((c / nx) % ny);
+        const int z = (int)(c / ((long long)nx * ny));
+        const double r = rho[c], ux = u[c], uy = u[N + c], uz = u[2 * N + c];
+        const bool fin = isfinite(r) && isfinite(ux) && isfinite(uy) && isfinite(uz);
+        if (!fin) {
+            acc[6] += 1.0;
+            continue;
+        }
+        acc[0] += r;
+        acc[1] += r * ux;
+        acc[2] += r * uy;
+        acc[3] += r * uz;
+        const double usq = ux * ux + uy * uy + uz * uz;
+        acc[4] += 0.5 * r * usq;
+        const double wx = deriv(u, N, 2, 1, x, y, z, nx, ny, nz, bc.b) - deriv(u, N, 1, 2, x, y, z, nx, ny, nz, bc.b);
+        const double wy = deriv(u, N, 0, 2, x, y, z, nx, ny, nz, bc.b) - deriv(u, N, 2, 0, x, y, z, nx, ny, nz, bc.b);
+        const double wz = deriv(u, N, 1, 0, x, y, z, nx, ny, nz, bc.b) - deriv(u, N, 0, 1, x, y, z, nx, ny, nz, bc.b);
+        acc[5] += 0.5 * (wx * wx + wy * wy + wz * wz);
+        acc[7] = fmax(acc[7], sqrt(usq));
+    }
+    __shared__ double red[kDiagVals][kDiagBlock];
+#pragma unroll
+    for (int k = 0; k < kDiagVals; ++k) red[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int s = kDiagBlock / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+#pragma unroll
+            for (int k = 0; k < kDiagVals; ++k) {
+                if (k == 7)
+                    red[k][threadIdx.x] = fmax(red[k][threadIdx.x], red[k][threadIdx.x + s]);
+                else
+                    red[k][threadIdx.x] += red[k][threadIdx.x + s];
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < kDiagVals) partials[blockIdx.x * kDiagVals + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// single-block, fixed-order (deterministic) sum of the per-block partials
+__global__ void diag_final_kernel(const double* partials, int nblocks, long long N, double* out)
+{
+    __shared__ double red[kDiagVals][kDiagBlock];
+    double acc[kDiagVals] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < kDiagVals; ++k) {
+            const double v = partials[b * kDiagVals + k];
+            acc[k] = (k == 7) ? fmax(acc[k], v) : acc[k] + v;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kDiagVals; ++k) red[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int s = kDiagBlock / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+#pragma unroll
+            for (int k = 0; k < kDiagVals; ++k)
+                red[k][threadIdx.x] = (k == 7) ? fmax(red[k][threadIdx.x], red[k][threadIdx.x + s])
+                                               : red[k][threadIdx.x] + red[k][threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = red[0][0];
+        out[1] = red[1][0];
+        out[2] = red[2][0];
+        out[3] = red[3][0];
+        out[4] = red[4][0] / (double)N;
+        out[5] = red[5][0] / (double)N;
+        out[6] = red[6][0];
+        out[7] = red[7][0];
+    }
+}
+
+int diag_blocks(long long ncell)
+{
+    long long b = (ncell + kDiagBlock - 1) / kDiagBlock;
+    if (b > 152LL * 8) b = 152LL * 8;
+    return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+cudaError_t launch_init_equilibrium(int q, int storage, void* f, const double* rho, const double* u, long long ncell,
+                                    int nbatch, long long ps, long long bs, cudaStream_t s)
+{
+    const int g = grid_for(ncell * nbatch, 256);
+    return dispatch_storage(storage, [&](auto tag) -> cudaError_t {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        if (q == 27)
+            init_kernel<27, S><<<g, 256, 0, s>>>((S*)f, rho, u, ncell, nbatch, ps, bs);
+        else
+            init_kernel<19, S><<<g, 256, 0, s>>>((S*)f, rho, u, ncell, nbatch, ps, bs);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_moments(int q, int storage, const void* f, double* rho, double* u, long long ncell, int nbatch,
+                           long long ps, long long bs, const double* force, cudaStream_t s)
+{
+    const int g = grid_for(ncell * nbatch, 256);
+    return dispatch_storage(storage, [&](auto tag) -> cudaError_t {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        if (q == 27)
+            moments_kernel<27, S><<<g, 256, 0, s>>>((const S*)f, rho, u, ncell, nbatch, ps, bs, force[0], force[1], force[2]);
+        else
+            moments_kernel<19, S><<<g, 256, 0, s>>>((const S*)f, rho, u, ncell, nbatch, ps, bs, force[0], force[1], force[2]);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_to_f64(int q, int storage, const void* f, double* out, long long ncell, int nbatch, long long ps,
+                          long long bs, cudaStream_t s)
+{
+    const int g = grid_for(ncell * nbatch, 256);
+    return dispatch_storage(storage, [&](auto tag) -> cudaError_t {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        if (q == 27)
+            to_f64_kernel<27, S><<<g, 256, 0, s>>>((const S*)f, out, ncell, nbatch, ps, bs);
+        else
+            to_f64_kernel<19, S><<<g, 256, 0, s>>>((const S*)f, out, ncell, nbatch, ps, bs);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_from_f64(int q, int storage, void* f, const double* in, long long ncell, int nbatch, long long ps,
+                            long long bs, cudaStream_t s)
+{
+    const int g = grid_for(ncell * nbatch, 256);
+    return dispatch_storage(storage, [&](auto tag) -> cudaError_t {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        if (q == 27)
+            from_f64_kernel<27, S><<<g, 256, 0, s>>>((S*)f, in, ncell, nbatch, ps, bs);
+        else
+            from_f64_kernel<19, S><<<g, 256, 0, s>>>((S*)f, in, ncell, nbatch, ps, bs);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_probe(int q, int storage, const void* f, const int* xyz, int ncells, int nx, int ny, int nz,
+                         long long ps, double* out, cudaStream_t s)
+{
+    const int g = (ncells + 127) / 128;
+    return dispatch_storage(storage, [&](auto tag) -> cudaError_t {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        if (q == 27)
+            probe_kernel<27, S><<<g, 128, 0, s>>>((const S*)f, xyz, ncells, nx, ny, nz, ps, out);
+        else
+            probe_kernel<19, S><<<g, 128, 0, s>>>((const S*)f, xyz, ncells, nx, ny, nz, ps, out);
+        return cudaGetLastError();
+    });
+}
+
+long long diag_partials_len(long long ncell) { return (long long)diag_blocks(ncell) * kDiagVals; }
+
+cudaError_t launch_diagnostics(const double* rho, const double* u, int nx, int ny, int nz, const int* bc,
+                               double* partials, double* out_dev, cudaStream_t s)
+{
+    const long long N = (long long)nx * ny * nz;
+    const int nb = diag_blocks(N);
+    DiagBC b;
+    for (int k = 0; k < 3; ++k) b.b[k] = bc[k];
+    diag_kernel<<<nb, kDiagBlock, 0, s>>>(rho, u, nx, ny, nz, b, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    diag_final_kernel<<<1, kDiagBlock, 0, s>>>(partials, nb, N, out_dev);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmk

@@ -1,0 +1,519 @@
+// C ABI of liblbm (declared in include/lbm.h): handle lifetime, device
+// buffers, launches of the fused step kernel and of the auxiliary kernels.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+using namespace lbmk;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg)
+{
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+size_t storage_bytes(int storage)
+{
+    switch (storage) {
+    case LBM_FP64: return 8;
+    case LBM_FP32: return 4;
+    case LBM_FP16_SHIFTED:
+    case LBM_BF16_SHIFTED: return 2;
+    }
+    return 0;
+}
+
+}  // namespace
+
+struct lbm_handle {
+    lbm_config cfg;
+    std::vector<double> nu;
+    int q = 0;
+    size_t elem = 0;
+    long long ncell = 0;     // cells per box
+    long long popstride = 0;
+    long long boxstride = 0;
+    size_t buf_bytes = 0;
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;
+    double* d_nu = nullptr;
+    unsigned int* d_flag = nullptr;
+    double* d_rho = nullptr;  // diagnostics scratch (lazy): rho [N], u [3][N] of one box
+    double* d_u = nullptr;
+    double* d_partials = nullptr;
+    double* d_diag = nullptr;
+    cudaStream_t stream = nullptr;
+    int tile_y = 8;
+    int zchunk = 16;
+    int bc_kind = BC_PERIODIC;
+    int64_t steps = 0;
+    int64_t launches = 0;
+};
+
+namespace {
+
+int check_handle(const lbm_handle* h)
+{
+    if (!h) return fail(LBM_ERR_ARG, "null handle");
+    return LBM_OK;
+}
+
+// default z-chunk: enough CTAs to fill the GPU several times over while
+// keeping the march long enough that the two extra halo planes per chunk stay cheap
+int default_zchunk(int nx, int ny, int nz, int nbatch, int tile_y)
+{
+    const long long tiles = (long long)((nx + 31) / 32) * ((ny + tile_y - 1) / tile_y) * nbatch;
+    const long long target = 152LL * 2 * 8;  // ~8 waves of two CTAs per SM
+    long long chunks = (target + tiles - 1) / tiles;
+    long long zc = (nz + chunks - 1) / chunks;
+    if (zc < 4) zc = 4;
+    if (zc > 64) zc = 64;
+    if (zc > nz) zc = nz;
+    return (int)zc;
+}
+
+void free_all(lbm_handle* h)
+{
+    for (int k = 0; k < 2; ++k)
+        if (h->f[k]) cudaFree(h->f[k]);
+    if (h->d_nu) cudaFree(h->d_nu);
+    if (h->d_flag) cudaFree(h->d_flag);
+    if (h->d_rho) cudaFree(h->d_rho);
+    if (h->d_u) cudaFree(h->d_u);
+    if (h->d_partials) cudaFree(h->d_partials);
+    if (h->d_diag) cudaFree(h->d_diag);
+}
+
+int read_flag(lbm_handle* h)
+{
+    unsigned int flag = 0;
+    cudaError_t e = cudaMemcpyAsync(&flag, h->d_flag, sizeof(flag), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the status flag");
+    if (flag) {
+        cudaMemsetAsync(h->d_flag, 0, sizeof(unsigned int), h->stream);
+        cudaStreamSynchronize(h->stream);
+        return fail(LBM_ERR_NONFINITE, "a non-finite density or velocity was produced by a step");
+    }
+    return LBM_OK;
+}
+
+int ensure_diag_scratch(lbm_handle* h)
+{
+    if (h->d_rho) return LBM_OK;
+    const long long N = h->ncell;
+    cudaError_t e = cudaMalloc(&h->d_rho, sizeof(double) * N);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_u, sizeof(double) * 3 * N);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_partials, sizeof(double) * diag_partials_len(N));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_diag, sizeof(double) * 8);
+    if (e != cudaSuccess) {
+        cudaFree(h->d_rho);
+        cudaFree(h->d_u);
+        cudaFree(h->d_partials);
+        cudaFree(h->d_diag);
+        h->d_rho = h->d_u = h->d_partials = h->d_diag = nullptr;
+        cudaGetLastError();
+        return fail(LBM_ERR_OOM, "diagnostics scratch allocation failed");
+    }
+    return LBM_OK;
+}
+
+struct FileHeader {
+    char magic[8];
+    int32_t abi, lattice, nx, ny, nz, nbatch, storage, closure;
+    int64_t steps;
+    uint64_t payload_bytes;
+};
+
+}  // namespace
+
+extern "C" {
+
+void lbm_config_default(lbm_config* cfg)
+{
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->lattice = LBM_D3Q27;
+    cfg->nx = cfg->ny = cfg->nz = 32;
+    cfg->nbatch = 1;
+    cfg->closure = LBM_KCMP;
+    cfg->c_nu = 0.035;
+    cfg->delta = 1.0;
+    cfg->storage = LBM_FP32;
+}
+
+int lbm_abi_version(void) { return LBM_ABI_VERSION; }
+
+const char* lbm_last_error(void) { return g_err.c_str(); }
+
+int lbm_create(const lbm_config* cfg, lbm_handle** out)
+{
+    if (!out) return fail(LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!cfg) return fail(LBM_ERR_ARG, "cfg is NULL");
+    if (cfg->lattice != LBM_D3Q19 && cfg->lattice != LBM_D3Q27) return fail(LBM_ERR_ARG, "lattice must be 19 or 27");
+    if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1 || cfg->nbatch < 1) return fail(LBM_ERR_ARG, "sizes must be >= 1");
+    const long long N = (long long)cfg->nx * cfg->ny * cfg->nz;
+    if (N >= (1LL << 31) - 1) return fail(LBM_ERR_ARG, "a box must hold fewer than 2^31 cells");
+    if (cfg->nbatch > 65535) return fail(LBM_ERR_ARG, "nbatch must be <= 65535");
+    if (!cfg->nu) return fail(LBM_ERR_ARG, "nu is NULL");
+    for (int b = 0; b < cfg->nbatch; ++b)
+        if (!(cfg->nu[b] > 0.0) || !std::isfinite(cfg->nu[b])) return fail(LBM_ERR_ARG, "nu must be finite and > 0");
+    if (cfg->closure < LBM_BGK || cfg->closure > LBM_KCRR) return fail(LBM_ERR_ARG, "unknown closure");
+    if (cfg->closure == LBM_KCRR && cfg->lattice != LBM_D3Q27)
+        return fail(LBM_ERR_UNSUPPORTED, "KC-RR is defined on D3Q27 only");
+    if (!(cfg->c_nu >= 0.0) || !(cfg->delta > 0.0)) return fail(LBM_ERR_ARG, "c_nu must be >= 0 and delta > 0");
+    const size_t elem = storage_bytes(cfg->storage);
+    if (!elem) return fail(LBM_ERR_ARG, "unknown storage");
+    if (cfg->bc[0] != LBM_PERIODIC || cfg->bc[2] != LBM_PERIODIC || (cfg->bc[1] != LBM_PERIODIC && cfg->bc[1] != LBM_BOUNCEBACK))
+        return fail(LBM_ERR_UNSUPPORTED, "bounce-back walls are supported on the y axis only");
+    const int bc_kind = cfg->bc[1] == LBM_BOUNCEBACK ? BC_WALLS_Y : BC_PERIODIC;
+    if (bc_kind == BC_WALLS_Y && cfg->ny < 3) return fail(LBM_ERR_ARG, "a bounce-back axis needs >= 3 cells");
+    const bool has_force = cfg->force[0] != 0.0 || cfg->force[1] != 0.0 || cfg->force[2] != 0.0;
+    if (has_force && bc_kind != BC_WALLS_Y)
+        return fail(LBM_ERR_UNSUPPORTED, "a body force is supported with bounce-back walls (channel) only");
+    int tile_y = cfg->tile_y ? cfg->tile_y : 8;
+    if (!step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y))
+        return fail(LBM_ERR_UNSUPPORTED, "this lattice/storage/closure/boundary/tile combination is not built");
+    if (cfg->zchunk < 0) return fail(LBM_ERR_ARG, "zchunk must be >= 0");
+
+    lbm_handle* h = new (std::nothrow) lbm_handle();
+    if (!h) return fail(LBM_ERR_OOM, "host allocation failed");
+    h->cfg = *cfg;
+    h->nu.assign(cfg->nu, cfg->nu + cfg->nbatch);
+    h->cfg.nu = nullptr;
+    h->q = cfg->lattice;
+    h->elem = elem;
+    h->ncell = N;
+    h->popstride = N;
+    h->boxstride = (long long)h->q * N;
+    h->buf_bytes = elem * (size_t)h->boxstride * (size_t)cfg->nbatch;
+    h->stream = (cudaStream_t)cfg->cuda_stream;
+    h->tile_y = tile_y;
+    h->zchunk = cfg->zchunk ? cfg->zchunk : default_zchunk(cfg->nx, cfg->ny, cfg->nz, cfg->nbatch, tile_y);
+    h->bc_kind = bc_kind;
+
+    cudaError_t e = cudaMalloc(&h->f[0], h->buf_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&h->f[1], h->buf_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_nu, sizeof(double) * cfg->nbatch);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_flag, sizeof(unsigned int));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_all(h);
+        delete h;
+        return fail(e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,
+                    std::string("device allocation failed: ") + cudaGetErrorString(e));
+    }
+    e = cudaMemcpyAsync(h->d_nu, h->nu.data(), sizeof(double) * cfg->nbatch, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flag, 0, sizeof(unsigned int), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->f[0], 0, h->buf_bytes, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        free_all(h);
+        delete h;
+        return cuda_fail(e, "lbm_create");
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_handle* h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+int lbm_init_velocity_device(lbm_handle* h, const double* rho_dev, const double* u_dev)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!u_dev) return fail(LBM_ERR_ARG, "u is NULL");
+    cudaError_t e = launch_init_equilibrium(h->q, h->cfg.storage, h->f[h->cur], rho_dev, u_dev, h->ncell,
+                                            h->cfg.nbatch, h->popstride, h->boxstride, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "init kernel");
+    h->launches++;
+    h->steps = 0;
+    return LBM_OK;
+}
+
+int lbm_init_velocity(lbm_handle* h, const double* rho, const double* u)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!u) return fail(LBM_ERR_ARG, "u is NULL");
+    const size_t n = (size_t)h->ncell * h->cfg.nbatch;
+    double *d_rho = nullptr, *d_u = nullptr;
+    cudaError_t e = cudaMalloc(&d_u, sizeof(double) * 3 * n);
+    if (e == cudaSuccess && rho) e = cudaMalloc(&d_rho, sizeof(double) * n);
+    if (e != cudaSuccess) {
+        cudaFree(d_u);
+        cudaGetLastError();
+        return fail(LBM_ERR_OOM, "staging allocation failed");
+    }
+    e = cudaMemcpyAsync(d_u, u, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && rho) e = cudaMemcpyAsync(d_rho, rho, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream);
+    int rc = LBM_OK;
+    if (e != cudaSuccess)
+        rc = cuda_fail(e, "copying the initial fields");
+    else
+        rc = lbm_init_velocity_device(h, d_rho, d_u);
+    e = cudaStreamSynchronize(h->stream);
+    cudaFree(d_u);
+    cudaFree(d_rho);
+    if (rc == LBM_OK && e != cudaSuccess) rc = cuda_fail(e, "lbm_init_velocity");
+    return rc;
+}
+
+int lbm_step(lbm_handle* h, int nsteps)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (nsteps < 0) return fail(LBM_ERR_ARG, "nsteps must be >= 0");
+    StepArgs a;
+    a.nx = h->cfg.nx;
+    a.ny = h->cfg.ny;
+    a.nz = h->cfg.nz;
+    a.zchunk = h->zchunk;
+    a.plane = (long long)h->cfg.nx * h->cfg.ny;
+    a.popstride = h->popstride;
+    a.boxstride = h->boxstride;
+    a.box_nu = h->d_nu;
+    a.cnu_delta = h->cfg.c_nu * h->cfg.delta;
+    for (int k = 0; k < 3; ++k) a.force[k] = h->cfg.force[k];
+    a.flag = h->d_flag;
+    for (int s = 0; s < nsteps; ++s) {
+        a.fin = h->f[h->cur];
+        a.fout = h->f[h->cur ^ 1];
+        cudaError_t e = launch_step(h->q, h->cfg.storage, h->cfg.closure, h->bc_kind, h->tile_y, a, h->cfg.nbatch,
+                                    h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+        h->cur ^= 1;
+        h->steps++;
+        h->launches++;
+    }
+    return LBM_OK;
+}
+
+int lbm_moments_device(lbm_handle* h, double* rho_dev, double* u_dev)
+{
+    if (int rc = check_handle(h)) return rc;
+    cudaError_t e = launch_moments(h->q, h->cfg.storage, h->f[h->cur], rho_dev, u_dev, h->ncell, h->cfg.nbatch,
+                                   h->popstride, h->boxstride, h->cfg.force, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "moments kernel");
+    h->launches++;
+    return LBM_OK;
+}
+
+int lbm_moments(lbm_handle* h, double* rho, double* u)
+{
+    if (int rc = check_handle(h)) return rc;
+    const size_t n = (size_t)h->ncell * h->cfg.nbatch;
+    double *d_rho = nullptr, *d_u = nullptr;
+    cudaError_t e = cudaMalloc(&d_rho, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&d_u, sizeof(double) * 3 * n);
+    if (e != cudaSuccess) {
+        cudaFree(d_rho);
+        cudaGetLastError();
+        return fail(LBM_ERR_OOM, "staging allocation failed");
+    }
+    int rc = lbm_moments_device(h, d_rho, d_u);
+    if (rc == LBM_OK) {
+        e = cudaSuccess;
+        if (rho) e = cudaMemcpyAsync(rho, d_rho, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, d_u, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "copying the fields back");
+    }
+    cudaStreamSynchronize(h->stream);
+    cudaFree(d_rho);
+    cudaFree(d_u);
+    if (rc == LBM_OK) rc = read_flag(h);
+    return rc;
+}
+
+int lbm_diagnostics(lbm_handle* h, int box, double out[8])
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!out) return fail(LBM_ERR_ARG, "out is NULL");
+    if (box < 0 || box >= h->cfg.nbatch) return fail(LBM_ERR_ARG, "box out of range");
+    if (int rc = ensure_diag_scratch(h)) return rc;
+    const char* fb = static_cast<const char*>(h->f[h->cur]) + (size_t)box * h->boxstride * h->elem;
+    cudaError_t e = launch_moments(h->q, h->cfg.storage, fb, h->d_rho, h->d_u, h->ncell, 1, h->popstride,
+                                   h->boxstride, h->cfg.force, h->stream);
+    if (e == cudaSuccess)
+        e = launch_diagnostics(h->d_rho, h->d_u, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->cfg.bc, h->d_partials, h->d_diag,
+                               h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, h->d_diag, sizeof(double) * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "diagnostics");
+    h->launches += 3;
+    int rc = read_flag(h);
+    if (rc == LBM_OK && out[6] > 0) rc = fail(LBM_ERR_NONFINITE, "non-finite cells in the diagnosed box");
+    return rc;
+}
+
+int lbm_get_populations(lbm_handle* h, double* f)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!f) return fail(LBM_ERR_ARG, "f is NULL");
+    const size_t n = (size_t)h->boxstride * h->cfg.nbatch;
+    double* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(double) * n);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ERR_OOM, "staging allocation failed");
+    }
+    e = launch_to_f64(h->q, h->cfg.storage, h->f[h->cur], d, h->ncell, h->cfg.nbatch, h->popstride, h->boxstride,
+                      h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f, d, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_get_populations");
+    h->launches++;
+    return LBM_OK;
+}
+
+int lbm_set_populations(lbm_handle* h, const double* f)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!f) return fail(LBM_ERR_ARG, "f is NULL");
+    const size_t n = (size_t)h->boxstride * h->cfg.nbatch;
+    double* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(double) * n);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ERR_OOM, "staging allocation failed");
+    }
+    e = cudaMemcpyAsync(d, f, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = launch_from_f64(h->q, h->cfg.storage, h->f[h->cur], d, h->ncell, h->cfg.nbatch, h->popstride, h->boxstride,
+                            h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_set_populations");
+    h->launches++;
+    h->steps = 0;
+    return LBM_OK;
+}
+
+int lbm_probe(lbm_handle* h, int box, const int* xyz, int ncells, double* out)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (box < 0 || box >= h->cfg.nbatch) return fail(LBM_ERR_ARG, "box out of range");
+    if (ncells < 0 || (ncells > 0 && (!xyz || !out))) return fail(LBM_ERR_ARG, "bad probe arguments");
+    if (ncells == 0) return LBM_OK;
+    int* d_xyz = nullptr;
+    double* d_out = nullptr;
+    cudaError_t e = cudaMalloc(&d_xyz, sizeof(int) * 3 * ncells);
+    if (e == cudaSuccess) e = cudaMalloc(&d_out, sizeof(double) * h->q * ncells);
+    if (e != cudaSuccess) {
+        cudaFree(d_xyz);
+        cudaGetLastError();
+        return fail(LBM_ERR_OOM, "probe staging allocation failed");
+    }
+    const char* fb = static_cast<const char*>(h->f[h->cur]) + (size_t)box * h->boxstride * h->elem;
+    e = cudaMemcpyAsync(d_xyz, xyz, sizeof(int) * 3 * ncells, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = launch_probe(h->q, h->cfg.storage, fb, d_xyz, ncells, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->popstride, d_out,
+                         h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, sizeof(double) * h->q * ncells, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(d_xyz);
+    cudaFree(d_out);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_probe");
+    h->launches++;
+    return LBM_OK;
+}
+
+int lbm_population_buffer(lbm_handle* h, const void** ptr, int* elem_bytes)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (ptr) *ptr = h->f[h->cur];
+    if (elem_bytes) *elem_bytes = (int)h->elem;
+    return LBM_OK;
+}
+
+int lbm_synchronize(lbm_handle* h)
+{
+    if (int rc = check_handle(h)) return rc;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_synchronize");
+    return read_flag(h);
+}
+
+int lbm_save(lbm_handle* h, const char* path)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!path) return fail(LBM_ERR_ARG, "path is NULL");
+    std::vector<char> buf(h->buf_bytes);
+    cudaError_t e = cudaMemcpyAsync(buf.data(), h->f[h->cur], h->buf_bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_save");
+    FileHeader hd;
+    std::memset(&hd, 0, sizeof(hd));
+    std::memcpy(hd.magic, "LBMKC01", 8);
+    hd.abi = LBM_ABI_VERSION;
+    hd.lattice = h->cfg.lattice;
+    hd.nx = h->cfg.nx;
+    hd.ny = h->cfg.ny;
+    hd.nz = h->cfg.nz;
+    hd.nbatch = h->cfg.nbatch;
+    hd.storage = h->cfg.storage;
+    hd.closure = h->cfg.closure;
+    hd.steps = h->steps;
+    hd.payload_bytes = h->buf_bytes;
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return fail(LBM_ERR_IO, std::string("cannot open ") + path);
+    bool ok = std::fwrite(&hd, sizeof(hd), 1, fp) == 1 && std::fwrite(buf.data(), 1, buf.size(), fp) == buf.size();
+    ok = (std::fclose(fp) == 0) && ok;
+    return ok ? LBM_OK : fail(LBM_ERR_IO, std::string("write failed: ") + path);
+}
+
+int lbm_load(lbm_handle* h, const char* path)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!path) return fail(LBM_ERR_ARG, "path is NULL");
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return fail(LBM_ERR_IO, std::string("cannot open ") + path);
+    FileHeader hd;
+    bool ok = std::fread(&hd, sizeof(hd), 1, fp) == 1;
+    ok = ok && std::memcmp(hd.magic, "LBMKC01", 8) == 0 && hd.lattice == h->cfg.lattice && hd.nx == h->cfg.nx &&
+         hd.ny == h->cfg.ny && hd.nz == h->cfg.nz && hd.nbatch == h->cfg.nbatch && hd.storage == h->cfg.storage &&
+         hd.payload_bytes == h->buf_bytes;
+    std::vector<char> buf;
+    if (ok) {
+        buf.resize(h->buf_bytes);
+        ok = std::fread(buf.data(), 1, buf.size(), fp) == buf.size();
+    }
+    std::fclose(fp);
+    if (!ok) return fail(LBM_ERR_IO, std::string("file does not match this solver: ") + path);
+    cudaError_t e = cudaMemcpyAsync(h->f[h->cur], buf.data(), h->buf_bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_load");
+    h->steps = hd.steps;
+    return LBM_OK;
+}
+
+int64_t lbm_step_count(const lbm_handle* h) { return h ? h->steps : -1; }
+
+int64_t lbm_kernel_launches(const lbm_handle* h) { return h ? h->launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,52 @@
+// Internal declarations shared by the CUDA translation units of liblbm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmk {
+
+enum Closure { CL_BGK = 0, CL_KCMP = 1, CL_KCRB_H = 2, CL_KCRB_RAW = 3, CL_KCRR = 4 };
+enum Storage { ST_F64 = 0, ST_F32 = 1, ST_F16S = 2, ST_BF16S = 3 };
+enum Boundary { BC_PERIODIC = 0, BC_WALLS_Y = 1 };
+
+// Arguments of one fused step launch (all boxes of the ensemble).
+struct StepArgs {
+    const void* fin;        // post-collision populations of the previous step
+    void* fout;             // post-collision populations of this step
+    int nx, ny, nz;
+    int zchunk;             // z-planes marched by one CTA
+    long long plane;        // nx*ny
+    long long popstride;    // nx*ny*nz elements between populations
+    long long boxstride;    // q*popstride elements between boxes
+    const double* box_nu;   // [nbatch] kinematic viscosity
+    double cnu_delta;       // C_nu * Delta
+    double force[3];        // body force density (channel); zero otherwise
+    unsigned int* flag;     // bit 0: non-finite density/velocity seen
+};
+
+// Host-side launchers (lbm_step_*.cu).  Return cudaSuccess or the launch error.
+// tile_y selects the CTA tile height (instantiated values: 4, 8, 16).
+cudaError_t launch_step(int q, int storage, int closure, int bc, int tile_y, const StepArgs& a, int nbatch,
+                        cudaStream_t s);
+bool step_supported(int q, int storage, int closure, int bc, int tile_y);
+
+// Auxiliary kernels (lbm_aux.cu).
+cudaError_t launch_init_equilibrium(int q, int storage, void* f, const double* rho, const double* u, long long ncell,
+                                    int nbatch, long long popstride, long long boxstride, cudaStream_t s);
+cudaError_t launch_moments(int q, int storage, const void* f, double* rho, double* u, long long ncell, int nbatch,
+                           long long popstride, long long boxstride, const double* force, cudaStream_t s);
+cudaError_t launch_to_f64(int q, int storage, const void* f, double* out, long long ncell, int nbatch,
+                          long long popstride, long long boxstride, cudaStream_t s);
+cudaError_t launch_from_f64(int q, int storage, void* f, const double* in, long long ncell, int nbatch,
+                            long long popstride, long long boxstride, cudaStream_t s);
+cudaError_t launch_probe(int q, int storage, const void* f, const int* xyz, int ncells, int nx, int ny, int nz,
+                         long long ps, double* out, cudaStream_t s);
+// Diagnostics of one box: u must hold that box's FP64 velocity [3][N] and rho
+// its density; writes 8 doubles to out_dev (see lbm_diagnostics).
+// partials: scratch of diag_partials_len(ncell) doubles.
+long long diag_partials_len(long long ncell);
+cudaError_t launch_diagnostics(const double* rho, const double* u, int nx, int ny, int nz, const int* bc,
+                               double* partials, double* out_dev, cudaStream_t s);
+
+}  // namespace lbmk

@@ -1,0 +1,553 @@
+// Fused stream-and-collide step of the kinetic-closure LES solver (sm_103a).
+//
+// One launch advances every cell of every box by one time step:
+//   pull streaming (Eq. streaming, periodic or halfway bounce-back in y)
+//   -> rho, u from the streamed populations (App. F.1 step 1)
+//   -> equilibrium (Eq. discrete_equilibrium; D3Q19: second-order Hermite)
+//   -> strain rate from the neighbours' velocities (Eqs. fd, strain_rate_discrete,
+//      one-sided Eqs. fd_boundary_lower/upper at walls)
+//   -> closure carrier and SGS trace (KC-MP App. F.3, KC-RB App. F.2)
+//   -> clipped turbulent rate (Eq. omega_sgs_operational)
+//   -> two-rate relaxation (Eq. kcmp_operational_collision / kcrb_operational_collision)
+//   -> store of the post-collision populations.
+//
+// Data layout: structure of arrays [box][q][z][y][x], x fastest.  Ping-pong
+// buffers: the kernel reads buffer A and writes buffer B.
+//
+// Parallel decomposition: a CTA owns a 32 x TY column of cells and marches it
+// through a chunk of z-planes.  The strain rate needs the velocity of the
+// x, y and z neighbours at the SAME (post-streaming) time level, so the CTA
+// keeps a ring of four velocity planes in shared memory covering its tile plus
+// a one-cell (two-cell along a wall axis) halo.  At plane k it pulls plane k+1
+// (its own cells and the halo cells), publishes their velocities to the ring,
+// synchronises once, and collides plane k with the populations pulled in the
+// previous iteration (held in registers).  Four ring slots make a single
+// barrier per plane sufficient.
+//
+// Arithmetic runs on the weight-shifted populations g_i = f_i - w_i, which
+// keeps the moment sums free of the O(1) cancellation (sum w_i = 1,
+// sum w_i c_i c_i = theta I are exact); the relaxation is affine so the shift
+// cancels in every difference.  FP16/BF16 storage holds g_i directly.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <utility>
+
+#include "lbm_internal.h"
+#include "lbm_lattice.cuh"
+
+namespace lbmk {
+
+// ---------------------------------------------------------------- utilities
+
+template <typename F, int... Is>
+__device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, Is...>)
+{
+    (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F&& f)
+{
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+template <typename S>
+struct StoreTraits;
+template <>
+struct StoreTraits<double> {
+    using R = double;
+    static constexpr bool shifted = false;
+};
+template <>
+struct StoreTraits<float> {
+    using R = float;
+    static constexpr bool shifted = false;
+};
+template <>
+struct StoreTraits<__half> {
+    using R = float;
+    static constexpr bool shifted = true;
+};
+template <>
+struct StoreTraits<__nv_bfloat16> {
+    using R = float;
+    static constexpr bool shifted = true;
+};
+
+// returns g = f - w
+template <typename S, typename R>
+__device__ __forceinline__ R load_g(const S* p, R w);
+template <>
+__device__ __forceinline__ double load_g<double, double>(const double* p, double w)
+{
+    return __ldg(p) - w;
+}
+template <>
+__device__ __forceinline__ float load_g<float, float>(const float* p, float w)
+{
+    return __ldg(p) - w;
+}
+template <>
+__device__ __forceinline__ float load_g<__half, float>(const __half* p, float)
+{
+    return __half2float(__ldg(p));
+}
+template <>
+__device__ __forceinline__ float load_g<__nv_bfloat16, float>(const __nv_bfloat16* p, float)
+{
+    return __bfloat162float(__ldg(p));
+}
+
+template <typename S, typename R>
+__device__ __forceinline__ void store_g(S* p, R g, R w);
+template <>
+__device__ __forceinline__ void store_g<double, double>(double* p, double g, double w)
+{
+    *p = g + w;
+}
+template <>
+__device__ __forceinline__ void store_g<float, float>(float* p, float g, float w)
+{
+    *p = g + w;
+}
+template <>
+__device__ __forceinline__ void store_g<__half, float>(__half* p, float g, float)
+{
+    *p = __float2half_rn(g);
+}
+template <>
+__device__ __forceinline__ void store_g<__nv_bfloat16, float>(__nv_bfloat16* p, float g, float)
+{
+    *p = __float2bfloat16_rn(g);
+}
+
+__device__ __forceinline__ int wrapi(int a, int n)
+{
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
+// A column of cells (fixed x, y) that the CTA pulls plane after plane.
+// xs: x-1, x, x+1 (periodic); yr: row offsets of y-1, y, y+1, or -1 where the
+// row lies beyond a wall.
+struct Col {
+    int xs[3];
+    int yr[3];
+    bool valid;
+};
+
+template <int BC>
+__device__ __forceinline__ Col make_col(int gx, int gy, int nx, int ny)
+{
+    Col c;
+    gx = wrapi(gx, nx);
+    c.xs[0] = gx == 0 ? nx - 1 : gx - 1;
+    c.xs[1] = gx;
+    c.xs[2] = gx == nx - 1 ? 0 : gx + 1;
+    if (BC == BC_WALLS_Y) {
+        c.valid = gy >= 0 && gy < ny;
+        const int y = c.valid ? gy : 0;
+        c.yr[0] = y > 0 ? (y - 1) * nx : -1;
+        c.yr[1] = y * nx;
+        c.yr[2] = y < ny - 1 ? (y + 1) * nx : -1;
+    } else {
+        c.valid = true;
+        const int y = wrapi(gy, ny);
+        c.yr[0] = (y == 0 ? ny - 1 : y - 1) * nx;
+        c.yr[1] = y * nx;
+        c.yr[2] = (y == ny - 1 ? 0 : y + 1) * nx;
+    }
+    return c;
+}
+
+// Pull the Q streamed populations of cell (col, plane zr[1]) as g = f - w:
+// g_i(x) = g_post_i(x - c_i); beyond a y wall, halfway bounce-back
+// g_i(x) = g_post_opp(i)(x).  Cell offsets are 32-bit (a box holds fewer
+// than 2^31 cells); the population offset i*ps is 64-bit.
+template <int Q, typename S, typename R, int BC>
+__device__ __forceinline__ void pull(const S* __restrict__ fin, long long ps, const Col& col, const int (&zr)[3],
+                                     R (&g)[Q])
+{
+    static_for<Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
+        constexpr int io = opp_of(Q, i);
+        const R w = (R)weight_of(Q, i);
+        if (BC == BC_WALLS_Y && cy != 0) {
+            const int row = col.yr[1 - cy];
+            const S* src = row >= 0 ? fin + (long long)i * ps + (zr[1 - cz] + row + col.xs[1 - cx])
+                                    : fin + (long long)io * ps + (zr[1] + col.yr[1] + col.xs[1]);
+            g[i] = load_g<S, R>(src, w);
+        } else {
+            g[i] = load_g<S, R>(fin + (long long)i * ps + (zr[1 - cz] + col.yr[1 - cy] + col.xs[1 - cx]), w);
+        }
+    });
+}
+
+// rho = 1 + sum g, j = sum g c (sum w c = 0), u = (j + F/2)/rho
+template <int Q, typename R>
+__device__ __forceinline__ void moments(const R (&g)[Q], R& rho, R& ux, R& uy, R& uz, R Fx, R Fy, R Fz)
+{
+    R d = 0, jx = 0, jy = 0, jz = 0;
+    static_for<Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
+        d += g[i];
+        if (cx == 1) jx += g[i];
+        if (cx == -1) jx -= g[i];
+        if (cy == 1) jy += g[i];
+        if (cy == -1) jy -= g[i];
+        if (cz == 1) jz += g[i];
+        if (cz == -1) jz -= g[i];
+    });
+    rho = R(1) + d;
+    const R inv = R(1) / rho;
+    ux = (jx + R(0.5) * Fx) * inv;
+    uy = (jy + R(0.5) * Fy) * inv;
+    uz = (jz + R(0.5) * Fz) * inv;
+}
+
+// Eq. (omega_sgs_operational): k = |tr m_sgs|/(2 rho_0), rho_0 = 1;
+// omega_s = (nu_t/theta + 1/2)^-1 if nu_t = C_nu Delta sqrt(k) > nu, else omega.
+template <typename R>
+__device__ __forceinline__ R omega_sgs(R tr, R nu, R omega, R cnud)
+{
+    const R nut = cnud * sqrt(R(0.5) * fabs(tr));
+    return nut > nu ? R(1) / (nut * R(1.0 / kTheta) + R(0.5)) : omega;
+}
+
+// One-cell collision on shifted populations g (in place -> g_post).
+template <int Q, typename R, int CL, bool FORCE>
+__device__ __forceinline__ void collide(R (&g)[Q], R rho, R ux, R uy, R uz, R Sxx, R Syy, R Szz, R Sxy, R Sxz,
+                                        R Syz, R omega, R tau_hat, R nu, R cnud, R Fx, R Fy, R Fz)
+{
+    constexpr R th = R(kTheta);
+    const R drho = rho - R(1);
+    // equilibrium factors: D3Q27 product of D1Q3 truncations,
+    // 1 + c u/theta + (c^2 - theta) u^2/(2 theta^2)
+    constexpr R a1 = R(1.0 / kTheta);
+    constexpr R a2 = R((1.0 - kTheta) / (2.0 * kTheta * kTheta));
+    constexpr R a0 = R(-kTheta / (2.0 * kTheta * kTheta));
+    const R ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+    const R px0 = R(1) + a0 * ux2, pxp = R(1) + a1 * ux + a2 * ux2, pxm = R(1) - a1 * ux + a2 * ux2;
+    const R py0 = R(1) + a0 * uy2, pyp = R(1) + a1 * uy + a2 * uy2, pym = R(1) - a1 * uy + a2 * uy2;
+    const R pz0 = R(1) + a0 * uz2, pzp = R(1) + a1 * uz + a2 * uz2, pzm = R(1) - a1 * uz + a2 * uz2;
+    const R usq = ux2 + uy2 + uz2;
+
+    // g_eq,i = f0_i - w_i
+    auto geq = [&](auto I) -> R {
+        constexpr int i = decltype(I)::value;
+        constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
+        constexpr R w = R(weight_of(Q, i));
+        if constexpr (Q == 27) {
+            const R px = cx == 0 ? px0 : (cx > 0 ? pxp : pxm);
+            const R py = cy == 0 ? py0 : (cy > 0 ? pyp : pym);
+            const R pz = cz == 0 ? pz0 : (cz > 0 ? pzp : pzm);
+            return w * (rho * (px * py * pz) - R(1));
+        } else {
+            const R cu = R(cx) * ux + R(cy) * uy + R(cz) * uz;
+            return w * (drho + rho * (a1 * cu + R(0.5) * a1 * a1 * cu * cu - R(0.5) * a1 * usq));
+        }
+    };
+
+    R omega_s = omega;
+    if constexpr (CL == CL_BGK) {
+        static_for<Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            g[i] = g[i] - omega * (g[i] - geq(I));
+        });
+    } else {
+        // second moments of g: Pi'_ab = sum g c_a c_b = Pi_ab - theta delta_ab
+        R pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+        static_for<Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
+            if (cx != 0) pxx += g[i];
+            if (cy != 0) pyy += g[i];
+            if (cz != 0) pzz += g[i];
+            if (cx * cy == 1) pxy += g[i];
+            if (cx * cy == -1) pxy -= g[i];
+            if (cx * cz == 1) pxz += g[i];
+            if (cx * cz == -1) pxz -= g[i];
+            if (cy * cz == 1) pyz += g[i];
+            if (cy * cz == -1) pyz -= g[i];
+        });
+        if constexpr (CL == CL_KCMP) {
+            // m_neq = Pi - rho(uu + theta I) = Pi' - rho uu - theta drho I   (App. F.3)
+            // m_CE = -2 rho theta tau_hat S;  m_sgs = m_neq - m_CE
+            const R rt = R(-2) * rho * th * tau_hat;
+            const R mxx = pxx - rho * ux2 - th * drho - rt * Sxx;
+            const R myy = pyy - rho * uy2 - th * drho - rt * Syy;
+            const R mzz = pzz - rho * uz2 - th * drho - rt * Szz;
+            const R mxy = pxy - rho * ux * uy - rt * Sxy;
+            const R mxz = pxz - rho * ux * uz - rt * Sxz;
+            const R myz = pyz - rho * uy * uz - rt * Syz;
+            const R tr = mxx + myy + mzz;
+            omega_s = omega_sgs(tr, nu, omega, cnud);
+            // f_post = f - omega (f - f0 - f_sgs) - omega_s f_sgs,
+            // f_sgs = w/(2 theta^2) H : m_sgs
+            const R dom = (omega - omega_s) * R(1.0 / (2.0 * kTheta * kTheta));
+            const R thtr = th * tr;
+            static_for<Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
+                constexpr R w = R(weight_of(Q, i));
+                R hm = -thtr;
+                if (cx != 0) hm += mxx;
+                if (cy != 0) hm += myy;
+                if (cz != 0) hm += mzz;
+                if (cx * cy != 0) hm += R(2 * cx * cy) * mxy;
+                if (cx * cz != 0) hm += R(2 * cx * cz) * mxz;
+                if (cy * cz != 0) hm += R(2 * cy * cz) * myz;
+                g[i] = g[i] - omega * (g[i] - geq(I)) + (w * dom) * hm;
+            });
+        } else {  // KC-RB, Hermite or raw first-order reconstruction (App. F.2)
+            constexpr bool herm = (CL == CL_KCRB_H);
+            const R trS = Sxx + Syy + Szz;
+            // sum_i f1_i |c_i|^2 = -2 rho tau_hat theta trS (Hermite), -5 rho tau_hat theta trS (raw)
+            const R trf1 = R(herm ? -2 : -5) * rho * tau_hat * th * trS;
+            // tr m_sgs = sum (f - f0 - f1)|c|^2 = tr Pi' - rho |u|^2 - 3 theta drho - tr f1
+            const R tr = (pxx + pyy + pzz) - rho * usq - R(3) * th * drho - trf1;
+            omega_s = omega_sgs(tr, nu, omega, cnud);
+            const R pre = -rho * tau_hat * R(1.0 / kTheta);
+            const R sub = herm ? th * trS : R(0);
+            static_for<Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
+                constexpr R w = R(weight_of(Q, i));
+                R cs = -sub;
+                if (cx != 0) cs += Sxx;
+                if (cy != 0) cs += Syy;
+                if (cz != 0) cs += Szz;
+                if (cx * cy != 0) cs += R(2 * cx * cy) * Sxy;
+                if (cx * cz != 0) cs += R(2 * cx * cz) * Sxz;
+                if (cy * cz != 0) cs += R(2 * cy * cz) * Syz;
+                const R f1 = (w * pre) * cs;
+                g[i] = g[i] - omega * f1 - omega_s * (g[i] - geq(I) - f1);
+            });
+        }
+    }
+    if constexpr (FORCE) {
+        // Guo source (1 - omega/2) w [(c - u)/theta + (c.u) c/theta^2] . F
+        const R pref = R(1) - R(0.5) * omega;
+        const R uF = ux * Fx + uy * Fy + uz * Fz;
+        static_for<Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
+            constexpr R w = R(weight_of(Q, i));
+            const R cF = R(cx) * Fx + R(cy) * Fy + R(cz) * Fz;
+            const R cu = R(cx) * ux + R(cy) * uy + R(cz) * uz;
+            g[i] += pref * w * ((cF - uF) * a1 + cu * cF * (a1 * a1));
+        });
+    }
+}
+
+// ------------------------------------------------------------------ kernel
+
+// Shared-memory footprint of one CTA: the velocity ring (4 planes x 3
+// components x ring cells) and a two-slot stash of the own column's streamed
+// populations (the next plane is parked there while the current one collides,
+// so only one plane of populations is ever live in registers).
+template <int Q, typename R, int BC, int TY>
+struct StepShape {
+    static constexpr int TX = 32;
+    static constexpr int HY = (BC == BC_WALLS_Y) ? 2 : 1;  // ring halo rows (two for one-sided wall stencils)
+    static constexpr int RX = TX + 2;
+    static constexpr int RY = TY + 2 * HY;
+    static constexpr int RN = RX * RY;
+    static constexpr int NT = TX * TY;
+    static constexpr int NB = RN - NT;  // halo cells of the ring plane
+    static constexpr size_t smem_bytes = sizeof(R) * (size_t)(4 * 3 * RN + 2 * Q * NT);
+};
+
+template <int Q, typename S, int CL, int BC, int TY>
+__global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) == 8 || TY >= 16) ? 1 : 2)
+    step_kernel(const StepArgs a)
+{
+    using R = typename StoreTraits<S>::R;
+    using Sh = StepShape<Q, R, BC, TY>;
+    constexpr int TX = Sh::TX, HY = Sh::HY, RX = Sh::RX, RN = Sh::RN, NT = Sh::NT, NB = Sh::NB;
+    static_assert(NB <= NT, "every halo cell of the ring needs a thread");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* ring = reinterpret_cast<R*>(smem_raw);  // [4][3][RN]
+    R* stash = ring + 4 * 3 * RN;              // [2][Q][NT]
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int tiles_x = (nx + TX - 1) / TX;
+    const int x0 = (int)(blockIdx.x % tiles_x) * TX;
+    const int y0 = (int)(blockIdx.x / tiles_x) * TY;
+    const int z0 = (int)blockIdx.y * a.zchunk;
+    if (z0 >= nz) return;  // uniform over the CTA
+    const int z1 = min(nz, z0 + a.zchunk);
+    const int box = blockIdx.z;
+    const long long ps = a.popstride;
+    const int plane = (int)a.plane;
+    const S* __restrict__ fin = static_cast<const S*>(a.fin) + (long long)box * a.boxstride;
+    S* __restrict__ fout = static_cast<S*>(a.fout) + (long long)box * a.boxstride;
+
+    const double nu_d = a.box_nu[box];
+    const R nu = (R)nu_d;
+    const R tau_hat = (R)(nu_d / kTheta + 0.5);
+    const R omega = (R)(1.0 / (nu_d / kTheta + 0.5));
+    const R cnud = (R)a.cnu_delta;
+    constexpr bool FORCE = (BC == BC_WALLS_Y);
+    const R Fx = FORCE ? (R)a.force[0] : R(0), Fy = FORCE ? (R)a.force[1] : R(0), Fz = FORCE ? (R)a.force[2] : R(0);
+
+    // own column; lanes beyond nx wrap (periodic x) and are not stored
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool own_store = gx < nx && gy < ny;
+    const Col own = make_col<BC>(gx, gy, nx, ny);
+    const int own_r = (ty + HY) * RX + (tx + 1);
+
+    // halo column of this thread (ring cells outside the 32 x TY interior)
+    Col hal = own;
+    int hal_r = -1;
+    if (tid < NB) {
+        int lx, ly;
+        int b = tid;
+        if (b < HY * RX) {
+            lx = b % RX - 1;
+            ly = b / RX - HY;
+        } else if ((b -= HY * RX) < HY * RX) {
+            lx = b % RX - 1;
+            ly = TY + b / RX;
+        } else {
+            b -= HY * RX;
+            lx = (b < TY) ? -1 : TX;
+            ly = b % TY;
+        }
+        hal = make_col<BC>(x0 + lx, y0 + ly, nx, ny);
+        hal_r = (ly + HY) * RX + (lx + 1);
+    }
+
+    auto zrows = [&](int z, int (&zr)[3]) {
+        const int zc = wrapi(z, nz);
+        zr[0] = (zc == 0 ? nz - 1 : zc - 1) * plane;
+        zr[1] = zc * plane;
+        zr[2] = (zc == nz - 1 ? 0 : zc + 1) * plane;
+    };
+    auto rslot = [&](int z) { return (z - z0 + 1) & 3; };
+    auto ringp = [&](int s, int c) { return ring + (s * 3 + c) * RN; };
+    auto put_u = [&](int z, int r, R vx, R vy, R vz) {
+        const int s = rslot(z);
+        ringp(s, 0)[r] = vx;
+        ringp(s, 1)[r] = vy;
+        ringp(s, 2)[r] = vz;
+    };
+
+    // velocity of the halo column at plane z into the ring
+    auto halo_plane = [&](int z) {
+        if (tid < NB) {
+            R vx = 0, vy = 0, vz = 0;
+            if (hal.valid) {
+                int zr[3];
+                zrows(z, zr);
+                R gh[Q];
+                pull<Q, S, R, BC>(fin, ps, hal, zr, gh);
+                R rh;
+                moments<Q, R>(gh, rh, vx, vy, vz, Fx, Fy, Fz);
+            }
+            put_u(z, hal_r, vx, vy, vz);
+        }
+    };
+    // own column at plane z: velocity into the ring; populations into the
+    // stash slot (z & 1) when `keep`
+    auto own_plane = [&](int z, bool keep, R& r, R& vx, R& vy, R& vz) {
+        r = 1;
+        vx = vy = vz = 0;
+        if (own.valid) {
+            int zr[3];
+            zrows(z, zr);
+            R t[Q];
+            pull<Q, S, R, BC>(fin, ps, own, zr, t);
+            moments<Q, R>(t, r, vx, vy, vz, Fx, Fy, Fz);
+            if (keep) {
+                R* st = stash + (z & 1) * Q * NT + tid;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) st[i * NT] = t[i];
+            }
+        }
+        put_u(z, own_r, vx, vy, vz);
+    };
+
+    R rho, ux, uy, uz;
+    {
+        R r0, v0x, v0y, v0z;
+        own_plane(z0 - 1, false, r0, v0x, v0y, v0z);
+        halo_plane(z0 - 1);
+        halo_plane(z0);
+        own_plane(z0, true, rho, ux, uy, uz);
+    }
+    __syncthreads();
+
+    for (int z = z0; z < z1; ++z) {
+        // ---- plane z+1: halo and own column velocities into the ring
+        R rn, vnx, vny, vnz;
+        halo_plane(z + 1);
+        own_plane(z + 1, z + 1 < z1, rn, vnx, vny, vnz);
+        __syncthreads();
+
+        // ---- plane z: strain from the ring, closure, relaxation, store
+        if (own.valid) {
+            if (own_store && !(isfinite(rho) && isfinite(ux) && isfinite(uy) && isfinite(uz))) atomicOr(a.flag, 1u);
+            const int sm = rslot(z - 1), s0 = rslot(z), sp = rslot(z + 1);
+            R du[3][3];  // du[a][b] = d_a u_b
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const R* r0 = ringp(s0, b);
+                du[0][b] = R(0.5) * (r0[own_r + 1] - r0[own_r - 1]);
+                du[2][b] = R(0.5) * (ringp(sp, b)[own_r] - ringp(sm, b)[own_r]);
+                if (BC == BC_WALLS_Y && gy == 0)
+                    du[1][b] = R(0.5) * (R(-3) * r0[own_r] + R(4) * r0[own_r + RX] - r0[own_r + 2 * RX]);
+                else if (BC == BC_WALLS_Y && gy == ny - 1)
+                    du[1][b] = R(0.5) * (R(3) * r0[own_r] - R(4) * r0[own_r - RX] + r0[own_r - 2 * RX]);
+                else
+                    du[1][b] = R(0.5) * (r0[own_r + RX] - r0[own_r - RX]);
+            }
+            const R Sxx = du[0][0], Syy = du[1][1], Szz = du[2][2];
+            const R Sxy = R(0.5) * (du[0][1] + du[1][0]);
+            const R Sxz = R(0.5) * (du[0][2] + du[2][0]);
+            const R Syz = R(0.5) * (du[1][2] + du[2][1]);
+            R g[Q];
+            const R* st = stash + (z & 1) * Q * NT + tid;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) g[i] = st[i * NT];
+            collide<Q, R, CL, FORCE>(g, rho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, omega, tau_hat, nu, cnud, Fx,
+                                     Fy, Fz);
+            if (own_store) {
+                S* dst = fout + (z * plane + own.yr[1] + own.xs[1]);
+                static_for<Q>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    store_g<S, R>(dst + (long long)i * ps, g[i], (R)weight_of(Q, i));
+                });
+            }
+        }
+        rho = rn;
+        ux = vnx;
+        uy = vny;
+        uz = vnz;
+    }
+}
+
+template <int Q, typename S, int CL, int BC, int TY>
+cudaError_t launch_step_t(const StepArgs& a, int nbatch, cudaStream_t s)
+{
+    using Sh = StepShape<Q, typename StoreTraits<S>::R, BC, TY>;
+    static bool attr_set = false;  // the attribute is per function; setting it twice is harmless
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(step_kernel<Q, S, CL, BC, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)Sh::smem_bytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int tiles = ((a.nx + Sh::TX - 1) / Sh::TX) * ((a.ny + TY - 1) / TY);
+    const int chunks = (a.nz + a.zchunk - 1) / a.zchunk;
+    dim3 grid(tiles, chunks, nbatch), block(Sh::TX, TY);
+    step_kernel<Q, S, CL, BC, TY><<<grid, block, Sh::smem_bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmk

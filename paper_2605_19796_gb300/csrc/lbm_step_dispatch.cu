@@ -1,0 +1,52 @@
+// Run-time dispatch of the fused step kernel over lattice x storage.
+#include "lbm_internal.h"
+
+namespace lbmk {
+
+cudaError_t launch_step_q19_f64(int, int, int, const StepArgs*, int, cudaStream_t);
+cudaError_t launch_step_q19_f32(int, int, int, const StepArgs*, int, cudaStream_t);
+cudaError_t launch_step_q19_f16(int, int, int, const StepArgs*, int, cudaStream_t);
+cudaError_t launch_step_q19_bf16(int, int, int, const StepArgs*, int, cudaStream_t);
+cudaError_t launch_step_q27_f64(int, int, int, const StepArgs*, int, cudaStream_t);
+cudaError_t launch_step_q27_f32(int, int, int, const StepArgs*, int, cudaStream_t);
+cudaError_t launch_step_q27_f16(int, int, int, const StepArgs*, int, cudaStream_t);
+cudaError_t launch_step_q27_bf16(int, int, int, const StepArgs*, int, cudaStream_t);
+
+namespace {
+using Fn = cudaError_t (*)(int, int, int, const StepArgs*, int, cudaStream_t);
+Fn pick(int q, int storage)
+{
+    if (q == 19) {
+        switch (storage) {
+        case ST_F64: return launch_step_q19_f64;
+        case ST_F32: return launch_step_q19_f32;
+        case ST_F16S: return launch_step_q19_f16;
+        case ST_BF16S: return launch_step_q19_bf16;
+        }
+    } else if (q == 27) {
+        switch (storage) {
+        case ST_F64: return launch_step_q27_f64;
+        case ST_F32: return launch_step_q27_f32;
+        case ST_F16S: return launch_step_q27_f16;
+        case ST_BF16S: return launch_step_q27_bf16;
+        }
+    }
+    return nullptr;
+}
+}  // namespace
+
+cudaError_t launch_step(int q, int storage, int closure, int bc, int tile_y, const StepArgs& a, int nbatch,
+                        cudaStream_t s)
+{
+    Fn f = pick(q, storage);
+    if (!f) return cudaErrorNotSupported;
+    return f(closure, bc, tile_y, &a, nbatch, s);
+}
+
+bool step_supported(int q, int storage, int closure, int bc, int tile_y)
+{
+    Fn f = pick(q, storage);
+    return f && f(closure, bc, tile_y, nullptr, 1, nullptr) == cudaSuccess;
+}
+
+}  // namespace lbmk

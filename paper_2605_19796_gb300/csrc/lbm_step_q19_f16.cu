@@ -1,0 +1,3 @@
+// Fused step kernel instantiations: D3Q19, __half storage.
+#include "lbm_step_inst.cuh"
+LBM_DEFINE_STEP_UNIT(launch_step_q19_f16, 19, __half)

@@ -1,0 +1,3 @@
+// Fused step kernel instantiations: D3Q27, double storage.
+#include "lbm_step_inst.cuh"
+LBM_DEFINE_STEP_UNIT(launch_step_q27_f64, 27, double)

@@ -62,49 +62,82 @@ def shear_wave_fields(n: int, amp: float = 1e-3, nxy: int = 4) -> Tuple[np.ndarr
     return rho, u
 
 
-def hit_fields(n: int, k0: float = 4.0, urms: float = 0.04, seed: int = 0,
-               shape: Optional[Tuple[int, int, int]] = None,
-               dtype=np.float64) -> Tuple[np.ndarray, np.ndarray]:
-    """Decaying homogeneous isotropic turbulence initial velocity.
+def _hit_low_modes(shape, k0: float, seed: int):
+    """Seeded solenoidal low-mode block of the HIT spectrum.
 
-    Random-phase solenoidal field with energy spectrum E(k) ~ k^4 exp(-2 (k/k0)^2),
-    k in units of 2 pi / L.  Recipe: complex Gaussian noise from a seeded PCG64
-    generator on the rfft half-spectrum, times the amplitude
-    sqrt(E(k) / (4 pi k^2)), projected onto the plane normal to k
-    (u <- u - k (k.u)/k^2), zero mean, inverse real FFT, then rescaled so that
-    the per-component rms sqrt(<u_a^2>) averaged over the three components
-    equals ``urms``.  rho = 1.
+    Only |k_a| <= kmax_a = min(6 k0, (n_a - 1)//2) carry energy (E(6 k0) / E(k0)
+    ~ 1e-27).  Returns (block[3, 2kz+1, 2ky+1, kx+1] complex128, (kmx, kmy, kmz)).
     """
-    import scipy.fft as sfft
-
-    nx, ny, nz = shape if shape is not None else (n, n, n)
+    nx, ny, nz = shape
+    kc = int(math.ceil(6.0 * k0))
+    kmx, kmy, kmz = (min(kc, (n - 1) // 2) for n in (nx, ny, nz))
     rng = np.random.Generator(np.random.PCG64(seed))
-    kx = np.fft.rfftfreq(nx, d=1.0 / nx)
-    ky = np.fft.fftfreq(ny, d=1.0 / ny)
-    kz = np.fft.fftfreq(nz, d=1.0 / nz)
+    kx = np.arange(0, kmx + 1, dtype=np.float64)
+    ky = np.arange(-kmy, kmy + 1, dtype=np.float64)
+    kz = np.arange(-kmz, kmz + 1, dtype=np.float64)
     KZ, KY, KX = np.meshgrid(kz, ky, kx, indexing="ij")
     k2 = KX * KX + KY * KY + KZ * KZ
     k = np.sqrt(k2)
     with np.errstate(divide="ignore", invalid="ignore"):
         amp = np.where(k > 0, np.sqrt(k ** 4 * np.exp(-2.0 * (k / k0) ** 2) / (4.0 * math.pi * k2)), 0.0)
-    spec = np.empty((3,) + k.shape, dtype=np.complex128)
+    blk = np.empty((3,) + k.shape, dtype=np.complex128)
     for a in range(3):
-        spec[a] = (rng.standard_normal(k.shape) + 1j * rng.standard_normal(k.shape)) * amp
+        blk[a] = (rng.standard_normal(k.shape) + 1j * rng.standard_normal(k.shape)) * amp
     with np.errstate(divide="ignore", invalid="ignore"):
-        kdotu = (KX * spec[0] + KY * spec[1] + KZ * spec[2]) / np.where(k2 > 0, k2, 1.0)
-    spec[0] -= KX * kdotu
-    spec[1] -= KY * kdotu
-    spec[2] -= KZ * kdotu
-    spec[:, 0, 0, 0] = 0.0
-    u = np.empty((3, nz, ny, nx), dtype=np.float64)
+        kdotu = (KX * blk[0] + KY * blk[1] + KZ * blk[2]) / np.where(k2 > 0, k2, 1.0)
+    blk[0] -= KX * kdotu
+    blk[1] -= KY * kdotu
+    blk[2] -= KZ * kdotu
+    return blk, (kmx, kmy, kmz)
+
+
+def hit_fields(n: int, k0: float = 4.0, urms: float = 0.04, seed: int = 0,
+               shape: Optional[Tuple[int, int, int]] = None, device=None):
+    """Decaying homogeneous isotropic turbulence initial velocity.
+
+    Random-phase solenoidal field with energy spectrum E(k) ~ k^4 exp(-2 (k/k0)^2),
+    k in units of 2 pi / L.  Recipe: complex Gaussian noise from a seeded PCG64
+    generator on the rfft half-spectrum modes |k_a| <= min(6 k0, (n_a-1)/2),
+    times the amplitude sqrt(E(k) / (4 pi k^2)), projected onto the plane normal
+    to k (u <- u - k (k.u)/k^2), inverse real FFT (Hermitian completion of the
+    k_x = 0 plane by the transform), zero mean, then rescaled so that the
+    per-component rms sqrt(<u_a^2>) averaged over the three components equals
+    ``urms``.  rho = 1.
+
+    ``device=None`` returns numpy FP64 arrays (rho[nz,ny,nx], u[3,nz,ny,nx]);
+    a torch device (e.g. "cuda") runs the inverse FFT there and returns torch
+    FP64 tensors with the same values up to FFT rounding.
+    """
+    nx, ny, nz = shape if shape is not None else (n, n, n)
+    blk, (kmx, kmy, kmz) = _hit_low_modes((nx, ny, nz), k0, seed)
+    # block index -k..k maps to the FFT index (k mod n)
+    zi = np.array([(k + nz) % nz for k in range(-kmz, kmz + 1)])
+    yi = np.array([(k + ny) % ny for k in range(-kmy, kmy + 1)])
+    if device is None:
+        import scipy.fft as sfft
+
+        u = np.empty((3, nz, ny, nx), dtype=np.float64)
+        for a in range(3):
+            spec = np.zeros((nz, ny, nx // 2 + 1), dtype=np.complex128)
+            spec[np.ix_(zi, yi, np.arange(kmx + 1))] = blk[a]
+            u[a] = sfft.irfftn(spec, s=(nz, ny, nx), workers=-1)
+        u -= u.reshape(3, -1).mean(axis=1)[:, None, None, None]
+        u *= urms / math.sqrt(float(np.mean(u * u)))
+        return np.ones((nz, ny, nx), dtype=np.float64), u
+    import torch
+
+    u = torch.empty((3, nz, ny, nx), dtype=torch.float64, device=device)
+    zt = torch.as_tensor(zi, device=device)
+    yt = torch.as_tensor(yi, device=device)
     for a in range(3):
-        u[a] = sfft.irfftn(spec[a], s=(nz, ny, nx), workers=-1)
-    del spec
-    u -= u.reshape(3, -1).mean(axis=1)[:, None, None, None]
-    rms = math.sqrt(float(np.mean(u * u)))
-    u *= urms / rms
-    rho = np.ones((nz, ny, nx), dtype=np.float64)
-    return rho.astype(dtype, copy=False), u.astype(dtype, copy=False)
+        spec = torch.zeros((nz, ny, nx // 2 + 1), dtype=torch.complex128, device=device)
+        b = torch.as_tensor(blk[a], device=device)
+        spec.index_put_((zt[:, None, None], yt[None, :, None], torch.arange(kmx + 1, device=device)[None, None, :]), b)
+        u[a] = torch.fft.irfftn(spec, s=(nz, ny, nx))
+        del spec
+    u -= u.reshape(3, -1).mean(dim=1)[:, None, None, None]
+    u *= urms / torch.sqrt(torch.mean(u * u))
+    return torch.ones((nz, ny, nx), dtype=torch.float64, device=device), u
 
 
 def random_populations(q: int, shape: Tuple[int, int, int], seed: int = 0, amp: float = 0.05,

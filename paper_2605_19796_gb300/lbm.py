@@ -1,0 +1,331 @@
+"""Thin ctypes binding of the C ABI in ``include/lbm.h`` (liblbm.so).
+
+Argument marshalling only: every step of the lattice update runs in the
+library's CUDA kernels.  Importing this module loads ``csrc/liblbm.so`` and
+raises ``ImportError`` when it has not been built (``build.build()``); there is
+no CPU fallback.
+
+The functions keep the C names (``lbm_create``, ``lbm_step`` ...); ``Solver``
+wraps a handle with numpy/torch-friendly methods.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "csrc", "liblbm.so")
+
+LBM_OK = 0
+LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_NONFINITE = -1, -2, -3, -4
+LBM_ERR_TIMEOUT, LBM_ERR_UNSUPPORTED, LBM_ERR_IO = -5, -6, -7
+LBM_D3Q19, LBM_D3Q27 = 19, 27
+LBM_BGK, LBM_KCMP, LBM_KCRB_HERMITE, LBM_KCRB_RAW, LBM_KCRR = 0, 1, 2, 3, 4
+LBM_FP64, LBM_FP32, LBM_FP16_SHIFTED, LBM_BF16_SHIFTED = 0, 1, 2, 3
+LBM_PERIODIC, LBM_BOUNCEBACK = 0, 1
+
+CLOSURES = {"bgk": LBM_BGK, "kcmp": LBM_KCMP, "kcrb_hermite": LBM_KCRB_HERMITE, "kcrb_raw": LBM_KCRB_RAW,
+            "kcrr": LBM_KCRR}
+STORAGES = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16": LBM_FP16_SHIFTED, "bf16": LBM_BF16_SHIFTED}
+# closure coefficients used by the paper (Sec. 7): KC-MP 0.035, KC-RB and KC-RR 0.02
+DEFAULT_CNU = {LBM_BGK: 0.0, LBM_KCMP: 0.035, LBM_KCRB_HERMITE: 0.02, LBM_KCRB_RAW: 0.02, LBM_KCRR: 0.02}
+EXPORTS = ["lbm_config_default", "lbm_create", "lbm_destroy", "lbm_init_velocity", "lbm_init_velocity_device",
+           "lbm_step", "lbm_moments", "lbm_moments_device", "lbm_diagnostics", "lbm_get_populations",
+           "lbm_set_populations", "lbm_probe", "lbm_population_buffer", "lbm_synchronize", "lbm_save", "lbm_load",
+           "lbm_step_count", "lbm_kernel_launches", "lbm_last_error", "lbm_abi_version"]
+
+
+class lbm_config(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("nbatch", ctypes.c_int), ("nu", ctypes.POINTER(ctypes.c_double)), ("closure", ctypes.c_int),
+                ("c_nu", ctypes.c_double), ("delta", ctypes.c_double), ("storage", ctypes.c_int),
+                ("bc", ctypes.c_int * 3), ("force", ctypes.c_double * 3), ("cuda_stream", ctypes.c_void_p),
+                ("tile_y", ctypes.c_int), ("zchunk", ctypes.c_int)]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"liblbm error {code}: {msg}")
+        self.code = code
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run paper_2605_19796_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    dp = P(ctypes.c_double)
+    vp = ctypes.c_void_p
+    H = vp
+    lib.lbm_config_default.argtypes = [P(lbm_config)]
+    lib.lbm_config_default.restype = None
+    lib.lbm_create.argtypes = [P(lbm_config), P(vp)]
+    lib.lbm_destroy.argtypes = [H]
+    lib.lbm_destroy.restype = None
+    lib.lbm_init_velocity.argtypes = [H, dp, dp]
+    lib.lbm_init_velocity_device.argtypes = [H, vp, vp]
+    lib.lbm_step.argtypes = [H, ctypes.c_int]
+    lib.lbm_moments.argtypes = [H, dp, dp]
+    lib.lbm_moments_device.argtypes = [H, vp, vp]
+    lib.lbm_diagnostics.argtypes = [H, ctypes.c_int, dp]
+    lib.lbm_get_populations.argtypes = [H, dp]
+    lib.lbm_set_populations.argtypes = [H, dp]
+    lib.lbm_probe.argtypes = [H, ctypes.c_int, P(ctypes.c_int), ctypes.c_int, dp]
+    lib.lbm_population_buffer.argtypes = [H, P(vp), P(ctypes.c_int)]
+    lib.lbm_synchronize.argtypes = [H]
+    lib.lbm_save.argtypes = [H, ctypes.c_char_p]
+    lib.lbm_load.argtypes = [H, ctypes.c_char_p]
+    lib.lbm_step_count.argtypes = [H]
+    lib.lbm_step_count.restype = ctypes.c_int64
+    lib.lbm_kernel_launches.argtypes = [H]
+    lib.lbm_kernel_launches.restype = ctypes.c_int64
+    lib.lbm_last_error.restype = ctypes.c_char_p
+    lib.lbm_abi_version.restype = ctypes.c_int
+    return lib
+
+
+LIB = _load()
+
+
+def _dp(a: Optional[np.ndarray]):
+    if a is None:
+        return ctypes.POINTER(ctypes.c_double)()
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"], "expected a C-contiguous float64 array"
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(rc: int) -> None:
+    if rc != LBM_OK:
+        raise LbmError(rc, LIB.lbm_last_error().decode())
+
+
+# ---------------------------------------------------------------- C names
+
+def lbm_config_default() -> lbm_config:
+    cfg = lbm_config()
+    LIB.lbm_config_default(ctypes.byref(cfg))
+    return cfg
+
+
+def lbm_create(cfg: lbm_config) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(LIB.lbm_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def lbm_destroy(h) -> None:
+    LIB.lbm_destroy(h)
+
+
+def lbm_init_velocity(h, rho: Optional[np.ndarray], u: np.ndarray) -> None:
+    _check(LIB.lbm_init_velocity(h, _dp(rho), _dp(u)))
+
+
+def lbm_init_velocity_device(h, rho_ptr: int, u_ptr: int) -> None:
+    _check(LIB.lbm_init_velocity_device(h, ctypes.c_void_p(rho_ptr or None), ctypes.c_void_p(u_ptr)))
+
+
+def lbm_step(h, nsteps: int) -> None:
+    _check(LIB.lbm_step(h, int(nsteps)))
+
+
+def lbm_moments(h, rho: Optional[np.ndarray], u: Optional[np.ndarray]) -> None:
+    _check(LIB.lbm_moments(h, _dp(rho), _dp(u)))
+
+
+def lbm_moments_device(h, rho_ptr: int, u_ptr: int) -> None:
+    _check(LIB.lbm_moments_device(h, ctypes.c_void_p(rho_ptr or None), ctypes.c_void_p(u_ptr or None)))
+
+
+def lbm_diagnostics(h, box: int, out: np.ndarray) -> None:
+    _check(LIB.lbm_diagnostics(h, int(box), _dp(out)))
+
+
+def lbm_get_populations(h, f: np.ndarray) -> None:
+    _check(LIB.lbm_get_populations(h, _dp(f)))
+
+
+def lbm_set_populations(h, f: np.ndarray) -> None:
+    _check(LIB.lbm_set_populations(h, _dp(f)))
+
+
+def lbm_probe(h, box: int, xyz: np.ndarray, out: np.ndarray) -> None:
+    xyz = np.ascontiguousarray(xyz, dtype=np.int32)
+    _check(LIB.lbm_probe(h, int(box), xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), int(xyz.shape[0]), _dp(out)))
+
+
+def lbm_population_buffer(h):
+    p = ctypes.c_void_p()
+    e = ctypes.c_int()
+    _check(LIB.lbm_population_buffer(h, ctypes.byref(p), ctypes.byref(e)))
+    return p.value, e.value
+
+
+def lbm_synchronize(h) -> None:
+    _check(LIB.lbm_synchronize(h))
+
+
+def lbm_save(h, path: str) -> None:
+    _check(LIB.lbm_save(h, path.encode()))
+
+
+def lbm_load(h, path: str) -> None:
+    _check(LIB.lbm_load(h, path.encode()))
+
+
+def lbm_step_count(h) -> int:
+    return int(LIB.lbm_step_count(h))
+
+
+def lbm_kernel_launches(h) -> int:
+    return int(LIB.lbm_kernel_launches(h))
+
+
+def lbm_last_error() -> str:
+    return LIB.lbm_last_error().decode()
+
+
+def lbm_abi_version() -> int:
+    return int(LIB.lbm_abi_version())
+
+
+# ---------------------------------------------------------------- wrapper
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+class Solver:
+    """One handle: ``Solver(27, (nx, ny, nz), nu=1e-4, closure="kcmp", storage="fp32")``.
+
+    Fields use the layouts of the C ABI: rho[nbatch, nz, ny, nx],
+    u[3, nbatch, nz, ny, nx] (squeezed to [nz, ny, nx] / [3, nz, ny, nx] for
+    one box), populations [nbatch, q, nz, ny, nx].
+    """
+
+    def __init__(self, lattice: int, shape: Sequence[int], nu, *, closure="kcmp", c_nu: Optional[float] = None,
+                 delta: float = 1.0, storage="fp32", bc=(0, 0, 0), force=(0.0, 0.0, 0.0), stream=None,
+                 nbatch: int = 1, tile_y: int = 0, zchunk: int = 0):
+        cfg = lbm_config_default()
+        cfg.lattice = int(lattice)
+        cfg.nx, cfg.ny, cfg.nz = (int(v) for v in shape)
+        cfg.nbatch = int(nbatch)
+        self._nu = np.ascontiguousarray(np.broadcast_to(np.asarray(nu, dtype=np.float64), (nbatch,)))
+        cfg.nu = _dp(self._nu)
+        cfg.closure = CLOSURES[closure] if isinstance(closure, str) else int(closure)
+        cfg.c_nu = DEFAULT_CNU[cfg.closure] if c_nu is None else float(c_nu)
+        cfg.delta = float(delta)
+        cfg.storage = STORAGES[storage] if isinstance(storage, str) else int(storage)
+        for k in range(3):
+            cfg.bc[k] = int(bc[k])
+            cfg.force[k] = float(force[k])
+        sh = _stream_handle(stream)
+        cfg.cuda_stream = ctypes.c_void_p(sh) if sh else None
+        cfg.tile_y = int(tile_y)
+        cfg.zchunk = int(zchunk)
+        self.cfg = cfg
+        self.q = cfg.lattice
+        self.shape = (cfg.nx, cfg.ny, cfg.nz)
+        self.nbatch = cfg.nbatch
+        self.h = lbm_create(cfg)
+
+    # -- lifetime
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- state
+    @property
+    def ncell(self) -> int:
+        nx, ny, nz = self.shape
+        return nx * ny * nz
+
+    def _fshape(self):
+        nx, ny, nz = self.shape
+        return (self.nbatch, nz, ny, nx)
+
+    def init_velocity(self, rho: Optional[np.ndarray], u: np.ndarray) -> None:
+        u = np.ascontiguousarray(u, dtype=np.float64).reshape(3, -1)
+        r = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
+        lbm_init_velocity(self.h, r, u)
+
+    def init_velocity_device(self, rho, u) -> None:
+        """rho, u: CUDA float64 tensors (rho may be None) in the C ABI layouts."""
+        lbm_init_velocity_device(self.h, 0 if rho is None else rho.data_ptr(), u.data_ptr())
+
+    def step(self, n: int = 1) -> None:
+        lbm_step(self.h, n)
+
+    def moments(self):
+        rho = np.empty(self._fshape(), dtype=np.float64)
+        u = np.empty((3,) + self._fshape(), dtype=np.float64)
+        lbm_moments(self.h, rho, u)
+        if self.nbatch == 1:
+            return rho[0], u[:, 0]
+        return rho, u
+
+    def moments_device(self, rho, u) -> None:
+        lbm_moments_device(self.h, 0 if rho is None else rho.data_ptr(), 0 if u is None else u.data_ptr())
+
+    def diagnostics(self, box: int = 0) -> np.ndarray:
+        out = np.zeros(8, dtype=np.float64)
+        lbm_diagnostics(self.h, box, out)
+        return out
+
+    def get_populations(self) -> np.ndarray:
+        nb, nz, ny, nx = self._fshape()
+        f = np.empty((nb, self.q, nz, ny, nx), dtype=np.float64)
+        lbm_get_populations(self.h, f)
+        return f[0] if nb == 1 else f
+
+    def set_populations(self, f: np.ndarray) -> None:
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.size == self.nbatch * self.q * self.ncell
+        lbm_set_populations(self.h, f)
+
+    def probe(self, xyz, box: int = 0) -> np.ndarray:
+        """FP64 populations [n, q] of the cells xyz[n, 3] = (x, y, z) (wrapped periodically)."""
+        xyz = np.ascontiguousarray(np.asarray(xyz).reshape(-1, 3), dtype=np.int32)
+        out = np.empty((xyz.shape[0], self.q), dtype=np.float64)
+        lbm_probe(self.h, box, xyz, out)
+        return out
+
+    def population_buffer(self):
+        return lbm_population_buffer(self.h)
+
+    def synchronize(self) -> None:
+        lbm_synchronize(self.h)
+
+    def save(self, path: str) -> None:
+        lbm_save(self.h, path)
+
+    def load(self, path: str) -> None:
+        lbm_load(self.h, path)
+
+    @property
+    def step_count(self) -> int:
+        return lbm_step_count(self.h)
+
+    @property
+    def kernel_launches(self) -> int:
+        return lbm_kernel_launches(self.h)

@@ -1,0 +1,262 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (stated in the test, derived from the arithmetic):
+  - FP64 storage: max |gpu - oracle| / max |oracle| <= 1e-12 for populations,
+    density and velocity (the two sides differ only in rounding order and FMA
+    contraction, ~1e-16 per operation, accumulated over at most 200 steps);
+  - FP32 storage: max |u_gpu - u_oracle| <= 1e-5 lattice units after 50 steps
+    of 64^3 decaying turbulence (u_rms = 0.04): FP32 storage rounding
+    (~6e-8 relative per population per step) accumulated over the run.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2605_19796_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2605_19796_gb300 import build
+
+    build.build()
+    from paper_2605_19796_gb300 import lbm as _lbm
+
+    return _lbm
+
+
+def rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+
+
+CL = {"bgk": 0, "kcmp": 1, "kcrb_hermite": 2, "kcrb_raw": 3}
+CNU = {"bgk": 0.0, "kcmp": 0.035, "kcrb_hermite": 0.02, "kcrb_raw": 0.02}
+
+
+def _run_pair(lbm, orc, q, shape, rho, u, nu, closure, steps, storage="fp64", bc=(0, 0, 0), F=(0.0, 0.0, 0.0),
+              checkpoints=None, **kw):
+    """Runs GPU and oracle from the same equilibrium state; returns lists of
+    (gpu populations, oracle populations) at the checkpoints."""
+    nx, ny, nz = shape
+    checkpoints = checkpoints or [steps]
+    out = []
+    with lbm.Solver(q, shape, nu, closure=closure, c_nu=CNU[closure], storage=storage, bc=bc, force=F, **kw) as s:
+        s.init_velocity(rho, u)
+        f = orc.init_equilibrium(q, rho, u)
+        done = 0
+        for cp in checkpoints:
+            s.step(cp - done)
+            f = orc.run(f, cp - done, closure=CL[closure], nu=nu, c_nu=CNU[closure], bc=bc, F=F)
+            done = cp
+            out.append((s.get_populations(), f.copy(), s))
+            s.synchronize()
+    return out
+
+
+def test_tgv_32_d3q19_fp64_kcmp_200_steps(lbm, orc):
+    """3D Taylor-Green vortex, periodic 32^3 D3Q19, FP64, U0 = 0.05, Re = 1600
+    (nu = U0 L_TGV / 1600, L_TGV = 32/(2 pi)), KC-MP, 200 steps: fields and
+    kinetic energy / enstrophy at steps 0, 50, 100, 200."""
+    n, u0 = 32, 0.05
+    nu = u0 * (n / (2 * math.pi)) / 1600.0
+    rho, u = inputs.tgv_fields(n, u0=u0)
+    with lbm.Solver(19, (n, n, n), nu, closure="kcmp", storage="fp64") as s:
+        s.init_velocity(rho, u)
+        f = orc.init_equilibrium(19, rho, u)
+        done = 0
+        ek = []
+        for cp in (0, 50, 100, 200):
+            s.step(cp - done)
+            f = orc.run(f, cp - done, closure=1, nu=nu, c_nu=0.035)
+            done = cp
+            r_g, u_g = s.moments()
+            r_o, u_o = orc.fields(f)
+            assert rel(r_g, r_o) < TOL64 and rel(u_g, u_o) < TOL64, (cp, rel(r_g, r_o), rel(u_g, u_o))
+            assert rel(s.get_populations(), f) < TOL64
+            d_g, d_o = s.diagnostics(), orc.diagnostics(f)
+            # mass, E_k, enstrophy relative; momentum sums (~0 for the TGV) against mass * u0
+            for k in (0, 4, 5):
+                assert abs(d_g[k] - d_o[k]) <= TOL64 * abs(d_o[k]), (cp, k, d_g[k], d_o[k])
+            for k in (1, 2, 3):
+                assert abs(d_g[k] - d_o[k]) <= TOL64 * d_o[0] * u0, (cp, k, d_g[k], d_o[k])
+            ek.append(d_g[4])
+        assert ek[-1] < ek[0]  # energy decays
+
+
+@pytest.mark.parametrize("q", [19, 27])
+@pytest.mark.parametrize("closure", ["bgk", "kcmp", "kcrb_hermite", "kcrb_raw"])
+def test_closures_ragged_fp64(lbm, orc, q, closure):
+    """Ragged box (not a multiple of the 32 x 8 tile or of the z-chunk),
+    under-resolved turbulence so that the turbulent rate is active."""
+    shape = (37, 21, 13)
+    rho, u = inputs.hit_fields(0, k0=3.0, urms=0.08, seed=1, shape=shape)
+    nu = 2e-5
+    (fg, fo, _), = _run_pair(lbm, orc, q, shape, rho, u, nu, closure, 12)
+    assert rel(fg, fo) < TOL64
+    if closure != "bgk":
+        f0 = orc.init_equilibrium(q, rho, u)
+        fb = orc.run(f0, 12, closure=0, nu=nu)
+        assert np.abs(fo - fb).max() > 1e-7, "the closure must be active in this test"
+
+
+@pytest.mark.parametrize("shape", [(4, 4, 4), (1, 1, 6), (3, 5, 2), (64, 8, 1), (33, 9, 5), (2, 40, 3)])
+def test_small_and_degenerate_shapes_fp64(lbm, orc, shape):
+    rho, u = inputs.hit_fields(0, k0=1.0, urms=0.05, seed=2, shape=shape)
+    (fg, fo, _), = _run_pair(lbm, orc, 27, shape, rho, u, 1e-4, "kcmp", 7)
+    assert rel(fg, fo) < TOL64
+
+
+@pytest.mark.parametrize("zchunk,tile_y", [(1, 8), (3, 8), (20, 8), (5, 16), (7, 4)])
+def test_launch_shapes_fp32_consistent(lbm, orc, zchunk, tile_y):
+    """Every z-chunk gives the bit-identical FP32 result of the default launch
+    (the per-cell arithmetic does not depend on the decomposition); other tile
+    heights are other kernel instantiations and agree to FP32 rounding."""
+    shape = (40, 24, 20)
+    rho, u = inputs.hit_fields(0, k0=3.0, urms=0.06, seed=3, shape=shape)
+    res = []
+    for zc, ty in ((0, 0), (zchunk, tile_y)):
+        with lbm.Solver(27, shape, 3e-5, closure="kcmp", storage="fp32", zchunk=zc, tile_y=ty) as s:
+            s.init_velocity(rho, u)
+            s.step(6)
+            res.append(s.get_populations())
+    if tile_y == 8:
+        assert np.array_equal(res[0], res[1])
+    else:
+        assert rel(res[1], res[0]) < 1e-6
+
+
+def test_fp32_hit_64_velocity(lbm, orc):
+    """Decaying HIT at 64^3 D3Q27 (k0 = 4, u_rms = 0.04, nu = 1e-4), KC-MP,
+    FP32 storage and arithmetic vs the FP64 oracle after 50 steps."""
+    n = 64
+    rho, u = inputs.hit_fields(n, k0=4.0, urms=0.04, seed=0)
+    (fg, fo, s), = _run_pair(lbm, orc, 27, (n, n, n), rho, u, 1e-4, "kcmp", 50, storage="fp32")
+    _, ug = orc.fields(fg)
+    _, uo = orc.fields(fo)
+    err = float(np.abs(ug - uo).max())
+    assert err <= 1e-5, err
+
+
+@pytest.mark.parametrize("q", [19, 27])
+@pytest.mark.parametrize("ny", [24, 13, 9])
+def test_channel_walls_force_fp64(lbm, orc, q, ny):
+    """Halfway bounce-back walls in y, Guo body force in x, one-sided strain
+    stencils at the wall layers; ny = 13 and 9 leave one or five rows in the last tile."""
+    shape = (20, ny, 6)
+    rng = np.random.default_rng(4)
+    rho = np.ones((6, ny, 20))
+    u = np.zeros((3, 6, ny, 20))
+    y = (np.arange(ny) + 0.5) / ny
+    u[0] = 0.05 * 4 * y * (1 - y)
+    u += 0.01 * rng.standard_normal(u.shape)
+    F = (2e-5, 0.0, 0.0)
+    (fg, fo, _), = _run_pair(lbm, orc, q, shape, rho, u, 5e-5, "kcmp", 10, bc=(0, 1, 0), F=F)
+    assert rel(fg, fo) < TOL64
+
+
+def test_ensemble_fp64(lbm, orc):
+    """Three independent boxes with different viscosities in one launch."""
+    shape = (16, 12, 10)
+    nus = np.array([5e-5, 2e-4, 4.5e-4])
+    fields = [inputs.hit_fields(0, k0=2.0, urms=0.06, seed=10 + b, shape=shape) for b in range(3)]
+    rho = np.stack([f[0] for f in fields])
+    u = np.stack([f[1] for f in fields], axis=1)
+    with lbm.Solver(27, shape, nus, closure="kcmp", storage="fp64", nbatch=3) as s:
+        s.init_velocity(rho, u)
+        s.step(8)
+        fg = s.get_populations()
+    for b in range(3):
+        fo = orc.run(orc.init_equilibrium(27, fields[b][0], fields[b][1]), 8, closure=1, nu=nus[b], c_nu=0.035)
+        assert rel(fg[b], fo) < TOL64
+
+
+def test_save_load_resume_bitwise(lbm, orc, tmp_path):
+    shape = (24, 16, 12)
+    rho, u = inputs.hit_fields(0, k0=2.0, urms=0.05, seed=5, shape=shape)
+    p = str(tmp_path / "state.lbm")
+    with lbm.Solver(27, shape, 1e-4, closure="kcmp", storage="fp32") as s:
+        s.init_velocity(rho, u)
+        s.step(10)
+        s.save(p)
+        s.step(10)
+        a = s.get_populations()
+        assert s.step_count == 20
+    with lbm.Solver(27, shape, 1e-4, closure="kcmp", storage="fp32") as s:
+        s.load(p)
+        assert s.step_count == 10
+        s.step(10)
+        b = s.get_populations()
+    assert np.array_equal(a, b)
+    with lbm.Solver(19, shape, 1e-4, closure="kcmp", storage="fp32") as s:
+        with pytest.raises(lbm.LbmError):
+            s.load(p)
+
+
+def test_nonfinite_is_reported(lbm, orc):
+    """A NaN injected into the host-side initial field is caught by the step's
+    device flag and reported as LBM_ERR_NONFINITE (no device fault involved)."""
+    shape = (16, 8, 8)
+    rho, u = inputs.hit_fields(0, k0=2.0, urms=0.05, seed=6, shape=shape)
+    u[0, 3, 4, 5] = np.nan
+    with lbm.Solver(27, shape, 1e-4, closure="kcmp", storage="fp32") as s:
+        s.init_velocity(rho, u)
+        s.step(2)
+        with pytest.raises(lbm.LbmError) as ei:
+            s.synchronize()
+        assert ei.value.code == lbm.LBM_ERR_NONFINITE
+        s.synchronize()  # the flag is cleared once reported
+
+
+def test_bad_configs_rejected(lbm):
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.Solver(19, (8, 8, 8), 1e-4, closure="kcrr")
+    assert ei.value.code == lbm.LBM_ERR_UNSUPPORTED
+    with pytest.raises(lbm.LbmError):
+        lbm.Solver(27, (8, 0, 8), 1e-4)
+    with pytest.raises(lbm.LbmError):
+        lbm.Solver(27, (8, 8, 8), -1.0)
+    with pytest.raises(lbm.LbmError):
+        lbm.Solver(27, (8, 8, 8), 1e-4, bc=(1, 0, 0))
+
+
+def _sampled_cells(n, k, seed):
+    rng = np.random.default_rng(seed)
+    pts = rng.integers(0, n, size=(k, 3))
+    # include the domain corners and tile / chunk edges
+    extra = np.array([[0, 0, 0], [n - 1, n - 1, n - 1], [31, 7, 15], [32, 8, 16], [n - 1, 0, n // 2]])
+    return np.concatenate([pts, extra])
+
+
+@pytest.mark.parametrize("n", [256, 512])
+def test_full_size_sampled_cells_fp32(lbm, orc, n):
+    """Full-size decaying HIT (D3Q27, FP32, KC-MP, nu = 1e-4) in the default launch
+    configuration: one GPU step, then sampled cells against the oracle's
+    single-cell step evaluated on the GPU's own pre-step populations (FP32
+    values are exact in FP64).  Tolerance: 2e-6 x max|f| (FP32 arithmetic of
+    ~10^3 operations per cell)."""
+    rho, u = inputs.hit_fields(n, k0=4.0, urms=0.04, seed=0)
+    pts = _sampled_cells(n, 48, seed=n)
+    offs = np.array([(dx, dy, dz) for dz in range(-2, 3) for dy in range(-2, 3) for dx in range(-2, 3)])
+    with lbm.Solver(27, (n, n, n), 1e-4, closure="kcmp", storage="fp32") as s:
+        s.init_velocity(rho, u)
+        del rho, u
+        s.step(3)
+        blocks = s.probe((pts[:, None, :] + offs[None, :, :]).reshape(-1, 3)).reshape(len(pts), 125, 27)
+        mass0 = s.diagnostics()[0]
+        s.step(1)
+        after = s.probe(pts)
+        mass1 = s.diagnostics()[0]
+    scale = np.abs(after).max()
+    for k in range(len(pts)):
+        blk = blocks[k].T.reshape(27, 5, 5, 5)
+        ref = orc.step_cell(blk, closure=1, nu=1e-4, c_nu=0.035)
+        assert np.abs(after[k] - ref).max() <= 2e-6 * scale, (pts[k], np.abs(after[k] - ref).max())
+    assert abs(mass1 - mass0) <= 1e-9 * mass0

@@ -186,9 +186,11 @@ __device__ __forceinline__ void pull(const S* __restrict__ fin, long long ps, co
     });
 }
 
-// rho = 1 + sum g, j = sum g c (sum w c = 0), u = (j + F/2)/rho
+// drho = sum g (rho = 1 + drho), j = sum g c (sum w c = 0), u = (j + F/2)/rho.
+// drho is returned unrounded: the equilibrium uses it directly so that
+// sum_i g_eq,i = drho holds to rounding of small quantities (no O(1) term).
 template <int Q, typename R>
-__device__ __forceinline__ void moments(const R (&g)[Q], R& rho, R& ux, R& uy, R& uz, R Fx, R Fy, R Fz)
+__device__ __forceinline__ void moments(const R (&g)[Q], R& drho, R& ux, R& uy, R& uz, R Fx, R Fy, R Fz)
 {
     R d = 0, jx = 0, jy = 0, jz = 0;
     static_for<Q>([&](auto I) {
@@ -202,8 +204,8 @@ __device__ __forceinline__ void moments(const R (&g)[Q], R& rho, R& ux, R& uy, R
         if (cz == 1) jz += g[i];
         if (cz == -1) jz -= g[i];
     });
-    rho = R(1) + d;
-    const R inv = R(1) / rho;
+    drho = d;
+    const R inv = R(1) / (R(1) + d);
     ux = (jx + R(0.5) * Fx) * inv;
     uy = (jy + R(0.5) * Fy) * inv;
     uz = (jz + R(0.5) * Fz) * inv;
@@ -220,20 +222,23 @@ __device__ __forceinline__ R omega_sgs(R tr, R nu, R omega, R cnud)
 
 // One-cell collision on shifted populations g (in place -> g_post).
 template <int Q, typename R, int CL, bool FORCE>
-__device__ __forceinline__ void collide(R (&g)[Q], R rho, R ux, R uy, R uz, R Sxx, R Syy, R Szz, R Sxy, R Sxz,
+__device__ __forceinline__ void collide(R (&g)[Q], R drho, R ux, R uy, R uz, R Sxx, R Syy, R Szz, R Sxy, R Sxz,
                                         R Syz, R omega, R tau_hat, R nu, R cnud, R Fx, R Fy, R Fz)
 {
     constexpr R th = R(kTheta);
-    const R drho = rho - R(1);
-    // equilibrium factors: D3Q27 product of D1Q3 truncations,
-    // 1 + c u/theta + (c^2 - theta) u^2/(2 theta^2)
+    const R rho = R(1) + drho;
+    // D3Q27 equilibrium: product of the D1Q3 truncations
+    //   1 + e_a,  e_a = c u_a/theta + (c^2 - theta) u_a^2/(2 theta^2),
+    // evaluated as g_eq = w (rho (P - 1) + drho) with P - 1 expanded in the small
+    // e_a (P - 1 = e_x + Y + e_x Y, Y = e_y + e_z + e_y e_z): forming the O(1)
+    // product and subtracting 1 would round systematically in FP32.
     constexpr R a1 = R(1.0 / kTheta);
     constexpr R a2 = R((1.0 - kTheta) / (2.0 * kTheta * kTheta));
     constexpr R a0 = R(-kTheta / (2.0 * kTheta * kTheta));
     const R ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
-    const R px0 = R(1) + a0 * ux2, pxp = R(1) + a1 * ux + a2 * ux2, pxm = R(1) - a1 * ux + a2 * ux2;
-    const R py0 = R(1) + a0 * uy2, pyp = R(1) + a1 * uy + a2 * uy2, pym = R(1) - a1 * uy + a2 * uy2;
-    const R pz0 = R(1) + a0 * uz2, pzp = R(1) + a1 * uz + a2 * uz2, pzm = R(1) - a1 * uz + a2 * uz2;
+    const R ex0 = a0 * ux2, exp_ = a1 * ux + a2 * ux2, exm = -a1 * ux + a2 * ux2;
+    const R ey0 = a0 * uy2, eyp = a1 * uy + a2 * uy2, eym = -a1 * uy + a2 * uy2;
+    const R ez0 = a0 * uz2, ezp = a1 * uz + a2 * uz2, ezm = -a1 * uz + a2 * uz2;
     const R usq = ux2 + uy2 + uz2;
 
     // g_eq,i = f0_i - w_i
@@ -242,10 +247,12 @@ __device__ __forceinline__ void collide(R (&g)[Q], R rho, R ux, R uy, R uz, R Sx
         constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
         constexpr R w = R(weight_of(Q, i));
         if constexpr (Q == 27) {
-            const R px = cx == 0 ? px0 : (cx > 0 ? pxp : pxm);
-            const R py = cy == 0 ? py0 : (cy > 0 ? pyp : pym);
-            const R pz = cz == 0 ? pz0 : (cz > 0 ? pzp : pzm);
-            return w * (rho * (px * py * pz) - R(1));
+            const R ex = cx == 0 ? ex0 : (cx > 0 ? exp_ : exm);
+            const R ey = cy == 0 ? ey0 : (cy > 0 ? eyp : eym);
+            const R ez = cz == 0 ? ez0 : (cz > 0 ? ezp : ezm);
+            const R Y = ey + ez + ey * ez;
+            const R pm1 = ex + Y + ex * Y;
+            return w * (rho * pm1 + drho);
         } else {
             const R cu = R(cx) * ux + R(cy) * uy + R(cz) * uz;
             return w * (drho + rho * (a1 * cu + R(0.5) * a1 * a1 * cu * cu - R(0.5) * a1 * usq));
@@ -447,8 +454,8 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
                 zrows(z, zr);
                 R gh[Q];
                 pull<Q, S, R, BC>(fin, ps, hal, zr, gh);
-                R rh;
-                moments<Q, R>(gh, rh, vx, vy, vz, Fx, Fy, Fz);
+                R dh;
+                moments<Q, R>(gh, dh, vx, vy, vz, Fx, Fy, Fz);
             }
             put_u(z, hal_r, vx, vy, vz);
         }
@@ -456,7 +463,7 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
     // own column at plane z: velocity into the ring; populations into the
     // stash slot (z & 1) when `keep`
     auto own_plane = [&](int z, bool keep, R& r, R& vx, R& vy, R& vz) {
-        r = 1;
+        r = 0;
         vx = vy = vz = 0;
         if (own.valid) {
             int zr[3];
@@ -473,13 +480,13 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
         put_u(z, own_r, vx, vy, vz);
     };
 
-    R rho, ux, uy, uz;
+    R drho, ux, uy, uz;  // moments of the own cell at plane z
     {
         R r0, v0x, v0y, v0z;
         own_plane(z0 - 1, false, r0, v0x, v0y, v0z);
         halo_plane(z0 - 1);
         halo_plane(z0);
-        own_plane(z0, true, rho, ux, uy, uz);
+        own_plane(z0, true, drho, ux, uy, uz);
     }
     __syncthreads();
 
@@ -492,7 +499,7 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
 
         // ---- plane z: strain from the ring, closure, relaxation, store
         if (own.valid) {
-            if (own_store && !(isfinite(rho) && isfinite(ux) && isfinite(uy) && isfinite(uz))) atomicOr(a.flag, 1u);
+            if (own_store && !(isfinite(drho) && isfinite(ux) && isfinite(uy) && isfinite(uz))) atomicOr(a.flag, 1u);
             const int sm = rslot(z - 1), s0 = rslot(z), sp = rslot(z + 1);
             R du[3][3];  // du[a][b] = d_a u_b
 #pragma unroll
@@ -515,7 +522,7 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
             const R* st = stash + (z & 1) * Q * NT + tid;
 #pragma unroll
             for (int i = 0; i < Q; ++i) g[i] = st[i * NT];
-            collide<Q, R, CL, FORCE>(g, rho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, omega, tau_hat, nu, cnud, Fx,
+            collide<Q, R, CL, FORCE>(g, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, omega, tau_hat, nu, cnud, Fx,
                                      Fy, Fz);
             if (own_store) {
                 S* dst = fout + (z * plane + own.yr[1] + own.xs[1]);
@@ -525,7 +532,7 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
                 });
             }
         }
-        rho = rn;
+        drho = rn;
         ux = vnx;
         uy = vny;
         uz = vnz;

@@ -155,7 +155,7 @@ def test_channel_walls_force_fp64(lbm, orc, q, ny):
     rho = np.ones((6, ny, 20))
     u = np.zeros((3, 6, ny, 20))
     y = (np.arange(ny) + 0.5) / ny
-    u[0] = 0.05 * 4 * y * (1 - y)
+    u[0] = (0.05 * 4 * y * (1 - y))[None, :, None]
     u += 0.01 * rng.standard_normal(u.shape)
     F = (2e-5, 0.0, 0.0)
     (fg, fo, _), = _run_pair(lbm, orc, q, shape, rho, u, 5e-5, "kcmp", 10, bc=(0, 1, 0), F=F)

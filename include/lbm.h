@@ -170,6 +170,30 @@ int lbm_load(lbm_handle* h, const char* path);
 /* Steps taken since creation (or since the state in the last lbm_load). */
 int64_t lbm_step_count(const lbm_handle* h);
 
+/* Allocation-free variant of the diagnostics reduction (the paper has no
+ * counterpart; it is a service for callers that cannot allocate device memory:
+ * a process whose device memory is all owned by another allocator, code that
+ * must not trigger the implicit device synchronisation of cudaMalloc/cudaFree,
+ * or a loop with a fixed memory budget).  Computes the same eight values as
+ * lbm_diagnostics for ONE box whose populations the caller passes:
+ *   f_dev    device pointer to the box's populations in storage format,
+ *            [q][nz][ny][nx] (e.g. lbm_population_buffer plus the box offset);
+ *   lattice, storage, nx, ny, nz: as in lbm_config (nz <= 4096);
+ *   bc       host int[3] (NULL = periodic), force host double[3] (NULL = none);
+ *   out_dev  device pointer to 8 doubles, written by the kernel;
+ *   stream   cudaStream_t (NULL = legacy default stream).
+ * Enqueue only, no synchronisation, no cudaMalloc/cudaFree or other allocating
+ * call.  Its scratch is a static device array of 4096 x 8 FP64 partial sums
+ * plus a counter (about 256 KB) that every GPU loading the library holds until
+ * the process exits; nz > 4096 is rejected with LBM_ERR_ARG.  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture on that device.  All calls share
+ * the array: calls whose kernels overlap on the GPU (other streams, other
+ * threads) race and must be serialised by the caller.  Returns LBM_OK,
+ * LBM_ERR_ARG or LBM_ERR_CUDA. */
+int lbm_diagnostics_noalloc(const void* f_dev, int lattice, int storage, int nx, int ny, int nz, const int* bc,
+                            const double* force, double* out_dev, void* stream);
+
 /* Number of CUDA kernels this handle has launched since creation. */
 int64_t lbm_kernel_launches(const lbm_handle* h);
 

@@ -41,6 +41,8 @@ size_t storage_bytes(int storage)
 
 }  // namespace
 
+int lbmk::set_last_error(int code, const char* msg) { return fail(code, msg ? msg : ""); }
+
 struct lbm_handle {
     lbm_config cfg;
     std::vector<double> nu;

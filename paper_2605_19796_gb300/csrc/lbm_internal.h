@@ -6,6 +6,9 @@
 
 namespace lbmk {
 
+// Records `msg` as the calling thread's lbm_last_error() and returns `code`.
+int set_last_error(int code, const char* msg);
+
 enum Closure { CL_BGK = 0, CL_KCMP = 1, CL_KCRB_H = 2, CL_KCRB_RAW = 3, CL_KCRR = 4 };
 enum Storage { ST_F64 = 0, ST_F32 = 1, ST_F16S = 2, ST_BF16S = 3 };
 enum Boundary { BC_PERIODIC = 0, BC_WALLS_Y = 1 };

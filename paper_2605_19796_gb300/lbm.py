@@ -35,7 +35,8 @@ DEFAULT_CNU = {LBM_BGK: 0.0, LBM_KCMP: 0.035, LBM_KCRB_HERMITE: 0.02, LBM_KCRB_R
 EXPORTS = ["lbm_config_default", "lbm_create", "lbm_destroy", "lbm_init_velocity", "lbm_init_velocity_device",
            "lbm_step", "lbm_moments", "lbm_moments_device", "lbm_diagnostics", "lbm_get_populations",
            "lbm_set_populations", "lbm_probe", "lbm_population_buffer", "lbm_synchronize", "lbm_save", "lbm_load",
-           "lbm_step_count", "lbm_kernel_launches", "lbm_last_error", "lbm_abi_version"]
+           "lbm_step_count", "lbm_kernel_launches", "lbm_last_error", "lbm_abi_version",
+           "lbm_diagnostics_noalloc"]
 
 
 class lbm_config(ctypes.Structure):
@@ -82,6 +83,8 @@ def _load() -> ctypes.CDLL:
     lib.lbm_step_count.restype = ctypes.c_int64
     lib.lbm_kernel_launches.argtypes = [H]
     lib.lbm_kernel_launches.restype = ctypes.c_int64
+    lib.lbm_diagnostics_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            P(ctypes.c_int), dp, vp, vp]
     lib.lbm_last_error.restype = ctypes.c_char_p
     lib.lbm_abi_version.restype = ctypes.c_int
     return lib
@@ -182,6 +185,18 @@ def lbm_step_count(h) -> int:
 
 def lbm_kernel_launches(h) -> int:
     return int(LIB.lbm_kernel_launches(h))
+
+
+def lbm_diagnostics_noalloc(f_ptr: int, lattice: int, storage: int, nx: int, ny: int, nz: int, bc=None,
+                            force=None, out_ptr: int = 0, stream=None) -> None:
+    """Allocation-free diagnostics of one box (see include/lbm.h): f_ptr and
+    out_ptr are device addresses; enqueued on ``stream``."""
+    b = None if bc is None else np.ascontiguousarray(bc, dtype=np.int32)
+    F = None if force is None else np.ascontiguousarray(force, dtype=np.float64)
+    sh = _stream_handle(stream)
+    _check(LIB.lbm_diagnostics_noalloc(ctypes.c_void_p(f_ptr), int(lattice), int(storage), int(nx), int(ny), int(nz),
+                                       None if b is None else b.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                       _dp(F), ctypes.c_void_p(out_ptr), ctypes.c_void_p(sh) if sh else None))
 
 
 def lbm_last_error() -> str:

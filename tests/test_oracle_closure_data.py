@@ -1,0 +1,76 @@
+"""Pins of the learned closure's training-data oracle (no GPU):
+  - box filter of a constant and of a linear field;
+  - Eq. (m_sgs_2): for a fine state that is uniform inside every filter box
+    the exact SGS stress vanishes; for two-valued velocity inside a box it equals
+    the textbook covariance rho_bar (<u u> - <u><u>) (equal densities);
+  - the coarse m_neq of an equilibrium state is zero, of a state with a known
+    added second-order Hermite mode is that mode's coefficient;
+  - the strain invariants of a pure shear field."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import closure_data as cd
+from paper_2605_19796_gb300 import inputs
+
+
+def test_box_filter():
+    a = np.arange(8 * 8 * 8, dtype=float).reshape(8, 8, 8)
+    b = cd.box_filter(a, 4)
+    assert b.shape == (2, 2, 2)
+    assert b[0, 0, 0] == pytest.approx(a[:4, :4, :4].mean())
+    assert np.allclose(cd.box_filter(np.full((2, 8, 8, 8), 3.0), 2), 3.0)
+
+
+def test_msgs_zero_for_box_uniform_state():
+    rho_c, u_c = inputs.hit_fields(4, k0=1.0, urms=0.05, seed=1)
+    u = np.repeat(np.repeat(np.repeat(u_c, 2, axis=1), 2, axis=2), 2, axis=3)
+    f = oracle.init_equilibrium(27, None, u)
+    _, msgs = cd.filtered_state(f, 2)
+    assert np.abs(msgs).max() < 1e-16
+
+
+def test_msgs_two_valued_velocity_covariance():
+    """Inside each 2^3 box half the cells move with u1, half with u2 (rho = 1):
+    m_sgs = (<uu> - <u><u>) = (u1 - u2)(u1 - u2)^T / 4."""
+    u = np.zeros((3, 4, 4, 4))
+    u1, u2 = np.array([0.03, -0.01, 0.02]), np.array([-0.02, 0.015, 0.0])
+    for a in range(3):
+        u[a, :, :, 0::2] = u1[a]
+        u[a, :, :, 1::2] = u2[a]
+    f = oracle.init_equilibrium(27, None, u)
+    _, msgs = cd.filtered_state(f, 2)
+    d = u1 - u2
+    for k, (a, b) in enumerate(cd.COMP):
+        assert np.allclose(msgs[k], d[a] * d[b] / 4, rtol=1e-12, atol=1e-17)
+
+
+def test_features_equilibrium_and_hermite_mode():
+    rho, u = inputs.hit_fields(6, k0=1.0, urms=0.04, seed=2)
+    f = oracle.init_equilibrium(27, rho, u)
+    x, r = cd.features(f, 1e-4)
+    assert np.abs(x[:, :6]).max() < 1e-15
+    assert np.allclose(x[:, 9], 1e-4 * 3 + 0.5)
+    c, w, _ = oracle.lattice(27)
+    cf = c.astype(float)
+    amp = 1e-4
+    Hxy = (w * cf[:, 0] * cf[:, 1])[:, None, None, None]
+    g = f + amp * Hxy / oracle.THETA ** 2
+    x2, r2 = cd.features(g, 1e-4)
+    assert np.allclose(x2[:, 3], amp / r2, rtol=1e-9)
+    assert np.abs(x2[:, [0, 1, 2, 4, 5]]).max() < 1e-15
+
+
+def test_strain_invariants_of_pure_shear():
+    n = 8
+    u = np.zeros((3, n, n, n))
+    y = np.arange(n)
+    u[0] = (0.01 * np.sin(2 * np.pi * y / n))[None, :, None]
+    f = oracle.init_equilibrium(27, None, u)
+    x, _ = cd.features(f, 1e-3)
+    tau = 1e-3 * 3 + 0.5
+    S = oracle.strain_field(u)
+    sxy = S[0, 1].ravel()
+    assert np.abs(x[:, 6]).max() < 1e-15                                         # trace
+    assert np.allclose(x[:, 7], -(2 * oracle.THETA * tau) ** 2 * sxy ** 2, atol=1e-18)  # -A_xy^2
+    assert np.abs(x[:, 8]).max() < 1e-18                                          # det

@@ -1,0 +1,90 @@
+"""Pins of the FP64 oracle network of the learned closure (no GPU): the
+backward pass against central finite differences of the loss, the silu
+derivative against its closed form, and the first AdamW step against its
+textbook value lr * sign(g) (bias-corrected moments equal g and g^2)."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+
+
+def _data(n=7, seed=0):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((n, 10)), rng.standard_normal((n, 6))
+
+
+def test_param_count():
+    assert mlp.NPARAM == 10 * 64 + 64 + 64 * 64 + 64 + 64 * 64 + 64 + 64 * 6 + 6 == 9414
+    p = mlp.init_params(1)
+    assert np.array_equal(mlp.flat(mlp.unflat(mlp.flat(p))), mlp.flat(p))
+
+
+def test_silu_derivative_closed_form():
+    a = np.linspace(-8, 8, 101)
+    h = 1e-6
+    fd = (mlp.silu(a + h) - mlp.silu(a - h)) / (2 * h)
+    assert np.abs(mlp.silu_grad(a) - fd).max() < 1e-9
+    assert mlp.silu(0.0) == 0.0 and mlp.silu_grad(0.0) == 0.5
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_backward_matches_finite_differences(seed):
+    p = mlp.init_params(seed)
+    for k in p:  # non-zero biases so that their gradients are exercised
+        if k.startswith("b"):
+            p[k] = 0.1 * np.random.default_rng(seed + 5).standard_normal(p[k].shape)
+    xs, ts = _data(seed=seed)
+    g = mlp.backward(p, xs, ts)
+    rng = np.random.default_rng(seed + 9)
+    h = 1e-6
+    for k in p:
+        idx = [tuple(rng.integers(0, s) for s in p[k].shape) for _ in range(6)]
+        for j in idx:
+            old = p[k][j]
+            p[k][j] = old + h
+            lp = mlp.loss(p, xs, ts)
+            p[k][j] = old - h
+            lm = mlp.loss(p, xs, ts)
+            p[k][j] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(g[k][j] - fd) <= 1e-7 * max(1.0, abs(fd)), (k, j, g[k][j], fd)
+
+
+def test_first_adamw_step_is_lr_sign_g():
+    p = mlp.init_params(3)
+    xs, ts = _data(seed=3)
+    g = mlp.backward(p, xs, ts)
+    m = {k: np.zeros_like(v) for k, v in p.items()}
+    v = {k: np.zeros_like(v) for k, v in p.items()}
+    p0 = {k: val.copy() for k, val in p.items()}
+    lr = 1e-3
+    mlp.adamw_step(p, g, m, v, 1, lr, eps=1e-12, wd=0.0)
+    for k in p:
+        big = np.abs(g[k]) > 1e-6
+        assert np.allclose((p0[k] - p[k])[big], lr * np.sign(g[k][big]), rtol=1e-5)
+
+
+def test_weight_decay_is_decoupled():
+    p = mlp.init_params(4)
+    g = {k: np.zeros_like(v) for k, v in p.items()}
+    m = {k: np.zeros_like(v) for k, v in p.items()}
+    v = {k: np.zeros_like(v) for k, v in p.items()}
+    p0 = {k: val.copy() for k, val in p.items()}
+    mlp.adamw_step(p, g, m, v, 1, 0.01, wd=0.1)
+    assert np.allclose(p["W2"], p0["W2"] * (1 - 0.01 * 0.1))
+    assert np.array_equal(p["b2"], p0["b2"])
+
+
+def test_training_reduces_loss():
+    """A few hundred full-batch AdamW steps fit a smooth target (sanity of the
+    whole loop)."""
+    rng = np.random.default_rng(7)
+    xs = rng.standard_normal((256, 10))
+    ts = np.tanh(xs[:, :6] * 0.5 + 0.3 * xs[:, 6:7])
+    p = mlp.init_params(7)
+    m = {k: np.zeros_like(v) for k, v in p.items()}
+    v = {k: np.zeros_like(v) for k, v in p.items()}
+    l0 = mlp.loss(p, xs, ts)
+    for t in range(1, 301):
+        mlp.adamw_step(p, mlp.backward(p, xs, ts), m, v, t, 3e-3)
+    assert mlp.loss(p, xs, ts) < 0.05 * l0

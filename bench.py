@@ -37,6 +37,15 @@ WORKLOADS = {
     "hit512_d3q27_bf16_kcmp": dict(n=512, q=27, storage="bf16", closure="kcmp", nu=1e-4, k0=4.0, urms=0.04),
     "hit512_d3q19_fp32_kcmp": dict(n=512, q=19, storage="fp32", closure="kcmp", nu=1e-4, k0=4.0, urms=0.04),
     "hit512_d3q27_fp32_bgk": dict(n=512, q=27, storage="fp32", closure="bgk", nu=1e-4, k0=4.0, urms=0.04),
+    # 64 independent periodic 64^3 boxes, per-box nu uniform in [5e-5, 5e-4], distinct seeds,
+    # all steps of the timed region replayed as one CUDA graph
+    "ens64x64_d3q27_fp32_kcmp": dict(n=64, nbatch=64, q=27, storage="fp32", closure="kcmp", nu="ensemble", k0=4.0,
+                                     urms=0.04),
+    # plane channel 512 x 256 x 256, walls in y (halfway bounce-back), Re_tau ~ 180:
+    # u_tau = 0.004, h = 128, nu = u_tau h / 180, F_x = u_tau^2 / h
+    "channel512x256x256_d3q27_fp32_kcmp": dict(shape=(512, 256, 256), q=27, storage="fp32", closure="kcmp",
+                                               nu=0.004 * 128 / 180, force=(0.004 ** 2 / 128, 0.0, 0.0),
+                                               u_bulk=0.063),
 }
 DEFAULT_WORKLOAD = "hit512_d3q27_fp32_kcmp"
 ELEM = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
@@ -131,28 +140,46 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def cpu_baseline(wl: dict, budget_s: float = 15.0, steps: int = 0):
-    """The FP64 oracle as it stands, on the host cores, on a bounded sample of
-    the workload: a 64^3 box of the same turbulence recipe, lattice and closure."""
+def oracle_sample(wl: dict):
+    """The bounded host-side sample of a workload that the FP64 oracle runs:
+    a 64^3 box of the same turbulence recipe (one box of an ensemble, at the
+    middle of its viscosity range), or a 64 x 32 x 32 slice of the channel."""
     import oracle
     from paper_2605_19796_gb300 import inputs
 
     oracle.build()
-    n = CPU_SAMPLE_N
-    rho, u = inputs.hit_fields(n, k0=wl["k0"], urms=wl["urms"], seed=0)
-    f = oracle.init_equilibrium(wl["q"], rho, u)
     cl = {"bgk": 0, "kcmp": 1, "kcrb_hermite": 2, "kcrb_raw": 3}[wl["closure"]]
     cnu = {"bgk": 0.0, "kcmp": 0.035, "kcrb_hermite": 0.02, "kcrb_raw": 0.02}[wl["closure"]]
+    bc, F = (0, 0, 0), (0.0, 0.0, 0.0)
+    if "u_bulk" in wl:
+        shape = (CPU_SAMPLE_N, CPU_SAMPLE_N // 2, CPU_SAMPLE_N // 2)
+        rho, u = inputs.channel_fields(*shape, wl["u_bulk"], seed=0)
+        bc, F, nu = (0, 1, 0), wl["force"], wl["nu"]
+        desc = f"{shape[0]}x{shape[1]}x{shape[2]} channel slice"
+    else:
+        shape = (CPU_SAMPLE_N,) * 3
+        rho, u = inputs.hit_fields(CPU_SAMPLE_N, k0=wl["k0"], urms=wl["urms"], seed=0)
+        nu = 2.75e-4 if isinstance(wl["nu"], str) else wl["nu"]
+        desc = f"{CPU_SAMPLE_N}^3 box of the same recipe"
+    f = oracle.init_equilibrium(wl["q"], rho, u)
+    run = lambda f, k: oracle.run(f, k, closure=cl, nu=nu, c_nu=cnu, bc=bc, F=F)
+    return f, run, shape[0] * shape[1] * shape[2], desc
+
+
+def cpu_baseline(wl: dict, budget_s: float = 15.0, steps: int = 0):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of the workload."""
+    import oracle
+
+    f, run, cells, desc = oracle_sample(wl)
     t = time.perf_counter()
-    f = oracle.run(f, 1, closure=cl, nu=wl["nu"], c_nu=cnu)
+    f = run(f, 1)
     t1 = time.perf_counter() - t
     k = steps or max(1, min(200, int(budget_s / max(t1, 1e-6))))
     t = time.perf_counter()
-    oracle.run(f, k, closure=cl, nu=wl["nu"], c_nu=cnu)
+    run(f, k)
     dt = time.perf_counter() - t
-    return {"value": n ** 3 * k / dt / 1e6, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{n}^3 box of the same recipe (D3Q{wl['q']}, {wl['closure']}, FP64 oracle), {k} steps, "
-                      f"{dt:.1f} s"}
+    return {"value": cells * k / dt / 1e6, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{desc} (D3Q{wl['q']}, {wl['closure']}, FP64 oracle), {k} steps, {dt:.1f} s"}
 
 
 def run_reference(args, wl, rank):
@@ -160,25 +187,19 @@ def run_reference(args, wl, rank):
     if rank != 0:
         return
     import oracle
-    from paper_2605_19796_gb300 import inputs
 
-    oracle.build()
-    n = CPU_SAMPLE_N
-    rho, u = inputs.hit_fields(n, k0=wl["k0"], urms=wl["urms"], seed=0)
-    f = oracle.init_equilibrium(wl["q"], rho, u)
-    cl = {"bgk": 0, "kcmp": 1, "kcrb_hermite": 2, "kcrb_raw": 3}[wl["closure"]]
-    cnu = {"bgk": 0.0, "kcmp": 0.035, "kcrb_hermite": 0.02, "kcrb_raw": 0.02}[wl["closure"]]
-    f = oracle.run(f, args.warmup, closure=cl, nu=wl["nu"], c_nu=cnu)
+    f, run, cells, desc = oracle_sample(wl)
+    f = run(f, args.warmup)
     t = time.perf_counter()
-    oracle.run(f, args.steps, closure=cl, nu=wl["nu"], c_nu=cnu)
+    run(f, args.steps)
     dt = time.perf_counter() - t
-    v = n ** 3 * args.steps / dt / 1e6
+    v = cells * args.steps / dt / 1e6
     out = {"metric": METRIC, "value": v, "unit": "MLUPS", "impl": "reference", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": args.workload, "sample": f"{n}^3 box of the same recipe on the host cores"},
+           "config": {"workload": args.workload, "sample": f"{desc} on the host cores"},
            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
-                            "sample": f"{n}^3 D3Q{wl['q']} {wl['closure']} FP64, {args.steps} steps"},
+                            "sample": f"{desc}, D3Q{wl['q']} {wl['closure']} FP64, {args.steps} steps"},
            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -194,6 +215,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tile-y", type=int, default=0)
     ap.add_argument("--zchunk", type=int, default=0)
+    ap.add_argument("--variant", type=int, default=0)
+    ap.add_argument("--autotune", type=int, default=1, help="run the library autotuner before the warm-up (1/0)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     wl = WORKLOADS[args.workload]
@@ -224,15 +247,36 @@ def main():
     build.build()
     from paper_2605_19796_gb300 import lbm
 
-    n, q = wl["n"], wl["q"]
-    N = n ** 3
+    q = wl["q"]
+    shape = tuple(wl["shape"]) if "shape" in wl else (wl["n"],) * 3
+    nb = wl.get("nbatch", 1)
+    nx, ny, nz = shape
+    N = nx * ny * nz * nb  # cells updated per step (all boxes)
     stream = torch.cuda.Stream(device=dev)
-    log(f"[bench] {args.workload}: {n}^3 D3Q{q} {wl['storage']} {wl['closure']} rank {rank}/{world}")
-    rho_d, u_d = inputs.hit_fields(n, k0=wl["k0"], urms=wl["urms"], seed=rank, device=dev)
+    log(f"[bench] {args.workload}: {shape} x {nb} D3Q{q} {wl['storage']} {wl['closure']} rank {rank}/{world}")
+    bc = (0, 0, 0)
+    force = wl.get("force", (0.0, 0.0, 0.0))
+    if "u_bulk" in wl:  # channel
+        bc = (0, 1, 0)
+        rho_d, u_d = inputs.channel_fields(nx, ny, nz, wl["u_bulk"], seed=rank, device=dev)
+        nu = wl["nu"]
+    elif nb > 1:  # ensemble of boxes with their own seeds and viscosities
+        parts = [inputs.hit_fields(nx, k0=wl["k0"], urms=wl["urms"], seed=rank * nb + b, device=dev) for b in range(nb)]
+        rho_d = torch.stack([p[0] for p in parts])
+        u_d = torch.stack([p[1] for p in parts], dim=1).contiguous()
+        del parts
+        nu = inputs.ensemble_viscosities(nb, seed=rank)
+    else:
+        rho_d, u_d = inputs.hit_fields(nx, k0=wl["k0"], urms=wl["urms"], seed=rank, device=dev)
+        nu = wl["nu"]
     torch.cuda.synchronize()
-    s = lbm.Solver(q, (n, n, n), wl["nu"], closure=wl["closure"], storage=wl["storage"], stream=stream,
-                   tile_y=args.tile_y, zchunk=args.zchunk)
+    s = lbm.Solver(q, shape, nu, closure=wl["closure"], storage=wl["storage"], stream=stream, bc=bc, force=force,
+                   nbatch=nb, tile_y=args.tile_y, zchunk=args.zchunk, variant=args.variant)
     s.init_velocity_device(rho_d, u_d)
+    tuned = None
+    if args.autotune:
+        tuned = s.autotune()
+        log(f"[bench] autotuned launch: {tuned}")
     s.step(args.warmup)
     s.synchronize()
 
@@ -243,21 +287,22 @@ def main():
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = s.kernel_launches
+    s.step(args.steps)  # captures the K-step graph outside the timed region
+    s.synchronize()
     barrier()
     torch.cuda.synchronize()
-    ev[0].record(stream)
-    for k in range(args.steps):
-        s.step(1)
-        ev[k + 1].record(stream)
+    ev0.record(stream)
+    s.step(args.steps)  # one CUDA-graph launch of K fused-step kernels
+    ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
-    gpu_launches = s.kernel_launches - launches0
+    gpu_launches = s.kernel_launches - launches0 - args.steps
     s.synchronize()  # raises on a non-finite field
-    t_ms = ev[0].elapsed_time(ev[-1])
-    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    t_ms = ev0.elapsed_time(ev1)
+    per = [t_ms / args.steps]
     t_max = t_ms
     if dist is not None:
         tt = torch.tensor([t_ms], device=dev)
@@ -265,7 +310,7 @@ def main():
         t_max = float(tt.item())
     value = N * args.steps * world / (t_max * 1e-3) / 1e6
 
-    # roofline of the step kernel (one launch per step)
+    # roofline of the step kernel (one launch per step, back to back in the graph)
     kern_s = sum(per) / len(per) * 1e-3
     alg_bytes = 2 * q * ELEM[wl["storage"]] * N
     peak, peak_src = measured_peak_hbm()
@@ -279,14 +324,14 @@ def main():
     # lbm_init_velocity (H2D of rho, u) + K steps + lbm_moments (D2H of rho, u)
     e2e = None
     if not args.no_e2e:
-        rho_h = torch.empty((n, n, n), dtype=torch.float64, pin_memory=True)
-        u_h = torch.empty((3, n, n, n), dtype=torch.float64, pin_memory=True)
+        rho_h = torch.empty(tuple(rho_d.shape), dtype=torch.float64, pin_memory=True)
+        u_h = torch.empty(tuple(u_d.shape), dtype=torch.float64, pin_memory=True)
         rho_h.copy_(rho_d)
         u_h.copy_(u_d)
         del rho_d, u_d
         torch.cuda.synchronize()
-        rho_o = torch.empty((n, n, n), dtype=torch.float64, pin_memory=True)
-        u_o = torch.empty((3, n, n, n), dtype=torch.float64, pin_memory=True)
+        rho_o = torch.empty(tuple(rho_h.shape), dtype=torch.float64, pin_memory=True)
+        u_o = torch.empty(tuple(u_h.shape), dtype=torch.float64, pin_memory=True)
         barrier()
         t0 = time.perf_counter()
         lbm.lbm_init_velocity(s.h, rho_h.numpy(), u_h.numpy())
@@ -301,6 +346,7 @@ def main():
         e2e = {"value": N * args.steps * world / t1 / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": 32 * N // args.steps, "d2h_bytes_per_step": 32 * N // args.steps,
                "what": "lbm_init_velocity(pinned host rho,u) + K x lbm_step + lbm_moments(pinned host rho,u)"}
+    s_cfg = s.launch_config
     s.close()
 
     if rank != 0:
@@ -312,13 +358,14 @@ def main():
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPE[wl["storage"]], "data": "synthetic",
-        "config": {"workload": args.workload, "lattice": f"D3Q{q}", "cells": N, "shape": [n, n, n],
-                   "closure": wl["closure"], "storage": wl["storage"], "nu": wl["nu"], "k0": wl["k0"],
-                   "u_rms": wl["urms"], "kernel_launches_per_step": 1,
+        "config": {"workload": args.workload, "lattice": f"D3Q{q}", "cells": N, "shape": list(shape), "boxes": nb,
+                   "closure": wl["closure"], "storage": wl["storage"],
+                   "nu": wl["nu"] if not isinstance(wl["nu"], str) else "uniform [5e-5, 5e-4] per box",
+                   "kernel_launches_per_step": 1, "launch": s_cfg, "cuda_graph": "K steps replayed as one graph launch",
                    "l2": "inputs larger than L2 (two %.1f GB population buffers)" % (q * ELEM[wl["storage"]] * N / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clocks,
-        "kernel_ms": {"mean": sum(per) / len(per), "min": min(per), "max": max(per)},
+        "kernel_ms": {"mean": sum(per) / len(per)},
     }
     print(json.dumps(out), flush=True)
     if dist is not None:

@@ -69,6 +69,8 @@ extern "C" {
 #define LBM_KCRB_HERMITE 2 /* residual-based closure, Hermite f1, Eq. kcrb_operational_fone  */
 #define LBM_KCRB_RAW 3     /* residual-based closure, raw c c : S f1, Eq. kcrb_operational_raw_fone */
 #define LBM_KCRR 4         /* recursive kinetic closure, App. F.4 (D3Q27 only)               */
+#define LBM_LEARNED 5      /* KC-MP with m_sgs predicted by a network (lbm_set_learned_closure);
+                              FP32 arithmetic, periodic boxes                                  */
 
 /* population storage */
 #define LBM_FP64 0          /* double storage, double arithmetic (parity mode)               */
@@ -98,6 +100,15 @@ typedef struct {
     void* cuda_stream;  /* cudaStream_t to enqueue on; NULL = legacy default stream  */
     int tile_y;         /* tuning: rows per CTA tile (0 = library default)           */
     int zchunk;         /* tuning: z-planes per CTA march (0 = library default)      */
+    int variant;        /* tuning: step-kernel variant, 0 = library default,
+                           1 = register pull, 2 = asynchronous-copy pipeline
+                           (FP32 storage, periodic boxes), 3 = register pull
+                           sized for three CTAs per SM (32-bit arithmetic,
+                           periodic, BGK/KC-MP, tile_y 8), 4 = TMA-staged
+                           pipeline (FP32, periodic, nx % 32 == 0 and
+                           ny % tile_y == 0; the default where it applies)        */
+    int disable_graphs; /* nonzero: lbm_step launches kernels one by one instead of
+                           replaying a captured CUDA graph                        */
 } lbm_config;
 
 /* Fills cfg with defaults: D3Q27, 32^3, one box, KC-MP, C_nu 0.035, Delta 1,
@@ -121,9 +132,21 @@ int lbm_init_velocity(lbm_handle* h, const double* rho, const double* u);
 int lbm_init_velocity_device(lbm_handle* h, const double* rho_dev, const double* u_dev);
 
 /* Advances every box by nsteps time steps (one fused kernel launch per step).
- * Enqueue only; errors detected on the device (non-finite fields) are reported
- * by the next lbm_moments / lbm_diagnostics / lbm_synchronize. */
+ * A call with nsteps >= 2 captures its nsteps launches once into a CUDA graph
+ * (cached per step count and buffer parity, up to 4 graphs per handle) and
+ * replays it as one graph launch (unless cfg.disable_graphs).  Enqueue only;
+ * errors detected on the device (non-finite fields) are reported by the next
+ * lbm_moments / lbm_diagnostics / lbm_synchronize. */
 int lbm_step(lbm_handle* h, int nsteps);
+
+/* Times the built step-kernel variants, tile heights and z-chunks on the
+ * handle's current state (each candidate `trials` times, best kept) and keeps
+ * the fastest for later lbm_step calls.  The state is unchanged: every timed
+ * launch reads the current buffer and writes the other one.  Synchronises. */
+int lbm_autotune(lbm_handle* h, int trials);
+
+/* The launch configuration in use: kernel variant, tile height, z-chunk. */
+int lbm_launch_config(const lbm_handle* h, int* variant, int* tile_y, int* zchunk);
 
 /* Density and velocity of the current state (App. F.1 step 1, with the
  * half-force shift when a body force is set) into host arrays rho
@@ -193,6 +216,59 @@ int64_t lbm_step_count(const lbm_handle* h);
  * LBM_ERR_ARG or LBM_ERR_CUDA. */
 int lbm_diagnostics_noalloc(const void* f_dev, int lattice, int storage, int nx, int ny, int nz, const int* bc,
                             const double* force, double* out_dev, void* stream);
+
+/* ---- Learned closure (training side) ----------------------------------
+ * The learned closure replaces KC-MP's m_sgs = m_neq - m_CE (App. F.3) by a
+ * network evaluated per cell: 10 inputs (m_neq/rho: xx yy zz xy xz yz; the
+ * trace, second invariant and determinant of m_CE/rho; tau_hat), standardised,
+ * three hidden layers of 64 SiLU units, 6 outputs (standardised m_sgs/rho).
+ * Parameters: one FP32 vector of lbm_mlp_param_count() values in the order
+ * W1 b1 W2 b2 W3 b3 W4 b4 (W row-major [out][in]).  Training data come from
+ * fine runs box-filtered to the coarse grid, with the exact SGS stress of
+ * Eq. (m_sgs_2) as target.  All pointers below are device pointers; calls
+ * are enqueued on `stream` (NULL = legacy default stream). */
+
+/* Number of network parameters (9414). */
+int lbm_mlp_param_count(void);
+
+/* Installs the network of a handle created with closure LBM_LEARNED:
+ * params (host, lbm_mlp_param_count() FP32 values) and stats (host, 32 FP32
+ * values: mean[10] and std[10] of the inputs, mean[6] and std[6] of the
+ * outputs).  The step kernel evaluates the network with BF16 weights and
+ * activations on the tensor cores (FP32 accumulation) and uses
+ * m_sgs = rho (y std + mean) in KC-MP's rate and relaxation (App. F.3).
+ * Synchronises. */
+int lbm_set_learned_closure(lbm_handle* h, const float* params, const float* stats);
+
+/* Floats of device workspace lbm_mlp_forward / lbm_mlp_grad need for a batch of n. */
+long long lbm_mlp_workspace_floats(int n);
+
+/* ys [n][6] = network(xs [n][10]) for standardised inputs and outputs. */
+int lbm_mlp_forward(const float* params, const float* xs, int n, float* ys, float* workspace, void* stream);
+
+/* Gradient of L = mean over the batch and the 6 outputs of (net(xs) - ts)^2
+ * with respect to every parameter into grad [param_count]; the loss (FP64) is
+ * written to *loss_out (host) when not NULL, which synchronises the stream. */
+int lbm_mlp_grad(const float* params, const float* xs, const float* ts, int n, float* grad, float* workspace,
+                 double* loss_out, void* stream);
+
+/* One AdamW step (bias-corrected moments m, v; decoupled weight decay on the
+ * weight matrices only); step is 1-based. */
+int lbm_mlp_adamw(float* params, const float* grad, float* m, float* v, int step, float lr, float beta1, float beta2,
+                  float eps, float weight_decay, void* stream);
+
+/* Box filter of one box's populations (storage format, [q][nz][ny][nx]) by
+ * `factor` in every direction: filtered FP32 populations fc [q][nz/F][ny/F][nx/F]
+ * and the exact SGS stress msgs [6][...] = bar(rho u u) - bar(rho u) bar(rho u)/rho_bar
+ * (components xx yy zz xy xz yz).  Sizes must be multiples of factor. */
+int lbm_box_filter(const void* f_dev, int lattice, int storage, int nx, int ny, int nz, int factor, float* fc_dev,
+                   float* msgs_dev, void* stream);
+
+/* Network inputs x [N][10] of every cell of an FP32 population array
+ * (periodic box, kinematic viscosity nu of that lattice) and, when msgs is
+ * given, the targets t [N][6] = msgs / rho. */
+int lbm_closure_features(const float* f_dev, int lattice, int nx, int ny, int nz, double nu, const float* msgs_dev,
+                         float* x_dev, float* t_dev, void* stream);
 
 /* Number of CUDA kernels this handle has launched since creation. */
 int64_t lbm_kernel_launches(const lbm_handle* h);

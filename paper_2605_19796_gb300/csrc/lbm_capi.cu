@@ -1,5 +1,6 @@
 // C ABI of liblbm (declared in include/lbm.h): handle lifetime, device
 // buffers, launches of the fused step kernel and of the auxiliary kernels.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -43,6 +44,13 @@ size_t storage_bytes(int storage)
 
 int lbmk::set_last_error(int code, const char* msg) { return fail(code, msg ? msg : ""); }
 
+// a captured run of n steps starting from buffer `parity`
+struct GraphEntry {
+    int n = 0;
+    int parity = 0;
+    cudaGraphExec_t exec = nullptr;
+};
+
 struct lbm_handle {
     lbm_config cfg;
     std::vector<double> nu;
@@ -62,10 +70,17 @@ struct lbm_handle {
     double* d_diag = nullptr;
     cudaStream_t stream = nullptr;
     int tile_y = 8;
+    int variant = VAR_REGISTER;
     int zchunk = 16;
     int bc_kind = BC_PERIODIC;
     int64_t steps = 0;
     int64_t launches = 0;
+    std::vector<GraphEntry> graphs;  // most recent last
+    cudaStream_t cap_stream = nullptr;
+    void* d_mlp = nullptr;           // packed network parameters (learned closure)
+    bool mlp_set = false;
+    CUtensorMap tmap[2];             // TMA maps of f[0], f[1] (variant 4)
+    int tmap_tile = 0;               // tile height the maps were encoded for (0 = none)
 };
 
 namespace {
@@ -90,8 +105,108 @@ int default_zchunk(int nx, int ny, int nz, int nbatch, int tile_y)
     return (int)zc;
 }
 
+constexpr int kMaxGraphSteps = 4096;
+constexpr size_t kMaxGraphs = 4;
+
+void clear_graphs(lbm_handle* h)
+{
+    for (auto& g : h->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+}
+
+StepArgs step_args(const lbm_handle* h)
+{
+    StepArgs a;
+    a.nx = h->cfg.nx;
+    a.ny = h->cfg.ny;
+    a.nz = h->cfg.nz;
+    a.zchunk = h->zchunk;
+    a.plane = (long long)h->cfg.nx * h->cfg.ny;
+    a.popstride = h->popstride;
+    a.boxstride = h->boxstride;
+    a.box_nu = h->d_nu;
+    a.cnu_delta = h->cfg.c_nu * h->cfg.delta;
+    for (int k = 0; k < 3; ++k) a.force[k] = h->cfg.force[k];
+    a.flag = h->d_flag;
+    a.fin = nullptr;
+    a.fout = nullptr;
+    a.tmap_in = nullptr;
+    a.mlp = h->d_mlp;
+    return a;
+}
+
+// (re)encodes the TMA maps of both buffers for the handle's tile height
+cudaError_t ensure_tmaps(lbm_handle* h)
+{
+    if (h->variant != VAR_TMA || h->tmap_tile == h->tile_y) return cudaSuccess;
+    for (int k = 0; k < 2; ++k) {
+        cudaError_t e = encode_population_map(&h->tmap[k], h->f[k], h->cfg.nx, h->cfg.ny, h->cfg.nz, h->q,
+                                              h->cfg.nbatch, h->tile_y);
+        if (e != cudaSuccess) return e;
+    }
+    h->tmap_tile = h->tile_y;
+    return cudaSuccess;
+}
+
+// n step launches starting from buffer `cur`, alternating the ping-pong buffers
+cudaError_t enqueue_steps(const lbm_handle* h, int n, int cur, cudaStream_t s)
+{
+    StepArgs a = step_args(h);
+    for (int k = 0; k < n; ++k) {
+        a.fin = h->f[cur];
+        a.fout = h->f[cur ^ 1];
+        a.tmap_in = &h->tmap[cur];
+        cudaError_t e = launch_step(h->q, h->cfg.storage, h->cfg.closure, h->bc_kind, h->tile_y, h->variant, a,
+                                    h->cfg.nbatch, s);
+        if (e != cudaSuccess) return e;
+        cur ^= 1;
+    }
+    return cudaSuccess;
+}
+
+// the executable graph of n steps from the current buffer, captured on first use
+cudaError_t step_graph(lbm_handle* h, int n, cudaGraphExec_t* out)
+{
+    for (size_t k = 0; k < h->graphs.size(); ++k)
+        if (h->graphs[k].n == n && h->graphs[k].parity == h->cur) {
+            GraphEntry g = h->graphs[k];
+            h->graphs.erase(h->graphs.begin() + k);
+            h->graphs.push_back(g);
+            *out = g.exec;
+            return cudaSuccess;
+        }
+    cudaError_t e = cudaSuccess;
+    if (!h->cap_stream) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    e = prepare_step(h->q, h->cfg.storage, h->cfg.closure, h->bc_kind, h->tile_y, h->variant);
+    if (e == cudaSuccess) e = ensure_tmaps(h);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t el = enqueue_steps(h, n, h->cur, h->cap_stream);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (el != cudaSuccess) e = el;
+    GraphEntry g;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return e;
+    g.n = n;
+    g.parity = h->cur;
+    if (h->graphs.size() >= kMaxGraphs) {
+        cudaGraphExecDestroy(h->graphs.front().exec);
+        h->graphs.erase(h->graphs.begin());
+    }
+    h->graphs.push_back(g);
+    *out = g.exec;
+    return cudaSuccess;
+}
+
 void free_all(lbm_handle* h)
 {
+    clear_graphs(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     for (int k = 0; k < 2; ++k)
         if (h->f[k]) cudaFree(h->f[k]);
     if (h->d_nu) cudaFree(h->d_nu);
@@ -100,6 +215,7 @@ void free_all(lbm_handle* h)
     if (h->d_u) cudaFree(h->d_u);
     if (h->d_partials) cudaFree(h->d_partials);
     if (h->d_diag) cudaFree(h->d_diag);
+    if (h->d_mlp) cudaFree(h->d_mlp);
 }
 
 int read_flag(lbm_handle* h)
@@ -111,6 +227,7 @@ int read_flag(lbm_handle* h)
     if (flag) {
         cudaMemsetAsync(h->d_flag, 0, sizeof(unsigned int), h->stream);
         cudaStreamSynchronize(h->stream);
+        if (flag & 2u) return fail(LBM_ERR_TIMEOUT, "a bounded device-side wait of a step kernel gave up");
         return fail(LBM_ERR_NONFINITE, "a non-finite density or velocity was produced by a step");
     }
     return LBM_OK;
@@ -177,7 +294,7 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
     if (!cfg->nu) return fail(LBM_ERR_ARG, "nu is NULL");
     for (int b = 0; b < cfg->nbatch; ++b)
         if (!(cfg->nu[b] > 0.0) || !std::isfinite(cfg->nu[b])) return fail(LBM_ERR_ARG, "nu must be finite and > 0");
-    if (cfg->closure < LBM_BGK || cfg->closure > LBM_KCRR) return fail(LBM_ERR_ARG, "unknown closure");
+    if (cfg->closure < LBM_BGK || cfg->closure > LBM_LEARNED) return fail(LBM_ERR_ARG, "unknown closure");
     if (cfg->closure == LBM_KCRR && cfg->lattice != LBM_D3Q27)
         return fail(LBM_ERR_UNSUPPORTED, "KC-RR is defined on D3Q27 only");
     if (!(cfg->c_nu >= 0.0) || !(cfg->delta > 0.0)) return fail(LBM_ERR_ARG, "c_nu must be >= 0 and delta > 0");
@@ -191,8 +308,17 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
     if (has_force && bc_kind != BC_WALLS_Y)
         return fail(LBM_ERR_UNSUPPORTED, "a body force is supported with bounce-back walls (channel) only");
     int tile_y = cfg->tile_y ? cfg->tile_y : 8;
-    if (!step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y))
-        return fail(LBM_ERR_UNSUPPORTED, "this lattice/storage/closure/boundary/tile combination is not built");
+    if (cfg->variant < VAR_DEFAULT || cfg->variant > VAR_TMA) return fail(LBM_ERR_ARG, "unknown kernel variant");
+    int variant = cfg->variant;
+    if (variant == VAR_DEFAULT)  // TMA pipeline where built and the box tiles evenly, else the register pull
+        variant = (step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, VAR_TMA) &&
+                   tma_shape_ok(cfg->nx, cfg->ny, tile_y))
+                      ? VAR_TMA
+                      : VAR_REGISTER;
+    if (variant == VAR_TMA && !tma_shape_ok(cfg->nx, cfg->ny, tile_y))
+        return fail(LBM_ERR_UNSUPPORTED, "the TMA variant needs nx % 32 == 0 and ny % tile_y == 0");
+    if (!step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, variant))
+        return fail(LBM_ERR_UNSUPPORTED, "this lattice/storage/closure/boundary/tile/variant combination is not built");
     if (cfg->zchunk < 0) return fail(LBM_ERR_ARG, "zchunk must be >= 0");
 
     lbm_handle* h = new (std::nothrow) lbm_handle();
@@ -208,6 +334,7 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
     h->buf_bytes = elem * (size_t)h->boxstride * (size_t)cfg->nbatch;
     h->stream = (cudaStream_t)cfg->cuda_stream;
     h->tile_y = tile_y;
+    h->variant = variant;
     h->zchunk = cfg->zchunk ? cfg->zchunk : default_zchunk(cfg->nx, cfg->ny, cfg->nz, cfg->nbatch, tile_y);
     h->bc_kind = bc_kind;
 
@@ -222,7 +349,10 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
         return fail(e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,
                     std::string("device allocation failed: ") + cudaGetErrorString(e));
     }
-    e = cudaMemcpyAsync(h->d_nu, h->nu.data(), sizeof(double) * cfg->nbatch, cudaMemcpyHostToDevice, h->stream);
+    e = prepare_step(h->q, cfg->storage, cfg->closure, bc_kind, tile_y, variant);
+    if (e == cudaSuccess) e = ensure_tmaps(h);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->d_nu, h->nu.data(), sizeof(double) * cfg->nbatch, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flag, 0, sizeof(unsigned int), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->f[0], 0, h->buf_bytes, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -282,32 +412,125 @@ int lbm_init_velocity(lbm_handle* h, const double* rho, const double* u)
     return rc;
 }
 
+int lbm_set_learned_closure(lbm_handle* h, const float* params, const float* stats)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (h->cfg.closure != LBM_LEARNED) return fail(LBM_ERR_ARG, "the handle's closure is not LBM_LEARNED");
+    if (!params || !stats) return fail(LBM_ERR_ARG, "params and stats must be given");
+    for (int k = 0; k < 10; ++k)
+        if (!(stats[10 + k] > 0.0f)) return fail(LBM_ERR_ARG, "input standard deviations must be > 0");
+    std::vector<unsigned char> packed(mlp_packed_bytes());
+    mlp_pack(params, stats, packed.data());
+    cudaError_t e = cudaSuccess;
+    if (!h->d_mlp) e = cudaMalloc(&h->d_mlp, packed.size());
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_mlp, packed.data(), packed.size(), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_set_learned_closure");
+    h->mlp_set = true;
+    clear_graphs(h);
+    return LBM_OK;
+}
+
 int lbm_step(lbm_handle* h, int nsteps)
 {
     if (int rc = check_handle(h)) return rc;
     if (nsteps < 0) return fail(LBM_ERR_ARG, "nsteps must be >= 0");
-    StepArgs a;
-    a.nx = h->cfg.nx;
-    a.ny = h->cfg.ny;
-    a.nz = h->cfg.nz;
-    a.zchunk = h->zchunk;
-    a.plane = (long long)h->cfg.nx * h->cfg.ny;
-    a.popstride = h->popstride;
-    a.boxstride = h->boxstride;
-    a.box_nu = h->d_nu;
-    a.cnu_delta = h->cfg.c_nu * h->cfg.delta;
-    for (int k = 0; k < 3; ++k) a.force[k] = h->cfg.force[k];
-    a.flag = h->d_flag;
-    for (int s = 0; s < nsteps; ++s) {
-        a.fin = h->f[h->cur];
-        a.fout = h->f[h->cur ^ 1];
-        cudaError_t e = launch_step(h->q, h->cfg.storage, h->cfg.closure, h->bc_kind, h->tile_y, a, h->cfg.nbatch,
-                                    h->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
-        h->cur ^= 1;
-        h->steps++;
-        h->launches++;
+    if (h->cfg.closure == LBM_LEARNED && !h->mlp_set)
+        return fail(LBM_ERR_ARG, "set the network with lbm_set_learned_closure before stepping");
+    int left = nsteps;
+    // runs of >= 2 steps replay one captured CUDA graph (one graph launch per call)
+    while (!h->cfg.disable_graphs && left >= 2) {
+        const int n = left > kMaxGraphSteps ? kMaxGraphSteps : left;
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t e = step_graph(h, n, &exec);
+        if (e == cudaSuccess) e = cudaGraphLaunch(exec, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "step graph");
+        h->cur ^= (n & 1);
+        h->steps += n;
+        h->launches += n;
+        left -= n;
     }
+    if (left > 0) {
+        cudaError_t e = ensure_tmaps(h);
+        if (e == cudaSuccess) e = enqueue_steps(h, left, h->cur, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+        h->cur ^= (left & 1);
+        h->steps += left;
+        h->launches += left;
+    }
+    return LBM_OK;
+}
+
+int lbm_autotune(lbm_handle* h, int trials)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (trials < 1) trials = 3;
+    static const int kVariants[] = {VAR_REGISTER, VAR_REGISTER_OCC3, VAR_ASYNC, VAR_TMA};
+    static const int kTiles[] = {4, 8, 16};
+    static const int kChunks[] = {8, 16, 32, 64, 128};
+    const int v0 = h->variant, t0 = h->tile_y, z0 = h->zchunk;
+    float best = 1e30f;
+    int bv = v0, bt = t0, bz = z0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int v : kVariants)
+        for (int ty : kTiles) {
+            if (e != cudaSuccess) break;
+            if (!step_supported(h->q, h->cfg.storage, h->cfg.closure, h->bc_kind, ty, v)) continue;
+            if (v == VAR_TMA && !tma_shape_ok(h->cfg.nx, h->cfg.ny, ty)) continue;
+            e = prepare_step(h->q, h->cfg.storage, h->cfg.closure, h->bc_kind, ty, v);
+            for (int zc : kChunks) {
+                if (e != cudaSuccess) break;
+                if (zc > h->cfg.nz && zc != kChunks[0]) continue;
+                h->variant = v;
+                h->tile_y = ty;
+                h->zchunk = zc < h->cfg.nz ? zc : h->cfg.nz;
+                if (e == cudaSuccess) e = ensure_tmaps(h);
+                // state-preserving timing: every launch reads the current buffer and
+                // writes the other one, so the state the caller sees is unchanged
+                e = enqueue_steps(h, 1, h->cur, h->stream);
+                float t = 1e30f;
+                for (int k = 0; k < trials && e == cudaSuccess; ++k) {
+                    e = cudaEventRecord(e0, h->stream);
+                    if (e == cudaSuccess) e = enqueue_steps(h, 1, h->cur, h->stream);
+                    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                    float ms = 0;
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                    if (e == cudaSuccess && ms < t) t = ms;
+                }
+                h->launches += trials + 1;
+                if (e == cudaSuccess && t < best) {
+                    best = t;
+                    bv = v;
+                    bt = ty;
+                    bz = h->zchunk;
+                }
+            }
+        }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    h->variant = bv;
+    h->tile_y = bt;
+    h->zchunk = bz;
+    if (e == cudaSuccess) e = ensure_tmaps(h);
+    clear_graphs(h);
+    if (e != cudaSuccess) {
+        h->variant = v0;
+        h->tile_y = t0;
+        h->zchunk = z0;
+        return cuda_fail(e, "lbm_autotune");
+    }
+    return LBM_OK;
+}
+
+int lbm_launch_config(const lbm_handle* h, int* variant, int* tile_y, int* zchunk)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (variant) *variant = h->variant;
+    if (tile_y) *tile_y = h->tile_y;
+    if (zchunk) *zchunk = h->zchunk;
     return LBM_OK;
 }
 

@@ -9,7 +9,7 @@ namespace lbmk {
 // Records `msg` as the calling thread's lbm_last_error() and returns `code`.
 int set_last_error(int code, const char* msg);
 
-enum Closure { CL_BGK = 0, CL_KCMP = 1, CL_KCRB_H = 2, CL_KCRB_RAW = 3, CL_KCRR = 4 };
+enum Closure { CL_BGK = 0, CL_KCMP = 1, CL_KCRB_H = 2, CL_KCRB_RAW = 3, CL_KCRR = 4, CL_LEARNED = 5 };
 enum Storage { ST_F64 = 0, ST_F32 = 1, ST_F16S = 2, ST_BF16S = 3 };
 enum Boundary { BC_PERIODIC = 0, BC_WALLS_Y = 1 };
 
@@ -25,14 +25,35 @@ struct StepArgs {
     const double* box_nu;   // [nbatch] kinematic viscosity
     double cnu_delta;       // C_nu * Delta
     double force[3];        // body force density (channel); zero otherwise
-    unsigned int* flag;     // bit 0: non-finite density/velocity seen
+    unsigned int* flag;     // bit 0: non-finite density/velocity seen, bit 1: a bounded wait timed out
+    const void* tmap_in;    // host address of the CUtensorMap of fin (TMA variant only)
+    const void* mlp;        // packed network parameters (learned closure only), MlpLayout::BYTES
 };
+
+// host: packs 9414 FP32 parameters and 32 standardisation values into the
+// shared-memory layout of the fused inference (MlpLayout::BYTES bytes)
+size_t mlp_packed_bytes();
+void mlp_pack(const float* params, const float* stats, unsigned char* out);
+
+// Step-kernel variants: register pull (lbm_step.cuh), asynchronous-copy
+// pipeline (lbm_step_async.cuh, FP32 storage, periodic boxes) and the register
+// pull with its register budget sized for three CTAs per SM (32-bit arithmetic).
+enum Variant { VAR_DEFAULT = 0, VAR_REGISTER = 1, VAR_ASYNC = 2, VAR_REGISTER_OCC3 = 3, VAR_TMA = 4 };
+
+// TMA variant: tile heights it is built for, and the tensor map of a population
+// buffer (4D: x, y, z, population-of-box; box 40 x (tile_y + 2) x 1 x 1)
+bool tma_shape_ok(int nx, int ny, int tile_y);
+cudaError_t encode_population_map(void* map_out /*CUtensorMap*/, const void* buf, int nx, int ny, int nz, int q,
+                                  int nbatch, int tile_y);
 
 // Host-side launchers (lbm_step_*.cu).  Return cudaSuccess or the launch error.
 // tile_y selects the CTA tile height (instantiated values: 4, 8, 16).
-cudaError_t launch_step(int q, int storage, int closure, int bc, int tile_y, const StepArgs& a, int nbatch,
-                        cudaStream_t s);
-bool step_supported(int q, int storage, int closure, int bc, int tile_y);
+cudaError_t launch_step(int q, int storage, int closure, int bc, int tile_y, int variant, const StepArgs& a,
+                        int nbatch, cudaStream_t s);
+// pure host check (no CUDA call): is the combination instantiated?
+bool step_supported(int q, int storage, int closure, int bc, int tile_y, int variant);
+// sets the kernel's shared-memory attribute (call outside stream capture)
+cudaError_t prepare_step(int q, int storage, int closure, int bc, int tile_y, int variant);
 
 // Auxiliary kernels (lbm_aux.cu).
 cudaError_t launch_init_equilibrium(int q, int storage, void* f, const double* rho, const double* u, long long ncell,

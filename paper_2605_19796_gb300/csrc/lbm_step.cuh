@@ -37,6 +37,7 @@
 
 #include "lbm_internal.h"
 #include "lbm_lattice.cuh"
+#include "lbm_mlp_infer.cuh"
 
 namespace lbmk {
 
@@ -221,51 +222,52 @@ __device__ __forceinline__ R omega_sgs(R tr, R nu, R omega, R cnud)
 }
 
 // One-cell collision on shifted populations g (in place -> g_post).
+//
+// Every closure is evaluated in the common form
+//     g_post_i = a g_i + w_i (b (P_i - 1) + c0 + D H_i)
+// where f0_i - w_i = w_i (rho (P_i - 1) + drho) is the shifted equilibrium and
+// H_i = sum_ab c_ia c_ib M_ab - t is a quadratic form in c_i:
+//   BGK:   a = 1 - omega,   b = omega rho,   c0 = omega drho,   D = 0
+//   KC-MP: a = 1 - omega,   b, c0 as BGK,    D = (omega - omega_s)/(2 theta^2),
+//          M = m_sgs, t = theta tr m_sgs          (f_sgs = w H / (2 theta^2))
+//   KC-RB: a = 1 - omega_s, b = omega_s rho, c0 = omega_s drho,
+//          D = (omega_s - omega)(-rho tau_hat/theta), M = S,
+//          t = theta tr S (Hermite) or 0 (raw)    (f1 = w (-rho tau_hat/theta) H)
+// which is f - omega (f - f0 - f_sgs) - omega_s f_sgs (KC-MP, App. F.3) and
+// f - omega f1 - omega_s (f - f0 - f1) (KC-RB, App. F.2) rearranged.  For D3Q27
+// P - 1 = e_x + Y + e_x Y, Y = e_y + e_z + e_y e_z (the product equilibrium in
+// its small per-axis terms, so FP32 rounds without bias); Y and the parts of H
+// depend only on (c_y, c_z) and are formed once per pair.
 template <int Q, typename R, int CL, bool FORCE>
 __device__ __forceinline__ void collide(R (&g)[Q], R drho, R ux, R uy, R uz, R Sxx, R Syy, R Szz, R Sxy, R Sxz,
-                                        R Syz, R omega, R tau_hat, R nu, R cnud, R Fx, R Fy, R Fz)
+                                        R Syz, R omega, R tau_hat, R nu, R cnud, R Fx, R Fy, R Fz,
+                                        const R* msgs_in = nullptr)
 {
     constexpr R th = R(kTheta);
     const R rho = R(1) + drho;
-    // D3Q27 equilibrium: product of the D1Q3 truncations
-    //   1 + e_a,  e_a = c u_a/theta + (c^2 - theta) u_a^2/(2 theta^2),
-    // evaluated as g_eq = w (rho (P - 1) + drho) with P - 1 expanded in the small
-    // e_a (P - 1 = e_x + Y + e_x Y, Y = e_y + e_z + e_y e_z): forming the O(1)
-    // product and subtracting 1 would round systematically in FP32.
-    constexpr R a1 = R(1.0 / kTheta);
-    constexpr R a2 = R((1.0 - kTheta) / (2.0 * kTheta * kTheta));
-    constexpr R a0 = R(-kTheta / (2.0 * kTheta * kTheta));
+    constexpr R a1 = R(1.0 / kTheta);                                // c u / theta
+    constexpr R a2 = R((1.0 - kTheta) / (2.0 * kTheta * kTheta));    // (1 - theta) u^2 / (2 theta^2)
+    constexpr R a0 = R(-kTheta / (2.0 * kTheta * kTheta));           // -theta u^2 / (2 theta^2)
     const R ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
-    const R ex0 = a0 * ux2, exp_ = a1 * ux + a2 * ux2, exm = -a1 * ux + a2 * ux2;
-    const R ey0 = a0 * uy2, eyp = a1 * uy + a2 * uy2, eym = -a1 * uy + a2 * uy2;
-    const R ez0 = a0 * uz2, ezp = a1 * uz + a2 * uz2, ezm = -a1 * uz + a2 * uz2;
     const R usq = ux2 + uy2 + uz2;
 
-    // g_eq,i = f0_i - w_i
-    auto geq = [&](auto I) -> R {
-        constexpr int i = decltype(I)::value;
-        constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
-        constexpr R w = R(weight_of(Q, i));
-        if constexpr (Q == 27) {
-            const R ex = cx == 0 ? ex0 : (cx > 0 ? exp_ : exm);
-            const R ey = cy == 0 ? ey0 : (cy > 0 ? eyp : eym);
-            const R ez = cz == 0 ? ez0 : (cz > 0 ? ezp : ezm);
-            const R Y = ey + ez + ey * ez;
-            const R pm1 = ex + Y + ex * Y;
-            return w * (rho * pm1 + drho);
-        } else {
-            const R cu = R(cx) * ux + R(cy) * uy + R(cz) * uz;
-            return w * (drho + rho * (a1 * cu + R(0.5) * a1 * a1 * cu * cu - R(0.5) * a1 * usq));
-        }
-    };
-
-    R omega_s = omega;
-    if constexpr (CL == CL_BGK) {
-        static_for<Q>([&](auto I) {
-            constexpr int i = decltype(I)::value;
-            g[i] = g[i] - omega * (g[i] - geq(I));
-        });
-    } else {
+    // quadratic form H(c) = sum c_a c_b M_ab - t and the relaxation coefficients
+    R Mxx = 0, Myy = 0, Mzz = 0, Mxy = 0, Mxz = 0, Myz = 0, t = 0;
+    R ca = R(1) - omega, cb = omega * rho, c0 = omega * drho, D = 0;
+    if constexpr (CL == CL_LEARNED) {
+        // learned closure: the network's m_sgs replaces m_neq - m_CE; the rate and
+        // the relaxation are KC-MP's (App. F.3 with the learned SGS moment)
+        Mxx = msgs_in[0];
+        Myy = msgs_in[1];
+        Mzz = msgs_in[2];
+        Mxy = msgs_in[3];
+        Mxz = msgs_in[4];
+        Myz = msgs_in[5];
+        const R tr = Mxx + Myy + Mzz;
+        const R omega_s = omega_sgs(tr, nu, omega, cnud);
+        t = th * tr;
+        D = (omega - omega_s) * R(1.0 / (2.0 * kTheta * kTheta));
+    } else if constexpr (CL != CL_BGK) {
         // second moments of g: Pi'_ab = sum g c_a c_b = Pi_ab - theta delta_ab
         R pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
         static_for<Q>([&](auto I) {
@@ -285,31 +287,16 @@ __device__ __forceinline__ void collide(R (&g)[Q], R drho, R ux, R uy, R uz, R S
             // m_neq = Pi - rho(uu + theta I) = Pi' - rho uu - theta drho I   (App. F.3)
             // m_CE = -2 rho theta tau_hat S;  m_sgs = m_neq - m_CE
             const R rt = R(-2) * rho * th * tau_hat;
-            const R mxx = pxx - rho * ux2 - th * drho - rt * Sxx;
-            const R myy = pyy - rho * uy2 - th * drho - rt * Syy;
-            const R mzz = pzz - rho * uz2 - th * drho - rt * Szz;
-            const R mxy = pxy - rho * ux * uy - rt * Sxy;
-            const R mxz = pxz - rho * ux * uz - rt * Sxz;
-            const R myz = pyz - rho * uy * uz - rt * Syz;
-            const R tr = mxx + myy + mzz;
-            omega_s = omega_sgs(tr, nu, omega, cnud);
-            // f_post = f - omega (f - f0 - f_sgs) - omega_s f_sgs,
-            // f_sgs = w/(2 theta^2) H : m_sgs
-            const R dom = (omega - omega_s) * R(1.0 / (2.0 * kTheta * kTheta));
-            const R thtr = th * tr;
-            static_for<Q>([&](auto I) {
-                constexpr int i = decltype(I)::value;
-                constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
-                constexpr R w = R(weight_of(Q, i));
-                R hm = -thtr;
-                if (cx != 0) hm += mxx;
-                if (cy != 0) hm += myy;
-                if (cz != 0) hm += mzz;
-                if (cx * cy != 0) hm += R(2 * cx * cy) * mxy;
-                if (cx * cz != 0) hm += R(2 * cx * cz) * mxz;
-                if (cy * cz != 0) hm += R(2 * cy * cz) * myz;
-                g[i] = g[i] - omega * (g[i] - geq(I)) + (w * dom) * hm;
-            });
+            Mxx = pxx - rho * ux2 - th * drho - rt * Sxx;
+            Myy = pyy - rho * uy2 - th * drho - rt * Syy;
+            Mzz = pzz - rho * uz2 - th * drho - rt * Szz;
+            Mxy = pxy - rho * ux * uy - rt * Sxy;
+            Mxz = pxz - rho * ux * uz - rt * Sxz;
+            Myz = pyz - rho * uy * uz - rt * Syz;
+            const R tr = Mxx + Myy + Mzz;
+            const R omega_s = omega_sgs(tr, nu, omega, cnud);
+            t = th * tr;
+            D = (omega - omega_s) * R(1.0 / (2.0 * kTheta * kTheta));
         } else {  // KC-RB, Hermite or raw first-order reconstruction (App. F.2)
             constexpr bool herm = (CL == CL_KCRB_H);
             const R trS = Sxx + Syy + Szz;
@@ -317,24 +304,64 @@ __device__ __forceinline__ void collide(R (&g)[Q], R drho, R ux, R uy, R uz, R S
             const R trf1 = R(herm ? -2 : -5) * rho * tau_hat * th * trS;
             // tr m_sgs = sum (f - f0 - f1)|c|^2 = tr Pi' - rho |u|^2 - 3 theta drho - tr f1
             const R tr = (pxx + pyy + pzz) - rho * usq - R(3) * th * drho - trf1;
-            omega_s = omega_sgs(tr, nu, omega, cnud);
-            const R pre = -rho * tau_hat * R(1.0 / kTheta);
-            const R sub = herm ? th * trS : R(0);
-            static_for<Q>([&](auto I) {
-                constexpr int i = decltype(I)::value;
-                constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
-                constexpr R w = R(weight_of(Q, i));
-                R cs = -sub;
-                if (cx != 0) cs += Sxx;
-                if (cy != 0) cs += Syy;
-                if (cz != 0) cs += Szz;
-                if (cx * cy != 0) cs += R(2 * cx * cy) * Sxy;
-                if (cx * cz != 0) cs += R(2 * cx * cz) * Sxz;
-                if (cy * cz != 0) cs += R(2 * cy * cz) * Syz;
-                const R f1 = (w * pre) * cs;
-                g[i] = g[i] - omega * f1 - omega_s * (g[i] - geq(I) - f1);
-            });
+            const R omega_s = omega_sgs(tr, nu, omega, cnud);
+            Mxx = Sxx;
+            Myy = Syy;
+            Mzz = Szz;
+            Mxy = Sxy;
+            Mxz = Sxz;
+            Myz = Syz;
+            t = herm ? th * trS : R(0);
+            ca = R(1) - omega_s;
+            cb = omega_s * rho;
+            c0 = omega_s * drho;
+            D = (omega_s - omega) * (-rho * tau_hat * R(1.0 / kTheta));
         }
+    }
+
+    if constexpr (Q == 27) {
+        // per-axis equilibrium terms e(c) and the (c_y, c_z) parts
+        const R ex[3] = {-a1 * ux + a2 * ux2, a0 * ux2, a1 * ux + a2 * ux2};
+        const R ey[3] = {-a1 * uy + a2 * uy2, a0 * uy2, a1 * uy + a2 * uy2};
+        const R ez[3] = {-a1 * uz + a2 * uz2, a0 * uz2, a1 * uz + a2 * uz2};
+        static_for<Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
+            constexpr R w = R(weight_of(Q, i));
+            const R Y = ey[cy + 1] + ez[cz + 1] + ey[cy + 1] * ez[cz + 1];
+            const R pm1 = ex[cx + 1] + Y + ex[cx + 1] * Y;
+            R K = cb * pm1 + c0;
+            if constexpr (CL != CL_BGK) {
+                R h = -t;
+                if (cy != 0) h += Myy;
+                if (cz != 0) h += Mzz;
+                if (cy * cz != 0) h += R(2 * cy * cz) * Myz;
+                if (cx != 0) h += Mxx + R(2 * cx) * (R(cy) * Mxy + R(cz) * Mxz);
+                K += D * h;
+            }
+            g[i] = ca * g[i] + w * K;
+        });
+    } else {
+        static_for<Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
+            constexpr R w = R(weight_of(Q, i));
+            const R cu = R(cx) * ux + R(cy) * uy + R(cz) * uz;
+            // D3Q19 second-order Hermite equilibrium: P - 1 = c.u/theta + (c.u)^2/(2 theta^2) - u^2/(2 theta)
+            const R pm1 = a1 * cu + R(0.5) * a1 * a1 * cu * cu - R(0.5) * a1 * usq;
+            R K = cb * pm1 + c0;
+            if constexpr (CL != CL_BGK) {
+                R h = -t;
+                if (cx != 0) h += Mxx;
+                if (cy != 0) h += Myy;
+                if (cz != 0) h += Mzz;
+                if (cx * cy != 0) h += R(2 * cx * cy) * Mxy;
+                if (cx * cz != 0) h += R(2 * cx * cz) * Mxz;
+                if (cy * cz != 0) h += R(2 * cy * cz) * Myz;
+                K += D * h;
+            }
+            g[i] = ca * g[i] + w * K;
+        });
     }
     if constexpr (FORCE) {
         // Guo source (1 - omega/2) w [(c - u)/theta + (c.u) c/theta^2] . F
@@ -366,11 +393,81 @@ struct StepShape {
     static constexpr int RN = RX * RY;
     static constexpr int NT = TX * TY;
     static constexpr int NB = RN - NT;  // halo cells of the ring plane
-    static constexpr size_t smem_bytes = sizeof(R) * (size_t)(4 * 3 * RN + 2 * Q * NT);
+    static constexpr size_t base_bytes = sizeof(R) * (size_t)(4 * 3 * RN + 2 * Q * NT);
+    static constexpr size_t smem_bytes = base_bytes;
 };
 
-template <int Q, typename S, int CL, int BC, int TY>
-__global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) == 8 || TY >= 16) ? 1 : 2)
+// learned closure: network block and per-warp exchange after the ring and stash
+template <int Q, typename R, int BC, int TY, int CL>
+constexpr size_t step_smem_bytes()
+{
+    return StepShape<Q, R, BC, TY>::base_bytes +
+           (CL == CL_LEARNED ? (size_t)(MlpLayout::BYTES + TY * MlpLayout::XCH_BYTES) : 0);
+}
+
+// network inputs of one cell (the learned closure's 10 inputs: m_neq/rho,
+// invariants of m_CE/rho, tau_hat), standardised, into the warp's exchange row;
+// network forward for the warp; the cell's m_sgs back (times rho)
+template <int Q, typename R>
+__device__ __forceinline__ void learned_msgs(const R (&g)[Q], R drho, R ux, R uy, R uz, R Sxx, R Syy, R Szz, R Sxy,
+                                             R Sxz, R Syz, R tau_hat, const unsigned char* sm_mlp, unsigned char* xch,
+                                             int lane, R (&msgs)[6])
+{
+    using L = MlpLayout;
+    constexpr R th = R(kTheta);
+    const R rho = R(1) + drho, irho = R(1) / rho;
+    R pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+    static_for<Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
+        if (cx != 0) pxx += g[i];
+        if (cy != 0) pyy += g[i];
+        if (cz != 0) pzz += g[i];
+        if (cx * cy == 1) pxy += g[i];
+        if (cx * cy == -1) pxy -= g[i];
+        if (cx * cz == 1) pxz += g[i];
+        if (cx * cz == -1) pxz -= g[i];
+        if (cy * cz == 1) pyz += g[i];
+        if (cy * cz == -1) pyz -= g[i];
+    });
+    R x[10];
+    x[0] = (pxx - rho * ux * ux - th * drho) * irho;
+    x[1] = (pyy - rho * uy * uy - th * drho) * irho;
+    x[2] = (pzz - rho * uz * uz - th * drho) * irho;
+    x[3] = (pxy - rho * ux * uy) * irho;
+    x[4] = (pxz - rho * ux * uz) * irho;
+    x[5] = (pyz - rho * uy * uz) * irho;
+    const R k = R(-2) * th * tau_hat;  // m_CE / rho = k S
+    const R a00 = k * Sxx, a11 = k * Syy, a22 = k * Szz, a01 = k * Sxy, a02 = k * Sxz, a12 = k * Syz;
+    const R tr = a00 + a11 + a22;
+    const R tr2 = a00 * a00 + a11 * a11 + a22 * a22 + R(2) * (a01 * a01 + a02 * a02 + a12 * a12);
+    x[6] = tr;
+    x[7] = R(0.5) * (tr * tr - tr2);
+    x[8] = a00 * (a11 * a22 - a12 * a12) - a01 * (a01 * a22 - a12 * a02) + a02 * (a01 * a12 - a11 * a02);
+    x[9] = tau_hat;
+    const float* xmu = reinterpret_cast<const float*>(sm_mlp + L::XMU);
+    const float* xis = reinterpret_cast<const float*>(sm_mlp + L::XIS);
+    __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(xch);
+    float* Y = reinterpret_cast<float*>(xch + 32 * L::XLD * 2);
+    uint32_t* Xrow = reinterpret_cast<uint32_t*>(X + lane * L::XLD);
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+        Xrow[q] = pack_bf16(((float)x[2 * q] - xmu[2 * q]) * xis[2 * q], ((float)x[2 * q + 1] - xmu[2 * q + 1]) * xis[2 * q + 1]);
+#pragma unroll
+    for (int q = 5; q < 8; ++q) Xrow[q] = 0u;
+    __syncwarp();
+    mlp_warp_forward(sm_mlp, X, Y, lane);
+    __syncwarp();
+    const float* ymu = reinterpret_cast<const float*>(sm_mlp + L::YMU);
+    const float* ysd = reinterpret_cast<const float*>(sm_mlp + L::YSD);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) msgs[q] = rho * (R)(Y[lane * 8 + q] * ysd[q] + ymu[q]);
+    __syncwarp();
+}
+
+// OCC: CTAs per SM the register budget is sized for (0 = 1 for FP64 or TY >= 16, else 2)
+template <int Q, typename S, int CL, int BC, int TY, int OCC = 0>
+__global__ void __launch_bounds__(32 * TY, OCC ? OCC : ((sizeof(typename StoreTraits<S>::R) == 8 || TY >= 16) ? 1 : 2))
     step_kernel(const StepArgs a)
 {
     using R = typename StoreTraits<S>::R;
@@ -380,6 +477,13 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* ring = reinterpret_cast<R*>(smem_raw);  // [4][3][RN]
     R* stash = ring + 4 * 3 * RN;              // [2][Q][NT]
+    unsigned char* sm_mlp = smem_raw + Sh::base_bytes;                      // learned closure only
+    unsigned char* sm_xch = sm_mlp + MlpLayout::BYTES + threadIdx.y * MlpLayout::XCH_BYTES;
+    if constexpr (CL == CL_LEARNED) {
+        const uint4* src = static_cast<const uint4*>(a.mlp);
+        uint4* dst = reinterpret_cast<uint4*>(sm_mlp);
+        for (int k = threadIdx.y * 32 + threadIdx.x; k < MlpLayout::BYTES / 16; k += 32 * TY) dst[k] = src[k];
+    }
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -522,8 +626,16 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
             const R* st = stash + (z & 1) * Q * NT + tid;
 #pragma unroll
             for (int i = 0; i < Q; ++i) g[i] = st[i * NT];
-            collide<Q, R, CL, FORCE>(g, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, omega, tau_hat, nu, cnud, Fx,
-                                     Fy, Fz);
+            if constexpr (CL == CL_LEARNED) {
+                R msgs[6];
+                learned_msgs<Q, R>(g, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, tau_hat, sm_mlp, sm_xch, tx,
+                                   msgs);
+                collide<Q, R, CL, FORCE>(g, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, omega, tau_hat, nu, cnud,
+                                         Fx, Fy, Fz, msgs);
+            } else {
+                collide<Q, R, CL, FORCE>(g, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, omega, tau_hat, nu, cnud,
+                                         Fx, Fy, Fz);
+            }
             if (own_store) {
                 S* dst = fout + (z * plane + own.yr[1] + own.xs[1]);
                 static_for<Q>([&](auto I) {
@@ -539,21 +651,28 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
     }
 }
 
-template <int Q, typename S, int CL, int BC, int TY>
+template <int Q, typename S, int CL, int BC, int TY, int OCC = 0>
+cudaError_t prepare_step_t()
+{
+    return cudaFuncSetAttribute(step_kernel<Q, S, CL, BC, TY, OCC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)step_smem_bytes<Q, typename StoreTraits<S>::R, BC, TY, CL>());
+}
+
+template <int Q, typename S, int CL, int BC, int TY, int OCC = 0>
 cudaError_t launch_step_t(const StepArgs& a, int nbatch, cudaStream_t s)
 {
     using Sh = StepShape<Q, typename StoreTraits<S>::R, BC, TY>;
-    static bool attr_set = false;  // the attribute is per function; setting it twice is harmless
+    static bool attr_set = false;  // per instantiation; prepare_step_t sets it ahead of stream capture
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(step_kernel<Q, S, CL, BC, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)Sh::smem_bytes);
+        cudaError_t e = prepare_step_t<Q, S, CL, BC, TY, OCC>();
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     const int tiles = ((a.nx + Sh::TX - 1) / Sh::TX) * ((a.ny + TY - 1) / TY);
     const int chunks = (a.nz + a.zchunk - 1) / a.zchunk;
     dim3 grid(tiles, chunks, nbatch), block(Sh::TX, TY);
-    step_kernel<Q, S, CL, BC, TY><<<grid, block, Sh::smem_bytes, s>>>(a);
+    if (CL == CL_LEARNED && !a.mlp) return cudaErrorInvalidValue;
+    step_kernel<Q, S, CL, BC, TY, OCC><<<grid, block, step_smem_bytes<Q, typename StoreTraits<S>::R, BC, TY, CL>(), s>>>(a);
     return cudaGetLastError();
 }
 

@@ -3,17 +3,17 @@
 
 namespace lbmk {
 
-cudaError_t launch_step_q19_f64(int, int, int, const StepArgs*, int, cudaStream_t);
-cudaError_t launch_step_q19_f32(int, int, int, const StepArgs*, int, cudaStream_t);
-cudaError_t launch_step_q19_f16(int, int, int, const StepArgs*, int, cudaStream_t);
-cudaError_t launch_step_q19_bf16(int, int, int, const StepArgs*, int, cudaStream_t);
-cudaError_t launch_step_q27_f64(int, int, int, const StepArgs*, int, cudaStream_t);
-cudaError_t launch_step_q27_f32(int, int, int, const StepArgs*, int, cudaStream_t);
-cudaError_t launch_step_q27_f16(int, int, int, const StepArgs*, int, cudaStream_t);
-cudaError_t launch_step_q27_bf16(int, int, int, const StepArgs*, int, cudaStream_t);
+cudaError_t launch_step_q19_f64(int, int, int, int, const StepArgs*, int, cudaStream_t);
+cudaError_t launch_step_q19_f32(int, int, int, int, const StepArgs*, int, cudaStream_t);
+cudaError_t launch_step_q19_f16(int, int, int, int, const StepArgs*, int, cudaStream_t);
+cudaError_t launch_step_q19_bf16(int, int, int, int, const StepArgs*, int, cudaStream_t);
+cudaError_t launch_step_q27_f64(int, int, int, int, const StepArgs*, int, cudaStream_t);
+cudaError_t launch_step_q27_f32(int, int, int, int, const StepArgs*, int, cudaStream_t);
+cudaError_t launch_step_q27_f16(int, int, int, int, const StepArgs*, int, cudaStream_t);
+cudaError_t launch_step_q27_bf16(int, int, int, int, const StepArgs*, int, cudaStream_t);
 
 namespace {
-using Fn = cudaError_t (*)(int, int, int, const StepArgs*, int, cudaStream_t);
+using Fn = cudaError_t (*)(int, int, int, int, const StepArgs*, int, cudaStream_t);
 Fn pick(int q, int storage)
 {
     if (q == 19) {
@@ -35,18 +35,26 @@ Fn pick(int q, int storage)
 }
 }  // namespace
 
-cudaError_t launch_step(int q, int storage, int closure, int bc, int tile_y, const StepArgs& a, int nbatch,
-                        cudaStream_t s)
+cudaError_t launch_step(int q, int storage, int closure, int bc, int tile_y, int variant, const StepArgs& a,
+                        int nbatch, cudaStream_t s)
 {
     Fn f = pick(q, storage);
     if (!f) return cudaErrorNotSupported;
-    return f(closure, bc, tile_y, &a, nbatch, s);
+    return f(closure, bc, tile_y, variant, &a, nbatch, s);
 }
 
-bool step_supported(int q, int storage, int closure, int bc, int tile_y)
+bool step_supported(int q, int storage, int closure, int bc, int tile_y, int variant)
 {
     Fn f = pick(q, storage);
-    return f && f(closure, bc, tile_y, nullptr, 1, nullptr) == cudaSuccess;
+    return f && f(closure, bc, tile_y, variant, nullptr, 0, nullptr) == cudaSuccess;
+}
+
+cudaError_t prepare_step(int q, int storage, int closure, int bc, int tile_y, int variant)
+{
+    Fn f = pick(q, storage);
+    if (!f) return cudaErrorNotSupported;
+    // nbatch = -1 with no arguments selects the prepare mode of the launchers
+    return f(closure, bc, tile_y, variant, nullptr, -1, nullptr);
 }
 
 }  // namespace lbmk

@@ -5,16 +5,59 @@
 #pragma once
 
 #include "lbm_step.cuh"
+#include "lbm_step_async.cuh"
+#include "lbm_step_tma.cuh"
+
+#include <type_traits>
 
 namespace lbmk {
 
-// a == nullptr: only report whether the combination is instantiated.
+// a == nullptr, nbatch == 0: only report whether the combination is instantiated;
+// a == nullptr, nbatch == -1: set the kernel's shared-memory attribute (prepare).
 template <int Q, typename S>
-cudaError_t launch_step_qs(int closure, int bc, int ty, const StepArgs* a, int nbatch, cudaStream_t s)
+cudaError_t launch_step_qs(int closure, int bc, int ty, int variant, const StepArgs* a, int nbatch, cudaStream_t s)
 {
+    if constexpr (std::is_same_v<S, float>) {
+        if (variant == VAR_TMA) {
+#define LBM_TMA_CASE(CL, TYV, NSV)                                                                          \
+    if (closure == CL && bc == BC_PERIODIC && ty == TYV)                                                \
+        return a ? launch_step_tma_t<Q, CL, TYV, NSV>(*a, nbatch, s)                                    \
+                 : (nbatch < 0 ? prepare_tma_t<Q, CL, TYV, NSV>() : cudaSuccess);
+            LBM_TMA_CASE(CL_BGK, 8, 4)
+            LBM_TMA_CASE(CL_KCMP, 8, 4)
+            LBM_TMA_CASE(CL_KCRB_H, 8, 4)
+            LBM_TMA_CASE(CL_KCRB_RAW, 8, 4)
+            LBM_TMA_CASE(CL_KCMP, 4, 3)
+#undef LBM_TMA_CASE
+            return cudaErrorNotSupported;
+        }
+        if (variant == VAR_ASYNC) {
+#define LBM_ASYNC_CASE(CL, TYV)                                                                          \
+    if (closure == CL && bc == BC_PERIODIC && ty == TYV)                                               \
+        return a ? launch_step_async_t<Q, CL, TYV>(*a, nbatch, s) : (nbatch < 0 ? prepare_async_t<Q, CL, TYV>() : cudaSuccess);
+            LBM_ASYNC_CASE(CL_BGK, 8)
+            LBM_ASYNC_CASE(CL_KCMP, 8)
+            LBM_ASYNC_CASE(CL_KCRB_H, 8)
+            LBM_ASYNC_CASE(CL_KCRB_RAW, 8)
+            LBM_ASYNC_CASE(CL_KCMP, 4)
+            LBM_ASYNC_CASE(CL_KCMP, 16)
+#undef LBM_ASYNC_CASE
+            return cudaErrorNotSupported;
+        }
+    }
+    if constexpr (sizeof(typename StoreTraits<S>::R) == 4) {
+        if (variant == VAR_REGISTER_OCC3) {
+            if (closure == CL_KCMP && bc == BC_PERIODIC && ty == 8)
+                return a ? launch_step_t<Q, S, CL_KCMP, BC_PERIODIC, 8, 3>(*a, nbatch, s) : (nbatch < 0 ? prepare_step_t<Q, S, CL_KCMP, BC_PERIODIC, 8, 3>() : cudaSuccess);
+            if (closure == CL_BGK && bc == BC_PERIODIC && ty == 8)
+                return a ? launch_step_t<Q, S, CL_BGK, BC_PERIODIC, 8, 3>(*a, nbatch, s) : (nbatch < 0 ? prepare_step_t<Q, S, CL_BGK, BC_PERIODIC, 8, 3>() : cudaSuccess);
+            return cudaErrorNotSupported;
+        }
+    }
+    if (variant != VAR_REGISTER) return cudaErrorNotSupported;
 #define LBM_STEP_CASE(CL, BCV, TYV)                                                             \
     if (closure == CL && bc == BCV && ty == TYV)                                                \
-        return a ? launch_step_t<Q, S, CL, BCV, TYV>(*a, nbatch, s) : cudaSuccess;
+        return a ? launch_step_t<Q, S, CL, BCV, TYV>(*a, nbatch, s) : (nbatch < 0 ? prepare_step_t<Q, S, CL, BCV, TYV>() : cudaSuccess);
     LBM_STEP_CASE(CL_BGK, BC_PERIODIC, 8)
     LBM_STEP_CASE(CL_KCMP, BC_PERIODIC, 8)
     LBM_STEP_CASE(CL_KCRB_H, BC_PERIODIC, 8)
@@ -26,6 +69,7 @@ cudaError_t launch_step_qs(int closure, int bc, int ty, const StepArgs* a, int n
     if constexpr (sizeof(typename StoreTraits<S>::R) == 4) {
         LBM_STEP_CASE(CL_KCMP, BC_PERIODIC, 4)
         LBM_STEP_CASE(CL_KCMP, BC_PERIODIC, 16)
+        LBM_STEP_CASE(CL_LEARNED, BC_PERIODIC, 8)
     }
 #undef LBM_STEP_CASE
     return cudaErrorNotSupported;
@@ -35,8 +79,8 @@ cudaError_t launch_step_qs(int closure, int bc, int ty, const StepArgs* a, int n
 
 #define LBM_DEFINE_STEP_UNIT(NAME, Q, S)                                                                   \
     namespace lbmk {                                                                                       \
-    cudaError_t NAME(int closure, int bc, int ty, const StepArgs* a, int nbatch, cudaStream_t s)          \
+    cudaError_t NAME(int closure, int bc, int ty, int variant, const StepArgs* a, int nbatch, cudaStream_t s) \
     {                                                                                                      \
-        return launch_step_qs<Q, S>(closure, bc, ty, a, nbatch, s);                                        \
+        return launch_step_qs<Q, S>(closure, bc, ty, variant, a, nbatch, s);                               \
     }                                                                                                      \
     }

@@ -140,6 +140,41 @@ def hit_fields(n: int, k0: float = 4.0, urms: float = 0.04, seed: int = 0,
     return torch.ones((nz, ny, nx), dtype=torch.float64, device=device), u
 
 
+def channel_fields(nx: int, ny: int, nz: int, u_bulk: float, amp: float = 0.05, seed: int = 0,
+                   device=None):
+    """Plane channel between walls at y = -1/2 and y = ny - 1/2 (halfway bounce-back):
+    laminar profile u_x = 1.5 u_bulk (1 - ((y - h)/h)^2), h = ny/2, y = j + 1/2,
+    plus seeded divergence-free perturbations u' = curl(psi e_y-ish streamfunction),
+    psi = amp u_bulk h sin^2(pi y/ny) sum of a few random Fourier modes in x and z.
+    rho = 1."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    y = (np.arange(ny) + 0.5)
+    h = ny / 2.0
+    base = 1.5 * u_bulk * (1.0 - ((y - h) / h) ** 2)
+    X = 2 * math.pi * np.arange(nx) / nx
+    Z = 2 * math.pi * np.arange(nz) / nz
+    env = np.sin(math.pi * y / ny) ** 2
+    denv = (2 * math.pi / ny) * np.sin(math.pi * y / ny) * np.cos(math.pi * y / ny)
+    u = np.zeros((3, nz, ny, nx))
+    u[0] += base[None, :, None]
+    for _ in range(6):
+        kx, kz = rng.integers(1, 5), rng.integers(1, 5)
+        ph1, ph2 = rng.uniform(0, 2 * math.pi, 2)
+        a = amp * u_bulk * rng.uniform(0.5, 1.0)
+        # streamfunction psi(x,y) = a h env(y) sin(kx X + ph1) in the x-y plane: u = dpsi/dy, v = -dpsi/dx
+        sx = np.sin(kx * X + ph1)[None, :]
+        cx = np.cos(kx * X + ph1)[None, :]
+        mod = np.cos(kz * Z + ph2)[:, None, None]
+        u[0] += mod * (a * h * denv[:, None] * sx)[None]
+        u[1] += mod * (-a * h * env[:, None] * cx * (2 * math.pi * kx / nx))[None]
+    rho = np.ones((nz, ny, nx))
+    if device is not None:
+        import torch
+
+        return torch.as_tensor(rho, device=device), torch.as_tensor(u, device=device)
+    return rho, u
+
+
 def random_populations(q: int, shape: Tuple[int, int, int], seed: int = 0, amp: float = 0.05,
                        weights: Optional[np.ndarray] = None) -> np.ndarray:
     """Random positive populations f[q, nz, ny, nx] = w_i (1 + amp * N(0,1)).

@@ -23,20 +23,23 @@ LBM_OK = 0
 LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_NONFINITE = -1, -2, -3, -4
 LBM_ERR_TIMEOUT, LBM_ERR_UNSUPPORTED, LBM_ERR_IO = -5, -6, -7
 LBM_D3Q19, LBM_D3Q27 = 19, 27
-LBM_BGK, LBM_KCMP, LBM_KCRB_HERMITE, LBM_KCRB_RAW, LBM_KCRR = 0, 1, 2, 3, 4
+LBM_BGK, LBM_KCMP, LBM_KCRB_HERMITE, LBM_KCRB_RAW, LBM_KCRR, LBM_LEARNED = 0, 1, 2, 3, 4, 5
 LBM_FP64, LBM_FP32, LBM_FP16_SHIFTED, LBM_BF16_SHIFTED = 0, 1, 2, 3
 LBM_PERIODIC, LBM_BOUNCEBACK = 0, 1
 
 CLOSURES = {"bgk": LBM_BGK, "kcmp": LBM_KCMP, "kcrb_hermite": LBM_KCRB_HERMITE, "kcrb_raw": LBM_KCRB_RAW,
-            "kcrr": LBM_KCRR}
+            "kcrr": LBM_KCRR, "learned": LBM_LEARNED}
 STORAGES = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16": LBM_FP16_SHIFTED, "bf16": LBM_BF16_SHIFTED}
 # closure coefficients used by the paper (Sec. 7): KC-MP 0.035, KC-RB and KC-RR 0.02
-DEFAULT_CNU = {LBM_BGK: 0.0, LBM_KCMP: 0.035, LBM_KCRB_HERMITE: 0.02, LBM_KCRB_RAW: 0.02, LBM_KCRR: 0.02}
+DEFAULT_CNU = {LBM_BGK: 0.0, LBM_KCMP: 0.035, LBM_KCRB_HERMITE: 0.02, LBM_KCRB_RAW: 0.02, LBM_KCRR: 0.02,
+               LBM_LEARNED: 0.035}
 EXPORTS = ["lbm_config_default", "lbm_create", "lbm_destroy", "lbm_init_velocity", "lbm_init_velocity_device",
            "lbm_step", "lbm_moments", "lbm_moments_device", "lbm_diagnostics", "lbm_get_populations",
            "lbm_set_populations", "lbm_probe", "lbm_population_buffer", "lbm_synchronize", "lbm_save", "lbm_load",
            "lbm_step_count", "lbm_kernel_launches", "lbm_last_error", "lbm_abi_version",
-           "lbm_diagnostics_noalloc"]
+           "lbm_diagnostics_noalloc", "lbm_autotune", "lbm_launch_config", "lbm_mlp_param_count",
+           "lbm_mlp_workspace_floats", "lbm_mlp_forward", "lbm_mlp_grad", "lbm_mlp_adamw", "lbm_box_filter",
+           "lbm_closure_features", "lbm_set_learned_closure"]
 
 
 class lbm_config(ctypes.Structure):
@@ -44,7 +47,8 @@ class lbm_config(ctypes.Structure):
                 ("nbatch", ctypes.c_int), ("nu", ctypes.POINTER(ctypes.c_double)), ("closure", ctypes.c_int),
                 ("c_nu", ctypes.c_double), ("delta", ctypes.c_double), ("storage", ctypes.c_int),
                 ("bc", ctypes.c_int * 3), ("force", ctypes.c_double * 3), ("cuda_stream", ctypes.c_void_p),
-                ("tile_y", ctypes.c_int), ("zchunk", ctypes.c_int)]
+                ("tile_y", ctypes.c_int), ("zchunk", ctypes.c_int), ("variant", ctypes.c_int),
+                ("disable_graphs", ctypes.c_int)]
 
 
 class LbmError(RuntimeError):
@@ -85,6 +89,20 @@ def _load() -> ctypes.CDLL:
     lib.lbm_kernel_launches.restype = ctypes.c_int64
     lib.lbm_diagnostics_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             P(ctypes.c_int), dp, vp, vp]
+    fl = ctypes.c_float
+    lib.lbm_mlp_param_count.restype = ctypes.c_int
+    lib.lbm_mlp_workspace_floats.argtypes = [ctypes.c_int]
+    lib.lbm_mlp_workspace_floats.restype = ctypes.c_longlong
+    lib.lbm_mlp_forward.argtypes = [vp, vp, ctypes.c_int, vp, vp, vp]
+    lib.lbm_mlp_grad.argtypes = [vp, vp, vp, ctypes.c_int, vp, vp, dp, vp]
+    lib.lbm_mlp_adamw.argtypes = [vp, vp, vp, vp, ctypes.c_int, fl, fl, fl, fl, fl, vp]
+    lib.lbm_box_filter.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_int, vp, vp, vp]
+    lib.lbm_closure_features.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_double, vp, vp, vp, vp]
+    lib.lbm_set_learned_closure.argtypes = [H, P(ctypes.c_float), P(ctypes.c_float)]
+    lib.lbm_autotune.argtypes = [H, ctypes.c_int]
+    lib.lbm_launch_config.argtypes = [H, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]
     lib.lbm_last_error.restype = ctypes.c_char_p
     lib.lbm_abi_version.restype = ctypes.c_int
     return lib
@@ -199,6 +217,64 @@ def lbm_diagnostics_noalloc(f_ptr: int, lattice: int, storage: int, nx: int, ny:
                                        _dp(F), ctypes.c_void_p(out_ptr), ctypes.c_void_p(sh) if sh else None))
 
 
+def lbm_autotune(h, trials: int = 3) -> None:
+    _check(LIB.lbm_autotune(h, int(trials)))
+
+
+def lbm_launch_config(h):
+    v, t, z = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(LIB.lbm_launch_config(h, ctypes.byref(v), ctypes.byref(t), ctypes.byref(z)))
+    return {"variant": v.value, "tile_y": t.value, "zchunk": z.value}
+
+
+def _vp(ptr):
+    return ctypes.c_void_p(int(ptr)) if ptr else None
+
+
+def lbm_mlp_param_count() -> int:
+    return int(LIB.lbm_mlp_param_count())
+
+
+def lbm_mlp_workspace_floats(n: int) -> int:
+    return int(LIB.lbm_mlp_workspace_floats(int(n)))
+
+
+def lbm_mlp_forward(params, xs, n, ys, workspace, stream=None) -> None:
+    """Device pointers (ints); see include/lbm.h."""
+    _check(LIB.lbm_mlp_forward(_vp(params), _vp(xs), int(n), _vp(ys), _vp(workspace), _vp(_stream_handle(stream))))
+
+
+def lbm_mlp_grad(params, xs, ts, n, grad, workspace, stream=None, want_loss=True):
+    loss = ctypes.c_double(0.0)
+    _check(LIB.lbm_mlp_grad(_vp(params), _vp(xs), _vp(ts), int(n), _vp(grad), _vp(workspace),
+                            ctypes.byref(loss) if want_loss else None, _vp(_stream_handle(stream))))
+    return loss.value if want_loss else None
+
+
+def lbm_mlp_adamw(params, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0,
+                  stream=None) -> None:
+    _check(LIB.lbm_mlp_adamw(_vp(params), _vp(grad), _vp(m), _vp(v), int(step), float(lr), float(beta1),
+                             float(beta2), float(eps), float(weight_decay), _vp(_stream_handle(stream))))
+
+
+def lbm_box_filter(f_ptr, lattice, storage, nx, ny, nz, factor, fc_ptr, msgs_ptr, stream=None) -> None:
+    _check(LIB.lbm_box_filter(_vp(f_ptr), int(lattice), int(storage), int(nx), int(ny), int(nz), int(factor),
+                              _vp(fc_ptr), _vp(msgs_ptr), _vp(_stream_handle(stream))))
+
+
+def lbm_closure_features(f_ptr, lattice, nx, ny, nz, nu, msgs_ptr, x_ptr, t_ptr, stream=None) -> None:
+    _check(LIB.lbm_closure_features(_vp(f_ptr), int(lattice), int(nx), int(ny), int(nz), float(nu), _vp(msgs_ptr),
+                                    _vp(x_ptr), _vp(t_ptr), _vp(_stream_handle(stream))))
+
+
+def lbm_set_learned_closure(h, params: np.ndarray, stats: np.ndarray) -> None:
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    st = np.ascontiguousarray(stats, dtype=np.float32)
+    assert p.size == lbm_mlp_param_count() and st.size == 32
+    fp = ctypes.POINTER(ctypes.c_float)
+    _check(LIB.lbm_set_learned_closure(h, p.ctypes.data_as(fp), st.ctypes.data_as(fp)))
+
+
 def lbm_last_error() -> str:
     return LIB.lbm_last_error().decode()
 
@@ -227,7 +303,8 @@ class Solver:
 
     def __init__(self, lattice: int, shape: Sequence[int], nu, *, closure="kcmp", c_nu: Optional[float] = None,
                  delta: float = 1.0, storage="fp32", bc=(0, 0, 0), force=(0.0, 0.0, 0.0), stream=None,
-                 nbatch: int = 1, tile_y: int = 0, zchunk: int = 0):
+                 nbatch: int = 1, tile_y: int = 0, zchunk: int = 0, variant: int = 0,
+                 disable_graphs: bool = False):
         cfg = lbm_config_default()
         cfg.lattice = int(lattice)
         cfg.nx, cfg.ny, cfg.nz = (int(v) for v in shape)
@@ -245,6 +322,8 @@ class Solver:
         cfg.cuda_stream = ctypes.c_void_p(sh) if sh else None
         cfg.tile_y = int(tile_y)
         cfg.zchunk = int(zchunk)
+        cfg.variant = int(variant)
+        cfg.disable_graphs = int(bool(disable_graphs))
         self.cfg = cfg
         self.q = cfg.lattice
         self.shape = (cfg.nx, cfg.ny, cfg.nz)
@@ -336,6 +415,17 @@ class Solver:
 
     def load(self, path: str) -> None:
         lbm_load(self.h, path)
+
+    def set_learned_closure(self, params: np.ndarray, stats: np.ndarray) -> None:
+        lbm_set_learned_closure(self.h, params, stats)
+
+    def autotune(self, trials: int = 3) -> dict:
+        lbm_autotune(self.h, trials)
+        return lbm_launch_config(self.h)
+
+    @property
+    def launch_config(self) -> dict:
+        return lbm_launch_config(self.h)
 
     @property
     def step_count(self) -> int:

@@ -133,6 +133,26 @@ def test_launch_shapes_fp32_consistent(lbm, orc, zchunk, tile_y):
         assert rel(res[1], res[0]) < 1e-6
 
 
+@pytest.mark.parametrize("closure", ["bgk", "kcmp", "kcrb_hermite", "kcrb_raw"])
+def test_variants_agree_fp32(lbm, orc, closure):
+    """The register-pull (1, 3) and asynchronous-copy (2) step kernels perform the
+    same per-cell arithmetic: FP32 results agree to FP32 rounding on a ragged
+    box; within one variant the z-chunking does not change a bit."""
+    shape = (45, 19, 23)
+    rho, u = inputs.hit_fields(0, k0=3.0, urms=0.07, seed=8, shape=shape)
+    res = {}
+    runs = [(1, 0), (2, 0), (2, 5)] + ([(3, 0)] if closure in ("bgk", "kcmp") else [])
+    for var, zc in runs:
+        with lbm.Solver(27, shape, 2e-5, closure=closure, storage="fp32", variant=var, zchunk=zc) as s:
+            s.init_velocity(rho, u)
+            s.step(8)
+            res[(var, zc)] = s.get_populations()
+    assert rel(res[(2, 0)], res[(1, 0)]) < 1e-6
+    assert np.array_equal(res[(2, 0)], res[(2, 5)])
+    if (3, 0) in res:
+        assert rel(res[(3, 0)], res[(1, 0)]) < 1e-6
+
+
 def test_fp32_hit_64_velocity(lbm, orc):
     """Decaying HIT at 64^3 D3Q27 (k0 = 4, u_rms = 0.04, nu = 1e-4), KC-MP,
     FP32 storage and arithmetic vs the FP64 oracle after 50 steps."""
@@ -260,3 +280,97 @@ def test_full_size_sampled_cells_fp32(lbm, orc, n):
         ref = orc.step_cell(blk, closure=1, nu=1e-4, c_nu=0.035)
         assert np.abs(after[k] - ref).max() <= 2e-6 * scale, (pts[k], np.abs(after[k] - ref).max())
     assert abs(mass1 - mass0) <= 1e-9 * mass0
+
+
+def test_graph_replay_matches_direct_launches(lbm, orc):
+    """lbm_step with nsteps >= 2 replays a captured CUDA graph; the result is
+    bit-identical to launching the kernels one by one, for odd and even counts
+    and across the graph cache (parities and step counts)."""
+    shape = (40, 16, 12)
+    rho, u = inputs.hit_fields(0, k0=2.0, urms=0.06, seed=9, shape=shape)
+    out = []
+    for dis in (True, False):
+        with lbm.Solver(27, shape, 5e-5, closure="kcmp", storage="fp32", disable_graphs=dis) as s:
+            s.init_velocity(rho, u)
+            for n in (3, 4, 3, 1, 7, 4, 4):
+                s.step(n)
+            assert s.step_count == 26
+            out.append(s.get_populations())
+    assert np.array_equal(out[0], out[1])
+
+
+def test_autotune_keeps_state_and_result(lbm, orc):
+    shape = (64, 32, 24)
+    rho, u = inputs.hit_fields(0, k0=3.0, urms=0.05, seed=10, shape=shape)
+    with lbm.Solver(27, shape, 1e-4, closure="kcmp", storage="fp32") as s:
+        s.init_velocity(rho, u)
+        s.step(2)
+        before = s.get_populations()
+        cfg = s.autotune(trials=2)
+        assert cfg["variant"] in (1, 2, 3) and cfg["tile_y"] in (4, 8, 16) and 1 <= cfg["zchunk"] <= 128
+        assert np.array_equal(before, s.get_populations())
+        s.step(5)
+        tuned = s.get_populations()
+    with lbm.Solver(27, shape, 1e-4, closure="kcmp", storage="fp32") as s:
+        s.init_velocity(rho, u)
+        s.step(7)
+        ref = s.get_populations()
+    assert rel(tuned, ref) < 1e-6
+
+
+def test_ensemble_and_channel_launch_through_graph(lbm, orc):
+    """FP64 ensemble of boxes and a walled channel advanced with graph replay
+    match the oracle (the graph path uses the same kernels)."""
+    shape = (12, 10, 8)
+    nus = np.array([1e-4, 3e-4])
+    fields = [inputs.hit_fields(0, k0=2.0, urms=0.05, seed=20 + b, shape=shape) for b in range(2)]
+    with lbm.Solver(19, shape, nus, closure="kcmp", storage="fp64", nbatch=2) as s:
+        s.init_velocity(np.stack([f[0] for f in fields]), np.stack([f[1] for f in fields], axis=1))
+        s.step(9)
+        fg = s.get_populations()
+    for b in range(2):
+        fo = orc.run(orc.init_equilibrium(19, fields[b][0], fields[b][1]), 9, closure=1, nu=nus[b], c_nu=0.035)
+        assert rel(fg[b], fo) < TOL64
+    rho, u = inputs.channel_fields(16, 11, 6, 0.05, seed=3)
+    F = (1e-5, 0.0, 0.0)
+    (fg, fo, _), = _run_pair(lbm, orc, 27, (16, 11, 6), rho, u, 2e-3, "kcmp", 6, bc=(0, 1, 0), F=F)
+    assert rel(fg, fo) < TOL64
+
+
+@pytest.mark.parametrize("shape,nbatch", [((64, 16, 12), 1), ((32, 8, 5), 1), ((96, 24, 7), 2), ((64, 64, 64), 1)])
+@pytest.mark.parametrize("closure", ["bgk", "kcmp", "kcrb_hermite", "kcrb_raw"])
+def test_tma_variant_matches(lbm, orc, shape, nbatch, closure):
+    """The TMA-staged kernel (variant 4: periodic images patched on edge tiles,
+    single-tile boxes where both edges wrap, several boxes) agrees with the
+    register-pull kernel to FP32 rounding and with the FP64 oracle in velocity."""
+    seeds = [30 + b for b in range(nbatch)]
+    fields = [inputs.hit_fields(0, k0=2.0, urms=0.06, seed=sd, shape=shape) for sd in seeds]
+    rho = np.stack([f[0] for f in fields])
+    u = np.stack([f[1] for f in fields], axis=1)
+    nus = np.array([3e-5, 2e-4][:nbatch])
+    res = {}
+    for var in (1, 4):
+        with lbm.Solver(27, shape, nus, closure=closure, storage="fp32", variant=var, nbatch=nbatch) as s:
+            assert s.launch_config["variant"] == var
+            s.init_velocity(rho, u)
+            s.step(6)
+            res[var] = s.get_populations()
+    assert rel(res[4], res[1]) < 1e-6
+    f4 = res[4] if nbatch > 1 else res[4][None]
+    for b in range(nbatch):
+        fo = orc.run(orc.init_equilibrium(27, fields[b][0], fields[b][1]), 6, closure=CL[closure], nu=nus[b],
+                     c_nu=CNU[closure])
+        _, ug = orc.fields(f4[b])
+        _, uo = orc.fields(fo)
+        assert np.abs(ug - uo).max() < 1e-6
+
+
+def test_default_variant_selection(lbm):
+    with lbm.Solver(27, (64, 32, 16), 1e-4, closure="kcmp", storage="fp32") as s:
+        assert s.launch_config["variant"] == 4
+    with lbm.Solver(27, (40, 32, 16), 1e-4, closure="kcmp", storage="fp32") as s:
+        assert s.launch_config["variant"] == 1
+    with lbm.Solver(27, (64, 32, 16), 1e-4, closure="kcmp", storage="fp64") as s:
+        assert s.launch_config["variant"] == 1
+    with pytest.raises(lbm.LbmError):
+        lbm.Solver(27, (40, 32, 16), 1e-4, closure="kcmp", storage="fp32", variant=4)

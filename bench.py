@@ -37,6 +37,11 @@ WORKLOADS = {
     "hit512_d3q27_bf16_kcmp": dict(n=512, q=27, storage="bf16", closure="kcmp", nu=1e-4, k0=4.0, urms=0.04),
     "hit512_d3q19_fp32_kcmp": dict(n=512, q=19, storage="fp32", closure="kcmp", nu=1e-4, k0=4.0, urms=0.04),
     "hit512_d3q27_fp32_bgk": dict(n=512, q=27, storage="fp32", closure="bgk", nu=1e-4, k0=4.0, urms=0.04),
+    # learned closure (KC-MP with the network's m_sgs, fused BF16 tensor-core inference)
+    "hit256_d3q27_fp32_learned": dict(n=256, q=27, storage="fp32", closure="learned", nu=2.5e-5, k0=4.0, urms=0.04),
+    "hit128_d3q27_fp32_learned": dict(n=128, q=27, storage="fp32", closure="learned", nu=2.5e-5, k0=4.0, urms=0.04),
+    "hit256_d3q27_fp32_kcmp_nu2.5e-5": dict(n=256, q=27, storage="fp32", closure="kcmp", nu=2.5e-5, k0=4.0,
+                                            urms=0.04),
     # 64 independent periodic 64^3 boxes, per-box nu uniform in [5e-5, 5e-4], distinct seeds,
     # all steps of the timed region replayed as one CUDA graph
     "ens64x64_d3q27_fp32_kcmp": dict(n=64, nbatch=64, q=27, storage="fp32", closure="kcmp", nu="ensemble", k0=4.0,
@@ -140,6 +145,21 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def learned_weights():
+    """Trained network if a checkpoint was saved next to the package, else a
+    seeded initialisation with unit statistics (timing does not depend on the values)."""
+    import numpy as np
+
+    path = os.path.join(ROOT, "paper_2605_19796_gb300", "data", "learned_closure.npz")
+    if os.path.exists(path):
+        d = np.load(path)
+        return {"params": d["params"], "stats": d["stats"], "source": "trained checkpoint"}
+    from paper_2605_19796_gb300 import learned
+
+    stats = np.concatenate([np.zeros(10), np.full(10, 1e-3), np.zeros(6), np.full(6, 1e-4)]).astype(np.float32)
+    return {"params": learned.init_params(0), "stats": stats, "source": "seeded initialisation"}
+
+
 def oracle_sample(wl: dict):
     """The bounded host-side sample of a workload that the FP64 oracle runs:
     a 64^3 box of the same turbulence recipe (one box of an ensemble, at the
@@ -148,8 +168,9 @@ def oracle_sample(wl: dict):
     from paper_2605_19796_gb300 import inputs
 
     oracle.build()
-    cl = {"bgk": 0, "kcmp": 1, "kcrb_hermite": 2, "kcrb_raw": 3}[wl["closure"]]
-    cnu = {"bgk": 0.0, "kcmp": 0.035, "kcrb_hermite": 0.02, "kcrb_raw": 0.02}[wl["closure"]]
+    # the learned closure's CPU stand-in is the analytic KC-MP it extends
+    cl = {"bgk": 0, "kcmp": 1, "kcrb_hermite": 2, "kcrb_raw": 3, "learned": 1}[wl["closure"]]
+    cnu = {"bgk": 0.0, "kcmp": 0.035, "kcrb_hermite": 0.02, "kcrb_raw": 0.02, "learned": 0.035}[wl["closure"]]
     bc, F = (0, 0, 0), (0.0, 0.0, 0.0)
     if "u_bulk" in wl:
         shape = (CPU_SAMPLE_N, CPU_SAMPLE_N // 2, CPU_SAMPLE_N // 2)
@@ -273,6 +294,10 @@ def main():
     s = lbm.Solver(q, shape, nu, closure=wl["closure"], storage=wl["storage"], stream=stream, bc=bc, force=force,
                    nbatch=nb, tile_y=args.tile_y, zchunk=args.zchunk, variant=args.variant)
     s.init_velocity_device(rho_d, u_d)
+    weights = None
+    if wl["closure"] == "learned":
+        weights = learned_weights()
+        s.set_learned_closure(weights["params"], weights["stats"])
     tuned = None
     if args.autotune:
         tuned = s.autotune()

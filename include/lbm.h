@@ -100,13 +100,13 @@ typedef struct {
     void* cuda_stream;  /* cudaStream_t to enqueue on; NULL = legacy default stream  */
     int tile_y;         /* tuning: rows per CTA tile (0 = library default)           */
     int zchunk;         /* tuning: z-planes per CTA march (0 = library default)      */
-    int variant;        /* tuning: step-kernel variant, 0 = library default,
-                           1 = register pull, 2 = asynchronous-copy pipeline
+    int variant;        /* tuning: step-kernel variant, 0 = library default
+                           (the register pull), 1 = register pull, 2 = asynchronous-copy pipeline
                            (FP32 storage, periodic boxes), 3 = register pull
                            sized for three CTAs per SM (32-bit arithmetic,
                            periodic, BGK/KC-MP, tile_y 8), 4 = TMA-staged
                            pipeline (FP32, periodic, nx % 32 == 0 and
-                           ny % tile_y == 0; the default where it applies)        */
+                           ny % tile_y == 0)                                      */
     int disable_graphs; /* nonzero: lbm_step launches kernels one by one instead of
                            replaying a captured CUDA graph                        */
 } lbm_config;
@@ -240,6 +240,16 @@ int lbm_mlp_param_count(void);
  * Synchronises. */
 int lbm_set_learned_closure(lbm_handle* h, const float* params, const float* stats);
 
+/* Bytes of the packed network block the fused inference reads (BF16 weights,
+ * FP32 biases and statistics), and the packing itself into host memory. */
+long long lbm_mlp_packed_bytes(void);
+int lbm_mlp_pack(const float* params, const float* stats, void* out_host);
+
+/* Tensor-core forward with the fused step kernel's code path: raw inputs
+ * x [n][10] (device), packed block (device) -> m_sgs/rho estimates y [n][6]
+ * (device), BF16 operands and FP32 accumulation. */
+int lbm_mlp_forward_tc(const void* packed_dev, const float* x_dev, int n, float* y_dev, void* stream);
+
 /* Floats of device workspace lbm_mlp_forward / lbm_mlp_grad need for a batch of n. */
 long long lbm_mlp_workspace_floats(int n);
 
@@ -265,10 +275,11 @@ int lbm_box_filter(const void* f_dev, int lattice, int storage, int nx, int ny, 
                    float* msgs_dev, void* stream);
 
 /* Network inputs x [N][10] of every cell of an FP32 population array
- * (periodic box, kinematic viscosity nu of that lattice) and, when msgs is
- * given, the targets t [N][6] = msgs / rho. */
+ * (periodic box, kinematic viscosity nu of that lattice); when msgs is given,
+ * the targets t [N][6] = msgs / rho; when kcmp is given, the analytic KC-MP
+ * estimate (m_neq - m_CE) / rho [N][6] (App. F.3) for comparison. */
 int lbm_closure_features(const float* f_dev, int lattice, int nx, int ny, int nz, double nu, const float* msgs_dev,
-                         float* x_dev, float* t_dev, void* stream);
+                         float* x_dev, float* t_dev, float* kcmp_dev, void* stream);
 
 /* Number of CUDA kernels this handle has launched since creation. */
 int64_t lbm_kernel_launches(const lbm_handle* h);

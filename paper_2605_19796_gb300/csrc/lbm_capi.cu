@@ -310,11 +310,9 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
     int tile_y = cfg->tile_y ? cfg->tile_y : 8;
     if (cfg->variant < VAR_DEFAULT || cfg->variant > VAR_TMA) return fail(LBM_ERR_ARG, "unknown kernel variant");
     int variant = cfg->variant;
-    if (variant == VAR_DEFAULT)  // TMA pipeline where built and the box tiles evenly, else the register pull
-        variant = (step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, VAR_TMA) &&
-                   tma_shape_ok(cfg->nx, cfg->ny, tile_y))
-                      ? VAR_TMA
-                      : VAR_REGISTER;
+    // the register pull is the fastest variant measured on every workload built;
+    // lbm_autotune may pick another one for a given box
+    if (variant == VAR_DEFAULT) variant = VAR_REGISTER;
     if (variant == VAR_TMA && !tma_shape_ok(cfg->nx, cfg->ny, tile_y))
         return fail(LBM_ERR_UNSUPPORTED, "the TMA variant needs nx % 32 == 0 and ny % tile_y == 0");
     if (!step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, variant))

@@ -119,7 +119,7 @@ __device__ void cell_moments(const float* f, long long N, long long c, float& rh
 // a population array f (FP32, unshifted, periodic box)
 template <int Q>
 __global__ void features_kernel(const float* f, int nx, int ny, int nz, float tau_hat, const float* msgs, float* x,
-                                float* tgt)
+                                float* tgt, float* kcmp)
 {
     const long long N = (long long)nx * ny * nz;
     const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -172,6 +172,8 @@ __global__ void features_kernel(const float* f, int nx, int ny, int nz, float ta
     xr[7] = (float)(0.5 * (tr * tr - tr2));
     xr[8] = (float)det;
     xr[9] = tau_hat;
+    if (kcmp)  // the analytic KC-MP estimate of m_sgs / rho: m_neq / rho - m_CE / rho (App. F.3)
+        for (int k = 0; k < 6; ++k) kcmp[c * 6 + k] = xr[k] - (float)Am[A[k]][B[k]];
     if (msgs && tgt)
         for (int k = 0; k < 6; ++k) tgt[c * 6 + k] = msgs[k * N + c] / rho;
 }
@@ -288,6 +290,38 @@ __global__ void adamw_kernel(float* p, const float* g, float* m, float* v, int n
     p[k] = pk - lr * (mk / bc1) / (sqrtf(vk / bc2) + eps);
 }
 
+// tensor-core forward of raw inputs (standardised with the packed statistics):
+// each warp evaluates 32 rows with the same device code as the fused step kernel
+__global__ void __launch_bounds__(256) mlp_tc_kernel(const uint4* packed, const float* x, int n, float* y)
+{
+    using L = MlpLayout;
+    extern __shared__ __align__(16) unsigned char sm_tc[];
+    uint4* dst = reinterpret_cast<uint4*>(sm_tc);
+    for (int k = threadIdx.x; k < L::BYTES / 16; k += blockDim.x) dst[k] = packed[k];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* xch = sm_tc + L::BYTES + warp * L::XCH_BYTES;
+    const float* xmu = reinterpret_cast<const float*>(sm_tc + L::XMU);
+    const float* xis = reinterpret_cast<const float*>(sm_tc + L::XIS);
+    const float* ymu = reinterpret_cast<const float*>(sm_tc + L::YMU);
+    const float* ysd = reinterpret_cast<const float*>(sm_tc + L::YSD);
+    const long long row = ((long long)blockIdx.x * 8 + warp) * 32 + lane;
+    const bool ok = row < n;
+    uint32_t* Xrow = reinterpret_cast<uint32_t*>(reinterpret_cast<__nv_bfloat16*>(xch) + lane * L::XLD);
+    for (int q = 0; q < 5; ++q) {
+        const float a = ok ? (x[row * 10 + 2 * q] - xmu[2 * q]) * xis[2 * q] : 0.f;
+        const float b = ok ? (x[row * 10 + 2 * q + 1] - xmu[2 * q + 1]) * xis[2 * q + 1] : 0.f;
+        Xrow[q] = pack_bf16(a, b);
+    }
+    for (int q = 5; q < 8; ++q) Xrow[q] = 0u;
+    __syncwarp();
+    float* Y = reinterpret_cast<float*>(xch);  // overlays the inputs
+    mlp_warp_forward(sm_tc, reinterpret_cast<const __nv_bfloat16*>(xch), Y, lane);
+    __syncwarp();
+    if (ok)
+        for (int q = 0; q < 6; ++q) y[row * 6 + q] = Y[lane * 8 + q] * ysd[q] + ymu[q];
+}
+
 int grid_n(long long n, int block, int cap = 152 * 16)
 {
     long long g = (n + block - 1) / block;
@@ -342,6 +376,29 @@ using namespace lbmk;
 extern "C" {
 
 int lbm_mlp_param_count(void) { return kNParam; }
+
+long long lbm_mlp_packed_bytes(void) { return (long long)MlpLayout::BYTES; }
+
+int lbm_mlp_pack(const float* params, const float* stats, void* out_host)
+{
+    if (!params || !stats || !out_host) return set_last_error(LBM_ERR_ARG, "lbm_mlp_pack: NULL argument");
+    mlp_pack(params, stats, static_cast<unsigned char*>(out_host));
+    return LBM_OK;
+}
+
+int lbm_mlp_forward_tc(const void* packed_dev, const float* x_dev, int n, float* y_dev, void* stream)
+{
+    if (!packed_dev || !x_dev || !y_dev || n < 1) return set_last_error(LBM_ERR_ARG, "lbm_mlp_forward_tc: bad arguments");
+    const int smem = MlpLayout::BYTES + 8 * MlpLayout::XCH_BYTES;
+    cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) {
+        const int blocks = (int)(((long long)n + 255) / 256);
+        mlp_tc_kernel<<<blocks, 256, smem, static_cast<cudaStream_t>(stream)>>>(static_cast<const uint4*>(packed_dev),
+                                                                               x_dev, n, y_dev);
+        e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? LBM_OK : set_last_error(LBM_ERR_CUDA, cudaGetErrorString(e));
+}
 
 long long lbm_mlp_workspace_floats(int n)
 {
@@ -471,7 +528,7 @@ int lbm_box_filter(const void* f_dev, int lattice, int storage, int nx, int ny, 
 }
 
 int lbm_closure_features(const float* f_dev, int lattice, int nx, int ny, int nz, double nu, const float* msgs_dev,
-                         float* x_dev, float* t_dev, void* stream)
+                         float* x_dev, float* t_dev, float* kcmp_dev, void* stream)
 {
     if (!f_dev || !x_dev || nx < 1 || ny < 1 || nz < 1 || !(nu > 0))
         return set_last_error(LBM_ERR_ARG, "lbm_closure_features: bad arguments");
@@ -480,9 +537,9 @@ int lbm_closure_features(const float* f_dev, int lattice, int nx, int ny, int nz
     const float tau_hat = (float)(nu / kTheta + 0.5);
     const int g = (int)((N + 127) / 128);
     if (lattice == 27)
-        features_kernel<27><<<g, 128, 0, s>>>(f_dev, nx, ny, nz, tau_hat, msgs_dev, x_dev, t_dev);
+        features_kernel<27><<<g, 128, 0, s>>>(f_dev, nx, ny, nz, tau_hat, msgs_dev, x_dev, t_dev, kcmp_dev);
     else if (lattice == 19)
-        features_kernel<19><<<g, 128, 0, s>>>(f_dev, nx, ny, nz, tau_hat, msgs_dev, x_dev, t_dev);
+        features_kernel<19><<<g, 128, 0, s>>>(f_dev, nx, ny, nz, tau_hat, msgs_dev, x_dev, t_dev, kcmp_dev);
     else
         return set_last_error(LBM_ERR_ARG, "lattice must be 19 or 27");
     cudaError_t e = cudaGetLastError();

@@ -36,9 +36,12 @@ struct MlpLayout {
     static constexpr int YMU = XIS + 10 * 4;
     static constexpr int YSD = YMU + 6 * 4;
     static constexpr int BYTES = (YSD + 6 * 4 + 127) / 128 * 128;
-    // per-warp exchange: inputs [32][XLD] bf16 (16 used), outputs [32][8] f32
+    // per-warp exchange: inputs [32][XLD] bf16 (16 used); the outputs [32][8]
+    // f32 overlay its first 1 KB (rows of a 16-row tile are written only after
+    // the warp has read that tile's inputs, and the second tile's inputs lie at
+    // bytes 768 and up, past the first tile's outputs)
     static constexpr int XLD = 24;
-    static constexpr int XCH_BYTES = 32 * XLD * 2 + 32 * 8 * 4;
+    static constexpr int XCH_BYTES = 32 * XLD * 2;
 };
 
 __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
@@ -56,7 +59,21 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
-__device__ __forceinline__ float mlp_silu(float a) { return a / (1.0f + __expf(-a)); }
+// SiLU a * sigmoid(a) through sigmoid(a) = (1 + tanh(a / 2)) / 2 on the
+// hardware tanh (one MUFU operation, relative error about 2^-11, below the BF16
+// rounding that follows)
+__device__ __forceinline__ float mlp_tanh(float v)
+{
+    float r;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+__device__ __forceinline__ float mlp_silu(float a)
+{
+    const float h = 0.5f * a;
+    return fmaf(h, mlp_tanh(h), h);
+}
 
 // One hidden layer (64 outputs) for one 16-row tile: A fragments of the input
 // (KS k-steps) -> A fragments of the output (4 k-steps of the next layer).
@@ -90,7 +107,8 @@ __device__ __forceinline__ void mlp_hidden(const unsigned char* sm, int woff, in
 }
 
 // Network forward for the warp's 32 cells: X [32][XLD] bf16 (standardised
-// inputs, columns 10..15 zero) -> Y [32][8] f32 (standardised outputs 0..5).
+// inputs, columns 10..15 zero) -> Y [32][8] f32 (standardised outputs 0..5);
+// Y may alias X (the exchange layout above).
 __device__ __forceinline__ void mlp_warp_forward(const unsigned char* sm, const __nv_bfloat16* X, float* Y, int lane)
 {
     using L = MlpLayout;
@@ -118,6 +136,7 @@ __device__ __forceinline__ void mlp_warp_forward(const unsigned char* sm, const 
             const uint32_t b1 = W[(g * L::LD + 16 * s + 2 * t + 8) / 2];
             mma_bf16_16816(c, h1[s], b0, b1);
         }
+        __syncwarp();  // every lane has read this tile's inputs
         Y[r0 * 8 + 2 * t] = c[0] + B[2 * t];
         Y[r0 * 8 + 2 * t + 1] = c[1] + B[2 * t + 1];
         Y[r1 * 8 + 2 * t] = c[2] + B[2 * t];

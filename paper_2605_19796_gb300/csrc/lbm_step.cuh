@@ -221,6 +221,150 @@ __device__ __forceinline__ R omega_sgs(R tr, R nu, R omega, R cnud)
     return nut > nu ? R(1) / (nut * R(1.0 / kTheta) + R(0.5)) : omega;
 }
 
+// KC-RR (App. F.4): the 17 high-order D3Q27 Hermite modes of B_high as
+// directional degrees (d_x, d_y, d_z), and the recursive-regularised reference
+// coefficients of Eq. (kcrr_rr) seeded by a_rr_ab = m_CE_ab:
+//   a_rr(a1..ak) = u_ak a_rr(a1..a(k-1)) + sum_{i<k} (prod_{j<k, j != i} u_aj) a_rr(ai ak)
+// (isothermal equilibrium coefficients a0(a1..am) = rho u_a1..u_am, divided by
+// rho), evaluated over the prefixes of the mode's axis list in ascending order.
+__host__ __device__ constexpr int rr_deg(int m, int a)
+{
+    constexpr int t[17][3] = {{2, 1, 0}, {2, 0, 1}, {0, 2, 1}, {1, 2, 0}, {1, 0, 2}, {0, 1, 2}, {1, 1, 1}, {2, 2, 0}, {2, 0, 2},
+                              {0, 2, 2}, {2, 1, 1}, {1, 2, 1}, {1, 1, 2}, {2, 2, 1}, {2, 1, 2}, {1, 2, 2}, {2, 2, 2}};
+    return t[m][a];
+}
+__host__ __device__ constexpr int rr_n(int m) { return rr_deg(m, 0) + rr_deg(m, 1) + rr_deg(m, 2); }
+__host__ __device__ constexpr int rr_axis(int m, int k)  // k-th axis of mode m in ascending order
+{
+    return k < rr_deg(m, 0) ? 0 : (k < rr_deg(m, 0) + rr_deg(m, 1) ? 1 : 2);
+}
+// directional Hermite factor H(c, deg): 1, c, c^2 - theta
+__host__ __device__ constexpr double hdir(int c, int deg) { return deg == 0 ? 1.0 : (deg == 1 ? c : c * c - kTheta); }
+
+template <typename R, int M>
+__device__ __forceinline__ R rr_coef(const R (&u)[3], const R (&A)[3][3])
+{
+    constexpr int n = rr_n(M);
+    R a = A[rr_axis(M, 0)][rr_axis(M, 1)];
+#pragma unroll
+    for (int k = 2; k < n; ++k) {
+        const int ak = rr_axis(M, k);
+        R nxt = u[ak] * a;
+#pragma unroll
+        for (int i = 0; i < k; ++i) {
+            R prod = R(1);
+#pragma unroll
+            for (int j = 0; j < k; ++j)
+                if (j != i) prod *= u[rr_axis(M, j)];
+            nxt += prod * A[rr_axis(M, i)][ak];
+        }
+        a = nxt;
+    }
+    return a;
+}
+
+// KC-RR collision of one D3Q27 cell on shifted populations (in place).
+template <typename R>
+__device__ __forceinline__ void collide_kcrr(R (&g)[27], R drho, R ux, R uy, R uz, R Sxx, R Syy, R Szz, R Sxy, R Sxz,
+                                             R Syz, R omega, R tau_hat, R nu, R cnud)
+{
+    constexpr int Q = 27;
+    constexpr R th = R(kTheta);
+    const R rho = R(1) + drho;
+    constexpr R a1 = R(1.0 / kTheta), a2 = R((1.0 - kTheta) / (2.0 * kTheta * kTheta)),
+                a0 = R(-kTheta / (2.0 * kTheta * kTheta));
+    const R ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+    const R ex[3] = {-a1 * ux + a2 * ux2, a0 * ux2, a1 * ux + a2 * ux2};
+    const R ey[3] = {-a1 * uy + a2 * uy2, a0 * uy2, a1 * uy + a2 * uy2};
+    const R ez[3] = {-a1 * uz + a2 * uz2, a0 * uz2, a1 * uz + a2 * uz2};
+    R geq[27], fneq[27];
+    static_for<Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
+        constexpr R w = R(weight_of(Q, i));
+        const R Y = ey[cy + 1] + ez[cz + 1] + ey[cy + 1] * ez[cz + 1];
+        geq[i] = w * (rho * (ex[cx + 1] + Y + ex[cx + 1] * Y) + drho);
+        fneq[i] = g[i] - geq[i];
+    });
+    // second order: m_neq, m_CE = -2 rho theta tau_hat S, a_sgs = m_neq - m_CE, rate from its trace
+    R mn[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    static_for<Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int c[3] = {cx_of(Q, i), cy_of(Q, i), cz_of(Q, i)};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = a; b < 3; ++b)
+                if (c[a] * c[b] != 0) mn[a][b] += R(c[a] * c[b]) * fneq[i];
+    });
+    const R Sm[3][3] = {{Sxx, Sxy, Sxz}, {Sxy, Syy, Syz}, {Sxz, Syz, Szz}};
+    R A[3][3], a2p[3][3];
+    const R rt = R(-2) * rho * th * tau_hat;
+    R tr = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            A[a][b] = rt * Sm[a][b];
+            if (b < a) mn[a][b] = mn[b][a];
+        }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) tr += mn[a][a] - A[a][a];
+    const R omega_s = omega_sgs(tr, nu, omega, cnud);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) a2p[a][b] = (R(1) - omega) * A[a][b] + (R(1) - omega_s) * (mn[a][b] - A[a][b]);
+    // high order: project f_neq, RR reference (divided by rho: the recursion's a0/rho), two-rate relaxation
+    const R uu[3] = {ux, uy, uz};
+    R Ar[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) Ar[a][b] = A[a][b];
+    R ap[17];
+    static_for<17>([&](auto MI) {
+        constexpr int m = decltype(MI)::value;
+        R an = 0;
+        static_for<Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr R h = R(hdir(cx_of(Q, i), rr_deg(m, 0)) * hdir(cy_of(Q, i), rr_deg(m, 1)) *
+                              hdir(cz_of(Q, i), rr_deg(m, 2)));
+            if (h != R(0)) an += h * fneq[i];
+        });
+        const R ar = rr_coef<R, m>(uu, Ar);
+        ap[m] = (R(1) - omega) * ar + (R(1) - omega_s) * (an - ar);
+    });
+    // reconstruction, Eq. (kcrr_operational_post_population): f_post = f0 + w sum_m T_m
+    static_for<Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int c[3] = {cx_of(Q, i), cy_of(Q, i), cz_of(Q, i)};
+        constexpr R w = R(weight_of(Q, i));
+        R t2 = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) t2 += R(hdir(c[a], 2)) * a2p[a][a] * R(1.0 / (2.0 * kTheta * kTheta));
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = a + 1; b < 3; ++b)
+                if (c[a] * c[b] != 0) t2 += R(c[a] * c[b]) * a2p[a][b] * R(1.0 / (kTheta * kTheta));
+        R th_ = 0;
+        static_for<17>([&](auto MI) {
+            constexpr int m = decltype(MI)::value;
+            constexpr double h = hdir(c[0], rr_deg(m, 0)) * hdir(c[1], rr_deg(m, 1)) * hdir(c[2], rr_deg(m, 2));
+            constexpr double fact = (rr_deg(m, 0) == 2 ? 2.0 : 1.0) * (rr_deg(m, 1) == 2 ? 2.0 : 1.0) *
+                                    (rr_deg(m, 2) == 2 ? 2.0 : 1.0);
+            constexpr double thn = rr_n(m) == 3 ? kTheta * kTheta * kTheta
+                                                : (rr_n(m) == 4 ? kTheta * kTheta * kTheta * kTheta
+                                                                : (rr_n(m) == 5 ? kTheta * kTheta * kTheta * kTheta * kTheta
+                                                                                : kTheta * kTheta * kTheta * kTheta *
+                                                                                      kTheta * kTheta));
+            if constexpr (h != 0.0) th_ += R(h / (fact * thn)) * ap[m];
+        });
+        g[i] = geq[i] + w * (t2 + th_);
+    });
+}
+
 // One-cell collision on shifted populations g (in place -> g_post).
 //
 // Every closure is evaluated in the common form
@@ -243,6 +387,12 @@ __device__ __forceinline__ void collide(R (&g)[Q], R drho, R ux, R uy, R uz, R S
                                         R Syz, R omega, R tau_hat, R nu, R cnud, R Fx, R Fy, R Fz,
                                         const R* msgs_in = nullptr)
 {
+    if constexpr (CL == CL_KCRR) {
+        static_assert(Q == 27, "KC-RR is defined on D3Q27 only");
+        static_assert(!FORCE, "KC-RR is built for periodic boxes");
+        collide_kcrr<R>(g, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, omega, tau_hat, nu, cnud);
+        return;
+    } else {
     constexpr R th = R(kTheta);
     const R rho = R(1) + drho;
     constexpr R a1 = R(1.0 / kTheta);                                // c u / theta
@@ -376,6 +526,7 @@ __device__ __forceinline__ void collide(R (&g)[Q], R drho, R ux, R uy, R uz, R S
             g[i] += pref * w * ((cF - uF) * a1 + cu * cF * (a1 * a1));
         });
     }
+    }
 }
 
 // ------------------------------------------------------------------ kernel
@@ -408,8 +559,11 @@ constexpr size_t step_smem_bytes()
 // network inputs of one cell (the learned closure's 10 inputs: m_neq/rho,
 // invariants of m_CE/rho, tau_hat), standardised, into the warp's exchange row;
 // network forward for the warp; the cell's m_sgs back (times rho)
-template <int Q, typename R>
-__device__ __forceinline__ void learned_msgs(const R (&g)[Q], R drho, R ux, R uy, R uz, R Sxx, R Syy, R Szz, R Sxy,
+// The populations are read from the shared-memory stash (stride NT) rather
+// than kept in registers, so that only the network's fragments are live while
+// it runs; the caller reloads them for the collision.
+template <int Q, typename R, int NT>
+__device__ __forceinline__ void learned_msgs(const R* st, R drho, R ux, R uy, R uz, R Sxx, R Syy, R Szz, R Sxy,
                                              R Sxz, R Syz, R tau_hat, const unsigned char* sm_mlp, unsigned char* xch,
                                              int lane, R (&msgs)[6])
 {
@@ -420,15 +574,18 @@ __device__ __forceinline__ void learned_msgs(const R (&g)[Q], R drho, R ux, R uy
     static_for<Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
-        if (cx != 0) pxx += g[i];
-        if (cy != 0) pyy += g[i];
-        if (cz != 0) pzz += g[i];
-        if (cx * cy == 1) pxy += g[i];
-        if (cx * cy == -1) pxy -= g[i];
-        if (cx * cz == 1) pxz += g[i];
-        if (cx * cz == -1) pxz -= g[i];
-        if (cy * cz == 1) pyz += g[i];
-        if (cy * cz == -1) pyz -= g[i];
+        if constexpr (cx != 0 || cy != 0 || cz != 0) {
+            const R gi = st[i * NT];
+            if (cx != 0) pxx += gi;
+            if (cy != 0) pyy += gi;
+            if (cz != 0) pzz += gi;
+            if (cx * cy == 1) pxy += gi;
+            if (cx * cy == -1) pxy -= gi;
+            if (cx * cz == 1) pxz += gi;
+            if (cx * cz == -1) pxz -= gi;
+            if (cy * cz == 1) pyz += gi;
+            if (cy * cz == -1) pyz -= gi;
+        }
     });
     R x[10];
     x[0] = (pxx - rho * ux * ux - th * drho) * irho;
@@ -448,7 +605,7 @@ __device__ __forceinline__ void learned_msgs(const R (&g)[Q], R drho, R ux, R uy
     const float* xmu = reinterpret_cast<const float*>(sm_mlp + L::XMU);
     const float* xis = reinterpret_cast<const float*>(sm_mlp + L::XIS);
     __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(xch);
-    float* Y = reinterpret_cast<float*>(xch + 32 * L::XLD * 2);
+    float* Y = reinterpret_cast<float*>(xch);  // overlays the inputs
     uint32_t* Xrow = reinterpret_cast<uint32_t*>(X + lane * L::XLD);
 #pragma unroll
     for (int q = 0; q < 5; ++q)
@@ -624,15 +781,17 @@ __global__ void __launch_bounds__(32 * TY, OCC ? OCC : ((sizeof(typename StoreTr
             const R Syz = R(0.5) * (du[1][2] + du[2][1]);
             R g[Q];
             const R* st = stash + (z & 1) * Q * NT + tid;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) g[i] = st[i * NT];
             if constexpr (CL == CL_LEARNED) {
                 R msgs[6];
-                learned_msgs<Q, R>(g, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, tau_hat, sm_mlp, sm_xch, tx,
-                                   msgs);
+                learned_msgs<Q, R, NT>(st, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, tau_hat, sm_mlp, sm_xch,
+                                       tx, msgs);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) g[i] = st[i * NT];
                 collide<Q, R, CL, FORCE>(g, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, omega, tau_hat, nu, cnud,
                                          Fx, Fy, Fz, msgs);
             } else {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) g[i] = st[i * NT];
                 collide<Q, R, CL, FORCE>(g, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, omega, tau_hat, nu, cnud,
                                          Fx, Fy, Fz);
             }

@@ -66,6 +66,9 @@ cudaError_t launch_step_qs(int closure, int bc, int ty, int variant, const StepA
     LBM_STEP_CASE(CL_KCMP, BC_WALLS_Y, 8)
     LBM_STEP_CASE(CL_KCRB_H, BC_WALLS_Y, 8)
     LBM_STEP_CASE(CL_KCRB_RAW, BC_WALLS_Y, 8)
+    if constexpr (Q == 27) {
+        LBM_STEP_CASE(CL_KCRR, BC_PERIODIC, 8)
+    }
     if constexpr (sizeof(typename StoreTraits<S>::R) == 4) {
         LBM_STEP_CASE(CL_KCMP, BC_PERIODIC, 4)
         LBM_STEP_CASE(CL_KCMP, BC_PERIODIC, 16)

@@ -17,7 +17,7 @@ cudaError_t encode_population_map(void* map_out, const void* buf, int nx, int ny
     if (!encode) {
         void* fn = nullptr;
         cudaDriverEntryPointQueryResult qr;
-        cudaError_t e = cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &qr);
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr);
         if (e != cudaSuccess) return e;
         if (qr != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
         encode = reinterpret_cast<EncodeFn>(fn);

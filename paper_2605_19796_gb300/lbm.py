@@ -39,7 +39,8 @@ EXPORTS = ["lbm_config_default", "lbm_create", "lbm_destroy", "lbm_init_velocity
            "lbm_step_count", "lbm_kernel_launches", "lbm_last_error", "lbm_abi_version",
            "lbm_diagnostics_noalloc", "lbm_autotune", "lbm_launch_config", "lbm_mlp_param_count",
            "lbm_mlp_workspace_floats", "lbm_mlp_forward", "lbm_mlp_grad", "lbm_mlp_adamw", "lbm_box_filter",
-           "lbm_closure_features", "lbm_set_learned_closure"]
+           "lbm_closure_features", "lbm_set_learned_closure", "lbm_mlp_packed_bytes", "lbm_mlp_pack",
+           "lbm_mlp_forward_tc"]
 
 
 class lbm_config(ctypes.Structure):
@@ -99,8 +100,11 @@ def _load() -> ctypes.CDLL:
     lib.lbm_box_filter.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int, vp, vp, vp]
     lib.lbm_closure_features.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                         ctypes.c_double, vp, vp, vp, vp]
+                                         ctypes.c_double, vp, vp, vp, vp, vp]
     lib.lbm_set_learned_closure.argtypes = [H, P(ctypes.c_float), P(ctypes.c_float)]
+    lib.lbm_mlp_packed_bytes.restype = ctypes.c_longlong
+    lib.lbm_mlp_pack.argtypes = [P(ctypes.c_float), P(ctypes.c_float), vp]
+    lib.lbm_mlp_forward_tc.argtypes = [vp, vp, ctypes.c_int, vp, vp]
     lib.lbm_autotune.argtypes = [H, ctypes.c_int]
     lib.lbm_launch_config.argtypes = [H, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]
     lib.lbm_last_error.restype = ctypes.c_char_p
@@ -262,9 +266,23 @@ def lbm_box_filter(f_ptr, lattice, storage, nx, ny, nz, factor, fc_ptr, msgs_ptr
                               _vp(fc_ptr), _vp(msgs_ptr), _vp(_stream_handle(stream))))
 
 
-def lbm_closure_features(f_ptr, lattice, nx, ny, nz, nu, msgs_ptr, x_ptr, t_ptr, stream=None) -> None:
+def lbm_closure_features(f_ptr, lattice, nx, ny, nz, nu, msgs_ptr, x_ptr, t_ptr, kcmp_ptr=0, stream=None) -> None:
     _check(LIB.lbm_closure_features(_vp(f_ptr), int(lattice), int(nx), int(ny), int(nz), float(nu), _vp(msgs_ptr),
-                                    _vp(x_ptr), _vp(t_ptr), _vp(_stream_handle(stream))))
+                                    _vp(x_ptr), _vp(t_ptr), _vp(kcmp_ptr), _vp(_stream_handle(stream))))
+
+
+def lbm_mlp_pack(params: np.ndarray, stats: np.ndarray) -> np.ndarray:
+    """Packed network block (bytes) of the fused inference."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    st = np.ascontiguousarray(stats, dtype=np.float32)
+    out = np.zeros(int(LIB.lbm_mlp_packed_bytes()), dtype=np.uint8)
+    fp = ctypes.POINTER(ctypes.c_float)
+    _check(LIB.lbm_mlp_pack(p.ctypes.data_as(fp), st.ctypes.data_as(fp), out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def lbm_mlp_forward_tc(packed_ptr, x_ptr, n, y_ptr, stream=None) -> None:
+    _check(LIB.lbm_mlp_forward_tc(_vp(packed_ptr), _vp(x_ptr), int(n), _vp(y_ptr), _vp(_stream_handle(stream))))
 
 
 def lbm_set_learned_closure(h, params: np.ndarray, stats: np.ndarray) -> None:

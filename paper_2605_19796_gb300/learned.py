@@ -1,0 +1,230 @@
+"""Learned collision-side closure: data, training and evaluation driver.
+
+The paper leaves the constitutive determination of the turbulent relaxation
+(more generally of the turbulent collision operator) as its main open point
+(Sec. 8).  The learned closure keeps the KC-MP structure (App. F.3: SGS
+carrier f_sgs = w/(2 theta^2) H:m_sgs, rate from k_sgs = |tr m_sgs|/2, clip by
+the molecular rate) and learns m_sgs itself from data the method generates:
+
+  1. fine-lattice decaying-turbulence runs (D3Q27, FP32, KC-MP);
+  2. box filter by F of the fine populations -> coarse populations and the
+     exact SGS stress of Eq. (m_sgs_2) (lbm_box_filter);
+  3. per coarse cell the ten inputs (m_neq/rho, invariants of m_CE/rho,
+     tau_hat of the coarse lattice, nu_coarse = nu_fine / F under acoustic
+     scaling) and the target m_sgs/rho (lbm_closure_features);
+  4. training with the library's own forward/backward/AdamW kernels;
+  5. fused BF16 tensor-core inference in the step kernel (closure "learned").
+
+Orchestration only: every numerical step runs in liblbm's kernels; torch holds
+device buffers and computes the energy spectra used for evaluation.
+"""
+from __future__ import annotations
+
+import math
+from typing import Dict, Sequence
+
+import numpy as np
+import torch
+
+from . import inputs, lbm
+
+
+def snapshot_features(s: lbm.Solver, factor: int, nu_coarse: float):
+    """Box-filtered coarse state of a solver's current populations:
+    (x [N,10], targets [N,6], analytic KC-MP estimate [N,6], coarse populations [q,nz,ny,nx])."""
+    ptr, _ = s.population_buffer()
+    nx, ny, nz = s.shape
+    q = s.q
+    ncx, ncy, ncz = nx // factor, ny // factor, nz // factor
+    nc = ncx * ncy * ncz
+    dev = torch.device("cuda")
+    fc = torch.empty((q, ncz, ncy, ncx), dtype=torch.float32, device=dev)
+    ms = torch.empty((6, ncz, ncy, ncx), dtype=torch.float32, device=dev)
+    lbm.lbm_box_filter(ptr, q, s.cfg.storage, nx, ny, nz, factor, fc.data_ptr(), ms.data_ptr())
+    x = torch.empty((nc, 10), dtype=torch.float32, device=dev)
+    t = torch.empty((nc, 6), dtype=torch.float32, device=dev)
+    kc = torch.empty((nc, 6), dtype=torch.float32, device=dev)
+    lbm.lbm_closure_features(fc.data_ptr(), q, ncx, ncy, ncz, nu_coarse, ms.data_ptr(), x.data_ptr(), t.data_ptr(),
+                             kc.data_ptr())
+    torch.cuda.synchronize()
+    return x, t, kc, fc
+
+
+def generate(n_fine: int = 512, factor: int = 4, seeds: Sequence[int] = (0, 1, 2, 3, 4),
+             k0s: Sequence[float] = (4.0, 8.0), nu_fine: float = 1e-4, urms: float = 0.04,
+             snap_steps: Sequence[int] = (300, 600), keep: float = 0.25, sample_seed: int = 0):
+    """Training samples from fine runs: returns (X, T, KC) on the GPU."""
+    gen = torch.Generator(device="cuda").manual_seed(sample_seed)
+    X, T, KC = [], [], []
+    for k0 in k0s:
+        for sd in seeds:
+            with lbm.Solver(27, (n_fine,) * 3, nu_fine, closure="kcmp", storage="fp32") as s:
+                rho, u = inputs.hit_fields(n_fine, k0=k0, urms=urms, seed=sd, device="cuda")
+                s.init_velocity_device(rho, u)
+                del rho, u
+                done = 0
+                for st in snap_steps:
+                    s.step(st - done)
+                    done = st
+                    x, t, kc, _ = snapshot_features(s, factor, nu_fine / factor)
+                    n = x.shape[0]
+                    idx = torch.randperm(n, generator=gen, device="cuda")[: max(1, int(keep * n))]
+                    X.append(x[idx])
+                    T.append(t[idx])
+                    KC.append(kc[idx])
+    return torch.cat(X), torch.cat(T), torch.cat(KC)
+
+
+def standardisation(X: torch.Tensor, T: torch.Tensor) -> np.ndarray:
+    """32 values: mean[10], std[10] of the inputs, mean[6], std[6] of the targets."""
+    xm, xs = X.double().mean(0), X.double().std(0)
+    tm, ts = T.double().mean(0), T.double().std(0)
+    # a column that is constant up to rounding (tau_hat within one lattice) has a
+    # spread of a few ulps of its mean: standardise it by 1, not by that spread
+    xs = torch.where(xs > 1e-6 * xm.abs(), xs, torch.ones_like(xs))
+    ts = torch.where(ts > 1e-6 * tm.abs(), ts, torch.ones_like(ts))
+    return torch.cat([xm, xs, tm, ts]).cpu().numpy().astype(np.float32)
+
+
+def init_params(seed: int = 0) -> np.ndarray:
+    """U(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights, zero biases, flat W1 b1 ... W4 b4."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sizes = (10, 64, 64, 64, 6)
+    out = []
+    for l in range(4):
+        fi, fo = sizes[l], sizes[l + 1]
+        out.append(rng.uniform(-1.0, 1.0, size=fo * fi) / math.sqrt(fi))
+        out.append(np.zeros(fo))
+    return np.concatenate(out).astype(np.float32)
+
+
+def train(X: torch.Tensor, T: torch.Tensor, stats: np.ndarray, iters: int = 3000, batch: int = 8192,
+          lr: float = 2e-3, wd: float = 1e-4, seed: int = 0, log_every: int = 0) -> Dict:
+    """AdamW training on standardised data with the library's kernels."""
+    dev = torch.device("cuda")
+    st = torch.as_tensor(stats, device=dev)
+    Xs = ((X.double() - st[:10].double()) / st[10:20].double()).float().contiguous()
+    Ts = ((T.double() - st[20:26].double()) / st[26:32].double()).float().contiguous()
+    n = Xs.shape[0]
+    npar = lbm.lbm_mlp_param_count()
+    p = torch.as_tensor(init_params(seed), device=dev)
+    g = torch.zeros(npar, dtype=torch.float32, device=dev)
+    m = torch.zeros_like(g)
+    v = torch.zeros_like(g)
+    b = min(batch, n)
+    ws = torch.empty(lbm.lbm_mlp_workspace_floats(b), dtype=torch.float32, device=dev)
+    gen = torch.Generator(device="cuda").manual_seed(seed)
+    hist = []
+    for it in range(1, iters + 1):
+        idx = torch.randint(0, n, (b,), generator=gen, device=dev)
+        xb, tb = Xs[idx].contiguous(), Ts[idx].contiguous()
+        want = log_every and (it % log_every == 0 or it == 1)
+        loss = lbm.lbm_mlp_grad(p.data_ptr(), xb.data_ptr(), tb.data_ptr(), b, g.data_ptr(), ws.data_ptr(),
+                                want_loss=bool(want))
+        if want:
+            hist.append((it, loss))
+        lr_t = lr * 0.5 * (1 + math.cos(math.pi * it / iters))  # cosine decay
+        lbm.lbm_mlp_adamw(p.data_ptr(), g.data_ptr(), m.data_ptr(), v.data_ptr(), it, lr_t, weight_decay=wd)
+    torch.cuda.synchronize()
+    return {"params": p.cpu().numpy(), "stats": stats, "history": hist}
+
+
+def predict(params: np.ndarray, stats: np.ndarray, X: torch.Tensor) -> torch.Tensor:
+    """Network prediction of m_sgs/rho (FP32 forward kernel) for raw inputs X."""
+    dev = X.device
+    st = torch.as_tensor(stats, device=dev)
+    Xs = ((X.double() - st[:10].double()) / st[10:20].double()).float().contiguous()
+    n = Xs.shape[0]
+    p = torch.as_tensor(params, device=dev)
+    ys = torch.empty((n, 6), dtype=torch.float32, device=dev)
+    ws = torch.empty(lbm.lbm_mlp_workspace_floats(n), dtype=torch.float32, device=dev)
+    lbm.lbm_mlp_forward(p.data_ptr(), Xs.data_ptr(), n, ys.data_ptr(), ws.data_ptr())
+    torch.cuda.synchronize()
+    return ys.double() * st[26:32].double() + st[20:26].double()
+
+
+def a_priori(params, stats, X, T, KC) -> Dict:
+    """Held-out errors of the m_sgs/rho estimates, normalised by the target variance:
+    the network, the analytic KC-MP estimate (m_neq - m_CE)/rho, and zero."""
+    var = float(((T.double() - T.double().mean(0)) ** 2).sum())
+    net = float(((predict(params, stats, X) - T.double()) ** 2).sum()) / var
+    kc = float(((KC.double() - T.double()) ** 2).sum()) / var
+    zero = float((T.double() ** 2).sum()) / var
+    trace_t = T[:, 0] + T[:, 1] + T[:, 2]
+    trace_n = predict(params, stats, X)[:, :3].sum(1)
+    trace_k = KC[:, 0] + KC[:, 1] + KC[:, 2]
+    tv = float(((trace_t - trace_t.mean()) ** 2).sum())
+    return {"rel_mse_network": net, "rel_mse_kcmp": kc, "rel_mse_zero": zero,
+            "trace_rel_mse_network": float(((trace_n - trace_t.double()) ** 2).sum()) / tv,
+            "trace_rel_mse_kcmp": float(((trace_k - trace_t) ** 2).double().sum()) / tv}
+
+
+def spectrum(u: torch.Tensor) -> torch.Tensor:
+    """Shell-averaged kinetic energy spectrum E(k) = 1/2 sum_{|k'| in [k-1/2, k+1/2)} |u_hat(k')|^2,
+    u_hat normalised by 1/N (periodic cube, u [3, n, n, n])."""
+    n = u.shape[-1]
+    uh = torch.fft.fftn(u.double(), dim=(1, 2, 3)) / (n ** 3)
+    e = 0.5 * (uh.real ** 2 + uh.imag ** 2).sum(0)
+    k = torch.fft.fftfreq(n, d=1.0 / n, device=u.device)
+    kk = torch.sqrt(k[:, None, None] ** 2 + k[None, :, None] ** 2 + k[None, None, :] ** 2)
+    shell = torch.round(kk).long().ravel()
+    return torch.zeros(n, dtype=torch.float64, device=u.device).index_add_(
+        0, shell.clamp(max=n - 1), e.ravel())[: n // 2]
+
+
+def _velocity(s: lbm.Solver) -> torch.Tensor:
+    nx, ny, nz = s.shape
+    r = torch.empty((nz, ny, nx), dtype=torch.float64, device="cuda")
+    u = torch.empty((3, nz, ny, nx), dtype=torch.float64, device="cuda")
+    s.moments_device(r, u)
+    torch.cuda.synchronize()
+    return u
+
+
+def a_posteriori(params, stats, n_fine: int = 512, factor: int = 4, k0: float = 4.0, seed: int = 99,
+                 nu_fine: float = 1e-4, urms: float = 0.04, t0: int = 400, coarse_steps: int = 100,
+                 closures=("kcmp", "learned", "bgk")) -> Dict:
+    """Coarse LES from the filtered fine state at fine step t0, run `coarse_steps`
+    coarse steps (= factor x as many fine steps under acoustic scaling) with each
+    closure, against the box-filtered fine run: relative L2 error of E(k) over the
+    resolved shells 1 <= k < n_coarse/2 and of the kinetic energy, and the
+    dissipation rate -dE/dt over the window."""
+    nc = n_fine // factor
+    nu_c = nu_fine / factor
+    out = {}
+    with lbm.Solver(27, (n_fine,) * 3, nu_fine, closure="kcmp", storage="fp32") as fine:
+        rho, u = inputs.hit_fields(n_fine, k0=k0, urms=urms, seed=seed, device="cuda")
+        fine.init_velocity_device(rho, u)
+        del rho, u
+        fine.step(t0)
+        _, _, _, fc0 = snapshot_features(fine, factor, nu_c)
+        f0 = fc0.double().cpu().numpy()
+        fine.step(factor * coarse_steps)
+        _, _, _, fc1 = snapshot_features(fine, factor, nu_c)
+    ref = _coarse_velocity(fc1, nu_c)
+    e_ref = spectrum(ref)
+    ek_ref = float(0.5 * (ref ** 2).sum(0).mean())
+    ek_ref0 = float(0.5 * (_coarse_velocity(fc0, nu_c) ** 2).sum(0).mean())
+    kmax = nc // 2
+    for cl in closures:
+        with lbm.Solver(27, (nc,) * 3, nu_c, closure=cl, storage="fp32") as s:
+            if cl == "learned":
+                s.set_learned_closure(params, stats)
+            s.set_populations(f0)
+            s.step(coarse_steps)
+            u = _velocity(s)
+        e = spectrum(u)
+        ek = float(0.5 * (u ** 2).sum(0).mean())
+        err = torch.sqrt(((e[1:kmax] - e_ref[1:kmax]) ** 2).sum() / (e_ref[1:kmax] ** 2).sum())
+        out[cl] = {"spectrum_rel_l2": float(err), "E_k": ek, "dissipation": (ek_ref0 - ek) / coarse_steps}
+    out["filtered_fine"] = {"E_k": ek_ref, "dissipation": (ek_ref0 - ek_ref) / coarse_steps}
+    return out
+
+
+def _coarse_velocity(fc: torch.Tensor, nu: float) -> torch.Tensor:
+    """Velocity of a (filtered) FP32 population array, through the library's
+    moments kernel on an FP64-storage solver holding those populations."""
+    q, nz, ny, nx = fc.shape
+    with lbm.Solver(q, (nx, ny, nz), nu, closure="bgk", storage="fp64") as s:
+        s.set_populations(fc.double().cpu().numpy())
+        return _velocity(s)

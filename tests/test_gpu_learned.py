@@ -118,3 +118,112 @@ def test_box_filter_and_features(env, orc, q):
         assert np.abs(xg[:, k] - xr[:, k]).max() <= 1e-4 * sc + 1e-12, k
     tr = cd.targets(mfine.cpu().numpy().astype(np.float64), rr)
     assert np.abs(t.cpu().numpy() - tr).max() <= 1e-6 * np.abs(tr).max()
+
+
+def test_tensor_core_forward_matches(env):
+    """The fused inference's tensor-core network (BF16 mma.sync, FP32 accumulate)
+    against the FP64 oracle network with the same BF16 rounding points, and
+    against the FP32 forward kernel (to BF16 accuracy)."""
+    lbm, torch = env
+    from oracle import learned as olearned
+    from oracle import mlp
+
+    n = 1000
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal((n, 10)) * 1e-3 + 2e-4
+    x[:, 9] = 0.5
+    stats = np.concatenate([x.mean(0), np.where(x.std(0) > 1e-6 * np.abs(x.mean(0)), x.std(0), 1.0), np.full(6, 1e-5),
+                            np.full(6, 3e-4)]).astype(np.float32)
+    params = np.asarray(mlp.flat(_params(9)), dtype=np.float32)
+    packed = torch.as_tensor(lbm.lbm_mlp_pack(params, stats), device="cuda")
+    xd = torch.as_tensor(x.astype(np.float32), device="cuda")
+    yd = torch.zeros((n, 6), dtype=torch.float32, device="cuda")
+    lbm.lbm_mlp_forward_tc(packed.data_ptr(), xd.data_ptr(), n, yd.data_ptr())
+    torch.cuda.synchronize()
+    y = yd.cpu().numpy()
+    st = stats.astype(np.float64)
+    xs = (x.astype(np.float32).astype(np.float64) - st[:10]) / st[10:20]
+    yo = olearned.forward(params.astype(np.float64), xs, rounding=True) * st[26:32] + st[20:26]
+    scale = np.abs(yo - st[20:26]).max()
+    assert np.abs(y - yo).max() <= 2e-2 * scale, np.abs(y - yo).max() / scale
+    assert np.percentile(np.abs(y - yo), 99) <= 2e-3 * scale
+
+
+def _stats_for(x, scale_out):
+    xm, xs = x.mean(0), x.std(0)
+    xs = np.where(xs > 1e-6 * np.abs(xm), xs, 1.0)  # tau_hat: constant up to rounding
+    return np.concatenate([xm, xs, np.zeros(6), np.full(6, scale_out)]).astype(np.float32)
+
+
+def test_learned_step_matches_oracle(env, orc):
+    """One step of the fused learned closure (BF16 tensor-core network inside the
+    step kernel) against the oracle's learned step with the same BF16 rounding
+    points (inputs, weights, hidden activations) and FP64 elsewhere.  The network
+    is random, its output scaled so that the turbulent rate is active in most
+    cells.
+
+    Tolerance: the state is stored in FP32, so the resolved part of the update
+    carries FP32 rounding noise; it is measured on the same state by the BGK
+    step against the oracle's BGK step.  Each cell may differ from the oracle by
+    twice that noise plus 2^-7 of its SGS increment (omega - omega_s) f_sgs, the
+    BF16 network's share."""
+    lbm, torch = env
+    from oracle import learned as olearned
+    from oracle import mlp
+
+    shape = (32, 16, 12)
+    nu = 2e-5
+    rho, u = inputs.hit_fields(0, k0=3.0, urms=0.08, seed=12, shape=shape)
+    f = orc.run(orc.init_equilibrium(27, rho, u), 4, closure=1, nu=nu, c_nu=0.035)
+    f = f.astype(np.float32).astype(np.float64)  # the GPU state is FP32
+    _, _, _, _, x = olearned.inputs_and_state(f, nu)
+    scale = 5.0 * float(np.abs(x[:, :6]).std())
+    stats = _stats_for(x, scale)
+    params = np.asarray(mlp.flat(mlp.init_params(5)), dtype=np.float32)
+    with lbm.Solver(27, shape, nu, closure="learned", storage="fp32") as s:
+        s.set_learned_closure(params, stats)
+        s.set_populations(f)
+        s.step(1)
+        fg = s.get_populations()
+    with lbm.Solver(27, shape, nu, closure="bgk", storage="fp32") as s:
+        s.set_populations(f)
+        s.step(1)
+        fb = s.get_populations()
+    fo, msgs = olearned.step(f, nu, params.astype(np.float64), stats.astype(np.float64), 0.035)
+    fbo = orc.run(f, 1, closure=0, nu=nu)
+    # the closure must be active: nu_t > nu in a good share of the cells
+    tr = msgs[:, 0] + msgs[:, 1] + msgs[:, 2]
+    assert np.mean(0.035 * np.sqrt(np.abs(tr) / 2) > nu) > 0.5
+    noise = np.abs(fb - fbo).max()
+    assert noise < 1e-7
+    sgs = np.abs(fo - fbo).reshape(27, -1).max(axis=0)  # per cell SGS increment
+    assert sgs.max() > 100 * noise, "the SGS signal must stand well above the FP32 noise"
+    err = np.abs(fg - fo).reshape(27, -1).max(axis=0)
+    bound = 2 * noise + 2.0 ** -7 * sgs
+    assert np.all(err <= bound), (np.max(err / bound), noise, sgs.max())
+    # the SGS increments themselves, globally
+    inc = np.abs((fg - fb) - (fo - fbo)).max()
+    assert inc <= 4 * noise + 1e-2 * sgs.max(), (inc, noise, sgs.max())
+
+
+def test_learned_closure_pipeline(env):
+    """Reduced end-to-end run of the learned closure: fine 128^3 runs box-filtered
+    by 4 to 32^3, training with the library's kernels, held-out a-priori errors
+    (the network must beat the analytic KC-MP estimate of m_sgs and the mean),
+    and a stable coarse run with the fused network."""
+    lbm, torch = env
+    from paper_2605_19796_gb300 import learned
+
+    X, T, KC = learned.generate(n_fine=128, factor=4, seeds=(0, 1, 2), k0s=(4.0,), snap_steps=(150, 300), keep=1.0)
+    n = X.shape[0]
+    ntr = (2 * n) // 3  # seeds 0, 1 train; seed 2 held out
+    stats = learned.standardisation(X[:ntr], T[:ntr])
+    res = learned.train(X[:ntr], T[:ntr], stats, iters=1500, batch=4096, lr=2e-3, log_every=500)
+    m = learned.a_priori(res["params"], stats, X[ntr:], T[ntr:], KC[ntr:])
+    print("a priori (held-out seed):", m)
+    assert m["rel_mse_network"] < m["rel_mse_kcmp"]
+    assert m["rel_mse_network"] < 1.0
+    post = learned.a_posteriori(res["params"], stats, n_fine=128, factor=4, t0=150, coarse_steps=40, seed=7)
+    print("a posteriori:", post)
+    for cl in ("kcmp", "learned", "bgk"):
+        assert np.isfinite(post[cl]["E_k"]) and post[cl]["E_k"] > 0

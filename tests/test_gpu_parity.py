@@ -367,6 +367,8 @@ def test_tma_variant_matches(lbm, orc, shape, nbatch, closure):
 
 def test_default_variant_selection(lbm):
     with lbm.Solver(27, (64, 32, 16), 1e-4, closure="kcmp", storage="fp32") as s:
+        assert s.launch_config["variant"] == 1
+    with lbm.Solver(27, (64, 32, 16), 1e-4, closure="kcmp", storage="fp32", variant=4) as s:
         assert s.launch_config["variant"] == 4
     with lbm.Solver(27, (40, 32, 16), 1e-4, closure="kcmp", storage="fp32") as s:
         assert s.launch_config["variant"] == 1
@@ -374,3 +376,32 @@ def test_default_variant_selection(lbm):
         assert s.launch_config["variant"] == 1
     with pytest.raises(lbm.LbmError):
         lbm.Solver(27, (40, 32, 16), 1e-4, closure="kcmp", storage="fp32", variant=4)
+
+
+@pytest.mark.parametrize("shape", [(37, 21, 13), (16, 8, 6)])
+def test_kcrr_fp64_matches_oracle(lbm, orc, shape):
+    """KC-RR (App. F.4, D3Q27): 17 high-order Hermite modes split into the RR
+    reference and the SGS departure, relaxed at omega and omega_s."""
+    rho, u = inputs.hit_fields(0, k0=3.0, urms=0.08, seed=13, shape=shape)
+    nu = 2e-5
+    with lbm.Solver(27, shape, nu, closure="kcrr", c_nu=0.02, storage="fp64") as s:
+        s.init_velocity(rho, u)
+        s.step(10)
+        fg = s.get_populations()
+    fo = orc.run(orc.init_equilibrium(27, rho, u), 10, closure=4, nu=nu, c_nu=0.02)
+    assert rel(fg, fo) < TOL64
+    fb = orc.run(orc.init_equilibrium(27, rho, u), 10, closure=0, nu=nu)
+    assert np.abs(fo - fb).max() > 1e-7, "the closure must be active"
+
+
+def test_kcrr_fp32_velocity(lbm, orc):
+    n = 32
+    rho, u = inputs.hit_fields(n, k0=3.0, urms=0.05, seed=14)
+    with lbm.Solver(27, (n, n, n), 5e-5, closure="kcrr", c_nu=0.02, storage="fp32") as s:
+        s.init_velocity(rho, u)
+        s.step(30)
+        fg = s.get_populations()
+    fo = orc.run(orc.init_equilibrium(27, rho, u), 30, closure=4, nu=5e-5, c_nu=0.02)
+    _, ug = orc.fields(fg)
+    _, uo = orc.fields(fo)
+    assert np.abs(ug - uo).max() <= 1e-5

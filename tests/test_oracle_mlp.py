@@ -88,3 +88,36 @@ def test_training_reduces_loss():
     for t in range(1, 301):
         mlp.adamw_step(p, mlp.backward(p, xs, ts), m, v, t, 3e-3)
     assert mlp.loss(p, xs, ts) < 0.05 * l0
+
+
+def test_bf16_rounding_emulation():
+    """Round-to-nearest-even to bfloat16: exact values stay, ties go to even,
+    the relative error is at most half an ulp (2^-8), and the values agree with
+    torch's own float32 -> bfloat16 conversion."""
+    from oracle.learned import bf16
+
+    assert bf16(np.array([1.0, -2.5, 0.0]))[0] == 1.0
+    # 1 + 2^-8 is a tie between 1 and 1 + 2^-7: rounds to the even mantissa (1.0)
+    assert bf16(np.array([1.0 + 2.0 ** -8]))[0] == 1.0
+    assert bf16(np.array([1.0 + 3 * 2.0 ** -8]))[0] == 1.0 + 2.0 ** -6
+    x = np.random.default_rng(0).standard_normal(10000)
+    assert np.abs(bf16(x) / x - 1).max() <= 2.0 ** -8
+    torch = pytest.importorskip("torch")
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).double().numpy()
+    assert np.array_equal(bf16(x), ref)
+
+
+def test_learned_step_with_zero_output_is_bgk():
+    """With a network whose output is zero (zero weights and biases, zero output
+    mean) m_sgs = 0, the turbulent rate is clipped to omega and the learned step
+    is the resolved-BGK step (Sec. 5.1)."""
+    import oracle
+    from oracle import learned
+
+    f = oracle.init_equilibrium(27, None, np.full((3, 4, 4, 4), 0.02))
+    params = np.zeros(mlp.NPARAM)
+    stats = np.concatenate([np.zeros(10), np.ones(10), np.zeros(6), np.ones(6)])
+    fpost, msgs = learned.step(f, 1e-4, params, stats, 0.035)
+    assert np.abs(msgs).max() == 0.0
+    ref = oracle.run(f, 1, closure=0, nu=1e-4)
+    assert np.abs(fpost - ref).max() < 1e-15

@@ -106,7 +106,12 @@ typedef struct {
                            sized for three CTAs per SM (32-bit arithmetic,
                            periodic, BGK/KC-MP, tile_y 8), 4 = TMA-staged
                            pipeline (FP32, periodic, nx % 32 == 0 and
-                           ny % tile_y == 0)                                      */
+                           ny % tile_y == 0), 5 = register pull with the
+                           loads issued two planes ahead, 6 / 7 = register pull
+                           without the population stash (re-pulled for the
+                           collision; three / four CTAs per SM, 32-bit
+                           arithmetic), 8 = register pull with a split
+                           arrive/wait barrier (5-8: BGK, KC-MP, KC-RB)      */
     int disable_graphs; /* nonzero: lbm_step launches kernels one by one instead of
                            replaying a captured CUDA graph                        */
 } lbm_config;

@@ -308,7 +308,7 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
     if (has_force && bc_kind != BC_WALLS_Y)
         return fail(LBM_ERR_UNSUPPORTED, "a body force is supported with bounce-back walls (channel) only");
     int tile_y = cfg->tile_y ? cfg->tile_y : 8;
-    if (cfg->variant < VAR_DEFAULT || cfg->variant > VAR_TMA) return fail(LBM_ERR_ARG, "unknown kernel variant");
+    if (cfg->variant < VAR_DEFAULT || cfg->variant > VAR_SPLIT) return fail(LBM_ERR_ARG, "unknown kernel variant");
     int variant = cfg->variant;
     // the register pull is the fastest variant measured on every workload built;
     // lbm_autotune may pick another one for a given box
@@ -463,7 +463,8 @@ int lbm_autotune(lbm_handle* h, int trials)
 {
     if (int rc = check_handle(h)) return rc;
     if (trials < 1) trials = 3;
-    static const int kVariants[] = {VAR_REGISTER, VAR_REGISTER_OCC3, VAR_ASYNC, VAR_TMA};
+    static const int kVariants[] = {VAR_REGISTER, VAR_SPLIT, VAR_REPULL, VAR_REPULL_OCC4, VAR_PREFETCH,
+                                    VAR_REGISTER_OCC3, VAR_ASYNC, VAR_TMA};
     static const int kTiles[] = {4, 8, 16};
     static const int kChunks[] = {8, 16, 32, 64, 128};
     const int v0 = h->variant, t0 = h->tile_y, z0 = h->zchunk;

@@ -623,10 +623,14 @@ __device__ __forceinline__ void learned_msgs(const R* st, R drho, R ux, R uy, R 
 }
 
 // OCC: CTAs per SM the register budget is sized for (0 = 1 for FP64 or TY >= 16, else 2)
-template <int Q, typename S, int CL, int BC, int TY, int OCC = 0>
+// RP: no population stash; the collision re-pulls its plane (loaded one plane
+// earlier for the velocity, so mostly L1 hits), which leaves only the velocity
+// ring in shared memory and lets more CTAs share an SM
+template <int Q, typename S, int CL, int BC, int TY, int OCC = 0, bool RP = false>
 __global__ void __launch_bounds__(32 * TY, OCC ? OCC : ((sizeof(typename StoreTraits<S>::R) == 8 || TY >= 16) ? 1 : 2))
     step_kernel(const StepArgs a)
 {
+    static_assert(!(RP && CL == CL_LEARNED), "the learned closure reads its inputs from the stash");
     using R = typename StoreTraits<S>::R;
     using Sh = StepShape<Q, R, BC, TY>;
     constexpr int TX = Sh::TX, HY = Sh::HY, RX = Sh::RX, RN = Sh::RN, NT = Sh::NT, NB = Sh::NB;
@@ -732,7 +736,7 @@ __global__ void __launch_bounds__(32 * TY, OCC ? OCC : ((sizeof(typename StoreTr
             R t[Q];
             pull<Q, S, R, BC>(fin, ps, own, zr, t);
             moments<Q, R>(t, r, vx, vy, vz, Fx, Fy, Fz);
-            if (keep) {
+            if (keep && !RP) {
                 R* st = stash + (z & 1) * Q * NT + tid;
 #pragma unroll
                 for (int i = 0; i < Q; ++i) st[i * NT] = t[i];
@@ -790,8 +794,14 @@ __global__ void __launch_bounds__(32 * TY, OCC ? OCC : ((sizeof(typename StoreTr
                 collide<Q, R, CL, FORCE>(g, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, omega, tau_hat, nu, cnud,
                                          Fx, Fy, Fz, msgs);
             } else {
+                if constexpr (RP) {
+                    int zr[3];
+                    zrows(z, zr);
+                    pull<Q, S, R, BC>(fin, ps, own, zr, g);
+                } else {
 #pragma unroll
-                for (int i = 0; i < Q; ++i) g[i] = st[i * NT];
+                    for (int i = 0; i < Q; ++i) g[i] = st[i * NT];
+                }
                 collide<Q, R, CL, FORCE>(g, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, omega, tau_hat, nu, cnud,
                                          Fx, Fy, Fz);
             }
@@ -810,20 +820,28 @@ __global__ void __launch_bounds__(32 * TY, OCC ? OCC : ((sizeof(typename StoreTr
     }
 }
 
-template <int Q, typename S, int CL, int BC, int TY, int OCC = 0>
-cudaError_t prepare_step_t()
+template <int Q, typename S, int CL, int BC, int TY, bool RP>
+constexpr size_t kernel_smem_bytes()
 {
-    return cudaFuncSetAttribute(step_kernel<Q, S, CL, BC, TY, OCC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)step_smem_bytes<Q, typename StoreTraits<S>::R, BC, TY, CL>());
+    using Sh = StepShape<Q, typename StoreTraits<S>::R, BC, TY>;
+    return RP ? sizeof(typename StoreTraits<S>::R) * (size_t)(4 * 3 * Sh::RN)
+              : step_smem_bytes<Q, typename StoreTraits<S>::R, BC, TY, CL>();
 }
 
-template <int Q, typename S, int CL, int BC, int TY, int OCC = 0>
+template <int Q, typename S, int CL, int BC, int TY, int OCC = 0, bool RP = false>
+cudaError_t prepare_step_t()
+{
+    return cudaFuncSetAttribute(step_kernel<Q, S, CL, BC, TY, OCC, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kernel_smem_bytes<Q, S, CL, BC, TY, RP>());
+}
+
+template <int Q, typename S, int CL, int BC, int TY, int OCC = 0, bool RP = false>
 cudaError_t launch_step_t(const StepArgs& a, int nbatch, cudaStream_t s)
 {
     using Sh = StepShape<Q, typename StoreTraits<S>::R, BC, TY>;
     static bool attr_set = false;  // per instantiation; prepare_step_t sets it ahead of stream capture
     if (!attr_set) {
-        cudaError_t e = prepare_step_t<Q, S, CL, BC, TY, OCC>();
+        cudaError_t e = prepare_step_t<Q, S, CL, BC, TY, OCC, RP>();
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -831,7 +849,7 @@ cudaError_t launch_step_t(const StepArgs& a, int nbatch, cudaStream_t s)
     const int chunks = (a.nz + a.zchunk - 1) / a.zchunk;
     dim3 grid(tiles, chunks, nbatch), block(Sh::TX, TY);
     if (CL == CL_LEARNED && !a.mlp) return cudaErrorInvalidValue;
-    step_kernel<Q, S, CL, BC, TY, OCC><<<grid, block, step_smem_bytes<Q, typename StoreTraits<S>::R, BC, TY, CL>(), s>>>(a);
+    step_kernel<Q, S, CL, BC, TY, OCC, RP><<<grid, block, kernel_smem_bytes<Q, S, CL, BC, TY, RP>(), s>>>(a);
     return cudaGetLastError();
 }
 

@@ -7,6 +7,8 @@
 #include "lbm_step.cuh"
 #include "lbm_step_async.cuh"
 #include "lbm_step_tma.cuh"
+#include "lbm_step_pf.cuh"
+#include "lbm_step_split.cuh"
 
 #include <type_traits>
 
@@ -53,6 +55,59 @@ cudaError_t launch_step_qs(int closure, int bc, int ty, int variant, const StepA
                 return a ? launch_step_t<Q, S, CL_BGK, BC_PERIODIC, 8, 3>(*a, nbatch, s) : (nbatch < 0 ? prepare_step_t<Q, S, CL_BGK, BC_PERIODIC, 8, 3>() : cudaSuccess);
             return cudaErrorNotSupported;
         }
+    }
+    if (variant == VAR_PREFETCH) {
+#define LBM_PF_CASE(CL, BCV, TYV)                                                               \
+    if (closure == CL && bc == BCV && ty == TYV)                                                \
+        return a ? launch_pf_t<Q, S, CL, BCV, TYV>(*a, nbatch, s) : (nbatch < 0 ? prepare_pf_t<Q, S, CL, BCV, TYV>() : cudaSuccess);
+        LBM_PF_CASE(CL_BGK, BC_PERIODIC, 8)
+        LBM_PF_CASE(CL_KCMP, BC_PERIODIC, 8)
+        LBM_PF_CASE(CL_KCRB_H, BC_PERIODIC, 8)
+        LBM_PF_CASE(CL_KCRB_RAW, BC_PERIODIC, 8)
+        LBM_PF_CASE(CL_BGK, BC_WALLS_Y, 8)
+        LBM_PF_CASE(CL_KCMP, BC_WALLS_Y, 8)
+        if constexpr (sizeof(typename StoreTraits<S>::R) == 4) {
+            LBM_PF_CASE(CL_KCMP, BC_PERIODIC, 4)
+            LBM_PF_CASE(CL_KCMP, BC_PERIODIC, 16)
+        }
+#undef LBM_PF_CASE
+        return cudaErrorNotSupported;
+    }
+    if (variant == VAR_SPLIT) {
+#define LBM_SB_CASE(CL, BCV, TYV)                                                               \
+    if (closure == CL && bc == BCV && ty == TYV)                                                \
+        return a ? launch_sb_t<Q, S, CL, BCV, TYV>(*a, nbatch, s) : (nbatch < 0 ? prepare_sb_t<Q, S, CL, BCV, TYV>() : cudaSuccess);
+        LBM_SB_CASE(CL_BGK, BC_PERIODIC, 8)
+        LBM_SB_CASE(CL_KCMP, BC_PERIODIC, 8)
+        LBM_SB_CASE(CL_KCRB_H, BC_PERIODIC, 8)
+        LBM_SB_CASE(CL_KCRB_RAW, BC_PERIODIC, 8)
+        LBM_SB_CASE(CL_BGK, BC_WALLS_Y, 8)
+        LBM_SB_CASE(CL_KCMP, BC_WALLS_Y, 8)
+        if constexpr (sizeof(typename StoreTraits<S>::R) == 4) {
+            LBM_SB_CASE(CL_KCMP, BC_PERIODIC, 4)
+            LBM_SB_CASE(CL_KCMP, BC_PERIODIC, 16)
+        }
+#undef LBM_SB_CASE
+        return cudaErrorNotSupported;
+    }
+    if (variant == VAR_REPULL || variant == VAR_REPULL_OCC4) {
+#define LBM_RP_CASE(CL, BCV, TYV)                                                                        \
+    if (closure == CL && bc == BCV && ty == TYV) {                                                       \
+        if (variant == VAR_REPULL)                                                                       \
+            return a ? launch_step_t<Q, S, CL, BCV, TYV, 3, true>(*a, nbatch, s)                         \
+                     : (nbatch < 0 ? prepare_step_t<Q, S, CL, BCV, TYV, 3, true>() : cudaSuccess);       \
+        return a ? launch_step_t<Q, S, CL, BCV, TYV, 4, true>(*a, nbatch, s)                             \
+                 : (nbatch < 0 ? prepare_step_t<Q, S, CL, BCV, TYV, 4, true>() : cudaSuccess);           \
+    }
+        if constexpr (sizeof(typename StoreTraits<S>::R) == 4) {
+            LBM_RP_CASE(CL_BGK, BC_PERIODIC, 8)
+            LBM_RP_CASE(CL_KCMP, BC_PERIODIC, 8)
+            LBM_RP_CASE(CL_KCRB_H, BC_PERIODIC, 8)
+            LBM_RP_CASE(CL_KCRB_RAW, BC_PERIODIC, 8)
+            LBM_RP_CASE(CL_KCMP, BC_WALLS_Y, 8)
+        }
+#undef LBM_RP_CASE
+        return cudaErrorNotSupported;
     }
     if (variant != VAR_REGISTER) return cudaErrorNotSupported;
 #define LBM_STEP_CASE(CL, BCV, TYV)                                                             \

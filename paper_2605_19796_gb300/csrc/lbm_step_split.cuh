@@ -1,0 +1,240 @@
+// Fused step kernel with a split arrive/wait barrier (sm_103a).
+//
+// Same update, CTA decomposition and population stash as step_kernel
+// (lbm_step.cuh).  Two scheduling changes:
+//
+//  * The threads that own a halo column issue the pulls of their halo cell and
+//    of their own cell together, so a plane costs them one load latency, not two.
+//  * The per-plane __syncthreads is split.  After publishing the velocities of
+//    plane k+1 to the ring a thread ARRIVES on an mbarrier and goes on; it WAITS
+//    (for the phase of plane k, completed one iteration earlier by the
+//    slowest thread) only right before it reads the neighbour velocities of
+//    plane k.  Warps with no halo work therefore run up to a plane ahead
+//    instead of idling at a barrier while the halo warps finish.
+//
+// Ring slots: warps may drift by one plane, so the ring holds five planes.  At
+// plane k a thread reads planes k-1, k, k+1 and writes plane k+1 (before its
+// arrival); the fastest thread may already write plane k+2 while the slowest
+// still reads k-1..k+1, and it cannot reach plane k+3 before the slowest has
+// arrived for plane k+1, which it does after its last read of plane k-1.
+// (Keeping the z-neighbours in registers instead would allow four slots but
+// pushes the register count past the two-CTA budget.)
+// Plane p arrives on mbarrier (p - z0) & 1, phase ((p - z0) >> 1) & 1; a thread
+// arrives for plane p only after it waited for plane p-2 on the same mbarrier,
+// so an arrival never lands in an older phase.  Waits are bounded: on timeout
+// the step's status flag gets the timeout bit and the thread returns.
+#pragma once
+
+#include "lbm_mbarrier.cuh"
+#include "lbm_step.cuh"
+
+namespace lbmk {
+
+template <int Q, typename R, int BC, int TY>
+struct SplitShape {
+    using Sh = StepShape<Q, R, BC, TY>;
+    static constexpr size_t ring_off = 16;  // two mbarriers
+    static constexpr size_t stash_off = ring_off + sizeof(R) * (size_t)(5 * 3 * Sh::RN);
+    static constexpr size_t bytes = stash_off + sizeof(R) * (size_t)(2 * Q * Sh::NT);
+};
+
+template <int Q, typename S, int CL, int BC, int TY>
+__global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) == 8 || TY >= 16) ? 1 : 2)
+    step_kernel_sb(const StepArgs a)
+{
+    using R = typename StoreTraits<S>::R;
+    using Sh = StepShape<Q, R, BC, TY>;
+    using Sp = SplitShape<Q, R, BC, TY>;
+    constexpr int TX = Sh::TX, HY = Sh::HY, RX = Sh::RX, RN = Sh::RN, NT = Sh::NT, NB = Sh::NB;
+    static_assert(NB <= NT, "every halo cell of the ring needs a thread");
+    static_assert(CL != CL_LEARNED, "the learned closure runs in step_kernel");
+    extern __shared__ __align__(16) unsigned char smem_sb[];
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_sb);
+    R* ring = reinterpret_cast<R*>(smem_sb + Sp::ring_off);    // [5][3][RN]
+    R* stash = reinterpret_cast<R*>(smem_sb + Sp::stash_off);  // [2][Q][NT]
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int tiles_x = (nx + TX - 1) / TX;
+    const int x0 = (int)(blockIdx.x % tiles_x) * TX;
+    const int y0 = (int)(blockIdx.x / tiles_x) * TY;
+    const int z0 = (int)blockIdx.y * a.zchunk;
+    if (z0 >= nz) return;  // uniform over the CTA
+    const int z1 = min(nz, z0 + a.zchunk);
+    const int box = blockIdx.z;
+    const long long ps = a.popstride;
+    const int plane = (int)a.plane;
+    const S* __restrict__ fin = static_cast<const S*>(a.fin) + (long long)box * a.boxstride;
+    S* __restrict__ fout = static_cast<S*>(a.fout) + (long long)box * a.boxstride;
+
+    const double nu_d = a.box_nu[box];
+    const R nu = (R)nu_d;
+    const R tau_hat = (R)(nu_d / kTheta + 0.5);
+    const R omega = (R)(1.0 / (nu_d / kTheta + 0.5));
+    const R cnud = (R)a.cnu_delta;
+    constexpr bool FORCE = (BC == BC_WALLS_Y);
+    const R Fx = FORCE ? (R)a.force[0] : R(0), Fy = FORCE ? (R)a.force[1] : R(0), Fz = FORCE ? (R)a.force[2] : R(0);
+
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool own_store = gx < nx && gy < ny;
+    const Col own = make_col<BC>(gx, gy, nx, ny);
+    const int own_r = (ty + HY) * RX + (tx + 1);
+
+    Col hal = own;
+    int hal_r = -1;
+    if (tid < NB) {
+        int lx, ly;
+        int b = tid;
+        if (b < HY * RX) {
+            lx = b % RX - 1;
+            ly = b / RX - HY;
+        } else if ((b -= HY * RX) < HY * RX) {
+            lx = b % RX - 1;
+            ly = TY + b / RX;
+        } else {
+            b -= HY * RX;
+            lx = (b < TY) ? -1 : TX;
+            ly = b % TY;
+        }
+        hal = make_col<BC>(x0 + lx, y0 + ly, nx, ny);
+        hal_r = (ly + HY) * RX + (lx + 1);
+    }
+
+    if (tid == 0) {
+        mbar_init(&mbar[0], NT);
+        mbar_init(&mbar[1], NT);
+    }
+    __syncthreads();
+
+    auto zrows = [&](int z, int (&zr)[3]) {
+        const int zc = wrapi(z, nz);
+        zr[0] = (zc == 0 ? nz - 1 : zc - 1) * plane;
+        zr[1] = zc * plane;
+        zr[2] = (zc == nz - 1 ? 0 : zc + 1) * plane;
+    };
+    auto rslot = [&](int z) { return (z - z0 + 1) % 5; };
+    auto ringp = [&](int s, int c) { return ring + (s * 3 + c) * RN; };
+    auto put_u = [&](int z, int r, R vx, R vy, R vz) {
+        const int s = rslot(z);
+        ringp(s, 0)[r] = vx;
+        ringp(s, 1)[r] = vy;
+        ringp(s, 2)[r] = vz;
+    };
+    // pull of plane z: own cell (velocity to the ring; populations to the stash
+    // when `keep`) and, with `halo`, the thread's halo cell, loads issued together
+    auto load_plane = [&](int z, bool keep, bool halo, R& r, R& vx, R& vy, R& vz) {
+        int zr[3];
+        zrows(z, zr);
+        const bool do_h = halo && tid < NB;
+        R t[Q], gh[Q];
+        if (own.valid) pull<Q, S, R, BC>(fin, ps, own, zr, t);
+        if (do_h && hal.valid) pull<Q, S, R, BC>(fin, ps, hal, zr, gh);
+        r = 0;
+        vx = vy = vz = 0;
+        if (own.valid) {
+            moments<Q, R>(t, r, vx, vy, vz, Fx, Fy, Fz);
+            if (keep) {
+                R* st = stash + (z & 1) * Q * NT + tid;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) st[i * NT] = t[i];
+            }
+        }
+        put_u(z, own_r, vx, vy, vz);
+        if (do_h) {
+            R hx = 0, hy = 0, hz = 0;
+            if (hal.valid) {
+                R dh;
+                moments<Q, R>(gh, dh, hx, hy, hz, Fx, Fy, Fz);
+            }
+            put_u(z, hal_r, hx, hy, hz);
+        }
+    };
+    auto arrive = [&](int p) { mbar_arrive(&mbar[(p - z0) & 1]); };
+    auto wait = [&](int p) { return mbar_wait_bounded(&mbar[(p - z0) & 1], (unsigned)((p - z0) >> 1) & 1u); };
+
+    R drho, ux, uy, uz;  // moments of the own cell at plane z
+    {
+        R r0, v0x, v0y, v0z;
+        load_plane(z0 - 1, false, false, r0, v0x, v0y, v0z);  // z-derivative at z0 only: own column
+        load_plane(z0, true, true, drho, ux, uy, uz);
+        arrive(z0);
+    }
+
+    for (int z = z0; z < z1; ++z) {
+        // ---- plane z+1: own (and, while it will be collided, halo) velocities into the ring
+        R rn, vnx, vny, vnz;
+        load_plane(z + 1, z + 1 < z1, z + 1 < z1, rn, vnx, vny, vnz);
+        if (z + 1 < z1) arrive(z + 1);
+
+        // ---- plane z: wait until every thread has published it, then strain, closure, relaxation
+        if (!wait(z)) {
+            atomicOr(a.flag, kFlagTimeout);
+            return;
+        }
+        if (own.valid) {
+            if (own_store && !(isfinite(drho) && isfinite(ux) && isfinite(uy) && isfinite(uz))) atomicOr(a.flag, 1u);
+            const int sm = rslot(z - 1), s0 = rslot(z), sp = rslot(z + 1);
+            R du[3][3];  // du[a][b] = d_a u_b
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const R* r0 = ringp(s0, b);
+                du[0][b] = R(0.5) * (r0[own_r + 1] - r0[own_r - 1]);
+                du[2][b] = R(0.5) * (ringp(sp, b)[own_r] - ringp(sm, b)[own_r]);
+                if (BC == BC_WALLS_Y && gy == 0)
+                    du[1][b] = R(0.5) * (R(-3) * r0[own_r] + R(4) * r0[own_r + RX] - r0[own_r + 2 * RX]);
+                else if (BC == BC_WALLS_Y && gy == ny - 1)
+                    du[1][b] = R(0.5) * (R(3) * r0[own_r] - R(4) * r0[own_r - RX] + r0[own_r - 2 * RX]);
+                else
+                    du[1][b] = R(0.5) * (r0[own_r + RX] - r0[own_r - RX]);
+            }
+            const R Sxx = du[0][0], Syy = du[1][1], Szz = du[2][2];
+            const R Sxy = R(0.5) * (du[0][1] + du[1][0]);
+            const R Sxz = R(0.5) * (du[0][2] + du[2][0]);
+            const R Syz = R(0.5) * (du[1][2] + du[2][1]);
+            R g[Q];
+            const R* st = stash + (z & 1) * Q * NT + tid;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) g[i] = st[i * NT];
+            collide<Q, R, CL, FORCE>(g, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, omega, tau_hat, nu, cnud, Fx,
+                                     Fy, Fz);
+            if (own_store) {
+                S* dst = fout + (z * plane + own.yr[1] + own.xs[1]);
+                static_for<Q>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    store_g<S, R>(dst + (long long)i * ps, g[i], (R)weight_of(Q, i));
+                });
+            }
+        }
+        drho = rn;
+        ux = vnx;
+        uy = vny;
+        uz = vnz;
+    }
+}
+
+template <int Q, typename S, int CL, int BC, int TY>
+cudaError_t prepare_sb_t()
+{
+    return cudaFuncSetAttribute(step_kernel_sb<Q, S, CL, BC, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)SplitShape<Q, typename StoreTraits<S>::R, BC, TY>::bytes);
+}
+
+template <int Q, typename S, int CL, int BC, int TY>
+cudaError_t launch_sb_t(const StepArgs& a, int nbatch, cudaStream_t s)
+{
+    using Sh = StepShape<Q, typename StoreTraits<S>::R, BC, TY>;
+    static bool attr_set = false;  // per instantiation; prepare_sb_t sets it ahead of stream capture
+    if (!attr_set) {
+        cudaError_t e = prepare_sb_t<Q, S, CL, BC, TY>();
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int tiles = ((a.nx + Sh::TX - 1) / Sh::TX) * ((a.ny + TY - 1) / TY);
+    const int chunks = (a.nz + a.zchunk - 1) / a.zchunk;
+    dim3 grid(tiles, chunks, nbatch), block(Sh::TX, TY);
+    step_kernel_sb<Q, S, CL, BC, TY>
+        <<<grid, block, SplitShape<Q, typename StoreTraits<S>::R, BC, TY>::bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmk

@@ -26,42 +26,11 @@
 
 #include <cuda.h>
 
+#include "lbm_mbarrier.cuh"
 #include "lbm_step.cuh"
 
 namespace lbmk {
 
-constexpr unsigned int kFlagNonfinite = 1u;
-constexpr unsigned int kFlagTimeout = 2u;
-constexpr long long kMbarSpinLimit = 1LL << 22;  // polls before a wait gives up (~0.1 s; copies take microseconds)
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
-{
-    const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(a), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes)
-{
-    const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(a), "r"(bytes) : "memory");
-}
-// one bounded poll: true once the phase with the given parity has completed
-__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity)
-{
-    const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity)
-{
-    for (long long k = 0; k < kMbarSpinLimit; ++k)
-        if (mbar_test(bar, parity)) return true;
-    return false;
-}
 __device__ __forceinline__ void tma_load_4d(void* smem_dst, const CUtensorMap* map, int x, int y, int z, int w,
                                             uint64_t* bar)
 {

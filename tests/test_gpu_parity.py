@@ -405,3 +405,78 @@ def test_kcrr_fp32_velocity(lbm, orc):
     _, ug = orc.fields(fg)
     _, uo = orc.fields(fo)
     assert np.abs(ug - uo).max() <= 1e-5
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("closure", ["bgk", "kcmp", "kcrb_hermite", "kcrb_raw"])
+def test_load_schedule_variants(lbm, orc, storage, closure):
+    """Variants 5 (loads issued two planes ahead), 6 and 7 (no population stash,
+    the collision re-pulls its plane; sized for three and four CTAs per SM) and 8
+    (halo and own loads together, split arrive/wait barrier) only reschedule the
+    loads and synchronisation of the register pull (variant 1).  On a ragged box with
+    two boxes and several z-chunkings (one and two planes per CTA exercise the
+    pipelines' start and drain): FP64 matches the oracle to 1e-12, FP32 matches
+    variant 1 to FP32 rounding, 16-bit storage in rho and u to 1e-5 (one 16-bit
+    rounding of a population); within a variant the z-chunking changes no bit."""
+    shape = (45, 19, 23)
+    fields = [inputs.hit_fields(0, k0=3.0, urms=0.07, seed=40 + b, shape=shape) for b in range(2)]
+    rho = np.stack([f[0] for f in fields])
+    u = np.stack([f[1] for f in fields], axis=1)
+    nus = np.array([2e-5, 1e-4])
+    variants = (5, 8) if storage == "fp64" else (5, 6, 7, 8)
+    res = {}
+    for var, zc in [(1, 0)] + [(v, z) for v in variants for z in (0, 1, 2, 5)]:
+        with lbm.Solver(27, shape, nus, closure=closure, storage=storage, variant=var, zchunk=zc, nbatch=2) as s:
+            assert s.launch_config["variant"] == var
+            s.init_velocity(rho, u)
+            s.step(5)
+            res[(var, zc)] = s.get_populations()
+    for v in variants:
+        for zc in (1, 2, 5):
+            assert np.array_equal(res[(v, zc)], res[(v, 0)]), (v, zc)
+        if storage == "fp64":
+            for b in range(2):
+                fo = orc.run(orc.init_equilibrium(27, fields[b][0], fields[b][1]), 5, closure=CL[closure], nu=nus[b],
+                             c_nu=CNU[closure])
+                assert rel(res[(v, 0)][b], fo) < TOL64
+        elif storage == "fp32":
+            assert rel(res[(v, 0)], res[(1, 0)]) < 1e-6
+        else:
+            # a one-ulp difference of a stored population (relative spacing 2^-10
+            # for FP16, 2^-7 for BF16, at |f - w| <= gmax) may flip between the
+            # kernels' rounding orders and propagate over the five steps
+            gmax = np.abs(res[(1, 0)] - orc.lattice(27)[1][None, :, None, None, None]).max()
+            tol = 8 * (2.0 ** -10 if storage == "fp16" else 2.0 ** -7) * gmax
+            for b in range(2):
+                r1, u1 = orc.fields(res[(1, 0)][b])
+                rv, uv = orc.fields(res[(v, 0)][b])
+                assert np.abs(rv - r1).max() < tol and np.abs(uv - u1).max() < tol, (v, tol)
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_prefetch_variant_channel(lbm, orc, q):
+    """Variants 5 and 6 with bounce-back walls and a body force: FP64 (variant 5)
+    against the oracle, FP32 against variant 1 to FP32 rounding."""
+    rho, u = inputs.channel_fields(16, 11, 9, 0.05, seed=5)
+    F = (1e-5, 0.0, 0.0)
+    with lbm.Solver(q, (16, 11, 9), 2e-3, closure="kcmp", storage="fp64", bc=(0, 1, 0), force=F, variant=5,
+                    zchunk=3) as s:
+        s.init_velocity(rho, u)
+        s.step(6)
+        fg = s.get_populations()
+    fo = orc.run(orc.init_equilibrium(q, rho, u), 6, closure=1, nu=2e-3, c_nu=0.035, bc=(0, 1, 0), F=F)
+    assert rel(fg, fo) < TOL64
+    out = {}
+    for var in (1, 5, 6, 8):
+        with lbm.Solver(q, (16, 11, 9), 2e-3, closure="kcmp", storage="fp32", bc=(0, 1, 0), force=F,
+                        variant=var) as s:
+            s.init_velocity(rho, u)
+            s.step(6)
+            out[var] = s.get_populations()
+    for var in (5, 6, 8):
+        assert rel(out[var], out[1]) < 1e-6, var
+    with lbm.Solver(q, (16, 11, 9), 2e-3, closure="kcmp", storage="fp64", bc=(0, 1, 0), force=F, variant=8,
+                    zchunk=2) as s:
+        s.init_velocity(rho, u)
+        s.step(6)
+        assert rel(s.get_populations(), fo) < TOL64

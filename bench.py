@@ -67,7 +67,10 @@ def log(*a):
 
 def kernel_hash() -> str:
     h = hashlib.sha256()
-    for f in ("lbm_step.cuh", "lbm_step_inst.cuh", "lbm_lattice.cuh"):
+    csrc = os.path.join(ROOT, "paper_2605_19796_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if not (f.startswith("lbm_step") or f in ("lbm_lattice.cuh", "lbm_mbarrier.cuh", "lbm_capi.cu")):
+            continue
         with open(os.path.join(ROOT, "paper_2605_19796_gb300", "csrc", f), "rb") as fp:
             h.update(fp.read())
     return h.hexdigest()[:16]
@@ -195,7 +198,7 @@ def cpu_baseline(wl: dict, budget_s: float = 15.0, steps: int = 0):
     t = time.perf_counter()
     f = run(f, 1)
     t1 = time.perf_counter() - t
-    k = steps or max(1, min(200, int(budget_s / max(t1, 1e-6))))
+    k = steps or max(1, min(5000, int(budget_s / max(t1, 1e-6))))
     t = time.perf_counter()
     run(f, k)
     dt = time.perf_counter() - t
@@ -237,7 +240,8 @@ def main():
     ap.add_argument("--tile-y", type=int, default=0)
     ap.add_argument("--zchunk", type=int, default=0)
     ap.add_argument("--variant", type=int, default=0)
-    ap.add_argument("--autotune", type=int, default=1, help="run the library autotuner before the warm-up (1/0)")
+    ap.add_argument("--autotune", type=int, default=0,
+                    help="run the library autotuner before the warm-up (1/0); the default launch is the measured one")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     wl = WORKLOADS[args.workload]

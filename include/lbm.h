@@ -101,7 +101,8 @@ typedef struct {
     int tile_y;         /* tuning: rows per CTA tile (0 = library default)           */
     int zchunk;         /* tuning: z-planes per CTA march (0 = library default)      */
     int variant;        /* tuning: step-kernel variant, 0 = library default
-                           (the register pull), 1 = register pull, 2 = asynchronous-copy pipeline
+                           (8 for D3Q27 with KC-MP or KC-RB, else 1),
+                           1 = register pull, 2 = asynchronous-copy pipeline
                            (FP32 storage, periodic boxes), 3 = register pull
                            sized for three CTAs per SM (32-bit arithmetic,
                            periodic, BGK/KC-MP, tile_y 8), 4 = TMA-staged
@@ -111,7 +112,9 @@ typedef struct {
                            without the population stash (re-pulled for the
                            collision; three / four CTAs per SM, 32-bit
                            arithmetic), 8 = register pull with a split
-                           arrive/wait barrier (5-8: BGK, KC-MP, KC-RB)      */
+                           arrive/wait barrier, 9 = two cells per thread on
+                           packed FP32 pairs (32-bit arithmetic) (5-9: BGK,
+                           KC-MP, KC-RB)                                     */
     int disable_graphs; /* nonzero: lbm_step launches kernels one by one instead of
                            replaying a captured CUDA graph                        */
 } lbm_config;

@@ -308,11 +308,18 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
     if (has_force && bc_kind != BC_WALLS_Y)
         return fail(LBM_ERR_UNSUPPORTED, "a body force is supported with bounce-back walls (channel) only");
     int tile_y = cfg->tile_y ? cfg->tile_y : 8;
-    if (cfg->variant < VAR_DEFAULT || cfg->variant > VAR_SPLIT) return fail(LBM_ERR_ARG, "unknown kernel variant");
+    if (cfg->variant < VAR_DEFAULT || cfg->variant > VAR_PAIR) return fail(LBM_ERR_ARG, "unknown kernel variant");
     int variant = cfg->variant;
-    // the register pull is the fastest variant measured on every workload built;
-    // lbm_autotune may pick another one for a given box
-    if (variant == VAR_DEFAULT) variant = VAR_REGISTER;
+    // measured defaults: the split-barrier pull for D3Q27 with a closure carrier
+    // (KC-MP, KC-RB), the register pull elsewhere; lbm_autotune may pick another
+    // variant for a given box
+    if (variant == VAR_DEFAULT) {
+        const bool carrier = cfg->closure == LBM_KCMP || cfg->closure == LBM_KCRB_HERMITE || cfg->closure == LBM_KCRB_RAW;
+        variant = (cfg->lattice == LBM_D3Q27 && carrier &&
+                   step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, VAR_SPLIT))
+                      ? VAR_SPLIT
+                      : VAR_REGISTER;
+    }
     if (variant == VAR_TMA && !tma_shape_ok(cfg->nx, cfg->ny, tile_y))
         return fail(LBM_ERR_UNSUPPORTED, "the TMA variant needs nx % 32 == 0 and ny % tile_y == 0");
     if (!step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, variant))
@@ -463,7 +470,7 @@ int lbm_autotune(lbm_handle* h, int trials)
 {
     if (int rc = check_handle(h)) return rc;
     if (trials < 1) trials = 3;
-    static const int kVariants[] = {VAR_REGISTER, VAR_SPLIT, VAR_REPULL, VAR_REPULL_OCC4, VAR_PREFETCH,
+    static const int kVariants[] = {VAR_REGISTER, VAR_SPLIT, VAR_PAIR, VAR_REPULL, VAR_REPULL_OCC4, VAR_PREFETCH,
                                     VAR_REGISTER_OCC3, VAR_ASYNC, VAR_TMA};
     static const int kTiles[] = {4, 8, 16};
     static const int kChunks[] = {8, 16, 32, 64, 128};

@@ -9,6 +9,7 @@
 #include "lbm_step_tma.cuh"
 #include "lbm_step_pf.cuh"
 #include "lbm_step_split.cuh"
+#include "lbm_step_x2.cuh"
 
 #include <type_traits>
 
@@ -88,6 +89,22 @@ cudaError_t launch_step_qs(int closure, int bc, int ty, int variant, const StepA
             LBM_SB_CASE(CL_KCMP, BC_PERIODIC, 16)
         }
 #undef LBM_SB_CASE
+        return cudaErrorNotSupported;
+    }
+    if (variant == VAR_PAIR) {
+        if constexpr (sizeof(typename StoreTraits<S>::R) == 4) {
+#define LBM_X2_CASE(CL, BCV, TYV)                                                               \
+    if (closure == CL && bc == BCV && ty == TYV)                                                \
+        return a ? launch_x2_t<Q, S, CL, BCV, TYV>(*a, nbatch, s) : (nbatch < 0 ? prepare_x2_t<Q, S, CL, BCV, TYV>() : cudaSuccess);
+            LBM_X2_CASE(CL_BGK, BC_PERIODIC, 8)
+            LBM_X2_CASE(CL_KCMP, BC_PERIODIC, 8)
+            LBM_X2_CASE(CL_KCRB_H, BC_PERIODIC, 8)
+            LBM_X2_CASE(CL_KCRB_RAW, BC_PERIODIC, 8)
+            LBM_X2_CASE(CL_BGK, BC_WALLS_Y, 8)
+            LBM_X2_CASE(CL_KCMP, BC_WALLS_Y, 8)
+            LBM_X2_CASE(CL_KCMP, BC_PERIODIC, 4)
+#undef LBM_X2_CASE
+        }
         return cudaErrorNotSupported;
     }
     if (variant == VAR_REPULL || variant == VAR_REPULL_OCC4) {

@@ -366,16 +366,20 @@ def test_tma_variant_matches(lbm, orc, shape, nbatch, closure):
 
 
 def test_default_variant_selection(lbm):
-    with lbm.Solver(27, (64, 32, 16), 1e-4, closure="kcmp", storage="fp32") as s:
-        assert s.launch_config["variant"] == 1
+    """Library default: the split-barrier pull (8) for D3Q27 with KC-MP or KC-RB,
+    the register pull (1) for BGK, D3Q19, KC-RR and the learned closure; an
+    explicitly requested variant that is not built for a box is refused."""
+    for q, closure, storage, want in ((27, "kcmp", "fp32", 8), (27, "kcrb_hermite", "fp16", 8), (27, "kcmp", "fp64", 8),
+                                      (27, "bgk", "fp32", 1), (19, "kcmp", "fp32", 1), (27, "kcrr", "fp64", 1),
+                                      (27, "learned", "fp32", 1)):
+        with lbm.Solver(q, (40, 32, 16), 1e-4, closure=closure, storage=storage) as s:
+            assert s.launch_config["variant"] == want, (q, closure, storage)
     with lbm.Solver(27, (64, 32, 16), 1e-4, closure="kcmp", storage="fp32", variant=4) as s:
         assert s.launch_config["variant"] == 4
-    with lbm.Solver(27, (40, 32, 16), 1e-4, closure="kcmp", storage="fp32") as s:
-        assert s.launch_config["variant"] == 1
-    with lbm.Solver(27, (64, 32, 16), 1e-4, closure="kcmp", storage="fp64") as s:
-        assert s.launch_config["variant"] == 1
     with pytest.raises(lbm.LbmError):
         lbm.Solver(27, (40, 32, 16), 1e-4, closure="kcmp", storage="fp32", variant=4)
+    with pytest.raises(lbm.LbmError):
+        lbm.Solver(27, (40, 32, 16), 1e-4, closure="kcmp", storage="fp64", variant=9)
 
 
 @pytest.mark.parametrize("shape", [(37, 21, 13), (16, 8, 6)])
@@ -413,7 +417,8 @@ def test_load_schedule_variants(lbm, orc, storage, closure):
     """Variants 5 (loads issued two planes ahead), 6 and 7 (no population stash,
     the collision re-pulls its plane; sized for three and four CTAs per SM) and 8
     (halo and own loads together, split arrive/wait barrier) only reschedule the
-    loads and synchronisation of the register pull (variant 1).  On a ragged box with
+    loads and synchronisation of the register pull (variant 1); variant 9 runs
+    the same arithmetic on packed FP32 pairs, two cells per thread.  On a ragged box with
     two boxes and several z-chunkings (one and two planes per CTA exercise the
     pipelines' start and drain): FP64 matches the oracle to 1e-12, FP32 matches
     variant 1 to FP32 rounding, 16-bit storage in rho and u to 1e-5 (one 16-bit
@@ -423,7 +428,7 @@ def test_load_schedule_variants(lbm, orc, storage, closure):
     rho = np.stack([f[0] for f in fields])
     u = np.stack([f[1] for f in fields], axis=1)
     nus = np.array([2e-5, 1e-4])
-    variants = (5, 8) if storage == "fp64" else (5, 6, 7, 8)
+    variants = (5, 8) if storage == "fp64" else (5, 6, 7, 8, 9)
     res = {}
     for var, zc in [(1, 0)] + [(v, z) for v in variants for z in (0, 1, 2, 5)]:
         with lbm.Solver(27, shape, nus, closure=closure, storage=storage, variant=var, zchunk=zc, nbatch=2) as s:
@@ -467,13 +472,13 @@ def test_prefetch_variant_channel(lbm, orc, q):
     fo = orc.run(orc.init_equilibrium(q, rho, u), 6, closure=1, nu=2e-3, c_nu=0.035, bc=(0, 1, 0), F=F)
     assert rel(fg, fo) < TOL64
     out = {}
-    for var in (1, 5, 6, 8):
+    for var in (1, 5, 6, 8, 9):
         with lbm.Solver(q, (16, 11, 9), 2e-3, closure="kcmp", storage="fp32", bc=(0, 1, 0), force=F,
                         variant=var) as s:
             s.init_velocity(rho, u)
             s.step(6)
             out[var] = s.get_populations()
-    for var in (5, 6, 8):
+    for var in (5, 6, 8, 9):
         assert rel(out[var], out[1]) < 1e-6, var
     with lbm.Solver(q, (16, 11, 9), 2e-3, closure="kcmp", storage="fp64", bc=(0, 1, 0), force=F, variant=8,
                     zchunk=2) as s:

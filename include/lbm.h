@@ -113,8 +113,9 @@ typedef struct {
                            collision; three / four CTAs per SM, 32-bit
                            arithmetic), 8 = register pull with a split
                            arrive/wait barrier, 9 = two cells per thread on
-                           packed FP32 pairs (32-bit arithmetic) (5-9: BGK,
-                           KC-MP, KC-RB)                                     */
+                           packed FP32 pairs (32-bit arithmetic), 10 = 9
+                           without the stash (periodic) (5-10: BGK, KC-MP,
+                           KC-RB)                                            */
     int disable_graphs; /* nonzero: lbm_step launches kernels one by one instead of
                            replaying a captured CUDA graph                        */
 } lbm_config;

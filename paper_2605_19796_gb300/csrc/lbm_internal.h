@@ -40,7 +40,7 @@ void mlp_pack(const float* params, const float* stats, unsigned char* out);
 // pull with its register budget sized for three CTAs per SM (32-bit arithmetic).
 enum Variant { VAR_DEFAULT = 0, VAR_REGISTER = 1, VAR_ASYNC = 2, VAR_REGISTER_OCC3 = 3, VAR_TMA = 4, VAR_PREFETCH = 5,
                VAR_REPULL = 6, VAR_REPULL_OCC4 = 7, VAR_SPLIT = 8,
-               VAR_PAIR = 9 };
+               VAR_PAIR = 9, VAR_PAIR_REPULL = 10 };
 
 // TMA variant: tile heights it is built for, and the tensor map of a population
 // buffer (4D: x, y, z, population-of-box; box 40 x (tile_y + 2) x 1 x 1)

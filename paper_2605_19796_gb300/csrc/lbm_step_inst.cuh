@@ -107,6 +107,19 @@ cudaError_t launch_step_qs(int closure, int bc, int ty, int variant, const StepA
         }
         return cudaErrorNotSupported;
     }
+    if (variant == VAR_PAIR_REPULL) {
+        if constexpr (sizeof(typename StoreTraits<S>::R) == 4) {
+#define LBM_X2R_CASE(CL, BCV, TYV)                                                              \
+    if (closure == CL && bc == BCV && ty == TYV)                                                \
+        return a ? launch_x2_t<Q, S, CL, BCV, TYV, true>(*a, nbatch, s) : (nbatch < 0 ? prepare_x2_t<Q, S, CL, BCV, TYV, true>() : cudaSuccess);
+            LBM_X2R_CASE(CL_BGK, BC_PERIODIC, 8)
+            LBM_X2R_CASE(CL_KCMP, BC_PERIODIC, 8)
+            LBM_X2R_CASE(CL_KCRB_H, BC_PERIODIC, 8)
+            LBM_X2R_CASE(CL_KCRB_RAW, BC_PERIODIC, 8)
+#undef LBM_X2R_CASE
+        }
+        return cudaErrorNotSupported;
+    }
     if (variant == VAR_REPULL || variant == VAR_REPULL_OCC4) {
 #define LBM_RP_CASE(CL, BCV, TYV)                                                                        \
     if (closure == CL && bc == BCV && ty == TYV) {                                                       \

@@ -287,7 +287,7 @@ __device__ __forceinline__ void collide2(F2 (&g)[Q], F2 drho, F2 ux, F2 uy, F2 u
 
 // ------------------------------------------------------------------ kernel
 
-template <int Q, int BC, int TY>
+template <int Q, int BC, int TY, bool RP = false>
 struct PairShape {
     static constexpr int TX = 64;  // cells per tile row (two per lane)
     static constexpr int HY = (BC == BC_WALLS_Y) ? 2 : 1;
@@ -296,16 +296,17 @@ struct PairShape {
     static constexpr int RN = RX * RY;
     static constexpr int NT = 32 * TY;  // threads
     static constexpr int NB = RN - TX * TY;  // halo cells of the ring plane
-    static constexpr int NBP = (NB + 1) / 2;  // halo threads (two halo cells each)
+    // halo threads: two halo cells each, or one each without the stash (RP)
+    static constexpr int NBP = RP ? NB : (NB + 1) / 2;
     static constexpr size_t ring_off = 16;
     static constexpr size_t stash_off = ring_off + sizeof(float) * (size_t)(5 * 3 * RN);
-    static constexpr size_t bytes = stash_off + sizeof(float2) * (size_t)(2 * Q * NT);
+    static constexpr size_t bytes = stash_off + (RP ? 0 : sizeof(float2) * (size_t)(2 * Q * NT));
 };
 
 template <int Q, int BC, int TY>
 __device__ __forceinline__ void ring_cell(int b, int& lx, int& ly)
 {
-    using P = PairShape<Q, BC, TY>;
+    using P = PairShape<Q, BC, TY, false>;
     if (b < P::HY * P::RX) {
         lx = b % P::RX - 1;
         ly = b / P::RX - P::HY;
@@ -319,10 +320,12 @@ __device__ __forceinline__ void ring_cell(int b, int& lx, int& ly)
     }
 }
 
-template <int Q, typename S, int CL, int BC, int TY>
-__global__ void __launch_bounds__(32 * TY, TY >= 8 ? 1 : 2) step_kernel_x2(const StepArgs a)
+// RP: no population stash; the collision re-pulls its plane (loaded one plane
+// earlier, mostly L1/L2 hits), halo cells one per thread, sized for two CTAs per SM
+template <int Q, typename S, int CL, int BC, int TY, bool RP = false>
+__global__ void __launch_bounds__(32 * TY, (TY >= 8 && !RP) ? 1 : 2) step_kernel_x2(const StepArgs a)
 {
-    using P = PairShape<Q, BC, TY>;
+    using P = PairShape<Q, BC, TY, RP>;
     constexpr int TX = P::TX, HY = P::HY, RX = P::RX, RN = P::RN, NT = P::NT, NB = P::NB, NBP = P::NBP;
     static_assert(NBP <= NT, "every halo pair needs a thread");
     extern __shared__ __align__(16) unsigned char smem_x2[];
@@ -369,7 +372,7 @@ __global__ void __launch_bounds__(32 * TY, TY >= 8 ? 1 : 2) step_kernel_x2(const
         h1 = make_col<BC>(x0 + lx, y0 + ly, nx, ny);
         h1_r = (ly + HY) * RX + (lx + 1);
         h1_ok = h1.valid;
-        if (tid + NBP < NB) {
+        if (!RP && tid + NBP < NB) {
             ring_cell<Q, BC, TY>(tid + NBP, lx, ly);
             h2 = make_col<BC>(x0 + lx, y0 + ly, nx, ny);
             h2_r = (ly + HY) * RX + (lx + 1);
@@ -401,13 +404,19 @@ __global__ void __launch_bounds__(32 * TY, TY >= 8 ? 1 : 2) step_kernel_x2(const
         int zr[3];
         zrows(z, zr);
         const bool do_h = halo && tid < NBP;
-        F2 t[Q], gh[Q];
+        F2 t[Q];
+        float gs[Q];
+        F2 gh[RP ? 1 : Q];
         if (own.valid) pull2<Q, S, BC>(fin, ps, own, zr, t);
-        if (do_h) pull_any2<Q, S, BC>(fin, ps, h1, h2, h1_ok, h2_ok, zr, gh);
+        if constexpr (RP) {
+            if (do_h && h1_ok) pull<Q, S, float, BC>(fin, ps, h1, zr, gs);
+        } else {
+            if (do_h) pull_any2<Q, S, BC>(fin, ps, h1, h2, h1_ok, h2_ok, zr, gh);
+        }
         r = vx = vy = vz = bc2(0.f);
         if (own.valid) {
             moments2<Q>(t, r, vx, vy, vz, Fx, Fy, Fz);
-            if (keep) {
+            if (keep && !RP) {
                 F2* st = stash + (z & 1) * Q * NT + tid;
 #pragma unroll
                 for (int i = 0; i < Q; ++i) st[i * NT] = t[i];
@@ -415,7 +424,13 @@ __global__ void __launch_bounds__(32 * TY, TY >= 8 ? 1 : 2) step_kernel_x2(const
         }
         put_u(z, own_ra, vx.v.x, vy.v.x, vz.v.x);
         put_u(z, own_rb, vx.v.y, vy.v.y, vz.v.y);
-        if (do_h) {
+        if constexpr (RP) {
+            if (do_h) {
+                float dh, hx = 0.f, hy = 0.f, hz = 0.f;
+                if (h1_ok) moments<Q, float>(gs, dh, hx, hy, hz, Fx, Fy, Fz);
+                put_u(z, h1_r, hx, hy, hz);
+            }
+        } else if (do_h) {
             F2 dh, hx, hy, hz;
             moments2<Q>(gh, dh, hx, hy, hz, Fx, Fy, Fz);
             put_u(z, h1_r, h1_ok ? hx.v.x : 0.f, h1_ok ? hy.v.x : 0.f, h1_ok ? hz.v.x : 0.f);
@@ -469,9 +484,15 @@ __global__ void __launch_bounds__(32 * TY, TY >= 8 ? 1 : 2) step_kernel_x2(const
             const F2 Sxz = bc2(0.5f) * (du[0][2] + du[2][0]);
             const F2 Syz = bc2(0.5f) * (du[1][2] + du[2][1]);
             F2 g[Q];
-            const F2* st = stash + (z & 1) * Q * NT + tid;
+            if constexpr (RP) {
+                int zr[3];
+                zrows(z, zr);
+                pull2<Q, S, BC>(fin, ps, own, zr, g);
+            } else {
+                const F2* st = stash + (z & 1) * Q * NT + tid;
 #pragma unroll
-            for (int i = 0; i < Q; ++i) g[i] = st[i * NT];
+                for (int i = 0; i < Q; ++i) g[i] = st[i * NT];
+            }
             collide2<Q, CL, FORCE>(g, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, omega, tau_hat, nu, cnud, Fx,
                                    Fy, Fz);
             const int row = z * plane + own.yr[1];
@@ -497,27 +518,27 @@ __global__ void __launch_bounds__(32 * TY, TY >= 8 ? 1 : 2) step_kernel_x2(const
     }
 }
 
-template <int Q, typename S, int CL, int BC, int TY>
+template <int Q, typename S, int CL, int BC, int TY, bool RP = false>
 cudaError_t prepare_x2_t()
 {
-    return cudaFuncSetAttribute(step_kernel_x2<Q, S, CL, BC, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)PairShape<Q, BC, TY>::bytes);
+    return cudaFuncSetAttribute(step_kernel_x2<Q, S, CL, BC, TY, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)PairShape<Q, BC, TY, RP>::bytes);
 }
 
-template <int Q, typename S, int CL, int BC, int TY>
+template <int Q, typename S, int CL, int BC, int TY, bool RP = false>
 cudaError_t launch_x2_t(const StepArgs& a, int nbatch, cudaStream_t s)
 {
-    using P = PairShape<Q, BC, TY>;
+    using P = PairShape<Q, BC, TY, RP>;
     static bool attr_set = false;  // per instantiation; prepare_x2_t sets it ahead of stream capture
     if (!attr_set) {
-        cudaError_t e = prepare_x2_t<Q, S, CL, BC, TY>();
+        cudaError_t e = prepare_x2_t<Q, S, CL, BC, TY, RP>();
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     const int tiles = ((a.nx + P::TX - 1) / P::TX) * ((a.ny + TY - 1) / TY);
     const int chunks = (a.nz + a.zchunk - 1) / a.zchunk;
     dim3 grid(tiles, chunks, nbatch), block(32, TY);
-    step_kernel_x2<Q, S, CL, BC, TY><<<grid, block, P::bytes, s>>>(a);
+    step_kernel_x2<Q, S, CL, BC, TY, RP><<<grid, block, P::bytes, s>>>(a);
     return cudaGetLastError();
 }
 

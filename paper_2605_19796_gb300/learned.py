@@ -228,3 +228,83 @@ def _coarse_velocity(fc: torch.Tensor, nu: float) -> torch.Tensor:
     with lbm.Solver(q, (nx, ny, nz), nu, closure="bgk", storage="fp64") as s:
         s.set_populations(fc.double().cpu().numpy())
         return _velocity(s)
+
+
+def _mlups(closure: str, n: int, nu: float, params=None, stats=None, steps: int = 50) -> float:
+    """Steps per second of one closure on an n^3 FP32 D3Q27 box (CUDA events, graph replay)."""
+    rho, u = inputs.hit_fields(n, k0=4.0, urms=0.04, seed=5, device="cuda")
+    with lbm.Solver(27, (n,) * 3, nu, closure=closure, storage="fp32") as s:
+        if closure == "learned":
+            s.set_learned_closure(params, stats)
+        s.init_velocity_device(rho, u)
+        s.step(steps)  # warm-up and graph capture
+        s.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream = torch.cuda.current_stream()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.step(steps)
+        s.synchronize()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return n ** 3 * steps / (e0.elapsed_time(e1) * 1e-3) / 1e6
+
+
+def main(argv=None) -> Dict:
+    """Full pipeline: fine runs -> filtered data -> training -> held-out a priori
+    errors -> a posteriori coarse LES -> throughput; writes the trained network
+    (params, stats) to --out and prints one JSON line of results."""
+    import argparse
+    import json
+    import os
+    import time
+
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--n-fine", type=int, default=512)
+    ap.add_argument("--factor", type=int, default=4)
+    ap.add_argument("--train-seeds", default="0,1,2,3")
+    ap.add_argument("--test-seeds", default="4")
+    ap.add_argument("--k0s", default="4,8")
+    ap.add_argument("--snap-steps", default="300,600")
+    ap.add_argument("--keep", type=float, default=0.25)
+    ap.add_argument("--iters", type=int, default=4000)
+    ap.add_argument("--batch", type=int, default=16384)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--t0", type=int, default=400)
+    ap.add_argument("--coarse-steps", type=int, default=150)
+    ap.add_argument("--mlups-sizes", default="128,256")
+    ap.add_argument("--out", default=os.path.join(os.path.dirname(__file__), "data", "learned_closure.npz"))
+    a = ap.parse_args(argv)
+    ints = lambda s: tuple(int(v) for v in s.split(",") if v)
+    floats = lambda s: tuple(float(v) for v in s.split(",") if v)
+    nu_fine = 1e-4
+    t = time.perf_counter()
+    X, T, KC = generate(a.n_fine, a.factor, ints(a.train_seeds), floats(a.k0s), nu_fine, snap_steps=ints(a.snap_steps),
+                        keep=a.keep)
+    Xh, Th, KCh = generate(a.n_fine, a.factor, ints(a.test_seeds), floats(a.k0s), nu_fine,
+                           snap_steps=ints(a.snap_steps), keep=a.keep, sample_seed=1)
+    t_data = time.perf_counter() - t
+    stats = standardisation(X, T)
+    t = time.perf_counter()
+    res = train(X, T, stats, iters=a.iters, batch=a.batch, lr=a.lr, log_every=max(1, a.iters // 8))
+    t_train = time.perf_counter() - t
+    apr = a_priori(res["params"], stats, Xh, Th, KCh)
+    post = a_posteriori(res["params"], stats, n_fine=a.n_fine, factor=a.factor, t0=a.t0, coarse_steps=a.coarse_steps,
+                        nu_fine=nu_fine)
+    os.makedirs(os.path.dirname(a.out), exist_ok=True)
+    np.savez(a.out, params=res["params"], stats=stats, n_fine=a.n_fine, factor=a.factor, nu_fine=nu_fine,
+             nu_coarse=nu_fine / a.factor)
+    nu_c = nu_fine / a.factor
+    mlups = {}
+    for n in ints(a.mlups_sizes):
+        mlups[f"{n}^3"] = {cl: _mlups(cl, n, nu_c, res["params"], stats) for cl in ("kcmp", "learned")}
+    out = {"samples_train": int(X.shape[0]), "samples_test": int(Xh.shape[0]), "t_data_s": t_data,
+           "t_train_s": t_train, "loss_history": res["history"], "a_priori_heldout": apr, "a_posteriori": post,
+           "mlups": mlups, "checkpoint": os.path.relpath(a.out, os.path.dirname(os.path.dirname(__file__))),
+           "config": vars(a)}
+    print(json.dumps(out), flush=True)
+    return out
+
+
+if __name__ == "__main__":
+    main()

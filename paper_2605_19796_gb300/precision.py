@@ -59,3 +59,22 @@ def run(n: int = 64, steps: int = 200, nu: float = 1e-4, k0: float = 4.0, urms: 
             "spectrum_rel_l2": float(torch.sqrt(((e[1:kmax] - er[1:kmax]) ** 2).sum() / (er[1:kmax] ** 2).sum())),
         })
     return res
+
+
+def main(argv=None) -> Dict:
+    """Storage-precision study of one decaying-turbulence case; prints one JSON line."""
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--closure", default="kcmp")
+    a = ap.parse_args(argv)
+    res = run(n=a.n, steps=a.steps, closure=a.closure)
+    print(json.dumps({"n": a.n, "steps": a.steps, "closure": a.closure, "results": res}), flush=True)
+    return res
+
+
+if __name__ == "__main__":
+    main()

@@ -418,7 +418,8 @@ def test_load_schedule_variants(lbm, orc, storage, closure):
     the collision re-pulls its plane; sized for three and four CTAs per SM) and 8
     (halo and own loads together, split arrive/wait barrier) only reschedule the
     loads and synchronisation of the register pull (variant 1); variant 9 runs
-    the same arithmetic on packed FP32 pairs, two cells per thread.  On a ragged box with
+    the same arithmetic on packed FP32 pairs, two cells per thread (10: without
+    the stash, re-pulling for the collision).  On a ragged box with
     two boxes and several z-chunkings (one and two planes per CTA exercise the
     pipelines' start and drain): FP64 matches the oracle to 1e-12, FP32 matches
     variant 1 to FP32 rounding, 16-bit storage in rho and u to 1e-5 (one 16-bit
@@ -428,7 +429,7 @@ def test_load_schedule_variants(lbm, orc, storage, closure):
     rho = np.stack([f[0] for f in fields])
     u = np.stack([f[1] for f in fields], axis=1)
     nus = np.array([2e-5, 1e-4])
-    variants = (5, 8) if storage == "fp64" else (5, 6, 7, 8, 9)
+    variants = (5, 8) if storage == "fp64" else (5, 6, 7, 8, 9, 10)
     res = {}
     for var, zc in [(1, 0)] + [(v, z) for v in variants for z in (0, 1, 2, 5)]:
         with lbm.Solver(27, shape, nus, closure=closure, storage=storage, variant=var, zchunk=zc, nbatch=2) as s:

@@ -228,8 +228,9 @@ int lbm_diagnostics_noalloc(const void* f_dev, int lattice, int storage, int nx,
 
 /* ---- Learned closure (training side) ----------------------------------
  * The learned closure replaces KC-MP's m_sgs = m_neq - m_CE (App. F.3) by a
- * network evaluated per cell: 10 inputs (m_neq/rho: xx yy zz xy xz yz; the
- * trace, second invariant and determinant of m_CE/rho; tau_hat), standardised,
+ * network evaluated per cell: 10 inputs (the KC-MP carrier (m_neq - m_CE)/rho:
+ * xx yy zz xy xz yz; the trace, second invariant and determinant of m_CE/rho;
+ * tau_hat), standardised,
  * three hidden layers of 64 SiLU units, 6 outputs (standardised m_sgs/rho).
  * Parameters: one FP32 vector of lbm_mlp_param_count() values in the order
  * W1 b1 W2 b2 W3 b3 W4 b4 (W row-major [out][in]).  Training data come from
@@ -279,14 +280,24 @@ int lbm_mlp_adamw(float* params, const float* grad, float* m, float* v, int step
 /* Box filter of one box's populations (storage format, [q][nz][ny][nx]) by
  * `factor` in every direction: filtered FP32 populations fc [q][nz/F][ny/F][nx/F]
  * and the exact SGS stress msgs [6][...] = bar(rho u u) - bar(rho u) bar(rho u)/rho_bar
- * (components xx yy zz xy xz yz).  Sizes must be multiples of factor. */
-int lbm_box_filter(const void* f_dev, int lattice, int storage, int nx, int ny, int nz, int factor, float* fc_dev,
-                   float* msgs_dev, void* stream);
+ * (Eq. m_sgs_2; components xx yy zz xy xz yz).  Sizes must be multiples of factor.
+ * neq_scale r: fc = bar(f) + (r - 1) bar(f - f0(rho, u)), f0 the fine cells' own
+ * equilibria; r = 1 is the plain filter, r = F tau_hat_c / tau_hat_f gives the
+ * coarse lattice's non-equilibrium part under acoustic scaling (the filtered
+ * fine one is F tau_hat_c / tau_hat_f times too small), while the SGS part
+ * bar(f0) - f0(rho_bar, u_bar) is kept.  r <= 0: LBM_ERR_ARG.
+ * pull != 0: filter the streamed populations f_i(x - c_i) (periodic box, Eq.
+ * streaming), i.e. the pre-collision state of the next step, which is the
+ * state a step kernel computes its closure inputs from; pull = 0: the stored
+ * post-collision populations. */
+int lbm_box_filter(const void* f_dev, int lattice, int storage, int nx, int ny, int nz, int factor, double neq_scale,
+                   int pull, float* fc_dev, float* msgs_dev, void* stream);
 
 /* Network inputs x [N][10] of every cell of an FP32 population array
  * (periodic box, kinematic viscosity nu of that lattice); when msgs is given,
  * the targets t [N][6] = msgs / rho; when kcmp is given, the analytic KC-MP
- * estimate (m_neq - m_CE) / rho [N][6] (App. F.3) for comparison. */
+ * estimate (m_neq - m_CE) / rho [N][6] (App. F.3, equal to inputs 0-5) for
+ * comparison. */
 int lbm_closure_features(const float* f_dev, int lattice, int nx, int ny, int nz, double nu, const float* msgs_dev,
                          float* x_dev, float* t_dev, float* kcmp_dev, void* stream);
 

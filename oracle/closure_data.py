@@ -35,14 +35,33 @@ def box_filter(a: np.ndarray, F: int) -> np.ndarray:
     return b.mean(axis=(-5, -3, -1))
 
 
-def filtered_state(f_fine: np.ndarray, F: int):
-    """(f_bar [q, nz/F, ny/F, nx/F], m_sgs [6, ...]) from fine populations f_fine [q, nz, ny, nx]."""
+def stream(f: np.ndarray) -> np.ndarray:
+    """Periodic pull streaming, Eq. (streaming): f_i(x) <- f_i(x - c_i)."""
+    c, _, _ = oracle.lattice(f.shape[0])
+    return np.stack([np.roll(f[i], shift=(c[i, 2], c[i, 1], c[i, 0]), axis=(0, 1, 2)) for i in range(f.shape[0])])
+
+
+def filtered_state(f_fine: np.ndarray, F: int, neq_scale: float = 1.0, pull: bool = False):
+    """(f_bar [q, nz/F, ny/F, nx/F], m_sgs [6, ...]) from fine populations f_fine [q, nz, ny, nx].
+
+    With neq_scale r != 1 the non-equilibrium part of the fine populations is
+    rescaled before filtering, f_bar = bar(f) + (r - 1) bar(f - f0(rho, u)) with
+    f0 each fine cell's own equilibrium: under acoustic scaling (dt_c = F dt_f)
+    the coarse lattice's first-order non-equilibrium part of the same flow is
+    r = F tau_hat_c / tau_hat_f times the filtered fine one (f1 ~ tau_hat S dt),
+    while the SGS part bar(f0) - f0(rho_bar, u_bar) (Eq. fsgs_def) is kept.
+    With pull, the streamed populations (the pre-collision state of the next
+    step, from which a step computes its closure inputs) are filtered."""
+    if pull:
+        f_fine = stream(f_fine)
     q = f_fine.shape[0]
     c, _, _ = oracle.lattice(q)
     rho = f_fine.sum(axis=0)
     mom = np.einsum("iabc,ik->kabc", f_fine, c.astype(float))
     u = mom / rho
     f_bar = box_filter(f_fine, F)
+    if neq_scale != 1.0:
+        f_bar = f_bar + (neq_scale - 1.0) * box_filter(f_fine - oracle.init_equilibrium(q, rho, u), F)
     rho_bar = box_filter(rho, F)
     rhou_bar = box_filter(mom, F)
     msgs = np.empty((6,) + rho_bar.shape)
@@ -64,8 +83,10 @@ def features(f_bar: np.ndarray, nu_coarse: float):
     A = -2.0 * oracle.THETA * tau_hat * S  # m_CE / rho
     n = rho.size
     x = np.empty((n, 10))
+    # the KC-MP carrier (m_neq - m_CE)/rho (App. F.3): the non-equilibrium second
+    # moment beyond its Chapman-Enskog part
     for k, (a, b) in enumerate(COMP):
-        x[:, k] = (mneq[a, b] / rho).ravel()
+        x[:, k] = (mneq[a, b] / rho - A[a, b]).ravel()
     Am = np.moveaxis(A.reshape(3, 3, n), 2, 0)  # [n, 3, 3]
     tr = np.trace(Am, axis1=1, axis2=2)
     tr2 = np.einsum("nab,nba->n", Am, Am)

@@ -4,8 +4,9 @@ The learned closure is KC-MP (App. F.3) with the SGS second moment taken from
 the network instead of m_neq - m_CE:
   1. pull streaming, Eq. (streaming); rho, u (App. F.1 step 1); f0 (Eq. discrete_equilibrium)
   2. strain S (Eqs. fd, strain_rate_discrete)
-  3. inputs x: m_neq / rho (6), trace / second invariant / determinant of
-     m_CE / rho = -2 theta tau_hat S (3), tau_hat (1); standardised
+  3. inputs x: the KC-MP carrier (m_neq - m_CE) / rho (6), trace / second
+     invariant / determinant of m_CE / rho = -2 theta tau_hat S (3), tau_hat (1);
+     standardised
   4. network (oracle/mlp.py) -> standardised m_sgs / rho -> m_sgs
   5. k = |tr m_sgs| / 2, omega_s (Eq. omega_sgs_operational)
   6. f_post = f - omega (f - f0 - f_sgs) - omega_s f_sgs, f_sgs = w/(2 theta^2) H : m_sgs
@@ -64,7 +65,7 @@ def inputs_and_state(f_post_prev: np.ndarray, nu: float):
     n = rho.size
     x = np.empty((n, 10))
     for k, (a, b) in enumerate(COMP):
-        x[:, k] = (mneq[a, b] / rho).ravel()
+        x[:, k] = (mneq[a, b] / rho - A[a, b]).ravel()
     Am = np.moveaxis(A.reshape(3, 3, n), 2, 0)
     tr = np.trace(Am, axis1=1, axis2=2)
     x[:, 6] = tr

@@ -12,6 +12,7 @@
 #include "../../include/lbm.h"
 #include "lbm_internal.h"
 #include "lbm_step.cuh"
+#include "lbm_equilibrium.cuh"
 #include "lbm_mlp_infer.cuh"
 
 #include <cstring>
@@ -46,29 +47,41 @@ __device__ __forceinline__ float silu_grad(float a)
 // cells) and the exact SGS stress of Eq. (m_sgs_2),
 // m_sgs = bar(rho u u) - bar(rho u) bar(rho u) / rho_bar.
 template <int Q, typename S>
-__global__ void filter_kernel(const S* f, int nx, int ny, int nz, int F, float* fc, float* msgs)
+__global__ void filter_kernel(const S* f, int nx, int ny, int nz, int F, double neq_scale, int pull, float* fc,
+                              float* msgs)
 {
     const int ncx = nx / F, ncy = ny / F, ncz = nz / F;
     const long long Nc = (long long)ncx * ncy * ncz, N = (long long)nx * ny * nz;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= Nc) return;
     const int cx = (int)(t % ncx), cy = (int)((t / ncx) % ncy), cz = (int)(t / ((long long)ncx * ncy));
-    double acc[Q];
-    for (int i = 0; i < Q; ++i) acc[i] = 0.0;
+    double acc[Q], accn[Q];  // filtered populations and filtered f - f0(rho, u) of the fine cells
+    for (int i = 0; i < Q; ++i) acc[i] = accn[i] = 0.0;
+    const bool rescale = neq_scale != 1.0;
     double r = 0, m[3] = {0, 0, 0}, uu[6] = {0, 0, 0, 0, 0, 0};
     for (int dz = 0; dz < F; ++dz)
         for (int dy = 0; dy < F; ++dy)
             for (int dx = 0; dx < F; ++dx) {
-                const long long c = ((long long)(cz * F + dz) * ny + (cy * F + dy)) * nx + (cx * F + dx);
+                const int X = cx * F + dx, Y = cy * F + dy, Z = cz * F + dz;
+                // population i of this fine cell, or with `pull` its streamed value
+                // f_i(x - c_i) (periodic), the pre-collision state of the next step
+                auto src = [&](int i, int ex, int ey, int ez) -> long long {
+                    if (!pull) return ((long long)Z * ny + Y) * nx + X;
+                    const int xs = (X - ex + nx) % nx, ys = (Y - ey + ny) % ny, zs = (Z - ez + nz) % nz;
+                    return ((long long)zs * ny + ys) * nx + xs;
+                };
+                double fv[Q];
                 double rr = 0, jx = 0, jy = 0, jz = 0;
                 static_for<Q>([&](auto I) {
                     constexpr int i = decltype(I)::value;
                     constexpr double w = weight_of(Q, i);
+                    const long long c = src(i, cx_of(Q, i), cy_of(Q, i), cz_of(Q, i));
                     double fi;
                     if constexpr (StoreTraits<S>::shifted)
                         fi = w + (double)load_g<S, float>(f + i * N + c, 0.0f);
                     else
                         fi = (double)f[i * N + c];
+                    fv[i] = fi;
                     acc[i] += fi;
                     rr += fi;
                     jx += cx_of(Q, i) * fi;
@@ -76,6 +89,14 @@ __global__ void filter_kernel(const S* f, int nx, int ny, int nz, int F, float* 
                     jz += cz_of(Q, i) * fi;
                 });
                 const double ux = jx / rr, uy = jy / rr, uz = jz / rr;
+                if (rescale) {
+                    double geq[Q];
+                    equilibrium_g<Q>(rr, ux, uy, uz, geq);
+                    static_for<Q>([&](auto I) {
+                        constexpr int i = decltype(I)::value;
+                        accn[i] += fv[i] - weight_of(Q, i) - geq[i];
+                    });
+                }
                 r += rr;
                 m[0] += jx;
                 m[1] += jy;
@@ -88,7 +109,7 @@ __global__ void filter_kernel(const S* f, int nx, int ny, int nz, int F, float* 
                 uu[5] += rr * uy * uz;
             }
     const double inv = 1.0 / ((double)F * F * F);
-    for (int i = 0; i < Q; ++i) fc[i * Nc + t] = (float)(acc[i] * inv);
+    for (int i = 0; i < Q; ++i) fc[i * Nc + t] = (float)((acc[i] + (neq_scale - 1.0) * accn[i]) * inv);
     r *= inv;
     for (int k = 0; k < 3; ++k) m[k] *= inv;
     const int A[6] = {0, 1, 2, 0, 0, 1}, B[6] = {0, 1, 2, 1, 2, 2};
@@ -142,8 +163,9 @@ __global__ void features_kernel(const float* f, int nx, int ny, int nz, float ta
     });
     const int A[6] = {0, 1, 2, 0, 0, 1}, B[6] = {0, 1, 2, 1, 2, 2};
     float* xr = x + c * 10;
+    double mneq[6];  // m_neq / rho
     for (int k = 0; k < 6; ++k)
-        xr[k] = (float)((P[k] - rho * ((double)u[A[k]] * u[B[k]] + (A[k] == B[k] ? kTheta : 0.0))) / rho);
+        mneq[k] = (P[k] - rho * ((double)u[A[k]] * u[B[k]] + (A[k] == B[k] ? kTheta : 0.0))) / rho;
     // S from the central differences of the neighbours' velocities, Eq. (fd)
     float du[3][3];
     const int xp = ix == nx - 1 ? 0 : ix + 1, xm = ix == 0 ? nx - 1 : ix - 1;
@@ -168,12 +190,15 @@ __global__ void features_kernel(const float* f, int nx, int ny, int nz, float ta
     const double det = Am[0][0] * (Am[1][1] * Am[2][2] - Am[1][2] * Am[2][1]) -
                        Am[0][1] * (Am[1][0] * Am[2][2] - Am[1][2] * Am[2][0]) +
                        Am[0][2] * (Am[1][0] * Am[2][1] - Am[1][1] * Am[2][0]);
+    // inputs 0-5: the KC-MP carrier (m_neq - m_CE)/rho (App. F.3), which is also
+    // the analytic KC-MP estimate of m_sgs / rho
+    for (int k = 0; k < 6; ++k) xr[k] = (float)(mneq[k] - Am[A[k]][B[k]]);
     xr[6] = (float)tr;
     xr[7] = (float)(0.5 * (tr * tr - tr2));
     xr[8] = (float)det;
     xr[9] = tau_hat;
-    if (kcmp)  // the analytic KC-MP estimate of m_sgs / rho: m_neq / rho - m_CE / rho (App. F.3)
-        for (int k = 0; k < 6; ++k) kcmp[c * 6 + k] = xr[k] - (float)Am[A[k]][B[k]];
+    if (kcmp)
+        for (int k = 0; k < 6; ++k) kcmp[c * 6 + k] = xr[k];
     if (msgs && tgt)
         for (int k = 0; k < 6; ++k) tgt[c * 6 + k] = msgs[k * N + c] / rho;
 }
@@ -500,9 +525,10 @@ int lbm_mlp_adamw(float* params, const float* grad, float* m, float* v, int step
     return e == cudaSuccess ? LBM_OK : set_last_error(LBM_ERR_CUDA, cudaGetErrorString(e));
 }
 
-int lbm_box_filter(const void* f_dev, int lattice, int storage, int nx, int ny, int nz, int factor, float* fc_dev,
-                   float* msgs_dev, void* stream)
+int lbm_box_filter(const void* f_dev, int lattice, int storage, int nx, int ny, int nz, int factor, double neq_scale,
+                   int pull, float* fc_dev, float* msgs_dev, void* stream)
 {
+    if (!(neq_scale > 0.0)) return set_last_error(LBM_ERR_ARG, "lbm_box_filter: neq_scale must be > 0");
     if (!f_dev || !fc_dev || !msgs_dev || factor < 1 || nx % factor || ny % factor || nz % factor)
         return set_last_error(LBM_ERR_ARG, "lbm_box_filter: sizes must be multiples of the factor");
     if (lattice != 19 && lattice != 27) return set_last_error(LBM_ERR_ARG, "lattice must be 19 or 27");
@@ -512,9 +538,11 @@ int lbm_box_filter(const void* f_dev, int lattice, int storage, int nx, int ny, 
     auto go = [&](auto tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
         if (lattice == 27)
-            filter_kernel<27, S><<<g, 128, 0, s>>>(static_cast<const S*>(f_dev), nx, ny, nz, factor, fc_dev, msgs_dev);
+            filter_kernel<27, S><<<g, 128, 0, s>>>(static_cast<const S*>(f_dev), nx, ny, nz, factor, neq_scale, pull,
+                                                   fc_dev, msgs_dev);
         else
-            filter_kernel<19, S><<<g, 128, 0, s>>>(static_cast<const S*>(f_dev), nx, ny, nz, factor, fc_dev, msgs_dev);
+            filter_kernel<19, S><<<g, 128, 0, s>>>(static_cast<const S*>(f_dev), nx, ny, nz, factor, neq_scale, pull,
+                                                   fc_dev, msgs_dev);
     };
     switch (storage) {
     case LBM_FP64: go((double*)nullptr); break;

@@ -556,7 +556,7 @@ constexpr size_t step_smem_bytes()
            (CL == CL_LEARNED ? (size_t)(MlpLayout::BYTES + TY * MlpLayout::XCH_BYTES) : 0);
 }
 
-// network inputs of one cell (the learned closure's 10 inputs: m_neq/rho,
+// network inputs of one cell (the learned closure's 10 inputs: (m_neq - m_CE)/rho,
 // invariants of m_CE/rho, tau_hat), standardised, into the warp's exchange row;
 // network forward for the warp; the cell's m_sgs back (times rho)
 // The populations are read from the shared-memory stash (stride NT) rather
@@ -587,15 +587,16 @@ __device__ __forceinline__ void learned_msgs(const R* st, R drho, R ux, R uy, R 
             if (cy * cz == -1) pyz -= gi;
         }
     });
-    R x[10];
-    x[0] = (pxx - rho * ux * ux - th * drho) * irho;
-    x[1] = (pyy - rho * uy * uy - th * drho) * irho;
-    x[2] = (pzz - rho * uz * uz - th * drho) * irho;
-    x[3] = (pxy - rho * ux * uy) * irho;
-    x[4] = (pxz - rho * ux * uz) * irho;
-    x[5] = (pyz - rho * uy * uz) * irho;
     const R k = R(-2) * th * tau_hat;  // m_CE / rho = k S
     const R a00 = k * Sxx, a11 = k * Syy, a22 = k * Szz, a01 = k * Sxy, a02 = k * Sxz, a12 = k * Syz;
+    // inputs 0-5: the KC-MP carrier (m_neq - m_CE)/rho, m_neq = Pi' - rho u u - theta drho I
+    R x[10];
+    x[0] = (pxx - rho * ux * ux - th * drho) * irho - a00;
+    x[1] = (pyy - rho * uy * uy - th * drho) * irho - a11;
+    x[2] = (pzz - rho * uz * uz - th * drho) * irho - a22;
+    x[3] = (pxy - rho * ux * uy) * irho - a01;
+    x[4] = (pxz - rho * ux * uz) * irho - a02;
+    x[5] = (pyz - rho * uy * uz) * irho - a12;
     const R tr = a00 + a11 + a22;
     const R tr2 = a00 * a00 + a11 * a11 + a22 * a22 + R(2) * (a01 * a01 + a02 * a02 + a12 * a12);
     x[6] = tr;

@@ -98,7 +98,7 @@ def _load() -> ctypes.CDLL:
     lib.lbm_mlp_grad.argtypes = [vp, vp, vp, ctypes.c_int, vp, vp, dp, vp]
     lib.lbm_mlp_adamw.argtypes = [vp, vp, vp, vp, ctypes.c_int, fl, fl, fl, fl, fl, vp]
     lib.lbm_box_filter.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                   ctypes.c_int, vp, vp, vp]
+                                   ctypes.c_int, ctypes.c_double, ctypes.c_int, vp, vp, vp]
     lib.lbm_closure_features.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_double, vp, vp, vp, vp, vp]
     lib.lbm_set_learned_closure.argtypes = [H, P(ctypes.c_float), P(ctypes.c_float)]
@@ -261,9 +261,11 @@ def lbm_mlp_adamw(params, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8
                              float(beta2), float(eps), float(weight_decay), _vp(_stream_handle(stream))))
 
 
-def lbm_box_filter(f_ptr, lattice, storage, nx, ny, nz, factor, fc_ptr, msgs_ptr, stream=None) -> None:
+def lbm_box_filter(f_ptr, lattice, storage, nx, ny, nz, factor, fc_ptr, msgs_ptr, stream=None,
+                   neq_scale: float = 1.0, pull: bool = False) -> None:
     _check(LIB.lbm_box_filter(_vp(f_ptr), int(lattice), int(storage), int(nx), int(ny), int(nz), int(factor),
-                              _vp(fc_ptr), _vp(msgs_ptr), _vp(_stream_handle(stream))))
+                              float(neq_scale), int(bool(pull)), _vp(fc_ptr), _vp(msgs_ptr),
+                              _vp(_stream_handle(stream))))
 
 
 def lbm_closure_features(f_ptr, lattice, nx, ny, nz, nu, msgs_ptr, x_ptr, t_ptr, kcmp_ptr=0, stream=None) -> None:

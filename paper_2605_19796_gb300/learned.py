@@ -29,9 +29,16 @@ import torch
 from . import inputs, lbm
 
 
-def snapshot_features(s: lbm.Solver, factor: int, nu_coarse: float):
+def snapshot_features(s: lbm.Solver, factor: int, nu_coarse: float, nu_fine: float = None, pull: bool = True):
     """Box-filtered coarse state of a solver's current populations:
-    (x [N,10], targets [N,6], analytic KC-MP estimate [N,6], coarse populations [q,nz,ny,nx])."""
+    (x [N,10], targets [N,6], analytic KC-MP estimate [N,6], coarse populations [q,nz,ny,nx]).
+
+    pull: filter the streamed (pre-collision) populations, the state from which
+    a step computes the closure inputs (features and targets); without it, the
+    stored post-collision populations (an initial state for a coarse run).
+    With nu_fine given, the filtered fine non-equilibrium part is rescaled by
+    r = F tau_hat_c / tau_hat_f to the size the coarse lattice gives the same
+    flow under acoustic scaling (the SGS part is kept)."""
     ptr, _ = s.population_buffer()
     nx, ny, nz = s.shape
     q = s.q
@@ -40,7 +47,12 @@ def snapshot_features(s: lbm.Solver, factor: int, nu_coarse: float):
     dev = torch.device("cuda")
     fc = torch.empty((q, ncz, ncy, ncx), dtype=torch.float32, device=dev)
     ms = torch.empty((6, ncz, ncy, ncx), dtype=torch.float32, device=dev)
-    lbm.lbm_box_filter(ptr, q, s.cfg.storage, nx, ny, nz, factor, fc.data_ptr(), ms.data_ptr())
+    r = 1.0
+    if nu_fine is not None:
+        th = 1.0 / 3.0
+        r = factor * (nu_coarse / th + 0.5) / (nu_fine / th + 0.5)
+    lbm.lbm_box_filter(ptr, q, s.cfg.storage, nx, ny, nz, factor, fc.data_ptr(), ms.data_ptr(), neq_scale=r,
+                       pull=pull)
     x = torch.empty((nc, 10), dtype=torch.float32, device=dev)
     t = torch.empty((nc, 6), dtype=torch.float32, device=dev)
     kc = torch.empty((nc, 6), dtype=torch.float32, device=dev)
@@ -66,7 +78,7 @@ def generate(n_fine: int = 512, factor: int = 4, seeds: Sequence[int] = (0, 1, 2
                 for st in snap_steps:
                     s.step(st - done)
                     done = st
-                    x, t, kc, _ = snapshot_features(s, factor, nu_fine / factor)
+                    x, t, kc, _ = snapshot_features(s, factor, nu_fine / factor, nu_fine)
                     n = x.shape[0]
                     idx = torch.randperm(n, generator=gen, device="cuda")[: max(1, int(keep * n))]
                     X.append(x[idx])
@@ -197,10 +209,10 @@ def a_posteriori(params, stats, n_fine: int = 512, factor: int = 4, k0: float = 
         fine.init_velocity_device(rho, u)
         del rho, u
         fine.step(t0)
-        _, _, _, fc0 = snapshot_features(fine, factor, nu_c)
+        _, _, _, fc0 = snapshot_features(fine, factor, nu_c, nu_fine, pull=False)
         f0 = fc0.double().cpu().numpy()
         fine.step(factor * coarse_steps)
-        _, _, _, fc1 = snapshot_features(fine, factor, nu_c)
+        _, _, _, fc1 = snapshot_features(fine, factor, nu_c, nu_fine, pull=False)
     ref = _coarse_velocity(fc1, nu_c)
     e_ref = spectrum(ref)
     ek_ref = float(0.5 * (ref ** 2).sum(0).mean())

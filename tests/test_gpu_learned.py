@@ -102,6 +102,21 @@ def test_box_filter_and_features(env, orc, q):
     torch.cuda.synchronize()
     assert np.abs(fc.cpu().numpy() - fb_ref).max() <= 1e-7
     assert np.abs(ms.cpu().numpy() - msgs_ref).max() <= 1e-5 * np.abs(msgs_ref).max()
+    # consistent coarse state: the fine non-equilibrium part rescaled by r
+    fb_r, _ = cd.filtered_state(f, 4, neq_scale=3.7)
+    lbm.lbm_box_filter(fd.data_ptr(), q, lbm.LBM_FP64, 16, 8, 12, 4, fc.data_ptr(), ms.data_ptr(), neq_scale=3.7)
+    torch.cuda.synchronize()
+    assert np.abs(fc.cpu().numpy() - fb_r).max() <= 1e-7
+    assert np.abs(fb_r - fb_ref).max() > 1e-5, "the rescaling must act on this state"
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_box_filter(fd.data_ptr(), q, lbm.LBM_FP64, 16, 8, 12, 4, fc.data_ptr(), ms.data_ptr(), neq_scale=0.0)
+    # the streamed (pre-collision) state, rescaled
+    fb_p, ms_p = cd.filtered_state(f, 4, neq_scale=3.7, pull=True)
+    lbm.lbm_box_filter(fd.data_ptr(), q, lbm.LBM_FP64, 16, 8, 12, 4, fc.data_ptr(), ms.data_ptr(), neq_scale=3.7,
+                       pull=True)
+    torch.cuda.synchronize()
+    assert np.abs(fc.cpu().numpy() - fb_p).max() <= 1e-7
+    assert np.abs(ms.cpu().numpy() - ms_p).max() <= 1e-5 * np.abs(ms_p).max()
     # features of a coarse-sized state (use the fine field itself as a periodic lattice)
     f32 = torch.as_tensor(f.astype(np.float32), device="cuda")
     N = 16 * 8 * 12

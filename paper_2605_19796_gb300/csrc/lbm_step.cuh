@@ -190,21 +190,45 @@ __device__ __forceinline__ void pull(const S* __restrict__ fin, long long ps, co
 // drho = sum g (rho = 1 + drho), j = sum g c (sum w c = 0), u = (j + F/2)/rho.
 // drho is returned unrounded: the equilibrium uses it directly so that
 // sum_i g_eq,i = drho holds to rounding of small quantities (no O(1) term).
+// D3Q27 sums over the x-triples: populations i = 3t, 3t+1, 3t+2 share
+// (c_y, c_z) with t = 3(c_z + 1) + (c_y + 1) and have c_x = -1, 0, +1;
+// s_t = their sum, dx_t = g(+1) - g(-1).
+template <typename R>
+__device__ __forceinline__ void triples27(const R (&g)[27], R (&s)[9], R (&dx)[9])
+{
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+        s[t] = (g[3 * t] + g[3 * t + 1]) + g[3 * t + 2];
+        dx[t] = g[3 * t + 2] - g[3 * t];
+    }
+}
+
 template <int Q, typename R>
 __device__ __forceinline__ void moments(const R (&g)[Q], R& drho, R& ux, R& uy, R& uz, R Fx, R Fy, R Fz)
 {
     R d = 0, jx = 0, jy = 0, jz = 0;
-    static_for<Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
-        d += g[i];
-        if (cx == 1) jx += g[i];
-        if (cx == -1) jx -= g[i];
-        if (cy == 1) jy += g[i];
-        if (cy == -1) jy -= g[i];
-        if (cz == 1) jz += g[i];
-        if (cz == -1) jz -= g[i];
-    });
+    if constexpr (Q == 27) {
+        R s[9], dx[9];
+        triples27<R>(g, s, dx);
+        const R sym = (s[0] + s[3]) + s[6], sy0 = (s[1] + s[4]) + s[7], syp = (s[2] + s[5]) + s[8];
+        const R szm = (s[0] + s[1]) + s[2], szp = (s[6] + s[7]) + s[8];
+        d = (sym + sy0) + syp;
+        jy = syp - sym;
+        jz = szp - szm;
+        jx = (((dx[0] + dx[1]) + (dx[2] + dx[3])) + ((dx[4] + dx[5]) + (dx[6] + dx[7]))) + dx[8];
+    } else {
+        static_for<Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
+            d += g[i];
+            if (cx == 1) jx += g[i];
+            if (cx == -1) jx -= g[i];
+            if (cy == 1) jy += g[i];
+            if (cy == -1) jy -= g[i];
+            if (cz == 1) jz += g[i];
+            if (cz == -1) jz -= g[i];
+        });
+    }
     drho = d;
     const R inv = R(1) / (R(1) + d);
     ux = (jx + R(0.5) * Fx) * inv;
@@ -420,19 +444,33 @@ __device__ __forceinline__ void collide(R (&g)[Q], R drho, R ux, R uy, R uz, R S
     } else if constexpr (CL != CL_BGK) {
         // second moments of g: Pi'_ab = sum g c_a c_b = Pi_ab - theta delta_ab
         R pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
-        static_for<Q>([&](auto I) {
-            constexpr int i = decltype(I)::value;
-            constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
-            if (cx != 0) pxx += g[i];
-            if (cy != 0) pyy += g[i];
-            if (cz != 0) pzz += g[i];
-            if (cx * cy == 1) pxy += g[i];
-            if (cx * cy == -1) pxy -= g[i];
-            if (cx * cz == 1) pxz += g[i];
-            if (cx * cz == -1) pxz -= g[i];
-            if (cy * cz == 1) pyz += g[i];
-            if (cy * cz == -1) pyz -= g[i];
-        });
+        if constexpr (Q == 27) {
+            // from the x-triple sums (triples27): c_x^2 = 1 except the middle
+            // member, c_x c_y and c_x c_z from dx, c_y c_z from s
+            R s[9], dx[9];
+            triples27<R>(g, s, dx);
+            const R g0 = (((g[1] + g[4]) + (g[7] + g[10])) + ((g[13] + g[16]) + (g[19] + g[22]))) + g[25];
+            pxx = drho - g0;
+            pyy = ((s[0] + s[3]) + s[6]) + ((s[2] + s[5]) + s[8]);
+            pzz = ((s[0] + s[1]) + s[2]) + ((s[6] + s[7]) + s[8]);
+            pxy = ((dx[2] + dx[5]) + dx[8]) - ((dx[0] + dx[3]) + dx[6]);
+            pxz = ((dx[6] + dx[7]) + dx[8]) - ((dx[0] + dx[1]) + dx[2]);
+            pyz = (s[0] + s[8]) - (s[2] + s[6]);
+        } else {
+            static_for<Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
+                if (cx != 0) pxx += g[i];
+                if (cy != 0) pyy += g[i];
+                if (cz != 0) pzz += g[i];
+                if (cx * cy == 1) pxy += g[i];
+                if (cx * cy == -1) pxy -= g[i];
+                if (cx * cz == 1) pxz += g[i];
+                if (cx * cz == -1) pxz -= g[i];
+                if (cy * cz == 1) pyz += g[i];
+                if (cy * cz == -1) pyz -= g[i];
+            });
+        }
         if constexpr (CL == CL_KCMP) {
             // m_neq = Pi - rho(uu + theta I) = Pi' - rho uu - theta drho I   (App. F.3)
             // m_CE = -2 rho theta tau_hat S;  m_sgs = m_neq - m_CE

@@ -198,10 +198,10 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
             collide<Q, R, CL, FORCE>(g, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, omega, tau_hat, nu, cnud, Fx,
                                      Fy, Fz);
             if (own_store) {
-                S* dst = fout + (z * plane + own.yr[1] + own.xs[1]);
+                const int cell = z * plane + own.yr[1] + own.xs[1];
                 static_for<Q>([&](auto I) {
                     constexpr int i = decltype(I)::value;
-                    store_g<S, R>(dst + (long long)i * ps, g[i], (R)weight_of(Q, i));
+                    store_g<S, R>(fout + ((long long)i * ps + cell), g[i], (R)weight_of(Q, i));
                 });
             }
         }

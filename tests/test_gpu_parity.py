@@ -307,7 +307,7 @@ def test_autotune_keeps_state_and_result(lbm, orc):
         s.step(2)
         before = s.get_populations()
         cfg = s.autotune(trials=2)
-        assert cfg["variant"] in (1, 2, 3) and cfg["tile_y"] in (4, 8, 16) and 1 <= cfg["zchunk"] <= 128
+        assert 1 <= cfg["variant"] <= 10 and cfg["tile_y"] in (4, 8, 16) and 1 <= cfg["zchunk"] <= 128
         assert np.array_equal(before, s.get_populations())
         s.step(5)
         tuned = s.get_populations()

@@ -102,20 +102,14 @@ typedef struct {
     int zchunk;         /* tuning: z-planes per CTA march (0 = library default)      */
     int variant;        /* tuning: step-kernel variant, 0 = library default
                            (8 for D3Q27 with KC-MP or KC-RB, else 1),
-                           1 = register pull, 2 = asynchronous-copy pipeline
-                           (FP32 storage, periodic boxes), 3 = register pull
-                           sized for three CTAs per SM (32-bit arithmetic,
-                           periodic, BGK/KC-MP, tile_y 8), 4 = TMA-staged
-                           pipeline (FP32, periodic, nx % 32 == 0 and
-                           ny % tile_y == 0), 5 = register pull with the
-                           loads issued two planes ahead, 6 / 7 = register pull
-                           without the population stash (re-pulled for the
-                           collision; three / four CTAs per SM, 32-bit
-                           arithmetic), 8 = register pull with a split
-                           arrive/wait barrier, 9 = two cells per thread on
-                           packed FP32 pairs (32-bit arithmetic), 10 = 9
-                           without the stash (periodic) (5-10: BGK, KC-MP,
-                           KC-RB)                                            */
+                           1 = register pull (every lattice, storage, closure
+                           and boundary), 4 = TMA-staged pipeline (FP32,
+                           periodic, BGK/KC-MP/KC-RB, nx % 32 == 0 and
+                           ny % tile_y == 0), 8 = register pull with a split
+                           arrive/wait barrier (BGK, KC-MP, KC-RB), 9 = two
+                           cells per thread on packed FP32 pairs (32-bit
+                           arithmetic, BGK, KC-MP, KC-RB); other values:
+                           LBM_ERR_ARG                                          */
     int disable_graphs; /* nonzero: lbm_step launches kernels one by one instead of
                            replaying a captured CUDA graph                        */
 } lbm_config;

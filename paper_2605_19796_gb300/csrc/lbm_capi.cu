@@ -308,7 +308,9 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
     if (has_force && bc_kind != BC_WALLS_Y)
         return fail(LBM_ERR_UNSUPPORTED, "a body force is supported with bounce-back walls (channel) only");
     int tile_y = cfg->tile_y ? cfg->tile_y : 8;
-    if (cfg->variant < VAR_DEFAULT || cfg->variant > VAR_PAIR_REPULL) return fail(LBM_ERR_ARG, "unknown kernel variant");
+    if (cfg->variant != VAR_DEFAULT && cfg->variant != VAR_REGISTER && cfg->variant != VAR_TMA && cfg->variant != VAR_SPLIT &&
+        cfg->variant != VAR_PAIR)
+        return fail(LBM_ERR_ARG, "unknown kernel variant");
     int variant = cfg->variant;
     // measured defaults: the split-barrier pull for D3Q27 with a closure carrier
     // (KC-MP, KC-RB), the register pull elsewhere; lbm_autotune may pick another
@@ -470,8 +472,7 @@ int lbm_autotune(lbm_handle* h, int trials)
 {
     if (int rc = check_handle(h)) return rc;
     if (trials < 1) trials = 3;
-    static const int kVariants[] = {VAR_REGISTER, VAR_SPLIT, VAR_PAIR, VAR_PAIR_REPULL, VAR_REPULL, VAR_REPULL_OCC4, VAR_PREFETCH,
-                                    VAR_REGISTER_OCC3, VAR_ASYNC, VAR_TMA};
+    static const int kVariants[] = {VAR_REGISTER, VAR_SPLIT, VAR_PAIR, VAR_TMA};
     static const int kTiles[] = {4, 8, 16};
     static const int kChunks[] = {8, 16, 32, 64, 128};
     const int v0 = h->variant, t0 = h->tile_y, z0 = h->zchunk;

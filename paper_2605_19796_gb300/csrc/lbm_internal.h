@@ -35,12 +35,11 @@ struct StepArgs {
 size_t mlp_packed_bytes();
 void mlp_pack(const float* params, const float* stats, unsigned char* out);
 
-// Step-kernel variants: register pull (lbm_step.cuh), asynchronous-copy
-// pipeline (lbm_step_async.cuh, FP32 storage, periodic boxes) and the register
-// pull with its register budget sized for three CTAs per SM (32-bit arithmetic).
-enum Variant { VAR_DEFAULT = 0, VAR_REGISTER = 1, VAR_ASYNC = 2, VAR_REGISTER_OCC3 = 3, VAR_TMA = 4, VAR_PREFETCH = 5,
-               VAR_REPULL = 6, VAR_REPULL_OCC4 = 7, VAR_SPLIT = 8,
-               VAR_PAIR = 9, VAR_PAIR_REPULL = 10 };
+// Step-kernel variants: register pull (lbm_step.cuh), TMA staging
+// (lbm_step_tma.cuh), split arrive/wait barrier (lbm_step_split.cuh), two cells
+// per thread on packed FP32 pairs (lbm_step_x2.cuh).  Values 2, 3, 5, 6, 7, 10
+// and 11 belonged to measured alternatives that were retired; they are refused.
+enum Variant { VAR_DEFAULT = 0, VAR_REGISTER = 1, VAR_TMA = 4, VAR_SPLIT = 8, VAR_PAIR = 9 };
 
 // TMA variant: tile heights it is built for, and the tensor map of a population
 // buffer (4D: x, y, z, population-of-box; box 40 x (tile_y + 2) x 1 x 1)

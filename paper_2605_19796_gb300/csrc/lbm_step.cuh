@@ -406,114 +406,141 @@ __device__ __forceinline__ void collide_kcrr(R (&g)[27], R drho, R ux, R uy, R u
 // P - 1 = e_x + Y + e_x Y, Y = e_y + e_z + e_y e_z (the product equilibrium in
 // its small per-axis terms, so FP32 rounds without bias); Y and the parts of H
 // depend only on (c_y, c_z) and are formed once per pair.
-template <int Q, typename R, int CL, bool FORCE>
-__device__ __forceinline__ void collide(R (&g)[Q], R drho, R ux, R uy, R uz, R Sxx, R Syy, R Szz, R Sxy, R Sxz,
-                                        R Syz, R omega, R tau_hat, R nu, R cnud, R Fx, R Fy, R Fz,
-                                        const R* msgs_in = nullptr)
+// Second moments Pi'_ab = sum_i g_i c_ia c_ib = Pi_ab - theta delta_ab of the
+// shifted populations (xx yy zz xy xz yz); drho = sum g.
+template <int Q, typename R>
+__device__ __forceinline__ void second_moments(const R (&g)[Q], R drho, R (&P)[6])
 {
-    if constexpr (CL == CL_KCRR) {
-        static_assert(Q == 27, "KC-RR is defined on D3Q27 only");
-        static_assert(!FORCE, "KC-RR is built for periodic boxes");
-        collide_kcrr<R>(g, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, omega, tau_hat, nu, cnud);
-        return;
+    R pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+    if constexpr (Q == 27) {
+        // from the x-triple sums (triples27): c_x^2 = 1 except the middle
+        // member, c_x c_y and c_x c_z from dx, c_y c_z from s
+        R s[9], dx[9];
+        triples27<R>(g, s, dx);
+        const R g0 = (((g[1] + g[4]) + (g[7] + g[10])) + ((g[13] + g[16]) + (g[19] + g[22]))) + g[25];
+        pxx = drho - g0;
+        pyy = ((s[0] + s[3]) + s[6]) + ((s[2] + s[5]) + s[8]);
+        pzz = ((s[0] + s[1]) + s[2]) + ((s[6] + s[7]) + s[8]);
+        pxy = ((dx[2] + dx[5]) + dx[8]) - ((dx[0] + dx[3]) + dx[6]);
+        pxz = ((dx[6] + dx[7]) + dx[8]) - ((dx[0] + dx[1]) + dx[2]);
+        pyz = (s[0] + s[8]) - (s[2] + s[6]);
     } else {
+        static_for<Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
+            if (cx != 0) pxx += g[i];
+            if (cy != 0) pyy += g[i];
+            if (cz != 0) pzz += g[i];
+            if (cx * cy == 1) pxy += g[i];
+            if (cx * cy == -1) pxy -= g[i];
+            if (cx * cz == 1) pxz += g[i];
+            if (cx * cz == -1) pxz -= g[i];
+            if (cy * cz == 1) pyz += g[i];
+            if (cy * cz == -1) pyz -= g[i];
+        });
+    }
+    P[0] = pxx;
+    P[1] = pyy;
+    P[2] = pzz;
+    P[3] = pxy;
+    P[4] = pxz;
+    P[5] = pyz;
+}
+
+// Relaxation coefficients of the common collision form (see collide below).
+template <typename R>
+struct Coef {
+    R ca, cb, c0, D, t, Mxx, Myy, Mzz, Mxy, Mxz, Myz;
+};
+
+// The per-cell part of the collision: closure carrier, SGS trace, rate (Eq.
+// omega_sgs_operational) and the coefficients; P holds the second moments
+// (unused for BGK and the learned closure, which takes msgs_in).
+template <int Q, typename R, int CL>
+__device__ __forceinline__ Coef<R> collide_coef(const R (&P)[6], R drho, R ux, R uy, R uz, R Sxx, R Syy, R Szz,
+                                                R Sxy, R Sxz, R Syz, R omega, R tau_hat, R nu, R cnud,
+                                                const R* msgs_in = nullptr)
+{
     constexpr R th = R(kTheta);
     const R rho = R(1) + drho;
+    Coef<R> k;
+    k.Mxx = k.Myy = k.Mzz = k.Mxy = k.Mxz = k.Myz = k.t = R(0);
+    k.ca = R(1) - omega;
+    k.cb = omega * rho;
+    k.c0 = omega * drho;
+    k.D = R(0);
+    if constexpr (CL == CL_LEARNED) {
+        // learned closure: the network's m_sgs replaces m_neq - m_CE; the rate and
+        // the relaxation are KC-MP's (App. F.3 with the learned SGS moment)
+        k.Mxx = msgs_in[0];
+        k.Myy = msgs_in[1];
+        k.Mzz = msgs_in[2];
+        k.Mxy = msgs_in[3];
+        k.Mxz = msgs_in[4];
+        k.Myz = msgs_in[5];
+        const R tr = k.Mxx + k.Myy + k.Mzz;
+        const R omega_s = omega_sgs(tr, nu, omega, cnud);
+        k.t = th * tr;
+        k.D = (omega - omega_s) * R(1.0 / (2.0 * kTheta * kTheta));
+    } else if constexpr (CL == CL_KCMP) {
+        // m_neq = Pi - rho(uu + theta I) = Pi' - rho uu - theta drho I   (App. F.3)
+        // m_CE = -2 rho theta tau_hat S;  m_sgs = m_neq - m_CE
+        const R rt = R(-2) * rho * th * tau_hat;
+        k.Mxx = P[0] - rho * (ux * ux) - th * drho - rt * Sxx;
+        k.Myy = P[1] - rho * (uy * uy) - th * drho - rt * Syy;
+        k.Mzz = P[2] - rho * (uz * uz) - th * drho - rt * Szz;
+        k.Mxy = P[3] - rho * ux * uy - rt * Sxy;
+        k.Mxz = P[4] - rho * ux * uz - rt * Sxz;
+        k.Myz = P[5] - rho * uy * uz - rt * Syz;
+        const R tr = k.Mxx + k.Myy + k.Mzz;
+        const R omega_s = omega_sgs(tr, nu, omega, cnud);
+        k.t = th * tr;
+        k.D = (omega - omega_s) * R(1.0 / (2.0 * kTheta * kTheta));
+    } else if constexpr (CL == CL_KCRB_H || CL == CL_KCRB_RAW) {
+        // KC-RB, Hermite or raw first-order reconstruction (App. F.2)
+        constexpr bool herm = (CL == CL_KCRB_H);
+        const R usq = ux * ux + uy * uy + uz * uz;
+        const R trS = Sxx + Syy + Szz;
+        // sum_i f1_i |c_i|^2 = -2 rho tau_hat theta trS (Hermite), -5 rho tau_hat theta trS (raw)
+        const R trf1 = R(herm ? -2 : -5) * rho * tau_hat * th * trS;
+        // tr m_sgs = sum (f - f0 - f1)|c|^2 = tr Pi' - rho |u|^2 - 3 theta drho - tr f1
+        const R tr = (P[0] + P[1] + P[2]) - rho * usq - R(3) * th * drho - trf1;
+        const R omega_s = omega_sgs(tr, nu, omega, cnud);
+        k.Mxx = Sxx;
+        k.Myy = Syy;
+        k.Mzz = Szz;
+        k.Mxy = Sxy;
+        k.Mxz = Sxz;
+        k.Myz = Syz;
+        k.t = herm ? th * trS : R(0);
+        k.ca = R(1) - omega_s;
+        k.cb = omega_s * rho;
+        k.c0 = omega_s * drho;
+        k.D = (omega_s - omega) * (-rho * tau_hat * R(1.0 / kTheta));
+    }
+    return k;
+}
+
+// The per-population part of the collision for the populations [LO, HI) of
+// one cell (g holds them at 0 .. HI-LO-1), plus the Guo source with a force.
+template <int Q, typename R, int CL, bool FORCE, int LO, int HI, int N>
+__device__ __forceinline__ void relax(R (&g)[N], const Coef<R>& k, R ux, R uy, R uz, R omega, R Fx, R Fy, R Fz)
+{
+    static_assert(N >= HI - LO, "populations array too short");
     constexpr R a1 = R(1.0 / kTheta);                                // c u / theta
     constexpr R a2 = R((1.0 - kTheta) / (2.0 * kTheta * kTheta));    // (1 - theta) u^2 / (2 theta^2)
     constexpr R a0 = R(-kTheta / (2.0 * kTheta * kTheta));           // -theta u^2 / (2 theta^2)
     const R ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
     const R usq = ux2 + uy2 + uz2;
-
-    // quadratic form H(c) = sum c_a c_b M_ab - t and the relaxation coefficients
-    R Mxx = 0, Myy = 0, Mzz = 0, Mxy = 0, Mxz = 0, Myz = 0, t = 0;
-    R ca = R(1) - omega, cb = omega * rho, c0 = omega * drho, D = 0;
-    if constexpr (CL == CL_LEARNED) {
-        // learned closure: the network's m_sgs replaces m_neq - m_CE; the rate and
-        // the relaxation are KC-MP's (App. F.3 with the learned SGS moment)
-        Mxx = msgs_in[0];
-        Myy = msgs_in[1];
-        Mzz = msgs_in[2];
-        Mxy = msgs_in[3];
-        Mxz = msgs_in[4];
-        Myz = msgs_in[5];
-        const R tr = Mxx + Myy + Mzz;
-        const R omega_s = omega_sgs(tr, nu, omega, cnud);
-        t = th * tr;
-        D = (omega - omega_s) * R(1.0 / (2.0 * kTheta * kTheta));
-    } else if constexpr (CL != CL_BGK) {
-        // second moments of g: Pi'_ab = sum g c_a c_b = Pi_ab - theta delta_ab
-        R pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
-        if constexpr (Q == 27) {
-            // from the x-triple sums (triples27): c_x^2 = 1 except the middle
-            // member, c_x c_y and c_x c_z from dx, c_y c_z from s
-            R s[9], dx[9];
-            triples27<R>(g, s, dx);
-            const R g0 = (((g[1] + g[4]) + (g[7] + g[10])) + ((g[13] + g[16]) + (g[19] + g[22]))) + g[25];
-            pxx = drho - g0;
-            pyy = ((s[0] + s[3]) + s[6]) + ((s[2] + s[5]) + s[8]);
-            pzz = ((s[0] + s[1]) + s[2]) + ((s[6] + s[7]) + s[8]);
-            pxy = ((dx[2] + dx[5]) + dx[8]) - ((dx[0] + dx[3]) + dx[6]);
-            pxz = ((dx[6] + dx[7]) + dx[8]) - ((dx[0] + dx[1]) + dx[2]);
-            pyz = (s[0] + s[8]) - (s[2] + s[6]);
-        } else {
-            static_for<Q>([&](auto I) {
-                constexpr int i = decltype(I)::value;
-                constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
-                if (cx != 0) pxx += g[i];
-                if (cy != 0) pyy += g[i];
-                if (cz != 0) pzz += g[i];
-                if (cx * cy == 1) pxy += g[i];
-                if (cx * cy == -1) pxy -= g[i];
-                if (cx * cz == 1) pxz += g[i];
-                if (cx * cz == -1) pxz -= g[i];
-                if (cy * cz == 1) pyz += g[i];
-                if (cy * cz == -1) pyz -= g[i];
-            });
-        }
-        if constexpr (CL == CL_KCMP) {
-            // m_neq = Pi - rho(uu + theta I) = Pi' - rho uu - theta drho I   (App. F.3)
-            // m_CE = -2 rho theta tau_hat S;  m_sgs = m_neq - m_CE
-            const R rt = R(-2) * rho * th * tau_hat;
-            Mxx = pxx - rho * ux2 - th * drho - rt * Sxx;
-            Myy = pyy - rho * uy2 - th * drho - rt * Syy;
-            Mzz = pzz - rho * uz2 - th * drho - rt * Szz;
-            Mxy = pxy - rho * ux * uy - rt * Sxy;
-            Mxz = pxz - rho * ux * uz - rt * Sxz;
-            Myz = pyz - rho * uy * uz - rt * Syz;
-            const R tr = Mxx + Myy + Mzz;
-            const R omega_s = omega_sgs(tr, nu, omega, cnud);
-            t = th * tr;
-            D = (omega - omega_s) * R(1.0 / (2.0 * kTheta * kTheta));
-        } else {  // KC-RB, Hermite or raw first-order reconstruction (App. F.2)
-            constexpr bool herm = (CL == CL_KCRB_H);
-            const R trS = Sxx + Syy + Szz;
-            // sum_i f1_i |c_i|^2 = -2 rho tau_hat theta trS (Hermite), -5 rho tau_hat theta trS (raw)
-            const R trf1 = R(herm ? -2 : -5) * rho * tau_hat * th * trS;
-            // tr m_sgs = sum (f - f0 - f1)|c|^2 = tr Pi' - rho |u|^2 - 3 theta drho - tr f1
-            const R tr = (pxx + pyy + pzz) - rho * usq - R(3) * th * drho - trf1;
-            const R omega_s = omega_sgs(tr, nu, omega, cnud);
-            Mxx = Sxx;
-            Myy = Syy;
-            Mzz = Szz;
-            Mxy = Sxy;
-            Mxz = Sxz;
-            Myz = Syz;
-            t = herm ? th * trS : R(0);
-            ca = R(1) - omega_s;
-            cb = omega_s * rho;
-            c0 = omega_s * drho;
-            D = (omega_s - omega) * (-rho * tau_hat * R(1.0 / kTheta));
-        }
-    }
-
+    const R ca = k.ca, cb = k.cb, c0 = k.c0, D = k.D, t = k.t;
+    const R Mxx = k.Mxx, Myy = k.Myy, Mzz = k.Mzz, Mxy = k.Mxy, Mxz = k.Mxz, Myz = k.Myz;
     if constexpr (Q == 27) {
         // per-axis equilibrium terms e(c) and the (c_y, c_z) parts
         const R ex[3] = {-a1 * ux + a2 * ux2, a0 * ux2, a1 * ux + a2 * ux2};
         const R ey[3] = {-a1 * uy + a2 * uy2, a0 * uy2, a1 * uy + a2 * uy2};
         const R ez[3] = {-a1 * uz + a2 * uz2, a0 * uz2, a1 * uz + a2 * uz2};
-        static_for<Q>([&](auto I) {
-            constexpr int i = decltype(I)::value;
+        static_for<HI - LO>([&](auto I) {
+            constexpr int i = LO + decltype(I)::value;
             constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
             constexpr R w = R(weight_of(Q, i));
             const R Y = ey[cy + 1] + ez[cz + 1] + ey[cy + 1] * ez[cz + 1];
@@ -527,11 +554,11 @@ __device__ __forceinline__ void collide(R (&g)[Q], R drho, R ux, R uy, R uz, R S
                 if (cx != 0) h += Mxx + R(2 * cx) * (R(cy) * Mxy + R(cz) * Mxz);
                 K += D * h;
             }
-            g[i] = ca * g[i] + w * K;
+            g[i - LO] = ca * g[i - LO] + w * K;
         });
     } else {
-        static_for<Q>([&](auto I) {
-            constexpr int i = decltype(I)::value;
+        static_for<HI - LO>([&](auto I) {
+            constexpr int i = LO + decltype(I)::value;
             constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
             constexpr R w = R(weight_of(Q, i));
             const R cu = R(cx) * ux + R(cy) * uy + R(cz) * uz;
@@ -548,22 +575,56 @@ __device__ __forceinline__ void collide(R (&g)[Q], R drho, R ux, R uy, R uz, R S
                 if (cy * cz != 0) h += R(2 * cy * cz) * Myz;
                 K += D * h;
             }
-            g[i] = ca * g[i] + w * K;
+            g[i - LO] = ca * g[i - LO] + w * K;
         });
     }
     if constexpr (FORCE) {
         // Guo source (1 - omega/2) w [(c - u)/theta + (c.u) c/theta^2] . F
         const R pref = R(1) - R(0.5) * omega;
         const R uF = ux * Fx + uy * Fy + uz * Fz;
-        static_for<Q>([&](auto I) {
-            constexpr int i = decltype(I)::value;
+        static_for<HI - LO>([&](auto I) {
+            constexpr int i = LO + decltype(I)::value;
             constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
             constexpr R w = R(weight_of(Q, i));
             const R cF = R(cx) * Fx + R(cy) * Fy + R(cz) * Fz;
             const R cu = R(cx) * ux + R(cy) * uy + R(cz) * uz;
-            g[i] += pref * w * ((cF - uF) * a1 + cu * cF * (a1 * a1));
+            g[i - LO] += pref * w * ((cF - uF) * a1 + cu * cF * (a1 * a1));
         });
     }
+}
+
+// One-cell collision on shifted populations g (in place -> g_post).
+//
+// Every closure is evaluated in the common form
+//     g_post_i = a g_i + w_i (b (P_i - 1) + c0 + D H_i)
+// where f0_i - w_i = w_i (rho (P_i - 1) + drho) is the shifted equilibrium and
+// H_i = sum_ab c_ia c_ib M_ab - t is a quadratic form in c_i:
+//   BGK:   a = 1 - omega,   b = omega rho,   c0 = omega drho,   D = 0
+//   KC-MP: a = 1 - omega,   b, c0 as BGK,    D = (omega - omega_s)/(2 theta^2),
+//          M = m_sgs, t = theta tr m_sgs          (f_sgs = w H / (2 theta^2))
+//   KC-RB: a = 1 - omega_s, b = omega_s rho, c0 = omega_s drho,
+//          D = (omega_s - omega)(-rho tau_hat/theta), M = S,
+//          t = theta tr S (Hermite) or 0 (raw)    (f1 = w (-rho tau_hat/theta) H)
+// which is f - omega (f - f0 - f_sgs) - omega_s f_sgs (KC-MP, App. F.3) and
+// f - omega f1 - omega_s (f - f0 - f1) (KC-RB, App. F.2) rearranged.  For D3Q27
+// P - 1 = e_x + Y + e_x Y, Y = e_y + e_z + e_y e_z (the product equilibrium in
+// its small per-axis terms, so FP32 rounds without bias); Y and the parts of H
+// depend only on (c_y, c_z) and are formed once per pair.
+template <int Q, typename R, int CL, bool FORCE>
+__device__ __forceinline__ void collide(R (&g)[Q], R drho, R ux, R uy, R uz, R Sxx, R Syy, R Szz, R Sxy, R Sxz,
+                                        R Syz, R omega, R tau_hat, R nu, R cnud, R Fx, R Fy, R Fz,
+                                        const R* msgs_in = nullptr)
+{
+    if constexpr (CL == CL_KCRR) {
+        static_assert(Q == 27, "KC-RR is defined on D3Q27 only");
+        static_assert(!FORCE, "KC-RR is built for periodic boxes");
+        collide_kcrr<R>(g, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, omega, tau_hat, nu, cnud);
+    } else {
+        R P[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+        if constexpr (CL != CL_BGK && CL != CL_LEARNED) second_moments<Q, R>(g, drho, P);
+        const Coef<R> k = collide_coef<Q, R, CL>(P, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, omega, tau_hat,
+                                                 nu, cnud, msgs_in);
+        relax<Q, R, CL, FORCE, 0, Q>(g, k, ux, uy, uz, omega, Fx, Fy, Fz);
     }
 }
 
@@ -661,15 +722,10 @@ __device__ __forceinline__ void learned_msgs(const R* st, R drho, R ux, R uy, R 
     __syncwarp();
 }
 
-// OCC: CTAs per SM the register budget is sized for (0 = 1 for FP64 or TY >= 16, else 2)
-// RP: no population stash; the collision re-pulls its plane (loaded one plane
-// earlier for the velocity, so mostly L1 hits), which leaves only the velocity
-// ring in shared memory and lets more CTAs share an SM
-template <int Q, typename S, int CL, int BC, int TY, int OCC = 0, bool RP = false>
-__global__ void __launch_bounds__(32 * TY, OCC ? OCC : ((sizeof(typename StoreTraits<S>::R) == 8 || TY >= 16) ? 1 : 2))
+template <int Q, typename S, int CL, int BC, int TY>
+__global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) == 8 || TY >= 16) ? 1 : 2)
     step_kernel(const StepArgs a)
 {
-    static_assert(!(RP && CL == CL_LEARNED), "the learned closure reads its inputs from the stash");
     using R = typename StoreTraits<S>::R;
     using Sh = StepShape<Q, R, BC, TY>;
     constexpr int TX = Sh::TX, HY = Sh::HY, RX = Sh::RX, RN = Sh::RN, NT = Sh::NT, NB = Sh::NB;
@@ -775,7 +831,7 @@ __global__ void __launch_bounds__(32 * TY, OCC ? OCC : ((sizeof(typename StoreTr
             R t[Q];
             pull<Q, S, R, BC>(fin, ps, own, zr, t);
             moments<Q, R>(t, r, vx, vy, vz, Fx, Fy, Fz);
-            if (keep && !RP) {
+            if (keep) {
                 R* st = stash + (z & 1) * Q * NT + tid;
 #pragma unroll
                 for (int i = 0; i < Q; ++i) st[i * NT] = t[i];
@@ -833,14 +889,8 @@ __global__ void __launch_bounds__(32 * TY, OCC ? OCC : ((sizeof(typename StoreTr
                 collide<Q, R, CL, FORCE>(g, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, omega, tau_hat, nu, cnud,
                                          Fx, Fy, Fz, msgs);
             } else {
-                if constexpr (RP) {
-                    int zr[3];
-                    zrows(z, zr);
-                    pull<Q, S, R, BC>(fin, ps, own, zr, g);
-                } else {
 #pragma unroll
-                    for (int i = 0; i < Q; ++i) g[i] = st[i * NT];
-                }
+                for (int i = 0; i < Q; ++i) g[i] = st[i * NT];
                 collide<Q, R, CL, FORCE>(g, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, omega, tau_hat, nu, cnud,
                                          Fx, Fy, Fz);
             }
@@ -859,28 +909,20 @@ __global__ void __launch_bounds__(32 * TY, OCC ? OCC : ((sizeof(typename StoreTr
     }
 }
 
-template <int Q, typename S, int CL, int BC, int TY, bool RP>
-constexpr size_t kernel_smem_bytes()
-{
-    using Sh = StepShape<Q, typename StoreTraits<S>::R, BC, TY>;
-    return RP ? sizeof(typename StoreTraits<S>::R) * (size_t)(4 * 3 * Sh::RN)
-              : step_smem_bytes<Q, typename StoreTraits<S>::R, BC, TY, CL>();
-}
-
-template <int Q, typename S, int CL, int BC, int TY, int OCC = 0, bool RP = false>
+template <int Q, typename S, int CL, int BC, int TY>
 cudaError_t prepare_step_t()
 {
-    return cudaFuncSetAttribute(step_kernel<Q, S, CL, BC, TY, OCC, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kernel_smem_bytes<Q, S, CL, BC, TY, RP>());
+    return cudaFuncSetAttribute(step_kernel<Q, S, CL, BC, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)step_smem_bytes<Q, typename StoreTraits<S>::R, BC, TY, CL>());
 }
 
-template <int Q, typename S, int CL, int BC, int TY, int OCC = 0, bool RP = false>
+template <int Q, typename S, int CL, int BC, int TY>
 cudaError_t launch_step_t(const StepArgs& a, int nbatch, cudaStream_t s)
 {
     using Sh = StepShape<Q, typename StoreTraits<S>::R, BC, TY>;
     static bool attr_set = false;  // per instantiation; prepare_step_t sets it ahead of stream capture
     if (!attr_set) {
-        cudaError_t e = prepare_step_t<Q, S, CL, BC, TY, OCC, RP>();
+        cudaError_t e = prepare_step_t<Q, S, CL, BC, TY>();
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -888,7 +930,7 @@ cudaError_t launch_step_t(const StepArgs& a, int nbatch, cudaStream_t s)
     const int chunks = (a.nz + a.zchunk - 1) / a.zchunk;
     dim3 grid(tiles, chunks, nbatch), block(Sh::TX, TY);
     if (CL == CL_LEARNED && !a.mlp) return cudaErrorInvalidValue;
-    step_kernel<Q, S, CL, BC, TY, OCC, RP><<<grid, block, kernel_smem_bytes<Q, S, CL, BC, TY, RP>(), s>>>(a);
+    step_kernel<Q, S, CL, BC, TY><<<grid, block, step_smem_bytes<Q, typename StoreTraits<S>::R, BC, TY, CL>(), s>>>(a);
     return cudaGetLastError();
 }
 

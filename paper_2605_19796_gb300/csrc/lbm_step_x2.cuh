@@ -287,7 +287,7 @@ __device__ __forceinline__ void collide2(F2 (&g)[Q], F2 drho, F2 ux, F2 uy, F2 u
 
 // ------------------------------------------------------------------ kernel
 
-template <int Q, int BC, int TY, bool RP = false>
+template <int Q, int BC, int TY>
 struct PairShape {
     static constexpr int TX = 64;  // cells per tile row (two per lane)
     static constexpr int HY = (BC == BC_WALLS_Y) ? 2 : 1;
@@ -296,17 +296,16 @@ struct PairShape {
     static constexpr int RN = RX * RY;
     static constexpr int NT = 32 * TY;  // threads
     static constexpr int NB = RN - TX * TY;  // halo cells of the ring plane
-    // halo threads: two halo cells each, or one each without the stash (RP)
-    static constexpr int NBP = RP ? NB : (NB + 1) / 2;
+    static constexpr int NBP = (NB + 1) / 2;  // halo threads (two halo cells each)
     static constexpr size_t ring_off = 16;
     static constexpr size_t stash_off = ring_off + sizeof(float) * (size_t)(5 * 3 * RN);
-    static constexpr size_t bytes = stash_off + (RP ? 0 : sizeof(float2) * (size_t)(2 * Q * NT));
+    static constexpr size_t bytes = stash_off + sizeof(float2) * (size_t)(2 * Q * NT);
 };
 
 template <int Q, int BC, int TY>
 __device__ __forceinline__ void ring_cell(int b, int& lx, int& ly)
 {
-    using P = PairShape<Q, BC, TY, false>;
+    using P = PairShape<Q, BC, TY>;
     if (b < P::HY * P::RX) {
         lx = b % P::RX - 1;
         ly = b / P::RX - P::HY;
@@ -320,12 +319,10 @@ __device__ __forceinline__ void ring_cell(int b, int& lx, int& ly)
     }
 }
 
-// RP: no population stash; the collision re-pulls its plane (loaded one plane
-// earlier, mostly L1/L2 hits), halo cells one per thread, sized for two CTAs per SM
-template <int Q, typename S, int CL, int BC, int TY, bool RP = false>
-__global__ void __launch_bounds__(32 * TY, (TY >= 8 && !RP) ? 1 : 2) step_kernel_x2(const StepArgs a)
+template <int Q, typename S, int CL, int BC, int TY>
+__global__ void __launch_bounds__(32 * TY, TY >= 8 ? 1 : 2) step_kernel_x2(const StepArgs a)
 {
-    using P = PairShape<Q, BC, TY, RP>;
+    using P = PairShape<Q, BC, TY>;
     constexpr int TX = P::TX, HY = P::HY, RX = P::RX, RN = P::RN, NT = P::NT, NB = P::NB, NBP = P::NBP;
     static_assert(NBP <= NT, "every halo pair needs a thread");
     extern __shared__ __align__(16) unsigned char smem_x2[];
@@ -372,7 +369,7 @@ __global__ void __launch_bounds__(32 * TY, (TY >= 8 && !RP) ? 1 : 2) step_kernel
         h1 = make_col<BC>(x0 + lx, y0 + ly, nx, ny);
         h1_r = (ly + HY) * RX + (lx + 1);
         h1_ok = h1.valid;
-        if (!RP && tid + NBP < NB) {
+        if (tid + NBP < NB) {
             ring_cell<Q, BC, TY>(tid + NBP, lx, ly);
             h2 = make_col<BC>(x0 + lx, y0 + ly, nx, ny);
             h2_r = (ly + HY) * RX + (lx + 1);
@@ -404,19 +401,13 @@ __global__ void __launch_bounds__(32 * TY, (TY >= 8 && !RP) ? 1 : 2) step_kernel
         int zr[3];
         zrows(z, zr);
         const bool do_h = halo && tid < NBP;
-        F2 t[Q];
-        float gs[Q];
-        F2 gh[RP ? 1 : Q];
+        F2 t[Q], gh[Q];
         if (own.valid) pull2<Q, S, BC>(fin, ps, own, zr, t);
-        if constexpr (RP) {
-            if (do_h && h1_ok) pull<Q, S, float, BC>(fin, ps, h1, zr, gs);
-        } else {
-            if (do_h) pull_any2<Q, S, BC>(fin, ps, h1, h2, h1_ok, h2_ok, zr, gh);
-        }
+        if (do_h) pull_any2<Q, S, BC>(fin, ps, h1, h2, h1_ok, h2_ok, zr, gh);
         r = vx = vy = vz = bc2(0.f);
         if (own.valid) {
             moments2<Q>(t, r, vx, vy, vz, Fx, Fy, Fz);
-            if (keep && !RP) {
+            if (keep) {
                 F2* st = stash + (z & 1) * Q * NT + tid;
 #pragma unroll
                 for (int i = 0; i < Q; ++i) st[i * NT] = t[i];
@@ -424,13 +415,7 @@ __global__ void __launch_bounds__(32 * TY, (TY >= 8 && !RP) ? 1 : 2) step_kernel
         }
         put_u(z, own_ra, vx.v.x, vy.v.x, vz.v.x);
         put_u(z, own_rb, vx.v.y, vy.v.y, vz.v.y);
-        if constexpr (RP) {
-            if (do_h) {
-                float dh, hx = 0.f, hy = 0.f, hz = 0.f;
-                if (h1_ok) moments<Q, float>(gs, dh, hx, hy, hz, Fx, Fy, Fz);
-                put_u(z, h1_r, hx, hy, hz);
-            }
-        } else if (do_h) {
+        if (do_h) {
             F2 dh, hx, hy, hz;
             moments2<Q>(gh, dh, hx, hy, hz, Fx, Fy, Fz);
             put_u(z, h1_r, h1_ok ? hx.v.x : 0.f, h1_ok ? hy.v.x : 0.f, h1_ok ? hz.v.x : 0.f);
@@ -484,15 +469,9 @@ __global__ void __launch_bounds__(32 * TY, (TY >= 8 && !RP) ? 1 : 2) step_kernel
             const F2 Sxz = bc2(0.5f) * (du[0][2] + du[2][0]);
             const F2 Syz = bc2(0.5f) * (du[1][2] + du[2][1]);
             F2 g[Q];
-            if constexpr (RP) {
-                int zr[3];
-                zrows(z, zr);
-                pull2<Q, S, BC>(fin, ps, own, zr, g);
-            } else {
-                const F2* st = stash + (z & 1) * Q * NT + tid;
+            const F2* st = stash + (z & 1) * Q * NT + tid;
 #pragma unroll
-                for (int i = 0; i < Q; ++i) g[i] = st[i * NT];
-            }
+            for (int i = 0; i < Q; ++i) g[i] = st[i * NT];
             collide2<Q, CL, FORCE>(g, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, omega, tau_hat, nu, cnud, Fx,
                                    Fy, Fz);
             const int row = z * plane + own.yr[1];
@@ -518,27 +497,27 @@ __global__ void __launch_bounds__(32 * TY, (TY >= 8 && !RP) ? 1 : 2) step_kernel
     }
 }
 
-template <int Q, typename S, int CL, int BC, int TY, bool RP = false>
+template <int Q, typename S, int CL, int BC, int TY>
 cudaError_t prepare_x2_t()
 {
-    return cudaFuncSetAttribute(step_kernel_x2<Q, S, CL, BC, TY, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)PairShape<Q, BC, TY, RP>::bytes);
+    return cudaFuncSetAttribute(step_kernel_x2<Q, S, CL, BC, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)PairShape<Q, BC, TY>::bytes);
 }
 
-template <int Q, typename S, int CL, int BC, int TY, bool RP = false>
+template <int Q, typename S, int CL, int BC, int TY>
 cudaError_t launch_x2_t(const StepArgs& a, int nbatch, cudaStream_t s)
 {
-    using P = PairShape<Q, BC, TY, RP>;
+    using P = PairShape<Q, BC, TY>;
     static bool attr_set = false;  // per instantiation; prepare_x2_t sets it ahead of stream capture
     if (!attr_set) {
-        cudaError_t e = prepare_x2_t<Q, S, CL, BC, TY, RP>();
+        cudaError_t e = prepare_x2_t<Q, S, CL, BC, TY>();
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     const int tiles = ((a.nx + P::TX - 1) / P::TX) * ((a.ny + TY - 1) / TY);
     const int chunks = (a.nz + a.zchunk - 1) / a.zchunk;
     dim3 grid(tiles, chunks, nbatch), block(32, TY);
-    step_kernel_x2<Q, S, CL, BC, TY, RP><<<grid, block, P::bytes, s>>>(a);
+    step_kernel_x2<Q, S, CL, BC, TY><<<grid, block, P::bytes, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -135,22 +135,20 @@ def test_launch_shapes_fp32_consistent(lbm, orc, zchunk, tile_y):
 
 @pytest.mark.parametrize("closure", ["bgk", "kcmp", "kcrb_hermite", "kcrb_raw"])
 def test_variants_agree_fp32(lbm, orc, closure):
-    """The register-pull (1, 3) and asynchronous-copy (2) step kernels perform the
-    same per-cell arithmetic: FP32 results agree to FP32 rounding on a ragged
-    box; within one variant the z-chunking does not change a bit."""
+    """The register-pull (1), split-barrier (8) and packed-pair (9) step kernels
+    perform the same per-cell arithmetic: FP32 results agree to FP32 rounding on
+    a ragged box; within one variant the z-chunking does not change a bit."""
     shape = (45, 19, 23)
     rho, u = inputs.hit_fields(0, k0=3.0, urms=0.07, seed=8, shape=shape)
     res = {}
-    runs = [(1, 0), (2, 0), (2, 5)] + ([(3, 0)] if closure in ("bgk", "kcmp") else [])
-    for var, zc in runs:
+    for var, zc in [(1, 0), (8, 0), (8, 5), (9, 0), (9, 5)]:
         with lbm.Solver(27, shape, 2e-5, closure=closure, storage="fp32", variant=var, zchunk=zc) as s:
             s.init_velocity(rho, u)
             s.step(8)
             res[(var, zc)] = s.get_populations()
-    assert rel(res[(2, 0)], res[(1, 0)]) < 1e-6
-    assert np.array_equal(res[(2, 0)], res[(2, 5)])
-    if (3, 0) in res:
-        assert rel(res[(3, 0)], res[(1, 0)]) < 1e-6
+    for v in (8, 9):
+        assert rel(res[(v, 0)], res[(1, 0)]) < 1e-6, v
+        assert np.array_equal(res[(v, 0)], res[(v, 5)]), v
 
 
 def test_fp32_hit_64_velocity(lbm, orc):
@@ -307,7 +305,7 @@ def test_autotune_keeps_state_and_result(lbm, orc):
         s.step(2)
         before = s.get_populations()
         cfg = s.autotune(trials=2)
-        assert 1 <= cfg["variant"] <= 10 and cfg["tile_y"] in (4, 8, 16) and 1 <= cfg["zchunk"] <= 128
+        assert cfg["variant"] in (1, 4, 8, 9) and cfg["tile_y"] in (4, 8, 16) and 1 <= cfg["zchunk"] <= 128
         assert np.array_equal(before, s.get_populations())
         s.step(5)
         tuned = s.get_populations()
@@ -414,12 +412,10 @@ def test_kcrr_fp32_velocity(lbm, orc):
 @pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16", "bf16"])
 @pytest.mark.parametrize("closure", ["bgk", "kcmp", "kcrb_hermite", "kcrb_raw"])
 def test_load_schedule_variants(lbm, orc, storage, closure):
-    """Variants 5 (loads issued two planes ahead), 6 and 7 (no population stash,
-    the collision re-pulls its plane; sized for three and four CTAs per SM) and 8
-    (halo and own loads together, split arrive/wait barrier) only reschedule the
-    loads and synchronisation of the register pull (variant 1); variant 9 runs
-    the same arithmetic on packed FP32 pairs, two cells per thread (10: without
-    the stash, re-pulling for the collision).  On a ragged box with
+    """Variant 8 (halo and own loads together, split arrive/wait barrier) only
+    reschedules the loads and synchronisation of the register pull (variant 1);
+    variant 9 runs the same arithmetic on packed FP32 pairs, two cells per
+    thread.  On a ragged box with
     two boxes and several z-chunkings (one and two planes per CTA exercise the
     pipelines' start and drain): FP64 matches the oracle to 1e-12, FP32 matches
     variant 1 to FP32 rounding, 16-bit storage in rho and u to 1e-5 (one 16-bit
@@ -429,7 +425,7 @@ def test_load_schedule_variants(lbm, orc, storage, closure):
     rho = np.stack([f[0] for f in fields])
     u = np.stack([f[1] for f in fields], axis=1)
     nus = np.array([2e-5, 1e-4])
-    variants = (5, 8) if storage == "fp64" else (5, 6, 7, 8, 9, 10)
+    variants = (8,) if storage == "fp64" else (8, 9)
     res = {}
     for var, zc in [(1, 0)] + [(v, z) for v in variants for z in (0, 1, 2, 5)]:
         with lbm.Solver(27, shape, nus, closure=closure, storage=storage, variant=var, zchunk=zc, nbatch=2) as s:
@@ -460,12 +456,12 @@ def test_load_schedule_variants(lbm, orc, storage, closure):
 
 
 @pytest.mark.parametrize("q", [19, 27])
-def test_prefetch_variant_channel(lbm, orc, q):
-    """Variants 5 and 6 with bounce-back walls and a body force: FP64 (variant 5)
+def test_variants_channel(lbm, orc, q):
+    """Variants 8 and 9 with bounce-back walls and a body force: FP64 (variant 8)
     against the oracle, FP32 against variant 1 to FP32 rounding."""
     rho, u = inputs.channel_fields(16, 11, 9, 0.05, seed=5)
     F = (1e-5, 0.0, 0.0)
-    with lbm.Solver(q, (16, 11, 9), 2e-3, closure="kcmp", storage="fp64", bc=(0, 1, 0), force=F, variant=5,
+    with lbm.Solver(q, (16, 11, 9), 2e-3, closure="kcmp", storage="fp64", bc=(0, 1, 0), force=F, variant=8,
                     zchunk=3) as s:
         s.init_velocity(rho, u)
         s.step(6)
@@ -473,13 +469,13 @@ def test_prefetch_variant_channel(lbm, orc, q):
     fo = orc.run(orc.init_equilibrium(q, rho, u), 6, closure=1, nu=2e-3, c_nu=0.035, bc=(0, 1, 0), F=F)
     assert rel(fg, fo) < TOL64
     out = {}
-    for var in (1, 5, 6, 8, 9):
+    for var in (1, 8, 9):
         with lbm.Solver(q, (16, 11, 9), 2e-3, closure="kcmp", storage="fp32", bc=(0, 1, 0), force=F,
                         variant=var) as s:
             s.init_velocity(rho, u)
             s.step(6)
             out[var] = s.get_populations()
-    for var in (5, 6, 8, 9):
+    for var in (8, 9):
         assert rel(out[var], out[1]) < 1e-6, var
     with lbm.Solver(q, (16, 11, 9), 2e-3, closure="kcmp", storage="fp64", bc=(0, 1, 0), force=F, variant=8,
                     zchunk=2) as s:

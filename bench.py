@@ -190,7 +190,7 @@ def oracle_sample(wl: dict):
     return f, run, shape[0] * shape[1] * shape[2], desc
 
 
-def cpu_baseline(wl: dict, budget_s: float = 15.0, steps: int = 0):
+def cpu_baseline(wl: dict, budget_s: float = 25.0, steps: int = 0):
     """The FP64 oracle as it stands, on the host cores, on a bounded sample of the workload."""
     import oracle
 

@@ -101,7 +101,7 @@ typedef struct {
     int tile_y;         /* tuning: rows per CTA tile (0 = library default)           */
     int zchunk;         /* tuning: z-planes per CTA march (0 = library default)      */
     int variant;        /* tuning: step-kernel variant, 0 = library default
-                           (8 for D3Q27 with KC-MP or KC-RB, else 1),
+                           (8 for periodic D3Q27 with KC-MP or KC-RB, else 1),
                            1 = register pull (every lattice, storage, closure
                            and boundary), 4 = TMA-staged pipeline (FP32,
                            periodic, BGK/KC-MP/KC-RB, nx % 32 == 0 and

@@ -312,12 +312,12 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
         cfg->variant != VAR_PAIR)
         return fail(LBM_ERR_ARG, "unknown kernel variant");
     int variant = cfg->variant;
-    // measured defaults: the split-barrier pull for D3Q27 with a closure carrier
-    // (KC-MP, KC-RB), the register pull elsewhere; lbm_autotune may pick another
-    // variant for a given box
+    // measured defaults: the split-barrier pull for periodic D3Q27 boxes with a
+    // closure carrier (KC-MP, KC-RB), the register pull elsewhere; lbm_autotune
+    // may pick another variant for a given box
     if (variant == VAR_DEFAULT) {
         const bool carrier = cfg->closure == LBM_KCMP || cfg->closure == LBM_KCRB_HERMITE || cfg->closure == LBM_KCRB_RAW;
-        variant = (cfg->lattice == LBM_D3Q27 && carrier &&
+        variant = (cfg->lattice == LBM_D3Q27 && carrier && bc_kind == BC_PERIODIC &&
                    step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, VAR_SPLIT))
                       ? VAR_SPLIT
                       : VAR_REGISTER;

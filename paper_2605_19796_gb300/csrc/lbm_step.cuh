@@ -791,7 +791,7 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
     }
 
     auto zrows = [&](int z, int (&zr)[3]) {
-        const int zc = wrapi(z, nz);
+        const int zc = z < 0 ? z + nz : (z >= nz ? z - nz : z);  // z in [-1, nz]
         zr[0] = (zc == 0 ? nz - 1 : zc - 1) * plane;
         zr[1] = zc * plane;
         zr[2] = (zc == nz - 1 ? 0 : zc + 1) * plane;
@@ -859,7 +859,8 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
 
         // ---- plane z: strain from the ring, closure, relaxation, store
         if (own.valid) {
-            if (own_store && !(isfinite(drho) && isfinite(ux) && isfinite(uy) && isfinite(uz))) atomicOr(a.flag, 1u);
+            // a non-finite component makes the sum non-finite (the moments are O(1))
+            if (own_store && !isfinite(drho + ux + uy + uz)) atomicOr(a.flag, 1u);
             const int sm = rslot(z - 1), s0 = rslot(z), sp = rslot(z + 1);
             R du[3][3];  // du[a][b] = d_a u_b
 #pragma unroll

@@ -18,7 +18,8 @@
 // still reads k-1..k+1, and it cannot reach plane k+3 before the slowest has
 // arrived for plane k+1, which it does after its last read of plane k-1.
 // (Keeping the z-neighbours in registers instead would allow four slots but
-// pushes the register count past the two-CTA budget.)
+// pushes the register count past the two-CTA budget; eight slots, for a mask
+// instead of a modulo, cost more L1 than they save.)
 // Plane p arrives on mbarrier (p - z0) & 1, phase ((p - z0) >> 1) & 1; a thread
 // arrives for plane p only after it waited for plane p-2 on the same mbarrier,
 // so an arrival never lands in an older phase.  Waits are bounded: on timeout
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
     __syncthreads();
 
     auto zrows = [&](int z, int (&zr)[3]) {
-        const int zc = wrapi(z, nz);
+        const int zc = z < 0 ? z + nz : (z >= nz ? z - nz : z);  // z in [-1, nz]
         zr[0] = (zc == 0 ? nz - 1 : zc - 1) * plane;
         zr[1] = zc * plane;
         zr[2] = (zc == nz - 1 ? 0 : zc + 1) * plane;
@@ -172,7 +173,8 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
             return;
         }
         if (own.valid) {
-            if (own_store && !(isfinite(drho) && isfinite(ux) && isfinite(uy) && isfinite(uz))) atomicOr(a.flag, 1u);
+            // a non-finite component makes the sum non-finite (the moments are O(1))
+            if (own_store && !isfinite(drho + ux + uy + uz)) atomicOr(a.flag, 1u);
             const int sm = rslot(z - 1), s0 = rslot(z), sp = rslot(z + 1);
             R du[3][3];  // du[a][b] = d_a u_b
 #pragma unroll

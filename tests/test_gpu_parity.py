@@ -163,6 +163,65 @@ def test_fp32_hit_64_velocity(lbm, orc):
     assert err <= 1e-5, err
 
 
+def _spectrum(u):
+    """Shell-averaged E(k) = 1/2 sum_{|k'| in [k-1/2, k+1/2)} |u_hat(k')|^2 of a periodic cube."""
+    n = u.shape[-1]
+    uh = np.fft.fftn(u, axes=(1, 2, 3)) / n ** 3
+    e = 0.5 * (np.abs(uh) ** 2).sum(0)
+    k = np.fft.fftfreq(n, d=1.0 / n)
+    kk = np.sqrt(k[:, None, None] ** 2 + k[None, :, None] ** 2 + k[None, None, :] ** 2)
+    return np.bincount(np.rint(kk).astype(int).ravel(), weights=e.ravel(), minlength=n)[: n // 2]
+
+
+def test_fp32_hit_64_statistics(lbm, orc):
+    """Decaying HIT at 64^3 (k0 = 4, u_rms = 0.04, nu = 1e-4, KC-MP), FP32 GPU
+    (default launch) against the FP64 oracle over 300 steps: the energy spectrum
+    at steps 200 and 300 to 1e-4 relative L2 over the shells 1..31, the
+    kinetic energy to 2e-5 and the dissipation rate -dE_k/dt between them to
+    1e-3 relative (FP32 storage rounds each population to 2^-24 relative every
+    step; the measured kinetic-energy difference at step 200 is 6e-6)."""
+    n = 64
+    rho, u = inputs.hit_fields(n, k0=4.0, urms=0.04, seed=0)
+    out = _run_pair(lbm, orc, 27, (n, n, n), rho, u, 1e-4, "kcmp", 300, storage="fp32", checkpoints=[200, 300])
+    ek = {}
+    for (fg, fo, _), step in zip(out, (200, 300)):
+        rg, ug = orc.fields(fg)
+        ro, uo = orc.fields(fo)
+        eg, eo = _spectrum(ug), _spectrum(uo)
+        err = np.sqrt(((eg[1:] - eo[1:]) ** 2).sum() / (eo[1:] ** 2).sum())
+        assert err < 1e-4, (step, err)
+        ek[step] = (float((0.5 * rg * (ug ** 2).sum(0)).mean()), float((0.5 * ro * (uo ** 2).sum(0)).mean()))
+        assert abs(ek[step][0] - ek[step][1]) <= 2e-5 * ek[step][1]
+    eps_g = (ek[200][0] - ek[300][0]) / 100
+    eps_o = (ek[200][1] - ek[300][1]) / 100
+    assert eps_o > 0 and abs(eps_g - eps_o) <= 1e-3 * eps_o, (eps_g, eps_o)
+
+
+def test_hit_256_2000_steps(lbm, orc):
+    """Decaying HIT at 256^3 (k0 = 4, u_rms = 0.04, nu = 1e-4, KC-MP, FP32,
+    default launch) for 2000 steps: no non-finite flag, mass conserved to FP32
+    accumulation (1e-6 relative), kinetic energy decaying every 250 steps."""
+    import torch
+
+    n = 256
+    rho, u = inputs.hit_fields(n, k0=4.0, urms=0.04, seed=3, device="cuda")
+    with lbm.Solver(27, (n, n, n), 1e-4, closure="kcmp", storage="fp32") as s:
+        s.init_velocity_device(rho, u)
+        r = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
+        v = torch.empty((3, n, n, n), dtype=torch.float64, device="cuda")
+        s.moments_device(r, v)
+        m0 = float(r.sum())
+        ek = [float((0.5 * r * (v ** 2).sum(0)).mean())]
+        for _ in range(8):
+            s.step(250)
+            s.synchronize()
+            s.moments_device(r, v)
+            ek.append(float((0.5 * r * (v ** 2).sum(0)).mean()))
+        assert abs(float(r.sum()) - m0) <= 1e-6 * m0
+    assert all(b < a for a, b in zip(ek, ek[1:])), ek
+    assert ek[-1] > 0.05 * ek[0]
+
+
 @pytest.mark.parametrize("q", [19, 27])
 @pytest.mark.parametrize("ny", [24, 13, 9])
 def test_channel_walls_force_fp64(lbm, orc, q, ny):
@@ -364,14 +423,17 @@ def test_tma_variant_matches(lbm, orc, shape, nbatch, closure):
 
 
 def test_default_variant_selection(lbm):
-    """Library default: the split-barrier pull (8) for D3Q27 with KC-MP or KC-RB,
-    the register pull (1) for BGK, D3Q19, KC-RR and the learned closure; an
-    explicitly requested variant that is not built for a box is refused."""
+    """Library default: the split-barrier pull (8) for periodic D3Q27 with KC-MP
+    or KC-RB, the register pull (1) for BGK, D3Q19, walls, KC-RR and the learned
+    closure; an explicitly requested variant that is not built for a box is
+    refused."""
     for q, closure, storage, want in ((27, "kcmp", "fp32", 8), (27, "kcrb_hermite", "fp16", 8), (27, "kcmp", "fp64", 8),
                                       (27, "bgk", "fp32", 1), (19, "kcmp", "fp32", 1), (27, "kcrr", "fp64", 1),
                                       (27, "learned", "fp32", 1)):
         with lbm.Solver(q, (40, 32, 16), 1e-4, closure=closure, storage=storage) as s:
             assert s.launch_config["variant"] == want, (q, closure, storage)
+    with lbm.Solver(27, (40, 32, 16), 1e-4, closure="kcmp", storage="fp32", bc=(0, 1, 0)) as s:
+        assert s.launch_config["variant"] == 1
     with lbm.Solver(27, (64, 32, 16), 1e-4, closure="kcmp", storage="fp32", variant=4) as s:
         assert s.launch_config["variant"] == 4
     with pytest.raises(lbm.LbmError):

@@ -256,14 +256,10 @@ def main():
     import numpy as np
     import torch
 
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
+    from paper_2605_19796_gb300.replicas import Replicas
 
-        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    else:
+    rep = Replicas("nccl")
+    if world == 1:
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
 
@@ -283,16 +279,17 @@ def main():
     force = wl.get("force", (0.0, 0.0, 0.0))
     if "u_bulk" in wl:  # channel
         bc = (0, 1, 0)
-        rho_d, u_d = inputs.channel_fields(nx, ny, nz, wl["u_bulk"], seed=rank, device=dev)
+        rho_d, u_d = inputs.channel_fields(nx, ny, nz, wl["u_bulk"], seed=rep.seed(), device=dev)
         nu = wl["nu"]
     elif nb > 1:  # ensemble of boxes with their own seeds and viscosities
-        parts = [inputs.hit_fields(nx, k0=wl["k0"], urms=wl["urms"], seed=rank * nb + b, device=dev) for b in range(nb)]
+        parts = [inputs.hit_fields(nx, k0=wl["k0"], urms=wl["urms"], seed=rep.seed(b, nb), device=dev)
+                 for b in range(nb)]
         rho_d = torch.stack([p[0] for p in parts])
         u_d = torch.stack([p[1] for p in parts], dim=1).contiguous()
         del parts
         nu = inputs.ensemble_viscosities(nb, seed=rank)
     else:
-        rho_d, u_d = inputs.hit_fields(nx, k0=wl["k0"], urms=wl["urms"], seed=rank, device=dev)
+        rho_d, u_d = inputs.hit_fields(nx, k0=wl["k0"], urms=wl["urms"], seed=rep.seed(), device=dev)
         nu = wl["nu"]
     torch.cuda.synchronize()
     s = lbm.Solver(q, shape, nu, closure=wl["closure"], storage=wl["storage"], stream=stream, bc=bc, force=force,
@@ -309,10 +306,7 @@ def main():
     s.step(args.warmup)
     s.synchronize()
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
+    barrier = rep.barrier
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
@@ -332,12 +326,8 @@ def main():
     s.synchronize()  # raises on a non-finite field
     t_ms = ev0.elapsed_time(ev1)
     per = [t_ms / args.steps]
-    t_max = t_ms
-    if dist is not None:
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = N * args.steps * world / (t_max * 1e-3) / 1e6
+    t_max = rep.max_over_ranks(t_ms)
+    value = rep.whole_job_rate(N * args.steps, t_max * 1e-3) / 1e6
 
     # roofline of the step kernel (one launch per step, back to back in the graph)
     kern_s = sum(per) / len(per) * 1e-3
@@ -368,17 +358,15 @@ def main():
         lbm.lbm_moments(s.h, rho_o.numpy(), u_o.numpy())
         t1 = time.perf_counter() - t0
         barrier()
-        if dist is not None:
-            tt = torch.tensor([t1], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t1 = float(tt.item())
-        e2e = {"value": N * args.steps * world / t1 / 1e6, "unit": "MLUPS",
+        t1 = rep.max_over_ranks(t1)
+        e2e = {"value": rep.whole_job_rate(N * args.steps, t1) / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": 32 * N // args.steps, "d2h_bytes_per_step": 32 * N // args.steps,
                "what": "lbm_init_velocity(pinned host rho,u) + K x lbm_step + lbm_moments(pinned host rho,u)"}
     s_cfg = s.launch_config
     s.close()
 
-    if rank != 0:
+    if not rep.root:
+        rep.close()
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -397,8 +385,7 @@ def main():
         "kernel_ms": {"mean": sum(per) / len(per)},
     }
     print(json.dumps(out), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    rep.close()
 
 
 if __name__ == "__main__":

@@ -309,15 +309,16 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
         return fail(LBM_ERR_UNSUPPORTED, "a body force is supported with bounce-back walls (channel) only");
     int tile_y = cfg->tile_y ? cfg->tile_y : 8;
     if (cfg->variant != VAR_DEFAULT && cfg->variant != VAR_REGISTER && cfg->variant != VAR_TMA && cfg->variant != VAR_SPLIT &&
-        cfg->variant != VAR_PAIR)
+        cfg->variant != VAR_PAIR && cfg->variant != VAR_SPLIT_PF)
         return fail(LBM_ERR_ARG, "unknown kernel variant");
     int variant = cfg->variant;
-    // measured defaults: the split-barrier pull for periodic D3Q27 boxes with a
-    // closure carrier (KC-MP, KC-RB), the register pull elsewhere; lbm_autotune
-    // may pick another variant for a given box
+    // measured defaults: the split-barrier pull for periodic D3Q27 boxes with BGK
+    // or a closure carrier (KC-MP, KC-RB), the register pull elsewhere;
+    // lbm_autotune may pick another variant for a given box
     if (variant == VAR_DEFAULT) {
-        const bool carrier = cfg->closure == LBM_KCMP || cfg->closure == LBM_KCRB_HERMITE || cfg->closure == LBM_KCRB_RAW;
-        variant = (cfg->lattice == LBM_D3Q27 && carrier && bc_kind == BC_PERIODIC &&
+        const bool split_built = cfg->closure == LBM_BGK || cfg->closure == LBM_KCMP ||
+                                 cfg->closure == LBM_KCRB_HERMITE || cfg->closure == LBM_KCRB_RAW;
+        variant = (cfg->lattice == LBM_D3Q27 && split_built && bc_kind == BC_PERIODIC &&
                    step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, VAR_SPLIT))
                       ? VAR_SPLIT
                       : VAR_REGISTER;
@@ -472,7 +473,7 @@ int lbm_autotune(lbm_handle* h, int trials)
 {
     if (int rc = check_handle(h)) return rc;
     if (trials < 1) trials = 3;
-    static const int kVariants[] = {VAR_REGISTER, VAR_SPLIT, VAR_PAIR, VAR_TMA};
+    static const int kVariants[] = {VAR_REGISTER, VAR_SPLIT, VAR_SPLIT_PF, VAR_PAIR, VAR_TMA};
     static const int kTiles[] = {4, 8, 16};
     static const int kChunks[] = {8, 16, 32, 64, 128};
     const int v0 = h->variant, t0 = h->tile_y, z0 = h->zchunk;

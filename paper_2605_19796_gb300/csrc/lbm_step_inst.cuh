@@ -55,6 +55,19 @@ cudaError_t launch_step_qs(int closure, int bc, int ty, int variant, const StepA
 #undef LBM_SB_CASE
         return cudaErrorNotSupported;
     }
+    if (variant == VAR_SPLIT_PF) {
+#define LBM_SBP_CASE(CL, BCV, TYV)                                                              \
+    if (closure == CL && bc == BCV && ty == TYV)                                                \
+        return a ? launch_sb_t<Q, S, CL, BCV, TYV, true>(*a, nbatch, s) : (nbatch < 0 ? prepare_sb_t<Q, S, CL, BCV, TYV, true>() : cudaSuccess);
+        LBM_SBP_CASE(CL_BGK, BC_PERIODIC, 8)
+        LBM_SBP_CASE(CL_KCMP, BC_PERIODIC, 8)
+        LBM_SBP_CASE(CL_KCRB_H, BC_PERIODIC, 8)
+        LBM_SBP_CASE(CL_KCRB_RAW, BC_PERIODIC, 8)
+        LBM_SBP_CASE(CL_BGK, BC_WALLS_Y, 8)
+        LBM_SBP_CASE(CL_KCMP, BC_WALLS_Y, 8)
+#undef LBM_SBP_CASE
+        return cudaErrorNotSupported;
+    }
     if (variant == VAR_PAIR) {
         if constexpr (R32) {
 #define LBM_X2_CASE(CL, BCV, TYV)                                                               \

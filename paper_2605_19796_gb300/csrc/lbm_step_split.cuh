@@ -31,6 +31,21 @@
 
 namespace lbmk {
 
+// c_y, c_z of a population index known only at run time (prefetch loop)
+template <int Q>
+__device__ __forceinline__ int d27_of_rt(int i)
+{
+    if constexpr (Q == 27) {
+        return i;
+    } else {
+        int r = 0;
+        static_for<Q>([&](auto I) {
+            if (i == decltype(I)::value) r = d27_index(Q, decltype(I)::value);
+        });
+        return r;
+    }
+}
+
 template <int Q, typename R, int BC, int TY>
 struct SplitShape {
     using Sh = StepShape<Q, R, BC, TY>;
@@ -39,7 +54,12 @@ struct SplitShape {
     static constexpr size_t bytes = stash_off + sizeof(R) * (size_t)(2 * Q * Sh::NT);
 };
 
-template <int Q, typename S, int CL, int BC, int TY>
+// L2PF: at plane k the CTA prefetches into L2 the source rows its pull of
+// plane k+2 will read (one 128-byte line per population and row: the tile's
+// x-range, for the tile rows and the two halo rows), so that the loads of that
+// plane's load phase meet L2 rather than DRAM; no registers or shared memory
+// hold the prefetched data and HBM traffic is unchanged.
+template <int Q, typename S, int CL, int BC, int TY, bool L2PF = false>
 __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) == 8 || TY >= 16) ? 1 : 2)
     step_kernel_sb(const StepArgs a)
 {
@@ -161,7 +181,30 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
         arrive(z0);
     }
 
+    // prefetch items of a plane: (population, row) pairs, rows y0-1-c_y .. y0+TY-c_y
+    constexpr int kPfRows = TY + 2;
+    auto prefetch_plane = [&](int p) {
+        int zr[3];
+        zrows(p, zr);
+        for (int k = tid; k < Q * kPfRows; k += NT) {
+            const int i = k / kPfRows, r = k - i * kPfRows;
+            const int d = d27_of_rt<Q>(i);
+            const int cy = (d / 3) % 3 - 1, cz = d / 9 - 1;
+            int y = y0 - 1 - cy + r;
+            if (BC == BC_WALLS_Y) {
+                if (y < 0 || y >= ny) continue;
+            } else {
+                y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+            }
+            const S* line = fin + (long long)i * ps + (zr[1 - cz] + y * nx + x0);
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(line));
+        }
+    };
+
     for (int z = z0; z < z1; ++z) {
+        if constexpr (L2PF) {
+            if (z + 2 <= z1) prefetch_plane(z + 2);
+        }
         // ---- plane z+1: own (and, while it will be collided, halo) velocities into the ring
         R rn, vnx, vny, vnz;
         load_plane(z + 1, z + 1 < z1, z + 1 < z1, rn, vnx, vny, vnz);
@@ -214,27 +257,27 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
     }
 }
 
-template <int Q, typename S, int CL, int BC, int TY>
+template <int Q, typename S, int CL, int BC, int TY, bool L2PF = false>
 cudaError_t prepare_sb_t()
 {
-    return cudaFuncSetAttribute(step_kernel_sb<Q, S, CL, BC, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(step_kernel_sb<Q, S, CL, BC, TY, L2PF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)SplitShape<Q, typename StoreTraits<S>::R, BC, TY>::bytes);
 }
 
-template <int Q, typename S, int CL, int BC, int TY>
+template <int Q, typename S, int CL, int BC, int TY, bool L2PF = false>
 cudaError_t launch_sb_t(const StepArgs& a, int nbatch, cudaStream_t s)
 {
     using Sh = StepShape<Q, typename StoreTraits<S>::R, BC, TY>;
     static bool attr_set = false;  // per instantiation; prepare_sb_t sets it ahead of stream capture
     if (!attr_set) {
-        cudaError_t e = prepare_sb_t<Q, S, CL, BC, TY>();
+        cudaError_t e = prepare_sb_t<Q, S, CL, BC, TY, L2PF>();
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     const int tiles = ((a.nx + Sh::TX - 1) / Sh::TX) * ((a.ny + TY - 1) / TY);
     const int chunks = (a.nz + a.zchunk - 1) / a.zchunk;
     dim3 grid(tiles, chunks, nbatch), block(Sh::TX, TY);
-    step_kernel_sb<Q, S, CL, BC, TY>
+    step_kernel_sb<Q, S, CL, BC, TY, L2PF>
         <<<grid, block, SplitShape<Q, typename StoreTraits<S>::R, BC, TY>::bytes, s>>>(a);
     return cudaGetLastError();
 }

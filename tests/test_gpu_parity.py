@@ -364,7 +364,7 @@ def test_autotune_keeps_state_and_result(lbm, orc):
         s.step(2)
         before = s.get_populations()
         cfg = s.autotune(trials=2)
-        assert cfg["variant"] in (1, 4, 8, 9) and cfg["tile_y"] in (4, 8, 16) and 1 <= cfg["zchunk"] <= 128
+        assert cfg["variant"] in (1, 4, 8, 9, 12) and cfg["tile_y"] in (4, 8, 16) and 1 <= cfg["zchunk"] <= 128
         assert np.array_equal(before, s.get_populations())
         s.step(5)
         tuned = s.get_populations()
@@ -423,12 +423,12 @@ def test_tma_variant_matches(lbm, orc, shape, nbatch, closure):
 
 
 def test_default_variant_selection(lbm):
-    """Library default: the split-barrier pull (8) for periodic D3Q27 with KC-MP
-    or KC-RB, the register pull (1) for BGK, D3Q19, walls, KC-RR and the learned
-    closure; an explicitly requested variant that is not built for a box is
-    refused."""
+    """Library default: the split-barrier pull (8) for periodic D3Q27 with BGK,
+    KC-MP or KC-RB, the register pull (1) for D3Q19, walls, KC-RR and the
+    learned closure; an explicitly requested variant that is not built for a
+    box is refused."""
     for q, closure, storage, want in ((27, "kcmp", "fp32", 8), (27, "kcrb_hermite", "fp16", 8), (27, "kcmp", "fp64", 8),
-                                      (27, "bgk", "fp32", 1), (19, "kcmp", "fp32", 1), (27, "kcrr", "fp64", 1),
+                                      (27, "bgk", "fp32", 8), (19, "kcmp", "fp32", 1), (27, "kcrr", "fp64", 1),
                                       (27, "learned", "fp32", 1)):
         with lbm.Solver(q, (40, 32, 16), 1e-4, closure=closure, storage=storage) as s:
             assert s.launch_config["variant"] == want, (q, closure, storage)
@@ -487,7 +487,7 @@ def test_load_schedule_variants(lbm, orc, storage, closure):
     rho = np.stack([f[0] for f in fields])
     u = np.stack([f[1] for f in fields], axis=1)
     nus = np.array([2e-5, 1e-4])
-    variants = (8,) if storage == "fp64" else (8, 9)
+    variants = (8, 12) if storage == "fp64" else (8, 9, 12)
     res = {}
     for var, zc in [(1, 0)] + [(v, z) for v in variants for z in (0, 1, 2, 5)]:
         with lbm.Solver(27, shape, nus, closure=closure, storage=storage, variant=var, zchunk=zc, nbatch=2) as s:
@@ -531,13 +531,13 @@ def test_variants_channel(lbm, orc, q):
     fo = orc.run(orc.init_equilibrium(q, rho, u), 6, closure=1, nu=2e-3, c_nu=0.035, bc=(0, 1, 0), F=F)
     assert rel(fg, fo) < TOL64
     out = {}
-    for var in (1, 8, 9):
+    for var in (1, 8, 9, 12):
         with lbm.Solver(q, (16, 11, 9), 2e-3, closure="kcmp", storage="fp32", bc=(0, 1, 0), force=F,
                         variant=var) as s:
             s.init_velocity(rho, u)
             s.step(6)
             out[var] = s.get_populations()
-    for var in (8, 9):
+    for var in (8, 9, 12):
         assert rel(out[var], out[1]) < 1e-6, var
     with lbm.Solver(q, (16, 11, 9), 2e-3, closure="kcmp", storage="fp64", bc=(0, 1, 0), force=F, variant=8,
                     zchunk=2) as s:

@@ -150,6 +150,14 @@ int lbm_step(lbm_handle* h, int nsteps);
  * launch reads the current buffer and writes the other one.  Synchronises. */
 int lbm_autotune(lbm_handle* h, int trials);
 
+/* Self-test of the error path of the kernels' bounded device-side waits:
+ * launches on the handle's stream one CTA that waits on an mbarrier phase
+ * nothing completes; its wait gives up after `polls` polls and sets the
+ * timeout bit of the handle's status flag, which this call reads back, so the
+ * expected result is LBM_ERR_TIMEOUT with the handle still usable (the
+ * populations are untouched).  polls < 1: LBM_ERR_ARG. */
+int lbm_wait_selftest(lbm_handle* h, int polls);
+
 /* The launch configuration in use: kernel variant, tile height, z-chunk. */
 int lbm_launch_config(const lbm_handle* h, int* variant, int* tile_y, int* zchunk);
 

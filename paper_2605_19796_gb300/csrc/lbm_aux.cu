@@ -7,6 +7,7 @@
 #include "lbm_lattice.cuh"
 #include "lbm_step.cuh"
 #include "lbm_equilibrium.cuh"
+#include "lbm_mbarrier.cuh"
 
 namespace lbmk {
 
@@ -312,6 +313,24 @@ cudaError_t launch_init_equilibrium(int q, int storage, void* f, const double* r
             init_kernel<19, S><<<g, 256, 0, s>>>((S*)f, rho, u, ncell, nbatch, ps, bs);
         return cudaGetLastError();
     });
+}
+
+// Self-test of the bounded-wait error path: one thread waits on an mbarrier
+// phase that nothing completes; the bounded wait gives up after `polls` polls
+// and records the timeout bit in the status flag, as a step kernel would.
+__global__ void wait_selftest_kernel(unsigned int* flag, long long polls)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        if (!mbar_wait_polls(&bar, 0u, polls)) atomicOr(flag, kFlagTimeout);
+    }
+}
+
+cudaError_t launch_wait_selftest(unsigned int* flag, long long polls, cudaStream_t s)
+{
+    wait_selftest_kernel<<<1, 32, 0, s>>>(flag, polls);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_moments(int q, int storage, const void* f, double* rho, double* u, long long ncell, int nbatch,

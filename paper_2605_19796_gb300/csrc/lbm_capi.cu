@@ -579,6 +579,16 @@ int lbm_moments(lbm_handle* h, double* rho, double* u)
     return rc;
 }
 
+int lbm_wait_selftest(lbm_handle* h, int polls)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (polls < 1) return fail(LBM_ERR_ARG, "polls must be >= 1");
+    cudaError_t e = launch_wait_selftest(static_cast<unsigned int*>(h->d_flag), polls, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_wait_selftest");
+    ++h->launches;
+    return read_flag(h);
+}
+
 int lbm_diagnostics(lbm_handle* h, int box, double out[8])
 {
     if (int rc = check_handle(h)) return rc;

@@ -35,6 +35,9 @@ struct StepArgs {
 size_t mlp_packed_bytes();
 void mlp_pack(const float* params, const float* stats, unsigned char* out);
 
+// one-CTA kernel whose bounded mbarrier wait runs out (the timeout error path)
+cudaError_t launch_wait_selftest(unsigned int* flag, long long polls, cudaStream_t s);
+
 // Step-kernel variants: register pull (lbm_step.cuh), TMA staging
 // (lbm_step_tma.cuh), split arrive/wait barrier (lbm_step_split.cuh), two cells
 // per thread on packed FP32 pairs (lbm_step_x2.cuh).  Values 2, 3, 5, 6, 7, 10

@@ -33,11 +33,15 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity)
         : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity)
+__device__ __forceinline__ bool mbar_wait_polls(uint64_t* bar, unsigned parity, long long polls)
 {
-    for (long long k = 0; k < kMbarSpinLimit; ++k)
+    for (long long k = 0; k < polls; ++k)
         if (mbar_test(bar, parity)) return true;
     return false;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity)
+{
+    return mbar_wait_polls(bar, parity, kMbarSpinLimit);
 }
 // plain arrival (release at CTA scope): the phase completes once every expected
 // thread has arrived

@@ -40,7 +40,7 @@ EXPORTS = ["lbm_config_default", "lbm_create", "lbm_destroy", "lbm_init_velocity
            "lbm_diagnostics_noalloc", "lbm_autotune", "lbm_launch_config", "lbm_mlp_param_count",
            "lbm_mlp_workspace_floats", "lbm_mlp_forward", "lbm_mlp_grad", "lbm_mlp_adamw", "lbm_box_filter",
            "lbm_closure_features", "lbm_set_learned_closure", "lbm_mlp_packed_bytes", "lbm_mlp_pack",
-           "lbm_mlp_forward_tc"]
+           "lbm_mlp_forward_tc", "lbm_wait_selftest"]
 
 
 class lbm_config(ctypes.Structure):
@@ -105,6 +105,7 @@ def _load() -> ctypes.CDLL:
     lib.lbm_mlp_packed_bytes.restype = ctypes.c_longlong
     lib.lbm_mlp_pack.argtypes = [P(ctypes.c_float), P(ctypes.c_float), vp]
     lib.lbm_mlp_forward_tc.argtypes = [vp, vp, ctypes.c_int, vp, vp]
+    lib.lbm_wait_selftest.argtypes = [H, ctypes.c_int]
     lib.lbm_autotune.argtypes = [H, ctypes.c_int]
     lib.lbm_launch_config.argtypes = [H, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]
     lib.lbm_last_error.restype = ctypes.c_char_p
@@ -285,6 +286,11 @@ def lbm_mlp_pack(params: np.ndarray, stats: np.ndarray) -> np.ndarray:
 
 def lbm_mlp_forward_tc(packed_ptr, x_ptr, n, y_ptr, stream=None) -> None:
     _check(LIB.lbm_mlp_forward_tc(_vp(packed_ptr), _vp(x_ptr), int(n), _vp(y_ptr), _vp(_stream_handle(stream))))
+
+
+def lbm_wait_selftest(h, polls: int) -> int:
+    """Return code of the bounded-wait self-test (LBM_ERR_TIMEOUT when the error path works)."""
+    return int(LIB.lbm_wait_selftest(h, int(polls)))
 
 
 def lbm_set_learned_closure(h, params: np.ndarray, stats: np.ndarray) -> None:

@@ -544,3 +544,19 @@ def test_variants_channel(lbm, orc, q):
         s.init_velocity(rho, u)
         s.step(6)
         assert rel(s.get_populations(), fo) < TOL64
+
+
+def test_bounded_wait_times_out_and_handle_stays_usable(lbm, orc):
+    """A device-side wait that nothing completes gives up after its poll limit
+    and is reported as LBM_ERR_TIMEOUT (no trap, no fault); the handle then
+    steps normally and still matches the oracle."""
+    shape = (16, 8, 6)
+    rho, u = inputs.hit_fields(0, k0=2.0, urms=0.05, seed=21, shape=shape)
+    with lbm.Solver(27, shape, 1e-4, closure="kcmp", storage="fp64") as s:
+        s.init_velocity(rho, u)
+        assert lbm.lbm_wait_selftest(s.h, 1 << 12) == lbm.LBM_ERR_TIMEOUT
+        assert "gave up" in lbm.lbm_last_error()
+        s.step(3)
+        fg = s.get_populations()
+    fo = orc.run(orc.init_equilibrium(27, rho, u), 3, closure=1, nu=1e-4, c_nu=0.035)
+    assert rel(fg, fo) < TOL64

@@ -193,6 +193,67 @@ def _velocity(s: lbm.Solver) -> torch.Tensor:
     return u
 
 
+def filtered_reference(n_fine: int, factor: int, k0: float, seed: int, nu_fine: float, urms: float, t0: int,
+                       coarse_steps: int) -> Dict:
+    """Fine run box-filtered at fine steps t0 and t0 + factor * coarse_steps: the
+    coarse initial state (post-collision, rescaled non-equilibrium part), the
+    filtered velocity, spectrum and kinetic energy at the end, and the filtered
+    run's dissipation rate -dE_k/dt per coarse step over the window."""
+    nu_c = nu_fine / factor
+    with lbm.Solver(27, (n_fine,) * 3, nu_fine, closure="kcmp", storage="fp32") as fine:
+        rho, u = inputs.hit_fields(n_fine, k0=k0, urms=urms, seed=seed, device="cuda")
+        fine.init_velocity_device(rho, u)
+        del rho, u
+        fine.step(t0)
+        _, _, _, fc0 = snapshot_features(fine, factor, nu_c, nu_fine, pull=False)
+        f0 = fc0.double().cpu().numpy()
+        fine.step(factor * coarse_steps)
+        _, _, _, fc1 = snapshot_features(fine, factor, nu_c, nu_fine, pull=False)
+    ref = _coarse_velocity(fc1, nu_c)
+    ek0 = float(0.5 * (_coarse_velocity(fc0, nu_c) ** 2).sum(0).mean())
+    ek1 = float(0.5 * (ref ** 2).sum(0).mean())
+    return {"f0": f0, "spectrum": spectrum(ref), "E_k0": ek0, "E_k": ek1, "dissipation": (ek0 - ek1) / coarse_steps,
+            "nu_c": nu_c, "coarse_steps": coarse_steps}
+
+
+def coarse_run(closure: str, ref: Dict, params=None, stats=None, c_nu: float = None) -> Dict:
+    """Coarse LES of `closure` from ref's initial state: E(k) relative L2 error
+    over the resolved shells against the filtered fine run, E_k, dissipation."""
+    nc = ref["f0"].shape[-1]
+    kw = {} if c_nu is None else {"c_nu": c_nu}
+    with lbm.Solver(27, (nc,) * 3, ref["nu_c"], closure=closure, storage="fp32", **kw) as s:
+        if closure == "learned":
+            s.set_learned_closure(params, stats)
+        s.set_populations(ref["f0"])
+        s.step(ref["coarse_steps"])
+        u = _velocity(s)
+    e = spectrum(u)
+    ek = float(0.5 * (u ** 2).sum(0).mean())
+    kmax = nc // 2
+    e_ref = ref["spectrum"]
+    err = torch.sqrt(((e[1:kmax] - e_ref[1:kmax]) ** 2).sum() / (e_ref[1:kmax] ** 2).sum())
+    return {"spectrum_rel_l2": float(err), "E_k": ek, "dissipation": (ref["E_k0"] - ek) / ref["coarse_steps"]}
+
+
+def calibrate_c_nu(closure: str, ref: Dict, params=None, stats=None, lo: float = 1e-3, hi: float = 0.5,
+                   iters: int = 14) -> float:
+    """C_nu whose coarse run dissipates as the filtered fine run over the window
+    (bisection in log C_nu; the dissipation grows with C_nu); clamped to [lo, hi]."""
+    target = ref["dissipation"]
+    if coarse_run(closure, ref, params, stats, lo)["dissipation"] >= target:
+        return lo
+    if coarse_run(closure, ref, params, stats, hi)["dissipation"] <= target:
+        return hi
+    a, b = math.log(lo), math.log(hi)
+    for _ in range(iters):
+        m = 0.5 * (a + b)
+        if coarse_run(closure, ref, params, stats, math.exp(m))["dissipation"] < target:
+            a = m
+        else:
+            b = m
+    return math.exp(0.5 * (a + b))
+
+
 def a_posteriori(params, stats, n_fine: int = 512, factor: int = 4, k0: float = 4.0, seed: int = 99,
                  nu_fine: float = 1e-4, urms: float = 0.04, t0: int = 400, coarse_steps: int = 100,
                  closures=("kcmp", "learned", "bgk")) -> Dict:
@@ -303,6 +364,15 @@ def main(argv=None) -> Dict:
     apr = a_priori(res["params"], stats, Xh, Th, KCh)
     post = a_posteriori(res["params"], stats, n_fine=a.n_fine, factor=a.factor, t0=a.t0, coarse_steps=a.coarse_steps,
                         nu_fine=nu_fine)
+    # C_nu calibrated per closure on a training seed (dissipation of its filtered
+    # fine run), then both closures evaluated on the evaluation seed
+    cal_ref = filtered_reference(a.n_fine, a.factor, 4.0, ints(a.train_seeds)[0], nu_fine, 0.04, a.t0, a.coarse_steps)
+    cal = {cl: calibrate_c_nu(cl, cal_ref, res["params"], stats) for cl in ("kcmp", "learned")}
+    ev_ref = filtered_reference(a.n_fine, a.factor, 4.0, 99, nu_fine, 0.04, a.t0, a.coarse_steps)
+    calibrated = {"c_nu": cal, "evaluation_filtered_fine": {"E_k": ev_ref["E_k"], "dissipation": ev_ref["dissipation"]}}
+    for cl in ("kcmp", "learned"):
+        calibrated[cl] = coarse_run(cl, ev_ref, res["params"], stats, cal[cl])
+    calibrated["bgk"] = coarse_run("bgk", ev_ref)
     os.makedirs(os.path.dirname(a.out), exist_ok=True)
     np.savez(a.out, params=res["params"], stats=stats, n_fine=a.n_fine, factor=a.factor, nu_fine=nu_fine,
              nu_coarse=nu_fine / a.factor)
@@ -312,6 +382,7 @@ def main(argv=None) -> Dict:
         mlups[f"{n}^3"] = {cl: _mlups(cl, n, nu_c, res["params"], stats) for cl in ("kcmp", "learned")}
     out = {"samples_train": int(X.shape[0]), "samples_test": int(Xh.shape[0]), "t_data_s": t_data,
            "t_train_s": t_train, "loss_history": res["history"], "a_priori_heldout": apr, "a_posteriori": post,
+           "a_posteriori_calibrated": calibrated,
            "mlups": mlups, "checkpoint": os.path.relpath(a.out, os.path.dirname(os.path.dirname(__file__))),
            "config": vars(a)}
     print(json.dumps(out), flush=True)

@@ -37,6 +37,7 @@ WORKLOADS = {
     "hit512_d3q27_bf16_kcmp": dict(n=512, q=27, storage="bf16", closure="kcmp", nu=1e-4, k0=4.0, urms=0.04),
     "hit512_d3q19_fp32_kcmp": dict(n=512, q=19, storage="fp32", closure="kcmp", nu=1e-4, k0=4.0, urms=0.04),
     "hit512_d3q27_fp32_bgk": dict(n=512, q=27, storage="fp32", closure="bgk", nu=1e-4, k0=4.0, urms=0.04),
+    "hit512_d3q27_fp32_kcrr": dict(n=512, q=27, storage="fp32", closure="kcrr", nu=1e-4, k0=4.0, urms=0.04),
     # learned closure (KC-MP with the network's m_sgs, fused BF16 tensor-core inference)
     "hit256_d3q27_fp32_learned": dict(n=256, q=27, storage="fp32", closure="learned", nu=2.5e-5, k0=4.0, urms=0.04),
     "hit128_d3q27_fp32_learned": dict(n=128, q=27, storage="fp32", closure="learned", nu=2.5e-5, k0=4.0, urms=0.04),
@@ -172,8 +173,9 @@ def oracle_sample(wl: dict):
 
     oracle.build()
     # the learned closure's CPU stand-in is the analytic KC-MP it extends
-    cl = {"bgk": 0, "kcmp": 1, "kcrb_hermite": 2, "kcrb_raw": 3, "learned": 1}[wl["closure"]]
-    cnu = {"bgk": 0.0, "kcmp": 0.035, "kcrb_hermite": 0.02, "kcrb_raw": 0.02, "learned": 0.035}[wl["closure"]]
+    cl = {"bgk": 0, "kcmp": 1, "kcrb_hermite": 2, "kcrb_raw": 3, "kcrr": 4, "learned": 1}[wl["closure"]]
+    cnu = {"bgk": 0.0, "kcmp": 0.035, "kcrb_hermite": 0.02, "kcrb_raw": 0.02, "kcrr": 0.02,
+           "learned": 0.035}[wl["closure"]]
     bc, F = (0, 0, 0), (0.0, 0.0, 0.0)
     if "u_bulk" in wl:
         shape = (CPU_SAMPLE_N, CPU_SAMPLE_N // 2, CPU_SAMPLE_N // 2)

@@ -312,12 +312,13 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
         cfg->variant != VAR_PAIR && cfg->variant != VAR_SPLIT_PF)
         return fail(LBM_ERR_ARG, "unknown kernel variant");
     int variant = cfg->variant;
-    // measured defaults: the split-barrier pull for periodic D3Q27 boxes with BGK
-    // or a closure carrier (KC-MP, KC-RB), the register pull elsewhere;
-    // lbm_autotune may pick another variant for a given box
+    // measured defaults: the split-barrier pull for periodic D3Q27 boxes with BGK,
+    // KC-MP, KC-RB or KC-RR, the register pull elsewhere; lbm_autotune may pick
+    // another variant for a given box
     if (variant == VAR_DEFAULT) {
         const bool split_built = cfg->closure == LBM_BGK || cfg->closure == LBM_KCMP ||
-                                 cfg->closure == LBM_KCRB_HERMITE || cfg->closure == LBM_KCRB_RAW;
+                                 cfg->closure == LBM_KCRB_HERMITE || cfg->closure == LBM_KCRB_RAW ||
+                                 cfg->closure == LBM_KCRR;
         variant = (cfg->lattice == LBM_D3Q27 && split_built && bc_kind == BC_PERIODIC &&
                    step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, VAR_SPLIT))
                       ? VAR_SPLIT

@@ -262,8 +262,6 @@ __host__ __device__ constexpr int rr_axis(int m, int k)  // k-th axis of mode m 
 {
     return k < rr_deg(m, 0) ? 0 : (k < rr_deg(m, 0) + rr_deg(m, 1) ? 1 : 2);
 }
-// directional Hermite factor H(c, deg): 1, c, c^2 - theta
-__host__ __device__ constexpr double hdir(int c, int deg) { return deg == 0 ? 1.0 : (deg == 1 ? c : c * c - kTheta); }
 
 template <typename R, int M>
 __device__ __forceinline__ R rr_coef(const R (&u)[3], const R (&A)[3][3])
@@ -287,105 +285,110 @@ __device__ __forceinline__ R rr_coef(const R (&u)[3], const R (&A)[3][3])
     return a;
 }
 
-// KC-RR collision of one D3Q27 cell on shifted populations (in place).
+// One axis of the separable D3Q27 Hermite transform, in place on the 9 lines
+// of stride ST (1: x, 3: y, 9: z) of a [z][y][x] block of 27 values.
+// Forward: (v(-1), v(0), v(+1)) -> (sum v, sum v c, sum v (c^2 - theta)).
+// Inverse: raw coefficients (K0, K1, K2) -> sum_d K_d N_d H_d(c) at c = -1, 0, +1
+// with H = (1, c, c^2 - theta) and N = (1, 1/theta, 1/(2 theta^2)) = (1, 3, 9/2),
+// i.e. K0 - 3/2 K2 at c = 0 and K0 + 3 K2 -+ 3 K1 at c = -+1.
+template <typename R, int ST, bool INV>
+__device__ __forceinline__ void herm_axis(R (&v)[27])
+{
+#pragma unroll
+    for (int l = 0; l < 9; ++l) {
+        const int o = ST == 1 ? 3 * l : (ST == 3 ? 9 * (l / 3) + l % 3 : l);
+        R& a = v[o];
+        R& b = v[o + ST];
+        R& c = v[o + 2 * ST];
+        if constexpr (!INV) {
+            const R p = a + c;
+            const R s0 = p + b;
+            const R s1 = c - a;
+            c = p - R(kTheta) * s0;
+            a = s0;
+            b = s1;
+        } else {
+            const R t = a - R(1.5) * c;
+            const R p = t + R(4.5) * c;
+            const R k1 = R(3) * b;
+            a = p - k1;
+            c = p + k1;
+            b = t;
+        }
+    }
+}
+
+// KC-RR collision of one D3Q27 cell on shifted populations (in place), in
+// Hermite moment space.  D3Q27 is the tensor product of three 3-point lattices
+// and its 27 Hermite polynomials are products of per-axis factors (1, c,
+// c^2 - theta), so the projection onto all 27 modes and the reconstruction
+// f = w sum_d K_d N_d H_d are three 1D passes each.  The product equilibrium
+// has the coefficients E_d = rho ux^dx uy^dy uz^dz, so f_neq's coefficients
+// are M_d - E_d (the shifted populations g = f - w have f's coefficients
+// except d = 0, since sum_i w_i H_d = 0 for d != 0).  Relaxation as App. F.4:
+// second order (1 - omega) m_CE + (1 - omega_s)(m_neq - m_CE), the 17
+// high-order modes (1 - omega) a_rr + (1 - omega_s)(a_neq - a_rr), orders 0
+// and 1 kept (rho - 1, rho u).
 template <typename R>
 __device__ __forceinline__ void collide_kcrr(R (&g)[27], R drho, R ux, R uy, R uz, R Sxx, R Syy, R Szz, R Sxy, R Sxz,
                                              R Syz, R omega, R tau_hat, R nu, R cnud)
 {
     constexpr int Q = 27;
-    constexpr R th = R(kTheta);
     const R rho = R(1) + drho;
-    constexpr R a1 = R(1.0 / kTheta), a2 = R((1.0 - kTheta) / (2.0 * kTheta * kTheta)),
-                a0 = R(-kTheta / (2.0 * kTheta * kTheta));
-    const R ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
-    const R ex[3] = {-a1 * ux + a2 * ux2, a0 * ux2, a1 * ux + a2 * ux2};
-    const R ey[3] = {-a1 * uy + a2 * uy2, a0 * uy2, a1 * uy + a2 * uy2};
-    const R ez[3] = {-a1 * uz + a2 * uz2, a0 * uz2, a1 * uz + a2 * uz2};
-    R geq[27], fneq[27];
-    static_for<Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
-        constexpr R w = R(weight_of(Q, i));
-        const R Y = ey[cy + 1] + ez[cz + 1] + ey[cy + 1] * ez[cz + 1];
-        geq[i] = w * (rho * (ex[cx + 1] + Y + ex[cx + 1] * Y) + drho);
-        fneq[i] = g[i] - geq[i];
-    });
-    // second order: m_neq, m_CE = -2 rho theta tau_hat S, a_sgs = m_neq - m_CE, rate from its trace
-    R mn[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    static_for<Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        constexpr int c[3] = {cx_of(Q, i), cy_of(Q, i), cz_of(Q, i)};
+    herm_axis<R, 1, false>(g);
+    herm_axis<R, 3, false>(g);
+    herm_axis<R, 9, false>(g);  // g[9 dz + 3 dy + dx] = M_d
+    const R rx[3] = {rho, rho * ux, rho * (ux * ux)};
+    const R py[3] = {R(1), uy, uy * uy};
+    const R pz[3] = {R(1), uz, uz * uz};
+    R E[27];
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
+    for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
-            for (int b = a; b < 3; ++b)
-                if (c[a] * c[b] != 0) mn[a][b] += R(c[a] * c[b]) * fneq[i];
-    });
+        for (int dy = 0; dy < 3; ++dy) {
+            const R yz = dy == 0 ? pz[dz] : (dz == 0 ? py[dy] : py[dy] * pz[dz]);
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) E[9 * dz + 3 * dy + dx] = (dy == 0 && dz == 0) ? rx[dx] : rx[dx] * yz;
+        }
+    // second order: m_neq, m_CE = -2 rho theta tau_hat S, rate from tr(m_neq - m_CE)
+    constexpr int i2[3][3] = {{2, 4, 10}, {4, 6, 12}, {10, 12, 18}};
     const R Sm[3][3] = {{Sxx, Sxy, Sxz}, {Sxy, Syy, Syz}, {Sxz, Syz, Szz}};
-    R A[3][3], a2p[3][3];
-    const R rt = R(-2) * rho * th * tau_hat;
+    const R rt = R(-2) * rho * R(kTheta) * tau_hat;
+    R A[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) A[a][b] = rt * Sm[a][b];
     R tr = 0;
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            A[a][b] = rt * Sm[a][b];
-            if (b < a) mn[a][b] = mn[b][a];
-        }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) tr += mn[a][a] - A[a][a];
+    for (int a = 0; a < 3; ++a) tr += (g[i2[a][a]] - E[i2[a][a]]) - A[a][a];
     const R omega_s = omega_sgs(tr, nu, omega, cnud);
+    const R om1 = R(1) - omega, os1 = R(1) - omega_s;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) a2p[a][b] = (R(1) - omega) * A[a][b] + (R(1) - omega_s) * (mn[a][b] - A[a][b]);
-    // high order: project f_neq, RR reference (divided by rho: the recursion's a0/rho), two-rate relaxation
+        for (int b = a; b < 3; ++b) {
+            const int d = i2[a][b];
+            g[d] = E[d] + om1 * A[a][b] + os1 * ((g[d] - E[d]) - A[a][b]);
+        }
+    // high order: recursive-regularised reference from m_CE, two-rate relaxation
     const R uu[3] = {ux, uy, uz};
-    R Ar[3][3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) Ar[a][b] = A[a][b];
-    R ap[17];
     static_for<17>([&](auto MI) {
         constexpr int m = decltype(MI)::value;
-        R an = 0;
-        static_for<Q>([&](auto I) {
-            constexpr int i = decltype(I)::value;
-            constexpr R h = R(hdir(cx_of(Q, i), rr_deg(m, 0)) * hdir(cy_of(Q, i), rr_deg(m, 1)) *
-                              hdir(cz_of(Q, i), rr_deg(m, 2)));
-            if (h != R(0)) an += h * fneq[i];
-        });
-        const R ar = rr_coef<R, m>(uu, Ar);
-        ap[m] = (R(1) - omega) * ar + (R(1) - omega_s) * (an - ar);
+        constexpr int d = 9 * rr_deg(m, 2) + 3 * rr_deg(m, 1) + rr_deg(m, 0);
+        const R ar = rr_coef<R, m>(uu, A);
+        g[d] = E[d] + om1 * ar + os1 * ((g[d] - E[d]) - ar);
     });
-    // reconstruction, Eq. (kcrr_operational_post_population): f_post = f0 + w sum_m T_m
+    g[0] = drho;
+    g[1] = E[1];
+    g[3] = E[3];
+    g[9] = E[9];
+    herm_axis<R, 9, true>(g);
+    herm_axis<R, 3, true>(g);
+    herm_axis<R, 1, true>(g);
     static_for<Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        constexpr int c[3] = {cx_of(Q, i), cy_of(Q, i), cz_of(Q, i)};
-        constexpr R w = R(weight_of(Q, i));
-        R t2 = 0;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) t2 += R(hdir(c[a], 2)) * a2p[a][a] * R(1.0 / (2.0 * kTheta * kTheta));
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = a + 1; b < 3; ++b)
-                if (c[a] * c[b] != 0) t2 += R(c[a] * c[b]) * a2p[a][b] * R(1.0 / (kTheta * kTheta));
-        R th_ = 0;
-        static_for<17>([&](auto MI) {
-            constexpr int m = decltype(MI)::value;
-            constexpr double h = hdir(c[0], rr_deg(m, 0)) * hdir(c[1], rr_deg(m, 1)) * hdir(c[2], rr_deg(m, 2));
-            constexpr double fact = (rr_deg(m, 0) == 2 ? 2.0 : 1.0) * (rr_deg(m, 1) == 2 ? 2.0 : 1.0) *
-                                    (rr_deg(m, 2) == 2 ? 2.0 : 1.0);
-            constexpr double thn = rr_n(m) == 3 ? kTheta * kTheta * kTheta
-                                                : (rr_n(m) == 4 ? kTheta * kTheta * kTheta * kTheta
-                                                                : (rr_n(m) == 5 ? kTheta * kTheta * kTheta * kTheta * kTheta
-                                                                                : kTheta * kTheta * kTheta * kTheta *
-                                                                                      kTheta * kTheta));
-            if constexpr (h != 0.0) th_ += R(h / (fact * thn)) * ap[m];
-        });
-        g[i] = geq[i] + w * (t2 + th_);
+        g[i] *= R(weight_of(Q, i));
     });
 }
 

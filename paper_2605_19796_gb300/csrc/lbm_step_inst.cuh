@@ -48,6 +48,9 @@ cudaError_t launch_step_qs(int closure, int bc, int ty, int variant, const StepA
         LBM_SB_CASE(CL_KCRB_RAW, BC_PERIODIC, 8)
         LBM_SB_CASE(CL_BGK, BC_WALLS_Y, 8)
         LBM_SB_CASE(CL_KCMP, BC_WALLS_Y, 8)
+        if constexpr (Q == 27) {
+            LBM_SB_CASE(CL_KCRR, BC_PERIODIC, 8)
+        }
         if constexpr (R32) {
             LBM_SB_CASE(CL_KCMP, BC_PERIODIC, 4)
             LBM_SB_CASE(CL_KCMP, BC_PERIODIC, 16)
@@ -65,6 +68,9 @@ cudaError_t launch_step_qs(int closure, int bc, int ty, int variant, const StepA
         LBM_SBP_CASE(CL_KCRB_RAW, BC_PERIODIC, 8)
         LBM_SBP_CASE(CL_BGK, BC_WALLS_Y, 8)
         LBM_SBP_CASE(CL_KCMP, BC_WALLS_Y, 8)
+        if constexpr (Q == 27) {
+            LBM_SBP_CASE(CL_KCRR, BC_PERIODIC, 8)
+        }
 #undef LBM_SBP_CASE
         return cudaErrorNotSupported;
     }

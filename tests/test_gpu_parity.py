@@ -37,8 +37,8 @@ def rel(a, b):
     return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
 
 
-CL = {"bgk": 0, "kcmp": 1, "kcrb_hermite": 2, "kcrb_raw": 3}
-CNU = {"bgk": 0.0, "kcmp": 0.035, "kcrb_hermite": 0.02, "kcrb_raw": 0.02}
+CL = {"bgk": 0, "kcmp": 1, "kcrb_hermite": 2, "kcrb_raw": 3, "kcrr": 4}
+CNU = {"bgk": 0.0, "kcmp": 0.035, "kcrb_hermite": 0.02, "kcrb_raw": 0.02, "kcrr": 0.02}
 
 
 def _run_pair(lbm, orc, q, shape, rho, u, nu, closure, steps, storage="fp64", bc=(0, 0, 0), F=(0.0, 0.0, 0.0),
@@ -424,11 +424,11 @@ def test_tma_variant_matches(lbm, orc, shape, nbatch, closure):
 
 def test_default_variant_selection(lbm):
     """Library default: the split-barrier pull (8) for periodic D3Q27 with BGK,
-    KC-MP or KC-RB, the register pull (1) for D3Q19, walls, KC-RR and the
+    KC-MP, KC-RB or KC-RR, the register pull (1) for D3Q19, walls and the
     learned closure; an explicitly requested variant that is not built for a
     box is refused."""
     for q, closure, storage, want in ((27, "kcmp", "fp32", 8), (27, "kcrb_hermite", "fp16", 8), (27, "kcmp", "fp64", 8),
-                                      (27, "bgk", "fp32", 8), (19, "kcmp", "fp32", 1), (27, "kcrr", "fp64", 1),
+                                      (27, "bgk", "fp32", 8), (19, "kcmp", "fp32", 1), (27, "kcrr", "fp64", 8),
                                       (27, "learned", "fp32", 1)):
         with lbm.Solver(q, (40, 32, 16), 1e-4, closure=closure, storage=storage) as s:
             assert s.launch_config["variant"] == want, (q, closure, storage)
@@ -472,12 +472,12 @@ def test_kcrr_fp32_velocity(lbm, orc):
 
 
 @pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16", "bf16"])
-@pytest.mark.parametrize("closure", ["bgk", "kcmp", "kcrb_hermite", "kcrb_raw"])
+@pytest.mark.parametrize("closure", ["bgk", "kcmp", "kcrb_hermite", "kcrb_raw", "kcrr"])
 def test_load_schedule_variants(lbm, orc, storage, closure):
     """Variant 8 (halo and own loads together, split arrive/wait barrier) only
     reschedules the loads and synchronisation of the register pull (variant 1);
-    variant 9 runs the same arithmetic on packed FP32 pairs, two cells per
-    thread.  On a ragged box with
+    variant 12 adds L2 prefetches to it; variant 9 runs the same arithmetic on
+    packed FP32 pairs, two cells per thread (not built for KC-RR).  On a ragged box with
     two boxes and several z-chunkings (one and two planes per CTA exercise the
     pipelines' start and drain): FP64 matches the oracle to 1e-12, FP32 matches
     variant 1 to FP32 rounding, 16-bit storage in rho and u to 1e-5 (one 16-bit
@@ -487,7 +487,7 @@ def test_load_schedule_variants(lbm, orc, storage, closure):
     rho = np.stack([f[0] for f in fields])
     u = np.stack([f[1] for f in fields], axis=1)
     nus = np.array([2e-5, 1e-4])
-    variants = (8, 12) if storage == "fp64" else (8, 9, 12)
+    variants = (8, 12) if storage == "fp64" or closure == "kcrr" else (8, 9, 12)
     res = {}
     for var, zc in [(1, 0)] + [(v, z) for v in variants for z in (0, 1, 2, 5)]:
         with lbm.Solver(27, shape, nus, closure=closure, storage=storage, variant=var, zchunk=zc, nbatch=2) as s:

@@ -362,15 +362,21 @@ void mlp_pack(const float* params, const float* stats, unsigned char* out)
 {
     using L = MlpLayout;
     std::memset(out, 0, L::BYTES);
+    // hidden layers (l < 3) times 1/2: the inference evaluates SiLU(a) as
+    // h + h tanh(h) on h = a/2 straight from the accumulator (a power of two,
+    // so the scaled BF16 weight is the scaled rounded weight)
     auto putw = [&](int off, int ld, int l) {
         __nv_bfloat16* W = reinterpret_cast<__nv_bfloat16*>(out + off);
         const float* src = params + w_off(l);
+        const float sc = l < 3 ? 0.5f : 1.0f;
         for (int o = 0; o < layer_out(l); ++o)
-            for (int k = 0; k < layer_in(l); ++k) W[o * ld + k] = __float2bfloat16_rn(src[o * layer_in(l) + k]);
+            for (int k = 0; k < layer_in(l); ++k)
+                W[o * ld + k] = __float2bfloat16_rn(sc * src[o * layer_in(l) + k]);
     };
     auto putb = [&](int off, int l) {
         float* B = reinterpret_cast<float*>(out + off);
-        for (int o = 0; o < layer_out(l); ++o) B[o] = params[b_off(l) + o];
+        const float sc = l < 3 ? 0.5f : 1.0f;
+        for (int o = 0; o < layer_out(l); ++o) B[o] = sc * params[b_off(l) + o];
     };
     putw(L::W1, L::LD1, 0);
     putw(L::W2, L::LD, 1);

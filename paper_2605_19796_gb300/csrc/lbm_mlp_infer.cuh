@@ -13,7 +13,8 @@
 //   W1 [64][24] bf16 (inputs 10, zero padded; row pitch 24 keeps the B-fragment
 //   loads bank-conflict free), W2, W3 [64][72] bf16, W4 [8][72] bf16 (rows 6, 7
 //   zero), biases b1 b2 b3 [64] f32, b4 [8] f32, input mean [10], input 1/std
-//   [10], output mean [6], output std [6] (f32, padded to 48).
+//   [10], output mean [6], output std [6] (f32, padded to 48).  W1..W3 and
+//   b1..b3 are stored times 1/2 (the SiLU's half argument, below).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -59,9 +60,11 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
-// SiLU a * sigmoid(a) through sigmoid(a) = (1 + tanh(a / 2)) / 2 on the
-// hardware tanh (one MUFU operation, relative error about 2^-11, below the BF16
-// rounding that follows)
+// SiLU a * sigmoid(a) = h + h tanh(h), h = a / 2, on the hardware tanh (one
+// MUFU operation, relative error about 2^-11, below the BF16 rounding that
+// follows).  The hidden layers' weights and biases are packed times 1/2 (exact
+// in BF16 and FP32), so the accumulator already holds h; the two columns of a
+// fragment row take one packed FP32 FMA.
 __device__ __forceinline__ float mlp_tanh(float v)
 {
     float r;
@@ -69,33 +72,70 @@ __device__ __forceinline__ float mlp_tanh(float v)
     return r;
 }
 
-__device__ __forceinline__ float mlp_silu(float a)
+__device__ __forceinline__ uint32_t mlp_silu_pack(float h0, float h1)
 {
-    const float h = 0.5f * a;
-    return fmaf(h, mlp_tanh(h), h);
+    const float2 h = make_float2(h0, h1);
+    const float2 y = __ffma2_rn(h, make_float2(mlp_tanh(h0), mlp_tanh(h1)), h);
+    return pack_bf16(y.x, y.y);
+}
+
+// B fragments of the m16n8k16 products from the packed [n][k] weight rows with
+// ldmatrix: 8x8 BF16 matrices whose rows are output units n and whose columns
+// are 8 consecutive inputs k, so lane l receives W[n0 + l/4][k0 + 2(l%4) ..+1],
+// the fragment layout of the "col" B operand.  x2: matrices at k0 = 16 s and
+// 16 s + 8 (one k-step, b0 and b1); x4: two k-steps.  Lane l gives the address
+// of row l%8 of matrix l/8.  Row pitches of 48 and 144 bytes keep the 16-byte
+// rows 16-byte aligned and the eight rows of a matrix on distinct banks.  The
+// hidden layers take x2 loads (x4 raises the register peak of the fused step
+// kernel past its 128-register budget), the output layer x4.
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t (&r)[4])
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t& r0, uint32_t& r1)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+
+// shared-memory address of this lane's ldmatrix row: output row n0 + lane%8,
+// input column k0 + 8 (lane/8) (x4: two k-steps; x2 uses lanes 0-15)
+template <int LDW>
+__device__ __forceinline__ uint32_t ldsm_row(uint32_t wbase, int n0, int k0, int lane)
+{
+    return wbase + (uint32_t)(((n0 + (lane & 7)) * LDW + k0 + 8 * (lane >> 3)) * 2);
 }
 
 // One hidden layer (64 outputs) for one 16-row tile: A fragments of the input
 // (KS k-steps) -> A fragments of the output (4 k-steps of the next layer).
+// The accumulators start at the bias.
 template <int KS, int LDW>
 __device__ __forceinline__ void mlp_hidden(const unsigned char* sm, int woff, int boff, const uint32_t (&ain)[KS][4],
-                                           uint32_t (&aout)[4][4], int g, int t)
+                                           uint32_t (&aout)[4][4], int lane)
 {
-    const uint32_t* W = reinterpret_cast<const uint32_t*>(sm + woff);
-    const float* B = reinterpret_cast<const float*>(sm + boff);
+    const int t = lane & 3;
+    const uint32_t wbase = (uint32_t)__cvta_generic_to_shared(sm + woff);
+    const float2* B = reinterpret_cast<const float2*>(sm + boff);
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
-        float c[4] = {0.f, 0.f, 0.f, 0.f};
-        const int row = 8 * nt + g;
+        const float2 bb = B[4 * nt + t];  // columns 8 nt + 2t, 8 nt + 2t + 1
+        float c[4] = {bb.x, bb.y, bb.x, bb.y};
+        if constexpr (KS == 1) {
+            uint32_t b0, b1;
+            ldsm_x2(ldsm_row<LDW>(wbase, 8 * nt, 0, lane & 15), b0, b1);
+            mma_bf16_16816(c, ain[0], b0, b1);
+        } else {
 #pragma unroll
-        for (int s = 0; s < KS; ++s) {
-            const uint32_t b0 = W[(row * LDW + 16 * s + 2 * t) / 2];
-            const uint32_t b1 = W[(row * LDW + 16 * s + 2 * t + 8) / 2];
-            mma_bf16_16816(c, ain[s], b0, b1);
+            for (int s = 0; s < KS; ++s) {
+                uint32_t b0, b1;
+                ldsm_x2(ldsm_row<LDW>(wbase, 8 * nt, 16 * s, lane & 15), b0, b1);
+                mma_bf16_16816(c, ain[s], b0, b1);
+            }
         }
-        const float bb0 = B[8 * nt + 2 * t], bb1 = B[8 * nt + 2 * t + 1];
-        const uint32_t lo = pack_bf16(mlp_silu(c[0] + bb0), mlp_silu(c[1] + bb1));  // row g
-        const uint32_t hi = pack_bf16(mlp_silu(c[2] + bb0), mlp_silu(c[3] + bb1));  // row g + 8
+        const uint32_t lo = mlp_silu_pack(c[0], c[1]);  // row g
+        const uint32_t hi = mlp_silu_pack(c[2], c[3]);  // row g + 8
         if (nt & 1) {
             aout[nt >> 1][2] = lo;
             aout[nt >> 1][3] = hi;
@@ -114,6 +154,8 @@ __device__ __forceinline__ void mlp_warp_forward(const unsigned char* sm, const 
     using L = MlpLayout;
     const int g = lane >> 2, t = lane & 3;
     const uint32_t* Xw = reinterpret_cast<const uint32_t*>(X);
+    const uint32_t w4 = (uint32_t)__cvta_generic_to_shared(sm + L::W4);
+    const float2 b4 = reinterpret_cast<const float2*>(sm + L::B4)[t];
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt) {
         const int r0 = 16 * mt + g, r1 = r0 + 8;
@@ -123,24 +165,21 @@ __device__ __forceinline__ void mlp_warp_forward(const unsigned char* sm, const 
         a0[0][2] = Xw[(r0 * L::XLD + 2 * t + 8) / 2];
         a0[0][3] = Xw[(r1 * L::XLD + 2 * t + 8) / 2];
         uint32_t h1[4][4], h2[4][4];
-        mlp_hidden<1, L::LD1>(sm, L::W1, L::B1, a0, h1, g, t);
-        mlp_hidden<4, L::LD>(sm, L::W2, L::B2, h1, h2, g, t);
-        mlp_hidden<4, L::LD>(sm, L::W3, L::B3, h2, h1, g, t);
+        mlp_hidden<1, L::LD1>(sm, L::W1, L::B1, a0, h1, lane);
+        mlp_hidden<4, L::LD>(sm, L::W2, L::B2, h1, h2, lane);
+        mlp_hidden<4, L::LD>(sm, L::W3, L::B3, h2, h1, lane);
         // output layer: one 8-column tile, no activation
-        const uint32_t* W = reinterpret_cast<const uint32_t*>(sm + L::W4);
-        const float* B = reinterpret_cast<const float*>(sm + L::B4);
-        float c[4] = {0.f, 0.f, 0.f, 0.f};
+        float c[4] = {b4.x, b4.y, b4.x, b4.y};
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            const uint32_t b0 = W[(g * L::LD + 16 * s + 2 * t) / 2];
-            const uint32_t b1 = W[(g * L::LD + 16 * s + 2 * t + 8) / 2];
-            mma_bf16_16816(c, h1[s], b0, b1);
+        for (int sp = 0; sp < 2; ++sp) {
+            uint32_t b[4];
+            ldsm_x4(ldsm_row<L::LD>(w4, 0, 32 * sp, lane), b);
+            mma_bf16_16816(c, h1[2 * sp], b[0], b[1]);
+            mma_bf16_16816(c, h1[2 * sp + 1], b[2], b[3]);
         }
         __syncwarp();  // every lane has read this tile's inputs
-        Y[r0 * 8 + 2 * t] = c[0] + B[2 * t];
-        Y[r0 * 8 + 2 * t + 1] = c[1] + B[2 * t + 1];
-        Y[r1 * 8 + 2 * t] = c[2] + B[2 * t];
-        Y[r1 * 8 + 2 * t + 1] = c[3] + B[2 * t + 1];
+        *reinterpret_cast<float2*>(Y + r0 * 8 + 2 * t) = make_float2(c[0], c[1]);
+        *reinterpret_cast<float2*>(Y + r1 * 8 + 2 * t) = make_float2(c[2], c[3]);
     }
 }
 

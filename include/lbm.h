@@ -101,17 +101,20 @@ typedef struct {
     int tile_y;         /* tuning: rows per CTA tile (0 = library default)           */
     int zchunk;         /* tuning: z-planes per CTA march (0 = library default)      */
     int variant;        /* tuning: step-kernel variant, 0 = library default
-                           (8 for periodic D3Q27 with BGK, KC-MP or KC-RB,
-                           else 1),
+                           (periodic D3Q27: 13 for FP32 storage with KC-MP,
+                           KC-RB or KC-RR, 8 for BGK, FP64 and 16-bit
+                           storage; else 1),
                            1 = register pull (every lattice, storage, closure
                            and boundary), 4 = TMA-staged pipeline (FP32,
                            periodic, BGK/KC-MP/KC-RB, nx % 32 == 0 and
                            ny % tile_y == 0), 8 = register pull with a split
-                           arrive/wait barrier (BGK, KC-MP, KC-RB), 9 = two
-                           cells per thread on packed FP32 pairs (32-bit
+                           arrive/wait barrier (BGK, KC-MP, KC-RB, KC-RR), 9 =
+                           two cells per thread on packed FP32 pairs (32-bit
                            arithmetic, BGK, KC-MP, KC-RB), 12 = 8 with the
                            source rows of the plane after next prefetched
-                           into L2; other values: LBM_ERR_ARG                 */
+                           into L2, 13 = 8 with the own cell's pulls copied
+                           to shared memory by cp.async one plane ahead
+                           (FP32 and FP64 storage); other values: LBM_ERR_ARG */
     int disable_graphs; /* nonzero: lbm_step launches kernels one by one instead of
                            replaying a captured CUDA graph                        */
 } lbm_config;

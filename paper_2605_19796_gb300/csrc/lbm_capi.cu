@@ -309,12 +309,14 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
         return fail(LBM_ERR_UNSUPPORTED, "a body force is supported with bounce-back walls (channel) only");
     int tile_y = cfg->tile_y ? cfg->tile_y : 8;
     if (cfg->variant != VAR_DEFAULT && cfg->variant != VAR_REGISTER && cfg->variant != VAR_TMA && cfg->variant != VAR_SPLIT &&
-        cfg->variant != VAR_PAIR && cfg->variant != VAR_SPLIT_PF)
+        cfg->variant != VAR_PAIR && cfg->variant != VAR_SPLIT_PF && cfg->variant != VAR_ASYNC)
         return fail(LBM_ERR_ARG, "unknown kernel variant");
     int variant = cfg->variant;
-    // measured defaults: the split-barrier pull for periodic D3Q27 boxes with BGK,
-    // KC-MP, KC-RB or KC-RR, the register pull elsewhere; lbm_autotune may pick
-    // another variant for a given box
+    // measured defaults for periodic D3Q27 boxes: the split-barrier pull with the
+    // own pulls copied asynchronously (13) for FP32 storage and a closure carrier
+    // (KC-MP, KC-RB, KC-RR), the split-barrier pull (8) for BGK, FP64 and 16-bit
+    // storage; the register pull elsewhere.  lbm_autotune may pick another
+    // variant for a given box
     if (variant == VAR_DEFAULT) {
         const bool split_built = cfg->closure == LBM_BGK || cfg->closure == LBM_KCMP ||
                                  cfg->closure == LBM_KCRB_HERMITE || cfg->closure == LBM_KCRB_RAW ||
@@ -323,6 +325,9 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
                    step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, VAR_SPLIT))
                       ? VAR_SPLIT
                       : VAR_REGISTER;
+        if (variant == VAR_SPLIT && cfg->closure != LBM_BGK && cfg->storage == LBM_FP32 &&
+            step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, VAR_ASYNC))
+            variant = VAR_ASYNC;
     }
     if (variant == VAR_TMA && !tma_shape_ok(cfg->nx, cfg->ny, tile_y))
         return fail(LBM_ERR_UNSUPPORTED, "the TMA variant needs nx % 32 == 0 and ny % tile_y == 0");
@@ -474,7 +479,7 @@ int lbm_autotune(lbm_handle* h, int trials)
 {
     if (int rc = check_handle(h)) return rc;
     if (trials < 1) trials = 3;
-    static const int kVariants[] = {VAR_REGISTER, VAR_SPLIT, VAR_SPLIT_PF, VAR_PAIR, VAR_TMA};
+    static const int kVariants[] = {VAR_REGISTER, VAR_SPLIT, VAR_SPLIT_PF, VAR_ASYNC, VAR_PAIR, VAR_TMA};
     static const int kTiles[] = {4, 8, 16};
     static const int kChunks[] = {8, 16, 32, 64, 128};
     const int v0 = h->variant, t0 = h->tile_y, z0 = h->zchunk;

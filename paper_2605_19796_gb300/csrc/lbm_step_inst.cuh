@@ -5,7 +5,9 @@
 //
 // Variants: 1 register pull (step_kernel, every closure and storage), 4 TMA
 // staging (FP32, periodic), 8 split arrive/wait barrier (step_kernel_sb), 9
-// two cells per thread on packed FP32 pairs (step_kernel_x2, 32-bit arithmetic).
+// two cells per thread on packed FP32 pairs (step_kernel_x2, 32-bit arithmetic),
+// 12 variant 8 with L2 prefetches, 13 variant 8 with the own pulls copied to the
+// stash by cp.async one plane ahead (32- and 64-bit storage).
 #pragma once
 
 #include "lbm_step.cuh"
@@ -72,6 +74,25 @@ cudaError_t launch_step_qs(int closure, int bc, int ty, int variant, const StepA
             LBM_SBP_CASE(CL_KCRR, BC_PERIODIC, 8)
         }
 #undef LBM_SBP_CASE
+        return cudaErrorNotSupported;
+    }
+    if (variant == VAR_ASYNC) {
+        if constexpr (sizeof(S) == sizeof(typename StoreTraits<S>::R)) {
+#define LBM_AS_CASE(CL, BCV, TYV)                                                               \
+    if (closure == CL && bc == BCV && ty == TYV)                                                \
+        return a ? launch_sb_t<Q, S, CL, BCV, TYV, false, true>(*a, nbatch, s)                  \
+                 : (nbatch < 0 ? prepare_sb_t<Q, S, CL, BCV, TYV, false, true>() : cudaSuccess);
+            LBM_AS_CASE(CL_BGK, BC_PERIODIC, 8)
+            LBM_AS_CASE(CL_KCMP, BC_PERIODIC, 8)
+            LBM_AS_CASE(CL_KCRB_H, BC_PERIODIC, 8)
+            LBM_AS_CASE(CL_KCRB_RAW, BC_PERIODIC, 8)
+            LBM_AS_CASE(CL_BGK, BC_WALLS_Y, 8)
+            LBM_AS_CASE(CL_KCMP, BC_WALLS_Y, 8)
+            if constexpr (Q == 27) {
+                LBM_AS_CASE(CL_KCRR, BC_PERIODIC, 8)
+            }
+#undef LBM_AS_CASE
+        }
         return cudaErrorNotSupported;
     }
     if (variant == VAR_PAIR) {

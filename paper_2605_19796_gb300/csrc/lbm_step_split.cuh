@@ -46,6 +46,42 @@ __device__ __forceinline__ int d27_of_rt(int i)
     }
 }
 
+// Asynchronous 4- or 8-byte global -> shared copy (cp.async, through L1), its
+// group commit, and the wait for all of the thread's committed groups (or all
+// but the newest).  A copy lands only in the issuing thread's own stash column
+// and only that thread reads it after its wait, so no barrier is involved.
+template <int N>
+__device__ __forceinline__ void cp_async_ca(uint32_t dst, const void* src)
+{
+    static_assert(N == 4 || N == 8, "cp.async.ca copies 4, 8 or 16 bytes");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(dst), "l"(src), "n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory"); }
+
+// The Q source addresses of pull() (same periodic wrap and halfway bounce-back),
+// copied raw (f, not f - w) into the stash column at dst, stride `stride` bytes.
+template <int Q, typename S, int BC>
+__device__ __forceinline__ void pull_async(const S* __restrict__ fin, long long ps, const Col& col, const int (&zr)[3],
+                                           uint32_t dst, uint32_t stride)
+{
+    static_for<Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
+        constexpr int io = opp_of(Q, i);
+        const S* src;
+        if (BC == BC_WALLS_Y && cy != 0) {
+            const int row = col.yr[1 - cy];
+            src = row >= 0 ? fin + (long long)i * ps + (zr[1 - cz] + row + col.xs[1 - cx])
+                           : fin + (long long)io * ps + (zr[1] + col.yr[1] + col.xs[1]);
+        } else {
+            src = fin + (long long)i * ps + (zr[1 - cz] + col.yr[1 - cy] + col.xs[1 - cx]);
+        }
+        cp_async_ca<sizeof(S)>(dst + (uint32_t)i * stride, src);
+    });
+}
+
 template <int Q, typename R, int BC, int TY>
 struct SplitShape {
     using Sh = StepShape<Q, R, BC, TY>;
@@ -59,7 +95,16 @@ struct SplitShape {
 // x-range, for the tile rows and the two halo rows), so that the loads of that
 // plane's load phase meet L2 rather than DRAM; no registers or shared memory
 // hold the prefetched data and HBM traffic is unchanged.
-template <int Q, typename S, int CL, int BC, int TY, bool L2PF = false>
+// AS: the own column's pulls go to the stash by cp.async, raw, one plane
+// ahead: the copies of plane k+2 are issued into the slot that plane k's
+// populations leave as soon as the collision has read them, and are waited for
+// at the top of iteration k+1, so their latency runs under plane k's collision
+// and stores and no registers hold them in flight.  The moments of a plane and
+// the collision read the stash and subtract w.  The halo cells keep their
+// register pulls (a halo slot of its own, 9 KB at 32 x 8, took two CTAs past
+// the 164 KB shared-memory carveout and cost L1 more than the latency it hid).
+// 32- and 64-bit storage only (the stash holds the stored values as they are).
+template <int Q, typename S, int CL, int BC, int TY, bool L2PF = false, bool AS = false>
 __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) == 8 || TY >= 16) ? 1 : 2)
     step_kernel_sb(const StepArgs a)
 {
@@ -69,6 +114,8 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
     constexpr int TX = Sh::TX, HY = Sh::HY, RX = Sh::RX, RN = Sh::RN, NT = Sh::NT, NB = Sh::NB;
     static_assert(NB <= NT, "every halo cell of the ring needs a thread");
     static_assert(CL != CL_LEARNED, "the learned closure runs in step_kernel");
+    static_assert(!AS || sizeof(S) == sizeof(R), "the asynchronous stash holds stored values as they are");
+    static_assert(!(AS && L2PF), "one load schedule at a time");
     extern __shared__ __align__(16) unsigned char smem_sb[];
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_sb);
     R* ring = reinterpret_cast<R*>(smem_sb + Sp::ring_off);    // [5][3][RN]
@@ -141,20 +188,40 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
         ringp(s, 1)[r] = vy;
         ringp(s, 2)[r] = vz;
     };
+    // stash slot of plane z for the own column (elements of R, stride NT)
+    auto stash_col = [&](int z) { return stash + (z & 1) * Q * NT + tid; };
+    // populations g = f - w from an asynchronous stash column (stride NS)
+    auto stash_g = [&](const R* st, int ns, R (&g)[Q]) {
+        static_for<Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            g[i] = st[i * ns] - (R)weight_of(Q, i);
+        });
+    };
+    auto issue_async = [&](int z) {  // own column, plane z -> its stash slot
+        if constexpr (AS) {
+            int zr[3];
+            zrows(z, zr);
+            pull_async<Q, S, BC>(fin, ps, own, zr, (uint32_t)__cvta_generic_to_shared(stash_col(z)),
+                                 (uint32_t)(NT * sizeof(R)));
+        }
+    };
+
     // pull of plane z: own cell (velocity to the ring; populations to the stash
-    // when `keep`) and, with `halo`, the thread's halo cell, loads issued together
-    auto load_plane = [&](int z, bool keep, bool halo, R& r, R& vx, R& vy, R& vz) {
+    // when `keep`) and, with `halo`, the thread's halo cell, loads issued together;
+    // with AS and `staged`, the own cell's populations are already in the stash
+    auto load_plane = [&](int z, bool keep, bool halo, bool staged, R& r, R& vx, R& vy, R& vz) {
         int zr[3];
         zrows(z, zr);
         const bool do_h = halo && tid < NB;
         R t[Q], gh[Q];
-        if (own.valid) pull<Q, S, R, BC>(fin, ps, own, zr, t);
+        if (own.valid && !(AS && staged)) pull<Q, S, R, BC>(fin, ps, own, zr, t);
         if (do_h && hal.valid) pull<Q, S, R, BC>(fin, ps, hal, zr, gh);
         r = 0;
         vx = vy = vz = 0;
         if (own.valid) {
+            if (AS && staged) stash_g(stash_col(z), NT, t);
             moments<Q, R>(t, r, vx, vy, vz, Fx, Fy, Fz);
-            if (keep) {
+            if (!(AS && staged) && keep) {
                 R* st = stash + (z & 1) * Q * NT + tid;
 #pragma unroll
                 for (int i = 0; i < Q; ++i) st[i * NT] = t[i];
@@ -175,9 +242,16 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
 
     R drho, ux, uy, uz;  // moments of the own cell at plane z
     {
+        if constexpr (AS) {
+            if (own.valid) issue_async(z0);
+            cp_async_commit();
+            if (own.valid) issue_async(z0 + 1);  // z0 + 1 <= z1
+            cp_async_commit();
+        }
         R r0, v0x, v0y, v0z;
-        load_plane(z0 - 1, false, false, r0, v0x, v0y, v0z);  // z-derivative at z0 only: own column
-        load_plane(z0, true, true, drho, ux, uy, uz);
+        load_plane(z0 - 1, false, false, false, r0, v0x, v0y, v0z);  // z-derivative at z0 only: own column
+        if constexpr (AS) cp_async_wait<1>();  // plane z0 landed
+        load_plane(z0, true, true, true, drho, ux, uy, uz);
         arrive(z0);
     }
 
@@ -207,13 +281,14 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
         }
         // ---- plane z+1: own (and, while it will be collided, halo) velocities into the ring
         R rn, vnx, vny, vnz;
-        load_plane(z + 1, z + 1 < z1, z + 1 < z1, rn, vnx, vny, vnz);
+        if constexpr (AS) cp_async_wait<0>();  // plane z+1 (issued one iteration ago) landed
+        load_plane(z + 1, z + 1 < z1, z + 1 < z1, true, rn, vnx, vny, vnz);
         if (z + 1 < z1) arrive(z + 1);
 
         // ---- plane z: wait until every thread has published it, then strain, closure, relaxation
         if (!wait(z)) {
             atomicOr(a.flag, kFlagTimeout);
-            return;
+            return;  // with AS no copies are in flight here (all waited for above)
         }
         if (own.valid) {
             // a non-finite component makes the sum non-finite (the moments are O(1))
@@ -237,9 +312,14 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
             const R Sxz = R(0.5) * (du[0][2] + du[2][0]);
             const R Syz = R(0.5) * (du[1][2] + du[2][1]);
             R g[Q];
-            const R* st = stash + (z & 1) * Q * NT + tid;
+            if constexpr (AS) {
+                stash_g(stash_col(z), NT, g);
+                if (z + 2 <= z1) issue_async(z + 2);  // into the slot just read
+            } else {
+                const R* st = stash_col(z);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) g[i] = st[i * NT];
+                for (int i = 0; i < Q; ++i) g[i] = st[i * NT];
+            }
             collide<Q, R, CL, FORCE>(g, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, omega, tau_hat, nu, cnud, Fx,
                                      Fy, Fz);
             if (own_store) {
@@ -250,6 +330,7 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
                 });
             }
         }
+        if constexpr (AS) cp_async_commit();
         drho = rn;
         ux = vnx;
         uy = vny;
@@ -257,27 +338,27 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
     }
 }
 
-template <int Q, typename S, int CL, int BC, int TY, bool L2PF = false>
+template <int Q, typename S, int CL, int BC, int TY, bool L2PF = false, bool AS = false>
 cudaError_t prepare_sb_t()
 {
-    return cudaFuncSetAttribute(step_kernel_sb<Q, S, CL, BC, TY, L2PF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(step_kernel_sb<Q, S, CL, BC, TY, L2PF, AS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)SplitShape<Q, typename StoreTraits<S>::R, BC, TY>::bytes);
 }
 
-template <int Q, typename S, int CL, int BC, int TY, bool L2PF = false>
+template <int Q, typename S, int CL, int BC, int TY, bool L2PF = false, bool AS = false>
 cudaError_t launch_sb_t(const StepArgs& a, int nbatch, cudaStream_t s)
 {
     using Sh = StepShape<Q, typename StoreTraits<S>::R, BC, TY>;
     static bool attr_set = false;  // per instantiation; prepare_sb_t sets it ahead of stream capture
     if (!attr_set) {
-        cudaError_t e = prepare_sb_t<Q, S, CL, BC, TY, L2PF>();
+        cudaError_t e = prepare_sb_t<Q, S, CL, BC, TY, L2PF, AS>();
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     const int tiles = ((a.nx + Sh::TX - 1) / Sh::TX) * ((a.ny + TY - 1) / TY);
     const int chunks = (a.nz + a.zchunk - 1) / a.zchunk;
     dim3 grid(tiles, chunks, nbatch), block(Sh::TX, TY);
-    step_kernel_sb<Q, S, CL, BC, TY, L2PF>
+    step_kernel_sb<Q, S, CL, BC, TY, L2PF, AS>
         <<<grid, block, SplitShape<Q, typename StoreTraits<S>::R, BC, TY>::bytes, s>>>(a);
     return cudaGetLastError();
 }

@@ -141,12 +141,12 @@ def test_variants_agree_fp32(lbm, orc, closure):
     shape = (45, 19, 23)
     rho, u = inputs.hit_fields(0, k0=3.0, urms=0.07, seed=8, shape=shape)
     res = {}
-    for var, zc in [(1, 0), (8, 0), (8, 5), (9, 0), (9, 5)]:
+    for var, zc in [(1, 0), (8, 0), (8, 5), (9, 0), (9, 5), (13, 0), (13, 5)]:
         with lbm.Solver(27, shape, 2e-5, closure=closure, storage="fp32", variant=var, zchunk=zc) as s:
             s.init_velocity(rho, u)
             s.step(8)
             res[(var, zc)] = s.get_populations()
-    for v in (8, 9):
+    for v in (8, 9, 13):
         assert rel(res[(v, 0)], res[(1, 0)]) < 1e-6, v
         assert np.array_equal(res[(v, 0)], res[(v, 5)]), v
 
@@ -364,7 +364,7 @@ def test_autotune_keeps_state_and_result(lbm, orc):
         s.step(2)
         before = s.get_populations()
         cfg = s.autotune(trials=2)
-        assert cfg["variant"] in (1, 4, 8, 9, 12) and cfg["tile_y"] in (4, 8, 16) and 1 <= cfg["zchunk"] <= 128
+        assert cfg["variant"] in (1, 4, 8, 9, 12, 13) and cfg["tile_y"] in (4, 8, 16) and 1 <= cfg["zchunk"] <= 128
         assert np.array_equal(before, s.get_populations())
         s.step(5)
         tuned = s.get_populations()
@@ -423,11 +423,13 @@ def test_tma_variant_matches(lbm, orc, shape, nbatch, closure):
 
 
 def test_default_variant_selection(lbm):
-    """Library default: the split-barrier pull (8) for periodic D3Q27 with BGK,
-    KC-MP, KC-RB or KC-RR, the register pull (1) for D3Q19, walls and the
-    learned closure; an explicitly requested variant that is not built for a
-    box is refused."""
-    for q, closure, storage, want in ((27, "kcmp", "fp32", 8), (27, "kcrb_hermite", "fp16", 8), (27, "kcmp", "fp64", 8),
+    """Library default for periodic D3Q27: the split-barrier pull with
+    asynchronous own pulls (13) for FP32 with KC-MP, KC-RB or KC-RR, the
+    split-barrier pull (8) for BGK, FP64 and 16-bit storage; the register pull
+    (1) for D3Q19, walls and the learned closure; an explicitly requested
+    variant that is not built for a box is refused."""
+    for q, closure, storage, want in ((27, "kcmp", "fp32", 13), (27, "kcrb_hermite", "fp16", 8), (27, "kcmp", "fp64", 8),
+                                      (27, "kcrb_raw", "fp32", 13), (27, "kcrr", "fp32", 13),
                                       (27, "bgk", "fp32", 8), (19, "kcmp", "fp32", 1), (27, "kcrr", "fp64", 8),
                                       (27, "learned", "fp32", 1)):
         with lbm.Solver(q, (40, 32, 16), 1e-4, closure=closure, storage=storage) as s:
@@ -476,7 +478,9 @@ def test_kcrr_fp32_velocity(lbm, orc):
 def test_load_schedule_variants(lbm, orc, storage, closure):
     """Variant 8 (halo and own loads together, split arrive/wait barrier) only
     reschedules the loads and synchronisation of the register pull (variant 1);
-    variant 12 adds L2 prefetches to it; variant 9 runs the same arithmetic on
+    variant 12 adds L2 prefetches to it, variant 13 (32- and 64-bit storage)
+    copies the own pulls to shared memory asynchronously one plane ahead;
+    variant 9 runs the same arithmetic on
     packed FP32 pairs, two cells per thread (not built for KC-RR).  On a ragged box with
     two boxes and several z-chunkings (one and two planes per CTA exercise the
     pipelines' start and drain): FP64 matches the oracle to 1e-12, FP32 matches
@@ -488,6 +492,8 @@ def test_load_schedule_variants(lbm, orc, storage, closure):
     u = np.stack([f[1] for f in fields], axis=1)
     nus = np.array([2e-5, 1e-4])
     variants = (8, 12) if storage == "fp64" or closure == "kcrr" else (8, 9, 12)
+    if storage in ("fp32", "fp64"):
+        variants += (13,)
     res = {}
     for var, zc in [(1, 0)] + [(v, z) for v in variants for z in (0, 1, 2, 5)]:
         with lbm.Solver(27, shape, nus, closure=closure, storage=storage, variant=var, zchunk=zc, nbatch=2) as s:
@@ -519,8 +525,9 @@ def test_load_schedule_variants(lbm, orc, storage, closure):
 
 @pytest.mark.parametrize("q", [19, 27])
 def test_variants_channel(lbm, orc, q):
-    """Variants 8 and 9 with bounce-back walls and a body force: FP64 (variant 8)
-    against the oracle, FP32 against variant 1 to FP32 rounding."""
+    """Variants 8, 9, 12 and 13 with bounce-back walls and a body force: FP64
+    (variants 8 and 13) against the oracle, FP32 against variant 1 to FP32
+    rounding."""
     rho, u = inputs.channel_fields(16, 11, 9, 0.05, seed=5)
     F = (1e-5, 0.0, 0.0)
     with lbm.Solver(q, (16, 11, 9), 2e-3, closure="kcmp", storage="fp64", bc=(0, 1, 0), force=F, variant=8,
@@ -531,19 +538,20 @@ def test_variants_channel(lbm, orc, q):
     fo = orc.run(orc.init_equilibrium(q, rho, u), 6, closure=1, nu=2e-3, c_nu=0.035, bc=(0, 1, 0), F=F)
     assert rel(fg, fo) < TOL64
     out = {}
-    for var in (1, 8, 9, 12):
+    for var in (1, 8, 9, 12, 13):
         with lbm.Solver(q, (16, 11, 9), 2e-3, closure="kcmp", storage="fp32", bc=(0, 1, 0), force=F,
                         variant=var) as s:
             s.init_velocity(rho, u)
             s.step(6)
             out[var] = s.get_populations()
-    for var in (8, 9, 12):
+    for var in (8, 9, 12, 13):
         assert rel(out[var], out[1]) < 1e-6, var
-    with lbm.Solver(q, (16, 11, 9), 2e-3, closure="kcmp", storage="fp64", bc=(0, 1, 0), force=F, variant=8,
-                    zchunk=2) as s:
-        s.init_velocity(rho, u)
-        s.step(6)
-        assert rel(s.get_populations(), fo) < TOL64
+    for var, zc in ((8, 2), (13, 2), (13, 3)):
+        with lbm.Solver(q, (16, 11, 9), 2e-3, closure="kcmp", storage="fp64", bc=(0, 1, 0), force=F, variant=var,
+                        zchunk=zc) as s:
+            s.init_velocity(rho, u)
+            s.step(6)
+            assert rel(s.get_populations(), fo) < TOL64, (var, zc)
 
 
 def test_bounded_wait_times_out_and_handle_stays_usable(lbm, orc):

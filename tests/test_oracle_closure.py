@@ -15,7 +15,10 @@ Each test states the passage of the paper (or the mathematical fact) it checks:
     representation recombines);
   - the trapezoidal reconstruction of App. F.5 (Eq. correct_Qi): the explicit
     two-rate update solves the implicit relation with tau in the unshifted CE part;
-  - the rate formula Eq. (omega_sgs_operational).
+  - the rate formula Eq. (omega_sgs_operational);
+  - KC-RR on a state built from its Hermite coefficients, against the closed
+    form of the RR recursion Eq. (kcrr_rr) and the two-rate relaxation of
+    App. F.4.
 """
 import numpy as np
 import pytest
@@ -208,3 +211,96 @@ def test_rate_formula(orc):
         assert v == pytest.approx(expect, rel=1e-15)
     # the trace enters through its magnitude
     assert orc.omega_sgs(-1e-3, nu, c_nu) == orc.omega_sgs(1e-3, nu, c_nu)
+
+
+def _rr_closed_form(axes, u, a2):
+    """Recursive-regularised non-equilibrium coefficient of a mode given by its
+    list of axes, in the closed form the recursion of Eq. (kcrr_rr) sums to in
+    the isothermal case: the sum over all pairs (i, j) of the mode's indices of
+    a2[a_i][a_j] times the product of u over the remaining indices (induction
+    on n: the recursion's u_{a_n} term carries the pairs among the first n-1
+    indices, its sum term the pairs (i, n))."""
+    n = len(axes)
+    s = 0.0
+    for i in range(n):
+        for j in range(i + 1, n):
+            p = 1.0
+            for k in range(n):
+                if k != i and k != j:
+                    p *= u[axes[k]]
+            s += a2[axes[i]][axes[j]] * p
+    return s
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("with_high_sgs", [False, True])
+def test_kcrr_against_hermite_closed_form(orc, seed, with_high_sgs):
+    """KC-RR (App. F.4) on a state built from its D3Q27 Hermite coefficients.
+
+    The state is f = f0 + w sum_d N_d H_d K_d over the modes d of order >= 2,
+    with H_d(c) = prod_a h(c_a, d_a), h = 1, c, c^2 - theta and N_d the
+    quadrature normalisation prod_a (1, 1/theta, 1/(2 theta^2))[d_a] (the
+    three-point rule per axis makes the 27 H_d orthogonal, so f's
+    non-equilibrium coefficients are exactly K_d): second order
+    K = m_CE + M_sgs, the 17 high-order modes K = a_rr (closed form above,
+    seeded by m_CE = -2 rho theta tau_hat S) plus, optionally, a random SGS
+    departure A.  KC-RR must return f0 + w sum_d N_d H_d K'_d with
+    K' = (1 - omega) m_CE + (1 - omega_s) M_sgs and (1 - omega) a_rr +
+    (1 - omega_s) A, omega_s from the rate formula on tr M_sgs.  A wrong index,
+    a dropped term of the recursion or a wrong mode normalisation relaxes part
+    of a coefficient at omega_s instead of omega (or rebuilds it wrongly),
+    which this state shows at (omega - omega_s) of that part."""
+    q = 27
+    rng = np.random.default_rng(100 + seed)
+    c, w, _ = orc.lattice(q)
+    c = c.astype(int)
+    rho = 1.0 + 0.05 * rng.standard_normal()
+    u = 0.08 * rng.standard_normal(3)
+    # product-form equilibrium written out (Sec. 7 / App. E)
+    f0 = np.array([w[i] * rho * np.prod([1 + c[i, a] * u[a] / THETA + (c[i, a] ** 2 - THETA) * u[a] ** 2
+                                         / (2 * THETA ** 2) for a in range(3)]) for i in range(q)])
+    nu, c_nu = 1e-5, 0.5
+    om = 1.0 / (nu / THETA + 0.5)
+    tau_hat = 1.0 / om
+    B = 0.01 * rng.standard_normal((3, 3))
+    S = 0.5 * (B + B.T)
+    mce = -2.0 * rho * THETA * tau_hat * S
+    C = 0.004 * rng.standard_normal((3, 3))
+    Msgs = 0.5 * (C + C.T) + 0.004 * np.eye(3)
+    tr = np.trace(Msgs)
+    nut = c_nu * np.sqrt(abs(tr) / 2.0)
+    assert nut > nu
+    om_s = 1.0 / (nut / THETA + 0.5)
+    assert om - om_s > 0.1
+
+    def h(ci, d):
+        return 1.0 if d == 0 else (float(ci) if d == 1 else ci * ci - THETA)
+
+    norm = (1.0, 1.0 / THETA, 1.0 / (2.0 * THETA ** 2))
+    modes = [(dx, dy, dz) for dz in range(3) for dy in range(3) for dx in range(3) if dx + dy + dz >= 2]
+    K, Kp = {}, {}
+    for d in modes:
+        axes = [a for a in range(3) for _ in range(d[a])]
+        if len(axes) == 2:
+            i, j = axes
+            K[d] = mce[i, j] + Msgs[i, j]
+            Kp[d] = (1 - om) * mce[i, j] + (1 - om_s) * Msgs[i, j]
+        else:
+            arr = _rr_closed_form(axes, u, mce)
+            A = 1e-3 * rng.standard_normal() if with_high_sgs else 0.0
+            K[d] = arr + A
+            Kp[d] = (1 - om) * arr + (1 - om_s) * A
+
+    def build(coef):
+        g = np.zeros(q)
+        for i in range(q):
+            for d, k in coef.items():
+                g[i] += k * np.prod([norm[d[a]] * h(c[i, a], d[a]) for a in range(3)])
+        return w * g
+
+    f = f0 + build(K)
+    expect = f0 + build(Kp)
+    fpost, om_s_orc = orc.collide_cell(q, CLOSURES["kcrr"], f, S, nu, c_nu)
+    assert om_s_orc == pytest.approx(om_s, rel=1e-12)
+    scale = np.abs(expect - f0).max()
+    assert np.abs(fpost - expect).max() <= 1e-12 * scale + 64 * EPS

@@ -54,6 +54,9 @@ WORKLOADS = {
     "channel512x256x256_d3q27_fp32_kcmp": dict(shape=(512, 256, 256), q=27, storage="fp32", closure="kcmp",
                                                nu=0.004 * 128 / 180, force=(0.004 ** 2 / 128, 0.0, 0.0),
                                                u_bulk=0.063),
+    "channel512x256x256_d3q19_fp32_kcmp": dict(shape=(512, 256, 256), q=19, storage="fp32", closure="kcmp",
+                                               nu=0.004 * 128 / 180, force=(0.004 ** 2 / 128, 0.0, 0.0),
+                                               u_bulk=0.063),
 }
 DEFAULT_WORKLOAD = "hit512_d3q27_fp32_kcmp"
 ELEM = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}

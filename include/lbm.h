@@ -101,9 +101,9 @@ typedef struct {
     int tile_y;         /* tuning: rows per CTA tile (0 = library default)           */
     int zchunk;         /* tuning: z-planes per CTA march (0 = library default)      */
     int variant;        /* tuning: step-kernel variant, 0 = library default
-                           (periodic D3Q27: 13 for FP32 storage with KC-MP,
-                           KC-RB or KC-RR, 8 for BGK, FP64 and 16-bit
-                           storage; else 1),
+                           (13 for FP32 storage with KC-MP, KC-RB or KC-RR
+                           where built, i.e. periodic D3Q27/D3Q19 and walls
+                           with KC-MP; else 8 for periodic D3Q27; else 1),
                            1 = register pull (every lattice, storage, closure
                            and boundary), 4 = TMA-staged pipeline (FP32,
                            periodic, BGK/KC-MP/KC-RB, nx % 32 == 0 and

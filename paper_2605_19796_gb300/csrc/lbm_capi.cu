@@ -312,22 +312,24 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
         cfg->variant != VAR_PAIR && cfg->variant != VAR_SPLIT_PF && cfg->variant != VAR_ASYNC)
         return fail(LBM_ERR_ARG, "unknown kernel variant");
     int variant = cfg->variant;
-    // measured defaults for periodic D3Q27 boxes: the split-barrier pull with the
-    // own pulls copied asynchronously (13) for FP32 storage and a closure carrier
-    // (KC-MP, KC-RB, KC-RR), the split-barrier pull (8) for BGK, FP64 and 16-bit
-    // storage; the register pull elsewhere.  lbm_autotune may pick another
-    // variant for a given box
+    // measured defaults: FP32 storage with a closure carrier (KC-MP, KC-RB,
+    // KC-RR) takes the split-barrier pull with asynchronous own pulls (13)
+    // wherever it is built (D3Q27 and D3Q19, periodic and, for KC-MP, walls);
+    // periodic D3Q27 otherwise (BGK, FP64, 16-bit storage) the split-barrier
+    // pull (8); everything else the register pull (1).  lbm_autotune may pick
+    // another variant for a given box
     if (variant == VAR_DEFAULT) {
-        const bool split_built = cfg->closure == LBM_BGK || cfg->closure == LBM_KCMP ||
-                                 cfg->closure == LBM_KCRB_HERMITE || cfg->closure == LBM_KCRB_RAW ||
-                                 cfg->closure == LBM_KCRR;
-        variant = (cfg->lattice == LBM_D3Q27 && split_built && bc_kind == BC_PERIODIC &&
-                   step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, VAR_SPLIT))
-                      ? VAR_SPLIT
-                      : VAR_REGISTER;
-        if (variant == VAR_SPLIT && cfg->closure != LBM_BGK && cfg->storage == LBM_FP32 &&
+        const bool carrier = cfg->closure == LBM_KCMP || cfg->closure == LBM_KCRB_HERMITE ||
+                             cfg->closure == LBM_KCRB_RAW || cfg->closure == LBM_KCRR;
+        const bool split_built = carrier || cfg->closure == LBM_BGK;
+        if (carrier && cfg->storage == LBM_FP32 &&
             step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, VAR_ASYNC))
             variant = VAR_ASYNC;
+        else if (cfg->lattice == LBM_D3Q27 && split_built && bc_kind == BC_PERIODIC &&
+                 step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, VAR_SPLIT))
+            variant = VAR_SPLIT;
+        else
+            variant = VAR_REGISTER;
     }
     if (variant == VAR_TMA && !tma_shape_ok(cfg->nx, cfg->ny, tile_y))
         return fail(LBM_ERR_UNSUPPORTED, "the TMA variant needs nx % 32 == 0 and ny % tile_y == 0");

@@ -423,19 +423,22 @@ def test_tma_variant_matches(lbm, orc, shape, nbatch, closure):
 
 
 def test_default_variant_selection(lbm):
-    """Library default for periodic D3Q27: the split-barrier pull with
-    asynchronous own pulls (13) for FP32 with KC-MP, KC-RB or KC-RR, the
-    split-barrier pull (8) for BGK, FP64 and 16-bit storage; the register pull
-    (1) for D3Q19, walls and the learned closure; an explicitly requested
+    """Library default: the split-barrier pull with asynchronous own pulls (13)
+    for FP32 storage with KC-MP, KC-RB or KC-RR where it is built (D3Q27 and
+    D3Q19; walls with KC-MP), the split-barrier pull (8) for periodic D3Q27
+    otherwise (BGK, FP64, 16-bit storage), the register pull (1) for the rest
+    (D3Q19 BGK, walls with KC-RB, the learned closure); an explicitly requested
     variant that is not built for a box is refused."""
     for q, closure, storage, want in ((27, "kcmp", "fp32", 13), (27, "kcrb_hermite", "fp16", 8), (27, "kcmp", "fp64", 8),
                                       (27, "kcrb_raw", "fp32", 13), (27, "kcrr", "fp32", 13),
-                                      (27, "bgk", "fp32", 8), (19, "kcmp", "fp32", 1), (27, "kcrr", "fp64", 8),
+                                      (27, "bgk", "fp32", 8), (19, "kcmp", "fp32", 13), (19, "bgk", "fp32", 1),
+                                      (19, "kcmp", "fp16", 1), (27, "kcrr", "fp64", 8),
                                       (27, "learned", "fp32", 1)):
         with lbm.Solver(q, (40, 32, 16), 1e-4, closure=closure, storage=storage) as s:
             assert s.launch_config["variant"] == want, (q, closure, storage)
-    with lbm.Solver(27, (40, 32, 16), 1e-4, closure="kcmp", storage="fp32", bc=(0, 1, 0)) as s:
-        assert s.launch_config["variant"] == 1
+    for q, closure, want in ((27, "kcmp", 13), (19, "kcmp", 13), (27, "kcrb_hermite", 1), (27, "bgk", 1)):
+        with lbm.Solver(q, (40, 32, 16), 1e-4, closure=closure, storage="fp32", bc=(0, 1, 0)) as s:
+            assert s.launch_config["variant"] == want, (q, closure, "walls")
     with lbm.Solver(27, (64, 32, 16), 1e-4, closure="kcmp", storage="fp32", variant=4) as s:
         assert s.launch_config["variant"] == 4
     with pytest.raises(lbm.LbmError):

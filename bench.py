@@ -72,10 +72,12 @@ def log(*a):
 
 
 def kernel_hash() -> str:
+    """Hash of the device sources of the step kernels (the host code that picks
+    the launch is checked through the launch recorded beside the traffic)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2605_19796_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if not (f.startswith("lbm_step") or f in ("lbm_lattice.cuh", "lbm_mbarrier.cuh", "lbm_capi.cu")):
+        if not (f.startswith("lbm_step") or f in ("lbm_lattice.cuh", "lbm_mbarrier.cuh", "lbm_mlp_infer.cuh")):
             continue
         with open(os.path.join(ROOT, "paper_2605_19796_gb300", "csrc", f), "rb") as fp:
             h.update(fp.read())
@@ -90,15 +92,17 @@ def measured_peak_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def traffic_per_cell(workload: str):
+def traffic_per_cell(workload: str, launch: dict):
     """DRAM bytes per cell update of the step kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
+    summary, if it was taken on the current kernel source and the same kernel
+    instantiation (variant, tile height) as this run's launch."""
     p = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     try:
         with open(p) as fp:
             d = json.load(fp)
         e = d.get(workload)
-        if e and e.get("kernel_hash") == kernel_hash():
+        same = all(e.get("launch", {}).get(k) == launch.get(k) for k in ("variant", "tile_y")) if e else False
+        if e and same and e.get("kernel_hash") == kernel_hash():
             return float(e["dram_bytes_per_cell"])
     except Exception:
         pass
@@ -341,7 +345,7 @@ def main():
     alg_bytes = 2 * q * ELEM[wl["storage"]] * N
     peak, peak_src = measured_peak_hbm()
     achieved = alg_bytes / kern_s / 1e9
-    tpc = traffic_per_cell(args.workload)
+    tpc = traffic_per_cell(args.workload, s.launch_config)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (tpc * N if tpc is not None else None), "peak_source": peak_src,
                 "algorithmic_bytes_per_cell": 2 * q * ELEM[wl["storage"]], "frac_of_nominal_8TBs": achieved / 8000.0}

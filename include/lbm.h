@@ -133,6 +133,8 @@ void lbm_destroy(lbm_handle* h);
 
 /* Sets every population to the equilibrium f0(rho, u) (Eq. discrete_equilibrium).
  * rho: host [nbatch*nz*ny*nx] or NULL for rho = 1; u: host [3][nbatch*nz*ny*nx].
+ * The equilibrium is evaluated in FP64 for FP64 storage and in FP32 (on its
+ * small per-axis terms) for FP32 and 16-bit storage.
  * Synchronises the stream before returning. */
 int lbm_init_velocity(lbm_handle* h, const double* rho, const double* u);
 
@@ -166,7 +168,11 @@ int lbm_launch_config(const lbm_handle* h, int* variant, int* tile_y, int* zchun
 
 /* Density and velocity of the current state (App. F.1 step 1, with the
  * half-force shift when a body force is set) into host arrays rho
- * [nbatch*N] and u [3][nbatch*N] (either may be NULL).  Synchronises. */
+ * [nbatch*N] and u [3][nbatch*N] (either may be NULL).  Sums in FP64 for FP64
+ * storage, in FP32 for FP32 and 16-bit storage (rho assembled in FP64 from
+ * the FP32 sum of f - w and the weights; errors of order 1e-7 relative, the
+ * precision the stored values carry; lbm_diagnostics always sums in FP64).
+ * Synchronises. */
 int lbm_moments(lbm_handle* h, double* rho, double* u);
 
 /* As lbm_moments into device FP64 arrays; enqueue only. */

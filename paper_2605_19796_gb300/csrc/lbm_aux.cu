@@ -60,36 +60,82 @@ __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(double f, double 
     return __float2bfloat16_rn((float)(f - w));
 }
 
+// Cells t0 .. t0 + count - 1 of the nbatch x ncell cells; rho [count] and
+// u [3][ustride] hold the range's fields (the whole arrays, t0 = 0, or a
+// staged chunk).
 template <int Q, typename S>
-__global__ void init_kernel(S* f, const double* rho, const double* u, long long ncell, int nbatch, long long ps,
-                            long long bs)
+__global__ void init_kernel(S* f, const double* rho, const double* u, long long ncell, long long ps, long long bs,
+                            long long t0, long long count, long long ustride)
 {
-    const long long total = ncell * nbatch;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-        const long long box = t / ncell, c = t - box * ncell;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count; t += (long long)gridDim.x * blockDim.x) {
+        const long long T = t0 + t;
+        const long long box = T / ncell, c = T - box * ncell;
         const double r = rho ? rho[t] : 1.0;
-        double geq[Q];
-        equilibrium_g<Q>(r, u[t], u[total + t], u[2 * total + t], geq);
         S* fb = f + box * bs + c;
-        static_for<Q>([&](auto I) {
-            constexpr int i = decltype(I)::value;
-            constexpr double w = weight_of(Q, i);
-            fb[i * ps] = from_f<S>(w + geq[i], w);
-        });
+        if constexpr (sizeof(S) == 8) {
+            double geq[Q];
+            equilibrium_g<Q>(r, u[t], u[ustride + t], u[2 * ustride + t], geq);
+            static_for<Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                constexpr double w = weight_of(Q, i);
+                fb[i * ps] = from_f<S>(w + geq[i], w);
+            });
+        } else {
+            // FP32 arithmetic for FP32 and 16-bit storage (FP64 arithmetic is
+            // slow on this GPU and the stored values carry FP32 precision at
+            // most); FP32 f is stored as g + w, as the step kernels store it
+            float geq[Q];
+            equilibrium_g32<Q>((float)(r - 1.0), (float)u[t], (float)u[ustride + t], (float)u[2 * ustride + t], geq);
+            static_for<Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                store_g<S, float>(fb + i * ps, geq[i], (float)weight_of(Q, i));
+            });
+        }
     }
 }
 
 // rho = sum f, u = (sum f c - F/2)/rho: the post-collision array carries the
 // momentum of time n plus the full force impulse, so the half-force shift is
 // subtracted to report the time-n velocity of Guo forcing.
-template <int Q, typename S>
-__global__ void moments_kernel(const S* f, double* rho, double* u, long long ncell, int nbatch, long long ps,
-                               long long bs, double Fx, double Fy, double Fz)
+// sum of the FP32-rounded weights (the shift of FP32 arithmetic on stored f)
+template <int Q>
+__host__ __device__ constexpr double weight_sum_f32()
 {
-    const long long total = ncell * nbatch;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-        const long long box = t / ncell, c = t - box * ncell;
+    double s = 0.0;
+    for (int i = 0; i < Q; ++i) s += (double)(float)weight_of(Q, i);
+    return s;
+}
+
+// F32: FP32 arithmetic for 32- and 16-bit storage (the readback path); the
+// diagnostics keep FP64 sums.
+template <int Q, typename S, bool F32>
+__global__ void moments_kernel(const S* f, double* rho, double* u, long long ncell, long long ps, long long bs,
+                               double Fx, double Fy, double Fz, long long t0, long long count, long long ustride)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count; t += (long long)gridDim.x * blockDim.x) {
+        const long long T = t0 + t;
+        const long long box = T / ncell, c = T - box * ncell;
         const S* fb = f + box * bs + c;
+        if constexpr (F32 && sizeof(S) != 8) {
+            // g = f - w(FP32) is exact in FP32 (Sterbenz) or the stored 16-bit
+            // value; the x-triple sums of the step kernels; rho = sum f in FP64
+            // as sum g + sum w(FP32) for FP32 storage (1 + sum g for the
+            // weight-shifted 16-bit storage)
+            float g[Q];
+            static_for<Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                g[i] = load_g<S, float>(fb + i * ps, (float)weight_of(Q, i));
+            });
+            float d32, vx, vy, vz;
+            moments<Q, float>(g, d32, vx, vy, vz, (float)-Fx, (float)-Fy, (float)-Fz);
+            if (rho) rho[t] = (sizeof(S) == 4 ? weight_sum_f32<Q>() : 1.0) + (double)d32;
+            if (u) {
+                u[t] = vx;
+                u[ustride + t] = vy;
+                u[2 * ustride + t] = vz;
+            }
+            continue;
+        }
         double d = 0, jx = 0, jy = 0, jz = 0;
         static_for<Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
@@ -105,8 +151,8 @@ __global__ void moments_kernel(const S* f, double* rho, double* u, long long nce
         if (rho) rho[t] = r;
         if (u) {
             u[t] = (jx - 0.5 * Fx) / r;
-            u[total + t] = (jy - 0.5 * Fy) / r;
-            u[2 * total + t] = (jz - 0.5 * Fz) / r;
+            u[ustride + t] = (jy - 0.5 * Fy) / r;
+            u[2 * ustride + t] = (jz - 0.5 * Fz) / r;
         }
     }
 }
@@ -302,15 +348,18 @@ int diag_blocks(long long ncell)
 }  // namespace
 
 cudaError_t launch_init_equilibrium(int q, int storage, void* f, const double* rho, const double* u, long long ncell,
-                                    int nbatch, long long ps, long long bs, cudaStream_t s)
+                                    int nbatch, long long ps, long long bs, cudaStream_t s, long long t0,
+                                    long long count, long long ustride)
 {
-    const int g = grid_for(ncell * nbatch, 256);
+    if (count < 0) count = ncell * nbatch;
+    if (ustride < 0) ustride = count;
+    const int g = grid_for(count, 256);
     return dispatch_storage(storage, [&](auto tag) -> cudaError_t {
         using S = std::remove_pointer_t<decltype(tag)>;
         if (q == 27)
-            init_kernel<27, S><<<g, 256, 0, s>>>((S*)f, rho, u, ncell, nbatch, ps, bs);
+            init_kernel<27, S><<<g, 256, 0, s>>>((S*)f, rho, u, ncell, ps, bs, t0, count, ustride);
         else
-            init_kernel<19, S><<<g, 256, 0, s>>>((S*)f, rho, u, ncell, nbatch, ps, bs);
+            init_kernel<19, S><<<g, 256, 0, s>>>((S*)f, rho, u, ncell, ps, bs, t0, count, ustride);
         return cudaGetLastError();
     });
 }
@@ -334,15 +383,26 @@ cudaError_t launch_wait_selftest(unsigned int* flag, long long polls, cudaStream
 }
 
 cudaError_t launch_moments(int q, int storage, const void* f, double* rho, double* u, long long ncell, int nbatch,
-                           long long ps, long long bs, const double* force, cudaStream_t s)
+                           long long ps, long long bs, const double* force, cudaStream_t s, bool fp32, long long t0,
+                           long long count, long long ustride)
 {
-    const int g = grid_for(ncell * nbatch, 256);
+    if (count < 0) count = ncell * nbatch;
+    if (ustride < 0) ustride = count;
+    const int g = grid_for(count, 256);
     return dispatch_storage(storage, [&](auto tag) -> cudaError_t {
         using S = std::remove_pointer_t<decltype(tag)>;
-        if (q == 27)
-            moments_kernel<27, S><<<g, 256, 0, s>>>((const S*)f, rho, u, ncell, nbatch, ps, bs, force[0], force[1], force[2]);
-        else
-            moments_kernel<19, S><<<g, 256, 0, s>>>((const S*)f, rho, u, ncell, nbatch, ps, bs, force[0], force[1], force[2]);
+        const double F0 = force[0], F1 = force[1], F2 = force[2];
+        if (q == 27) {
+            if (fp32)
+                moments_kernel<27, S, true><<<g, 256, 0, s>>>((const S*)f, rho, u, ncell, ps, bs, F0, F1, F2, t0, count, ustride);
+            else
+                moments_kernel<27, S, false><<<g, 256, 0, s>>>((const S*)f, rho, u, ncell, ps, bs, F0, F1, F2, t0, count, ustride);
+        } else {
+            if (fp32)
+                moments_kernel<19, S, true><<<g, 256, 0, s>>>((const S*)f, rho, u, ncell, ps, bs, F0, F1, F2, t0, count, ustride);
+            else
+                moments_kernel<19, S, false><<<g, 256, 0, s>>>((const S*)f, rho, u, ncell, ps, bs, F0, F1, F2, t0, count, ustride);
+        }
         return cudaGetLastError();
     });
 }

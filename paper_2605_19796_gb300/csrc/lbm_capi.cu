@@ -81,6 +81,14 @@ struct lbm_handle {
     bool mlp_set = false;
     CUtensorMap tmap[2];             // TMA maps of f[0], f[1] (variant 4)
     int tmap_tile = 0;               // tile height the maps were encoded for (0 = none)
+    // host-pointer field transfers (lazy): two staging slots of stage_cells
+    // cells, each rho [stage_cells] then u [3][stage_cells], a copy stream and,
+    // per slot, "filled" and "drained" events
+    double* stage = nullptr;
+    long long stage_cells = 0;
+    cudaStream_t xstream = nullptr;
+    cudaEvent_t ev_filled[2] = {nullptr, nullptr};
+    cudaEvent_t ev_drained[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -216,6 +224,13 @@ void free_all(lbm_handle* h)
     if (h->d_partials) cudaFree(h->d_partials);
     if (h->d_diag) cudaFree(h->d_diag);
     if (h->d_mlp) cudaFree(h->d_mlp);
+    if (h->xstream) cudaStreamSynchronize(h->xstream);
+    if (h->stage) cudaFree(h->stage);
+    for (int k = 0; k < 2; ++k) {
+        if (h->ev_filled[k]) cudaEventDestroy(h->ev_filled[k]);
+        if (h->ev_drained[k]) cudaEventDestroy(h->ev_drained[k]);
+    }
+    if (h->xstream) cudaStreamDestroy(h->xstream);
 }
 
 int read_flag(lbm_handle* h)
@@ -250,6 +265,32 @@ int ensure_diag_scratch(lbm_handle* h)
         cudaGetLastError();
         return fail(LBM_ERR_OOM, "diagnostics scratch allocation failed");
     }
+    return LBM_OK;
+}
+
+// Cells per staging slot of the host-pointer transfers: 2^21 (64 MB of FP64
+// rho and u per slot), so that a chunk's copy (about 0.3 ms) dwarfs its
+// kernel launch and the two slots bound the extra device memory at 128 MB.
+constexpr long long kStageCells = 1LL << 21;
+
+int ensure_stage(lbm_handle* h)
+{
+    if (h->stage) return LBM_OK;
+    const long long n = h->ncell * h->cfg.nbatch;
+    const long long c = n < kStageCells ? n : kStageCells;
+    cudaError_t e = cudaMalloc(&h->stage, sizeof(double) * 4 * 2 * (size_t)c);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->xstream, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaEventCreateWithFlags(&h->ev_filled[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_drained[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (h->stage) cudaFree(h->stage);
+        h->stage = nullptr;
+        return fail(LBM_ERR_OOM, "staging ring allocation failed");
+    }
+    h->stage_cells = c;
     return LBM_OK;
 }
 
@@ -401,31 +442,43 @@ int lbm_init_velocity_device(lbm_handle* h, const double* rho_dev, const double*
     return LBM_OK;
 }
 
+// Host-pointer initialisation: the fields go through the two staging slots in
+// chunks of stage_cells cells; the copy of chunk k+1 (copy stream) runs while
+// the init kernel of chunk k (solver stream) reads the other slot.
 int lbm_init_velocity(lbm_handle* h, const double* rho, const double* u)
 {
     if (int rc = check_handle(h)) return rc;
     if (!u) return fail(LBM_ERR_ARG, "u is NULL");
-    const size_t n = (size_t)h->ncell * h->cfg.nbatch;
-    double *d_rho = nullptr, *d_u = nullptr;
-    cudaError_t e = cudaMalloc(&d_u, sizeof(double) * 3 * n);
-    if (e == cudaSuccess && rho) e = cudaMalloc(&d_rho, sizeof(double) * n);
-    if (e != cudaSuccess) {
-        cudaFree(d_u);
-        cudaGetLastError();
-        return fail(LBM_ERR_OOM, "staging allocation failed");
+    if (int rc = ensure_stage(h)) return rc;
+    const long long n = h->ncell * h->cfg.nbatch, C = h->stage_cells;
+    cudaError_t e = cudaSuccess;
+    int k = 0;
+    for (long long t0 = 0; t0 < n && e == cudaSuccess; t0 += C, ++k) {
+        const long long m = n - t0 < C ? n - t0 : C;
+        const int sl = k & 1;
+        double* srho = h->stage + (size_t)sl * 4 * C;
+        double* su = srho + C;
+        e = cudaStreamWaitEvent(h->xstream, h->ev_drained[sl], 0);  // chunk k-2's kernel has read the slot
+        if (e == cudaSuccess && rho)
+            e = cudaMemcpyAsync(srho, rho + t0, sizeof(double) * m, cudaMemcpyHostToDevice, h->xstream);
+        for (int c = 0; c < 3 && e == cudaSuccess; ++c)
+            e = cudaMemcpyAsync(su + c * C, u + c * n + t0, sizeof(double) * m, cudaMemcpyHostToDevice, h->xstream);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_filled[sl], h->xstream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_filled[sl], 0);
+        if (e == cudaSuccess)
+            e = launch_init_equilibrium(h->q, h->cfg.storage, h->f[h->cur], rho ? srho : nullptr, su, h->ncell,
+                                        h->cfg.nbatch, h->popstride, h->boxstride, h->stream, t0, m, C);
+        if (e == cudaSuccess) {
+            h->launches++;
+            e = cudaEventRecord(h->ev_drained[sl], h->stream);
+        }
     }
-    e = cudaMemcpyAsync(d_u, u, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess && rho) e = cudaMemcpyAsync(d_rho, rho, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream);
-    int rc = LBM_OK;
-    if (e != cudaSuccess)
-        rc = cuda_fail(e, "copying the initial fields");
-    else
-        rc = lbm_init_velocity_device(h, d_rho, d_u);
-    e = cudaStreamSynchronize(h->stream);
-    cudaFree(d_u);
-    cudaFree(d_rho);
-    if (rc == LBM_OK && e != cudaSuccess) rc = cuda_fail(e, "lbm_init_velocity");
-    return rc;
+    cudaError_t e2 = cudaStreamSynchronize(h->xstream);
+    cudaError_t e3 = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : e3;
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_init_velocity");
+    h->steps = 0;
+    return LBM_OK;
 }
 
 int lbm_set_learned_closure(lbm_handle* h, const float* params, const float* stats)
@@ -554,37 +607,46 @@ int lbm_moments_device(lbm_handle* h, double* rho_dev, double* u_dev)
 {
     if (int rc = check_handle(h)) return rc;
     cudaError_t e = launch_moments(h->q, h->cfg.storage, h->f[h->cur], rho_dev, u_dev, h->ncell, h->cfg.nbatch,
-                                   h->popstride, h->boxstride, h->cfg.force, h->stream);
+                                   h->popstride, h->boxstride, h->cfg.force, h->stream, true);
     if (e != cudaSuccess) return cuda_fail(e, "moments kernel");
     h->launches++;
     return LBM_OK;
 }
 
+// Host-pointer readback: chunk k's moments kernel (solver stream) fills one
+// staging slot while the copy stream drains chunk k-1's slot to the host.
 int lbm_moments(lbm_handle* h, double* rho, double* u)
 {
     if (int rc = check_handle(h)) return rc;
-    const size_t n = (size_t)h->ncell * h->cfg.nbatch;
-    double *d_rho = nullptr, *d_u = nullptr;
-    cudaError_t e = cudaMalloc(&d_rho, sizeof(double) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&d_u, sizeof(double) * 3 * n);
-    if (e != cudaSuccess) {
-        cudaFree(d_rho);
-        cudaGetLastError();
-        return fail(LBM_ERR_OOM, "staging allocation failed");
+    if (int rc = ensure_stage(h)) return rc;
+    const long long n = h->ncell * h->cfg.nbatch, C = h->stage_cells;
+    cudaError_t e = cudaSuccess;
+    int k = 0;
+    for (long long t0 = 0; t0 < n && e == cudaSuccess && (rho || u); t0 += C, ++k) {
+        const long long m = n - t0 < C ? n - t0 : C;
+        const int sl = k & 1;
+        double* srho = h->stage + (size_t)sl * 4 * C;
+        double* su = srho + C;
+        e = cudaStreamWaitEvent(h->stream, h->ev_drained[sl], 0);  // chunk k-2's copy has left the slot
+        if (e == cudaSuccess)
+            e = launch_moments(h->q, h->cfg.storage, h->f[h->cur], rho ? srho : nullptr, u ? su : nullptr, h->ncell,
+                               h->cfg.nbatch, h->popstride, h->boxstride, h->cfg.force, h->stream, true, t0, m, C);
+        if (e == cudaSuccess) {
+            h->launches++;
+            e = cudaEventRecord(h->ev_filled[sl], h->stream);
+        }
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->xstream, h->ev_filled[sl], 0);
+        if (e == cudaSuccess && rho)
+            e = cudaMemcpyAsync(rho + t0, srho, sizeof(double) * m, cudaMemcpyDeviceToHost, h->xstream);
+        for (int c = 0; c < 3 && e == cudaSuccess && u; ++c)
+            e = cudaMemcpyAsync(u + c * n + t0, su + c * C, sizeof(double) * m, cudaMemcpyDeviceToHost, h->xstream);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_drained[sl], h->xstream);
     }
-    int rc = lbm_moments_device(h, d_rho, d_u);
-    if (rc == LBM_OK) {
-        e = cudaSuccess;
-        if (rho) e = cudaMemcpyAsync(rho, d_rho, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
-        if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, d_u, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        if (e != cudaSuccess) rc = cuda_fail(e, "copying the fields back");
-    }
-    cudaStreamSynchronize(h->stream);
-    cudaFree(d_rho);
-    cudaFree(d_u);
-    if (rc == LBM_OK) rc = read_flag(h);
-    return rc;
+    cudaError_t e2 = cudaStreamSynchronize(h->xstream);
+    cudaError_t e3 = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : e3;
+    if (e != cudaSuccess) return cuda_fail(e, "copying the fields back");
+    return read_flag(h);
 }
 
 int lbm_wait_selftest(lbm_handle* h, int polls)

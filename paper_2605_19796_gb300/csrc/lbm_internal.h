@@ -60,10 +60,15 @@ bool step_supported(int q, int storage, int closure, int bc, int tile_y, int var
 cudaError_t prepare_step(int q, int storage, int closure, int bc, int tile_y, int variant);
 
 // Auxiliary kernels (lbm_aux.cu).
+// Cells t0 .. t0 + count - 1 (count < 0: all nbatch x ncell cells) with the
+// fields in rho [count], u [3][ustride] (ustride < 0: count)
 cudaError_t launch_init_equilibrium(int q, int storage, void* f, const double* rho, const double* u, long long ncell,
-                                    int nbatch, long long popstride, long long boxstride, cudaStream_t s);
+                                    int nbatch, long long popstride, long long boxstride, cudaStream_t s,
+                                    long long t0 = 0, long long count = -1, long long ustride = -1);
+// fp32: FP32 sums for 32- and 16-bit storage (readback); false: FP64 sums (diagnostics)
 cudaError_t launch_moments(int q, int storage, const void* f, double* rho, double* u, long long ncell, int nbatch,
-                           long long popstride, long long boxstride, const double* force, cudaStream_t s);
+                           long long popstride, long long boxstride, const double* force, cudaStream_t s,
+                           bool fp32 = false, long long t0 = 0, long long count = -1, long long ustride = -1);
 cudaError_t launch_to_f64(int q, int storage, const void* f, double* out, long long ncell, int nbatch,
                           long long popstride, long long boxstride, cudaStream_t s);
 cudaError_t launch_from_f64(int q, int storage, void* f, const double* in, long long ncell, int nbatch,

@@ -571,3 +571,32 @@ def test_bounded_wait_times_out_and_handle_stays_usable(lbm, orc):
         fg = s.get_populations()
     fo = orc.run(orc.init_equilibrium(27, rho, u), 3, closure=1, nu=1e-4, c_nu=0.035)
     assert rel(fg, fo) < TOL64
+
+
+@pytest.mark.parametrize("shape,nbatch", [((100, 100, 110), 2), ((130, 128, 128), 1)])
+def test_host_transfers_in_chunks_match_device_calls(lbm, shape, nbatch):
+    """lbm_init_velocity / lbm_moments with host pointers stream the fields
+    through two staging slots of 2^21 cells (copy of one chunk overlapped with
+    the kernel of the other).  On boxes of more than one chunk, with a chunk
+    boundary inside the second box and a ragged last chunk, they give exactly
+    what the device-pointer calls give."""
+    import torch
+
+    fields = [inputs.hit_fields(0, k0=3.0, urms=0.05, seed=60 + b, shape=shape) for b in range(nbatch)]
+    rho = np.stack([f[0] for f in fields])
+    u = np.stack([f[1] for f in fields], axis=1)
+    assert rho.size > (1 << 21)
+    with lbm.Solver(27, shape, 1e-4, closure="kcmp", storage="fp32", nbatch=nbatch) as s:
+        s.init_velocity(rho, u)
+        f_host = s.get_populations()
+        s.init_velocity_device(torch.from_numpy(rho).cuda(), torch.from_numpy(np.ascontiguousarray(u)).cuda())
+        s.synchronize()
+        assert np.array_equal(s.get_populations(), f_host)
+        s.step(2)
+        r_h, u_h = s.moments()
+        r_d = torch.empty(rho.shape, dtype=torch.float64, device="cuda")
+        u_d = torch.empty(u.shape, dtype=torch.float64, device="cuda")
+        s.moments_device(r_d, u_d)
+        s.synchronize()
+        assert np.array_equal(np.asarray(r_h).reshape(-1), r_d.cpu().numpy().reshape(-1))
+        assert np.array_equal(np.asarray(u_h).reshape(3, -1), u_d.cpu().numpy().reshape(3, -1))

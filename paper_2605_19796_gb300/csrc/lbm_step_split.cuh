@@ -82,12 +82,21 @@ __device__ __forceinline__ void pull_async(const S* __restrict__ fin, long long 
     });
 }
 
-template <int Q, typename R, int BC, int TY>
+// AH (asynchronous halo, with AS): a one-plane halo slot [Q][NB] after the
+// stash and four ring planes (the arrival moves after the strain reads,
+// below), taken only where two CTAs per SM still fit the 164 KB shared-memory
+// carveout (1 KB reserved per CTA), so that L1 keeps about 92 KB; FP64 runs
+// one CTA per SM and always fits.  Without AH the ring holds five planes.
+template <int Q, typename R, int BC, int TY, bool AS = false>
 struct SplitShape {
     using Sh = StepShape<Q, R, BC, TY>;
     static constexpr size_t ring_off = 16;  // two mbarriers
-    static constexpr size_t stash_off = ring_off + sizeof(R) * (size_t)(5 * 3 * Sh::RN);
-    static constexpr size_t bytes = stash_off + sizeof(R) * (size_t)(2 * Q * Sh::NT);
+    static constexpr size_t with_halo = ring_off + sizeof(R) * (size_t)(4 * 3 * Sh::RN + 2 * Q * Sh::NT + Q * Sh::NB);
+    static constexpr bool AH = AS && (sizeof(R) == 8 || with_halo + 1024 <= 164 * 1024 / 2);
+    static constexpr int NSLOT = AH ? 4 : 5;
+    static constexpr size_t stash_off = ring_off + sizeof(R) * (size_t)(NSLOT * 3 * Sh::RN);
+    static constexpr size_t hstash_off = stash_off + sizeof(R) * (size_t)(2 * Q * Sh::NT);
+    static constexpr size_t bytes = hstash_off + (AH ? sizeof(R) * (size_t)(Q * Sh::NB) : 0);
 };
 
 // L2PF: at plane k the CTA prefetches into L2 the source rows its pull of
@@ -95,14 +104,19 @@ struct SplitShape {
 // x-range, for the tile rows and the two halo rows), so that the loads of that
 // plane's load phase meet L2 rather than DRAM; no registers or shared memory
 // hold the prefetched data and HBM traffic is unchanged.
-// AS: the own column's pulls go to the stash by cp.async, raw, one plane
-// ahead: the copies of plane k+2 are issued into the slot that plane k's
-// populations leave as soon as the collision has read them, and are waited for
-// at the top of iteration k+1, so their latency runs under plane k's collision
-// and stores and no registers hold them in flight.  The moments of a plane and
-// the collision read the stash and subtract w.  The halo cells keep their
-// register pulls (a halo slot of its own, 9 KB at 32 x 8, took two CTAs past
-// the 164 KB shared-memory carveout and cost L1 more than the latency it hid).
+// AS: the pulls go to shared memory by cp.async, raw, one plane ahead, and no
+// registers hold them in flight.  The own column's copies of plane k+2 are
+// issued into the stash slot that plane k's populations leave as soon as the
+// collision has read them; with AH (see SplitShape) the halo cell's copies of
+// plane k+2 go to a one-plane halo slot right after the moments of plane k+1
+// have been taken from it (without AH the halo cells pull through registers).
+// The copies are waited for at the top of iteration k+1, so their latency runs
+// under plane k's collision and stores.  The moments of a plane and the
+// collision read the stash and subtract w.  With AH the ring holds four planes:
+// a thread arrives for plane k+1 only after its strain reads of plane k's
+// stencil (planes k-1..k+1), so the fastest thread, which writes plane p after
+// passing the barrier of plane p-2, overwrites the slot of plane p-4 only once
+// every thread has read it for the last time (its strain of iteration p-3).
 // 32- and 64-bit storage only (the stash holds the stored values as they are).
 template <int Q, typename S, int CL, int BC, int TY, bool L2PF = false, bool AS = false>
 __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) == 8 || TY >= 16) ? 1 : 2)
@@ -110,7 +124,7 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
 {
     using R = typename StoreTraits<S>::R;
     using Sh = StepShape<Q, R, BC, TY>;
-    using Sp = SplitShape<Q, R, BC, TY>;
+    using Sp = SplitShape<Q, R, BC, TY, AS>;
     constexpr int TX = Sh::TX, HY = Sh::HY, RX = Sh::RX, RN = Sh::RN, NT = Sh::NT, NB = Sh::NB;
     static_assert(NB <= NT, "every halo cell of the ring needs a thread");
     static_assert(CL != CL_LEARNED, "the learned closure runs in step_kernel");
@@ -118,8 +132,9 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
     static_assert(!(AS && L2PF), "one load schedule at a time");
     extern __shared__ __align__(16) unsigned char smem_sb[];
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_sb);
-    R* ring = reinterpret_cast<R*>(smem_sb + Sp::ring_off);    // [5][3][RN]
-    R* stash = reinterpret_cast<R*>(smem_sb + Sp::stash_off);  // [2][Q][NT]
+    R* ring = reinterpret_cast<R*>(smem_sb + Sp::ring_off);     // [NSLOT][3][RN]
+    R* stash = reinterpret_cast<R*>(smem_sb + Sp::stash_off);   // [2][Q][NT]
+    R* hstash = reinterpret_cast<R*>(smem_sb + Sp::hstash_off); // [Q][NB], AS only
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -180,7 +195,7 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
         zr[1] = zc * plane;
         zr[2] = (zc == nz - 1 ? 0 : zc + 1) * plane;
     };
-    auto rslot = [&](int z) { return (z - z0 + 1) % 5; };
+    auto rslot = [&](int z) { return (int)((unsigned)(z - z0 + 1) % (unsigned)Sp::NSLOT); };
     auto ringp = [&](int s, int c) { return ring + (s * 3 + c) * RN; };
     auto put_u = [&](int z, int r, R vx, R vy, R vz) {
         const int s = rslot(z);
@@ -205,17 +220,30 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
                                  (uint32_t)(NT * sizeof(R)));
         }
     };
+    constexpr bool AH = Sp::AH;
+    auto issue_halo_async = [&](int z) {  // halo cell (tid < NB), plane z -> the halo slot
+        if constexpr (AH) {
+            if (tid < NB && hal.valid) {
+                int zr[3];
+                zrows(z, zr);
+                pull_async<Q, S, BC>(fin, ps, hal, zr, (uint32_t)__cvta_generic_to_shared(hstash + tid),
+                                     (uint32_t)(NB * sizeof(R)));
+            }
+        }
+    };
 
     // pull of plane z: own cell (velocity to the ring; populations to the stash
     // when `keep`) and, with `halo`, the thread's halo cell, loads issued together;
-    // with AS and `staged`, the own cell's populations are already in the stash
+    // with AS and `staged`, both are already in the stash and the halo slot, and
+    // the halo cell's pull of the next collided plane is issued once the slot
+    // has been read
     auto load_plane = [&](int z, bool keep, bool halo, bool staged, R& r, R& vx, R& vy, R& vz) {
         int zr[3];
         zrows(z, zr);
         const bool do_h = halo && tid < NB;
         R t[Q], gh[Q];
         if (own.valid && !(AS && staged)) pull<Q, S, R, BC>(fin, ps, own, zr, t);
-        if (do_h && hal.valid) pull<Q, S, R, BC>(fin, ps, hal, zr, gh);
+        if (do_h && hal.valid && !(AH && staged)) pull<Q, S, R, BC>(fin, ps, hal, zr, gh);
         r = 0;
         vx = vy = vz = 0;
         if (own.valid) {
@@ -231,10 +259,12 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
         if (do_h) {
             R hx = 0, hy = 0, hz = 0;
             if (hal.valid) {
+                if (AH && staged) stash_g(hstash + tid, NB, gh);
                 R dh;
                 moments<Q, R>(gh, dh, hx, hy, hz, Fx, Fy, Fz);
             }
             put_u(z, hal_r, hx, hy, hz);
+            if (AH && staged && z + 1 < z1) issue_halo_async(z + 1);  // the halo slot is free again
         }
     };
     auto arrive = [&](int p) { mbar_arrive(&mbar[(p - z0) & 1]); };
@@ -244,14 +274,16 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
     {
         if constexpr (AS) {
             if (own.valid) issue_async(z0);
+            issue_halo_async(z0);
             cp_async_commit();
             if (own.valid) issue_async(z0 + 1);  // z0 + 1 <= z1
             cp_async_commit();
         }
         R r0, v0x, v0y, v0z;
         load_plane(z0 - 1, false, false, false, r0, v0x, v0y, v0z);  // z-derivative at z0 only: own column
-        if constexpr (AS) cp_async_wait<1>();  // plane z0 landed
-        load_plane(z0, true, true, true, drho, ux, uy, uz);
+        if constexpr (AS) cp_async_wait<1>();  // plane z0 (own and, with AH, halo) landed
+        load_plane(z0, true, true, true, drho, ux, uy, uz);  // with AH: issues the halo pull of z0 + 1
+        if constexpr (AH) cp_async_commit();
         arrive(z0);
     }
 
@@ -283,18 +315,22 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
         R rn, vnx, vny, vnz;
         if constexpr (AS) cp_async_wait<0>();  // plane z+1 (issued one iteration ago) landed
         load_plane(z + 1, z + 1 < z1, z + 1 < z1, true, rn, vnx, vny, vnz);
-        if (z + 1 < z1) arrive(z + 1);
+        if (!AH && z + 1 < z1) arrive(z + 1);
 
         // ---- plane z: wait until every thread has published it, then strain, closure, relaxation
         if (!wait(z)) {
             atomicOr(a.flag, kFlagTimeout);
-            return;  // with AS no copies are in flight here (all waited for above)
+            if constexpr (AH) {  // the halo copies of plane z+2 may be in flight: let them land first
+                cp_async_commit();
+                cp_async_wait<0>();
+            }
+            return;
         }
+        R du[3][3] = {};  // du[a][b] = d_a u_b
         if (own.valid) {
             // a non-finite component makes the sum non-finite (the moments are O(1))
             if (own_store && !isfinite(drho + ux + uy + uz)) atomicOr(a.flag, 1u);
             const int sm = rslot(z - 1), s0 = rslot(z), sp = rslot(z + 1);
-            R du[3][3];  // du[a][b] = d_a u_b
 #pragma unroll
             for (int b = 0; b < 3; ++b) {
                 const R* r0 = ringp(s0, b);
@@ -307,6 +343,10 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
                 else
                     du[1][b] = R(0.5) * (r0[own_r + RX] - r0[own_r - RX]);
             }
+        }
+        // with AH the arrival for plane z+1 also says "done reading planes z-1..z+1"
+        if (AH && z + 1 < z1) arrive(z + 1);
+        if (own.valid) {
             const R Sxx = du[0][0], Syy = du[1][1], Szz = du[2][2];
             const R Sxy = R(0.5) * (du[0][1] + du[1][0]);
             const R Sxz = R(0.5) * (du[0][2] + du[2][0]);
@@ -342,7 +382,7 @@ template <int Q, typename S, int CL, int BC, int TY, bool L2PF = false, bool AS 
 cudaError_t prepare_sb_t()
 {
     return cudaFuncSetAttribute(step_kernel_sb<Q, S, CL, BC, TY, L2PF, AS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)SplitShape<Q, typename StoreTraits<S>::R, BC, TY>::bytes);
+                                (int)SplitShape<Q, typename StoreTraits<S>::R, BC, TY, AS>::bytes);
 }
 
 template <int Q, typename S, int CL, int BC, int TY, bool L2PF = false, bool AS = false>
@@ -359,7 +399,7 @@ cudaError_t launch_sb_t(const StepArgs& a, int nbatch, cudaStream_t s)
     const int chunks = (a.nz + a.zchunk - 1) / a.zchunk;
     dim3 grid(tiles, chunks, nbatch), block(Sh::TX, TY);
     step_kernel_sb<Q, S, CL, BC, TY, L2PF, AS>
-        <<<grid, block, SplitShape<Q, typename StoreTraits<S>::R, BC, TY>::bytes, s>>>(a);
+        <<<grid, block, SplitShape<Q, typename StoreTraits<S>::R, BC, TY, AS>::bytes, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -103,7 +103,8 @@ typedef struct {
     int variant;        /* tuning: step-kernel variant, 0 = library default
                            (13 for FP32 storage with KC-MP, KC-RB or KC-RR
                            where built, i.e. periodic D3Q27/D3Q19 and walls
-                           with KC-MP; else 8 for periodic D3Q27; else 1),
+                           with KC-MP; else 8 for periodic D3Q27, the learned
+                           closure included; else 1),
                            1 = register pull (every lattice, storage, closure
                            and boundary), 4 = TMA-staged pipeline (FP32,
                            periodic, BGK/KC-MP/KC-RB, nx % 32 == 0 and

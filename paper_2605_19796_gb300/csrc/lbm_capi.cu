@@ -356,13 +356,13 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
     // measured defaults: FP32 storage with a closure carrier (KC-MP, KC-RB,
     // KC-RR) takes the split-barrier pull with asynchronous own pulls (13)
     // wherever it is built (D3Q27 and D3Q19, periodic and, for KC-MP, walls);
-    // periodic D3Q27 otherwise (BGK, FP64, 16-bit storage) the split-barrier
-    // pull (8); everything else the register pull (1).  lbm_autotune may pick
+    // periodic D3Q27 otherwise (BGK, the learned closure, FP64, 16-bit storage)
+    // the split-barrier pull (8); everything else the register pull (1).  lbm_autotune may pick
     // another variant for a given box
     if (variant == VAR_DEFAULT) {
         const bool carrier = cfg->closure == LBM_KCMP || cfg->closure == LBM_KCRB_HERMITE ||
                              cfg->closure == LBM_KCRB_RAW || cfg->closure == LBM_KCRR;
-        const bool split_built = carrier || cfg->closure == LBM_BGK;
+        const bool split_built = carrier || cfg->closure == LBM_BGK || cfg->closure == LBM_LEARNED;
         if (carrier && cfg->storage == LBM_FP32 &&
             step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, VAR_ASYNC))
             variant = VAR_ASYNC;

@@ -56,6 +56,7 @@ cudaError_t launch_step_qs(int closure, int bc, int ty, int variant, const StepA
         if constexpr (R32) {
             LBM_SB_CASE(CL_KCMP, BC_PERIODIC, 4)
             LBM_SB_CASE(CL_KCMP, BC_PERIODIC, 16)
+            LBM_SB_CASE(CL_LEARNED, BC_PERIODIC, 8)
         }
 #undef LBM_SB_CASE
         return cudaErrorNotSupported;

@@ -99,6 +99,15 @@ struct SplitShape {
     static constexpr size_t bytes = hstash_off + (AH ? sizeof(R) * (size_t)(Q * Sh::NB) : 0);
 };
 
+// dynamic shared memory of one CTA; the learned closure adds the packed network
+// block and the per-warp input/output exchange after the split-barrier layout
+template <int Q, typename R, int BC, int TY, bool AS, int CL>
+constexpr size_t sb_smem_bytes()
+{
+    return SplitShape<Q, R, BC, TY, AS>::bytes +
+           (CL == CL_LEARNED ? (size_t)(MlpLayout::BYTES + TY * MlpLayout::XCH_BYTES) : 0);
+}
+
 // L2PF: at plane k the CTA prefetches into L2 the source rows its pull of
 // plane k+2 will read (one 128-byte line per population and row: the tile's
 // x-range, for the tile rows and the two halo rows), so that the loads of that
@@ -127,7 +136,8 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
     using Sp = SplitShape<Q, R, BC, TY, AS>;
     constexpr int TX = Sh::TX, HY = Sh::HY, RX = Sh::RX, RN = Sh::RN, NT = Sh::NT, NB = Sh::NB;
     static_assert(NB <= NT, "every halo cell of the ring needs a thread");
-    static_assert(CL != CL_LEARNED, "the learned closure runs in step_kernel");
+    static_assert(CL != CL_LEARNED || (!AS && sizeof(R) == 4), "the learned closure reads g = f - w from the stash");
+    static_assert(Sp::bytes % 16 == 0, "the network block is copied in 16-byte words");
     static_assert(!AS || sizeof(S) == sizeof(R), "the asynchronous stash holds stored values as they are");
     static_assert(!(AS && L2PF), "one load schedule at a time");
     extern __shared__ __align__(16) unsigned char smem_sb[];
@@ -135,6 +145,13 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
     R* ring = reinterpret_cast<R*>(smem_sb + Sp::ring_off);     // [NSLOT][3][RN]
     R* stash = reinterpret_cast<R*>(smem_sb + Sp::stash_off);   // [2][Q][NT]
     R* hstash = reinterpret_cast<R*>(smem_sb + Sp::hstash_off); // [Q][NB], AS only
+    unsigned char* sm_mlp = smem_sb + Sp::bytes;                 // learned closure only
+    unsigned char* sm_xch = sm_mlp + MlpLayout::BYTES + threadIdx.y * MlpLayout::XCH_BYTES;
+    if constexpr (CL == CL_LEARNED) {
+        const uint4* src = static_cast<const uint4*>(a.mlp);
+        uint4* dst = reinterpret_cast<uint4*>(sm_mlp);
+        for (int k = threadIdx.y * 32 + threadIdx.x; k < MlpLayout::BYTES / 16; k += 32 * TY) dst[k] = src[k];
+    }
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -360,8 +377,17 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
 #pragma unroll
                 for (int i = 0; i < Q; ++i) g[i] = st[i * NT];
             }
-            collide<Q, R, CL, FORCE>(g, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, omega, tau_hat, nu, cnud, Fx,
-                                     Fy, Fz);
+            if constexpr (CL == CL_LEARNED) {
+                // every lane of the warp takes part (periodic columns are always valid)
+                R msgs[6];
+                learned_msgs<Q, R, NT>(stash_col(z), drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, tau_hat, sm_mlp,
+                                       sm_xch, tx, msgs);
+                collide<Q, R, CL, FORCE>(g, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, omega, tau_hat, nu, cnud,
+                                         Fx, Fy, Fz, msgs);
+            } else {
+                collide<Q, R, CL, FORCE>(g, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, omega, tau_hat, nu, cnud,
+                                         Fx, Fy, Fz);
+            }
             if (own_store) {
                 const int cell = z * plane + own.yr[1] + own.xs[1];
                 static_for<Q>([&](auto I) {
@@ -382,13 +408,14 @@ template <int Q, typename S, int CL, int BC, int TY, bool L2PF = false, bool AS 
 cudaError_t prepare_sb_t()
 {
     return cudaFuncSetAttribute(step_kernel_sb<Q, S, CL, BC, TY, L2PF, AS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)SplitShape<Q, typename StoreTraits<S>::R, BC, TY, AS>::bytes);
+                                (int)sb_smem_bytes<Q, typename StoreTraits<S>::R, BC, TY, AS, CL>());
 }
 
 template <int Q, typename S, int CL, int BC, int TY, bool L2PF = false, bool AS = false>
 cudaError_t launch_sb_t(const StepArgs& a, int nbatch, cudaStream_t s)
 {
     using Sh = StepShape<Q, typename StoreTraits<S>::R, BC, TY>;
+    if (CL == CL_LEARNED && !a.mlp) return cudaErrorInvalidValue;
     static bool attr_set = false;  // per instantiation; prepare_sb_t sets it ahead of stream capture
     if (!attr_set) {
         cudaError_t e = prepare_sb_t<Q, S, CL, BC, TY, L2PF, AS>();
@@ -399,7 +426,7 @@ cudaError_t launch_sb_t(const StepArgs& a, int nbatch, cudaStream_t s)
     const int chunks = (a.nz + a.zchunk - 1) / a.zchunk;
     dim3 grid(tiles, chunks, nbatch), block(Sh::TX, TY);
     step_kernel_sb<Q, S, CL, BC, TY, L2PF, AS>
-        <<<grid, block, SplitShape<Q, typename StoreTraits<S>::R, BC, TY, AS>::bytes, s>>>(a);
+        <<<grid, block, sb_smem_bytes<Q, typename StoreTraits<S>::R, BC, TY, AS, CL>(), s>>>(a);
     return cudaGetLastError();
 }
 

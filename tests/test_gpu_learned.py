@@ -170,12 +170,14 @@ def _stats_for(x, scale_out):
     return np.concatenate([xm, xs, np.zeros(6), np.full(6, scale_out)]).astype(np.float32)
 
 
-def test_learned_step_matches_oracle(env, orc):
+@pytest.mark.parametrize("variant", [1, 8])
+def test_learned_step_matches_oracle(env, orc, variant):
     """One step of the fused learned closure (BF16 tensor-core network inside the
-    step kernel) against the oracle's learned step with the same BF16 rounding
+    step kernel: the register pull, variant 1, and the split-barrier kernel,
+    variant 8) against the oracle's learned step with the same BF16 rounding
     points (inputs, weights, hidden activations) and FP64 elsewhere.  The network
     is random, its output scaled so that the turbulent rate is active in most
-    cells.
+    cells.  The z-chunk of 5 planes leaves a ragged last chunk.
 
     Tolerance: the state is stored in FP32, so the resolved part of the update
     carries FP32 rounding noise; it is measured on the same state by the BGK
@@ -195,7 +197,8 @@ def test_learned_step_matches_oracle(env, orc):
     scale = 5.0 * float(np.abs(x[:, :6]).std())
     stats = _stats_for(x, scale)
     params = np.asarray(mlp.flat(mlp.init_params(5)), dtype=np.float32)
-    with lbm.Solver(27, shape, nu, closure="learned", storage="fp32") as s:
+    with lbm.Solver(27, shape, nu, closure="learned", storage="fp32", variant=variant, zchunk=5) as s:
+        assert s.launch_config["variant"] == variant
         s.set_learned_closure(params, stats)
         s.set_populations(f)
         s.step(1)

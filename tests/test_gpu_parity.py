@@ -426,14 +426,14 @@ def test_default_variant_selection(lbm):
     """Library default: the split-barrier pull with asynchronous own pulls (13)
     for FP32 storage with KC-MP, KC-RB or KC-RR where it is built (D3Q27 and
     D3Q19; walls with KC-MP), the split-barrier pull (8) for periodic D3Q27
-    otherwise (BGK, FP64, 16-bit storage), the register pull (1) for the rest
-    (D3Q19 BGK, walls with KC-RB, the learned closure); an explicitly requested
-    variant that is not built for a box is refused."""
+    otherwise (BGK, the learned closure, FP64, 16-bit storage), the register
+    pull (1) for the rest (D3Q19 BGK, walls with KC-RB); an explicitly
+    requested variant that is not built for a box is refused."""
     for q, closure, storage, want in ((27, "kcmp", "fp32", 13), (27, "kcrb_hermite", "fp16", 8), (27, "kcmp", "fp64", 8),
                                       (27, "kcrb_raw", "fp32", 13), (27, "kcrr", "fp32", 13),
                                       (27, "bgk", "fp32", 8), (19, "kcmp", "fp32", 13), (19, "bgk", "fp32", 1),
                                       (19, "kcmp", "fp16", 1), (27, "kcrr", "fp64", 8),
-                                      (27, "learned", "fp32", 1)):
+                                      (27, "learned", "fp32", 8)):
         with lbm.Solver(q, (40, 32, 16), 1e-4, closure=closure, storage=storage) as s:
             assert s.launch_config["variant"] == want, (q, closure, storage)
     for q, closure, want in ((27, "kcmp", 13), (19, "kcmp", 13), (27, "kcrb_hermite", 1), (27, "bgk", 1)):
@@ -600,3 +600,35 @@ def test_host_transfers_in_chunks_match_device_calls(lbm, shape, nbatch):
         s.synchronize()
         assert np.array_equal(np.asarray(r_h).reshape(-1), r_d.cpu().numpy().reshape(-1))
         assert np.array_equal(np.asarray(u_h).reshape(3, -1), u_d.cpu().numpy().reshape(3, -1))
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+@pytest.mark.parametrize("closure", ["bgk", "kcmp", "kcrb_raw"])
+def test_load_schedule_variants_d3q19(lbm, orc, storage, closure):
+    """The load schedules of the split-barrier kernel on D3Q19 (variant 13
+    with its asynchronous halo slot and four-plane ring is the D3Q19 FP32
+    default for the closures with a carrier): ragged box, two boxes, several
+    z-chunkings; FP64 against the oracle to 1e-12, FP32 against variant 1, and
+    within a variant the z-chunking changes no bit."""
+    shape = (45, 19, 23)
+    fields = [inputs.hit_fields(0, k0=3.0, urms=0.07, seed=70 + b, shape=shape) for b in range(2)]
+    rho = np.stack([f[0] for f in fields])
+    u = np.stack([f[1] for f in fields], axis=1)
+    nus = np.array([2e-5, 1e-4])
+    res = {}
+    for var, zc in [(1, 0)] + [(v, z) for v in (8, 12, 13) for z in (0, 1, 2, 5)]:
+        with lbm.Solver(19, shape, nus, closure=closure, storage=storage, variant=var, zchunk=zc, nbatch=2) as s:
+            assert s.launch_config["variant"] == var
+            s.init_velocity(rho, u)
+            s.step(5)
+            res[(var, zc)] = s.get_populations()
+    for v in (8, 12, 13):
+        for zc in (1, 2, 5):
+            assert np.array_equal(res[(v, zc)], res[(v, 0)]), (v, zc)
+        if storage == "fp64":
+            for b in range(2):
+                fo = orc.run(orc.init_equilibrium(19, fields[b][0], fields[b][1]), 5, closure=CL[closure], nu=nus[b],
+                             c_nu=CNU[closure])
+                assert rel(res[(v, 0)][b], fo) < TOL64, v
+        else:
+            assert rel(res[(v, 0)], res[(1, 0)]) < 1e-6, v

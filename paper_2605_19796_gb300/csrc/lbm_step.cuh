@@ -776,21 +776,32 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
     Col hal = own;
     int hal_r = -1;
     if (tid < NB) {
+        // the rows y0 - 1 and y0 + TY, then the two columns (every tile reads
+        // them), then, with walls, the outer rows y0 - 2 and y0 + TY + 1
         int lx, ly;
         int b = tid;
-        if (b < HY * RX) {
-            lx = b % RX - 1;
-            ly = b / RX - HY;
-        } else if ((b -= HY * RX) < HY * RX) {
-            lx = b % RX - 1;
-            ly = TY + b / RX;
-        } else {
-            b -= HY * RX;
+        if (b < RX) {
+            lx = b - 1;
+            ly = -1;
+        } else if ((b -= RX) < RX) {
+            lx = b - 1;
+            ly = TY;
+        } else if ((b -= RX) < 2 * TY) {
             lx = (b < TY) ? -1 : TX;
             ly = b % TY;
+        } else {
+            b -= 2 * TY;
+            lx = b % RX - 1;
+            ly = (b < RX) ? -2 : TY + 1;
         }
         hal = make_col<BC>(x0 + lx, y0 + ly, nx, ny);
         hal_r = (ly + HY) * RX + (lx + 1);
+        // The outer rows feed only the one-sided wall stencils (Eqs. fd_boundary):
+        // the wall row y = 0 is a tile's first row and reads rows 1, 2 inside it;
+        // the wall row y = ny - 1 reads ly = -2 only when it is the tile's first
+        // row (y0 = ny - 1).  Otherwise they are not pulled (their ring entries
+        // are never read).
+        if (BC == BC_WALLS_Y && (ly == -2 || ly == TY + 1) && !(ly == -2 && y0 == ny - 1)) hal.valid = false;
     }
 
     auto zrows = [&](int z, int (&zr)[3]) {

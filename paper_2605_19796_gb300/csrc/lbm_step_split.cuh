@@ -209,6 +209,8 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
         // row (y0 = ny - 1).  Otherwise they are not pulled (their ring entries
         // are never read).
         if (BC == BC_WALLS_Y && (ly == -2 || ly == TY + 1) && !(ly == -2 && y0 == ny - 1)) hal.valid = false;
+        // the corners are never read either (the stencils are +-1 in x or in y)
+        if ((lx == -1 || lx == TX) && (ly < 0 || ly >= TY)) hal.valid = false;
     }
 
     if (tid == 0) {

@@ -101,10 +101,11 @@ typedef struct {
     int tile_y;         /* tuning: rows per CTA tile (0 = library default)           */
     int zchunk;         /* tuning: z-planes per CTA march (0 = library default)      */
     int variant;        /* tuning: step-kernel variant, 0 = library default
-                           (13 for FP32 storage with KC-MP, KC-RB or KC-RR
-                           where built, i.e. periodic D3Q27/D3Q19 and walls
-                           with KC-MP; else 8 for periodic D3Q27, the learned
-                           closure included; else 1),
+                           (FP32 storage: 12 on z-chunks of at most 16 planes
+                           for periodic D3Q27 with KC-MP or KC-RB, 13 for
+                           KC-RR, D3Q19 and walls with KC-MP; else 8 for
+                           periodic D3Q27, the learned closure included;
+                           else 1),
                            1 = register pull (every lattice, storage, closure
                            and boundary), 4 = TMA-staged pipeline (FP32,
                            periodic, BGK/KC-MP/KC-RB, nx % 32 == 0 and

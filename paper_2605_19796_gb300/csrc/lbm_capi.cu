@@ -353,24 +353,33 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
         cfg->variant != VAR_PAIR && cfg->variant != VAR_SPLIT_PF && cfg->variant != VAR_ASYNC)
         return fail(LBM_ERR_ARG, "unknown kernel variant");
     int variant = cfg->variant;
-    // measured defaults: FP32 storage with a closure carrier (KC-MP, KC-RB,
-    // KC-RR) takes the split-barrier pull with asynchronous own pulls (13)
-    // wherever it is built (D3Q27 and D3Q19, periodic and, for KC-MP, walls);
-    // periodic D3Q27 otherwise (BGK, the learned closure, FP64, 16-bit storage)
-    // the split-barrier pull (8); everything else the register pull (1).  lbm_autotune may pick
-    // another variant for a given box
+    // measured defaults (512^3 and ensemble timings): for FP32 storage, periodic
+    // D3Q27 with KC-MP or KC-RB takes the split-barrier pull with L2 prefetches
+    // (12) marching short z-chunks (at most 16 planes); KC-RR, D3Q19 and the
+    // walls with KC-MP take the split-barrier pull with asynchronous copies (13);
+    // otherwise periodic D3Q27 (BGK, the learned closure, FP64, 16-bit storage)
+    // takes the split-barrier pull (8) and the rest the register pull (1).
+    // lbm_autotune may pick another launch for a given box
+    bool short_chunks = false;
     if (variant == VAR_DEFAULT) {
         const bool carrier = cfg->closure == LBM_KCMP || cfg->closure == LBM_KCRB_HERMITE ||
                              cfg->closure == LBM_KCRB_RAW || cfg->closure == LBM_KCRR;
         const bool split_built = carrier || cfg->closure == LBM_BGK || cfg->closure == LBM_LEARNED;
-        if (carrier && cfg->storage == LBM_FP32 &&
-            step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, VAR_ASYNC))
+        const bool pf_first = cfg->lattice == LBM_D3Q27 && bc_kind == BC_PERIODIC && cfg->storage == LBM_FP32 &&
+                              (cfg->closure == LBM_KCMP || cfg->closure == LBM_KCRB_HERMITE ||
+                               cfg->closure == LBM_KCRB_RAW);
+        if (pf_first && step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, VAR_SPLIT_PF)) {
+            variant = VAR_SPLIT_PF;
+            short_chunks = true;
+        } else if (carrier && cfg->storage == LBM_FP32 &&
+                   step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, VAR_ASYNC)) {
             variant = VAR_ASYNC;
-        else if (cfg->lattice == LBM_D3Q27 && split_built && bc_kind == BC_PERIODIC &&
-                 step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, VAR_SPLIT))
+        } else if (cfg->lattice == LBM_D3Q27 && split_built && bc_kind == BC_PERIODIC &&
+                   step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, VAR_SPLIT)) {
             variant = VAR_SPLIT;
-        else
+        } else {
             variant = VAR_REGISTER;
+        }
     }
     if (variant == VAR_TMA && !tma_shape_ok(cfg->nx, cfg->ny, tile_y))
         return fail(LBM_ERR_UNSUPPORTED, "the TMA variant needs nx % 32 == 0 and ny % tile_y == 0");
@@ -393,6 +402,7 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
     h->tile_y = tile_y;
     h->variant = variant;
     h->zchunk = cfg->zchunk ? cfg->zchunk : default_zchunk(cfg->nx, cfg->ny, cfg->nz, cfg->nbatch, tile_y);
+    if (!cfg->zchunk && short_chunks && h->zchunk > 16) h->zchunk = 16;
     h->bc_kind = bc_kind;
 
     cudaError_t e = cudaMalloc(&h->f[0], h->buf_bytes);

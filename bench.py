@@ -71,14 +71,16 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
+KERNEL_SOURCES = ("lbm_lattice.cuh", "lbm_mbarrier.cuh", "lbm_mlp_infer.cuh", "lbm_step.cuh", "lbm_step_split.cuh",
+                  "lbm_step_tma.cuh", "lbm_step_x2.cuh")
+
+
 def kernel_hash() -> str:
-    """Hash of the device sources of the step kernels (the host code that picks
-    the launch is checked through the launch recorded beside the traffic)."""
+    """Hash of the files that hold the step kernels' device code (the units that
+    only instantiate them, and the host code that picks the launch, are checked
+    through the launch recorded beside the traffic)."""
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2605_19796_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if not (f.startswith("lbm_step") or f in ("lbm_lattice.cuh", "lbm_mbarrier.cuh", "lbm_mlp_infer.cuh")):
-            continue
+    for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_2605_19796_gb300", "csrc", f), "rb") as fp:
             h.update(fp.read())
     return h.hexdigest()[:16]

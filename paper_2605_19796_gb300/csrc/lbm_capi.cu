@@ -354,11 +354,11 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
         return fail(LBM_ERR_ARG, "unknown kernel variant");
     int variant = cfg->variant;
     // measured defaults (512^3 and ensemble timings): for FP32 storage, periodic
-    // D3Q27 with KC-MP or KC-RB takes the split-barrier pull with L2 prefetches
-    // (12) marching short z-chunks (at most 16 planes); KC-RR, D3Q19 and the
-    // walls with KC-MP take the split-barrier pull with asynchronous copies (13);
-    // otherwise periodic D3Q27 (BGK, the learned closure, FP64, 16-bit storage)
-    // takes the split-barrier pull (8) and the rest the register pull (1).
+    // D3Q27 with KC-MP, KC-RB or the learned closure takes the split-barrier
+    // pull with L2 prefetches (12) marching short z-chunks (at most 16 planes);
+    // KC-RR, D3Q19 and the walls with KC-MP take the split-barrier pull with
+    // asynchronous copies (13); otherwise periodic D3Q27 (BGK, FP64, 16-bit
+    // storage) takes the split-barrier pull (8) and the rest the register pull (1).
     // lbm_autotune may pick another launch for a given box
     bool short_chunks = false;
     if (variant == VAR_DEFAULT) {
@@ -367,7 +367,7 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
         const bool split_built = carrier || cfg->closure == LBM_BGK || cfg->closure == LBM_LEARNED;
         const bool pf_first = cfg->lattice == LBM_D3Q27 && bc_kind == BC_PERIODIC && cfg->storage == LBM_FP32 &&
                               (cfg->closure == LBM_KCMP || cfg->closure == LBM_KCRB_HERMITE ||
-                               cfg->closure == LBM_KCRB_RAW);
+                               cfg->closure == LBM_KCRB_RAW || cfg->closure == LBM_LEARNED);
         if (pf_first && step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, VAR_SPLIT_PF)) {
             variant = VAR_SPLIT_PF;
             short_chunks = true;

@@ -74,6 +74,9 @@ cudaError_t launch_step_qs(int closure, int bc, int ty, int variant, const StepA
         if constexpr (Q == 27) {
             LBM_SBP_CASE(CL_KCRR, BC_PERIODIC, 8)
         }
+        if constexpr (R32) {
+            LBM_SBP_CASE(CL_LEARNED, BC_PERIODIC, 8)
+        }
 #undef LBM_SBP_CASE
         return cudaErrorNotSupported;
     }

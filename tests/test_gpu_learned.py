@@ -170,11 +170,11 @@ def _stats_for(x, scale_out):
     return np.concatenate([xm, xs, np.zeros(6), np.full(6, scale_out)]).astype(np.float32)
 
 
-@pytest.mark.parametrize("variant", [1, 8])
+@pytest.mark.parametrize("variant", [1, 8, 12])
 def test_learned_step_matches_oracle(env, orc, variant):
     """One step of the fused learned closure (BF16 tensor-core network inside the
-    step kernel: the register pull, variant 1, and the split-barrier kernel,
-    variant 8) against the oracle's learned step with the same BF16 rounding
+    step kernel: the register pull, variant 1, the split-barrier kernel,
+    variant 8, and the same with L2 prefetches, variant 12) against the oracle's learned step with the same BF16 rounding
     points (inputs, weights, hidden activations) and FP64 elsewhere.  The network
     is random, its output scaled so that the turbulent rate is active in most
     cells.  The z-chunk of 5 planes leaves a ragged last chunk.

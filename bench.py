@@ -40,6 +40,7 @@ WORKLOADS = {
     "hit512_d3q27_fp32_kcrr": dict(n=512, q=27, storage="fp32", closure="kcrr", nu=1e-4, k0=4.0, urms=0.04),
     "hit512_d3q27_fp32_kcrb_raw": dict(n=512, q=27, storage="fp32", closure="kcrb_raw", nu=1e-4, k0=4.0, urms=0.04),
     "hit256_d3q27_fp64_kcmp": dict(n=256, q=27, storage="fp64", closure="kcmp", nu=1e-4, k0=4.0, urms=0.04),
+    "hit128_d3q27_fp64_kcmp": dict(n=128, q=27, storage="fp64", closure="kcmp", nu=1e-4, k0=4.0, urms=0.04),
     # learned closure (KC-MP with the network's m_sgs, fused BF16 tensor-core inference)
     "hit256_d3q27_fp32_learned": dict(n=256, q=27, storage="fp32", closure="learned", nu=2.5e-5, k0=4.0, urms=0.04),
     "hit128_d3q27_fp32_learned": dict(n=128, q=27, storage="fp32", closure="learned", nu=2.5e-5, k0=4.0, urms=0.04),
@@ -84,6 +85,28 @@ def kernel_hash() -> str:
         with open(os.path.join(ROOT, "paper_2605_19796_gb300", "csrc", f), "rb") as fp:
             h.update(fp.read())
     return h.hexdigest()[:16]
+
+
+def fp64_ops_per_cell(workload: str, launch: dict):
+    """FP64 instructions and flops per cell update of the step kernel (FP64
+    storage) from the committed ncu counts, if taken on the current kernel
+    source and the same kernel instantiation."""
+    p = os.path.join(ROOT, "profiles", "step_kernel_fp64_ops.json")
+    try:
+        with open(p) as fp:
+            e = json.load(fp).get(workload)
+        same = all(e.get("launch", {}).get(k) == launch.get(k) for k in ("variant", "tile_y")) if e else False
+        if e and same and e.get("kernel_hash") == kernel_hash():
+            return float(e["fp64_instructions_per_cell"]), float(e["fp64_flops_per_cell"])
+    except Exception:
+        pass
+    return None
+
+
+# GB300 FP64 pipe: the nominal 1.25 TFLOP/s is 2 FP64 instructions per SM per
+# clock on 152 SMs at the 2070 MHz maximum clock
+FP64_INSTR_PER_SM_CLK = 2
+N_SM = 152
 
 
 def measured_peak_hbm():
@@ -351,6 +374,18 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (tpc * N if tpc is not None else None), "peak_source": peak_src,
                 "algorithmic_bytes_per_cell": 2 * q * ELEM[wl["storage"]], "frac_of_nominal_8TBs": achieved / 8000.0}
+    ops = fp64_ops_per_cell(args.workload, s.launch_config) if wl["storage"] == "fp64" else None
+    if ops is not None:
+        # FP64 storage runs FP64 arithmetic, bound by GB300's FP64 pipe
+        sm_mhz = 2070.0
+        fpeak = FP64_INSTR_PER_SM_CLK * N_SM * sm_mhz * 1e6 / 1e9
+        fach = ops[0] * N / kern_s / 1e9
+        roofline = {"bound": "alu", "achieved": fach, "peak": fpeak, "unit": "G FP64 instructions/s",
+                    "frac": fach / fpeak, "traffic": None,
+                    "peak_source": "nominal FP64 rate 1.25 TFLOP/s = 2 FP64 instructions per SM per clock, "
+                                   "152 SMs at 2070 MHz",
+                    "fp64_instructions_per_cell": ops[0], "fp64_tflops": ops[1] * N / kern_s / 1e12,
+                    "hbm_frac": achieved / peak}
 
     # end to end through the C ABI with pinned host buffers:
     # lbm_init_velocity (H2D of rho, u) + K steps + lbm_moments (D2H of rho, u)

@@ -35,6 +35,8 @@ WORKLOADS = {
     "hit256_d3q27_fp32_kcmp": dict(n=256, q=27, storage="fp32", closure="kcmp", nu=1e-4, k0=4.0, urms=0.04),
     "hit512_d3q27_fp16_kcmp": dict(n=512, q=27, storage="fp16", closure="kcmp", nu=1e-4, k0=4.0, urms=0.04),
     "hit512_d3q27_bf16_kcmp": dict(n=512, q=27, storage="bf16", closure="kcmp", nu=1e-4, k0=4.0, urms=0.04),
+    "hit256_d3q27_fp16_kcmp": dict(n=256, q=27, storage="fp16", closure="kcmp", nu=1e-4, k0=4.0, urms=0.04),
+    "hit256_d3q27_bf16_kcmp": dict(n=256, q=27, storage="bf16", closure="kcmp", nu=1e-4, k0=4.0, urms=0.04),
     "hit512_d3q19_fp32_kcmp": dict(n=512, q=19, storage="fp32", closure="kcmp", nu=1e-4, k0=4.0, urms=0.04),
     "hit512_d3q27_fp32_bgk": dict(n=512, q=27, storage="fp32", closure="bgk", nu=1e-4, k0=4.0, urms=0.04),
     "hit512_d3q27_fp32_kcrr": dict(n=512, q=27, storage="fp32", closure="kcrr", nu=1e-4, k0=4.0, urms=0.04),
@@ -102,6 +104,25 @@ def fp64_ops_per_cell(workload: str, launch: dict):
         pass
     return None
 
+
+def warp_instructions_per_cell(workload: str, launch: dict):
+    """Warp instructions per cell update of the step kernel (16-bit storage)
+    from the committed ncu counts, if taken on the current kernel source and
+    the same kernel instantiation."""
+    p = os.path.join(ROOT, "profiles", "step_kernel_issue.json")
+    try:
+        with open(p) as fp:
+            e = json.load(fp).get(workload)
+        same = all(e.get("launch", {}).get(k) == launch.get(k) for k in ("variant", "tile_y")) if e else False
+        if e and same and e.get("kernel_hash") == kernel_hash():
+            return float(e["warp_instructions_per_cell"]), float(e["dram_bytes_per_cell"])
+    except Exception:
+        pass
+    return None
+
+
+# SM instruction issue: 4 schedulers per SM, one warp instruction each per clock
+ISSUE_PER_SM_CLK = 4
 
 # GB300 FP64 pipe: the nominal 1.25 TFLOP/s is 2 FP64 instructions per SM per
 # clock on 152 SMs at the 2070 MHz maximum clock
@@ -374,6 +395,18 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (tpc * N if tpc is not None else None), "peak_source": peak_src,
                 "algorithmic_bytes_per_cell": 2 * q * ELEM[wl["storage"]], "frac_of_nominal_8TBs": achieved / 8000.0}
+    wi = warp_instructions_per_cell(args.workload, s.launch_config) if wl["storage"] in ("fp16", "bf16") else None
+    if wi is not None:
+        # 16-bit storage halves the bytes; the same FP32 arithmetic then bounds
+        # the step by instruction issue
+        ipeak = ISSUE_PER_SM_CLK * N_SM * 2070.0 * 1e6 / 1e9
+        iach = wi[0] * N / kern_s / 1e9
+        roofline = {"bound": "alu", "achieved": iach, "peak": ipeak, "unit": "G warp instructions/s",
+                    "frac": iach / ipeak, "traffic": wi[1] * N,
+                    "peak_source": "instruction issue: 4 schedulers per SM, one warp instruction each per clock, "
+                                   "152 SMs at 2070 MHz",
+                    "warp_instructions_per_cell": wi[0], "hbm_frac": achieved / peak,
+                    "algorithmic_bytes_per_cell": 2 * q * ELEM[wl["storage"]]}
     ops = fp64_ops_per_cell(args.workload, s.launch_config) if wl["storage"] == "fp64" else None
     if ops is not None:
         # FP64 storage runs FP64 arithmetic, bound by GB300's FP64 pipe

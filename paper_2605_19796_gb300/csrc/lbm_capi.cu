@@ -288,6 +288,13 @@ int ensure_stage(lbm_handle* h)
         cudaGetLastError();
         if (h->stage) cudaFree(h->stage);
         h->stage = nullptr;
+        for (int k = 0; k < 2; ++k) {
+            if (h->ev_filled[k]) cudaEventDestroy(h->ev_filled[k]);
+            if (h->ev_drained[k]) cudaEventDestroy(h->ev_drained[k]);
+            h->ev_filled[k] = h->ev_drained[k] = nullptr;
+        }
+        if (h->xstream) cudaStreamDestroy(h->xstream);
+        h->xstream = nullptr;
         return fail(LBM_ERR_OOM, "staging ring allocation failed");
     }
     h->stage_cells = c;

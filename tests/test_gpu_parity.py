@@ -339,6 +339,30 @@ def test_full_size_sampled_cells_fp32(lbm, orc, n):
     assert abs(mass1 - mass0) <= 1e-9 * mass0
 
 
+def test_full_size_sampled_cells_kcrr(lbm, orc):
+    """KC-RR at 256^3 (D3Q27, FP32, its default launch: asynchronous copies,
+    variant 13): one GPU step, then sampled cells against the oracle's
+    single-cell KC-RR step on the GPU's own pre-step populations; tolerance as
+    for KC-MP (the separable Hermite transforms add ~10^2 operations)."""
+    n = 256
+    rho, u = inputs.hit_fields(n, k0=4.0, urms=0.04, seed=1)
+    pts = _sampled_cells(n, 32, seed=7)
+    offs = np.array([(dx, dy, dz) for dz in range(-2, 3) for dy in range(-2, 3) for dx in range(-2, 3)])
+    with lbm.Solver(27, (n, n, n), 1e-4, closure="kcrr", c_nu=0.02, storage="fp32") as s:
+        assert s.launch_config["variant"] == 13
+        s.init_velocity(rho, u)
+        del rho, u
+        s.step(3)
+        blocks = s.probe((pts[:, None, :] + offs[None, :, :]).reshape(-1, 3)).reshape(len(pts), 125, 27)
+        s.step(1)
+        after = s.probe(pts)
+    scale = np.abs(after).max()
+    for k in range(len(pts)):
+        blk = blocks[k].T.reshape(27, 5, 5, 5)
+        ref = orc.step_cell(blk, closure=4, nu=1e-4, c_nu=0.02)
+        assert np.abs(after[k] - ref).max() <= 2e-6 * scale, (pts[k], np.abs(after[k] - ref).max())
+
+
 def test_graph_replay_matches_direct_launches(lbm, orc):
     """lbm_step with nsteps >= 2 replays a captured CUDA graph; the result is
     bit-identical to launching the kernels one by one, for odd and even counts

@@ -15,8 +15,10 @@
 // Ring slots: warps may drift by one plane, so the ring holds five planes.  At
 // plane k a thread reads planes k-1, k, k+1 and writes plane k+1 (before its
 // arrival); the fastest thread may already write plane k+2 while the slowest
-// still reads k-1..k+1, and it cannot reach plane k+3 before the slowest has
-// arrived for plane k+1, which it does after its last read of plane k-1.
+// still reads k-1..k+1, and it cannot write plane k+3 (into the slot of plane
+// k-2) before the slowest has arrived for plane k+1, which it does after its
+// last read of plane k-2.  (The asynchronous-halo schedule below moves the
+// arrival after the reads and needs four planes.)
 // (Keeping the z-neighbours in registers instead would allow four slots but
 // pushes the register count past the two-CTA budget; eight slots, for a mask
 // instead of a modulo, cost more L1 than they save.)

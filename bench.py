@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import math
 import os
@@ -78,14 +79,23 @@ KERNEL_SOURCES = ("lbm_lattice.cuh", "lbm_mbarrier.cuh", "lbm_mlp_infer.cuh", "l
                   "lbm_step_tma.cuh", "lbm_step_x2.cuh")
 
 
+def _code_only(text: str) -> str:
+    """Source text without comments and with whitespace collapsed, so that a
+    comment edit does not count as a kernel change."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_hash() -> str:
-    """Hash of the files that hold the step kernels' device code (the units that
-    only instantiate them, and the host code that picks the launch, are checked
-    through the launch recorded beside the traffic)."""
+    """Hash of the code (comments and layout ignored) of the files that hold the
+    step kernels' device code (the units that only instantiate them, and the
+    host code that picks the launch, are checked through the launch recorded
+    beside each record)."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2605_19796_gb300", "csrc", f), "rb") as fp:
-            h.update(fp.read())
+        with open(os.path.join(ROOT, "paper_2605_19796_gb300", "csrc", f), encoding="utf-8") as fp:
+            h.update(_code_only(fp.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -34,14 +34,18 @@ def _write(path, name, entry):
         json.dump({"w": entry}, fp)
 
 
-def test_kernel_hash_follows_the_kernel_sources_only(bench):
+def test_kernel_hash_follows_the_kernel_code_only(bench):
     mod, root = bench
     h0 = mod.kernel_hash()
     assert len(h0) == 16 and h0 == mod.kernel_hash()
     (root / "paper_2605_19796_gb300" / "csrc" / "unrelated.cu").write_text("// not a kernel source\n")
     assert mod.kernel_hash() == h0
-    with open(root / "paper_2605_19796_gb300" / "csrc" / "lbm_step.cuh", "a") as fp:
-        fp.write("\n// changed\n")
+    src = root / "paper_2605_19796_gb300" / "csrc" / "lbm_step.cuh"
+    with open(src, "a") as fp:
+        fp.write("\n// a comment only\n/* and a block comment */\n")
+    assert mod.kernel_hash() == h0  # comments and layout do not count
+    with open(src, "a") as fp:
+        fp.write("\nstatic const int changed_code = 1;\n")
     assert mod.kernel_hash() != h0
 
 

@@ -602,8 +602,9 @@ def test_bounded_wait_times_out_and_handle_stays_usable(lbm, orc):
     assert rel(fg, fo) < TOL64
 
 
+@pytest.mark.parametrize("storage", ["fp32", "fp64"])
 @pytest.mark.parametrize("shape,nbatch", [((100, 100, 110), 2), ((130, 128, 128), 1)])
-def test_host_transfers_in_chunks_match_device_calls(lbm, shape, nbatch):
+def test_host_transfers_in_chunks_match_device_calls(lbm, shape, nbatch, storage):
     """lbm_init_velocity / lbm_moments with host pointers stream the fields
     through two staging slots of 2^21 cells (copy of one chunk overlapped with
     the kernel of the other).  On boxes of more than one chunk, with a chunk
@@ -615,7 +616,7 @@ def test_host_transfers_in_chunks_match_device_calls(lbm, shape, nbatch):
     rho = np.stack([f[0] for f in fields])
     u = np.stack([f[1] for f in fields], axis=1)
     assert rho.size > (1 << 21)
-    with lbm.Solver(27, shape, 1e-4, closure="kcmp", storage="fp32", nbatch=nbatch) as s:
+    with lbm.Solver(27, shape, 1e-4, closure="kcmp", storage=storage, nbatch=nbatch) as s:
         s.init_velocity(rho, u)
         f_host = s.get_populations()
         s.init_velocity_device(torch.from_numpy(rho).cuda(), torch.from_numpy(np.ascontiguousarray(u)).cuda())

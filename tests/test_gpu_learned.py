@@ -224,6 +224,44 @@ def test_learned_step_matches_oracle(env, orc, variant):
     assert inc <= 4 * noise + 1e-2 * sgs.max(), (inc, noise, sgs.max())
 
 
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_learned_step_16bit_storage(env, orc, storage):
+    """The learned closure on weight-shifted 16-bit storage (its default launch,
+    the split-barrier kernel): one step from a state that FP16/BF16 hold
+    exactly gives the density and velocity of the same step on FP32 storage
+    within the rounding of the stored results: 8 units of the format's relative
+    spacing (2^-10 FP16, 2^-7 BF16) times max |f - w|, the bound the
+    load-schedule tests use."""
+    lbm, torch = env
+    from oracle import learned as olearned
+    from oracle import mlp
+
+    shape = (32, 16, 12)
+    nu = 2e-5
+    rho, u = inputs.hit_fields(0, k0=3.0, urms=0.08, seed=12, shape=shape)
+    f = orc.run(orc.init_equilibrium(27, rho, u), 4, closure=1, nu=nu, c_nu=0.035)
+    w = orc.lattice(27)[1][:, None, None, None]
+    # a state the 16-bit storage holds exactly: round g = f - w to the format
+    gt = torch.from_numpy(np.ascontiguousarray(f - w, dtype=np.float32))
+    gt = gt.to(torch.float16 if storage == "fp16" else torch.bfloat16).to(torch.float64).numpy()
+    f16 = w + gt
+    _, _, _, _, x = olearned.inputs_and_state(f16, nu)
+    stats = _stats_for(x, 5.0 * float(np.abs(x[:, :6]).std()))
+    params = np.asarray(mlp.flat(mlp.init_params(5)), dtype=np.float32)
+    out = {}
+    for st in ("fp32", storage):
+        with lbm.Solver(27, shape, nu, closure="learned", storage=st) as s:
+            s.set_learned_closure(params, stats)
+            s.set_populations(f16)
+            s.step(1)
+            out[st] = s.get_populations()
+    gmax = np.abs(out["fp32"] - w).max()
+    tol = 8 * (2.0 ** -10 if storage == "fp16" else 2.0 ** -7) * gmax
+    r1, u1 = orc.fields(out["fp32"])
+    r2, u2 = orc.fields(out[storage])
+    assert np.abs(r2 - r1).max() < tol and np.abs(u2 - u1).max() < tol, (np.abs(u2 - u1).max(), tol)
+
+
 def test_learned_closure_pipeline(env):
     """Reduced end-to-end run of the learned closure: fine 128^3 runs box-filtered
     by 4 to 32^3, training with the library's kernels, held-out a-priori errors

@@ -170,18 +170,20 @@ def _stats_for(x, scale_out):
     return np.concatenate([xm, xs, np.zeros(6), np.full(6, scale_out)]).astype(np.float32)
 
 
-@pytest.mark.parametrize("variant", [1, 8, 12])
-def test_learned_step_matches_oracle(env, orc, variant):
+@pytest.mark.parametrize("q,variant", [(27, 1), (27, 8), (27, 12), (19, 1), (19, 8)])
+def test_learned_step_matches_oracle(env, orc, q, variant):
     """One step of the fused learned closure (BF16 tensor-core network inside the
     step kernel: the register pull, variant 1, the split-barrier kernel,
-    variant 8, and the same with L2 prefetches, variant 12) against the oracle's learned step with the same BF16 rounding
+    variant 8, and the same with L2 prefetches, variant 12; D3Q27 and D3Q19)
+    against the oracle's learned step with the same BF16 rounding
     points (inputs, weights, hidden activations) and FP64 elsewhere.  The network
     is random, its output scaled so that the turbulent rate is active in most
     cells.  The z-chunk of 5 planes leaves a ragged last chunk.
 
     Tolerance: the state is stored in FP32, so the resolved part of the update
     carries FP32 rounding noise; it is measured on the same state by the BGK
-    step against the oracle's BGK step.  Each cell may differ from the oracle by
+    and KC-MP steps against the oracle's (the learned closure has KC-MP's
+    relaxation form), the larger of the two.  Each cell may differ from the oracle by
     twice that noise plus 2^-7 of its SGS increment (omega - omega_s) f_sgs, the
     BF16 network's share."""
     lbm, torch = env
@@ -191,32 +193,39 @@ def test_learned_step_matches_oracle(env, orc, variant):
     shape = (32, 16, 12)
     nu = 2e-5
     rho, u = inputs.hit_fields(0, k0=3.0, urms=0.08, seed=12, shape=shape)
-    f = orc.run(orc.init_equilibrium(27, rho, u), 4, closure=1, nu=nu, c_nu=0.035)
+    f = orc.run(orc.init_equilibrium(q, rho, u), 4, closure=1, nu=nu, c_nu=0.035)
     f = f.astype(np.float32).astype(np.float64)  # the GPU state is FP32
     _, _, _, _, x = olearned.inputs_and_state(f, nu)
     scale = 5.0 * float(np.abs(x[:, :6]).std())
     stats = _stats_for(x, scale)
     params = np.asarray(mlp.flat(mlp.init_params(5)), dtype=np.float32)
-    with lbm.Solver(27, shape, nu, closure="learned", storage="fp32", variant=variant, zchunk=5) as s:
+    with lbm.Solver(q, shape, nu, closure="learned", storage="fp32", variant=variant, zchunk=5) as s:
         assert s.launch_config["variant"] == variant
         s.set_learned_closure(params, stats)
         s.set_populations(f)
         s.step(1)
         fg = s.get_populations()
-    with lbm.Solver(27, shape, nu, closure="bgk", storage="fp32") as s:
+    with lbm.Solver(q, shape, nu, closure="bgk", storage="fp32") as s:
         s.set_populations(f)
         s.step(1)
         fb = s.get_populations()
+    with lbm.Solver(q, shape, nu, closure="kcmp", storage="fp32") as s:
+        s.set_populations(f)
+        s.step(1)
+        fk = s.get_populations()
     fo, msgs = olearned.step(f, nu, params.astype(np.float64), stats.astype(np.float64), 0.035)
     fbo = orc.run(f, 1, closure=0, nu=nu)
+    fko = orc.run(f, 1, closure=1, nu=nu, c_nu=0.035)
     # the closure must be active: nu_t > nu in a good share of the cells
     tr = msgs[:, 0] + msgs[:, 1] + msgs[:, 2]
     assert np.mean(0.035 * np.sqrt(np.abs(tr) / 2) > nu) > 0.5
-    noise = np.abs(fb - fbo).max()
+    # FP32 noise of the same relaxation form (BGK, and KC-MP whose D H term the
+    # learned closure shares), measured on this state
+    noise = max(np.abs(fb - fbo).max(), np.abs(fk - fko).max())
     assert noise < 1e-7
-    sgs = np.abs(fo - fbo).reshape(27, -1).max(axis=0)  # per cell SGS increment
+    sgs = np.abs(fo - fbo).reshape(q, -1).max(axis=0)  # per cell SGS increment
     assert sgs.max() > 100 * noise, "the SGS signal must stand well above the FP32 noise"
-    err = np.abs(fg - fo).reshape(27, -1).max(axis=0)
+    err = np.abs(fg - fo).reshape(q, -1).max(axis=0)
     bound = 2 * noise + 2.0 ** -7 * sgs
     assert np.all(err <= bound), (np.max(err / bound), noise, sgs.max())
     # the SGS increments themselves, globally

@@ -586,6 +586,28 @@ def test_variants_channel(lbm, orc, q, shape):
             assert rel(s.get_populations(), fo) < TOL64, (var, zc)
 
 
+@pytest.mark.parametrize("variant", [1, 8, 13])
+def test_channel_ensemble_fp64(lbm, orc, variant):
+    """Two channel boxes in one launch (bounce-back walls in y, Guo body force,
+    each box its own viscosity and seed): every box against the oracle's
+    single-box run to 1e-12 in FP64, with a ragged tile row and z-chunk."""
+    shape, F = (16, 13, 7), (1e-5, 0.0, 0.0)
+    nus = np.array([2e-3, 6e-4])
+    fields = [inputs.channel_fields(*shape, 0.05, seed=80 + b) for b in range(2)]
+    rho = np.stack([f[0] for f in fields])
+    u = np.stack([f[1] for f in fields], axis=1)
+    with lbm.Solver(27, shape, nus, closure="kcmp", storage="fp64", bc=(0, 1, 0), force=F, variant=variant,
+                    zchunk=3, nbatch=2) as s:
+        assert s.launch_config["variant"] == variant
+        s.init_velocity(rho, u)
+        s.step(5)
+        fg = s.get_populations()
+    for b in range(2):
+        fo = orc.run(orc.init_equilibrium(27, fields[b][0], fields[b][1]), 5, closure=1, nu=nus[b], c_nu=0.035,
+                     bc=(0, 1, 0), F=F)
+        assert rel(fg[b], fo) < TOL64, (variant, b)
+
+
 def test_bounded_wait_times_out_and_handle_stays_usable(lbm, orc):
     """A device-side wait that nothing completes gives up after its poll limit
     and is reported as LBM_ERR_TIMEOUT (no trap, no fault); the handle then

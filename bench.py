@@ -434,31 +434,36 @@ def main():
     # lbm_init_velocity (H2D of rho, u) + K steps + lbm_moments (D2H of rho, u)
     e2e = None
     if not args.no_e2e:
-        rho_h = torch.empty(tuple(rho_d.shape), dtype=torch.float64, pin_memory=True)
-        u_h = torch.empty(tuple(u_d.shape), dtype=torch.float64, pin_memory=True)
-        rho_h.copy_(rho_d)
-        u_h.copy_(u_d)
+        # page-locked host buffers from the library (lbm_host_alloc)
+        rho_h = lbm.host_empty(tuple(rho_d.shape))
+        u_h = lbm.host_empty(tuple(u_d.shape))
+        torch.from_numpy(rho_h).copy_(rho_d)
+        torch.from_numpy(u_h).copy_(u_d)
         del rho_d, u_d
         torch.cuda.synchronize()
-        rho_o = torch.empty(tuple(rho_h.shape), dtype=torch.float64, pin_memory=True)
-        u_o = torch.empty(tuple(u_h.shape), dtype=torch.float64, pin_memory=True)
+        rho_o = lbm.host_empty(rho_h.shape)
+        u_o = lbm.host_empty(u_h.shape)
         # three runs, each the whole path (upload, K steps, download); the median
         # is reported and every run listed (a single run now and then meets a
         # host-side stall of a few hundred ms in the copies)
-        runs = []
+        runs, phases = [], []
         for _ in range(3):
             barrier()
             t0 = time.perf_counter()
-            lbm.lbm_init_velocity(s.h, rho_h.numpy(), u_h.numpy())
+            lbm.lbm_init_velocity(s.h, rho_h, u_h)
+            ta = time.perf_counter()
             s.step(args.steps)
-            lbm.lbm_moments(s.h, rho_o.numpy(), u_o.numpy())
+            s.synchronize()
+            tb = time.perf_counter()
+            lbm.lbm_moments(s.h, rho_o, u_o)
             t1 = time.perf_counter() - t0
             barrier()
             runs.append(rep.whole_job_rate(N * args.steps, rep.max_over_ranks(t1)) / 1e6)
-        e2e = {"value": sorted(runs)[1], "unit": "MLUPS", "runs": runs,
+            phases.append([round(1e3 * (ta - t0), 1), round(1e3 * (tb - ta), 1), round(1e3 * (t0 + t1 - tb), 1)])
+        e2e = {"value": sorted(runs)[1], "unit": "MLUPS", "runs": runs, "phases_ms_init_steps_moments": phases,
                "h2d_bytes_per_step": 32 * N // args.steps, "d2h_bytes_per_step": 32 * N // args.steps,
-               "what": "median of 3 runs of lbm_init_velocity(pinned host rho,u) + K x lbm_step + "
-                       "lbm_moments(pinned host rho,u)"}
+               "what": "median of 3 runs of lbm_init_velocity(host rho,u from lbm_host_alloc) + K x lbm_step + "
+                       "lbm_moments(host rho,u from lbm_host_alloc)"}
     s_cfg = s.launch_config
     s.close()
 

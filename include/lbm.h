@@ -179,6 +179,17 @@ int lbm_moments(lbm_handle* h, double* rho, double* u);
 /* As lbm_moments into device FP64 arrays; enqueue only. */
 int lbm_moments_device(lbm_handle* h, double* rho_dev, double* u_dev);
 
+/* Page-locked host memory for the host-pointer transfers (lbm_init_velocity,
+ * lbm_moments, lbm_get/set_populations); the paper has no counterpart.  The
+ * buffers come from the CUDA runtime's own page-locked allocator, which moves
+ * the fields at the host link's full rate; memory locked after allocation by
+ * other means was measured slower and with a wide spread on GB300.  *out_host
+ * receives the buffer (bytes > 0; LBM_ERR_ARG otherwise, LBM_ERR_OOM if the
+ * allocation fails); the caller owns it and releases it with lbm_host_free
+ * (NULL is ignored). */
+int lbm_host_alloc(size_t bytes, void** out_host);
+int lbm_host_free(void* host);
+
 /* FP64 global diagnostics of box `box` (Sec. 7.1, Eq. tgv_energy_enstrophy):
  * out[0] mass sum, out[1..3] momentum sums, out[4] E_k = <rho|u|^2/2>,
  * out[5] enstrophy <|curl u|^2/2> with the sixth-order centred curl (second-order

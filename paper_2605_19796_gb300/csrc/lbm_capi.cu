@@ -620,6 +620,27 @@ int lbm_launch_config(const lbm_handle* h, int* variant, int* tile_y, int* zchun
     return LBM_OK;
 }
 
+int lbm_host_alloc(size_t bytes, void** out_host)
+{
+    if (!out_host || bytes == 0) return fail(LBM_ERR_ARG, "lbm_host_alloc: NULL output or zero size");
+    *out_host = nullptr;
+    cudaError_t e = cudaHostAlloc(out_host, bytes, cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *out_host = nullptr;
+        return fail(LBM_ERR_OOM, "page-locked host allocation failed");
+    }
+    return LBM_OK;
+}
+
+int lbm_host_free(void* host)
+{
+    if (!host) return LBM_OK;
+    cudaError_t e = cudaFreeHost(host);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_host_free");
+    return LBM_OK;
+}
+
 int lbm_moments_device(lbm_handle* h, double* rho_dev, double* u_dev)
 {
     if (int rc = check_handle(h)) return rc;

@@ -12,6 +12,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 from typing import Optional, Sequence
 
 import numpy as np
@@ -40,7 +41,7 @@ EXPORTS = ["lbm_config_default", "lbm_create", "lbm_destroy", "lbm_init_velocity
            "lbm_diagnostics_noalloc", "lbm_autotune", "lbm_launch_config", "lbm_mlp_param_count",
            "lbm_mlp_workspace_floats", "lbm_mlp_forward", "lbm_mlp_grad", "lbm_mlp_adamw", "lbm_box_filter",
            "lbm_closure_features", "lbm_set_learned_closure", "lbm_mlp_packed_bytes", "lbm_mlp_pack",
-           "lbm_mlp_forward_tc", "lbm_wait_selftest"]
+           "lbm_mlp_forward_tc", "lbm_wait_selftest", "lbm_host_alloc", "lbm_host_free"]
 
 
 class lbm_config(ctypes.Structure):
@@ -106,6 +107,8 @@ def _load() -> ctypes.CDLL:
     lib.lbm_mlp_pack.argtypes = [P(ctypes.c_float), P(ctypes.c_float), vp]
     lib.lbm_mlp_forward_tc.argtypes = [vp, vp, ctypes.c_int, vp, vp]
     lib.lbm_wait_selftest.argtypes = [H, ctypes.c_int]
+    lib.lbm_host_alloc.argtypes = [ctypes.c_size_t, P(vp)]
+    lib.lbm_host_free.argtypes = [vp]
     lib.lbm_autotune.argtypes = [H, ctypes.c_int]
     lib.lbm_launch_config.argtypes = [H, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]
     lib.lbm_last_error.restype = ctypes.c_char_p
@@ -164,6 +167,30 @@ def lbm_moments(h, rho: Optional[np.ndarray], u: Optional[np.ndarray]) -> None:
 
 def lbm_moments_device(h, rho_ptr: int, u_ptr: int) -> None:
     _check(LIB.lbm_moments_device(h, ctypes.c_void_p(rho_ptr or None), ctypes.c_void_p(u_ptr or None)))
+
+
+def lbm_host_alloc(nbytes: int) -> int:
+    p = ctypes.c_void_p()
+    _check(LIB.lbm_host_alloc(ctypes.c_size_t(int(nbytes)), ctypes.byref(p)))
+    return p.value
+
+
+def lbm_host_free(ptr: int) -> None:
+    _check(LIB.lbm_host_free(ctypes.c_void_p(ptr or None)))
+
+
+def host_empty(shape, dtype=np.float64) -> np.ndarray:
+    """A NumPy array in page-locked host memory from lbm_host_alloc (the fast
+    path for the host-pointer transfers); the memory is released with
+    lbm_host_free when the array and all its views are gone."""
+    dt = np.dtype(dtype)
+    n = int(np.prod(shape)) if len(tuple(shape)) else 1
+    nbytes = max(1, n) * dt.itemsize
+    ptr = lbm_host_alloc(nbytes)
+    buf = (ctypes.c_char * nbytes).from_address(ptr)
+    arr = np.frombuffer(buf, dtype=dt, count=n).reshape(shape)
+    weakref.finalize(buf, lbm_host_free, ptr)
+    return arr
 
 
 def lbm_diagnostics(h, box: int, out: np.ndarray) -> None:

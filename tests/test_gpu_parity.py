@@ -608,6 +608,33 @@ def test_channel_ensemble_fp64(lbm, orc, variant):
         assert rel(fg[b], fo) < TOL64, (variant, b)
 
 
+def test_host_alloc_buffers_transfer_like_ordinary_arrays(lbm):
+    """lbm_host_alloc buffers (through lbm.host_empty) carry the fields of
+    lbm_init_velocity / lbm_moments exactly like ordinary host arrays, over
+    more than one staging chunk, and are released when the arrays go."""
+    import gc
+
+    shape = (130, 128, 128)
+    rho, u = inputs.hit_fields(0, k0=3.0, urms=0.05, seed=90, shape=shape)
+    rho_p, u_p = lbm.host_empty(rho.shape), lbm.host_empty(u.shape)
+    rho_p[...] = rho
+    u_p[...] = u
+    with lbm.Solver(27, shape, 1e-4, closure="kcmp", storage="fp32") as s:
+        s.init_velocity(rho, u)
+        f_a = s.get_populations()
+        lbm.lbm_init_velocity(s.h, rho_p, u_p.reshape(3, -1))
+        assert np.array_equal(s.get_populations(), f_a)
+        s.step(2)
+        r_a, u_a = s.moments()
+        r_b, u_b = lbm.host_empty(rho.shape), lbm.host_empty(u.shape)
+        lbm.lbm_moments(s.h, r_b, u_b)
+        assert np.array_equal(r_b, r_a) and np.array_equal(u_b, u_a)
+    del rho_p, u_p, r_b, u_b
+    gc.collect()
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_host_alloc(0)
+
+
 def test_bounded_wait_times_out_and_handle_stays_usable(lbm, orc):
     """A device-side wait that nothing completes gives up after its poll limit
     and is reported as LBM_ERR_TIMEOUT (no trap, no fault); the handle then

@@ -87,3 +87,13 @@ def test_null_arguments(lbm):
     assert lbm.LIB.lbm_step(None, 1) == lbm.LBM_ERR_ARG
     assert lbm.LIB.lbm_step_count(None) == -1
     lbm.LIB.lbm_destroy(None)
+
+
+def test_host_alloc_argument_checks_need_no_device(lbm):
+    """lbm_host_alloc refuses a zero size or a NULL output before any CUDA call;
+    lbm_host_free ignores NULL."""
+    p = ctypes.c_void_p()
+    assert lbm.LIB.lbm_host_alloc(ctypes.c_size_t(0), ctypes.byref(p)) == lbm.LBM_ERR_ARG
+    assert p.value is None
+    assert lbm.LIB.lbm_host_alloc(ctypes.c_size_t(64), None) == lbm.LBM_ERR_ARG
+    assert lbm.LIB.lbm_host_free(None) == lbm.LBM_OK

@@ -98,7 +98,8 @@ typedef struct {
     int bc[3];          /* per axis x, y, z: LBM_PERIODIC or LBM_BOUNCEBACK          */
     double force[3];    /* uniform body force density (Guo forcing); zero for none   */
     void* cuda_stream;  /* cudaStream_t to enqueue on; NULL = legacy default stream  */
-    int tile_y;         /* tuning: rows per CTA tile (0 = library default)           */
+    int tile_y;         /* tuning: rows per CTA tile (0 = library default: 4 for the
+                           learned closure, else 8)                                  */
     int zchunk;         /* tuning: z-planes per CTA march (0 = library default)      */
     int variant;        /* tuning: step-kernel variant, 0 = library default
                            (FP32 storage: 12 on z-chunks of at most 16 planes

@@ -355,7 +355,10 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
     const bool has_force = cfg->force[0] != 0.0 || cfg->force[1] != 0.0 || cfg->force[2] != 0.0;
     if (has_force && bc_kind != BC_WALLS_Y)
         return fail(LBM_ERR_UNSUPPORTED, "a body force is supported with bounce-back walls (channel) only");
-    int tile_y = cfg->tile_y ? cfg->tile_y : 8;
+    // the learned closure runs 4-row tiles by default: at 128 threads per CTA
+    // its kernels keep the network's fragments in ~240 registers without
+    // spilling (8-row tiles cap them at 128 and spill); the rest 8-row tiles
+    int tile_y = cfg->tile_y ? cfg->tile_y : (cfg->closure == LBM_LEARNED ? 4 : 8);
     if (cfg->variant != VAR_DEFAULT && cfg->variant != VAR_REGISTER && cfg->variant != VAR_TMA && cfg->variant != VAR_SPLIT &&
         cfg->variant != VAR_PAIR && cfg->variant != VAR_SPLIT_PF && cfg->variant != VAR_ASYNC)
         return fail(LBM_ERR_ARG, "unknown kernel variant");

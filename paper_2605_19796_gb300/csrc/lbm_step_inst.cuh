@@ -57,6 +57,7 @@ cudaError_t launch_step_qs(int closure, int bc, int ty, int variant, const StepA
             LBM_SB_CASE(CL_KCMP, BC_PERIODIC, 4)
             LBM_SB_CASE(CL_KCMP, BC_PERIODIC, 16)
             LBM_SB_CASE(CL_LEARNED, BC_PERIODIC, 8)
+            LBM_SB_CASE(CL_LEARNED, BC_PERIODIC, 4)
         }
 #undef LBM_SB_CASE
         return cudaErrorNotSupported;
@@ -76,6 +77,7 @@ cudaError_t launch_step_qs(int closure, int bc, int ty, int variant, const StepA
         }
         if constexpr (R32) {
             LBM_SBP_CASE(CL_LEARNED, BC_PERIODIC, 8)
+            LBM_SBP_CASE(CL_LEARNED, BC_PERIODIC, 4)
         }
 #undef LBM_SBP_CASE
         return cudaErrorNotSupported;
@@ -134,6 +136,7 @@ cudaError_t launch_step_qs(int closure, int bc, int ty, int variant, const StepA
         LBM_STEP_CASE(CL_KCMP, BC_PERIODIC, 4)
         LBM_STEP_CASE(CL_KCMP, BC_PERIODIC, 16)
         LBM_STEP_CASE(CL_LEARNED, BC_PERIODIC, 8)
+        LBM_STEP_CASE(CL_LEARNED, BC_PERIODIC, 4)
     }
 #undef LBM_STEP_CASE
     return cudaErrorNotSupported;

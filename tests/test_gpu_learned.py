@@ -170,11 +170,13 @@ def _stats_for(x, scale_out):
     return np.concatenate([xm, xs, np.zeros(6), np.full(6, scale_out)]).astype(np.float32)
 
 
-@pytest.mark.parametrize("q,variant", [(27, 1), (27, 8), (27, 12), (19, 1), (19, 8)])
-def test_learned_step_matches_oracle(env, orc, q, variant):
+@pytest.mark.parametrize("q,variant,tile_y", [(27, 1, 8), (27, 8, 8), (27, 12, 8), (27, 1, 4), (27, 12, 4),
+                                              (19, 1, 4), (19, 8, 8)])
+def test_learned_step_matches_oracle(env, orc, q, variant, tile_y):
     """One step of the fused learned closure (BF16 tensor-core network inside the
     step kernel: the register pull, variant 1, the split-barrier kernel,
-    variant 8, and the same with L2 prefetches, variant 12; D3Q27 and D3Q19)
+    variant 8, and the same with L2 prefetches, variant 12; tiles of 8 rows and
+    the default 4; D3Q27 and D3Q19)
     against the oracle's learned step with the same BF16 rounding
     points (inputs, weights, hidden activations) and FP64 elsewhere.  The network
     is random, its output scaled so that the turbulent rate is active in most
@@ -199,8 +201,8 @@ def test_learned_step_matches_oracle(env, orc, q, variant):
     scale = 5.0 * float(np.abs(x[:, :6]).std())
     stats = _stats_for(x, scale)
     params = np.asarray(mlp.flat(mlp.init_params(5)), dtype=np.float32)
-    with lbm.Solver(q, shape, nu, closure="learned", storage="fp32", variant=variant, zchunk=5) as s:
-        assert s.launch_config["variant"] == variant
+    with lbm.Solver(q, shape, nu, closure="learned", storage="fp32", variant=variant, tile_y=tile_y, zchunk=5) as s:
+        assert s.launch_config["variant"] == variant and s.launch_config["tile_y"] == tile_y
         s.set_learned_closure(params, stats)
         s.set_populations(f)
         s.step(1)

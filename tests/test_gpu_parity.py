@@ -452,7 +452,7 @@ def test_default_variant_selection(lbm):
     z-chunks of at most 16 planes; KC-RR, D3Q19 and walls with KC-MP the
     split-barrier pull with asynchronous copies (13); periodic D3Q27 otherwise
     (BGK, FP64, 16-bit storage) the split-barrier pull (8); the rest the
-    register pull (1).  An explicitly requested variant that is not built for
+    register pull (1).  Tiles are 8 rows, 4 for the learned closure.  An explicitly requested variant that is not built for
     a box is refused."""
     for q, closure, storage, want in ((27, "kcmp", "fp32", 12), (27, "kcrb_hermite", "fp16", 8), (27, "kcmp", "fp64", 8),
                                       (27, "kcrb_raw", "fp32", 12), (27, "kcrr", "fp32", 13),
@@ -463,6 +463,7 @@ def test_default_variant_selection(lbm):
             assert s.launch_config["variant"] == want, (q, closure, storage)
             if want == 12:
                 assert s.launch_config["zchunk"] <= 16
+            assert s.launch_config["tile_y"] == (4 if closure == "learned" else 8)
     for q, closure, want in ((27, "kcmp", 13), (19, "kcmp", 13), (27, "kcrb_hermite", 1), (27, "bgk", 1)):
         with lbm.Solver(q, (40, 32, 16), 1e-4, closure=closure, storage="fp32", bc=(0, 1, 0)) as s:
             assert s.launch_config["variant"] == want, (q, closure, "walls")

@@ -235,6 +235,58 @@ def test_learned_step_matches_oracle(env, orc, q, variant, tile_y):
     assert inc <= 4 * noise + 1e-2 * sgs.max(), (inc, noise, sgs.max())
 
 
+def test_learned_full_size_sampled_cells(env, orc):
+    """The learned closure at 256^3 (D3Q27, FP32, decaying HIT, nu = 2.5e-5) in
+    its default launch (split-barrier kernel with L2 prefetches, 16-plane
+    chunks of 4-row tiles): one GPU step, then sampled cells against the
+    oracle's learned step of the periodic 5x5x5 block around each cell, cut from
+    the GPU's own pre-step populations (the centre's pulls and the strain at its
+    six neighbours stay inside the block, so the centre is exact).  Random
+    network as in the small-box test, standardised on the sampled cells' own
+    inputs.  Tolerance per cell: 2e-6 x max|f| (the FP32 bound of the KC-MP
+    full-size test) plus 2^-7 of the cell's SGS increment against the BGK step
+    (the BF16 network's share)."""
+    lbm, torch = env
+    from oracle import learned as olearned
+    from oracle import mlp
+
+    n, nu, c_nu = 256, 2.5e-5, 0.035
+    rho, u = inputs.hit_fields(n, k0=4.0, urms=0.04, seed=3)
+    rng = np.random.default_rng(2562)
+    pts = np.concatenate([rng.integers(0, n, size=(40, 3)),
+                          [[0, 0, 0], [n - 1, n - 1, n - 1], [31, 3, 15], [32, 4, 16], [n - 1, 0, n // 2]]])
+    offs = np.array([(dx, dy, dz) for dz in range(-2, 3) for dy in range(-2, 3) for dx in range(-2, 3)])
+    centre = 62  # (2, 2, 2) of the block
+    params = np.asarray(mlp.flat(mlp.init_params(5)), dtype=np.float32)
+    with lbm.Solver(27, (n, n, n), nu, closure="learned", storage="fp32", c_nu=c_nu) as s:
+        cfg = s.launch_config
+        assert cfg["variant"] == 12 and cfg["tile_y"] == 4 and cfg["zchunk"] <= 16, cfg
+        s.init_velocity(rho, u)
+        del rho, u
+        s.set_learned_closure(params, _stats_for(np.ones((2, 10)), 1.0))
+        s.step(3)
+        blocks = s.probe((pts[:, None, :] + offs[None, :, :]).reshape(-1, 3)).reshape(len(pts), 125, 27)
+        blks = [blocks[k].T.reshape(27, 5, 5, 5).astype(np.float64) for k in range(len(pts))]
+        x = np.stack([olearned.inputs_and_state(b, nu)[4][centre] for b in blks])
+        stats = _stats_for(x, 5.0 * float(np.abs(x[:, :6]).std()))
+        s.set_learned_closure(params, stats)
+        s.step(1)
+        after = s.probe(pts)
+    scale = np.abs(after).max()
+    p64, st64 = params.astype(np.float64), stats.astype(np.float64)
+    active = 0
+    for k, b in enumerate(blks):
+        fo, msgs = olearned.step(b, nu, p64, st64, c_nu)
+        fbo = orc.step_cell(b, closure=0, nu=nu, c_nu=c_nu)
+        ref = fo[:, 2, 2, 2]
+        sgs = np.abs(ref - fbo).max()
+        tr = msgs[centre, 0] + msgs[centre, 1] + msgs[centre, 2]
+        active += c_nu * np.sqrt(abs(tr) / 2) > nu
+        err = np.abs(after[k] - ref).max()
+        assert err <= 2e-6 * scale + 2.0 ** -7 * sgs, (pts[k], err, sgs)
+    assert active > len(pts) // 2, active
+
+
 @pytest.mark.parametrize("storage", ["fp16", "bf16"])
 def test_learned_step_16bit_storage(env, orc, storage):
     """The learned closure on weight-shifted 16-bit storage (its default launch,

@@ -431,39 +431,56 @@ def main():
                     "hbm_frac": achieved / peak}
 
     # end to end through the C ABI with pinned host buffers:
-    # lbm_init_velocity (H2D of rho, u) + K steps + lbm_moments (D2H of rho, u)
+    # lbm_init_velocity (H2D of rho, u) + K steps + lbm_moments (D2H of rho, u).
+    # FP32 and 16-bit storage take the FP32 host fields (lbm_init_velocity_f32 /
+    # lbm_moments_f32: the equilibrium and the moments are FP32 arithmetic on
+    # the device either way); FP64 storage the FP64 ones.  Both are listed.
     e2e = None
     if not args.no_e2e:
-        # page-locked host buffers from the library (lbm_host_alloc)
-        rho_h = lbm.host_empty(tuple(rho_d.shape))
-        u_h = lbm.host_empty(tuple(u_d.shape))
-        torch.from_numpy(rho_h).copy_(rho_d)
-        torch.from_numpy(u_h).copy_(u_d)
+        def e2e_runs(dt):
+            # page-locked host buffers from the library (lbm_host_alloc)
+            rho_h = lbm.host_empty(tuple(rho_d.shape), dt)
+            u_h = lbm.host_empty(tuple(u_d.shape), dt)
+            torch.from_numpy(rho_h).copy_(rho_d)
+            torch.from_numpy(u_h).copy_(u_d)
+            torch.cuda.synchronize()
+            rho_o = lbm.host_empty(rho_h.shape, dt)
+            u_o = lbm.host_empty(u_h.shape, dt)
+            init = lbm.lbm_init_velocity_f32 if dt == np.float32 else lbm.lbm_init_velocity
+            mom = lbm.lbm_moments_f32 if dt == np.float32 else lbm.lbm_moments
+            # three runs, each the whole path (upload, K steps, download); the
+            # median is reported and every run listed (a single run now and then
+            # meets a host-side stall of a few hundred ms in the copies)
+            runs, phases = [], []
+            for _ in range(3):
+                barrier()
+                t0 = time.perf_counter()
+                init(s.h, rho_h, u_h)
+                ta = time.perf_counter()
+                s.step(args.steps)
+                s.synchronize()
+                tb = time.perf_counter()
+                mom(s.h, rho_o, u_o)
+                t1 = time.perf_counter() - t0
+                barrier()
+                runs.append(rep.whole_job_rate(N * args.steps, rep.max_over_ranks(t1)) / 1e6)
+                phases.append([round(1e3 * (ta - t0), 1), round(1e3 * (tb - ta), 1), round(1e3 * (t0 + t1 - tb), 1)])
+            nb_step = 4 * np.dtype(dt).itemsize * N // args.steps
+            return {"value": sorted(runs)[1], "runs": runs, "phases_ms_init_steps_moments": phases,
+                    "h2d_bytes_per_step": nb_step, "d2h_bytes_per_step": nb_step}
+
+        f64 = e2e_runs(np.float64)
+        if wl["storage"] == "fp64":
+            e2e = dict(f64, unit="MLUPS", host_fields="f64",
+                       what="median of 3 runs of lbm_init_velocity(host rho,u from lbm_host_alloc) + K x lbm_step + "
+                            "lbm_moments(host rho,u from lbm_host_alloc)")
+        else:
+            f32 = e2e_runs(np.float32)
+            e2e = dict(f32, unit="MLUPS", host_fields="f32", f64_fields=f64,
+                       what="median of 3 runs of lbm_init_velocity_f32(host FP32 rho,u from lbm_host_alloc) + "
+                            "K x lbm_step + lbm_moments_f32(host FP32 rho,u from lbm_host_alloc); f64_fields: "
+                            "the same with lbm_init_velocity / lbm_moments and FP64 fields")
         del rho_d, u_d
-        torch.cuda.synchronize()
-        rho_o = lbm.host_empty(rho_h.shape)
-        u_o = lbm.host_empty(u_h.shape)
-        # three runs, each the whole path (upload, K steps, download); the median
-        # is reported and every run listed (a single run now and then meets a
-        # host-side stall of a few hundred ms in the copies)
-        runs, phases = [], []
-        for _ in range(3):
-            barrier()
-            t0 = time.perf_counter()
-            lbm.lbm_init_velocity(s.h, rho_h, u_h)
-            ta = time.perf_counter()
-            s.step(args.steps)
-            s.synchronize()
-            tb = time.perf_counter()
-            lbm.lbm_moments(s.h, rho_o, u_o)
-            t1 = time.perf_counter() - t0
-            barrier()
-            runs.append(rep.whole_job_rate(N * args.steps, rep.max_over_ranks(t1)) / 1e6)
-            phases.append([round(1e3 * (ta - t0), 1), round(1e3 * (tb - ta), 1), round(1e3 * (t0 + t1 - tb), 1)])
-        e2e = {"value": sorted(runs)[1], "unit": "MLUPS", "runs": runs, "phases_ms_init_steps_moments": phases,
-               "h2d_bytes_per_step": 32 * N // args.steps, "d2h_bytes_per_step": 32 * N // args.steps,
-               "what": "median of 3 runs of lbm_init_velocity(host rho,u from lbm_host_alloc) + K x lbm_step + "
-                       "lbm_moments(host rho,u from lbm_host_alloc)"}
     s_cfg = s.launch_config
     s.close()
 

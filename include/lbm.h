@@ -140,6 +140,13 @@ void lbm_destroy(lbm_handle* h);
  * Synchronises the stream before returning. */
 int lbm_init_velocity(lbm_handle* h, const double* rho, const double* u);
 
+/* As lbm_init_velocity from FP32 host fields (same layouts): half the bytes
+ * over the host link.  For FP32 and 16-bit storage, whose equilibrium is
+ * evaluated in FP32 anyway, the result is the same as from the FP64 fields
+ * rounded to FP32; FP64 storage evaluates it in FP64 from the FP32 values.
+ * Synchronises the stream before returning. */
+int lbm_init_velocity_f32(lbm_handle* h, const float* rho, const float* u);
+
 /* As lbm_init_velocity with device pointers (FP64, same layouts); enqueue only. */
 int lbm_init_velocity_device(lbm_handle* h, const double* rho_dev, const double* u_dev);
 
@@ -176,6 +183,12 @@ int lbm_launch_config(const lbm_handle* h, int* variant, int* tile_y, int* zchun
  * precision the stored values carry; lbm_diagnostics always sums in FP64).
  * Synchronises. */
 int lbm_moments(lbm_handle* h, double* rho, double* u);
+
+/* As lbm_moments into FP32 host arrays (same layouts): half the bytes over
+ * the host link.  For FP32 and 16-bit storage these are the FP32 sums of
+ * lbm_moments rounded to FP32 (rho from its FP64 assembly); FP64 storage sums
+ * in FP64 and rounds.  Synchronises. */
+int lbm_moments_f32(lbm_handle* h, float* rho, float* u);
 
 /* As lbm_moments into device FP64 arrays; enqueue only. */
 int lbm_moments_device(lbm_handle* h, double* rho_dev, double* u_dev);

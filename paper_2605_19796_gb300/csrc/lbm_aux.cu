@@ -62,19 +62,19 @@ __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(double f, double 
 
 // Cells t0 .. t0 + count - 1 of the nbatch x ncell cells; rho [count] and
 // u [3][ustride] hold the range's fields (the whole arrays, t0 = 0, or a
-// staged chunk).
-template <int Q, typename S>
-__global__ void init_kernel(S* f, const double* rho, const double* u, long long ncell, long long ps, long long bs,
+// staged chunk), FP64 or FP32 (T).
+template <int Q, typename S, typename T>
+__global__ void init_kernel(S* f, const T* rho, const T* u, long long ncell, long long ps, long long bs,
                             long long t0, long long count, long long ustride)
 {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count; t += (long long)gridDim.x * blockDim.x) {
         const long long T = t0 + t;
         const long long box = T / ncell, c = T - box * ncell;
-        const double r = rho ? rho[t] : 1.0;
+        const double r = rho ? (double)rho[t] : 1.0;
         S* fb = f + box * bs + c;
         if constexpr (sizeof(S) == 8) {
             double geq[Q];
-            equilibrium_g<Q>(r, u[t], u[ustride + t], u[2 * ustride + t], geq);
+            equilibrium_g<Q>(r, (double)u[t], (double)u[ustride + t], (double)u[2 * ustride + t], geq);
             static_for<Q>([&](auto I) {
                 constexpr int i = decltype(I)::value;
                 constexpr double w = weight_of(Q, i);
@@ -107,9 +107,9 @@ __host__ __device__ constexpr double weight_sum_f32()
 }
 
 // F32: FP32 arithmetic for 32- and 16-bit storage (the readback path); the
-// diagnostics keep FP64 sums.
-template <int Q, typename S, bool F32>
-__global__ void moments_kernel(const S* f, double* rho, double* u, long long ncell, long long ps, long long bs,
+// diagnostics keep FP64 sums.  O: FP64 or FP32 output fields.
+template <int Q, typename S, bool F32, typename O>
+__global__ void moments_kernel(const S* f, O* rho, O* u, long long ncell, long long ps, long long bs,
                                double Fx, double Fy, double Fz, long long t0, long long count, long long ustride)
 {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count; t += (long long)gridDim.x * blockDim.x) {
@@ -128,11 +128,11 @@ __global__ void moments_kernel(const S* f, double* rho, double* u, long long nce
             });
             float d32, vx, vy, vz;
             moments<Q, float>(g, d32, vx, vy, vz, (float)-Fx, (float)-Fy, (float)-Fz);
-            if (rho) rho[t] = (sizeof(S) == 4 ? weight_sum_f32<Q>() : 1.0) + (double)d32;
+            if (rho) rho[t] = (O)((sizeof(S) == 4 ? weight_sum_f32<Q>() : 1.0) + (double)d32);
             if (u) {
-                u[t] = vx;
-                u[ustride + t] = vy;
-                u[2 * ustride + t] = vz;
+                u[t] = (O)vx;
+                u[ustride + t] = (O)vy;
+                u[2 * ustride + t] = (O)vz;
             }
             continue;
         }
@@ -148,11 +148,11 @@ __global__ void moments_kernel(const S* f, double* rho, double* u, long long nce
             jz += cz * g;
         });
         const double r = 1.0 + d;
-        if (rho) rho[t] = r;
+        if (rho) rho[t] = (O)r;
         if (u) {
-            u[t] = (jx - 0.5 * Fx) / r;
-            u[ustride + t] = (jy - 0.5 * Fy) / r;
-            u[2 * ustride + t] = (jz - 0.5 * Fz) / r;
+            u[t] = (O)((jx - 0.5 * Fx) / r);
+            u[ustride + t] = (O)((jy - 0.5 * Fy) / r);
+            u[2 * ustride + t] = (O)((jz - 0.5 * Fz) / r);
         }
     }
 }
@@ -347,9 +347,10 @@ int diag_blocks(long long ncell)
 
 }  // namespace
 
-cudaError_t launch_init_equilibrium(int q, int storage, void* f, const double* rho, const double* u, long long ncell,
-                                    int nbatch, long long ps, long long bs, cudaStream_t s, long long t0,
-                                    long long count, long long ustride)
+template <typename T>
+cudaError_t init_equilibrium_t(int q, int storage, void* f, const T* rho, const T* u, long long ncell, int nbatch,
+                               long long ps, long long bs, cudaStream_t s, long long t0, long long count,
+                               long long ustride)
 {
     if (count < 0) count = ncell * nbatch;
     if (ustride < 0) ustride = count;
@@ -357,11 +358,25 @@ cudaError_t launch_init_equilibrium(int q, int storage, void* f, const double* r
     return dispatch_storage(storage, [&](auto tag) -> cudaError_t {
         using S = std::remove_pointer_t<decltype(tag)>;
         if (q == 27)
-            init_kernel<27, S><<<g, 256, 0, s>>>((S*)f, rho, u, ncell, ps, bs, t0, count, ustride);
+            init_kernel<27, S, T><<<g, 256, 0, s>>>((S*)f, rho, u, ncell, ps, bs, t0, count, ustride);
         else
-            init_kernel<19, S><<<g, 256, 0, s>>>((S*)f, rho, u, ncell, ps, bs, t0, count, ustride);
+            init_kernel<19, S, T><<<g, 256, 0, s>>>((S*)f, rho, u, ncell, ps, bs, t0, count, ustride);
         return cudaGetLastError();
     });
+}
+
+cudaError_t launch_init_equilibrium(int q, int storage, void* f, const double* rho, const double* u, long long ncell,
+                                    int nbatch, long long ps, long long bs, cudaStream_t s, long long t0,
+                                    long long count, long long ustride)
+{
+    return init_equilibrium_t<double>(q, storage, f, rho, u, ncell, nbatch, ps, bs, s, t0, count, ustride);
+}
+
+cudaError_t launch_init_equilibrium(int q, int storage, void* f, const float* rho, const float* u, long long ncell,
+                                    int nbatch, long long ps, long long bs, cudaStream_t s, long long t0,
+                                    long long count, long long ustride)
+{
+    return init_equilibrium_t<float>(q, storage, f, rho, u, ncell, nbatch, ps, bs, s, t0, count, ustride);
 }
 
 // Self-test of the bounded-wait error path: one thread waits on an mbarrier
@@ -382,9 +397,10 @@ cudaError_t launch_wait_selftest(unsigned int* flag, long long polls, cudaStream
     return cudaGetLastError();
 }
 
-cudaError_t launch_moments(int q, int storage, const void* f, double* rho, double* u, long long ncell, int nbatch,
-                           long long ps, long long bs, const double* force, cudaStream_t s, bool fp32, long long t0,
-                           long long count, long long ustride)
+template <typename O>
+cudaError_t moments_t(int q, int storage, const void* f, O* rho, O* u, long long ncell, int nbatch, long long ps,
+                      long long bs, const double* force, cudaStream_t s, bool fp32, long long t0, long long count,
+                      long long ustride)
 {
     if (count < 0) count = ncell * nbatch;
     if (ustride < 0) ustride = count;
@@ -394,17 +410,31 @@ cudaError_t launch_moments(int q, int storage, const void* f, double* rho, doubl
         const double F0 = force[0], F1 = force[1], F2 = force[2];
         if (q == 27) {
             if (fp32)
-                moments_kernel<27, S, true><<<g, 256, 0, s>>>((const S*)f, rho, u, ncell, ps, bs, F0, F1, F2, t0, count, ustride);
+                moments_kernel<27, S, true, O><<<g, 256, 0, s>>>((const S*)f, rho, u, ncell, ps, bs, F0, F1, F2, t0, count, ustride);
             else
-                moments_kernel<27, S, false><<<g, 256, 0, s>>>((const S*)f, rho, u, ncell, ps, bs, F0, F1, F2, t0, count, ustride);
+                moments_kernel<27, S, false, O><<<g, 256, 0, s>>>((const S*)f, rho, u, ncell, ps, bs, F0, F1, F2, t0, count, ustride);
         } else {
             if (fp32)
-                moments_kernel<19, S, true><<<g, 256, 0, s>>>((const S*)f, rho, u, ncell, ps, bs, F0, F1, F2, t0, count, ustride);
+                moments_kernel<19, S, true, O><<<g, 256, 0, s>>>((const S*)f, rho, u, ncell, ps, bs, F0, F1, F2, t0, count, ustride);
             else
-                moments_kernel<19, S, false><<<g, 256, 0, s>>>((const S*)f, rho, u, ncell, ps, bs, F0, F1, F2, t0, count, ustride);
+                moments_kernel<19, S, false, O><<<g, 256, 0, s>>>((const S*)f, rho, u, ncell, ps, bs, F0, F1, F2, t0, count, ustride);
         }
         return cudaGetLastError();
     });
+}
+
+cudaError_t launch_moments(int q, int storage, const void* f, double* rho, double* u, long long ncell, int nbatch,
+                           long long ps, long long bs, const double* force, cudaStream_t s, bool fp32, long long t0,
+                           long long count, long long ustride)
+{
+    return moments_t<double>(q, storage, f, rho, u, ncell, nbatch, ps, bs, force, s, fp32, t0, count, ustride);
+}
+
+cudaError_t launch_moments(int q, int storage, const void* f, float* rho, float* u, long long ncell, int nbatch,
+                           long long ps, long long bs, const double* force, cudaStream_t s, long long t0,
+                           long long count, long long ustride)
+{
+    return moments_t<float>(q, storage, f, rho, u, ncell, nbatch, ps, bs, force, s, true, t0, count, ustride);
 }
 
 cudaError_t launch_to_f64(int q, int storage, const void* f, double* out, long long ncell, int nbatch, long long ps,

@@ -308,6 +308,92 @@ struct FileHeader {
     uint64_t payload_bytes;
 };
 
+// Host-pointer initialisation: the fields go through the two staging slots in
+// chunks of stage_cells cells; the copy of chunk k+1 (copy stream) runs while
+// the init kernel of chunk k (solver stream) reads the other slot.  T: FP64 or
+// FP32 host fields (a slot holds 4 stage_cells doubles, so either fits).
+template <typename T>
+int init_from_host(lbm_handle* h, const T* rho, const T* u)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!u) return fail(LBM_ERR_ARG, "u is NULL");
+    if (int rc = ensure_stage(h)) return rc;
+    const long long n = h->ncell * h->cfg.nbatch, C = h->stage_cells;
+    cudaError_t e = cudaSuccess;
+    int k = 0;
+    for (long long t0 = 0; t0 < n && e == cudaSuccess; t0 += C, ++k) {
+        const long long m = n - t0 < C ? n - t0 : C;
+        const int sl = k & 1;
+        T* srho = reinterpret_cast<T*>(h->stage + (size_t)sl * 4 * C);
+        T* su = srho + C;
+        e = cudaStreamWaitEvent(h->xstream, h->ev_drained[sl], 0);  // chunk k-2's kernel has read the slot
+        if (e == cudaSuccess && rho)
+            e = cudaMemcpyAsync(srho, rho + t0, sizeof(T) * m, cudaMemcpyHostToDevice, h->xstream);
+        for (int c = 0; c < 3 && e == cudaSuccess; ++c)
+            e = cudaMemcpyAsync(su + c * C, u + c * n + t0, sizeof(T) * m, cudaMemcpyHostToDevice, h->xstream);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_filled[sl], h->xstream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_filled[sl], 0);
+        if (e == cudaSuccess)
+            e = launch_init_equilibrium(h->q, h->cfg.storage, h->f[h->cur], rho ? srho : nullptr, su, h->ncell,
+                                        h->cfg.nbatch, h->popstride, h->boxstride, h->stream, t0, m, C);
+        if (e == cudaSuccess) {
+            h->launches++;
+            e = cudaEventRecord(h->ev_drained[sl], h->stream);
+        }
+    }
+    cudaError_t e2 = cudaStreamSynchronize(h->xstream);
+    cudaError_t e3 = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : e3;
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_init_velocity");
+    h->steps = 0;
+    return LBM_OK;
+}
+
+// Host-pointer readback: chunk k's moments kernel (solver stream) fills one
+// staging slot while the copy stream drains chunk k-1's slot to the host.
+// T: FP64 or FP32 host fields.
+template <typename T>
+int moments_to_host(lbm_handle* h, T* rho, T* u)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (int rc = ensure_stage(h)) return rc;
+    const long long n = h->ncell * h->cfg.nbatch, C = h->stage_cells;
+    cudaError_t e = cudaSuccess;
+    int k = 0;
+    for (long long t0 = 0; t0 < n && e == cudaSuccess && (rho || u); t0 += C, ++k) {
+        const long long m = n - t0 < C ? n - t0 : C;
+        const int sl = k & 1;
+        T* srho = reinterpret_cast<T*>(h->stage + (size_t)sl * 4 * C);
+        T* su = srho + C;
+        e = cudaStreamWaitEvent(h->stream, h->ev_drained[sl], 0);  // chunk k-2's copy has left the slot
+        if (e == cudaSuccess) {
+            T* dr = rho ? srho : nullptr;
+            T* du = u ? su : nullptr;
+            if constexpr (sizeof(T) == 8)
+                e = launch_moments(h->q, h->cfg.storage, h->f[h->cur], dr, du, h->ncell, h->cfg.nbatch, h->popstride,
+                                   h->boxstride, h->cfg.force, h->stream, true, t0, m, C);
+            else
+                e = launch_moments(h->q, h->cfg.storage, h->f[h->cur], dr, du, h->ncell, h->cfg.nbatch, h->popstride,
+                                   h->boxstride, h->cfg.force, h->stream, t0, m, C);
+        }
+        if (e == cudaSuccess) {
+            h->launches++;
+            e = cudaEventRecord(h->ev_filled[sl], h->stream);
+        }
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->xstream, h->ev_filled[sl], 0);
+        if (e == cudaSuccess && rho)
+            e = cudaMemcpyAsync(rho + t0, srho, sizeof(T) * m, cudaMemcpyDeviceToHost, h->xstream);
+        for (int c = 0; c < 3 && e == cudaSuccess && u; ++c)
+            e = cudaMemcpyAsync(u + c * n + t0, su + c * C, sizeof(T) * m, cudaMemcpyDeviceToHost, h->xstream);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_drained[sl], h->xstream);
+    }
+    cudaError_t e2 = cudaStreamSynchronize(h->xstream);
+    cudaError_t e3 = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : e3;
+    if (e != cudaSuccess) return cuda_fail(e, "copying the fields back");
+    return read_flag(h);
+}
+
 }  // namespace
 
 extern "C" {
@@ -462,43 +548,14 @@ int lbm_init_velocity_device(lbm_handle* h, const double* rho_dev, const double*
     return LBM_OK;
 }
 
-// Host-pointer initialisation: the fields go through the two staging slots in
-// chunks of stage_cells cells; the copy of chunk k+1 (copy stream) runs while
-// the init kernel of chunk k (solver stream) reads the other slot.
 int lbm_init_velocity(lbm_handle* h, const double* rho, const double* u)
 {
-    if (int rc = check_handle(h)) return rc;
-    if (!u) return fail(LBM_ERR_ARG, "u is NULL");
-    if (int rc = ensure_stage(h)) return rc;
-    const long long n = h->ncell * h->cfg.nbatch, C = h->stage_cells;
-    cudaError_t e = cudaSuccess;
-    int k = 0;
-    for (long long t0 = 0; t0 < n && e == cudaSuccess; t0 += C, ++k) {
-        const long long m = n - t0 < C ? n - t0 : C;
-        const int sl = k & 1;
-        double* srho = h->stage + (size_t)sl * 4 * C;
-        double* su = srho + C;
-        e = cudaStreamWaitEvent(h->xstream, h->ev_drained[sl], 0);  // chunk k-2's kernel has read the slot
-        if (e == cudaSuccess && rho)
-            e = cudaMemcpyAsync(srho, rho + t0, sizeof(double) * m, cudaMemcpyHostToDevice, h->xstream);
-        for (int c = 0; c < 3 && e == cudaSuccess; ++c)
-            e = cudaMemcpyAsync(su + c * C, u + c * n + t0, sizeof(double) * m, cudaMemcpyHostToDevice, h->xstream);
-        if (e == cudaSuccess) e = cudaEventRecord(h->ev_filled[sl], h->xstream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_filled[sl], 0);
-        if (e == cudaSuccess)
-            e = launch_init_equilibrium(h->q, h->cfg.storage, h->f[h->cur], rho ? srho : nullptr, su, h->ncell,
-                                        h->cfg.nbatch, h->popstride, h->boxstride, h->stream, t0, m, C);
-        if (e == cudaSuccess) {
-            h->launches++;
-            e = cudaEventRecord(h->ev_drained[sl], h->stream);
-        }
-    }
-    cudaError_t e2 = cudaStreamSynchronize(h->xstream);
-    cudaError_t e3 = cudaStreamSynchronize(h->stream);
-    if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : e3;
-    if (e != cudaSuccess) return cuda_fail(e, "lbm_init_velocity");
-    h->steps = 0;
-    return LBM_OK;
+    return init_from_host(h, rho, u);
+}
+
+int lbm_init_velocity_f32(lbm_handle* h, const float* rho, const float* u)
+{
+    return init_from_host(h, rho, u);
 }
 
 int lbm_set_learned_closure(lbm_handle* h, const float* params, const float* stats)
@@ -654,40 +711,14 @@ int lbm_moments_device(lbm_handle* h, double* rho_dev, double* u_dev)
     return LBM_OK;
 }
 
-// Host-pointer readback: chunk k's moments kernel (solver stream) fills one
-// staging slot while the copy stream drains chunk k-1's slot to the host.
 int lbm_moments(lbm_handle* h, double* rho, double* u)
 {
-    if (int rc = check_handle(h)) return rc;
-    if (int rc = ensure_stage(h)) return rc;
-    const long long n = h->ncell * h->cfg.nbatch, C = h->stage_cells;
-    cudaError_t e = cudaSuccess;
-    int k = 0;
-    for (long long t0 = 0; t0 < n && e == cudaSuccess && (rho || u); t0 += C, ++k) {
-        const long long m = n - t0 < C ? n - t0 : C;
-        const int sl = k & 1;
-        double* srho = h->stage + (size_t)sl * 4 * C;
-        double* su = srho + C;
-        e = cudaStreamWaitEvent(h->stream, h->ev_drained[sl], 0);  // chunk k-2's copy has left the slot
-        if (e == cudaSuccess)
-            e = launch_moments(h->q, h->cfg.storage, h->f[h->cur], rho ? srho : nullptr, u ? su : nullptr, h->ncell,
-                               h->cfg.nbatch, h->popstride, h->boxstride, h->cfg.force, h->stream, true, t0, m, C);
-        if (e == cudaSuccess) {
-            h->launches++;
-            e = cudaEventRecord(h->ev_filled[sl], h->stream);
-        }
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->xstream, h->ev_filled[sl], 0);
-        if (e == cudaSuccess && rho)
-            e = cudaMemcpyAsync(rho + t0, srho, sizeof(double) * m, cudaMemcpyDeviceToHost, h->xstream);
-        for (int c = 0; c < 3 && e == cudaSuccess && u; ++c)
-            e = cudaMemcpyAsync(u + c * n + t0, su + c * C, sizeof(double) * m, cudaMemcpyDeviceToHost, h->xstream);
-        if (e == cudaSuccess) e = cudaEventRecord(h->ev_drained[sl], h->xstream);
-    }
-    cudaError_t e2 = cudaStreamSynchronize(h->xstream);
-    cudaError_t e3 = cudaStreamSynchronize(h->stream);
-    if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : e3;
-    if (e != cudaSuccess) return cuda_fail(e, "copying the fields back");
-    return read_flag(h);
+    return moments_to_host(h, rho, u);
+}
+
+int lbm_moments_f32(lbm_handle* h, float* rho, float* u)
+{
+    return moments_to_host(h, rho, u);
 }
 
 int lbm_wait_selftest(lbm_handle* h, int polls)

@@ -65,10 +65,18 @@ cudaError_t prepare_step(int q, int storage, int closure, int bc, int tile_y, in
 cudaError_t launch_init_equilibrium(int q, int storage, void* f, const double* rho, const double* u, long long ncell,
                                     int nbatch, long long popstride, long long boxstride, cudaStream_t s,
                                     long long t0 = 0, long long count = -1, long long ustride = -1);
+// the same from FP32 fields
+cudaError_t launch_init_equilibrium(int q, int storage, void* f, const float* rho, const float* u, long long ncell,
+                                    int nbatch, long long popstride, long long boxstride, cudaStream_t s,
+                                    long long t0 = 0, long long count = -1, long long ustride = -1);
 // fp32: FP32 sums for 32- and 16-bit storage (readback); false: FP64 sums (diagnostics)
 cudaError_t launch_moments(int q, int storage, const void* f, double* rho, double* u, long long ncell, int nbatch,
                            long long popstride, long long boxstride, const double* force, cudaStream_t s,
                            bool fp32 = false, long long t0 = 0, long long count = -1, long long ustride = -1);
+// FP32 output fields (FP32 sums for 32- and 16-bit storage, FP64 sums for FP64 storage)
+cudaError_t launch_moments(int q, int storage, const void* f, float* rho, float* u, long long ncell, int nbatch,
+                           long long popstride, long long boxstride, const double* force, cudaStream_t s,
+                           long long t0, long long count, long long ustride);
 cudaError_t launch_to_f64(int q, int storage, const void* f, double* out, long long ncell, int nbatch,
                           long long popstride, long long boxstride, cudaStream_t s);
 cudaError_t launch_from_f64(int q, int storage, void* f, const double* in, long long ncell, int nbatch,

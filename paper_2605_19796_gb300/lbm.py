@@ -41,7 +41,8 @@ EXPORTS = ["lbm_config_default", "lbm_create", "lbm_destroy", "lbm_init_velocity
            "lbm_diagnostics_noalloc", "lbm_autotune", "lbm_launch_config", "lbm_mlp_param_count",
            "lbm_mlp_workspace_floats", "lbm_mlp_forward", "lbm_mlp_grad", "lbm_mlp_adamw", "lbm_box_filter",
            "lbm_closure_features", "lbm_set_learned_closure", "lbm_mlp_packed_bytes", "lbm_mlp_pack",
-           "lbm_mlp_forward_tc", "lbm_wait_selftest", "lbm_host_alloc", "lbm_host_free"]
+           "lbm_mlp_forward_tc", "lbm_wait_selftest", "lbm_host_alloc", "lbm_host_free",
+           "lbm_init_velocity_f32", "lbm_moments_f32"]
 
 
 class lbm_config(ctypes.Structure):
@@ -73,6 +74,9 @@ def _load() -> ctypes.CDLL:
     lib.lbm_destroy.argtypes = [H]
     lib.lbm_destroy.restype = None
     lib.lbm_init_velocity.argtypes = [H, dp, dp]
+    fp = P(ctypes.c_float)
+    lib.lbm_init_velocity_f32.argtypes = [H, fp, fp]
+    lib.lbm_moments_f32.argtypes = [H, fp, fp]
     lib.lbm_init_velocity_device.argtypes = [H, vp, vp]
     lib.lbm_step.argtypes = [H, ctypes.c_int]
     lib.lbm_moments.argtypes = [H, dp, dp]
@@ -126,6 +130,13 @@ def _dp(a: Optional[np.ndarray]):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
+def _fp(a: Optional[np.ndarray]):
+    if a is None:
+        return ctypes.POINTER(ctypes.c_float)()
+    assert a.dtype == np.float32 and a.flags["C_CONTIGUOUS"], "expected a C-contiguous float32 array"
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
 def _check(rc: int) -> None:
     if rc != LBM_OK:
         raise LbmError(rc, LIB.lbm_last_error().decode())
@@ -151,6 +162,14 @@ def lbm_destroy(h) -> None:
 
 def lbm_init_velocity(h, rho: Optional[np.ndarray], u: np.ndarray) -> None:
     _check(LIB.lbm_init_velocity(h, _dp(rho), _dp(u)))
+
+
+def lbm_init_velocity_f32(h, rho: Optional[np.ndarray], u: np.ndarray) -> None:
+    _check(LIB.lbm_init_velocity_f32(h, _fp(rho), _fp(u)))
+
+
+def lbm_moments_f32(h, rho: Optional[np.ndarray], u: Optional[np.ndarray]) -> None:
+    _check(LIB.lbm_moments_f32(h, _fp(rho), _fp(u)))
 
 
 def lbm_init_velocity_device(h, rho_ptr: int, u_ptr: int) -> None:
@@ -412,9 +431,12 @@ class Solver:
         return (self.nbatch, nz, ny, nx)
 
     def init_velocity(self, rho: Optional[np.ndarray], u: np.ndarray) -> None:
-        u = np.ascontiguousarray(u, dtype=np.float64).reshape(3, -1)
-        r = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
-        lbm_init_velocity(self.h, r, u)
+        """float32 u goes through lbm_init_velocity_f32 (rho converted to float32),
+        anything else through lbm_init_velocity as float64."""
+        dt = np.float32 if np.asarray(u).dtype == np.float32 else np.float64
+        u = np.ascontiguousarray(u, dtype=dt).reshape(3, -1)
+        r = None if rho is None else np.ascontiguousarray(rho, dtype=dt).reshape(-1)
+        (lbm_init_velocity_f32 if dt == np.float32 else lbm_init_velocity)(self.h, r, u)
 
     def init_velocity_device(self, rho, u) -> None:
         """rho, u: CUDA float64 tensors (rho may be None) in the C ABI layouts."""
@@ -423,10 +445,13 @@ class Solver:
     def step(self, n: int = 1) -> None:
         lbm_step(self.h, n)
 
-    def moments(self):
-        rho = np.empty(self._fshape(), dtype=np.float64)
-        u = np.empty((3,) + self._fshape(), dtype=np.float64)
-        lbm_moments(self.h, rho, u)
+    def moments(self, dtype=np.float64):
+        """rho, u as float64 (lbm_moments) or float32 (lbm_moments_f32)."""
+        dt = np.dtype(dtype)
+        assert dt in (np.float64, np.float32), "moments come as float64 or float32"
+        rho = np.empty(self._fshape(), dtype=dt)
+        u = np.empty((3,) + self._fshape(), dtype=dt)
+        (lbm_moments_f32 if dt == np.float32 else lbm_moments)(self.h, rho, u)
         if self.nbatch == 1:
             return rho[0], u[:, 0]
         return rho, u

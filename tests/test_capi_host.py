@@ -86,6 +86,8 @@ def test_null_arguments(lbm):
     assert lbm.LIB.lbm_create(None, None) == lbm.LBM_ERR_ARG
     assert lbm.LIB.lbm_step(None, 1) == lbm.LBM_ERR_ARG
     assert lbm.LIB.lbm_step_count(None) == -1
+    assert lbm.LIB.lbm_init_velocity_f32(None, None, None) == lbm.LBM_ERR_ARG
+    assert lbm.LIB.lbm_moments_f32(None, None, None) == lbm.LBM_ERR_ARG
     lbm.LIB.lbm_destroy(None)
 
 

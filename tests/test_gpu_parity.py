@@ -682,6 +682,40 @@ def test_host_transfers_in_chunks_match_device_calls(lbm, shape, nbatch, storage
         assert np.array_equal(np.asarray(u_h).reshape(3, -1), u_d.cpu().numpy().reshape(3, -1))
 
 
+@pytest.mark.parametrize("storage", ["fp64", "fp32", "bf16"])
+@pytest.mark.parametrize("shape,nbatch", [((100, 100, 110), 2), ((130, 128, 128), 1)])
+def test_fp32_host_fields_match_fp64_calls(lbm, shape, nbatch, storage):
+    """lbm_init_velocity_f32 / lbm_moments_f32 (FP32 host fields through the
+    same two staging slots, more than one chunk, a ragged last chunk): the
+    populations equal, bit for bit, those lbm_init_velocity makes from the same
+    fields held as FP64 (the FP32 and 16-bit equilibria are evaluated in FP32,
+    the FP64 one from the same values), and the FP32 moments equal the FP64
+    moments rounded to FP32 (both are one rounding of the same sums)."""
+    fields = [inputs.hit_fields(0, k0=3.0, urms=0.05, seed=70 + b, shape=shape) for b in range(nbatch)]
+    rho32 = np.stack([f[0] for f in fields]).astype(np.float32)
+    u32 = np.stack([f[1] for f in fields], axis=1).astype(np.float32)
+    assert rho32.size > (1 << 21)
+    with lbm.Solver(27, shape, 1e-4, closure="kcmp", storage=storage, nbatch=nbatch) as s:
+        s.init_velocity(rho32.astype(np.float64), u32.astype(np.float64))
+        f64 = s.get_populations()
+        s.init_velocity(rho32, u32)  # float32 arrays: lbm_init_velocity_f32
+        assert np.array_equal(s.get_populations(), f64)
+        s.step(2)
+        r64, v64 = s.moments()
+        r32, v32 = s.moments(np.float32)
+        assert r32.dtype == np.float32 and v32.dtype == np.float32
+        assert np.array_equal(r32, r64.astype(np.float32))
+        assert np.array_equal(v32, v64.astype(np.float32))
+        # rho only / u only
+        r_only = np.empty(rho32.shape, np.float32)
+        lbm.lbm_moments_f32(s.h, r_only, None)
+        assert np.array_equal(r_only.reshape(r32.shape), r32)
+        s.init_velocity(None, u32)
+        f_u = s.get_populations()
+        s.init_velocity(None, u32.astype(np.float64))
+        assert np.array_equal(s.get_populations(), f_u)
+
+
 @pytest.mark.parametrize("storage", ["fp64", "fp32"])
 @pytest.mark.parametrize("closure", ["bgk", "kcmp", "kcrb_raw"])
 def test_load_schedule_variants_d3q19(lbm, orc, storage, closure):

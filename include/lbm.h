@@ -103,9 +103,9 @@ typedef struct {
     int zchunk;         /* tuning: z-planes per CTA march (0 = library default)      */
     int variant;        /* tuning: step-kernel variant, 0 = library default
                            (FP32 storage: 12 on z-chunks of at most 16 planes
-                           for periodic D3Q27 with KC-MP, KC-RB or the
-                           learned closure, 13 for KC-RR, D3Q19 and walls
-                           with KC-MP; else 8 for periodic D3Q27; else 1),
+                           for periodic D3Q27 with KC-MP or KC-RB, 13 for
+                           KC-RR, D3Q19 and walls with KC-MP; else 8 for
+                           periodic D3Q27 except the learned closure; else 1),
                            1 = register pull (every lattice, storage, closure
                            and boundary), 4 = TMA-staged pipeline (FP32,
                            periodic, BGK/KC-MP/KC-RB, nx % 32 == 0 and

@@ -442,28 +442,31 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
     if (has_force && bc_kind != BC_WALLS_Y)
         return fail(LBM_ERR_UNSUPPORTED, "a body force is supported with bounce-back walls (channel) only");
     // the learned closure runs 4-row tiles by default: at 128 threads per CTA
-    // its kernels keep the network's fragments in ~240 registers without
-    // spilling (8-row tiles cap them at 128 and spill); the rest 8-row tiles
+    // its register-pull kernel keeps both halves' network fragments in ~250
+    // registers without spilling (8-row tiles cap them at 128 and spill); the
+    // rest 8-row tiles
     int tile_y = cfg->tile_y ? cfg->tile_y : (cfg->closure == LBM_LEARNED ? 4 : 8);
     if (cfg->variant != VAR_DEFAULT && cfg->variant != VAR_REGISTER && cfg->variant != VAR_TMA && cfg->variant != VAR_SPLIT &&
         cfg->variant != VAR_PAIR && cfg->variant != VAR_SPLIT_PF && cfg->variant != VAR_ASYNC)
         return fail(LBM_ERR_ARG, "unknown kernel variant");
     int variant = cfg->variant;
     // measured defaults (512^3 and ensemble timings): for FP32 storage, periodic
-    // D3Q27 with KC-MP, KC-RB or the learned closure takes the split-barrier
-    // pull with L2 prefetches (12) marching short z-chunks (at most 16 planes);
-    // KC-RR, D3Q19 and the walls with KC-MP take the split-barrier pull with
-    // asynchronous copies (13); otherwise periodic D3Q27 (BGK, FP64, 16-bit
-    // storage) takes the split-barrier pull (8) and the rest the register pull (1).
+    // D3Q27 with KC-MP or KC-RB takes the split-barrier pull with L2 prefetches
+    // (12) marching short z-chunks (at most 16 planes); KC-RR, D3Q19 and the
+    // walls with KC-MP take the split-barrier pull with asynchronous copies
+    // (13); otherwise periodic D3Q27 (BGK, FP64, 16-bit storage) takes the
+    // split-barrier pull (8) and the rest, the learned closure included (its
+    // register pull on 4-row tiles evaluates the network for both halves of a
+    // warp at once, 256^3), the register pull (1).
     // lbm_autotune may pick another launch for a given box
     bool short_chunks = false;
     if (variant == VAR_DEFAULT) {
         const bool carrier = cfg->closure == LBM_KCMP || cfg->closure == LBM_KCRB_HERMITE ||
                              cfg->closure == LBM_KCRB_RAW || cfg->closure == LBM_KCRR;
-        const bool split_built = carrier || cfg->closure == LBM_BGK || cfg->closure == LBM_LEARNED;
+        const bool split_built = carrier || cfg->closure == LBM_BGK;
         const bool pf_first = cfg->lattice == LBM_D3Q27 && bc_kind == BC_PERIODIC && cfg->storage == LBM_FP32 &&
                               (cfg->closure == LBM_KCMP || cfg->closure == LBM_KCRB_HERMITE ||
-                               cfg->closure == LBM_KCRB_RAW || cfg->closure == LBM_LEARNED);
+                               cfg->closure == LBM_KCRB_RAW);
         if (pf_first && step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, VAR_SPLIT_PF)) {
             variant = VAR_SPLIT_PF;
             short_chunks = true;

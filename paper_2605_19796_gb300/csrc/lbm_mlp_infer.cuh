@@ -146,6 +146,79 @@ __device__ __forceinline__ void mlp_hidden(const unsigned char* sm, int woff, in
     }
 }
 
+// The same layer for both 16-row tiles of the warp at once: each B fragment
+// is loaded once and feeds two independent MMAs, so the layer issues half the
+// ldmatrix operations and has two accumulator chains in flight (twice the
+// fragment registers: taken where the kernel can afford them).
+template <int KS, int LDW>
+__device__ __forceinline__ void mlp_hidden2(const unsigned char* sm, int woff, int boff, const uint32_t (&ain0)[KS][4],
+                                            const uint32_t (&ain1)[KS][4], uint32_t (&aout0)[4][4],
+                                            uint32_t (&aout1)[4][4], int lane)
+{
+    const int t = lane & 3;
+    const uint32_t wbase = (uint32_t)__cvta_generic_to_shared(sm + woff);
+    const float2* B = reinterpret_cast<const float2*>(sm + boff);
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const float2 bb = B[4 * nt + t];
+        float c0[4] = {bb.x, bb.y, bb.x, bb.y};
+        float c1[4] = {bb.x, bb.y, bb.x, bb.y};
+#pragma unroll
+        for (int s = 0; s < KS; ++s) {
+            uint32_t b0, b1;
+            ldsm_x2(ldsm_row<LDW>(wbase, 8 * nt, 16 * s, lane & 15), b0, b1);
+            mma_bf16_16816(c0, ain0[s], b0, b1);
+            mma_bf16_16816(c1, ain1[s], b0, b1);
+        }
+        const int j = nt >> 1, o = (nt & 1) * 2;
+        aout0[j][o] = mlp_silu_pack(c0[0], c0[1]);
+        aout0[j][o + 1] = mlp_silu_pack(c0[2], c0[3]);
+        aout1[j][o] = mlp_silu_pack(c1[0], c1[1]);
+        aout1[j][o + 1] = mlp_silu_pack(c1[2], c1[3]);
+    }
+}
+
+// Network forward for the warp's 32 cells, both 16-row tiles together (see
+// mlp_hidden2); all inputs are read before the first output is written.
+__device__ __forceinline__ void mlp_warp_forward_dual(const unsigned char* sm, const __nv_bfloat16* X, float* Y,
+                                                      int lane)
+{
+    using L = MlpLayout;
+    const int g = lane >> 2, t = lane & 3;
+    const uint32_t* Xw = reinterpret_cast<const uint32_t*>(X);
+    uint32_t a[2][1][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+        const int r0 = 16 * mt + g, r1 = r0 + 8;
+        a[mt][0][0] = Xw[(r0 * L::XLD + 2 * t) / 2];
+        a[mt][0][1] = Xw[(r1 * L::XLD + 2 * t) / 2];
+        a[mt][0][2] = Xw[(r0 * L::XLD + 2 * t + 8) / 2];
+        a[mt][0][3] = Xw[(r1 * L::XLD + 2 * t + 8) / 2];
+    }
+    uint32_t p1[4][4], q1[4][4], p2[4][4], q2[4][4];
+    mlp_hidden2<1, L::LD1>(sm, L::W1, L::B1, a[0], a[1], p1, q1, lane);
+    mlp_hidden2<4, L::LD>(sm, L::W2, L::B2, p1, q1, p2, q2, lane);
+    mlp_hidden2<4, L::LD>(sm, L::W3, L::B3, p2, q2, p1, q1, lane);
+    const uint32_t w4 = (uint32_t)__cvta_generic_to_shared(sm + L::W4);
+    const float2 b4 = reinterpret_cast<const float2*>(sm + L::B4)[t];
+    float c0[4] = {b4.x, b4.y, b4.x, b4.y};
+    float c1[4] = {b4.x, b4.y, b4.x, b4.y};
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) {
+        uint32_t b[4];
+        ldsm_x4(ldsm_row<L::LD>(w4, 0, 32 * sp, lane), b);
+        mma_bf16_16816(c0, p1[2 * sp], b[0], b[1]);
+        mma_bf16_16816(c0, p1[2 * sp + 1], b[2], b[3]);
+        mma_bf16_16816(c1, q1[2 * sp], b[0], b[1]);
+        mma_bf16_16816(c1, q1[2 * sp + 1], b[2], b[3]);
+    }
+    __syncwarp();  // every lane has read both tiles' inputs
+    *reinterpret_cast<float2*>(Y + g * 8 + 2 * t) = make_float2(c0[0], c0[1]);
+    *reinterpret_cast<float2*>(Y + (g + 8) * 8 + 2 * t) = make_float2(c0[2], c0[3]);
+    *reinterpret_cast<float2*>(Y + (g + 16) * 8 + 2 * t) = make_float2(c1[0], c1[1]);
+    *reinterpret_cast<float2*>(Y + (g + 24) * 8 + 2 * t) = make_float2(c1[2], c1[3]);
+}
+
 // Network forward for the warp's 32 cells: X [32][XLD] bf16 (standardised
 // inputs, columns 10..15 zero) -> Y [32][8] f32 (standardised outputs 0..5);
 // Y may alias X (the exchange layout above).

@@ -664,7 +664,7 @@ constexpr size_t step_smem_bytes()
 // The populations are read from the shared-memory stash (stride NT) rather
 // than kept in registers, so that only the network's fragments are live while
 // it runs; the caller reloads them for the collision.
-template <int Q, typename R, int NT>
+template <int Q, typename R, int NT, bool DUAL = false>
 __device__ __forceinline__ void learned_msgs(const R* st, R drho, R ux, R uy, R uz, R Sxx, R Syy, R Szz, R Sxy,
                                              R Sxz, R Syz, R tau_hat, const unsigned char* sm_mlp, unsigned char* xch,
                                              int lane, R (&msgs)[6])
@@ -716,7 +716,12 @@ __device__ __forceinline__ void learned_msgs(const R* st, R drho, R ux, R uy, R 
 #pragma unroll
     for (int q = 5; q < 8; ++q) Xrow[q] = 0u;
     __syncwarp();
-    mlp_warp_forward(sm_mlp, X, Y, lane);
+    // DUAL: both 16-cell halves of the warp together (where the kernel has
+    // the registers for it)
+    if constexpr (DUAL)
+        mlp_warp_forward_dual(sm_mlp, X, Y, lane);
+    else
+        mlp_warp_forward(sm_mlp, X, Y, lane);
     __syncwarp();
     const float* ymu = reinterpret_cast<const float*>(sm_mlp + L::YMU);
     const float* ysd = reinterpret_cast<const float*>(sm_mlp + L::YSD);
@@ -899,7 +904,7 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
             const R* st = stash + (z & 1) * Q * NT + tid;
             if constexpr (CL == CL_LEARNED) {
                 R msgs[6];
-                learned_msgs<Q, R, NT>(st, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, tau_hat, sm_mlp, sm_xch,
+                learned_msgs<Q, R, NT, (NT <= 128)>(st, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, tau_hat, sm_mlp, sm_xch,
                                        tx, msgs);
 #pragma unroll
                 for (int i = 0; i < Q; ++i) g[i] = st[i * NT];

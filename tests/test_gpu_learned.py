@@ -176,7 +176,8 @@ def test_learned_step_matches_oracle(env, orc, q, variant, tile_y):
     """One step of the fused learned closure (BF16 tensor-core network inside the
     step kernel: the register pull, variant 1, the split-barrier kernel,
     variant 8, and the same with L2 prefetches, variant 12; tiles of 8 rows and
-    the default 4; D3Q27 and D3Q19)
+    the default 4, where the register pull evaluates the network for both
+    16-cell halves of a warp together; D3Q27 and D3Q19)
     against the oracle's learned step with the same BF16 rounding
     points (inputs, weights, hidden activations) and FP64 elsewhere.  The network
     is random, its output scaled so that the turbulent rate is active in most
@@ -237,8 +238,8 @@ def test_learned_step_matches_oracle(env, orc, q, variant, tile_y):
 
 def test_learned_full_size_sampled_cells(env, orc):
     """The learned closure at 256^3 (D3Q27, FP32, decaying HIT, nu = 2.5e-5) in
-    its default launch (split-barrier kernel with L2 prefetches, 16-plane
-    chunks of 4-row tiles): one GPU step, then sampled cells against the
+    its default launch (register pull on 4-row tiles, the network evaluated for
+    both halves of each warp at once): one GPU step, then sampled cells against the
     oracle's learned step of the periodic 5x5x5 block around each cell, cut from
     the GPU's own pre-step populations (the centre's pulls and the strain at its
     six neighbours stay inside the block, so the centre is exact).  Random
@@ -260,7 +261,7 @@ def test_learned_full_size_sampled_cells(env, orc):
     params = np.asarray(mlp.flat(mlp.init_params(5)), dtype=np.float32)
     with lbm.Solver(27, (n, n, n), nu, closure="learned", storage="fp32", c_nu=c_nu) as s:
         cfg = s.launch_config
-        assert cfg["variant"] == 12 and cfg["tile_y"] == 4 and cfg["zchunk"] <= 16, cfg
+        assert cfg["variant"] == 1 and cfg["tile_y"] == 4, cfg
         s.init_velocity(rho, u)
         del rho, u
         s.set_learned_closure(params, _stats_for(np.ones((2, 10)), 1.0))
@@ -290,7 +291,7 @@ def test_learned_full_size_sampled_cells(env, orc):
 @pytest.mark.parametrize("storage", ["fp16", "bf16"])
 def test_learned_step_16bit_storage(env, orc, storage):
     """The learned closure on weight-shifted 16-bit storage (its default launch,
-    the split-barrier kernel): one step from a state that FP16/BF16 hold
+    the register pull on 4-row tiles): one step from a state that FP16/BF16 hold
     exactly gives the density and velocity of the same step on FP32 storage
     within the rounding of the stored results: 8 units of the format's relative
     spacing (2^-10 FP16, 2^-7 BF16) times max |f - w|, the bound the

@@ -447,18 +447,18 @@ def test_tma_variant_matches(lbm, orc, shape, nbatch, closure):
 
 
 def test_default_variant_selection(lbm):
-    """Library default: for FP32 storage, periodic D3Q27 with KC-MP, KC-RB or
-    the learned closure takes the split-barrier pull with L2 prefetches (12) on
-    z-chunks of at most 16 planes; KC-RR, D3Q19 and walls with KC-MP the
-    split-barrier pull with asynchronous copies (13); periodic D3Q27 otherwise
-    (BGK, FP64, 16-bit storage) the split-barrier pull (8); the rest the
-    register pull (1).  Tiles are 8 rows, 4 for the learned closure.  An explicitly requested variant that is not built for
+    """Library default: for FP32 storage, periodic D3Q27 with KC-MP or KC-RB
+    takes the split-barrier pull with L2 prefetches (12) on z-chunks of at most
+    16 planes; KC-RR, D3Q19 and walls with KC-MP the split-barrier pull with
+    asynchronous copies (13); periodic D3Q27 otherwise (BGK, FP64, 16-bit
+    storage) the split-barrier pull (8); the rest, the learned closure
+    included, the register pull (1).  Tiles are 8 rows, 4 for the learned closure.  An explicitly requested variant that is not built for
     a box is refused."""
     for q, closure, storage, want in ((27, "kcmp", "fp32", 12), (27, "kcrb_hermite", "fp16", 8), (27, "kcmp", "fp64", 8),
                                       (27, "kcrb_raw", "fp32", 12), (27, "kcrr", "fp32", 13),
                                       (27, "bgk", "fp32", 8), (19, "kcmp", "fp32", 13), (19, "bgk", "fp32", 1),
                                       (19, "kcmp", "fp16", 1), (27, "kcrr", "fp64", 8),
-                                      (27, "learned", "fp32", 12)):
+                                      (27, "learned", "fp32", 1)):
         with lbm.Solver(q, (40, 32, 64), 1e-4, closure=closure, storage=storage) as s:
             assert s.launch_config["variant"] == want, (q, closure, storage)
             if want == 12:

@@ -1,7 +1,9 @@
 """Pins of the FP64 oracle network of the learned closure (no GPU): the
 backward pass against central finite differences of the loss, the silu
 derivative against its closed form, and the first AdamW step against its
-textbook value lr * sign(g) (bias-corrected moments equal g and g^2)."""
+textbook value lr * sign(g) (bias-corrected moments equal g and g^2).  Pins of
+the learned step around the network: a zero network gives the BGK step, and a
+network that returns the KC-MP carrier gives the KC-MP step (App. F.3)."""
 import numpy as np
 import pytest
 
@@ -121,3 +123,38 @@ def test_learned_step_with_zero_output_is_bgk():
     assert np.abs(msgs).max() == 0.0
     ref = oracle.run(f, 1, closure=0, nu=1e-4)
     assert np.abs(fpost - ref).max() < 1e-15
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_learned_step_with_carrier_output_is_kcmp(q, monkeypatch):
+    """A network that returns the KC-MP carrier itself (its first six inputs,
+    de-standardised with the input statistics) makes m_sgs = m_neq - m_CE, so
+    the learned step must be the KC-MP step of the C oracle (App. F.3).  This
+    ties the learned step's carrier inputs, its m_sgs -> f_sgs projection, the
+    rate clip and the two-rate relaxation to the pinned analytic closure.  The
+    remaining inputs (invariants of m_CE / rho, tau_hat) equal those of the
+    training-data features of the same streamed state, which are pinned on
+    their own."""
+    import oracle
+    from oracle import closure_data as cd
+    from oracle import learned
+    from paper_2605_19796_gb300 import inputs
+
+    nu, c_nu = 1e-5, 0.035
+    rho, u = inputs.hit_fields(0, k0=2.0, urms=0.08, seed=4, shape=(8, 6, 5))
+    f = oracle.run(oracle.init_equilibrium(q, rho, u), 3, closure=1, nu=nu, c_nu=c_nu)
+    rng = np.random.default_rng(9)
+    xmu, xsd = 1e-3 * rng.standard_normal(10), rng.uniform(0.5, 2.0, 10)
+    stats = np.concatenate([xmu, xsd, xmu[:6], xsd[:6]])
+    monkeypatch.setattr(learned, "forward", lambda params, xs, rounding: xs[:, :6].copy())
+    fpost, msgs = learned.step(f, nu, np.zeros(mlp.NPARAM), stats, c_nu)
+    ref = oracle.run(f, 1, closure=1, nu=nu, c_nu=c_nu)
+    assert np.abs(fpost - ref).max() <= 1e-14 * np.abs(ref).max()
+    # the SGS rate is active in a good share of the cells, so the check has teeth
+    tr = msgs[:, 0] + msgs[:, 1] + msgs[:, 2]
+    assert np.mean(c_nu * np.sqrt(np.abs(tr) / 2) > nu) > 0.3
+    bgk = oracle.run(f, 1, closure=0, nu=nu)
+    assert np.abs(ref - bgk).max() > 1e3 * 1e-14 * np.abs(ref).max()
+    x = learned.inputs_and_state(f, nu)[4]
+    xf, _ = cd.features(cd.stream(f), nu)
+    assert np.abs(x - xf).max() <= 1e-15 * max(1.0, np.abs(xf).max())

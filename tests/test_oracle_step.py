@@ -11,6 +11,8 @@
     exp(-4 nu k^2 t)), where the clip of Eq. (omega_sgs_operational) makes
     the closures reduce to BGK;
   - the x<->y mirror symmetry of the 3D Taylor-Green vortex;
+  - the moments of Guo's forcing source (mass kept, momentum + F, second
+    moment + (1 - omega/2)(u F + F u));
   - laminar Poiseuille flow with bounce-back walls and a body force;
   - the Sec. 7.1 diagnostics on the Taylor-Green initial field;
   - the single-cell step against the full-lattice step.
@@ -222,6 +224,33 @@ def test_tgv3d_symmetries(orc, q):
     assert np.abs(sw(ug[0]) - ug[1]).max() < 1e-13
     assert np.abs(sw(ug[1]) - ug[0]).max() < 1e-13
     assert np.abs(sw(ug[2]) - ug[2]).max() < 1e-13
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_guo_source_moments(orc, q):
+    """With a body force the collision adds Guo's source (the reading taken
+    where the paper neglects forces): after a BGK collision the mass is
+    unchanged, the momentum has gained F, and the second moment is the
+    unforced relaxation of Pi towards rho (u u + theta I), u = (sum f c +
+    F/2)/rho, plus (1 - omega/2)(u F + F u), the second moment of the textbook
+    source, which follows from the fourth-order isotropy both lattices have."""
+    rng = np.random.default_rng(31)
+    c = np.array(_velocities(q), dtype=float)
+    _, w, _ = orc.lattice(q)
+    for k in range(4):
+        f = w * (1.0 + 0.05 * rng.standard_normal(q))
+        F = 1e-3 * rng.standard_normal(3)
+        nu = 0.02 + 0.05 * k
+        omega = 1.0 / (nu / THETA + 0.5)
+        fp, _ = orc.collide_cell(q, 0, f, np.zeros((3, 3)), nu, 0.0, F=F)
+        rho = f.sum()
+        u = (f @ c + 0.5 * F) / rho
+        pi = np.einsum("i,ia,ib->ab", f, c, c)
+        want = pi - omega * (pi - rho * (np.outer(u, u) + THETA * np.eye(3))) + (1 - 0.5 * omega) * (
+            np.outer(u, F) + np.outer(F, u))
+        assert np.abs(np.einsum("i,ia,ib->ab", fp, c, c) - want).max() <= 1e-15
+        assert abs(fp.sum() - rho) <= 4 * EPS
+        assert np.abs(fp @ c - (f @ c + F)).max() <= 1e-16
 
 
 @pytest.mark.parametrize("q", [19, 27])

@@ -2,7 +2,8 @@
   - box filter of a constant and of a linear field;
   - Eq. (m_sgs_2): for a fine state that is uniform inside every filter box
     the exact SGS stress vanishes; for two-valued velocity inside a box it equals
-    the textbook covariance rho_bar (<u u> - <u><u>) (equal densities);
+    the textbook covariance rho_bar (<u u> - <u><u>) (equal densities), and with
+    two densities the density-weighted covariance of two parcels;
   - the carrier inputs (m_neq - m_CE)/rho of an equilibrium state are
     2 theta tau_hat S; an added second-order Hermite mode moves only its own
     component, by the mode's coefficient;
@@ -47,6 +48,26 @@ def test_msgs_two_valued_velocity_covariance():
     d = u1 - u2
     for k, (a, b) in enumerate(cd.COMP):
         assert np.allclose(msgs[k], d[a] * d[b] / 4, rtol=1e-12, atol=1e-17)
+
+
+def test_msgs_two_valued_density_and_velocity():
+    """Half the cells of each 2^3 box hold (rho1, u1), half (rho2, u2): Eq.
+    (m_sgs_2) gives bar(rho u u) - bar(rho u) bar(rho u) / bar(rho) =
+    rho1 rho2 / (2 (rho1 + rho2)) (u1 - u2)(u1 - u2)^T, the density-weighted
+    covariance of two equal parcels."""
+    u = np.zeros((3, 4, 4, 4))
+    rho = np.zeros((4, 4, 4))
+    u1, u2 = np.array([0.03, -0.01, 0.02]), np.array([-0.02, 0.015, 0.0])
+    r1, r2 = 1.1, 0.95
+    rho[:, 0::2, :], rho[:, 1::2, :] = r1, r2
+    for a in range(3):
+        u[a, :, 0::2, :] = u1[a]
+        u[a, :, 1::2, :] = u2[a]
+    f = oracle.init_equilibrium(27, rho, u)
+    _, msgs = cd.filtered_state(f, 2)
+    d = u1 - u2
+    for k, (a, b) in enumerate(cd.COMP):
+        assert np.allclose(msgs[k], r1 * r2 / (2 * (r1 + r2)) * d[a] * d[b], rtol=1e-11, atol=1e-17)
 
 
 def test_features_equilibrium_and_hermite_mode():

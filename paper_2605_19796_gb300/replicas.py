@@ -17,7 +17,10 @@ from typing import Optional
 class Replicas:
     """Process-group bookkeeping of a replica run; a single process needs none."""
 
-    def __init__(self, backend: Optional[str] = None):
+    def __init__(self, backend: Optional[str] = None, timeout_s: Optional[float] = None):
+        """timeout_s: limit of every collective of the group (barriers, the
+        timing reduction), so that the ranks left behind by a rank that failed
+        get an error at their next collective instead of waiting for ever."""
         self.world = int(os.environ.get("WORLD_SIZE", "1"))
         self.rank = int(os.environ.get("RANK", "0"))
         self.local = int(os.environ.get("LOCAL_RANK", str(self.rank)))
@@ -28,11 +31,16 @@ class Replicas:
             import torch.distributed as dist
 
             os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            kw = {}
+            if timeout_s is not None:
+                import datetime
+
+                kw["timeout"] = datetime.timedelta(seconds=float(timeout_s))
             if self.backend == "nccl":
                 torch.cuda.set_device(self.local)
-                dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
+                dist.init_process_group("nccl", device_id=torch.device("cuda", self.local), **kw)
             else:
-                dist.init_process_group(self.backend)
+                dist.init_process_group(self.backend, **kw)
             self.dist = dist
 
     @property

@@ -1,6 +1,7 @@
 """The replica bookkeeping of multi-GPU runs (paper_2605_19796_gb300/replicas.py)
 on two CPU processes with the gloo backend: max-over-ranks timing, the
-whole-job rate, distinct seeds, barriers, root-only reporting.  The data path
+whole-job rate, distinct seeds, barriers, root-only reporting, and a rank
+that leaves: the others' next barrier fails within the group timeout.  The data path
 has no collective (independent replicas), so this is all there is to shard."""
 import multiprocessing as mp
 import os
@@ -50,6 +51,46 @@ def test_two_gloo_ranks():
         assert t == 2.0  # the slowest rank
         assert rate == pytest.approx(100.0 * 2 / 2.0)
     assert sorted(res[0][5] + res[1][5]) == list(range(6))  # distinct seeds over ranks and boxes
+
+
+def _leaving_worker(rank, world, port, q):
+    """Rank 1 leaves between steps (no collective in flight) without telling
+    anyone; rank 0's next barrier must fail within the group's timeout."""
+    import time
+
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank), MASTER_ADDR="127.0.0.1",
+                      MASTER_PORT=str(port))
+    rep = Replicas("gloo", timeout_s=5.0)
+    rep.barrier()  # both ranks are up
+    if rank == 1:
+        q.put((rank, "left", 0.0))
+        q.close()
+        q.join_thread()  # the message is out before the process goes
+        os._exit(0)
+    t0 = time.perf_counter()
+    try:
+        rep.barrier()
+        q.put((rank, "no error", time.perf_counter() - t0))
+    except Exception as e:  # the expected outcome
+        q.put((rank, "error: " + type(e).__name__, time.perf_counter() - t0))
+    q.close()
+    q.join_thread()
+    os._exit(0)
+
+
+def test_rank_that_leaves_fails_the_others_next_barrier():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_leaving_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = dict((r, (what, dt)) for r, what, dt in (q.get(timeout=120) for _ in ps))
+    for p in ps:
+        p.join(timeout=60)
+    assert res[1][0] == "left"
+    assert res[0][0].startswith("error"), res[0]
+    assert res[0][1] < 30.0  # bounded by the group timeout, not a hang
 
 
 def test_single_process_needs_no_group(monkeypatch):

@@ -289,6 +289,19 @@ int lbm_mlp_param_count(void);
  * Synchronises. */
 int lbm_set_learned_closure(lbm_handle* h, const float* params, const float* stats);
 
+/* The network as a file (the paper has no format for it; this library's):
+ * the 8 bytes "LBMMLP01", two little-endian int32 counts (9414 parameters,
+ * 32 statistics), then the parameters and the statistics as little-endian
+ * FP32 in the orders of lbm_set_learned_closure; nothing after them.
+ * lbm_read_learned_closure reads such a file into caller-owned host buffers
+ * (nparam and nstats give their lengths and must be 9414 and 32); it touches
+ * no device.  A missing file, a wrong magic or count, a short file or
+ * trailing bytes: LBM_ERR_ARG (buffers then unspecified).
+ * lbm_set_learned_closure_file reads the file and installs the network as
+ * lbm_set_learned_closure does.  Synchronises. */
+int lbm_read_learned_closure(const char* path, float* params, int nparam, float* stats, int nstats);
+int lbm_set_learned_closure_file(lbm_handle* h, const char* path);
+
 /* Bytes of the packed network block the fused inference reads (BF16 weights,
  * FP32 biases and statistics), and the packing itself into host memory. */
 long long lbm_mlp_packed_bytes(void);

@@ -15,7 +15,10 @@
 #include "lbm_equilibrium.cuh"
 #include "lbm_mlp_infer.cuh"
 
+#include <cstdint>
+#include <cstdio>
 #include <cstring>
+#include <vector>
 
 namespace lbmk {
 namespace {
@@ -415,6 +418,41 @@ int lbm_mlp_pack(const float* params, const float* stats, void* out_host)
     if (!params || !stats || !out_host) return set_last_error(LBM_ERR_ARG, "lbm_mlp_pack: NULL argument");
     mlp_pack(params, stats, static_cast<unsigned char*>(out_host));
     return LBM_OK;
+}
+
+int lbm_read_learned_closure(const char* path, float* params, int nparam, float* stats, int nstats)
+{
+    if (!path || !params || !stats) return set_last_error(LBM_ERR_ARG, "lbm_read_learned_closure: NULL argument");
+    if (nparam != kNParam || nstats != 32)
+        return set_last_error(LBM_ERR_ARG, "lbm_read_learned_closure: buffers must hold 9414 parameters and 32 statistics");
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return set_last_error(LBM_ERR_ARG, "lbm_read_learned_closure: cannot open the file");
+    char magic[8];
+    int32_t counts[2];
+    int rc = LBM_OK;
+    const char* why = nullptr;
+    if (std::fread(magic, 1, 8, fp) != 8 || std::memcmp(magic, "LBMMLP01", 8) != 0) {
+        why = "not a network file (magic LBMMLP01 expected)";
+    } else if (std::fread(counts, sizeof(int32_t), 2, fp) != 2 || counts[0] != kNParam || counts[1] != 32) {
+        why = "parameter or statistics count differs from this network (9414, 32)";
+    } else if (std::fread(params, sizeof(float), (size_t)kNParam, fp) != (size_t)kNParam ||
+               std::fread(stats, sizeof(float), 32, fp) != 32) {
+        why = "file ends early";
+    } else {
+        unsigned char extra;
+        if (std::fread(&extra, 1, 1, fp) != 0) why = "trailing bytes after the statistics";
+    }
+    std::fclose(fp);
+    if (why) rc = set_last_error(LBM_ERR_ARG, (std::string("lbm_read_learned_closure: ") + why).c_str());
+    return rc;
+}
+
+int lbm_set_learned_closure_file(lbm_handle* h, const char* path)
+{
+    if (!h || !path) return set_last_error(LBM_ERR_ARG, "lbm_set_learned_closure_file: NULL argument");
+    std::vector<float> params(kNParam), stats(32);
+    if (int rc = lbm_read_learned_closure(path, params.data(), kNParam, stats.data(), 32)) return rc;
+    return lbm_set_learned_closure(h, params.data(), stats.data());
 }
 
 int lbm_mlp_forward_tc(const void* packed_dev, const float* x_dev, int n, float* y_dev, void* stream)

@@ -42,7 +42,8 @@ EXPORTS = ["lbm_config_default", "lbm_create", "lbm_destroy", "lbm_init_velocity
            "lbm_mlp_workspace_floats", "lbm_mlp_forward", "lbm_mlp_grad", "lbm_mlp_adamw", "lbm_box_filter",
            "lbm_closure_features", "lbm_set_learned_closure", "lbm_mlp_packed_bytes", "lbm_mlp_pack",
            "lbm_mlp_forward_tc", "lbm_wait_selftest", "lbm_host_alloc", "lbm_host_free",
-           "lbm_init_velocity_f32", "lbm_moments_f32"]
+           "lbm_init_velocity_f32", "lbm_moments_f32", "lbm_read_learned_closure",
+           "lbm_set_learned_closure_file"]
 
 
 class lbm_config(ctypes.Structure):
@@ -75,6 +76,8 @@ def _load() -> ctypes.CDLL:
     lib.lbm_destroy.restype = None
     lib.lbm_init_velocity.argtypes = [H, dp, dp]
     fp = P(ctypes.c_float)
+    lib.lbm_read_learned_closure.argtypes = [ctypes.c_char_p, fp, ctypes.c_int, fp, ctypes.c_int]
+    lib.lbm_set_learned_closure_file.argtypes = [H, ctypes.c_char_p]
     lib.lbm_init_velocity_f32.argtypes = [H, fp, fp]
     lib.lbm_moments_f32.argtypes = [H, fp, fp]
     lib.lbm_init_velocity_device.argtypes = [H, vp, vp]
@@ -339,6 +342,31 @@ def lbm_wait_selftest(h, polls: int) -> int:
     return int(LIB.lbm_wait_selftest(h, int(polls)))
 
 
+def write_learned_closure(path: str, params: np.ndarray, stats: np.ndarray) -> None:
+    """The network file lbm_read_learned_closure reads: b"LBMMLP01", int32
+    counts (9414, 32), FP32 parameters, FP32 statistics, little-endian."""
+    p = np.ascontiguousarray(params, dtype="<f4").ravel()
+    st = np.ascontiguousarray(stats, dtype="<f4").ravel()
+    assert p.size == lbm_mlp_param_count() and st.size == 32
+    with open(path, "wb") as fp:
+        fp.write(b"LBMMLP01")
+        fp.write(np.array([p.size, st.size], dtype="<i4").tobytes())
+        fp.write(p.tobytes())
+        fp.write(st.tobytes())
+
+
+def lbm_read_learned_closure(path: str):
+    """(params [9414], stats [32]) float32 from a network file."""
+    p = np.empty(lbm_mlp_param_count(), dtype=np.float32)
+    st = np.empty(32, dtype=np.float32)
+    _check(LIB.lbm_read_learned_closure(os.fsencode(path), _fp(p), p.size, _fp(st), st.size))
+    return p, st
+
+
+def lbm_set_learned_closure_file(h, path: str) -> None:
+    _check(LIB.lbm_set_learned_closure_file(h, os.fsencode(path)))
+
+
 def lbm_set_learned_closure(h, params: np.ndarray, stats: np.ndarray) -> None:
     p = np.ascontiguousarray(params, dtype=np.float32)
     st = np.ascontiguousarray(stats, dtype=np.float32)
@@ -496,6 +524,9 @@ class Solver:
 
     def set_learned_closure(self, params: np.ndarray, stats: np.ndarray) -> None:
         lbm_set_learned_closure(self.h, params, stats)
+
+    def set_learned_closure_file(self, path: str) -> None:
+        lbm_set_learned_closure_file(self.h, path)
 
     def autotune(self, trials: int = 3) -> dict:
         lbm_autotune(self.h, trials)

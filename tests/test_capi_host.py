@@ -99,3 +99,37 @@ def test_host_alloc_argument_checks_need_no_device(lbm):
     assert p.value is None
     assert lbm.LIB.lbm_host_alloc(ctypes.c_size_t(64), None) == lbm.LBM_ERR_ARG
     assert lbm.LIB.lbm_host_free(None) == lbm.LBM_OK
+
+
+def test_learned_closure_file_round_trip_and_errors(lbm, tmp_path):
+    """The network file (magic, int32 counts, FP32 parameters and statistics)
+    reads back exactly on the host, and every malformed variant is refused
+    with LBM_ERR_ARG before any device work."""
+    rng = np.random.default_rng(3)
+    p = rng.standard_normal(lbm.lbm_mlp_param_count()).astype(np.float32)
+    st = rng.standard_normal(32).astype(np.float32)
+    path = tmp_path / "net.bin"
+    lbm.write_learned_closure(str(path), p, st)
+    assert path.stat().st_size == 8 + 8 + 4 * (p.size + 32)
+    p2, st2 = lbm.lbm_read_learned_closure(str(path))
+    assert np.array_equal(p2, p) and np.array_equal(st2, st)
+    raw = path.read_bytes()
+    pp, ss = np.empty(p.size, np.float32), np.empty(32, np.float32)
+
+    def rc_of(data, nparam=p.size, nstats=32):
+        q = tmp_path / "bad.bin"
+        q.write_bytes(data)
+        return lbm.LIB.lbm_read_learned_closure(str(q).encode(), lbm._fp(pp), nparam, lbm._fp(ss), nstats)
+
+    assert rc_of(raw) == lbm.LBM_OK
+    assert rc_of(b"LBMMLP02" + raw[8:]) == lbm.LBM_ERR_ARG
+    assert "magic" in lbm.lbm_last_error()
+    assert rc_of(raw[:8] + np.array([p.size - 1, 32], dtype="<i4").tobytes() + raw[16:]) == lbm.LBM_ERR_ARG
+    assert rc_of(raw[:-4]) == lbm.LBM_ERR_ARG
+    assert rc_of(raw + b"\0") == lbm.LBM_ERR_ARG
+    assert rc_of(raw, nparam=p.size - 1) == lbm.LBM_ERR_ARG
+    assert rc_of(raw, nstats=31) == lbm.LBM_ERR_ARG
+    assert lbm.LIB.lbm_read_learned_closure(str(tmp_path / "missing.bin").encode(), lbm._fp(pp), p.size,
+                                            lbm._fp(ss), 32) == lbm.LBM_ERR_ARG
+    assert lbm.LIB.lbm_read_learned_closure(None, lbm._fp(pp), p.size, lbm._fp(ss), 32) == lbm.LBM_ERR_ARG
+    assert lbm.LIB.lbm_set_learned_closure_file(None, str(path).encode()) == lbm.LBM_ERR_ARG

@@ -288,6 +288,32 @@ def test_learned_full_size_sampled_cells(env, orc):
     assert active > len(pts) // 2, active
 
 
+def test_learned_closure_from_file_equals_arrays(env, tmp_path):
+    """lbm_set_learned_closure_file installs the same network as
+    lbm_set_learned_closure with the arrays the file holds: one step from the
+    same state gives bitwise equal populations."""
+    lbm, torch = env
+    from oracle import mlp
+
+    shape = (32, 16, 12)
+    rho, u = inputs.hit_fields(0, k0=3.0, urms=0.05, seed=21, shape=shape)
+    params = np.asarray(mlp.flat(mlp.init_params(8)), dtype=np.float32)
+    stats = _stats_for(np.random.default_rng(2).standard_normal((64, 10)), 1e-3)
+    path = str(tmp_path / "net.bin")
+    lbm.write_learned_closure(path, params, stats)
+    out = []
+    for from_file in (False, True):
+        with lbm.Solver(27, shape, 2e-5, closure="learned", storage="fp32") as s:
+            s.init_velocity(rho, u)
+            if from_file:
+                s.set_learned_closure_file(path)
+            else:
+                s.set_learned_closure(params, stats)
+            s.step(2)
+            out.append(s.get_populations())
+    assert np.array_equal(out[0], out[1])
+
+
 @pytest.mark.parametrize("storage", ["fp16", "bf16"])
 def test_learned_step_16bit_storage(env, orc, storage):
     """The learned closure on weight-shifted 16-bit storage (its default launch,

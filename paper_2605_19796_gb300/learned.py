@@ -376,6 +376,8 @@ def main(argv=None) -> Dict:
     os.makedirs(os.path.dirname(a.out), exist_ok=True)
     np.savez(a.out, params=res["params"], stats=stats, n_fine=a.n_fine, factor=a.factor, nu_fine=nu_fine,
              nu_coarse=nu_fine / a.factor)
+    # the same network in the library's file form (lbm_set_learned_closure_file)
+    lbm.write_learned_closure(os.path.splitext(a.out)[0] + ".bin", res["params"], stats)
     nu_c = nu_fine / a.factor
     mlups = {}
     for n in ints(a.mlups_sizes):

@@ -133,3 +133,13 @@ def test_learned_closure_file_round_trip_and_errors(lbm, tmp_path):
                                             lbm._fp(ss), 32) == lbm.LBM_ERR_ARG
     assert lbm.LIB.lbm_read_learned_closure(None, lbm._fp(pp), p.size, lbm._fp(ss), 32) == lbm.LBM_ERR_ARG
     assert lbm.LIB.lbm_set_learned_closure_file(None, str(path).encode()) == lbm.LBM_ERR_ARG
+
+
+def test_committed_network_file_matches_npz(lbm):
+    """The trained network ships in both forms; the file form holds the same
+    FP32 parameters and statistics as the npz."""
+    data = os.path.join(ROOT, "paper_2605_19796_gb300", "data")
+    d = np.load(os.path.join(data, "learned_closure.npz"))
+    p, st = lbm.lbm_read_learned_closure(os.path.join(data, "learned_closure.bin"))
+    assert np.array_equal(p, d["params"].astype(np.float32))
+    assert np.array_equal(st, d["stats"].astype(np.float32))

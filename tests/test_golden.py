@@ -1,9 +1,11 @@
 """Values the paper prints, kept as cited text fixtures under tests/golden/
 (no GPU): the lattice constants of App. F, the closure constants of Sec. 7,
-and the App. G comparison of the two KC-RB reconstructions on the 64^3
-Taylor-Green vortex, which the FP64 oracle reproduces (its trajectories are
-stored by tests/golden/make_kcrb_sensitivity.py, and the first steps are
-re-run here to tie the stored file to the current oracle)."""
+the App. G comparison of the two KC-RB reconstructions on the 64^3
+Taylor-Green vortex, which the FP64 oracle reproduces, and the Sec. 7.1
+statement that at N = 128 the closures follow the resolved-BGK energy curve
+(the oracle trajectories are stored by the make_*.py scripts beside the
+fixtures, and their first steps are re-run here to tie the stored files to
+the current oracle)."""
 import importlib.util
 import json
 import os
@@ -99,6 +101,38 @@ def test_stored_sensitivity_trajectories_are_the_oracles():
         traj = json.load(fp)
     for name, closure in (("hermite", 2), ("raw", 3)):
         now = mk.trajectory(closure, steps_max=60)
+        k = len(now["ek"])
+        for key in ("t", "ek", "z"):
+            a, b = np.array(now[key]), np.array(traj[name][key][:k])
+            assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max(), (name, key)
+
+
+def test_tgv128_closure_follows_bgk_as_sec_7_1_states():
+    """Sec. 7.1: at N = 128 the rate limiter clips the SGS relaxation almost
+    everywhere, so KC-MP's kinetic energy follows the resolved-BGK curve
+    (stored oracle trajectories, t u0/L in [0, 20]).  The paper gives no
+    number; the reading is a maximum relative E_k difference below the
+    fixture's bound."""
+    g = read_golden("tgv128_clip.txt")
+    path = os.path.join(GOLDEN, "tgv128_clip_oracle.json")
+    with open(path) as fp:
+        traj = json.load(fp)
+    b, k = np.array(traj["bgk"]["ek"]), np.array(traj["kcmp"]["ek"])
+    assert len(b) == len(k) and traj["bgk"]["t"][-1] > 19.9
+    diff = 100 * float(np.max(np.abs(k - b) / np.abs(b)))
+    assert diff < float(g["ek_max_rel_diff_percent_below"]), diff
+
+
+def test_stored_tgv128_trajectories_are_the_oracles():
+    """The first 20 steps of both N = 128 runs, re-run with the current
+    oracle, equal the stored trajectories."""
+    spec = importlib.util.spec_from_file_location("make_tgv128_clip", os.path.join(GOLDEN, "make_tgv128_clip.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    with open(os.path.join(GOLDEN, "tgv128_clip_oracle.json")) as fp:
+        traj = json.load(fp)
+    for name, closure, c_nu in mk.RUNS:
+        now = mk.trajectory(closure, c_nu, steps_max=20)
         k = len(now["ek"])
         for key in ("t", "ek", "z"):
             a, b = np.array(now[key]), np.array(traj[name][key][:k])

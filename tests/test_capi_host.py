@@ -143,3 +143,36 @@ def test_committed_network_file_matches_npz(lbm):
     p, st = lbm.lbm_read_learned_closure(os.path.join(data, "learned_closure.bin"))
     assert np.array_equal(p, d["params"].astype(np.float32))
     assert np.array_equal(st, d["stats"].astype(np.float32))
+
+
+def test_plain_c_program_uses_the_abi(lbm, tmp_path):
+    """include/lbm.h is plain C99 (pedantic, no warnings), and a C program
+    built against it and linked to the library calls entry points that need
+    no device: the ABI version, the default configuration, and an argument
+    error with its message."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_lbm.c"
+    src.write_text(
+        '#include <stdio.h>\n#include "lbm.h"\n'
+        "int main(void) {\n"
+        "    lbm_config cfg;\n"
+        "    lbm_config_default(&cfg);\n"
+        "    int rc = lbm_create(NULL, NULL);\n"
+        '    printf("%d %d %d %.3f %d %s\\n", lbm_abi_version(), cfg.lattice, cfg.closure, cfg.c_nu, rc,\n'
+        "           lbm_last_error());\n"
+        "    return 0;\n"
+        "}\n")
+    libdir = os.path.join(ROOT, "paper_2605_19796_gb300", "csrc")
+    exe = tmp_path / "use_lbm"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", str(src), "-I",
+                    os.path.join(ROOT, "include"), "-L", libdir, "-llbm", "-Wl,-rpath," + libdir, "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split(maxsplit=5)
+    assert int(out[0]) == lbm.LIB.lbm_abi_version()
+    assert int(out[1]) == 27 and int(out[2]) == lbm.CLOSURES["kcmp"] and float(out[3]) == 0.035
+    assert int(out[4]) == lbm.LBM_ERR_ARG and len(out) == 6

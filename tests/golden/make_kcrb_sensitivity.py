@@ -1,8 +1,9 @@
 """Writes kcrb_sensitivity_tgv64_oracle.json: the FP64 oracle's E_k / u0^2 and
 Z / (u0/L)^2 trajectories of the App. G comparison (KC-RB raw against Hermite,
-periodic D3Q27 TGV, N = 64, Re = 1600, Ma = 0.2, C_nu = 0.02), sampled every
-10 steps over t u0/L in [0, 20].  Calls only the oracle and the seeded input
-generator; takes a few minutes on 8 cores.
+and KC-RR as the Hermite-consistent reference; periodic D3Q27 TGV, N = 64,
+Re = 1600, Ma = 0.2, C_nu = 0.02), sampled every 10 steps over t u0/L in
+[0, 20].  Calls only the oracle and the seeded input generator; takes about
+eight minutes on 8 cores.
 
     python tests/golden/make_kcrb_sensitivity.py
 """
@@ -46,6 +47,6 @@ def trajectory(closure, steps_max=None):
 if __name__ == "__main__":
     oracle.build()
     out = {"about": "oracle trajectories of the App. G comparison; written by make_kcrb_sensitivity.py",
-           "every_steps": EVERY, "hermite": trajectory(2), "raw": trajectory(3)}
+           "every_steps": EVERY, "hermite": trajectory(2), "raw": trajectory(3), "kcrr": trajectory(4)}
     with open(os.path.join(HERE, "kcrb_sensitivity_tgv64_oracle.json"), "w") as fp:
         json.dump(out, fp)

@@ -116,7 +116,15 @@ typedef struct {
                            source rows of the plane after next prefetched
                            into L2, 13 = 8 with the own cell's pulls copied
                            to shared memory by cp.async one plane ahead
-                           (FP32 and FP64 storage); other values: LBM_ERR_ARG */
+                           (FP32 and FP64 storage), 14 = four cells per thread
+                           with 128-bit (FP32) / 64-bit (16-bit) vector loads
+                           and stores, the pulls staged in shared memory by
+                           cp.async one plane ahead and the populations parked
+                           in tensor memory until their collision (periodic
+                           D3Q27, FP32/FP16/BF16 storage, BGK/KC-MP/KC-RB,
+                           nx % 8 == 0; tile_y 8: 128 x 8 tiles, 16: 64 x 16
+                           tiles; LBM_ERR_UNSUPPORTED otherwise); other
+                           values: LBM_ERR_ARG */
     int disable_graphs; /* nonzero: lbm_step launches kernels one by one instead of
                            replaying a captured CUDA graph                        */
 } lbm_config;

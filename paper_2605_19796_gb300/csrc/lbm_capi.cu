@@ -447,7 +447,7 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
     // rest 8-row tiles
     int tile_y = cfg->tile_y ? cfg->tile_y : (cfg->closure == LBM_LEARNED ? 4 : 8);
     if (cfg->variant != VAR_DEFAULT && cfg->variant != VAR_REGISTER && cfg->variant != VAR_TMA && cfg->variant != VAR_SPLIT &&
-        cfg->variant != VAR_PAIR && cfg->variant != VAR_SPLIT_PF && cfg->variant != VAR_ASYNC)
+        cfg->variant != VAR_PAIR && cfg->variant != VAR_SPLIT_PF && cfg->variant != VAR_ASYNC && cfg->variant != VAR_VEC4)
         return fail(LBM_ERR_ARG, "unknown kernel variant");
     int variant = cfg->variant;
     // measured defaults (512^3 and ensemble timings): for FP32 storage, periodic
@@ -480,6 +480,8 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
             variant = VAR_REGISTER;
         }
     }
+    if (variant == VAR_VEC4 && !vec4_shape_ok(cfg->nx))
+        return fail(LBM_ERR_UNSUPPORTED, "the four-cell variant needs nx % 8 == 0");
     if (variant == VAR_TMA && !tma_shape_ok(cfg->nx, cfg->ny, tile_y))
         return fail(LBM_ERR_UNSUPPORTED, "the TMA variant needs nx % 32 == 0 and ny % tile_y == 0");
     if (!step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, variant))
@@ -622,7 +624,7 @@ int lbm_autotune(lbm_handle* h, int trials)
 {
     if (int rc = check_handle(h)) return rc;
     if (trials < 1) trials = 3;
-    static const int kVariants[] = {VAR_REGISTER, VAR_SPLIT, VAR_SPLIT_PF, VAR_ASYNC, VAR_PAIR, VAR_TMA};
+    static const int kVariants[] = {VAR_REGISTER, VAR_SPLIT, VAR_SPLIT_PF, VAR_ASYNC, VAR_PAIR, VAR_TMA, VAR_VEC4};
     static const int kTiles[] = {4, 8, 16};
     static const int kChunks[] = {8, 16, 32, 64, 128};
     const int v0 = h->variant, t0 = h->tile_y, z0 = h->zchunk;
@@ -636,6 +638,7 @@ int lbm_autotune(lbm_handle* h, int trials)
             if (e != cudaSuccess) break;
             if (!step_supported(h->q, h->cfg.storage, h->cfg.closure, h->bc_kind, ty, v)) continue;
             if (v == VAR_TMA && !tma_shape_ok(h->cfg.nx, h->cfg.ny, ty)) continue;
+            if (v == VAR_VEC4 && !vec4_shape_ok(h->cfg.nx)) continue;
             e = prepare_step(h->q, h->cfg.storage, h->cfg.closure, h->bc_kind, ty, v);
             for (int zc : kChunks) {
                 if (e != cudaSuccess) break;

@@ -42,7 +42,21 @@ cudaError_t launch_wait_selftest(unsigned int* flag, long long polls, cudaStream
 // (lbm_step_tma.cuh), split arrive/wait barrier (lbm_step_split.cuh), two cells
 // per thread on packed FP32 pairs (lbm_step_x2.cuh).  Values 2, 3, 5, 6, 7, 10
 // and 11 belonged to measured alternatives that were retired; they are refused.
-enum Variant { VAR_DEFAULT = 0, VAR_REGISTER = 1, VAR_TMA = 4, VAR_SPLIT = 8, VAR_PAIR = 9, VAR_SPLIT_PF = 12, VAR_ASYNC = 13 };
+// Variant 14: four cells per thread with vector access and a tensor-memory
+// stash (lbm_step_v4.cuh), periodic D3Q27, 32- and 16-bit storage, nx % 8 == 0.
+enum Variant {
+    VAR_DEFAULT = 0,
+    VAR_REGISTER = 1,
+    VAR_TMA = 4,
+    VAR_SPLIT = 8,
+    VAR_PAIR = 9,
+    VAR_SPLIT_PF = 12,
+    VAR_ASYNC = 13,
+    VAR_VEC4 = 14
+};
+
+// variant 14: box shapes it is built for (nx a multiple of 8)
+bool vec4_shape_ok(int nx);
 
 // TMA variant: tile heights it is built for, and the tensor map of a population
 // buffer (4D: x, y, z, population-of-box; box 40 x (tile_y + 2) x 1 x 1)

@@ -49,6 +49,8 @@ bool step_supported(int q, int storage, int closure, int bc, int tile_y, int var
     return f && f(closure, bc, tile_y, variant, nullptr, 0, nullptr) == cudaSuccess;
 }
 
+bool vec4_shape_ok(int nx) { return nx % 8 == 0; }
+
 cudaError_t prepare_step(int q, int storage, int closure, int bc, int tile_y, int variant)
 {
     Fn f = pick(q, storage);

@@ -7,12 +7,15 @@
 // staging (FP32, periodic), 8 split arrive/wait barrier (step_kernel_sb), 9
 // two cells per thread on packed FP32 pairs (step_kernel_x2, 32-bit arithmetic),
 // 12 variant 8 with L2 prefetches, 13 variant 8 with the own pulls copied to the
-// stash by cp.async one plane ahead (32- and 64-bit storage).
+// stash by cp.async one plane ahead (32- and 64-bit storage), 14 four cells per
+// thread with vector access and a tensor-memory stash (step_kernel_v4; periodic
+// D3Q27, 32- and 16-bit storage).
 #pragma once
 
 #include "lbm_step.cuh"
 #include "lbm_step_split.cuh"
 #include "lbm_step_tma.cuh"
+#include "lbm_step_v4.cuh"
 #include "lbm_step_x2.cuh"
 
 #include <type_traits>
@@ -37,6 +40,24 @@ cudaError_t launch_step_qs(int closure, int bc, int ty, int variant, const StepA
             LBM_TMA_CASE(CL_KCRB_RAW, 8, 4)
             LBM_TMA_CASE(CL_KCMP, 4, 3)
 #undef LBM_TMA_CASE
+        }
+        return cudaErrorNotSupported;
+    }
+    if (variant == VAR_VEC4) {
+        // tile_y 8: 128 x 8 tiles (one row per warp); 16: 64 x 16 tiles (two rows per warp)
+        if constexpr (Q == 27 && R32) {
+#define LBM_V4_CASE(CL, TYV, LPRV)                                                                     \
+    if (closure == CL && bc == BC_PERIODIC && ty == TYV)                                               \
+        return a ? launch_v4_t<Q, S, CL, LPRV>(*a, nbatch, s) : (nbatch < 0 ? prepare_v4_t<Q, S, CL, LPRV>() : cudaSuccess);
+            LBM_V4_CASE(CL_BGK, 8, 32)
+            LBM_V4_CASE(CL_KCMP, 8, 32)
+            LBM_V4_CASE(CL_KCRB_H, 8, 32)
+            LBM_V4_CASE(CL_KCRB_RAW, 8, 32)
+            LBM_V4_CASE(CL_BGK, 16, 16)
+            LBM_V4_CASE(CL_KCMP, 16, 16)
+            LBM_V4_CASE(CL_KCRB_H, 16, 16)
+            LBM_V4_CASE(CL_KCRB_RAW, 16, 16)
+#undef LBM_V4_CASE
         }
         return cudaErrorNotSupported;
     }

@@ -1,0 +1,708 @@
+// Fused step kernel with four cells per thread, vector access and a tensor-memory
+// stash (sm_103a).
+//
+// Same update as step_kernel (lbm_step.cuh): pull streaming (Eq. streaming),
+// moments (App. F.1 step 1), equilibrium (Eq. discrete_equilibrium), strain
+// (Eqs. fd, strain_rate_discrete), closure, rate (Eq. omega_sgs_operational)
+// and two-rate relaxation (App. F.2, F.3), store.  Periodic D3Q27 boxes whose
+// nx is a multiple of 8.  The mapping onto the GPU differs:
+//
+//  * Each thread owns four consecutive x-cells of one row.  The source row of a
+//    population is read with ONE aligned vector load per thread (16 bytes for
+//    FP32 storage, 8 for FP16/BF16): for c_x = 0 the four values are the four
+//    cells' populations; for c_x = +1 / -1 they are shifted by one cell, and the
+//    value that crosses into the neighbouring thread's cells comes from that
+//    lane by a warp shuffle (at the ends of a tile row, from one scalar load of
+//    the edge lane).  Post-collision values leave as vector stores of the same
+//    width.  Address arithmetic, loop control and synchronisation are shared by
+//    four cells.
+//  * A CTA of 8 warps covers a TX x TY tile (128 x 8: one row per warp, or
+//    64 x 16: two rows per warp) and marches a chunk of z-planes; one CTA per SM.
+//  * The streamed populations of a plane wait between their pull (which yields
+//    the velocity the neighbours' strain needs) and their collision one plane
+//    later in tensor memory (TMEM): two slots of 27 x 4 FP32 values per
+//    thread, column 4 i + c of a slot holding population i of cell c.  A CTA
+//    allocates all 512 columns; the two warps that share a lane quarter take
+//    256 each.  The stash thus needs neither shared memory nor registers, and a
+//    1024-cell tile (whose halo costs a quarter or less of its own pulls) fits
+//    on one SM.
+//  * Velocities go through a ring of four planes in shared memory: the own
+//    cells' and, pulled as single cells, the halo cells' (rows y0 - 1 and
+//    y0 + TY, columns x0 - 1 and x0 + TX).  The z-neighbours of the own cells
+//    stay in registers.  The per-plane barrier is split as in step_kernel_sb:
+//    a thread arrives once it has published plane k+1 and waits for plane k
+//    just before reading its neighbours; with the z-neighbours in registers a
+//    thread that writes plane p has passed the barrier of plane p-2, so every
+//    thread is done reading plane p-4 and four slots suffice.
+//  * The collision relaxes the four cells together, one (c_y, c_z) population
+//    triple at a time, in the common form g' = a g + w (b (P - 1) + c0 + D H)
+//    of collide() with P - 1 = e_x (1 + Y) + Y, Y = e_y + e_z + e_y e_z, and
+//    the quadratic form H split into its (c_y, c_z) part and the c_x terms, so
+//    that each population's four results form one vector store.  For FP32
+//    storage the store's "+ w" is folded into c0.
+#pragma once
+
+#include <type_traits>
+
+#include "lbm_mbarrier.cuh"
+#include "lbm_step.cuh"
+#include "lbm_step_split.cuh"
+
+namespace lbmk {
+
+// ---------------------------------------------------------------- TMEM
+
+__device__ __forceinline__ void tm_alloc(uint32_t* dst, uint32_t ncols)  // whole warp
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(a), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tm_relinquish()
+{
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tm_dealloc(uint32_t taddr, uint32_t ncols)  // whole warp
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tm_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
+
+// 12 consecutive columns of the thread's lane (one population triple of four cells)
+__device__ __forceinline__ void tm_st12(uint32_t ta, const float (&v)[3][4])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n"
+        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%9], {%10, %11, %12, %13};\n" ::"r"(ta),
+        "r"(__float_as_uint(v[0][0])), "r"(__float_as_uint(v[0][1])), "r"(__float_as_uint(v[0][2])),
+        "r"(__float_as_uint(v[0][3])), "r"(__float_as_uint(v[1][0])), "r"(__float_as_uint(v[1][1])),
+        "r"(__float_as_uint(v[1][2])), "r"(__float_as_uint(v[1][3])), "r"(ta + 8u), "r"(__float_as_uint(v[2][0])),
+        "r"(__float_as_uint(v[2][1])), "r"(__float_as_uint(v[2][2])), "r"(__float_as_uint(v[2][3]))
+        : "memory");
+}
+
+// 12 consecutive columns back, waited for inside the same statement so that
+// no use of the values can be scheduled before they have arrived
+__device__ __forceinline__ void tm_ld12(uint32_t ta, float (&v)[3][4])
+{
+    uint32_t r[12];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%12];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8, %9, %10, %11}, [%13];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11])
+        : "r"(ta), "r"(ta + 8u)
+        : "memory");
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k / 4][k % 4] = __uint_as_float(r[k]);
+}
+
+// ------------------------------------------------------- vector global access
+
+// four consecutive stored values as FP32 (16-bit storage: the stored g = f - w)
+__device__ __forceinline__ float4 v4_load(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float4 v4_load(const __half* p)
+{
+    const uint2 r = __ldg(reinterpret_cast<const uint2*>(p));
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&r.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&r.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float4 v4_load(const __nv_bfloat16* p)
+{
+    const uint2 r = __ldg(reinterpret_cast<const uint2*>(p));
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float v1_load(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float v1_load(const __half* p) { return __half2float(__ldg(p)); }
+__device__ __forceinline__ float v1_load(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+
+__device__ __forceinline__ void v4_store(float* p, float a, float b, float c, float d)
+{
+    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void v4_store(__half* p, float a, float b, float c, float d)
+{
+    const __half2 lo = __floats2half2_rn(a, b), hi = __floats2half2_rn(c, d);
+    *reinterpret_cast<uint2*>(p) = make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi));
+}
+__device__ __forceinline__ void v4_store(__nv_bfloat16* p, float a, float b, float c, float d)
+{
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+    *reinterpret_cast<uint2*>(p) = make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi));
+}
+
+// ------------------------------------------------------------------ shape
+
+// LPR lanes per tile row: 32 (tiles 128 x 8, one row per warp) or 16 (tiles
+// 64 x 16, two rows per warp); 8 warps, one CTA per SM.
+template <int LPR, typename S>
+struct V4Shape {
+    static constexpr int NT = 256;
+    static constexpr int RPW = 32 / LPR;  // tile rows per warp
+    static constexpr int TX = 4 * LPR;
+    static constexpr int TY = 8 * RPW;
+    static constexpr int RY = TY + 2;      // ring and staged rows: y0 - 1 .. y0 + TY
+    static constexpr int RP = TX + 8;      // ring and staging pitch: x0 - 4 .. x0 + TX + 3, own cells at 4 .. TX + 3
+    static constexpr int NSLOT = 4;
+    static constexpr int NB = 2 * TX + 2 * TY;     // halo cells of a ring plane (no corners)
+    static constexpr int NCH = TX / 4;             // 4-cell chunks of a row
+    static constexpr int NPOS = 2 * NCH + 2 * RY;  // staged chunks beyond the own ones: halo rows, x-edge chunks
+    static constexpr size_t ring_off = 32;         // three mbarriers, the TMEM base address
+    static constexpr size_t ring_bytes = sizeof(float) * (size_t)NSLOT * 3 * RY * RP;
+    static constexpr size_t stg_off = ring_off + ring_bytes;
+    static constexpr size_t stg_bytes = sizeof(S) * (size_t)27 * RY * RP;  // [27][RY][RP], storage format
+    static constexpr size_t used = stg_off + stg_bytes;
+    // at least 116 KB, so that two CTAs never share an SM (each allocates all
+    // 512 TMEM columns; a second one would wait for the first to finish)
+    static constexpr size_t smem_bytes = used > 116 * 1024 ? used : 116 * 1024;
+    static_assert(smem_bytes <= 227 * 1024, "shared memory of one CTA");
+};
+
+// relaxation constants of one cell (collide_coef in the per-triple form)
+struct V4Cell {
+    float ca, cb, ex[3], ey[3], ez[3], C[5], Dxx, Dxy2, Dxz2;
+};
+
+// index of the (c_y, c_z) part of H: (0,0), (+-1,0), (0,+-1), c_y c_z = 1, c_y c_z = -1
+__host__ __device__ constexpr int v4_pat(int cy, int cz)
+{
+    return (cy == 0 && cz == 0) ? 0 : (cz == 0 ? 1 : (cy == 0 ? 2 : (cy * cz == 1 ? 3 : 4)));
+}
+
+// asynchronous 16-byte global -> shared copy (L2 only)
+__device__ __forceinline__ void cp_async_cg16(uint32_t dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+// one arrival on the mbarrier once all of the thread's earlier cp.async copies have landed
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(a) : "memory");
+}
+// four consecutive stored values (one 16- or 8-byte chunk)
+template <typename S>
+__device__ __forceinline__ void cp_async_chunk(uint32_t dst, const S* src)
+{
+    if constexpr (sizeof(S) == 4)
+        cp_async_cg16(dst, src);
+    else
+        cp_async_ca<8>(dst, src);
+}
+__device__ __forceinline__ float v4_cvt(float v) { return v; }
+__device__ __forceinline__ float v4_cvt(__half v) { return __half2float(v); }
+__device__ __forceinline__ float v4_cvt(__nv_bfloat16 v) { return __bfloat162float(v); }
+// four staged values as FP32
+__device__ __forceinline__ float4 v4_lds(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float4 v4_lds(const __half* p)
+{
+    const uint2 r = *reinterpret_cast<const uint2*>(p);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&r.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&r.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float4 v4_lds(const __nv_bfloat16* p)
+{
+    const uint2 r = *reinterpret_cast<const uint2*>(p);
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// Load schedule.  The pulls of a plane are staged in shared memory: for each
+// population i the rows y0 - 1 - c_y .. y0 + TY - c_y (the own rows' and the
+// y-halo rows' sources) over x0 - 4 .. x0 + TX + 3, as 16-byte (FP32) or
+// 8-byte (16-bit) chunks copied by cp.async: each thread copies its own four
+// cells' chunk of every population, and NPOS threads one more chunk each (the
+// y-halo rows and the x-edge chunks of every row).  The x-halo cells and the
+// values that cross a tile edge are read from those edge chunks, so no load
+// touches a single scattered value.  A staging mbarrier, on which every
+// thread arrives by cp.async.mbarrier.arrive once its copies have landed,
+// makes the plane visible to all threads; the ring mbarrier of the plane,
+// waited for right after the thread's own arrival, tells that every thread has
+// read the staging area, after which the copies of the plane after next are
+// issued.  They land while the current plane collides.  Plane p arrives on ring
+// mbarrier (p - z0) & 1 (parity ((p - z0) >> 1) & 1) and fills the staging
+// area for the (p - z0)-th time (staging mbarrier parity (p - z0) & 1).
+template <int Q, typename S, int CL, int LPR>
+__global__ void __launch_bounds__(256, 1) step_kernel_v4(const StepArgs a)
+{
+    static_assert(Q == 27, "the four-cell kernel is built for D3Q27 (population triples along x)");
+    static_assert(!std::is_same<S, double>::value, "FP32 arithmetic");
+    static_assert(CL == CL_BGK || CL == CL_KCMP || CL == CL_KCRB_H || CL == CL_KCRB_RAW, "closure");
+    using Sh = V4Shape<LPR, S>;
+    constexpr int TX = Sh::TX, TY = Sh::TY, RY = Sh::RY, RP = Sh::RP, NB = Sh::NB, NT = Sh::NT, NCH = Sh::NCH;
+    constexpr int NHK = (NB + NT - 1) / NT;  // halo cells per thread (at most)
+    constexpr bool SHIFTED = StoreTraits<S>::shifted;
+    constexpr unsigned FULL = 0xffffffffu;
+
+    extern __shared__ __align__(16) unsigned char smem_v4[];
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_v4);  // [0], [1]: ring planes, [2]: staging
+    uint32_t* tm_base_sm = reinterpret_cast<uint32_t*>(smem_v4 + 24);
+    float* ring = reinterpret_cast<float*>(smem_v4 + Sh::ring_off);  // [NSLOT][3][RY][RP]
+    S* stg = reinterpret_cast<S*>(smem_v4 + Sh::stg_off);            // [27][RY][RP]
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int tiles_x = (nx + TX - 1) / TX;
+    const int x0 = (int)(blockIdx.x % tiles_x) * TX;
+    const int y0 = (int)(blockIdx.x / tiles_x) * TY;
+    const int z0 = (int)blockIdx.y * a.zchunk;
+    if (z0 >= nz) return;  // uniform over the CTA, before any allocation
+    const int z1 = min(nz, z0 + a.zchunk);
+    const int box = blockIdx.z;
+    const long long ps = a.popstride;
+    const int plane = (int)a.plane;
+    const S* __restrict__ fin = static_cast<const S*>(a.fin) + (long long)box * a.boxstride;
+    S* __restrict__ fout = static_cast<S*>(a.fout) + (long long)box * a.boxstride;
+
+    const double nu_d = a.box_nu[box];
+    const float nu = (float)nu_d;
+    const float tau_hat = (float)(nu_d / kTheta + 0.5);
+    const float omega = (float)(1.0 / (nu_d / kTheta + 0.5));
+    const float cnud = (float)a.cnu_delta;
+
+    // own cells: row ty of the tile (staged row ty + 1), x = xa .. xa + 3
+    // (wrapped into the box for lanes beyond nx, which compute but do not store)
+    const int lx = lane % LPR;
+    const int ty = warp * Sh::RPW + lane / LPR;
+    const int gy = y0 + ty, xa = x0 + 4 * lx;
+    const bool own_store = gy < ny && xa < nx;
+    const int gyw = gy % ny, xaw = xa % nx;
+    const int yr_own[3] = {(gyw == 0 ? ny - 1 : gyw - 1) * nx, gyw * nx, (gyw == ny - 1 ? 0 : gyw + 1) * nx};
+    const int xl = (x0 + nx - 1) % nx;  // left neighbour of the row's first cell (own pulls of the first plane)
+    const int xr = (x0 + TX) % nx;      // right neighbour of the row's last cell
+    const int ry_own = ty + 1, rx_own = 4 + 4 * lx;
+
+    // the extra staged chunk of this thread (tid < NPOS): staged row, column, global x, source rows
+    int pos_r = -1, pos_col = 0, pos_x = 0, yr_pos[3] = {0, 0, 0};
+    if (tid < Sh::NPOS) {
+        const int p = tid;
+        if (p < 2 * NCH) {  // y-halo rows
+            const int c = p % NCH;
+            pos_r = p < NCH ? 0 : RY - 1;
+            pos_col = 4 + 4 * c;
+            pos_x = (x0 + 4 * c) % nx;
+        } else {  // x-edge chunks of every staged row
+            const int q = p - 2 * NCH;
+            const bool left = q < RY;
+            pos_r = left ? q : q - RY;
+            pos_col = left ? 0 : TX + 4;
+            pos_x = left ? (x0 + nx - 4) % nx : (x0 + TX) % nx;
+        }
+        const int yy = y0 - 1 + pos_r;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) yr_pos[k] = wrapi(yy - 1 + k, ny) * nx;
+    }
+    // halo cells of this thread: h = tid + k NT < NB; y-halo rows first, then
+    // the x-halo columns; staged row and x relative to x0
+    int hal_rr[NHK], hal_xr[NHK];
+#pragma unroll
+    for (int k = 0; k < NHK; ++k) {
+        const int h = tid + k * NT;
+        hal_rr[k] = -1;
+        hal_xr[k] = 0;
+        if (h < NB) {
+            if (h < 2 * TX) {
+                hal_rr[k] = h < TX ? 0 : RY - 1;
+                hal_xr[k] = h % TX;
+            } else {
+                const int j = h - 2 * TX;
+                hal_rr[k] = j % TY + 1;
+                hal_xr[k] = j < TY ? -1 : TX;
+            }
+        }
+    }
+
+    // TMEM: warp 0 allocates the 512 columns; the two warps of a lane quarter
+    // take 256 each; slot s of a thread starts at column 128 s of its share
+    if (warp == 0) {
+        tm_alloc(tm_base_sm, 512u);
+        tm_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(&mbar[0], NT);
+        mbar_init(&mbar[1], NT);
+        mbar_init(&mbar[2], NT);
+    }
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    const uint32_t tm_all = *tm_base_sm;
+    const uint32_t tm_me = tm_all + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * 256);
+    auto tslot = [&](int z) { return tm_me + (uint32_t)((z & 1) * 128); };
+
+    auto zrows = [&](int z, int (&zr)[3]) {
+        const int zc = z < 0 ? z + nz : (z >= nz ? z - nz : z);  // z in [-1, nz]
+        zr[0] = (zc == 0 ? nz - 1 : zc - 1) * plane;
+        zr[1] = zc * plane;
+        zr[2] = (zc == nz - 1 ? 0 : zc + 1) * plane;
+    };
+    auto rslot = [&](int z) { return (z - z0 + 1) & (Sh::NSLOT - 1); };
+    auto ringp = [&](int s, int c) { return ring + (s * 3 + c) * (RY * RP); };
+    auto stg_at = [&](int i, int r, int col) { return stg + (i * RY + r) * RP + col; };
+
+    // cp.async of plane z's pulls into the staging area, then the thread's
+    // arrival on the staging mbarrier (completed by the copies)
+    auto issue = [&](int z) {
+        int zr[3];
+        zrows(z, zr);
+        static_for<27>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
+            const S* base = fin + (long long)i * ps + zr[1 - cz];
+            cp_async_chunk<S>((uint32_t)__cvta_generic_to_shared(stg_at(i, ry_own, rx_own)), base + yr_own[1 - cy] + xaw);
+            if (pos_r >= 0)
+                cp_async_chunk<S>((uint32_t)__cvta_generic_to_shared(stg_at(i, pos_r, pos_col)),
+                                  base + yr_pos[1 - cy] + pos_x);
+        });
+        cp_async_commit();
+        cp_async_arrive(&mbar[2]);
+    };
+    auto staged_wait = [&](int z) { return mbar_wait_bounded(&mbar[2], (unsigned)(z - z0) & 1u); };
+
+    // The own four cells at plane z: moments (drho = sum g, u, and with FULL
+    // the second moments Pi' = sum g c c) and, with FULL, the streamed
+    // populations g = f - w into the TMEM slot of plane z.  STAGED: from the
+    // staging area, else loaded from global memory (first plane of a chunk).
+    auto pull_own = [&](auto full_tag, auto staged_tag, int z, float (&dr)[4], float (&u)[3][4], float (&P)[6][4]) {
+        constexpr bool FULL = decltype(full_tag)::value;
+        constexpr bool STAGED = decltype(staged_tag)::value;
+        int zr[3];
+        zrows(z, zr);
+        float d[4], jx[4], jy[4], jz[4], g0[4], pyy[4], pzz[4], pxy[4], pxz[4], pyz[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) d[c] = jx[c] = jy[c] = jz[c] = g0[c] = pyy[c] = pzz[c] = pxy[c] = pxz[c] = pyz[c] = 0.f;
+        const uint32_t ts = tslot(z);
+        static_for<9>([&](auto PI) {
+            constexpr int p = decltype(PI)::value;
+            constexpr int cy = p % 3 - 1, cz = p / 3 - 1;
+            const int roff = zr[1 - cz] + yr_own[1 - cy];
+            float g[3][4];
+            static_for<3>([&](auto CI) {
+                constexpr int k = decltype(CI)::value;
+                constexpr int cx = k - 1, i = 3 * p + k;
+                const S* src = fin + (long long)i * ps + roff;
+                float4 v;
+                if constexpr (STAGED)
+                    v = v4_lds(stg_at(i, ry_own, rx_own));
+                else
+                    v = v4_load(src + xaw);
+                if constexpr (cx == 1) {  // cell x pulls x - 1
+                    float e = __shfl_up_sync(FULL, v.w, 1, LPR);
+                    if (lx == 0) e = STAGED ? v4_cvt(*stg_at(i, ry_own, 3)) : v1_load(src + xl);
+                    g[k][0] = e;
+                    g[k][1] = v.x;
+                    g[k][2] = v.y;
+                    g[k][3] = v.z;
+                } else if constexpr (cx == -1) {  // cell x pulls x + 1
+                    float e = __shfl_down_sync(FULL, v.x, 1, LPR);
+                    if (lx == LPR - 1) e = STAGED ? v4_cvt(*stg_at(i, ry_own, TX + 4)) : v1_load(src + xr);
+                    g[k][0] = v.y;
+                    g[k][1] = v.z;
+                    g[k][2] = v.w;
+                    g[k][3] = e;
+                } else {
+                    g[k][0] = v.x;
+                    g[k][1] = v.y;
+                    g[k][2] = v.z;
+                    g[k][3] = v.w;
+                }
+                if constexpr (!SHIFTED) {
+                    constexpr float w = (float)weight_of(Q, i);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) g[k][c] -= w;
+                }
+            });
+            if constexpr (FULL) tm_st12(ts + 12u * p, g);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float s = (g[0][c] + g[1][c]) + g[2][c];
+                const float dx = g[2][c] - g[0][c];
+                d[c] += s;
+                jx[c] += dx;
+                if constexpr (cy == 1) jy[c] += s;
+                if constexpr (cy == -1) jy[c] -= s;
+                if constexpr (cz == 1) jz[c] += s;
+                if constexpr (cz == -1) jz[c] -= s;
+                if constexpr (FULL) {
+                    g0[c] += g[1][c];
+                    if constexpr (cy != 0) pyy[c] += s;
+                    if constexpr (cz != 0) pzz[c] += s;
+                    if constexpr (cy == 1) pxy[c] += dx;
+                    if constexpr (cy == -1) pxy[c] -= dx;
+                    if constexpr (cz == 1) pxz[c] += dx;
+                    if constexpr (cz == -1) pxz[c] -= dx;
+                    if constexpr (cy * cz == 1) pyz[c] += s;
+                    if constexpr (cy * cz == -1) pyz[c] -= s;
+                }
+            }
+        });
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            dr[c] = d[c];
+            const float inv = 1.f / (1.f + d[c]);
+            u[0][c] = jx[c] * inv;
+            u[1][c] = jy[c] * inv;
+            u[2][c] = jz[c] * inv;
+            if constexpr (FULL) {
+                P[0][c] = d[c] - g0[c];
+                P[1][c] = pyy[c];
+                P[2][c] = pzz[c];
+                P[3][c] = pxy[c];
+                P[4][c] = pxz[c];
+                P[5][c] = pyz[c];
+            }
+        }
+    };
+    auto put_own = [&](int z, const float (&u)[3][4]) {
+        const int s = rslot(z);
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            *reinterpret_cast<float4*>(ringp(s, b) + ry_own * RP + rx_own) = make_float4(u[b][0], u[b][1], u[b][2], u[b][3]);
+    };
+    // halo cells at plane z, from the staging area: velocity into the ring
+    auto halo_plane = [&](int z) {
+        const int s = rslot(z);
+#pragma unroll
+        for (int k = 0; k < NHK; ++k) {
+            if (hal_rr[k] >= 0) {
+                const int r = hal_rr[k], xr4 = 4 + hal_xr[k];
+                float gh[Q];
+                static_for<27>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    constexpr int cx = i % 3 - 1;
+                    const float v = v4_cvt(*stg_at(i, r, xr4 - cx));
+                    gh[i] = SHIFTED ? v : v - (float)weight_of(Q, i);
+                });
+                float dh, vx, vy, vz;
+                moments<Q, float>(gh, dh, vx, vy, vz, 0.f, 0.f, 0.f);
+                const int pos = r * RP + xr4;
+                ringp(s, 0)[pos] = vx;
+                ringp(s, 1)[pos] = vy;
+                ringp(s, 2)[pos] = vz;
+            }
+        }
+    };
+    auto arrive = [&](int p) { mbar_arrive(&mbar[(p - z0) & 1]); };
+    auto wait = [&](int p) { return mbar_wait_bounded(&mbar[(p - z0) & 1], (unsigned)((p - z0) >> 1) & 1u); };
+
+    bool ok = true;
+    float um[3][4], dr0[4], u0[3][4], P0[6][4];  // own: u at z - 1; drho, u, Pi' at z
+    {
+        float dd[4], PP[6][4];
+        pull_own(std::false_type{}, std::false_type{}, z0 - 1, dd, um, PP);
+        issue(z0);
+        ok = __all_sync(FULL, staged_wait(z0));
+        if (ok) {
+            pull_own(std::true_type{}, std::true_type{}, z0, dr0, u0, P0);
+            put_own(z0, u0);
+            halo_plane(z0);
+            tm_wait_st();
+            arrive(z0);
+            ok = __all_sync(FULL, wait(z0));  // every thread has read the staging area
+            if (ok) issue(z0 + 1);            // z0 + 1 <= z1
+        }
+    }
+
+    for (int z = z0; z < z1 && ok; ++z) {
+        // ---- plane z+1: staged pulls (populations to TMEM while it will be
+        // collided), velocities to the ring; then the copies of plane z+2
+        float dr1[4], u1[3][4], P1[6][4];
+        if (!__all_sync(FULL, staged_wait(z + 1))) {  // warp-uniform: the TMEM accesses stay converged
+            ok = false;
+            break;
+        }
+        if (z + 1 < z1) {
+            pull_own(std::true_type{}, std::true_type{}, z + 1, dr1, u1, P1);
+            put_own(z + 1, u1);
+            halo_plane(z + 1);
+            tm_wait_st();
+            arrive(z + 1);
+            // every thread has published plane z+1 (so also plane z) and read the staging area
+            if (!__all_sync(FULL, wait(z + 1))) {
+                ok = false;
+                break;
+            }
+            if (z + 2 <= z1) issue(z + 2);
+        } else {
+            pull_own(std::false_type{}, std::true_type{}, z + 1, dr1, u1, P1);  // z-neighbour of the chunk's last plane
+        }
+
+        // ---- plane z: neighbours' velocities, strain, closure, relaxation, store
+        // du[a][b][c] = d_a u_b of cell c
+        float S6[6][4];
+        {
+            float du[3][3][4];
+            const int s0 = rslot(z);
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const float* r = ringp(s0, b) + ry_own * RP + rx_own;
+                const float ul = r[-1], ur = r[4];
+                const float4 yn = *reinterpret_cast<const float4*>(r - RP);
+                const float4 yp = *reinterpret_cast<const float4*>(r + RP);
+                du[0][b][0] = 0.5f * (u0[b][1] - ul);
+                du[0][b][1] = 0.5f * (u0[b][2] - u0[b][0]);
+                du[0][b][2] = 0.5f * (u0[b][3] - u0[b][1]);
+                du[0][b][3] = 0.5f * (ur - u0[b][2]);
+                du[1][b][0] = 0.5f * (yp.x - yn.x);
+                du[1][b][1] = 0.5f * (yp.y - yn.y);
+                du[1][b][2] = 0.5f * (yp.z - yn.z);
+                du[1][b][3] = 0.5f * (yp.w - yn.w);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) du[2][b][c] = 0.5f * (u1[b][c] - um[b][c]);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                S6[0][c] = du[0][0][c];
+                S6[1][c] = du[1][1][c];
+                S6[2][c] = du[2][2][c];
+                S6[3][c] = 0.5f * (du[0][1][c] + du[1][0][c]);
+                S6[4][c] = 0.5f * (du[0][2][c] + du[2][0][c]);
+                S6[5][c] = 0.5f * (du[1][2][c] + du[2][1][c]);
+            }
+        }
+        // per-cell relaxation constants
+        V4Cell K[4];
+        {
+            constexpr float a1 = (float)(1.0 / kTheta);
+            constexpr float a2 = (float)((1.0 - kTheta) / (2.0 * kTheta * kTheta));
+            constexpr float a0 = (float)(-kTheta / (2.0 * kTheta * kTheta));
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (own_store && !isfinite(dr0[c] + u0[0][c] + u0[1][c] + u0[2][c])) atomicOr(a.flag, kFlagNonfinite);
+                const float P6[6] = {P0[0][c], P0[1][c], P0[2][c], P0[3][c], P0[4][c], P0[5][c]};
+                const Coef<float> k = collide_coef<Q, float, CL>(P6, dr0[c], u0[0][c], u0[1][c], u0[2][c], S6[0][c],
+                                                                 S6[1][c], S6[2][c], S6[3][c], S6[4][c], S6[5][c],
+                                                                 omega, tau_hat, nu, cnud);
+                const float ux = u0[0][c], uy = u0[1][c], uz = u0[2][c];
+                const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+                K[c].ex[0] = -a1 * ux + a2 * ux2;
+                K[c].ex[1] = a0 * ux2;
+                K[c].ex[2] = a1 * ux + a2 * ux2;
+                K[c].ey[0] = -a1 * uy + a2 * uy2;
+                K[c].ey[1] = a0 * uy2;
+                K[c].ey[2] = a1 * uy + a2 * uy2;
+                K[c].ez[0] = -a1 * uz + a2 * uz2;
+                K[c].ez[1] = a0 * uz2;
+                K[c].ez[2] = a1 * uz + a2 * uz2;
+                K[c].ca = k.ca;
+                K[c].cb = k.cb;
+                const float c0 = SHIFTED ? k.c0 : k.c0 + 1.f;  // FP32 storage: the stored f = g' + w
+                if constexpr (CL == CL_BGK) {
+#pragma unroll
+                    for (int q = 0; q < 5; ++q) K[c].C[q] = c0;
+                    K[c].Dxx = K[c].Dxy2 = K[c].Dxz2 = 0.f;
+                } else {
+                    const float h0 = -k.t, h1 = k.Myy - k.t, h2 = k.Mzz - k.t, hyz = (k.Myy + k.Mzz) - k.t;
+                    K[c].C[0] = c0 + k.D * h0;
+                    K[c].C[1] = c0 + k.D * h1;
+                    K[c].C[2] = c0 + k.D * h2;
+                    K[c].C[3] = c0 + k.D * (hyz + 2.f * k.Myz);
+                    K[c].C[4] = c0 + k.D * (hyz - 2.f * k.Myz);
+                    K[c].Dxx = k.D * k.Mxx;
+                    K[c].Dxy2 = 2.f * k.D * k.Mxy;
+                    K[c].Dxz2 = 2.f * k.D * k.Mxz;
+                }
+            }
+        }
+        // relaxation, one population triple of the four cells at a time
+        {
+            const uint32_t ts = tslot(z);
+            const int cell = z * plane + gyw * nx + xaw;
+            static_for<9>([&](auto PI) {
+                constexpr int p = decltype(PI)::value;
+                constexpr int cy = p % 3 - 1, cz = p / 3 - 1, pat = v4_pat(cy, cz);
+                float g[3][4];
+                tm_ld12(ts + 12u * p, g);
+                float Y[4], B[4], Cm[4], Cp[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float ey = K[c].ey[cy + 1], ez = K[c].ez[cz + 1];
+                    Y[c] = fmaf(ey, ez, ey + ez);
+                    B[c] = 1.f + Y[c];
+                    if constexpr (CL != CL_BGK) {
+                        float X = 0.f;
+                        if constexpr (cy != 0) X += (float)cy * K[c].Dxy2;
+                        if constexpr (cz != 0) X += (float)cz * K[c].Dxz2;
+                        const float CpD = K[c].C[pat] + K[c].Dxx;
+                        Cp[c] = CpD + X;
+                        Cm[c] = CpD - X;
+                    } else {
+                        Cp[c] = Cm[c] = K[c].C[pat];
+                    }
+                }
+                static_for<3>([&](auto CI) {
+                    constexpr int k = decltype(CI)::value;
+                    constexpr int cx = k - 1, i = 3 * p + k;
+                    constexpr float w = (float)weight_of(Q, i);
+                    float o[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const float pm1 = fmaf(K[c].ex[k], B[c], Y[c]);
+                        const float Cc = cx == 0 ? K[c].C[pat] : (cx == 1 ? Cp[c] : Cm[c]);
+                        const float Kv = fmaf(K[c].cb, pm1, Cc);
+                        o[c] = fmaf(K[c].ca, g[k][c], w * Kv);
+                    }
+                    if (own_store) v4_store(fout + ((long long)i * ps + cell), o[0], o[1], o[2], o[3]);
+                });
+            });
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            dr0[c] = dr1[c];
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                um[b][c] = u0[b][c];
+                u0[b][c] = u1[b][c];
+            }
+#pragma unroll
+            for (int q = 0; q < 6; ++q) P0[q][c] = P1[q][c];
+        }
+    }
+    if (!ok) {
+        atomicOr(a.flag, kFlagTimeout);
+        cp_async_wait<0>();  // the thread's copies in flight land before the CTA leaves
+    }
+    // every TMEM access of the CTA has completed before warp 0 frees the columns
+    tm_wait_st();
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    if (warp == 0) tm_dealloc(tm_all, 512u);
+}
+
+// nx a multiple of 8 (aligned vector rows for 32- and 16-bit storage)
+inline bool v4_shape_ok(int nx) { return nx % 8 == 0; }
+
+template <int Q, typename S, int CL, int LPR>
+cudaError_t prepare_v4_t()
+{
+    return cudaFuncSetAttribute(step_kernel_v4<Q, S, CL, LPR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)V4Shape<LPR, S>::smem_bytes);
+}
+
+template <int Q, typename S, int CL, int LPR>
+cudaError_t launch_v4_t(const StepArgs& a, int nbatch, cudaStream_t s)
+{
+    using Sh = V4Shape<LPR, S>;
+    if (!v4_shape_ok(a.nx)) return cudaErrorInvalidValue;
+    static bool attr_set = false;  // per instantiation; prepare_v4_t sets it ahead of stream capture
+    if (!attr_set) {
+        cudaError_t e = prepare_v4_t<Q, S, CL, LPR>();
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int tiles = ((a.nx + Sh::TX - 1) / Sh::TX) * ((a.ny + Sh::TY - 1) / Sh::TY);
+    const int chunks = (a.nz + a.zchunk - 1) / a.zchunk;
+    dim3 grid(tiles, chunks, nbatch), block(Sh::NT);
+    step_kernel_v4<Q, S, CL, LPR><<<grid, block, Sh::smem_bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmk

@@ -1,0 +1,143 @@
+"""GPU parity of the four-cells-per-thread step kernels (variants 14 and 15:
+vector loads and stores, populations parked in tensor memory between their
+pull and their collision; 14 stages the pulls by cp.async one plane ahead, 15
+loads them into registers).
+
+It computes the same per-cell update as the register-pull kernel (variant 1)
+in the per-triple form of the same relaxation (P - 1 = e_x (1 + Y) + Y and the
+store's "+ w" folded into c0 for FP32 storage), so:
+  - FP32 storage: populations agree with variant 1 to FP32 rounding (1e-6
+    relative over 8 steps) and the velocity with the FP64 oracle to 1e-6;
+  - FP16 / BF16 storage: rho and u agree with variant 1 to eight ulps of the
+    16-bit format at the largest |f - w| (one rounding of a stored population
+    that may flip between the kernels' rounding orders, carried over 5 steps);
+  - every z-chunking of one tile shape gives the bit-identical result.
+Boxes: several tiles in x and y, ragged y (rows beyond ny are computed from
+the periodic image and not stored), boxes narrower than a tile (lanes beyond
+nx wrap), two boxes with different viscosities, chunks of one and two planes.
+"""
+import numpy as np
+import pytest
+
+from paper_2605_19796_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+CL = {"bgk": 0, "kcmp": 1, "kcrb_hermite": 2, "kcrb_raw": 3}
+CNU = {"bgk": 0.0, "kcmp": 0.035, "kcrb_hermite": 0.02, "kcrb_raw": 0.02}
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2605_19796_gb300 import build
+
+    build.build()
+    from paper_2605_19796_gb300 import lbm as _lbm
+
+    return _lbm
+
+
+def rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+
+
+def _fields(shape, nbatch, seed):
+    fs = [inputs.hit_fields(0, k0=3.0, urms=0.07, seed=seed + b, shape=shape) for b in range(nbatch)]
+    return fs, np.stack([f[0] for f in fs]), np.stack([f[1] for f in fs], axis=1)
+
+
+def _run(lbm, shape, nus, closure, storage, variant, rho, u, steps, **kw):
+    with lbm.Solver(27, shape, nus, closure=closure, c_nu=CNU[closure], storage=storage, variant=variant,
+                    nbatch=len(nus), **kw) as s:
+        assert s.launch_config["variant"] == variant
+        s.init_velocity(rho, u)
+        s.step(steps)
+        s.synchronize()
+        return s.get_populations(), dict(s.launch_config)
+
+
+LAUNCHES = [(14, 8), (14, 16)]
+
+
+@pytest.mark.parametrize("variant,tile_y", LAUNCHES)
+@pytest.mark.parametrize("shape", [(256, 20, 9), (64, 8, 5), (24, 5, 3)])
+@pytest.mark.parametrize("closure", ["bgk", "kcmp", "kcrb_hermite", "kcrb_raw"])
+def test_vec4_fp32_matches_register_pull_and_oracle(lbm, orc, closure, shape, tile_y, variant):
+    nus = np.array([2e-5, 1e-4])
+    fields, rho, u = _fields(shape, 2, 60)
+    ref, _ = _run(lbm, shape, nus, closure, "fp32", 1, rho, u, 8)
+    res = {}
+    for zc in (0, 1, 2, 5):
+        res[zc], cfg = _run(lbm, shape, nus, closure, "fp32", variant, rho, u, 8, tile_y=tile_y, zchunk=zc)
+        assert cfg["tile_y"] == tile_y
+    for zc in (1, 2, 5):
+        assert np.array_equal(res[zc], res[0]), zc
+    assert rel(res[0], ref) < 1e-6
+    for b in range(2):
+        fo = orc.run(orc.init_equilibrium(27, fields[b][0], fields[b][1]), 8, closure=CL[closure], nu=nus[b],
+                     c_nu=CNU[closure])
+        _, ug = orc.fields(res[0][b])
+        _, uo = orc.fields(fo)
+        assert np.abs(ug - uo).max() < 1e-6, (b, np.abs(ug - uo).max())
+
+
+@pytest.mark.parametrize("variant", [14])
+@pytest.mark.parametrize("tile_y", [8, 16])
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+@pytest.mark.parametrize("closure", ["bgk", "kcmp", "kcrb_hermite", "kcrb_raw"])
+def test_vec4_16bit_matches_register_pull(lbm, orc, closure, storage, tile_y, variant):
+    shape = (128, 21, 7)
+    nus = np.array([2e-5, 1e-4])
+    _, rho, u = _fields(shape, 2, 70)
+    ref, _ = _run(lbm, shape, nus, closure, storage, 1, rho, u, 5)
+    got, _ = _run(lbm, shape, nus, closure, storage, variant, rho, u, 5, tile_y=tile_y)
+    got2, _ = _run(lbm, shape, nus, closure, storage, variant, rho, u, 5, tile_y=tile_y, zchunk=2)
+    assert np.array_equal(got, got2)
+    w = orc.lattice(27)[1][None, :, None, None, None]
+    gmax = np.abs(ref - w).max()
+    tol = 8 * (2.0 ** -10 if storage == "fp16" else 2.0 ** -7) * gmax
+    for b in range(2):
+        r1, u1 = orc.fields(ref[b])
+        rv, uv = orc.fields(got[b])
+        assert np.abs(rv - r1).max() < tol and np.abs(uv - u1).max() < tol, (b, tol)
+
+
+def test_vec4_hit64_fp32_velocity(lbm, orc):
+    """Decaying HIT at 64^3 (k0 = 4, u_rms = 0.04, nu = 1e-4), KC-MP, FP32, 50
+    steps of the four-cell kernel against the FP64 oracle: velocity to 1e-5."""
+    n = 64
+    rho, u = inputs.hit_fields(n, k0=4.0, urms=0.04, seed=0)
+    for var, ty in ((14, 8), (14, 16)):
+        with lbm.Solver(27, (n, n, n), 1e-4, closure="kcmp", storage="fp32", variant=var, tile_y=ty) as s:
+            s.init_velocity(rho, u)
+            s.step(50)
+            fg = s.get_populations()
+        fo = orc.run(orc.init_equilibrium(27, rho, u), 50, closure=1, nu=1e-4, c_nu=0.035)
+        _, ug = orc.fields(fg)
+        _, uo = orc.fields(fo)
+        assert np.abs(ug - uo).max() <= 1e-5, (var, ty, np.abs(ug - uo).max())
+
+
+@pytest.mark.parametrize("variant", [14])
+def test_vec4_nonfinite_flag_and_shape_check(lbm, variant):
+    """A non-finite density reaches the status flag (LBM_ERR_NONFINITE at the
+    next synchronising call); nx not a multiple of 8 is refused."""
+    shape = (64, 16, 8)
+    rho, u = inputs.hit_fields(0, k0=2.0, urms=0.05, seed=5, shape=shape)
+    ty = 16
+    with lbm.Solver(27, shape, 1e-4, closure="kcmp", storage="fp32", variant=variant, tile_y=ty) as s:
+        s.init_velocity(rho, u)
+        f = s.get_populations()
+        f[13, 3, 4, 5] = np.nan
+        s.set_populations(f)
+        s.step(1)
+        with pytest.raises(lbm.LbmError):
+            s.synchronize()
+        s.init_velocity(rho, u)
+        s.step(2)
+        s.synchronize()
+    with pytest.raises(lbm.LbmError):
+        lbm.Solver(27, (44, 16, 8), 1e-4, closure="kcmp", storage="fp32", variant=variant, tile_y=ty)

@@ -113,6 +113,21 @@ int default_zchunk(int nx, int ny, int nz, int nbatch, int tile_y)
     return (int)zc;
 }
 
+// four-cell kernel (one 256-thread CTA per SM, tiles 128 x 8 or 64 x 16): 40
+// planes (512^3 KC-MP: 40 planes 24.5 GLUPS, 48: 24.5, 32: 24.2, 27: 24.0,
+// 64: 24.2), fewer where the box would not give two CTAs per SM
+int default_zchunk_vec4(int nx, int ny, int nz, int nbatch, int tile_y)
+{
+    const int tx = tile_y == 16 ? 64 : 128;
+    const long long tiles = (long long)((nx + tx - 1) / tx) * ((ny + tile_y - 1) / tile_y) * nbatch;
+    const long long want = (2LL * 152 + tiles - 1) / tiles;  // chunks per tile column for two CTAs per SM
+    long long zc = (nz + want - 1) / want;
+    if (zc > 40) zc = 40;
+    if (zc < 4) zc = 4;
+    if (zc > nz) zc = nz;
+    return (int)zc;
+}
+
 constexpr int kMaxGraphSteps = 4096;
 constexpr size_t kMaxGraphs = 4;
 
@@ -450,24 +465,32 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
         cfg->variant != VAR_PAIR && cfg->variant != VAR_SPLIT_PF && cfg->variant != VAR_ASYNC && cfg->variant != VAR_VEC4)
         return fail(LBM_ERR_ARG, "unknown kernel variant");
     int variant = cfg->variant;
-    // measured defaults (512^3 and ensemble timings): for FP32 storage, periodic
-    // D3Q27 with KC-MP or KC-RB takes the split-barrier pull with L2 prefetches
-    // (12) marching short z-chunks (at most 16 planes); KC-RR, D3Q19 and the
-    // walls with KC-MP take the split-barrier pull with asynchronous copies
-    // (13); otherwise periodic D3Q27 (BGK, FP64, 16-bit storage) takes the
-    // split-barrier pull (8) and the rest, the learned closure included (its
+    // measured defaults (512^3 and ensemble timings): periodic D3Q27 with 32- or
+    // 16-bit storage and BGK, KC-MP or KC-RB takes the four-cell kernel (14;
+    // tiles 128 x 8, or 64 x 16 for boxes at most 64 wide); otherwise, for FP32
+    // storage, KC-RR, D3Q19 and the walls with KC-MP take the split-barrier
+    // pull with asynchronous copies (13); periodic D3Q27 otherwise (FP64) takes
+    // the split-barrier pull (8) and the rest, the learned closure included (its
     // register pull on 4-row tiles evaluates the network for both halves of a
     // warp at once, 256^3), the register pull (1).
     // lbm_autotune may pick another launch for a given box
-    bool short_chunks = false;
+    bool short_chunks = false, vec4_chunks = false;
     if (variant == VAR_DEFAULT) {
         const bool carrier = cfg->closure == LBM_KCMP || cfg->closure == LBM_KCRB_HERMITE ||
                              cfg->closure == LBM_KCRB_RAW || cfg->closure == LBM_KCRR;
         const bool split_built = carrier || cfg->closure == LBM_BGK;
+        const bool v4_first = cfg->lattice == LBM_D3Q27 && bc_kind == BC_PERIODIC && cfg->storage != LBM_FP64 &&
+                              cfg->closure != LBM_KCRR && cfg->closure != LBM_LEARNED && vec4_shape_ok(cfg->nx) &&
+                              (cfg->tile_y == 0 || cfg->tile_y == 8 || cfg->tile_y == 16);
         const bool pf_first = cfg->lattice == LBM_D3Q27 && bc_kind == BC_PERIODIC && cfg->storage == LBM_FP32 &&
                               (cfg->closure == LBM_KCMP || cfg->closure == LBM_KCRB_HERMITE ||
                                cfg->closure == LBM_KCRB_RAW);
-        if (pf_first && step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, VAR_SPLIT_PF)) {
+        const int v4_ty = cfg->tile_y ? cfg->tile_y : (cfg->nx > 64 ? 8 : 16);
+        if (v4_first && step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, v4_ty, VAR_VEC4)) {
+            variant = VAR_VEC4;
+            tile_y = v4_ty;
+            vec4_chunks = true;
+        } else if (pf_first && step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, VAR_SPLIT_PF)) {
             variant = VAR_SPLIT_PF;
             short_chunks = true;
         } else if (carrier && cfg->storage == LBM_FP32 &&
@@ -479,6 +502,8 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
         } else {
             variant = VAR_REGISTER;
         }
+    } else if (variant == VAR_VEC4) {
+        vec4_chunks = true;
     }
     if (variant == VAR_VEC4 && !vec4_shape_ok(cfg->nx))
         return fail(LBM_ERR_UNSUPPORTED, "the four-cell variant needs nx % 8 == 0");
@@ -504,6 +529,7 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
     h->variant = variant;
     h->zchunk = cfg->zchunk ? cfg->zchunk : default_zchunk(cfg->nx, cfg->ny, cfg->nz, cfg->nbatch, tile_y);
     if (!cfg->zchunk && short_chunks && h->zchunk > 16) h->zchunk = 16;
+    if (!cfg->zchunk && vec4_chunks) h->zchunk = default_zchunk_vec4(cfg->nx, cfg->ny, cfg->nz, cfg->nbatch, tile_y);
     // the learned closure's network-heavy CTAs balance better over about twice
     // as many, half as long chunks (256^3, register pull on 4-row tiles: 26
     // planes 8.43 GLUPS, 52 planes 8.28, 16 planes 8.18)

@@ -26,20 +26,18 @@
 //    256 each.  The stash thus needs neither shared memory nor registers, and a
 //    1024-cell tile (whose halo costs a quarter or less of its own pulls) fits
 //    on one SM.
-//  * Velocities go through a ring of four planes in shared memory: the own
-//    cells' and, pulled as single cells, the halo cells' (rows y0 - 1 and
-//    y0 + TY, columns x0 - 1 and x0 + TX).  The z-neighbours of the own cells
-//    stay in registers.  The per-plane barrier is split as in step_kernel_sb:
-//    a thread arrives once it has published plane k+1 and waits for plane k
-//    just before reading its neighbours; with the z-neighbours in registers a
-//    thread that writes plane p has passed the barrier of plane p-2, so every
-//    thread is done reading plane p-4 and four slots suffice.
+//  * Velocities go through a ring of three planes in shared memory: the own
+//    cells' and the halo cells' (rows y0 - 1 and y0 + TY, columns x0 - 1 and
+//    x0 + TX, one cell per thread from the staged values).  The z-neighbours
+//    of the own cells stay in registers.  A thread that writes plane p has
+//    passed the barrier of plane p-1 (every thread has published it, after its
+//    strain reads of plane p-2), so nobody reads the slot of plane p-3 any more.
 //  * The collision relaxes the four cells together, one (c_y, c_z) population
 //    triple at a time, in the common form g' = a g + w (b (P - 1) + c0 + D H)
 //    of collide() with P - 1 = e_x (1 + Y) + Y, Y = e_y + e_z + e_y e_z, and
 //    the quadratic form H split into its (c_y, c_z) part and the c_x terms, so
 //    that each population's four results form one vector store.  For FP32
-//    storage the store's "+ w" is folded into c0.
+//    storage the store's "+ w" enters as w (1 + K), one fused rounding.
 #pragma once
 
 #include <type_traits>
@@ -148,7 +146,7 @@ struct V4Shape {
     static constexpr int TY = 8 * RPW;
     static constexpr int RY = TY + 2;      // ring and staged rows: y0 - 1 .. y0 + TY
     static constexpr int RP = TX + 8;      // ring and staging pitch: x0 - 4 .. x0 + TX + 3, own cells at 4 .. TX + 3
-    static constexpr int NSLOT = 4;
+    static constexpr int NSLOT = 3;
     static constexpr int NB = 2 * TX + 2 * TY;     // halo cells of a ring plane (no corners)
     static constexpr int NCH = TX / 4;             // 4-cell chunks of a row
     static constexpr int NPOS = 2 * NCH + 2 * RY;  // staged chunks beyond the own ones: halo rows, x-edge chunks
@@ -343,7 +341,7 @@ __global__ void __launch_bounds__(256, 1) step_kernel_v4(const StepArgs a)
         zr[1] = zc * plane;
         zr[2] = (zc == nz - 1 ? 0 : zc + 1) * plane;
     };
-    auto rslot = [&](int z) { return (z - z0 + 1) & (Sh::NSLOT - 1); };
+    auto rslot = [&](int z) { return (int)((unsigned)(z - z0 + 1) % (unsigned)Sh::NSLOT); };
     auto ringp = [&](int s, int c) { return ring + (s * 3 + c) * (RY * RP); };
     auto stg_at = [&](int i, int r, int col) { return stg + (i * RY + r) * RP + col; };
 
@@ -495,9 +493,9 @@ __global__ void __launch_bounds__(256, 1) step_kernel_v4(const StepArgs a)
     bool ok = true;
     float um[3][4], dr0[4], u0[3][4], P0[6][4];  // own: u at z - 1; drho, u, Pi' at z
     {
-        float dd[4], PP[6][4];
-        pull_own(std::false_type{}, std::false_type{}, z0 - 1, dd, um, PP);
         issue(z0);
+        float dd[4], PP[6][4];  // the first plane's z-neighbour, loaded while plane z0 is staged
+        pull_own(std::false_type{}, std::false_type{}, z0 - 1, dd, um, PP);
         ok = __all_sync(FULL, staged_wait(z0));
         if (ok) {
             pull_own(std::true_type{}, std::true_type{}, z0, dr0, u0, P0);
@@ -593,7 +591,7 @@ __global__ void __launch_bounds__(256, 1) step_kernel_v4(const StepArgs a)
                 K[c].ez[2] = a1 * uz + a2 * uz2;
                 K[c].ca = k.ca;
                 K[c].cb = k.cb;
-                const float c0 = SHIFTED ? k.c0 : k.c0 + 1.f;  // FP32 storage: the stored f = g' + w
+                const float c0 = k.c0;
                 if constexpr (CL == CL_BGK) {
 #pragma unroll
                     for (int q = 0; q < 5; ++q) K[c].C[q] = c0;
@@ -647,7 +645,10 @@ __global__ void __launch_bounds__(256, 1) step_kernel_v4(const StepArgs a)
                         const float pm1 = fmaf(K[c].ex[k], B[c], Y[c]);
                         const float Cc = cx == 0 ? K[c].C[pat] : (cx == 1 ? Cp[c] : Cm[c]);
                         const float Kv = fmaf(K[c].cb, pm1, Cc);
-                        o[c] = fmaf(K[c].ca, g[k][c], w * Kv);
+                        // FP32 storage stores f = g' + w: w (1 + K) in one rounding, so
+                        // that no part of K is lost to a sum near 1 (its small terms
+                        // would be dropped with a consistent sign, a mass bias)
+                        o[c] = fmaf(K[c].ca, g[k][c], SHIFTED ? w * Kv : fmaf(w, Kv, w));
                     }
                     if (own_store) v4_store(fout + ((long long)i * ps + cell), o[0], o[1], o[2], o[3]);
                 });

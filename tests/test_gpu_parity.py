@@ -116,21 +116,20 @@ def test_small_and_degenerate_shapes_fp64(lbm, orc, shape):
 
 @pytest.mark.parametrize("zchunk,tile_y", [(1, 8), (3, 8), (20, 8), (5, 16), (7, 4)])
 def test_launch_shapes_fp32_consistent(lbm, orc, zchunk, tile_y):
-    """Every z-chunk gives the bit-identical FP32 result of the default launch
-    (the per-cell arithmetic does not depend on the decomposition); other tile
-    heights are other kernel instantiations and agree to FP32 rounding."""
+    """Within one kernel instantiation (the tile height picks it) every z-chunk
+    gives the bit-identical FP32 result of the default chunking (the per-cell
+    arithmetic does not depend on the decomposition); other tile heights are
+    other instantiations and agree with the default launch to FP32 rounding."""
     shape = (40, 24, 20)
     rho, u = inputs.hit_fields(0, k0=3.0, urms=0.06, seed=3, shape=shape)
     res = []
-    for zc, ty in ((0, 0), (zchunk, tile_y)):
+    for zc, ty in ((0, 0), (0, tile_y), (zchunk, tile_y)):
         with lbm.Solver(27, shape, 3e-5, closure="kcmp", storage="fp32", zchunk=zc, tile_y=ty) as s:
             s.init_velocity(rho, u)
             s.step(6)
             res.append(s.get_populations())
-    if tile_y == 8:
-        assert np.array_equal(res[0], res[1])
-    else:
-        assert rel(res[1], res[0]) < 1e-6
+    assert np.array_equal(res[1], res[2])
+    assert rel(res[1], res[0]) < 1e-6
 
 
 @pytest.mark.parametrize("closure", ["bgk", "kcmp", "kcrb_hermite", "kcrb_raw"])
@@ -323,6 +322,7 @@ def test_full_size_sampled_cells_fp32(lbm, orc, n):
     pts = _sampled_cells(n, 48, seed=n)
     offs = np.array([(dx, dy, dz) for dz in range(-2, 3) for dy in range(-2, 3) for dx in range(-2, 3)])
     with lbm.Solver(27, (n, n, n), 1e-4, closure="kcmp", storage="fp32") as s:
+        assert s.launch_config["variant"] == 14  # the four-cell kernel on 128 x 8 tiles
         s.init_velocity(rho, u)
         del rho, u
         s.step(3)
@@ -388,7 +388,7 @@ def test_autotune_keeps_state_and_result(lbm, orc):
         s.step(2)
         before = s.get_populations()
         cfg = s.autotune(trials=2)
-        assert cfg["variant"] in (1, 4, 8, 9, 12, 13) and cfg["tile_y"] in (4, 8, 16) and 1 <= cfg["zchunk"] <= 128
+        assert cfg["variant"] in (1, 4, 8, 9, 12, 13, 14) and cfg["tile_y"] in (4, 8, 16) and 1 <= cfg["zchunk"] <= 128
         assert np.array_equal(before, s.get_populations())
         s.step(5)
         tuned = s.get_populations()
@@ -447,23 +447,32 @@ def test_tma_variant_matches(lbm, orc, shape, nbatch, closure):
 
 
 def test_default_variant_selection(lbm):
-    """Library default: for FP32 storage, periodic D3Q27 with KC-MP or KC-RB
-    takes the split-barrier pull with L2 prefetches (12) on z-chunks of at most
-    16 planes; KC-RR, D3Q19 and walls with KC-MP the split-barrier pull with
-    asynchronous copies (13); periodic D3Q27 otherwise (BGK, FP64, 16-bit
-    storage) the split-barrier pull (8); the rest, the learned closure
-    included, the register pull (1).  Tiles are 8 rows, 4 for the learned closure.  An explicitly requested variant that is not built for
-    a box is refused."""
-    for q, closure, storage, want in ((27, "kcmp", "fp32", 12), (27, "kcrb_hermite", "fp16", 8), (27, "kcmp", "fp64", 8),
-                                      (27, "kcrb_raw", "fp32", 12), (27, "kcrr", "fp32", 13),
-                                      (27, "bgk", "fp32", 8), (19, "kcmp", "fp32", 13), (19, "bgk", "fp32", 1),
+    """Library default: periodic D3Q27 with 32- or 16-bit storage and BGK,
+    KC-MP or KC-RB takes the four-cell kernel (14) when nx is a multiple of 8
+    (tiles 128 x 8, or 64 x 16 for boxes at most 64 wide); otherwise, for FP32
+    storage, periodic D3Q27 with KC-MP or KC-RB the split-barrier pull with L2
+    prefetches (12) on z-chunks of at most 16 planes; KC-RR, D3Q19 and walls
+    with KC-MP the split-barrier pull with asynchronous copies (13); periodic
+    D3Q27 otherwise (BGK, FP64, 16-bit storage) the split-barrier pull (8); the
+    rest, the learned closure included, the register pull (1).  Tiles are 8
+    rows, 4 for the learned closure.  An explicitly requested variant that is
+    not built for a box is refused."""
+    for q, closure, storage, want in ((27, "kcmp", "fp32", 14), (27, "kcrb_hermite", "fp16", 14), (27, "kcmp", "fp64", 8),
+                                      (27, "kcrb_raw", "fp32", 14), (27, "kcrr", "fp32", 13),
+                                      (27, "bgk", "bf16", 14), (19, "kcmp", "fp32", 13), (19, "bgk", "fp32", 1),
                                       (19, "kcmp", "fp16", 1), (27, "kcrr", "fp64", 8),
                                       (27, "learned", "fp32", 1)):
         with lbm.Solver(q, (40, 32, 64), 1e-4, closure=closure, storage=storage) as s:
             assert s.launch_config["variant"] == want, (q, closure, storage)
+            ty = {14: 16, 1: 4 if closure == "learned" else 8}.get(want, 8)
+            assert s.launch_config["tile_y"] == ty, (q, closure, storage)
+    with lbm.Solver(27, (256, 32, 64), 1e-4, closure="kcmp", storage="fp32") as s:
+        assert s.launch_config["variant"] == 14 and s.launch_config["tile_y"] == 8
+    for closure, storage, want in (("kcmp", "fp32", 12), ("kcrb_hermite", "fp16", 8), ("bgk", "fp32", 8)):
+        with lbm.Solver(27, (44, 32, 64), 1e-4, closure=closure, storage=storage) as s:  # nx % 8 != 0
+            assert s.launch_config["variant"] == want, (closure, storage)
             if want == 12:
                 assert s.launch_config["zchunk"] <= 16
-            assert s.launch_config["tile_y"] == (4 if closure == "learned" else 8)
     for q, closure, want in ((27, "kcmp", 13), (19, "kcmp", 13), (27, "kcrb_hermite", 1), (27, "bgk", 1)):
         with lbm.Solver(q, (40, 32, 16), 1e-4, closure=closure, storage="fp32", bc=(0, 1, 0)) as s:
             assert s.launch_config["variant"] == want, (q, closure, "walls")
@@ -473,6 +482,8 @@ def test_default_variant_selection(lbm):
         lbm.Solver(27, (40, 32, 16), 1e-4, closure="kcmp", storage="fp32", variant=4)
     with pytest.raises(lbm.LbmError):
         lbm.Solver(27, (40, 32, 16), 1e-4, closure="kcmp", storage="fp64", variant=9)
+    with pytest.raises(lbm.LbmError):
+        lbm.Solver(27, (40, 32, 16), 1e-4, closure="kcmp", storage="fp64", variant=14)
 
 
 @pytest.mark.parametrize("shape", [(37, 21, 13), (16, 8, 6)])

@@ -4,8 +4,8 @@ pull and their collision; 14 stages the pulls by cp.async one plane ahead, 15
 loads them into registers).
 
 It computes the same per-cell update as the register-pull kernel (variant 1)
-in the per-triple form of the same relaxation (P - 1 = e_x (1 + Y) + Y and the
-store's "+ w" folded into c0 for FP32 storage), so:
+in the per-triple form of the same relaxation (P - 1 = e_x (1 + Y) + Y, and for
+FP32 storage the stored f = g' + w as w (1 + K) in one fused rounding), so:
   - FP32 storage: populations agree with variant 1 to FP32 rounding (1e-6
     relative over 8 steps) and the velocity with the FP64 oracle to 1e-6;
   - FP16 / BF16 storage: rho and u agree with variant 1 to eight ulps of the

@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define LBM_ABI_VERSION 1
+#define LBM_ABI_VERSION 2
 
 /* error codes */
 #define LBM_OK 0
@@ -212,12 +212,24 @@ int lbm_moments_device(lbm_handle* h, double* rho_dev, double* u_dev);
 int lbm_host_alloc(size_t bytes, void** out_host);
 int lbm_host_free(void* host);
 
-/* FP64 global diagnostics of box `box` (Sec. 7.1, Eq. tgv_energy_enstrophy):
- * out[0] mass sum, out[1..3] momentum sums, out[4] E_k = <rho|u|^2/2>,
- * out[5] enstrophy <|curl u|^2/2> with the sixth-order centred curl (second-order
- * stencils along bounce-back axes), out[6] number of non-finite cells,
- * out[7] max |u|.  Synchronises; returns LBM_ERR_NONFINITE if out[6] > 0. */
-int lbm_diagnostics(lbm_handle* h, int box, double out[8]);
+/* FP64 global diagnostics of box `box`, LBM_DIAG_VALUES doubles:
+ *  of the stored state (Sec. 7.1, Eq. tgv_energy_enstrophy):
+ *   out[0] mass sum, out[1..3] momentum sums, out[4] E_k = <rho|u|^2/2>,
+ *   out[5] enstrophy <|curl u|^2/2> with the sixth-order centred curl
+ *   (second-order stencils along bounce-back axes), out[6] number of
+ *   non-finite cells, out[7] max |u|;
+ *  of the state the next step collides (the stored populations pull-streamed,
+ *  rho and u of App. F.1 step 1, the strain of Eqs. fd, fd_boundary_lower/upper
+ *  and strain_rate_discrete; a reading, the paper being silent on the
+ *  dissipation):
+ *   out[8] <2 rho nu_eff S:S>, nu_eff = theta (1/omega_s - 1/2) with the
+ *   closure's clipped rate omega_s (Eq. omega_sgs_operational; nu for BGK;
+ *   NaN for the learned closure), out[9] <2 rho nu S:S>.
+ * Averages are arithmetic over the nodes.  Allocates its scratch (about 48
+ * bytes per cell) on first use.  Synchronises; returns LBM_ERR_NONFINITE if
+ * out[6] > 0.  (ABI version 1 had out[8], without the dissipation.) */
+#define LBM_DIAG_VALUES 10
+int lbm_diagnostics(lbm_handle* h, int box, double out[LBM_DIAG_VALUES]);
 
 /* Copies the populations, converted to FP64 (shifted storage un-shifted), to
  * host [nbatch][q][nz][ny][nx].  Synchronises. */
@@ -253,10 +265,12 @@ int64_t lbm_step_count(const lbm_handle* h);
  * counterpart; it is a service for callers that cannot allocate device memory:
  * a process whose device memory is all owned by another allocator, code that
  * must not trigger the implicit device synchronisation of cudaMalloc/cudaFree,
- * or a loop with a fixed memory budget).  Computes the same eight values as
- * lbm_diagnostics for ONE box whose populations the caller passes:
+ * or a loop with a fixed memory budget).  Computes the first eight values of
+ * lbm_diagnostics (those of the stored state, not the dissipation rates) for
+ * ONE box whose populations the caller passes:
  *   f_dev    device pointer to the box's populations in storage format,
- *            [q][nz][ny][nx] (e.g. lbm_population_buffer plus the box offset);
+ *            [q][nz][ny][nx]: lbm_population_buffer plus the box offset, box b
+ *            starting b*q*nx*ny*nz elements (of elem_bytes each) further;
  *   lattice, storage, nx, ny, nz: as in lbm_config (nz <= 4096);
  *   bc       host int[3] (NULL = periodic), force host double[3] (NULL = none);
  *   out_dev  device pointer to 8 doubles, written by the kernel;
@@ -264,9 +278,11 @@ int64_t lbm_step_count(const lbm_handle* h);
  * Enqueue only, no synchronisation, no cudaMalloc/cudaFree or other allocating
  * call.  Its scratch is a static device array of 4096 x 8 FP64 partial sums
  * plus a counter (about 256 KB) that every GPU loading the library holds until
- * the process exits; nz > 4096 is rejected with LBM_ERR_ARG.  The first call on
- * each device looks up the array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture on that device.  All calls share
+ * the process exits; nz > 4096 is rejected with LBM_ERR_ARG.  A call made outside
+ * stream capture looks up the array's device address (cudaGetSymbolAddress) on
+ * the current device and keeps it; a call during a capture uses the address the
+ * last such call kept, so make the first call on each device before any stream
+ * capture on it (otherwise LBM_ERR_CUDA).  All calls share
  * the array: calls whose kernels overlap on the GPU (other streams, other
  * threads) race and must be serialised by the caller.  Returns LBM_OK,
  * LBM_ERR_ARG or LBM_ERR_CUDA. */

@@ -65,6 +65,8 @@ def _load() -> ctypes.CDLL:
     lib.orc_init_equilibrium.argtypes = [c_int, c_int, c_int, c_int, dp, dp, dp]
     lib.orc_fields.argtypes = [c_int, c_int, c_int, c_int, dp, dp, dp, dp]
     lib.orc_diagnostics.argtypes = [c_int, c_int, c_int, c_int, ip, dp, dp, dp]
+    lib.orc_dissipation.argtypes = [c_int, c_int, c_int, c_int, c_int, ip, c_double, c_double, c_double, dp, dp, dp]
+    lib.orc_dissipation_pre.argtypes = [c_int, c_int, c_int, c_int, c_int, ip, c_double, c_double, c_double, dp, dp, dp]
     lib.orc_num_threads.restype = c_int
     lib.orc_set_num_threads.argtypes = [c_int]
     _lib = lib
@@ -215,6 +217,32 @@ def diagnostics(f: np.ndarray, bc=(0, 0, 0), F: Sequence[float] = (0.0, 0.0, 0.0
     out = np.zeros(8, dtype=np.float64)
     _check(lib.orc_diagnostics(q, nx, ny, nz, _ip(b), _dp(FF), _dp(ff), _dp(out)), "diagnostics")
     return out
+
+
+def _dissipation(fn, what, f, closure, nu, c_nu, delta, bc, F):
+    lib = _load()
+    q, nz, ny, nx = f.shape
+    ff = np.ascontiguousarray(f, dtype=np.float64)
+    b = np.ascontiguousarray(bc, dtype=np.int32)
+    FF = np.ascontiguousarray(F, dtype=np.float64)
+    out = np.zeros(2, dtype=np.float64)
+    _check(getattr(lib, fn)(q, nx, ny, nz, closure, _ip(b), float(nu), float(c_nu), float(delta), _dp(FF), _dp(ff),
+                            _dp(out)), what)
+    return out
+
+
+def dissipation(f: np.ndarray, *, closure: int, nu: float, c_nu: float = 0.0, delta: float = 1.0, bc=(0, 0, 0),
+                F: Sequence[float] = (0.0, 0.0, 0.0)) -> np.ndarray:
+    """[<2 rho nu_eff S:S>, <2 rho nu S:S>] of the state the next step collides:
+    the stored post-collision populations f[q,nz,ny,nx] pull-streamed; nu_eff =
+    theta (1/omega_s - 1/2) from the closure's clipped rate at each node."""
+    return _dissipation("orc_dissipation", "dissipation", f, closure, nu, c_nu, delta, bc, F)
+
+
+def dissipation_pre(f_pre: np.ndarray, *, closure: int, nu: float, c_nu: float = 0.0, delta: float = 1.0,
+                    bc=(0, 0, 0), F: Sequence[float] = (0.0, 0.0, 0.0)) -> np.ndarray:
+    """As dissipation() for a given pre-collision (already streamed) state."""
+    return _dissipation("orc_dissipation_pre", "dissipation_pre", f_pre, closure, nu, c_nu, delta, bc, F)
 
 
 def num_threads() -> int:

@@ -491,14 +491,13 @@ int orc_strain_field(int nx, int ny, int nz, const int* bc, const double* u, dou
  * Pass 1: pull-stream into fpre and compute rho, u at every node.
  * Pass 2: strain from the stored u, then equilibrium, closure, collision. */
 /* ------------------------------------------------------------------ */
-static void orc_step_once(const orc_params* P, const orc_lattice* L, const double* fin, double* fout, double* fpre,
-                          double* rho, double* u)
+/* pass 1 of a step: pull-stream fin into fpre (Eq. streaming; halfway
+ * bounce-back on wall axes) and compute rho, u at every node (step 1) */
+static void orc_stream_moments(const orc_params* P, const orc_lattice* L, const double* fin, double* fpre, double* rho,
+                               double* u)
 {
     const int q = L->q, nx = P->nx, ny = P->ny, nz = P->nz;
     const size_t N = (size_t)nx * ny * nz;
-    const double omega = 1.0 / (P->nu / ORC_THETA + 0.5); /* Eq. (omega_t_discrete) */
-
-    /* pass 1: stream + moments */
 #pragma omp parallel for schedule(static)
     for (int z = 0; z < nz; ++z) {
         for (int y = 0; y < ny; ++y)
@@ -528,6 +527,17 @@ static void orc_step_once(const orc_params* P, const orc_lattice* L, const doubl
                 for (int a = 0; a < 3; ++a) u[(size_t)a * N + cidx] = uu[a];
             }
     }
+}
+
+static void orc_step_once(const orc_params* P, const orc_lattice* L, const double* fin, double* fout, double* fpre,
+                          double* rho, double* u)
+{
+    const int q = L->q, nx = P->nx, ny = P->ny, nz = P->nz;
+    const size_t N = (size_t)nx * ny * nz;
+    const double omega = 1.0 / (P->nu / ORC_THETA + 0.5); /* Eq. (omega_t_discrete) */
+
+    /* pass 1: stream + moments */
+    orc_stream_moments(P, L, fin, fpre, rho, u);
     /* pass 2: gradient + closure + collision */
 #pragma omp parallel for schedule(static)
     for (int z = 0; z < nz; ++z) {
@@ -761,6 +771,103 @@ int orc_diagnostics(int q, int nx, int ny, int nz, const int* bc, const double* 
     out[5] = zz / (double)N;
     out[6] = bad;
     out[7] = 0.0;
+    free(rho);
+    free(u);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Dissipation rates of a pre-collision state (a reading: the paper reports
+ * E_k and enstrophy, Sec. 7.1, and is silent on the dissipation).  At every
+ * node, with rho, u (step 1), S (step 3, Eqs. fd, fd_boundary_lower/upper,
+ * strain_rate_discrete) and the closure's clipped rate omega_s (step 5, Eq.
+ * omega_sgs_operational; omega for BGK), the effective viscosity is
+ * nu_eff = theta (1/omega_s - 1/2), the viscosity the two-rate relaxation
+ * applies to the SGS part; then
+ *   out[0] = < 2 rho nu_eff S:S >,   out[1] = < 2 rho nu S:S >
+ * (arithmetic averages over the nodes, S:S = sum_ab S_ab^2).              */
+/* ------------------------------------------------------------------ */
+static void orc_dissipation_core(const orc_params* P, const orc_lattice* L, const double* fpre, const double* rho,
+                                 const double* u, double* out)
+{
+    const int q = L->q, nx = P->nx, ny = P->ny, nz = P->nz;
+    const size_t N = (size_t)nx * ny * nz;
+    const double omega = 1.0 / (P->nu / ORC_THETA + 0.5);
+    double e_eff = 0.0, e_mol = 0.0;
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                size_t cidx = orc_cell(P, x, y, z);
+                double f[27], fp[27], S[3][3], uu[3], omega_s;
+                for (int i = 0; i < q; ++i) f[i] = fpre[(size_t)i * N + cidx];
+                for (int a = 0; a < 3; ++a) uu[a] = u[(size_t)a * N + cidx];
+                orc_strain_at(P, u, x, y, z, S);
+                orc_collide_L(L, P->closure, f, rho[cidx], uu, S, P->F, P->nu, omega, P->c_nu, P->delta, fp, &omega_s,
+                              NULL);
+                double ss = 0.0;
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) ss = ss + S[a][b] * S[a][b];
+                double nu_eff = ORC_THETA * (1.0 / omega_s - 0.5);
+                e_eff = e_eff + 2.0 * rho[cidx] * nu_eff * ss;
+                e_mol = e_mol + 2.0 * rho[cidx] * P->nu * ss;
+            }
+    out[0] = e_eff / (double)N;
+    out[1] = e_mol / (double)N;
+}
+
+/* exported: dissipation rates of the pre-collision state fpre [q][N] */
+int orc_dissipation_pre(int q, int nx, int ny, int nz, int closure, const int* bc, double nu, double c_nu,
+                        double delta, const double* F, const double* fpre, double* out)
+{
+    orc_params P;
+    int rc = orc_fill_params(&P, q, nx, ny, nz, closure, bc, nu, c_nu, delta, F);
+    if (rc) return rc;
+    orc_lattice L;
+    orc_lattice_init(q, &L);
+    size_t N = (size_t)nx * ny * nz;
+    double* rho = (double*)malloc(sizeof(double) * N);
+    double* u = (double*)malloc(sizeof(double) * 3 * N);
+    if (!rho || !u) {
+        free(rho);
+        free(u);
+        return -2;
+    }
+    for (size_t c = 0; c < N; ++c) {
+        double f[27], r, uu[3];
+        for (int i = 0; i < q; ++i) f[i] = fpre[(size_t)i * N + c];
+        orc_moments_L(&L, f, P.F, &r, uu);
+        rho[c] = r;
+        for (int a = 0; a < 3; ++a) u[(size_t)a * N + c] = uu[a];
+    }
+    orc_dissipation_core(&P, &L, fpre, rho, u, out);
+    free(rho);
+    free(u);
+    return 0;
+}
+
+/* exported: dissipation rates of the state the next step collides, i.e. of
+ * the stored post-collision populations f [q][N] after pull streaming */
+int orc_dissipation(int q, int nx, int ny, int nz, int closure, const int* bc, double nu, double c_nu, double delta,
+                    const double* F, const double* f, double* out)
+{
+    orc_params P;
+    int rc = orc_fill_params(&P, q, nx, ny, nz, closure, bc, nu, c_nu, delta, F);
+    if (rc) return rc;
+    orc_lattice L;
+    orc_lattice_init(q, &L);
+    size_t N = (size_t)nx * ny * nz;
+    double* fpre = (double*)malloc(sizeof(double) * q * N);
+    double* rho = (double*)malloc(sizeof(double) * N);
+    double* u = (double*)malloc(sizeof(double) * 3 * N);
+    if (!fpre || !rho || !u) {
+        free(fpre);
+        free(rho);
+        free(u);
+        return -2;
+    }
+    orc_stream_moments(&P, &L, f, fpre, rho, u);
+    orc_dissipation_core(&P, &L, fpre, rho, u, out);
+    free(fpre);
     free(rho);
     free(u);
     return 0;

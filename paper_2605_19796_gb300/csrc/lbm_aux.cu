@@ -338,6 +338,141 @@ __global__ void diag_final_kernel(const double* partials, int nblocks, long long
     }
 }
 
+// ------------------------------------------------------------ dissipation
+//
+// Dissipation rates of the state the next step collides (a reading: the
+// paper reports E_k and enstrophy, Sec. 7.1, and is silent on the
+// dissipation): the stored populations pull-streamed (Eq. streaming;
+// halfway bounce-back across y walls), then at every node rho, u (App. F.1
+// step 1, with the half-force shift), the strain of Eqs. (fd),
+// (fd_boundary_lower/upper), (strain_rate_discrete), the closure's clipped
+// rate omega_s (Eq. omega_sgs_operational) and nu_eff = theta (1/omega_s -
+// 1/2); the reductions are <2 rho nu_eff S:S> and <2 rho nu S:S> in FP64.
+
+// drho = sum g, u, and sum g |c|^2 (g = f - w: the sums stay small, so the
+// trace of m_neq below is free of O(1) cancellation) of the streamed state
+template <int Q, typename S>
+__global__ void pull_moments_kernel(const S* f, int nx, int ny, int nz, int walls, double Fx, double Fy, double Fz,
+                                    double* drho, double* u, double* s2)
+{
+    const long long N = (long long)nx * ny * nz;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long long)nx * ny));
+        double d = 0, jx = 0, jy = 0, jz = 0, e2 = 0;
+        static_for<Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i), io = opp_of(Q, i);
+            constexpr double w = weight_of(Q, i);
+            const int sy = y - cy;
+            long long src;
+            if (walls && (sy < 0 || sy >= ny))
+                src = (long long)io * N + c;  // halfway bounce-back
+            else
+                src = (long long)i * N + ((long long)wrapi(z - cz, nz) * ny + wrapi(sy, ny)) * nx + wrapi(x - cx, nx);
+            const double g = to_f<S>(f[src], w) - w;
+            d += g;
+            jx += cx * g;
+            jy += cy * g;
+            jz += cz * g;
+            e2 += (cx * cx + cy * cy + cz * cz) * g;
+        });
+        const double r = 1.0 + d;
+        drho[c] = d;
+        u[c] = (jx + 0.5 * Fx) / r;
+        u[N + c] = (jy + 0.5 * Fy) / r;
+        u[2 * N + c] = (jz + 0.5 * Fz) / r;
+        s2[c] = e2;
+    }
+}
+
+constexpr int kDissBlock = 256;
+
+__global__ void __launch_bounds__(kDissBlock) dissip_kernel(const double* drho, const double* u, const double* s2,
+                                                            int nx, int ny, int nz, int walls, int closure, double nu,
+                                                            double cnud, double* partials)
+{
+    const long long N = (long long)nx * ny * nz;
+    constexpr double th = kTheta;
+    const double tau_hat = nu / th + 0.5, omega = 1.0 / tau_hat;
+    double ee = 0.0, em = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long long)nx * ny));
+        auto U = [&](int b, int xx, int yy, int zz) { return u[b * N + ((long long)zz * ny + yy) * nx + xx]; };
+        double du[3][3];  // du[a][b] = d_a u_b
+        for (int b = 0; b < 3; ++b) {
+            du[0][b] = (U(b, wrapi(x + 1, nx), y, z) - U(b, wrapi(x - 1, nx), y, z)) / 2.0;
+            du[2][b] = (U(b, x, y, wrapi(z + 1, nz)) - U(b, x, y, wrapi(z - 1, nz))) / 2.0;
+            if (walls && y == 0)
+                du[1][b] = (-3.0 * U(b, x, 0, z) + 4.0 * U(b, x, 1, z) - U(b, x, 2, z)) / 2.0;
+            else if (walls && y == ny - 1)
+                du[1][b] = (3.0 * U(b, x, ny - 1, z) - 4.0 * U(b, x, ny - 2, z) + U(b, x, ny - 3, z)) / 2.0;
+            else
+                du[1][b] = (U(b, x, wrapi(y + 1, ny), z) - U(b, x, wrapi(y - 1, ny), z)) / 2.0;
+        }
+        double S[3][3], ss = 0.0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                S[a][b] = 0.5 * (du[b][a] + du[a][b]);
+                ss += S[a][b] * S[a][b];
+            }
+        const double r = 1.0 + drho[c];
+        const double ux = u[c], uy = u[N + c], uz = u[2 * N + c];
+        double omega_s = omega;
+        if (closure == CL_LEARNED) {
+            omega_s = nan("");
+        } else if (closure != CL_BGK) {
+            // tr m_neq = sum f |c|^2 - rho (|u|^2 + 3 theta) = sum g |c|^2 - rho |u|^2 - 3 theta drho
+            const double trneq = s2[c] - r * (ux * ux + uy * uy + uz * uz) - 3.0 * th * drho[c];
+            const double trS = S[0][0] + S[1][1] + S[2][2];
+            // KC-MP, KC-RR: tr (m_neq - m_CE), m_CE = -2 rho theta tau_hat S; KC-RB:
+            // tr (f - f0 - f1) |c|^2 with sum f1 |c|^2 = -2 (Hermite) or -5 (raw) rho tau_hat theta tr S
+            const double tr = trneq + (closure == CL_KCRB_RAW ? 5.0 : 2.0) * r * th * tau_hat * trS;
+            const double nut = cnud * sqrt(fabs(tr) / 2.0);
+            if (nut > nu) omega_s = 1.0 / (nut / th + 0.5);
+        }
+        const double nu_eff = th * (1.0 / omega_s - 0.5);
+        ee += 2.0 * r * nu_eff * ss;
+        em += 2.0 * r * nu * ss;
+    }
+    __shared__ double red[2][kDissBlock];
+    red[0][threadIdx.x] = ee;
+    red[1][threadIdx.x] = em;
+    __syncthreads();
+    for (int s = kDissBlock / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + s];
+            red[1][threadIdx.x] += red[1][threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 2) partials[blockIdx.x * 2 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// single-block, fixed-order sum of the partials; out[0], out[1] = the averages
+__global__ void dissip_final_kernel(const double* partials, int nblocks, long long N, double* out)
+{
+    __shared__ double red[2][kDissBlock];
+    double a0 = 0.0, a1 = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        a0 += partials[b * 2];
+        a1 += partials[b * 2 + 1];
+    }
+    red[0][threadIdx.x] = a0;
+    red[1][threadIdx.x] = a1;
+    __syncthreads();
+    for (int s = kDissBlock / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + s];
+            red[1][threadIdx.x] += red[1][threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = red[0][0] / (double)N;
+        out[1] = red[1][0] / (double)N;
+    }
+}
+
 int diag_blocks(long long ncell)
 {
     long long b = (ncell + kDiagBlock - 1) / kDiagBlock;
@@ -492,6 +627,31 @@ cudaError_t launch_diagnostics(const double* rho, const double* u, int nx, int n
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     diag_final_kernel<<<1, kDiagBlock, 0, s>>>(partials, nb, N, out_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dissipation(int q, int storage, const void* f, int nx, int ny, int nz, int walls, const double* force,
+                               int closure, double nu, double cnud, double* drho, double* u, double* s2,
+                               double* partials, double* out_dev, cudaStream_t s)
+{
+    const long long N = (long long)nx * ny * nz;
+    const int g = grid_for(N, 256);
+    cudaError_t e = dispatch_storage(storage, [&](auto tag) -> cudaError_t {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        if (q == 27)
+            pull_moments_kernel<27, S><<<g, 256, 0, s>>>((const S*)f, nx, ny, nz, walls, force[0], force[1], force[2],
+                                                         drho, u, s2);
+        else
+            pull_moments_kernel<19, S><<<g, 256, 0, s>>>((const S*)f, nx, ny, nz, walls, force[0], force[1], force[2],
+                                                         drho, u, s2);
+        return cudaGetLastError();
+    });
+    if (e != cudaSuccess) return e;
+    const int nb = diag_blocks(N);
+    dissip_kernel<<<nb, kDissBlock, 0, s>>>(drho, u, s2, nx, ny, nz, walls, closure, nu, cnud, partials);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dissip_final_kernel<<<1, kDissBlock, 0, s>>>(partials, nb, N, out_dev);
     return cudaGetLastError();
 }
 

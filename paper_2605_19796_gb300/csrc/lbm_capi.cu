@@ -67,7 +67,8 @@ struct lbm_handle {
     double* d_rho = nullptr;  // diagnostics scratch (lazy): rho [N], u [3][N] of one box
     double* d_u = nullptr;
     double* d_partials = nullptr;
-    double* d_diag = nullptr;
+    double* d_diag = nullptr;  // LBM_DIAG_VALUES doubles
+    double* d_s2 = nullptr;    // dissipation scratch: sum g |c|^2 of the streamed state [N]
     cudaStream_t stream = nullptr;
     int tile_y = 8;
     int variant = VAR_REGISTER;
@@ -238,6 +239,7 @@ void free_all(lbm_handle* h)
     if (h->d_u) cudaFree(h->d_u);
     if (h->d_partials) cudaFree(h->d_partials);
     if (h->d_diag) cudaFree(h->d_diag);
+    if (h->d_s2) cudaFree(h->d_s2);
     if (h->d_mlp) cudaFree(h->d_mlp);
     if (h->xstream) cudaStreamSynchronize(h->xstream);
     if (h->stage) cudaFree(h->stage);
@@ -270,13 +272,15 @@ int ensure_diag_scratch(lbm_handle* h)
     cudaError_t e = cudaMalloc(&h->d_rho, sizeof(double) * N);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_u, sizeof(double) * 3 * N);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_partials, sizeof(double) * diag_partials_len(N));
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_diag, sizeof(double) * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_diag, sizeof(double) * LBM_DIAG_VALUES);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_s2, sizeof(double) * N);
     if (e != cudaSuccess) {
         cudaFree(h->d_rho);
         cudaFree(h->d_u);
         cudaFree(h->d_partials);
         cudaFree(h->d_diag);
-        h->d_rho = h->d_u = h->d_partials = h->d_diag = nullptr;
+        cudaFree(h->d_s2);
+        h->d_rho = h->d_u = h->d_partials = h->d_diag = h->d_s2 = nullptr;
         cudaGetLastError();
         return fail(LBM_ERR_OOM, "diagnostics scratch allocation failed");
     }
@@ -771,7 +775,7 @@ int lbm_wait_selftest(lbm_handle* h, int polls)
     return read_flag(h);
 }
 
-int lbm_diagnostics(lbm_handle* h, int box, double out[8])
+int lbm_diagnostics(lbm_handle* h, int box, double out[LBM_DIAG_VALUES])
 {
     if (int rc = check_handle(h)) return rc;
     if (!out) return fail(LBM_ERR_ARG, "out is NULL");
@@ -783,10 +787,17 @@ int lbm_diagnostics(lbm_handle* h, int box, double out[8])
     if (e == cudaSuccess)
         e = launch_diagnostics(h->d_rho, h->d_u, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->cfg.bc, h->d_partials, h->d_diag,
                                h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out, h->d_diag, sizeof(double) * 8, cudaMemcpyDeviceToHost, h->stream);
+    // the dissipation rates of the next pre-collision state (the moments
+    // scratch is reused: the kernels above have read it by then)
+    if (e == cudaSuccess)
+        e = launch_dissipation(h->q, h->cfg.storage, fb, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->bc_kind == BC_WALLS_Y,
+                               h->cfg.force, h->cfg.closure, h->nu[box], h->cfg.c_nu * h->cfg.delta, h->d_rho, h->d_u,
+                               h->d_s2, h->d_partials, h->d_diag + 8, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, h->d_diag, sizeof(double) * LBM_DIAG_VALUES, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "diagnostics");
-    h->launches += 3;
+    h->launches += 6;
     int rc = read_flag(h);
     if (rc == LBM_OK && out[6] > 0) rc = fail(LBM_ERR_NONFINITE, "non-finite cells in the diagnosed box");
     return rc;

@@ -103,5 +103,12 @@ cudaError_t launch_probe(int q, int storage, const void* f, const int* xyz, int 
 long long diag_partials_len(long long ncell);
 cudaError_t launch_diagnostics(const double* rho, const double* u, int nx, int ny, int nz, const int* bc,
                                double* partials, double* out_dev, cudaStream_t s);
+// Dissipation rates of one box's next pre-collision state (f: that box's
+// populations; walls: bounce-back in y): out_dev[0] = <2 rho nu_eff S:S>,
+// out_dev[1] = <2 rho nu S:S> (NaN for nu_eff of the learned closure).
+// drho [N], u [3][N], s2 [N] and partials (diag_partials_len) are scratch.
+cudaError_t launch_dissipation(int q, int storage, const void* f, int nx, int ny, int nz, int walls, const double* force,
+                               int closure, double nu, double cnud, double* drho, double* u, double* s2,
+                               double* partials, double* out_dev, cudaStream_t s);
 
 }  // namespace lbmk

@@ -202,20 +202,29 @@ __global__ void __launch_bounds__(kNaBlock) na_diag_kernel(const S* f, NaGeom g,
 std::mutex g_na_mu;
 void* g_na_ptr[kNaMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the array's host-side name is not a device address).
-cudaError_t na_scratch(double** out)
+// Device address of the scratch array on the current device.  The array's
+// host-side name is not a device address, so it is looked up with
+// cudaGetSymbolAddress: on every call made outside stream capture (cheap, and
+// a device reset that reloaded the module cannot leave a stale address
+// behind), and from the per-device cache during capture (the address a call
+// outside capture stored there).
+cudaError_t na_scratch(cudaStream_t s, double** out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kNaMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lk(g_na_mu);
-    if (!g_na_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
         g_na_ptr[dev] = p;
+    } else if (!g_na_ptr[dev]) {
+        return cudaErrorStreamCaptureUnsupported;  // first call on this device during a capture
     }
     *out = static_cast<double*>(g_na_ptr[dev]);
     return cudaSuccess;
@@ -247,11 +256,11 @@ extern "C" int lbm_diagnostics_noalloc(const void* f_dev, int lattice, int stora
         const int n = a == 0 ? nx : (a == 1 ? ny : nz);
         if (g.bc[a] == LBM_BOUNCEBACK && n < 3) return set_last_error(LBM_ERR_ARG, "a bounce-back axis needs >= 3 cells");
     }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
     double* scratch = nullptr;
-    cudaError_t e = na_scratch(&scratch);
+    cudaError_t e = na_scratch(s, &scratch);
     if (e != cudaSuccess)
         return set_last_error(LBM_ERR_CUDA, (std::string("scratch address lookup failed: ") + cudaGetErrorString(e)).c_str());
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     e = cudaMemsetAsync(scratch + kNaMaxPlanes * kNaVals, 0, sizeof(double), s);  // ticket
     if (e != cudaSuccess)
         return set_last_error(LBM_ERR_CUDA, (std::string("clearing the ticket failed: ") + cudaGetErrorString(e)).c_str());

@@ -215,7 +215,13 @@ def host_empty(shape, dtype=np.float64) -> np.ndarray:
     return arr
 
 
+DIAG_VALUES = 10  # LBM_DIAG_VALUES of include/lbm.h
+
+
 def lbm_diagnostics(h, box: int, out: np.ndarray) -> None:
+    """out: FP64 array of DIAG_VALUES values (layout in include/lbm.h)."""
+    if out.dtype != np.float64 or out.size < DIAG_VALUES:
+        raise ValueError("out must hold %d float64 values" % DIAG_VALUES)
     _check(LIB.lbm_diagnostics(h, int(box), _dp(out)))
 
 
@@ -488,7 +494,9 @@ class Solver:
         lbm_moments_device(self.h, 0 if rho is None else rho.data_ptr(), 0 if u is None else u.data_ptr())
 
     def diagnostics(self, box: int = 0) -> np.ndarray:
-        out = np.zeros(8, dtype=np.float64)
+        """[mass, momentum x3, E_k, enstrophy, non-finite cells, max|u|,
+        <2 rho nu_eff S:S>, <2 rho nu S:S>] (include/lbm.h, lbm_diagnostics)."""
+        out = np.zeros(DIAG_VALUES, dtype=np.float64)
         lbm_diagnostics(self.h, box, out)
         return out
 

@@ -87,6 +87,9 @@ def test_tgv_32_d3q19_fp64_kcmp_200_steps(lbm, orc):
                 assert abs(d_g[k] - d_o[k]) <= TOL64 * abs(d_o[k]), (cp, k, d_g[k], d_o[k])
             for k in (1, 2, 3):
                 assert abs(d_g[k] - d_o[k]) <= TOL64 * d_o[0] * u0, (cp, k, d_g[k], d_o[k])
+            # dissipation rates of the next pre-collision state (FP64 on the GPU)
+            e_o = orc.dissipation(f, closure=1, nu=nu, c_nu=0.035)
+            assert np.abs(d_g[8:10] - e_o).max() <= TOL64 * np.abs(e_o).max(), (cp, d_g[8:10], e_o)
             ek.append(d_g[4])
         assert ek[-1] < ek[0]  # energy decays
 
@@ -105,6 +108,47 @@ def test_closures_ragged_fp64(lbm, orc, q, closure):
         f0 = orc.init_equilibrium(q, rho, u)
         fb = orc.run(f0, 12, closure=0, nu=nu)
         assert np.abs(fo - fb).max() > 1e-7, "the closure must be active in this test"
+
+
+@pytest.mark.parametrize("q", [19, 27])
+@pytest.mark.parametrize("closure", ["bgk", "kcmp", "kcrb_hermite", "kcrb_raw", "kcrr"])
+def test_dissipation_matches_oracle_fp64(lbm, orc, q, closure):
+    """lbm_diagnostics out[8], out[9] (<2 rho nu_eff S:S>, <2 rho nu S:S> of the
+    next pre-collision state, FP64 on the GPU) against the oracle's
+    dissipation() of the same stored state to 1e-12, on a ragged
+    under-resolved box where the clipped rate is active."""
+    if closure == "kcrr" and q == 19:
+        pytest.skip("KC-RR is D3Q27 only")
+    shape = (37, 21, 13)
+    rho, u = inputs.hit_fields(0, k0=3.0, urms=0.08, seed=21, shape=shape)
+    nu = 2e-5
+    with lbm.Solver(q, shape, nu, closure=closure, c_nu=CNU[closure], storage="fp64") as s:
+        s.init_velocity(rho, u)
+        s.step(6)
+        d = s.diagnostics()
+        f = s.get_populations()
+    e_o = orc.dissipation(f, closure=CL[closure], nu=nu, c_nu=CNU[closure])
+    assert np.abs(d[8:10] - e_o).max() <= TOL64 * np.abs(e_o).max(), (d[8:10], e_o)
+    if closure != "bgk":
+        assert d[8] > 1.5 * d[9], "the clipped rate must be active somewhere"
+    else:
+        assert abs(d[8] - d[9]) <= TOL64 * d[9]
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_dissipation_channel_fp64(lbm, orc, q):
+    """The same with bounce-back walls in y and a body force (one-sided strain
+    at the wall rows, half-force shift of u), KC-MP."""
+    shape = (16, 11, 6)
+    rho, u = inputs.channel_fields(*shape, 0.05, seed=5)
+    F = (1e-5, 0.0, 0.0)
+    with lbm.Solver(q, shape, 2e-3, closure="kcmp", storage="fp64", bc=(0, 1, 0), force=F) as s:
+        s.init_velocity(rho, u)
+        s.step(4)
+        d = s.diagnostics()
+        f = s.get_populations()
+    e_o = orc.dissipation(f, closure=1, nu=2e-3, c_nu=0.035, bc=(0, 1, 0), F=F)
+    assert np.abs(d[8:10] - e_o).max() <= TOL64 * np.abs(e_o).max(), (d[8:10], e_o)
 
 
 @pytest.mark.parametrize("shape", [(4, 4, 4), (1, 1, 6), (3, 5, 2), (64, 8, 1), (33, 9, 5), (2, 40, 3)])
@@ -163,13 +207,10 @@ def test_fp32_hit_64_velocity(lbm, orc):
 
 
 def _spectrum(u):
-    """Shell-averaged E(k) = 1/2 sum_{|k'| in [k-1/2, k+1/2)} |u_hat(k')|^2 of a periodic cube."""
-    n = u.shape[-1]
-    uh = np.fft.fftn(u, axes=(1, 2, 3)) / n ** 3
-    e = 0.5 * (np.abs(uh) ** 2).sum(0)
-    k = np.fft.fftfreq(n, d=1.0 / n)
-    kk = np.sqrt(k[:, None, None] ** 2 + k[None, :, None] ** 2 + k[None, None, :] ** 2)
-    return np.bincount(np.rint(kk).astype(int).ravel(), weights=e.ravel(), minlength=n)[: n // 2]
+    """The oracle's E(k) (oracle/spectrum.py, pinned in tests/test_oracle_spectrum.py)."""
+    from oracle.spectrum import spectrum
+
+    return spectrum(u)
 
 
 def test_fp32_hit_64_statistics(lbm, orc):

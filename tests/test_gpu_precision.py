@@ -1,15 +1,110 @@
-"""Storage precision (weight-shifted FP16 / BF16 vs FP32 vs FP64) on 64^3
-decaying HIT, 100 steps, against the FP64-storage GPU run (itself parity-checked
-against the oracle).  Bounds (stated here, from the storage mantissas: FP32
-24 bits on f, FP16 11 bits and BF16 8 bits on g = f - w, |g| ~ 1e-3):
-u rms error vs u_rms = 0.04: FP32 < 1e-6, FP16 < 1e-3 x u_rms, BF16 < 1e-2 x u_rms;
-errors ordered FP32 < FP16 < BF16; kinetic energy within 1e-2 (BF16)."""
+"""Storage precision of weight-shifted FP16 / BF16 storage (FP32 arithmetic)
+on 64^3 decaying HIT (k0 = 4, u_rms = 0.04, nu = 1e-4, KC-MP), 100 steps,
+against the FP64 ORACLE run of the same initial state, per result (rho, u,
+E_k, E(k)), with bounds derived from the storage rounding:
+
+  - each step stores every population rounded to the format, g = f - w with a
+    relative error of at most u_s = 2^-11 (FP16, 11 significand bits) or 2^-8
+    (BF16, 8 bits); these errors are independent and zero-mean, of standard
+    deviation u_s |g_i| / sqrt(3);
+  - rho and rho u are sums of the 27 populations, so a step adds to them an
+    error of standard deviation at most sigma_1 = u_s ||g|| / sqrt(3) (||g||
+    the largest per-cell Euclidean norm of the 27 g_i); both are conserved, so
+    the errors persist and spread, and an L2-stable conserving propagator does
+    not amplify them: after n steps (plus the initial rounding) their standard
+    deviation per cell is at most sqrt(n + 1) sigma_1;
+  - u = rho u / rho: sigma_u <= sqrt(n + 1) sigma_1 (1 + |u|max) / rho_min;
+  - bounds: rms error <= 1.5 sigma, max over the 262144 cells <= 6 sigma
+    (a Gaussian maximum over that many cells is about 5 sigma);
+  - E_k and E(k) from the velocity error dv by Cauchy-Schwarz and Parseval
+    (u_hat normalised by 1/N^3): |dE_k| <= rho_max rms(u) rms(dv) +
+    rho_max rms(dv)^2 / 2 + rms(drho) max|u|^2 / 2, and the summed shell errors
+    sum_k |E_gpu(k) - E_o(k)| <= rms(u) rms(dv) + rms(dv)^2 / 2, with the
+    derived rms bounds for drho and dv;
+  - FP32 arithmetic on the GPU against FP64 in the oracle adds errors of
+    relative size 1e-7, far below these (FP32 storage: see test_gpu_parity).
+The measured errors are recorded (printed) for the design notes.
+"""
+import math
+
+import numpy as np
 import pytest
+
+from paper_2605_19796_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
+N_CELLS_SIDE, STEPS, NU = 64, 100, 1e-4
 
-def test_storage_precision():
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2605_19796_gb300 import build
+
+    build.build()
+    from paper_2605_19796_gb300 import lbm as _lbm
+
+    return _lbm
+
+
+@pytest.fixture(scope="module")
+def oracle_run(orc):
+    n = N_CELLS_SIDE
+    rho, u = inputs.hit_fields(n, k0=4.0, urms=0.04, seed=0)
+    f0 = orc.init_equilibrium(27, rho, u)
+    f = orc.run(f0, STEPS, closure=1, nu=NU, c_nu=0.035)
+    return rho, u, f0, f
+
+
+@pytest.mark.parametrize("storage,u_s", [("fp16", 2.0 ** -11), ("bf16", 2.0 ** -8)])
+def test_16bit_storage_against_fp64_oracle(lbm, orc, oracle_run, storage, u_s):
+    from oracle.spectrum import spectrum
+
+    rho, u, f0, fo = oracle_run
+    n = N_CELLS_SIDE
+    with lbm.Solver(27, (n, n, n), NU, closure="kcmp", storage=storage) as s:
+        assert s.launch_config["variant"] == 14  # the default launch of 16-bit storage
+        s.init_velocity(rho, u)
+        s.step(STEPS)
+        fg = s.get_populations()
+    rg, ug = orc.fields(fg)
+    ro, uo = orc.fields(fo)
+    _, w, _ = orc.lattice(27)
+    gnorm = max(np.sqrt(((f - w[:, None, None, None]) ** 2).sum(axis=0)).max() for f in (f0, fo))
+    sig1 = u_s * gnorm / math.sqrt(3.0)
+    sig_rho = math.sqrt(STEPS + 1) * sig1
+    umax = max(np.sqrt((uo ** 2).sum(axis=0)).max(), np.sqrt((u ** 2).sum(axis=0)).max())
+    sig_u = sig_rho * (1.0 + umax) / ro.min()
+    drho, du = rg - ro, ug - uo
+    rms = lambda a: float(np.sqrt(np.mean(a ** 2)))  # noqa: E731
+    dv_rms = float(np.sqrt(np.mean((du ** 2).sum(axis=0))))
+    res = {"rho_max": float(np.abs(drho).max()), "rho_rms": rms(drho), "u_max": float(np.abs(du).max()),
+           "u_rms": rms(du), "sig_rho": sig_rho, "sig_u": sig_u}
+    assert res["rho_rms"] <= 1.5 * sig_rho and res["rho_max"] <= 6 * sig_rho, res
+    assert res["u_rms"] <= 1.5 * sig_u and res["u_max"] <= 6 * sig_u, res
+    # kinetic energy and spectrum through the derived rms bounds
+    dv_b = 1.5 * math.sqrt(3.0) * sig_u  # rms of the 3-vector error
+    u_rms3 = float(np.sqrt(np.mean((uo ** 2).sum(axis=0))))
+    ek_g = float(np.mean(0.5 * rg * (ug ** 2).sum(axis=0)))
+    ek_o = float(np.mean(0.5 * ro * (uo ** 2).sum(axis=0)))
+    ek_b = ro.max() * u_rms3 * dv_b + ro.max() * dv_b ** 2 / 2 + 1.5 * sig_rho * umax ** 2 / 2
+    res["E_k_rel"] = abs(ek_g - ek_o) / ek_o
+    assert abs(ek_g - ek_o) <= ek_b, (res, ek_b)
+    eg, eo = spectrum(ug), spectrum(uo)
+    spec_b = u_rms3 * dv_b + dv_b ** 2 / 2
+    res["Ek_shell_abs_sum"] = float(np.abs(eg - eo).sum())
+    res["Ek_rel_l2"] = float(np.sqrt(((eg[1:] - eo[1:]) ** 2).sum() / (eo[1:] ** 2).sum()))
+    assert res["Ek_shell_abs_sum"] <= spec_b, (res, spec_b)
+    assert dv_rms > 0  # the storage rounding is visible
+    print(storage, "vs FP64 oracle, 64^3, 100 steps:", res)
+
+
+def test_storage_precision_ordering():
+    """FP32 < FP16 < BF16 against the FP64-storage GPU run on the same case
+    (the precision study's comparison), and FP32 velocity within 1e-6."""
     import torch
 
     assert torch.cuda.is_available()
@@ -20,9 +115,5 @@ def test_storage_precision():
 
     res = precision.run(n=64, steps=100)
     print(res)
-    urms = 0.04
     assert res["fp32"]["u_rms_err"] < 1e-6
-    assert res["fp16"]["u_rms_err"] < 1e-3 * urms
-    assert res["bf16"]["u_rms_err"] < 1e-2 * urms
     assert res["fp32"]["u_rms_err"] < res["fp16"]["u_rms_err"] < res["bf16"]["u_rms_err"]
-    assert res["bf16"]["E_k_rel_err"] < 1e-2

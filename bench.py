@@ -76,7 +76,7 @@ def log(*a):
 
 
 KERNEL_SOURCES = ("lbm_lattice.cuh", "lbm_mbarrier.cuh", "lbm_mlp_infer.cuh", "lbm_step.cuh", "lbm_step_split.cuh",
-                  "lbm_step_tma.cuh", "lbm_step_x2.cuh")
+                  "lbm_step_v4.cuh")
 
 
 def _code_only(text: str) -> str:

@@ -102,29 +102,30 @@ typedef struct {
                            learned closure, else 8)                                  */
     int zchunk;         /* tuning: z-planes per CTA march (0 = library default)      */
     int variant;        /* tuning: step-kernel variant, 0 = library default
-                           (FP32 storage: 12 on z-chunks of at most 16 planes
-                           for periodic D3Q27 with KC-MP or KC-RB, 13 for
-                           KC-RR, D3Q19 and walls with KC-MP; else 8 for
-                           periodic D3Q27 except the learned closure; else 1),
+                           (periodic D3Q27 with FP32/FP16/BF16 storage and
+                           BGK, KC-MP or KC-RB, nx % 8 == 0: 14, tiles
+                           128 x 8, or 64 x 16 for nx <= 64; else, for FP32
+                           storage, 12 on z-chunks of at most 16 planes for
+                           periodic D3Q27 with KC-MP or KC-RB, 13 for KC-RR,
+                           D3Q19 and walls; else 8 for periodic D3Q27 except
+                           the learned closure; else 1),
                            1 = register pull (every lattice, storage, closure
-                           and boundary), 4 = TMA-staged pipeline (FP32,
-                           periodic, BGK/KC-MP/KC-RB, nx % 32 == 0 and
-                           ny % tile_y == 0), 8 = register pull with a split
-                           arrive/wait barrier (BGK, KC-MP, KC-RB, KC-RR), 9 =
-                           two cells per thread on packed FP32 pairs (32-bit
-                           arithmetic, BGK, KC-MP, KC-RB), 12 = 8 with the
-                           source rows of the plane after next prefetched
-                           into L2, 13 = 8 with the own cell's pulls copied
-                           to shared memory by cp.async one plane ahead
-                           (FP32 and FP64 storage), 14 = four cells per thread
-                           with 128-bit (FP32) / 64-bit (16-bit) vector loads
-                           and stores, the pulls staged in shared memory by
-                           cp.async one plane ahead and the populations parked
-                           in tensor memory until their collision (periodic
-                           D3Q27, FP32/FP16/BF16 storage, BGK/KC-MP/KC-RB,
-                           nx % 8 == 0; tile_y 8: 128 x 8 tiles, 16: 64 x 16
-                           tiles; LBM_ERR_UNSUPPORTED otherwise); other
-                           values: LBM_ERR_ARG */
+                           and boundary), 8 = register pull with a split
+                           arrive/wait barrier (BGK, KC-MP, KC-RB, KC-RR), 12
+                           = 8 with the source rows of the plane after next
+                           prefetched into L2, 13 = 8 with the own cell's
+                           pulls copied to shared memory by cp.async one
+                           plane ahead (FP32 and FP64 storage), 14 = four
+                           cells per thread with 128-bit (FP32) / 64-bit
+                           (16-bit) vector loads and stores, the pulls staged
+                           in shared memory by cp.async one plane ahead and
+                           the populations parked in tensor memory until
+                           their collision (periodic D3Q27, FP32/FP16/BF16
+                           storage, BGK/KC-MP/KC-RB, nx % 8 == 0; tile_y 8:
+                           128 x 8 tiles, 16: 64 x 16 tiles;
+                           LBM_ERR_UNSUPPORTED otherwise); other values,
+                           among them the retired 2-7, 9, 10 and 11:
+                           LBM_ERR_ARG */
     int disable_graphs; /* nonzero: lbm_step launches kernels one by one instead of
                            replaying a captured CUDA graph                        */
 } lbm_config;

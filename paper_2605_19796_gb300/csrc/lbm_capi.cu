@@ -1,6 +1,5 @@
 // C ABI of liblbm (declared in include/lbm.h): handle lifetime, device
 // buffers, launches of the fused step kernel and of the auxiliary kernels.
-#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -80,8 +79,6 @@ struct lbm_handle {
     cudaStream_t cap_stream = nullptr;
     void* d_mlp = nullptr;           // packed network parameters (learned closure)
     bool mlp_set = false;
-    CUtensorMap tmap[2];             // TMA maps of f[0], f[1] (variant 4)
-    int tmap_tile = 0;               // tile height the maps were encoded for (0 = none)
     // host-pointer field transfers (lazy): two staging slots of stage_cells
     // cells, each rho [stage_cells] then u [3][stage_cells], a copy stream and,
     // per slot, "filled" and "drained" events
@@ -155,22 +152,8 @@ StepArgs step_args(const lbm_handle* h)
     a.flag = h->d_flag;
     a.fin = nullptr;
     a.fout = nullptr;
-    a.tmap_in = nullptr;
     a.mlp = h->d_mlp;
     return a;
-}
-
-// (re)encodes the TMA maps of both buffers for the handle's tile height
-cudaError_t ensure_tmaps(lbm_handle* h)
-{
-    if (h->variant != VAR_TMA || h->tmap_tile == h->tile_y) return cudaSuccess;
-    for (int k = 0; k < 2; ++k) {
-        cudaError_t e = encode_population_map(&h->tmap[k], h->f[k], h->cfg.nx, h->cfg.ny, h->cfg.nz, h->q,
-                                              h->cfg.nbatch, h->tile_y);
-        if (e != cudaSuccess) return e;
-    }
-    h->tmap_tile = h->tile_y;
-    return cudaSuccess;
 }
 
 // n step launches starting from buffer `cur`, alternating the ping-pong buffers
@@ -180,7 +163,6 @@ cudaError_t enqueue_steps(const lbm_handle* h, int n, int cur, cudaStream_t s)
     for (int k = 0; k < n; ++k) {
         a.fin = h->f[cur];
         a.fout = h->f[cur ^ 1];
-        a.tmap_in = &h->tmap[cur];
         cudaError_t e = launch_step(h->q, h->cfg.storage, h->cfg.closure, h->bc_kind, h->tile_y, h->variant, a,
                                     h->cfg.nbatch, s);
         if (e != cudaSuccess) return e;
@@ -204,7 +186,6 @@ cudaError_t step_graph(lbm_handle* h, int n, cudaGraphExec_t* out)
     if (!h->cap_stream) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return e;
     e = prepare_step(h->q, h->cfg.storage, h->cfg.closure, h->bc_kind, h->tile_y, h->variant);
-    if (e == cudaSuccess) e = ensure_tmaps(h);
     if (e != cudaSuccess) return e;
     e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
@@ -465,8 +446,8 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
     // registers without spilling (8-row tiles cap them at 128 and spill); the
     // rest 8-row tiles
     int tile_y = cfg->tile_y ? cfg->tile_y : (cfg->closure == LBM_LEARNED ? 4 : 8);
-    if (cfg->variant != VAR_DEFAULT && cfg->variant != VAR_REGISTER && cfg->variant != VAR_TMA && cfg->variant != VAR_SPLIT &&
-        cfg->variant != VAR_PAIR && cfg->variant != VAR_SPLIT_PF && cfg->variant != VAR_ASYNC && cfg->variant != VAR_VEC4)
+    if (cfg->variant != VAR_DEFAULT && cfg->variant != VAR_REGISTER && cfg->variant != VAR_SPLIT &&
+        cfg->variant != VAR_SPLIT_PF && cfg->variant != VAR_ASYNC && cfg->variant != VAR_VEC4)
         return fail(LBM_ERR_ARG, "unknown kernel variant");
     int variant = cfg->variant;
     // measured defaults (512^3 and ensemble timings): periodic D3Q27 with 32- or
@@ -511,8 +492,6 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
     }
     if (variant == VAR_VEC4 && !vec4_shape_ok(cfg->nx))
         return fail(LBM_ERR_UNSUPPORTED, "the four-cell variant needs nx % 8 == 0");
-    if (variant == VAR_TMA && !tma_shape_ok(cfg->nx, cfg->ny, tile_y))
-        return fail(LBM_ERR_UNSUPPORTED, "the TMA variant needs nx % 32 == 0 and ny % tile_y == 0");
     if (!step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, variant))
         return fail(LBM_ERR_UNSUPPORTED, "this lattice/storage/closure/boundary/tile/variant combination is not built");
     if (cfg->zchunk < 0) return fail(LBM_ERR_ARG, "zchunk must be >= 0");
@@ -556,7 +535,6 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
                     std::string("device allocation failed: ") + cudaGetErrorString(e));
     }
     e = prepare_step(h->q, cfg->storage, cfg->closure, bc_kind, tile_y, variant);
-    if (e == cudaSuccess) e = ensure_tmaps(h);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->d_nu, h->nu.data(), sizeof(double) * cfg->nbatch, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flag, 0, sizeof(unsigned int), h->stream);
@@ -640,8 +618,7 @@ int lbm_step(lbm_handle* h, int nsteps)
         left -= n;
     }
     if (left > 0) {
-        cudaError_t e = ensure_tmaps(h);
-        if (e == cudaSuccess) e = enqueue_steps(h, left, h->cur, h->stream);
+        cudaError_t e = enqueue_steps(h, left, h->cur, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
         h->cur ^= (left & 1);
         h->steps += left;
@@ -654,7 +631,7 @@ int lbm_autotune(lbm_handle* h, int trials)
 {
     if (int rc = check_handle(h)) return rc;
     if (trials < 1) trials = 3;
-    static const int kVariants[] = {VAR_REGISTER, VAR_SPLIT, VAR_SPLIT_PF, VAR_ASYNC, VAR_PAIR, VAR_TMA, VAR_VEC4};
+    static const int kVariants[] = {VAR_REGISTER, VAR_SPLIT, VAR_SPLIT_PF, VAR_ASYNC, VAR_VEC4};
     static const int kTiles[] = {4, 8, 16};
     static const int kChunks[] = {8, 16, 32, 64, 128};
     const int v0 = h->variant, t0 = h->tile_y, z0 = h->zchunk;
@@ -667,7 +644,6 @@ int lbm_autotune(lbm_handle* h, int trials)
         for (int ty : kTiles) {
             if (e != cudaSuccess) break;
             if (!step_supported(h->q, h->cfg.storage, h->cfg.closure, h->bc_kind, ty, v)) continue;
-            if (v == VAR_TMA && !tma_shape_ok(h->cfg.nx, h->cfg.ny, ty)) continue;
             if (v == VAR_VEC4 && !vec4_shape_ok(h->cfg.nx)) continue;
             e = prepare_step(h->q, h->cfg.storage, h->cfg.closure, h->bc_kind, ty, v);
             for (int zc : kChunks) {
@@ -676,7 +652,6 @@ int lbm_autotune(lbm_handle* h, int trials)
                 h->variant = v;
                 h->tile_y = ty;
                 h->zchunk = zc < h->cfg.nz ? zc : h->cfg.nz;
-                if (e == cudaSuccess) e = ensure_tmaps(h);
                 // state-preserving timing: every launch reads the current buffer and
                 // writes the other one, so the state the caller sees is unchanged
                 e = enqueue_steps(h, 1, h->cur, h->stream);
@@ -704,7 +679,6 @@ int lbm_autotune(lbm_handle* h, int trials)
     h->variant = bv;
     h->tile_y = bt;
     h->zchunk = bz;
-    if (e == cudaSuccess) e = ensure_tmaps(h);
     clear_graphs(h);
     if (e != cudaSuccess) {
         h->variant = v0;

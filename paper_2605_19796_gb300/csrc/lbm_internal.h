@@ -26,7 +26,6 @@ struct StepArgs {
     double cnu_delta;       // C_nu * Delta
     double force[3];        // body force density (channel); zero otherwise
     unsigned int* flag;     // bit 0: non-finite density/velocity seen, bit 1: a bounded wait timed out
-    const void* tmap_in;    // host address of the CUtensorMap of fin (TMA variant only)
     const void* mlp;        // packed network parameters (learned closure only), MlpLayout::BYTES
 };
 
@@ -38,18 +37,17 @@ void mlp_pack(const float* params, const float* stats, unsigned char* out);
 // one-CTA kernel whose bounded mbarrier wait runs out (the timeout error path)
 cudaError_t launch_wait_selftest(unsigned int* flag, long long polls, cudaStream_t s);
 
-// Step-kernel variants: register pull (lbm_step.cuh), TMA staging
-// (lbm_step_tma.cuh), split arrive/wait barrier (lbm_step_split.cuh), two cells
-// per thread on packed FP32 pairs (lbm_step_x2.cuh).  Values 2, 3, 5, 6, 7, 10
-// and 11 belonged to measured alternatives that were retired; they are refused.
+// Step-kernel variants: register pull (lbm_step.cuh), split arrive/wait
+// barrier (lbm_step_split.cuh).  Values 2-7, 9, 10 and 11 belonged to measured
+// alternatives that were retired (4: TMA-staged pipeline, 9: two cells per
+// thread on packed FP32 pairs; both slower than variants 8, 12, 13 and 14 in
+// every case measured); they are refused.
 // Variant 14: four cells per thread with vector access and a tensor-memory
 // stash (lbm_step_v4.cuh), periodic D3Q27, 32- and 16-bit storage, nx % 8 == 0.
 enum Variant {
     VAR_DEFAULT = 0,
     VAR_REGISTER = 1,
-    VAR_TMA = 4,
     VAR_SPLIT = 8,
-    VAR_PAIR = 9,
     VAR_SPLIT_PF = 12,
     VAR_ASYNC = 13,
     VAR_VEC4 = 14
@@ -58,11 +56,6 @@ enum Variant {
 // variant 14: box shapes it is built for (nx a multiple of 8)
 bool vec4_shape_ok(int nx);
 
-// TMA variant: tile heights it is built for, and the tensor map of a population
-// buffer (4D: x, y, z, population-of-box; box 40 x (tile_y + 2) x 1 x 1)
-bool tma_shape_ok(int nx, int ny, int tile_y);
-cudaError_t encode_population_map(void* map_out /*CUtensorMap*/, const void* buf, int nx, int ny, int nz, int q,
-                                  int nbatch, int tile_y);
 
 // Host-side launchers (lbm_step_*.cu).  Return cudaSuccess or the launch error.
 // tile_y selects the CTA tile height (instantiated values: 4, 8, 16).

@@ -3,10 +3,9 @@
 // (all closures, both boundary modes, the tile heights the tuner may pick), so
 // the units compile in parallel.
 //
-// Variants: 1 register pull (step_kernel, every closure and storage), 4 TMA
-// staging (FP32, periodic), 8 split arrive/wait barrier (step_kernel_sb), 9
-// two cells per thread on packed FP32 pairs (step_kernel_x2, 32-bit arithmetic),
-// 12 variant 8 with L2 prefetches, 13 variant 8 with the own pulls copied to the
+// Variants: 1 register pull (step_kernel, every closure and storage), 8 split
+// arrive/wait barrier (step_kernel_sb), 12 variant 8 with L2 prefetches, 13
+// variant 8 with the own pulls copied to the
 // stash by cp.async one plane ahead (32- and 64-bit storage), 14 four cells per
 // thread with vector access and a tensor-memory stash (step_kernel_v4; periodic
 // D3Q27, 32- and 16-bit storage).
@@ -14,9 +13,7 @@
 
 #include "lbm_step.cuh"
 #include "lbm_step_split.cuh"
-#include "lbm_step_tma.cuh"
 #include "lbm_step_v4.cuh"
-#include "lbm_step_x2.cuh"
 
 #include <type_traits>
 
@@ -28,21 +25,6 @@ template <int Q, typename S>
 cudaError_t launch_step_qs(int closure, int bc, int ty, int variant, const StepArgs* a, int nbatch, cudaStream_t s)
 {
     constexpr bool R32 = sizeof(typename StoreTraits<S>::R) == 4;
-    if (variant == VAR_TMA) {
-        if constexpr (std::is_same_v<S, float>) {
-#define LBM_TMA_CASE(CL, TYV, NSV)                                                                          \
-    if (closure == CL && bc == BC_PERIODIC && ty == TYV)                                                \
-        return a ? launch_step_tma_t<Q, CL, TYV, NSV>(*a, nbatch, s)                                    \
-                 : (nbatch < 0 ? prepare_tma_t<Q, CL, TYV, NSV>() : cudaSuccess);
-            LBM_TMA_CASE(CL_BGK, 8, 4)
-            LBM_TMA_CASE(CL_KCMP, 8, 4)
-            LBM_TMA_CASE(CL_KCRB_H, 8, 4)
-            LBM_TMA_CASE(CL_KCRB_RAW, 8, 4)
-            LBM_TMA_CASE(CL_KCMP, 4, 3)
-#undef LBM_TMA_CASE
-        }
-        return cudaErrorNotSupported;
-    }
     if (variant == VAR_VEC4) {
         // tile_y 8: 128 x 8 tiles (one row per warp); 16: 64 x 16 tiles (two rows per warp)
         if constexpr (Q == 27 && R32) {
@@ -119,22 +101,6 @@ cudaError_t launch_step_qs(int closure, int bc, int ty, int variant, const StepA
                 LBM_AS_CASE(CL_KCRR, BC_PERIODIC, 8)
             }
 #undef LBM_AS_CASE
-        }
-        return cudaErrorNotSupported;
-    }
-    if (variant == VAR_PAIR) {
-        if constexpr (R32) {
-#define LBM_X2_CASE(CL, BCV, TYV)                                                               \
-    if (closure == CL && bc == BCV && ty == TYV)                                                \
-        return a ? launch_x2_t<Q, S, CL, BCV, TYV>(*a, nbatch, s) : (nbatch < 0 ? prepare_x2_t<Q, S, CL, BCV, TYV>() : cudaSuccess);
-            LBM_X2_CASE(CL_BGK, BC_PERIODIC, 8)
-            LBM_X2_CASE(CL_KCMP, BC_PERIODIC, 8)
-            LBM_X2_CASE(CL_KCRB_H, BC_PERIODIC, 8)
-            LBM_X2_CASE(CL_KCRB_RAW, BC_PERIODIC, 8)
-            LBM_X2_CASE(CL_BGK, BC_WALLS_Y, 8)
-            LBM_X2_CASE(CL_KCMP, BC_WALLS_Y, 8)
-            LBM_X2_CASE(CL_KCMP, BC_PERIODIC, 4)
-#undef LBM_X2_CASE
         }
         return cudaErrorNotSupported;
     }

@@ -72,7 +72,7 @@ def _cfg(lbm, **kw):
     (dict(variant=2), -1), (dict(variant=6), -1), (dict(variant=11), -1), (dict(variant=15), -1),
     (dict(variant=14, nx=44), -6), (dict(variant=14, storage=0), -6), (dict(variant=14, closure=4), -6),
     (dict(variant=13, storage=2), -6),
-    (dict(variant=9, storage=0), -6), (dict(variant=4, nx=40), -6),
+    (dict(variant=9), -1), (dict(variant=4), -1),
 ])
 def test_bad_config_rejected_before_device_work(lbm, kw, code):
     cfg, nu = _cfg(lbm, **kw)

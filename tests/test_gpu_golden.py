@@ -98,14 +98,23 @@ def test_kcrb_sensitivity_tgv64_matches_app_g(lbm):
 
 def test_kcrr_against_hermite_kcrb_tgv64_matches_app_g(lbm):
     """The same case with KC-RR (App. G's Hermite-consistent reference):
-    printed 0.061 % (E_k) and 0.314 % (Z) against Hermite KC-RB.  The bound
-    (25 %) is wider than the oracle test's 10 %, since this small difference
-    of two GPU trajectories also carries their rounding-order drift from the
-    oracle's."""
+    printed 0.061 % (E_k) and 0.314 % (Z) against Hermite KC-RB.  The
+    difference is small (E_k: at most 1.6e-5 of u0^2), so each trajectory's
+    own bound does not fix it; the GPU's difference r - h is therefore held
+    sample by sample to the oracle's stored difference, within 5 % of that
+    difference's largest magnitude.  The oracle's maxima (0.0623 % and
+    0.310 %) lie within 2.2 % of the printed values, so that puts the GPU's
+    within about 7 % of them; 10 % is asserted."""
     gold = _gold()
+    with open(os.path.join(GOLDEN, "kcrb_sensitivity_tgv64_oracle.json")) as fp:
+        stored = json.load(fp)
     traj = _runs(lbm, ("hermite", "kcrr"))
     for key, printed in (("ek", gold["kcrr_vs_hermite_ek_max_rel_diff_percent"]),
                          ("z", gold["kcrr_vs_hermite_z_max_rel_diff_percent"])):
         h, r = traj["hermite"][key], traj["kcrr"][key]
+        d_o = np.array(stored["kcrr"][key]) - np.array(stored["hermite"][key])
+        drift = float(np.abs((r - h) - d_o).max() / np.abs(d_o).max())
+        print(key, "GPU r-h against the oracle's, largest deviation / max|d|:", drift)
+        assert drift <= 0.05, (key, drift)
         got = 100 * float(np.max(np.abs(r - h) / np.abs(h)))
-        assert got == pytest.approx(printed, rel=0.25), (key, got)
+        assert got == pytest.approx(printed, rel=0.10), (key, got)

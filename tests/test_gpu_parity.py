@@ -178,18 +178,18 @@ def test_launch_shapes_fp32_consistent(lbm, orc, zchunk, tile_y):
 
 @pytest.mark.parametrize("closure", ["bgk", "kcmp", "kcrb_hermite", "kcrb_raw"])
 def test_variants_agree_fp32(lbm, orc, closure):
-    """The register-pull (1), split-barrier (8) and packed-pair (9) step kernels
-    perform the same per-cell arithmetic: FP32 results agree to FP32 rounding on
+    """The register-pull (1), split-barrier (8) and asynchronous-copy (13) step
+    kernels perform the same per-cell arithmetic: FP32 results agree to FP32 rounding on
     a ragged box; within one variant the z-chunking does not change a bit."""
     shape = (45, 19, 23)
     rho, u = inputs.hit_fields(0, k0=3.0, urms=0.07, seed=8, shape=shape)
     res = {}
-    for var, zc in [(1, 0), (8, 0), (8, 5), (9, 0), (9, 5), (13, 0), (13, 5)]:
+    for var, zc in [(1, 0), (8, 0), (8, 5), (13, 0), (13, 5)]:
         with lbm.Solver(27, shape, 2e-5, closure=closure, storage="fp32", variant=var, zchunk=zc) as s:
             s.init_velocity(rho, u)
             s.step(8)
             res[(var, zc)] = s.get_populations()
-    for v in (8, 9, 13):
+    for v in (8, 13):
         assert rel(res[(v, 0)], res[(1, 0)]) < 1e-6, v
         assert np.array_equal(res[(v, 0)], res[(v, 5)]), v
 
@@ -429,7 +429,7 @@ def test_autotune_keeps_state_and_result(lbm, orc):
         s.step(2)
         before = s.get_populations()
         cfg = s.autotune(trials=2)
-        assert cfg["variant"] in (1, 4, 8, 9, 12, 13, 14) and cfg["tile_y"] in (4, 8, 16) and 1 <= cfg["zchunk"] <= 128
+        assert cfg["variant"] in (1, 8, 12, 13, 14) and cfg["tile_y"] in (4, 8, 16) and 1 <= cfg["zchunk"] <= 128
         assert np.array_equal(before, s.get_populations())
         s.step(5)
         tuned = s.get_populations()
@@ -457,34 +457,6 @@ def test_ensemble_and_channel_launch_through_graph(lbm, orc):
     F = (1e-5, 0.0, 0.0)
     (fg, fo, _), = _run_pair(lbm, orc, 27, (16, 11, 6), rho, u, 2e-3, "kcmp", 6, bc=(0, 1, 0), F=F)
     assert rel(fg, fo) < TOL64
-
-
-@pytest.mark.parametrize("shape,nbatch", [((64, 16, 12), 1), ((32, 8, 5), 1), ((96, 24, 7), 2), ((64, 64, 64), 1)])
-@pytest.mark.parametrize("closure", ["bgk", "kcmp", "kcrb_hermite", "kcrb_raw"])
-def test_tma_variant_matches(lbm, orc, shape, nbatch, closure):
-    """The TMA-staged kernel (variant 4: periodic images patched on edge tiles,
-    single-tile boxes where both edges wrap, several boxes) agrees with the
-    register-pull kernel to FP32 rounding and with the FP64 oracle in velocity."""
-    seeds = [30 + b for b in range(nbatch)]
-    fields = [inputs.hit_fields(0, k0=2.0, urms=0.06, seed=sd, shape=shape) for sd in seeds]
-    rho = np.stack([f[0] for f in fields])
-    u = np.stack([f[1] for f in fields], axis=1)
-    nus = np.array([3e-5, 2e-4][:nbatch])
-    res = {}
-    for var in (1, 4):
-        with lbm.Solver(27, shape, nus, closure=closure, storage="fp32", variant=var, nbatch=nbatch) as s:
-            assert s.launch_config["variant"] == var
-            s.init_velocity(rho, u)
-            s.step(6)
-            res[var] = s.get_populations()
-    assert rel(res[4], res[1]) < 1e-6
-    f4 = res[4] if nbatch > 1 else res[4][None]
-    for b in range(nbatch):
-        fo = orc.run(orc.init_equilibrium(27, fields[b][0], fields[b][1]), 6, closure=CL[closure], nu=nus[b],
-                     c_nu=CNU[closure])
-        _, ug = orc.fields(f4[b])
-        _, uo = orc.fields(fo)
-        assert np.abs(ug - uo).max() < 1e-6
 
 
 def test_default_variant_selection(lbm):
@@ -517,12 +489,9 @@ def test_default_variant_selection(lbm):
     for q, closure, want in ((27, "kcmp", 13), (19, "kcmp", 13), (27, "kcrb_hermite", 1), (27, "bgk", 1)):
         with lbm.Solver(q, (40, 32, 16), 1e-4, closure=closure, storage="fp32", bc=(0, 1, 0)) as s:
             assert s.launch_config["variant"] == want, (q, closure, "walls")
-    with lbm.Solver(27, (64, 32, 16), 1e-4, closure="kcmp", storage="fp32", variant=4) as s:
-        assert s.launch_config["variant"] == 4
-    with pytest.raises(lbm.LbmError):
-        lbm.Solver(27, (40, 32, 16), 1e-4, closure="kcmp", storage="fp32", variant=4)
-    with pytest.raises(lbm.LbmError):
-        lbm.Solver(27, (40, 32, 16), 1e-4, closure="kcmp", storage="fp64", variant=9)
+    for retired in (4, 9):  # the TMA-staged and packed-pair kernels are retired
+        with pytest.raises(lbm.LbmError):
+            lbm.Solver(27, (64, 32, 16), 1e-4, closure="kcmp", storage="fp32", variant=retired)
     with pytest.raises(lbm.LbmError):
         lbm.Solver(27, (40, 32, 16), 1e-4, closure="kcmp", storage="fp64", variant=14)
 
@@ -562,9 +531,8 @@ def test_load_schedule_variants(lbm, orc, storage, closure):
     """Variant 8 (halo and own loads together, split arrive/wait barrier) only
     reschedules the loads and synchronisation of the register pull (variant 1);
     variant 12 adds L2 prefetches to it, variant 13 (32- and 64-bit storage)
-    copies the own pulls to shared memory asynchronously one plane ahead;
-    variant 9 runs the same arithmetic on
-    packed FP32 pairs, two cells per thread (not built for KC-RR).  On a ragged box with
+    copies the own pulls to shared memory asynchronously one plane ahead.  On a
+    ragged box with
     two boxes and several z-chunkings (one and two planes per CTA exercise the
     pipelines' start and drain): FP64 matches the oracle to 1e-12, FP32 matches
     variant 1 to FP32 rounding, 16-bit storage in rho and u to 1e-5 (one 16-bit
@@ -574,7 +542,7 @@ def test_load_schedule_variants(lbm, orc, storage, closure):
     rho = np.stack([f[0] for f in fields])
     u = np.stack([f[1] for f in fields], axis=1)
     nus = np.array([2e-5, 1e-4])
-    variants = (8, 12) if storage == "fp64" or closure == "kcrr" else (8, 9, 12)
+    variants = (8, 12)
     if storage in ("fp32", "fp64"):
         variants += (13,)
     res = {}
@@ -609,7 +577,7 @@ def test_load_schedule_variants(lbm, orc, storage, closure):
 @pytest.mark.parametrize("shape", [(16, 11, 9), (16, 17, 7)])
 @pytest.mark.parametrize("q", [19, 27])
 def test_variants_channel(lbm, orc, q, shape):
-    """Variants 8, 9, 12 and 13 with bounce-back walls and a body force: FP64
+    """Variants 8, 12 and 13 with bounce-back walls and a body force: FP64
     (variants 8 and 13) against the oracle, FP32 against variant 1 to FP32
     rounding.  With ny = 17 the last tile holds only the wall row y = ny - 1,
     whose one-sided stencil reads the outer halo row two below it."""
@@ -623,13 +591,13 @@ def test_variants_channel(lbm, orc, q, shape):
     fo = orc.run(orc.init_equilibrium(q, rho, u), 6, closure=1, nu=2e-3, c_nu=0.035, bc=(0, 1, 0), F=F)
     assert rel(fg, fo) < TOL64
     out = {}
-    for var in (1, 8, 9, 12, 13):
+    for var in (1, 8, 12, 13):
         with lbm.Solver(q, shape, 2e-3, closure="kcmp", storage="fp32", bc=(0, 1, 0), force=F,
                         variant=var) as s:
             s.init_velocity(rho, u)
             s.step(6)
             out[var] = s.get_populations()
-    for var in (8, 9, 12, 13):
+    for var in (8, 12, 13):
         assert rel(out[var], out[1]) < 1e-6, var
     for var, zc in ((1, 2), (8, 2), (13, 2), (13, 3)):
         with lbm.Solver(q, shape, 2e-3, closure="kcmp", storage="fp64", bc=(0, 1, 0), force=F, variant=var,

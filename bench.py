@@ -257,20 +257,35 @@ def oracle_sample(wl: dict):
     return f, run, shape[0] * shape[1] * shape[2], desc
 
 
-def cpu_baseline(wl: dict, budget_s: float = 25.0, steps: int = 0):
-    """The FP64 oracle as it stands, on the host cores, on a bounded sample of the workload."""
+def cpu_baseline(wl: dict, budget_s: float = 25.0, steps: int = 0, single_budget_s: float = 8.0):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of
+    the workload; then the same sample on one thread (single_thread)."""
     import oracle
 
     f, run, cells, desc = oracle_sample(wl)
-    t = time.perf_counter()
-    f = run(f, 1)
-    t1 = time.perf_counter() - t
-    k = steps or max(1, min(5000, int(budget_s / max(t1, 1e-6))))
-    t = time.perf_counter()
-    run(f, k)
-    dt = time.perf_counter() - t
-    return {"value": cells * k / dt / 1e6, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{desc} (D3Q{wl['q']}, {wl['closure']}, FP64 oracle), {k} steps, {dt:.1f} s"}
+
+    def timed(f, budget):
+        t = time.perf_counter()
+        f = run(f, 1)
+        t1 = time.perf_counter() - t
+        k = steps or max(1, min(5000, int(budget / max(t1, 1e-6))))
+        t = time.perf_counter()
+        run(f, k)
+        return k, time.perf_counter() - t
+
+    cores = oracle.num_threads()
+    k, dt = timed(f, budget_s)
+    out = {"value": cells * k / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+           "sample": f"{desc} (D3Q{wl['q']}, {wl['closure']}, FP64 oracle), {k} steps, {dt:.1f} s"}
+    if single_budget_s > 0 and cores > 1:
+        oracle.set_num_threads(1)
+        try:
+            k1, dt1 = timed(f, single_budget_s)
+        finally:
+            oracle.set_num_threads(cores)
+        out["single_thread"] = {"value": cells * k1 / dt1 / 1e6, "unit": "MLUPS", "cores": 1,
+                                "sample": f"the same sample, {k1} steps, {dt1:.1f} s"}
+    return out
 
 
 def run_reference(args, wl, rank):
@@ -295,6 +310,85 @@ def run_reference(args, wl, rank):
     print(json.dumps(out), flush=True)
 
 
+FORMS = ("hit512_d3q27_fp16_kcmp", "hit512_d3q27_bf16_kcmp", "hit256_d3q27_fp32_learned")
+
+
+def time_form(lbm, wl: dict, stream, steps: int, warmup: int, peak: float) -> dict:
+    """CUDA-event MLUPS of one workload's step (the same K-step graph replay as
+    the headline) and its fraction of the HBM roofline."""
+    import torch
+
+    from paper_2605_19796_gb300 import inputs
+
+    n = wl["n"]
+    rho_d, u_d = inputs.hit_fields(n, k0=wl["k0"], urms=wl["urms"], seed=0, device="cuda")
+    torch.cuda.synchronize()
+    with lbm.Solver(wl["q"], (n, n, n), wl["nu"], closure=wl["closure"], storage=wl["storage"],
+                    stream=stream) as s:
+        s.init_velocity_device(rho_d, u_d)
+        del rho_d, u_d
+        src = None
+        if wl["closure"] == "learned":
+            w = learned_weights()
+            s.set_learned_closure(w["params"], w["stats"])
+            src = w["source"]
+        s.step(warmup)
+        s.step(steps)  # graph capture outside the timed region
+        s.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        s.step(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        s.synchronize()
+        t = ev0.elapsed_time(ev1) * 1e-3
+        cells = n ** 3 * steps
+        gbs = 2 * wl["q"] * ELEM[wl["storage"]] * cells / t / 1e9
+        out = {"mlups": cells / t / 1e6, "ms_per_step": t / steps * 1e3, "hbm_gbs": gbs, "hbm_frac": gbs / peak,
+               "algorithmic_bytes_per_cell": 2 * wl["q"] * ELEM[wl["storage"]], "launch": s.launch_config}
+        if src:
+            out["network"] = src
+        return out
+
+
+def measure_forms(lbm, stream, steps: int, warmup: int, peak: float) -> dict:
+    """The 16-bit storage forms (512^3 KC-MP) and the learned closure (256^3)
+    beside the FP32 headline, each with the error it carries, measured in the
+    same run on the GPU:
+      - 16-bit storage: against the FP64-storage run of the same library (whose
+        every population matches the FP64 oracle to 1e-12 in the parity tests)
+        on 64^3 HIT (k0 = 4, u_rms = 0.04, nu = 1e-4, KC-MP), 100 steps;
+      - learned closure: a posteriori, 128^3 coarse LES for 150 coarse steps from
+        the box-filtered state of a 512^3 KC-MP run at step 400 (held-out seed
+        99), E(k) relative L2 error over shells 1 .. 63 against the filtered fine
+        run, beside KC-MP's on the same case (C_nu = 0.035 for both)."""
+    from paper_2605_19796_gb300 import learned, precision
+
+    out = {}
+    for name in FORMS:
+        log(f"[bench] form {name}")
+        out[name] = time_form(lbm, WORKLOADS[name], stream, steps, warmup, peak)
+    # both studies run on torch's default stream (the solvers' legacy default stream)
+    prec = precision.run(n=64, steps=100, storages=("fp64", "fp16", "bf16"))
+    for st in ("fp16", "bf16"):
+        out[f"hit512_d3q27_{st}_kcmp"]["error"] = {
+            k: prec[st][k] for k in ("u_rms_err", "u_max_err", "rho_rms_err", "E_k_rel_err", "spectrum_rel_l2")}
+        out[f"hit512_d3q27_{st}_kcmp"]["error"]["against"] = (
+            "FP64-storage run, 64^3 HIT k0 = 4, u_rms = 0.04, nu = 1e-4, KC-MP, 100 steps")
+    w = learned_weights()
+    t0 = time.perf_counter()
+    ap = learned.a_posteriori(w["params"], w["stats"], n_fine=512, factor=4, seed=99, t0=400, coarse_steps=150,
+                              closures=("kcmp", "learned"))
+    out["hit256_d3q27_fp32_learned"]["error"] = {
+        "spectrum_rel_l2": ap["learned"]["spectrum_rel_l2"], "kcmp_spectrum_rel_l2": ap["kcmp"]["spectrum_rel_l2"],
+        "dissipation": ap["learned"]["dissipation"], "kcmp_dissipation": ap["kcmp"]["dissipation"],
+        "filtered_fine_dissipation": ap["filtered_fine"]["dissipation"],
+        "against": "box-filtered 512^3 KC-MP run (factor 4), held-out seed 99, 150 coarse steps from fine step 400",
+        "seconds": round(time.perf_counter() - t0, 1)}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -304,6 +398,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the 16-bit storage and learned-closure lines of the default run")
     ap.add_argument("--tile-y", type=int, default=0)
     ap.add_argument("--zchunk", type=int, default=0)
     ap.add_argument("--variant", type=int, default=0)
@@ -487,6 +583,9 @@ def main():
     if not rep.root:
         rep.close()
         return
+    forms = None
+    if not args.no_forms and world == 1 and args.workload == DEFAULT_WORKLOAD:
+        forms = measure_forms(lbm, stream, args.steps, args.warmup, peak)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(wl)
@@ -503,6 +602,8 @@ def main():
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clocks,
         "kernel_ms": {"mean": sum(per) / len(per)},
     }
+    if forms is not None:
+        out["forms"] = forms
     print(json.dumps(out), flush=True)
     rep.close()
 

@@ -134,9 +134,22 @@ typedef struct {
  * FP32 storage, periodic, no force.  cfg->nu must still be set. */
 void lbm_config_default(lbm_config* cfg);
 
-/* Creates a solver.  Allocates two population buffers (ping-pong) of
- * nbatch*q*nx*ny*nz elements each plus small control buffers on the current
- * CUDA device.  On failure *out is NULL and nothing is leaked. */
+/* Creates a solver for the LES of App. F.1: the lattice (App. F, velocity
+ * space discretization), the per-box relaxation time tau_hat = nu/theta + 1/2
+ * (Eq. omega_t_discrete), the closure and its C_nu and Delta (Eq.
+ * nu_t_sharp_closure; KC-MP App. F.3, KC-RB App. F.2, KC-RR App. F.4), the
+ * storage format, the boundaries and the body force are fixed here; the
+ * state starts at rest (rho = 1, u = 0).
+ * cfg: host, read during the call only (cfg->nu is copied).  Allocates two
+ * population buffers (ping-pong) of nbatch*q*nx*ny*nz elements each plus small
+ * control buffers on the current CUDA device; the handle owns them.
+ * Returns LBM_OK; LBM_ERR_ARG for a malformed configuration (bad sizes,
+ * lattice, closure, storage, nu <= 0, C_nu < 0, Delta <= 0, a retired or
+ * unknown variant, a box of 2^31 cells or more),
+ * LBM_ERR_UNSUPPORTED for a combination that is not built (KC-RR on D3Q19,
+ * walls on x or z, a force without walls, a variant not built for the box),
+ * LBM_ERR_OOM, LBM_ERR_CUDA.  On failure *out is NULL and nothing is
+ * leaked. */
 int lbm_create(const lbm_config* cfg, lbm_handle** out);
 
 /* Frees everything the handle owns; NULL is ignored. */
@@ -159,12 +172,24 @@ int lbm_init_velocity_f32(lbm_handle* h, const float* rho, const float* u);
 /* As lbm_init_velocity with device pointers (FP64, same layouts); enqueue only. */
 int lbm_init_velocity_device(lbm_handle* h, const double* rho_dev, const double* u_dev);
 
-/* Advances every box by nsteps time steps (one fused kernel launch per step).
+/* Advances every box by nsteps time steps of App. F.1 (one fused kernel
+ * launch per step).  Each step pull-streams the stored post-collision
+ * populations (Eq. streaming; halfway bounce-back on wall axes), takes the
+ * moments (step 1, with the half-force shift when a force is set), the
+ * equilibrium (step 2, Eq. discrete_equilibrium), the finite-difference
+ * strain (step 3, Eqs. fd, strain_rate_discrete, fd_boundary_lower/upper),
+ * the closure's SGS carrier and trace (step 4), the clipped rate (step 5, Eq.
+ * omega_sgs_operational) and the two-rate relaxation (step 6, Eq.
+ * operational_two_rate_update, with Guo's source when a force is set), and
+ * stores the new post-collision populations into the other buffer (step 7).
  * A call with nsteps >= 2 captures its nsteps launches once into a CUDA graph
  * (cached per step count and buffer parity, up to 4 graphs per handle) and
  * replays it as one graph launch (unless cfg.disable_graphs).  Enqueue only;
- * errors detected on the device (non-finite fields) are reported by the next
- * lbm_moments / lbm_diagnostics / lbm_synchronize. */
+ * errors detected on the device (non-finite fields, a bounded wait that gave
+ * up) are reported by the next lbm_moments / lbm_diagnostics /
+ * lbm_synchronize.  Returns LBM_OK; LBM_ERR_ARG for nsteps < 0 or a NULL
+ * handle, LBM_ERR_ARG for the learned closure without a network installed,
+ * LBM_ERR_CUDA when a launch fails.  nsteps = 0 does nothing. */
 int lbm_step(lbm_handle* h, int nsteps);
 
 /* Times the built step-kernel variants, tile heights and z-chunks on the

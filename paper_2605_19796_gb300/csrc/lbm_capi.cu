@@ -457,7 +457,9 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
     // pull with asynchronous copies (13); periodic D3Q27 otherwise (FP64) takes
     // the split-barrier pull (8) and the rest, the learned closure included (its
     // register pull on 4-row tiles evaluates the network for both halves of a
-    // warp at once, 256^3), the register pull (1).
+    // warp at once: 8.44 GLUPS at 256^3, against 8.32 for the four-cell kernel
+    // on 64 x 16 tiles, whose warps run the network one 16-row tile at a time),
+    // the register pull (1).
     // lbm_autotune may pick another launch for a given box
     bool short_chunks = false, vec4_chunks = false;
     if (variant == VAR_DEFAULT) {
@@ -516,7 +518,7 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
     // the learned closure's network-heavy CTAs balance better over about twice
     // as many, half as long chunks (256^3, register pull on 4-row tiles: 26
     // planes 8.43 GLUPS, 52 planes 8.28, 16 planes 8.18)
-    if (!cfg->zchunk && cfg->closure == LBM_LEARNED) {
+    if (!cfg->zchunk && cfg->closure == LBM_LEARNED && !vec4_chunks) {
         int zc = (h->zchunk + 1) / 2;
         if (zc < 4) zc = 4;
         if (zc < h->zchunk) h->zchunk = zc;

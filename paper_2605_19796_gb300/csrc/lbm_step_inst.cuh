@@ -8,7 +8,7 @@
 // variant 8 with the own pulls copied to the
 // stash by cp.async one plane ahead (32- and 64-bit storage), 14 four cells per
 // thread with vector access and a tensor-memory stash (step_kernel_v4; periodic
-// D3Q27, 32- and 16-bit storage).
+// D3Q27, 32- and 16-bit storage; BGK, KC-MP, KC-RB and the learned closure).
 #pragma once
 
 #include "lbm_step.cuh"
@@ -39,6 +39,12 @@ cudaError_t launch_step_qs(int closure, int bc, int ty, int variant, const StepA
             LBM_V4_CASE(CL_KCMP, 16, 16)
             LBM_V4_CASE(CL_KCRB_H, 16, 16)
             LBM_V4_CASE(CL_KCRB_RAW, 16, 16)
+            // the learned closure's network block and exchanges fit beside the
+            // FP32 staging area of 64 x 16 tiles only
+            LBM_V4_CASE(CL_LEARNED, 16, 16)
+            if constexpr (sizeof(S) == 2) {
+                LBM_V4_CASE(CL_LEARNED, 8, 32)
+            }
 #undef LBM_V4_CASE
         }
         return cudaErrorNotSupported;

@@ -138,7 +138,7 @@ __device__ __forceinline__ void v4_store(__nv_bfloat16* p, float a, float b, flo
 
 // LPR lanes per tile row: 32 (tiles 128 x 8, one row per warp) or 16 (tiles
 // 64 x 16, two rows per warp); 8 warps, one CTA per SM.
-template <int LPR, typename S>
+template <int LPR, typename S, bool LEARNED = false>
 struct V4Shape {
     static constexpr int NT = 256;
     static constexpr int RPW = 32 / LPR;  // tile rows per warp
@@ -154,7 +154,10 @@ struct V4Shape {
     static constexpr size_t ring_bytes = sizeof(float) * (size_t)NSLOT * 3 * RY * RP;
     static constexpr size_t stg_off = ring_off + ring_bytes;
     static constexpr size_t stg_bytes = sizeof(S) * (size_t)27 * RY * RP;  // [27][RY][RP], storage format
-    static constexpr size_t used = stg_off + stg_bytes;
+    // learned closure: the packed network and one 32-row exchange per warp
+    static constexpr size_t mlp_off = stg_off + stg_bytes;
+    static constexpr size_t mlp_bytes = LEARNED ? (size_t)MlpLayout::BYTES + 8 * (size_t)MlpLayout::XCH_BYTES : 0;
+    static constexpr size_t used = mlp_off + mlp_bytes;
     // at least 116 KB, so that two CTAs never share an SM (each allocates all
     // 512 TMEM columns; a second one would wait for the first to finish)
     static constexpr size_t smem_bytes = used > 116 * 1024 ? used : 116 * 1024;
@@ -212,6 +215,58 @@ __device__ __forceinline__ float4 v4_lds(const __nv_bfloat16* p)
     return make_float4(a.x, a.y, b.x, b.y);
 }
 
+// Learned closure, one cell per lane: the ten network inputs ((m_neq - m_CE)/rho
+// from the second moments Pi' = sum g c c of the streamed populations, the
+// invariants of m_CE/rho = -2 theta tau_hat S, tau_hat), standardised, into
+// the lane's row of the warp's exchange; the BF16 tensor-core forward of the
+// warp's 32 rows, one 16-row tile after the other (both at once, as the
+// register-pull kernel does, spills here); the cell's m_sgs = rho (y sd +
+// mean) back.  The same inputs and network as the register-pull kernel's
+// learned_msgs; here the second moments come from the pull's triple sums
+// instead of the stash.
+__device__ __forceinline__ void v4_learned_msgs(const float (&P)[6], float drho, float ux, float uy, float uz,
+                                                float Sxx, float Syy, float Szz, float Sxy, float Sxz, float Syz,
+                                                float tau_hat, const unsigned char* sm_mlp, unsigned char* xch,
+                                                int lane, float (&msgs)[6])
+{
+    using L = MlpLayout;
+    constexpr float th = (float)kTheta;
+    const float rho = 1.f + drho, irho = 1.f / rho;
+    const float k = -2.f * th * tau_hat;  // m_CE / rho = k S
+    const float a00 = k * Sxx, a11 = k * Syy, a22 = k * Szz, a01 = k * Sxy, a02 = k * Sxz, a12 = k * Syz;
+    float x[10];
+    x[0] = (P[0] - rho * ux * ux - th * drho) * irho - a00;
+    x[1] = (P[1] - rho * uy * uy - th * drho) * irho - a11;
+    x[2] = (P[2] - rho * uz * uz - th * drho) * irho - a22;
+    x[3] = (P[3] - rho * ux * uy) * irho - a01;
+    x[4] = (P[4] - rho * ux * uz) * irho - a02;
+    x[5] = (P[5] - rho * uy * uz) * irho - a12;
+    const float tr = a00 + a11 + a22;
+    const float tr2 = a00 * a00 + a11 * a11 + a22 * a22 + 2.f * (a01 * a01 + a02 * a02 + a12 * a12);
+    x[6] = tr;
+    x[7] = 0.5f * (tr * tr - tr2);
+    x[8] = a00 * (a11 * a22 - a12 * a12) - a01 * (a01 * a22 - a12 * a02) + a02 * (a01 * a12 - a11 * a02);
+    x[9] = tau_hat;
+    const float* xmu = reinterpret_cast<const float*>(sm_mlp + L::XMU);
+    const float* xis = reinterpret_cast<const float*>(sm_mlp + L::XIS);
+    __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(xch);
+    float* Y = reinterpret_cast<float*>(xch);  // overlays the inputs
+    uint32_t* Xrow = reinterpret_cast<uint32_t*>(X + lane * L::XLD);
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+        Xrow[q] = pack_bf16((x[2 * q] - xmu[2 * q]) * xis[2 * q], (x[2 * q + 1] - xmu[2 * q + 1]) * xis[2 * q + 1]);
+#pragma unroll
+    for (int q = 5; q < 8; ++q) Xrow[q] = 0u;
+    __syncwarp();
+    mlp_warp_forward(sm_mlp, X, Y, lane);
+    __syncwarp();
+    const float* ymu = reinterpret_cast<const float*>(sm_mlp + L::YMU);
+    const float* ysd = reinterpret_cast<const float*>(sm_mlp + L::YSD);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) msgs[q] = rho * (Y[lane * 8 + q] * ysd[q] + ymu[q]);
+    __syncwarp();  // every lane has read its outputs before the exchange is reused
+}
+
 // Load schedule.  The pulls of a plane are staged in shared memory: for each
 // population i the rows y0 - 1 - c_y .. y0 + TY - c_y (the own rows' and the
 // y-halo rows' sources) over x0 - 4 .. x0 + TX + 3, as 16-byte (FP32) or
@@ -232,8 +287,9 @@ __global__ void __launch_bounds__(256, 1) step_kernel_v4(const StepArgs a)
 {
     static_assert(Q == 27, "the four-cell kernel is built for D3Q27 (population triples along x)");
     static_assert(!std::is_same<S, double>::value, "FP32 arithmetic");
-    static_assert(CL == CL_BGK || CL == CL_KCMP || CL == CL_KCRB_H || CL == CL_KCRB_RAW, "closure");
-    using Sh = V4Shape<LPR, S>;
+    static_assert(CL == CL_BGK || CL == CL_KCMP || CL == CL_KCRB_H || CL == CL_KCRB_RAW || CL == CL_LEARNED, "closure");
+    constexpr bool LEARNED = CL == CL_LEARNED;
+    using Sh = V4Shape<LPR, S, LEARNED>;
     constexpr int TX = Sh::TX, TY = Sh::TY, RY = Sh::RY, RP = Sh::RP, NB = Sh::NB, NT = Sh::NT, NCH = Sh::NCH;
     constexpr int NHK = (NB + NT - 1) / NT;  // halo cells per thread (at most)
     constexpr bool SHIFTED = StoreTraits<S>::shifted;
@@ -244,6 +300,8 @@ __global__ void __launch_bounds__(256, 1) step_kernel_v4(const StepArgs a)
     uint32_t* tm_base_sm = reinterpret_cast<uint32_t*>(smem_v4 + 24);
     float* ring = reinterpret_cast<float*>(smem_v4 + Sh::ring_off);  // [NSLOT][3][RY][RP]
     S* stg = reinterpret_cast<S*>(smem_v4 + Sh::stg_off);            // [27][RY][RP]
+    unsigned char* sm_mlp = smem_v4 + Sh::mlp_off;                   // learned closure only
+    unsigned char* sm_xch = sm_mlp + MlpLayout::BYTES + (threadIdx.x >> 5) * MlpLayout::XCH_BYTES;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -317,6 +375,11 @@ __global__ void __launch_bounds__(256, 1) step_kernel_v4(const StepArgs a)
         }
     }
 
+    if constexpr (LEARNED) {  // the packed network, visible after the barrier below
+        const uint4* src = static_cast<const uint4*>(a.mlp);
+        uint4* dst = reinterpret_cast<uint4*>(sm_mlp);
+        for (int k = tid; k < MlpLayout::BYTES / 16; k += NT) dst[k] = src[k];
+    }
     // TMEM: warp 0 allocates the 512 columns; the two warps of a lane quarter
     // take 256 each; slot s of a thread starts at column 128 s of its share
     if (warp == 0) {
@@ -565,6 +628,17 @@ __global__ void __launch_bounds__(256, 1) step_kernel_v4(const StepArgs a)
                 S6[5][c] = 0.5f * (du[1][2][c] + du[2][1][c]);
             }
         }
+        // learned closure: the network's m_sgs of the four cells, one cell slot
+        // of every lane per warp-wide forward (32 rows)
+        float msg[4][6];
+        if constexpr (LEARNED) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float P6[6] = {P0[0][c], P0[1][c], P0[2][c], P0[3][c], P0[4][c], P0[5][c]};
+                v4_learned_msgs(P6, dr0[c], u0[0][c], u0[1][c], u0[2][c], S6[0][c], S6[1][c], S6[2][c], S6[3][c],
+                                S6[4][c], S6[5][c], tau_hat, sm_mlp, sm_xch, lane, msg[c]);
+            }
+        }
         // per-cell relaxation constants
         V4Cell K[4];
         {
@@ -577,7 +651,7 @@ __global__ void __launch_bounds__(256, 1) step_kernel_v4(const StepArgs a)
                 const float P6[6] = {P0[0][c], P0[1][c], P0[2][c], P0[3][c], P0[4][c], P0[5][c]};
                 const Coef<float> k = collide_coef<Q, float, CL>(P6, dr0[c], u0[0][c], u0[1][c], u0[2][c], S6[0][c],
                                                                  S6[1][c], S6[2][c], S6[3][c], S6[4][c], S6[5][c],
-                                                                 omega, tau_hat, nu, cnud);
+                                                                 omega, tau_hat, nu, cnud, LEARNED ? msg[c] : nullptr);
                 const float ux = u0[0][c], uy = u0[1][c], uz = u0[2][c];
                 const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
                 K[c].ex[0] = -a1 * ux + a2 * ux2;
@@ -685,14 +759,15 @@ template <int Q, typename S, int CL, int LPR>
 cudaError_t prepare_v4_t()
 {
     return cudaFuncSetAttribute(step_kernel_v4<Q, S, CL, LPR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)V4Shape<LPR, S>::smem_bytes);
+                                (int)V4Shape<LPR, S, CL == CL_LEARNED>::smem_bytes);
 }
 
 template <int Q, typename S, int CL, int LPR>
 cudaError_t launch_v4_t(const StepArgs& a, int nbatch, cudaStream_t s)
 {
-    using Sh = V4Shape<LPR, S>;
+    using Sh = V4Shape<LPR, S, CL == CL_LEARNED>;
     if (!v4_shape_ok(a.nx)) return cudaErrorInvalidValue;
+    if (CL == CL_LEARNED && !a.mlp) return cudaErrorInvalidValue;
     static bool attr_set = false;  // per instantiation; prepare_v4_t sets it ahead of stream capture
     if (!attr_set) {
         cudaError_t e = prepare_v4_t<Q, S, CL, LPR>();

@@ -101,10 +101,11 @@ def test_kcrr_against_hermite_kcrb_tgv64_matches_app_g(lbm):
     printed 0.061 % (E_k) and 0.314 % (Z) against Hermite KC-RB.  The
     difference is small (E_k: at most 1.6e-5 of u0^2), so each trajectory's
     own bound does not fix it; the GPU's difference r - h is therefore held
-    sample by sample to the oracle's stored difference, within 5 % of that
-    difference's largest magnitude.  The oracle's maxima (0.0623 % and
-    0.310 %) lie within 2.2 % of the printed values, so that puts the GPU's
-    within about 7 % of them; 10 % is asserted."""
+    sample by sample to the oracle's stored difference, within 1e-6 of that
+    difference's largest magnitude (both are FP64 runs that differ only in
+    rounding order; measured on a GB300: 1.8e-9 for E_k, 7.9e-10 for Z).
+    The oracle's maxima (0.0623 % and 0.310 %) lie within 2.2 % of the printed
+    values, so the GPU's do too; 10 % is asserted, as for the oracle."""
     gold = _gold()
     with open(os.path.join(GOLDEN, "kcrb_sensitivity_tgv64_oracle.json")) as fp:
         stored = json.load(fp)
@@ -115,6 +116,6 @@ def test_kcrr_against_hermite_kcrb_tgv64_matches_app_g(lbm):
         d_o = np.array(stored["kcrr"][key]) - np.array(stored["hermite"][key])
         drift = float(np.abs((r - h) - d_o).max() / np.abs(d_o).max())
         print(key, "GPU r-h against the oracle's, largest deviation / max|d|:", drift)
-        assert drift <= 0.05, (key, drift)
+        assert drift <= 1e-6, (key, drift)
         got = 100 * float(np.max(np.abs(r - h) / np.abs(h)))
         assert got == pytest.approx(printed, rel=0.10), (key, got)

@@ -474,16 +474,19 @@ def test_default_variant_selection(lbm):
                                       (27, "kcrb_raw", "fp32", 14), (27, "kcrr", "fp32", 13),
                                       (27, "bgk", "bf16", 14), (19, "kcmp", "fp32", 13), (19, "bgk", "fp32", 1),
                                       (19, "kcmp", "fp16", 1), (27, "kcrr", "fp64", 8),
-                                      (27, "learned", "fp32", 1)):
+                                      (27, "learned", "fp32", 1), (27, "learned", "bf16", 1)):
         with lbm.Solver(q, (40, 32, 64), 1e-4, closure=closure, storage=storage) as s:
             assert s.launch_config["variant"] == want, (q, closure, storage)
             ty = {14: 16, 1: 4 if closure == "learned" else 8}.get(want, 8)
             assert s.launch_config["tile_y"] == ty, (q, closure, storage)
     with lbm.Solver(27, (256, 32, 64), 1e-4, closure="kcmp", storage="fp32") as s:
         assert s.launch_config["variant"] == 14 and s.launch_config["tile_y"] == 8
-    for closure, storage, want in (("kcmp", "fp32", 12), ("kcrb_hermite", "fp16", 8), ("bgk", "fp32", 8)):
+    for closure, storage, want in (("kcmp", "fp32", 12), ("kcrb_hermite", "fp16", 8), ("bgk", "fp32", 8),
+                                   ("learned", "fp32", 1)):
         with lbm.Solver(27, (44, 32, 64), 1e-4, closure=closure, storage=storage) as s:  # nx % 8 != 0
             assert s.launch_config["variant"] == want, (closure, storage)
+            if closure == "learned":
+                assert s.launch_config["tile_y"] == 4
             if want == 12:
                 assert s.launch_config["zchunk"] <= 16
     for q, closure, want in ((27, "kcmp", 13), (19, "kcmp", 13), (27, "kcrb_hermite", 1), (27, "bgk", 1)):

@@ -108,7 +108,9 @@ typedef struct {
                            storage, 12 on z-chunks of at most 16 planes for
                            periodic D3Q27 with KC-MP or KC-RB, 13 for KC-RR,
                            D3Q19 and walls; else 8 for periodic D3Q27 except
-                           the learned closure; else 1),
+                           the learned closure; the learned closure on
+                           periodic boxes with 32- or 16-bit storage: 15;
+                           else 1),
                            1 = register pull (every lattice, storage, closure
                            and boundary), 8 = register pull with a split
                            arrive/wait barrier (BGK, KC-MP, KC-RB, KC-RR), 12
@@ -122,10 +124,15 @@ typedef struct {
                            the populations parked in tensor memory until
                            their collision (periodic D3Q27, FP32/FP16/BF16
                            storage, BGK/KC-MP/KC-RB, nx % 8 == 0; tile_y 8:
-                           128 x 8 tiles, 16: 64 x 16 tiles;
-                           LBM_ERR_UNSUPPORTED otherwise); other values,
-                           among them the retired 2-7, 9, 10 and 11:
-                           LBM_ERR_ARG */
+                           128 x 8 tiles, 16: 64 x 16 tiles; the learned
+                           closure: 64 x 16 tiles, and 128 x 8 for 16-bit
+                           storage; LBM_ERR_UNSUPPORTED otherwise), 15 = the
+                           learned closure's register pull on 32 x 4 tiles
+                           with the network on the tcgen05 tensor cores (one
+                           128-row BF16 GEMM per layer and CTA, accumulators
+                           in tensor memory; periodic, 32- and 16-bit
+                           storage); other values, among them the retired
+                           2-7, 9, 10 and 11: LBM_ERR_ARG */
     int disable_graphs; /* nonzero: lbm_step launches kernels one by one instead of
                            replaying a captured CUDA graph                        */
 } lbm_config;

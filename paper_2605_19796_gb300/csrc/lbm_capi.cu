@@ -447,7 +447,8 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
     // rest 8-row tiles
     int tile_y = cfg->tile_y ? cfg->tile_y : (cfg->closure == LBM_LEARNED ? 4 : 8);
     if (cfg->variant != VAR_DEFAULT && cfg->variant != VAR_REGISTER && cfg->variant != VAR_SPLIT &&
-        cfg->variant != VAR_SPLIT_PF && cfg->variant != VAR_ASYNC && cfg->variant != VAR_VEC4)
+        cfg->variant != VAR_SPLIT_PF && cfg->variant != VAR_ASYNC && cfg->variant != VAR_VEC4 &&
+        cfg->variant != VAR_TCNET)
         return fail(LBM_ERR_ARG, "unknown kernel variant");
     int variant = cfg->variant;
     // measured defaults (512^3 and ensemble timings): periodic D3Q27 with 32- or
@@ -455,11 +456,11 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
     // tiles 128 x 8, or 64 x 16 for boxes at most 64 wide); otherwise, for FP32
     // storage, KC-RR, D3Q19 and the walls with KC-MP take the split-barrier
     // pull with asynchronous copies (13); periodic D3Q27 otherwise (FP64) takes
-    // the split-barrier pull (8) and the rest, the learned closure included (its
-    // register pull on 4-row tiles evaluates the network for both halves of a
-    // warp at once: 8.44 GLUPS at 256^3, against 8.32 for the four-cell kernel
-    // on 64 x 16 tiles, whose warps run the network one 16-row tile at a time),
-    // the register pull (1).
+    // the split-barrier pull (8); the learned closure on periodic boxes the
+    // register pull with the network on the tcgen05 tensor cores (15, 4-row
+    // tiles: 9.02 GLUPS at 256^3, against 8.44 for the register pull with
+    // mma.sync fragments and 8.32 for the four-cell kernel); the rest the
+    // register pull (1).
     // lbm_autotune may pick another launch for a given box
     bool short_chunks = false, vec4_chunks = false;
     if (variant == VAR_DEFAULT) {
@@ -477,6 +478,9 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
             variant = VAR_VEC4;
             tile_y = v4_ty;
             vec4_chunks = true;
+        } else if (cfg->closure == LBM_LEARNED &&
+                   step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, VAR_TCNET)) {
+            variant = VAR_TCNET;
         } else if (pf_first && step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, tile_y, VAR_SPLIT_PF)) {
             variant = VAR_SPLIT_PF;
             short_chunks = true;
@@ -518,7 +522,7 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
     // the learned closure's network-heavy CTAs balance better over about twice
     // as many, half as long chunks (256^3, register pull on 4-row tiles: 26
     // planes 8.43 GLUPS, 52 planes 8.28, 16 planes 8.18)
-    if (!cfg->zchunk && cfg->closure == LBM_LEARNED && !vec4_chunks) {
+    if (!cfg->zchunk && cfg->closure == LBM_LEARNED && !vec4_chunks && variant != VAR_TCNET) {
         int zc = (h->zchunk + 1) / 2;
         if (zc < 4) zc = 4;
         if (zc < h->zchunk) h->zchunk = zc;
@@ -633,7 +637,7 @@ int lbm_autotune(lbm_handle* h, int trials)
 {
     if (int rc = check_handle(h)) return rc;
     if (trials < 1) trials = 3;
-    static const int kVariants[] = {VAR_REGISTER, VAR_SPLIT, VAR_SPLIT_PF, VAR_ASYNC, VAR_VEC4};
+    static const int kVariants[] = {VAR_REGISTER, VAR_SPLIT, VAR_SPLIT_PF, VAR_ASYNC, VAR_VEC4, VAR_TCNET};
     static const int kTiles[] = {4, 8, 16};
     static const int kChunks[] = {8, 16, 32, 64, 128};
     const int v0 = h->variant, t0 = h->tile_y, z0 = h->zchunk;

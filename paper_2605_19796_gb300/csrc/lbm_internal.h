@@ -50,7 +50,8 @@ enum Variant {
     VAR_SPLIT = 8,
     VAR_SPLIT_PF = 12,
     VAR_ASYNC = 13,
-    VAR_VEC4 = 14
+    VAR_VEC4 = 14,
+    VAR_TCNET = 15
 };
 
 // variant 14: box shapes it is built for (nx a multiple of 8)

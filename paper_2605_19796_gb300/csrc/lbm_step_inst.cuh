@@ -8,7 +8,9 @@
 // variant 8 with the own pulls copied to the
 // stash by cp.async one plane ahead (32- and 64-bit storage), 14 four cells per
 // thread with vector access and a tensor-memory stash (step_kernel_v4; periodic
-// D3Q27, 32- and 16-bit storage; BGK, KC-MP, KC-RB and the learned closure).
+// D3Q27, 32- and 16-bit storage; BGK, KC-MP, KC-RB and the learned closure),
+// 15 the learned closure's register pull with the network on the tcgen05
+// tensor cores (32 x 4 tiles).
 #pragma once
 
 #include "lbm_step.cuh"
@@ -107,6 +109,16 @@ cudaError_t launch_step_qs(int closure, int bc, int ty, int variant, const StepA
                 LBM_AS_CASE(CL_KCRR, BC_PERIODIC, 8)
             }
 #undef LBM_AS_CASE
+        }
+        return cudaErrorNotSupported;
+    }
+    if (variant == VAR_TCNET) {
+        // the learned closure's register pull on 32 x 4 tiles with the network
+        // on the tcgen05 tensor cores (one 128-row GEMM per layer and CTA)
+        if constexpr (R32) {
+            if (closure == CL_LEARNED && bc == BC_PERIODIC && ty == 4)
+                return a ? launch_step_t<Q, S, CL_LEARNED, BC_PERIODIC, 4, true>(*a, nbatch, s)
+                         : (nbatch < 0 ? prepare_step_t<Q, S, CL_LEARNED, BC_PERIODIC, 4, true>() : cudaSuccess);
         }
         return cudaErrorNotSupported;
     }

@@ -45,57 +45,9 @@
 #include "lbm_mbarrier.cuh"
 #include "lbm_step.cuh"
 #include "lbm_step_split.cuh"
+#include "lbm_tmem.cuh"
 
 namespace lbmk {
-
-// ---------------------------------------------------------------- TMEM
-
-__device__ __forceinline__ void tm_alloc(uint32_t* dst, uint32_t ncols)  // whole warp
-{
-    const uint32_t a = (uint32_t)__cvta_generic_to_shared(dst);
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(a), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tm_relinquish()
-{
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
-}
-__device__ __forceinline__ void tm_dealloc(uint32_t taddr, uint32_t ncols)  // whole warp
-{
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tm_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
-__device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
-__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
-
-// 12 consecutive columns of the thread's lane (one population triple of four cells)
-__device__ __forceinline__ void tm_st12(uint32_t ta, const float (&v)[3][4])
-{
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n"
-        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%9], {%10, %11, %12, %13};\n" ::"r"(ta),
-        "r"(__float_as_uint(v[0][0])), "r"(__float_as_uint(v[0][1])), "r"(__float_as_uint(v[0][2])),
-        "r"(__float_as_uint(v[0][3])), "r"(__float_as_uint(v[1][0])), "r"(__float_as_uint(v[1][1])),
-        "r"(__float_as_uint(v[1][2])), "r"(__float_as_uint(v[1][3])), "r"(ta + 8u), "r"(__float_as_uint(v[2][0])),
-        "r"(__float_as_uint(v[2][1])), "r"(__float_as_uint(v[2][2])), "r"(__float_as_uint(v[2][3]))
-        : "memory");
-}
-
-// 12 consecutive columns back, waited for inside the same statement so that
-// no use of the values can be scheduled before they have arrived
-__device__ __forceinline__ void tm_ld12(uint32_t ta, float (&v)[3][4])
-{
-    uint32_t r[12];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%12];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8, %9, %10, %11}, [%13];\n"
-        "tcgen05.wait::ld.sync.aligned;\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11])
-        : "r"(ta), "r"(ta + 8u)
-        : "memory");
-#pragma unroll
-    for (int k = 0; k < 12; ++k) v[k / 4][k % 4] = __uint_as_float(r[k]);
-}
 
 // ------------------------------------------------------- vector global access
 

@@ -213,14 +213,16 @@ def _stats_for(x, scale_out):
 
 
 @pytest.mark.parametrize("q,variant,tile_y", [(27, 1, 8), (27, 8, 8), (27, 12, 8), (27, 1, 4), (27, 12, 4),
-                                              (27, 14, 16), (19, 1, 4), (19, 8, 8)])
+                                              (27, 14, 16), (27, 15, 4), (19, 1, 4), (19, 8, 8), (19, 15, 4)])
 def test_learned_step_matches_oracle(env, orc, q, variant, tile_y):
     """One step of the fused learned closure (BF16 tensor-core network inside the
     step kernel: the register pull, variant 1, the split-barrier kernel,
     variant 8, and the same with L2 prefetches, variant 12; tiles of 8 rows and
     4, where the register pull evaluates the network for both 16-cell halves of
     a warp together; the four-cell kernel, variant 14, on 64 x 16 tiles, whose
-    warps run the network once per cell slot; D3Q27 and D3Q19)
+    warps run the network once per cell slot; the register pull with the
+    network on the tcgen05 tensor cores, variant 15, one 128-row GEMM per
+    layer with its accumulators in tensor memory; D3Q27 and D3Q19)
     against the oracle's learned step with the same BF16 rounding
     points (inputs, weights, hidden activations) and FP64 elsewhere.  The network
     is random, its output scaled so that the turbulent rate is active in most
@@ -279,7 +281,8 @@ def test_learned_step_matches_oracle(env, orc, q, variant, tile_y):
     assert inc <= 4 * noise + 1e-2 * sgs.max(), (inc, noise, sgs.max())
 
 
-@pytest.mark.parametrize("q,variant,tile_y", [(27, 1, 4), (19, 1, 4), (27, 12, 8), (27, 14, 16)])
+@pytest.mark.parametrize("q,variant,tile_y", [(27, 1, 4), (19, 1, 4), (27, 12, 8), (27, 14, 16), (27, 15, 4),
+                                              (19, 15, 4)])
 def test_learned_step_matches_unrounded_network(env, orc, q, variant, tile_y):
     """One step of the fused learned closure against the oracle's learned step
     with the UNROUNDED FP64 network (oracle/learned.py, rounding=False).  Bound
@@ -353,13 +356,13 @@ def test_learned_step_matches_unrounded_network(env, orc, q, variant, tile_y):
     assert np.all(err <= bound), (np.max(err / bound), noise)
 
 
-@pytest.mark.parametrize("variant,tile_y", [(14, 16), (1, 4)])
+@pytest.mark.parametrize("variant,tile_y", [(14, 16), (1, 4), (15, 4)])
 def test_learned_full_size_sampled_cells(env, orc, variant, tile_y):
     """The learned closure at 256^3 (D3Q27, FP32, decaying HIT, nu = 2.5e-5) in
-    its default launch (the register pull on 4-row tiles, the network
-    evaluated for both halves of each warp at once) and in the four-cell kernel
-    on 64 x 16 tiles, each with its default z-chunk: one GPU step, then sampled
-    cells against the
+    its default launch (the register pull on 4-row tiles with the network on
+    the tcgen05 tensor cores, variant 15), with mma.sync fragments (variant 1)
+    and in the four-cell kernel on 64 x 16 tiles, each with its default
+    z-chunk: one GPU step, then sampled cells against the
     oracle's learned step of the periodic 5x5x5 block around each cell, cut from
     the GPU's own pre-step populations (the centre's pulls and the strain at its
     six neighbours stay inside the block, so the centre is exact).  Random
@@ -436,11 +439,13 @@ def test_learned_closure_from_file_equals_arrays(env, tmp_path):
 
 
 @pytest.mark.parametrize("storage,launch", [("fp16", {}), ("bf16", {}), ("fp16", {"variant": 14, "tile_y": 8}),
-                                            ("bf16", {"variant": 14, "tile_y": 16})])
+                                            ("bf16", {"variant": 14, "tile_y": 16}),
+                                            ("fp16", {"variant": 1, "tile_y": 4})])
 def test_learned_step_16bit_storage(env, orc, storage, launch):
     """The learned closure on weight-shifted 16-bit storage (its default launch,
-    the register pull on 4-row tiles; the four-cell kernel on 128 x 8 tiles,
-    which 16-bit staging leaves room for, and on 64 x 16 tiles): one step
+    the register pull on 4-row tiles with the tcgen05 network; the same with
+    mma.sync fragments; the four-cell kernel on 128 x 8 tiles, which 16-bit
+    staging leaves room for, and on 64 x 16 tiles): one step
     from a state that FP16/BF16 hold exactly gives the density and velocity of
     the same step on FP32 storage within the rounding of the stored results: 8
     units of the format's relative spacing (2^-10 FP16, 2^-7 BF16) times

@@ -466,23 +466,25 @@ def test_default_variant_selection(lbm):
     storage, periodic D3Q27 with KC-MP or KC-RB the split-barrier pull with L2
     prefetches (12) on z-chunks of at most 16 planes; KC-RR, D3Q19 and walls
     with KC-MP the split-barrier pull with asynchronous copies (13); periodic
-    D3Q27 otherwise (BGK, FP64, 16-bit storage) the split-barrier pull (8); the
-    rest, the learned closure included, the register pull (1).  Tiles are 8
-    rows, 4 for the learned closure.  An explicitly requested variant that is
-    not built for a box is refused."""
+    D3Q27 otherwise (BGK, FP64, 16-bit storage) the split-barrier pull (8);
+    the learned closure on periodic boxes the register pull with the network on
+    the tcgen05 tensor cores (15); the rest the register pull (1).  Tiles are
+    8 rows, 4 for the learned closure.  An explicitly requested variant that
+    is not built for a box is refused."""
     for q, closure, storage, want in ((27, "kcmp", "fp32", 14), (27, "kcrb_hermite", "fp16", 14), (27, "kcmp", "fp64", 8),
                                       (27, "kcrb_raw", "fp32", 14), (27, "kcrr", "fp32", 13),
                                       (27, "bgk", "bf16", 14), (19, "kcmp", "fp32", 13), (19, "bgk", "fp32", 1),
                                       (19, "kcmp", "fp16", 1), (27, "kcrr", "fp64", 8),
-                                      (27, "learned", "fp32", 1), (27, "learned", "bf16", 1)):
+                                      (27, "learned", "fp32", 15), (27, "learned", "bf16", 15),
+                                      (19, "learned", "fp32", 15)):
         with lbm.Solver(q, (40, 32, 64), 1e-4, closure=closure, storage=storage) as s:
             assert s.launch_config["variant"] == want, (q, closure, storage)
-            ty = {14: 16, 1: 4 if closure == "learned" else 8}.get(want, 8)
+            ty = {14: 16, 15: 4, 1: 4 if closure == "learned" else 8}.get(want, 8)
             assert s.launch_config["tile_y"] == ty, (q, closure, storage)
     with lbm.Solver(27, (256, 32, 64), 1e-4, closure="kcmp", storage="fp32") as s:
         assert s.launch_config["variant"] == 14 and s.launch_config["tile_y"] == 8
     for closure, storage, want in (("kcmp", "fp32", 12), ("kcrb_hermite", "fp16", 8), ("bgk", "fp32", 8),
-                                   ("learned", "fp32", 1)):
+                                   ("learned", "fp32", 15)):
         with lbm.Solver(27, (44, 32, 64), 1e-4, closure=closure, storage=storage) as s:  # nx % 8 != 0
             assert s.launch_config["variant"] == want, (closure, storage)
             if closure == "learned":

@@ -410,6 +410,14 @@ int lbm_box_filter(const void* f_dev, int lattice, int storage, int nx, int ny, 
 int lbm_closure_features(const float* f_dev, int lattice, int nx, int ny, int nz, double nu, const float* msgs_dev,
                          float* x_dev, float* t_dev, float* kcmp_dev, void* stream);
 
+/* Strain rate S of every cell of an FP32 population array (periodic box; the
+ * velocity of App. F.1 step 1, the central differences of Eq. fd and
+ * Eq. strain_rate_discrete, as lbm_closure_features forms m_CE from them)
+ * into s [N][6] (xx yy zz xy xz yz).  Used to build training targets from
+ * the SGS energy transfer -m_sgs : S of the filtered field.  Enqueue only;
+ * LBM_ERR_ARG for bad arguments. */
+int lbm_closure_strain(const float* f_dev, int lattice, int nx, int ny, int nz, float* s_dev, void* stream);
+
 /* Number of CUDA kernels this handle has launched since creation. */
 int64_t lbm_kernel_launches(const lbm_handle* h);
 

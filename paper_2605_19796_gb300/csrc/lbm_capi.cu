@@ -118,6 +118,10 @@ int default_zchunk_vec4(int nx, int ny, int nz, int nbatch, int tile_y)
 {
     const int tx = tile_y == 16 ? 64 : 128;
     const long long tiles = (long long)((nx + tx - 1) / tx) * ((ny + tile_y - 1) / tile_y) * nbatch;
+    // boxes at most 64 deep (ensembles of small boxes) take 16-plane chunks
+    // where that still gives two CTAs per SM (64 x 64^3 boxes, 64 x 16 tiles:
+    // 22.55 GLUPS, against 21.43 / 20.93 / 20.97 on chunks of 64 / 32 / 22 planes)
+    if (nz <= 64 && nz >= 16 && tiles * ((nz + 15) / 16) >= 2LL * 152) return 16;
     const long long want = (2LL * 152 + tiles - 1) / tiles;  // chunks per tile column for two CTAs per SM
     long long zc = (nz + want - 1) / want;
     if (zc > 40) zc = 40;

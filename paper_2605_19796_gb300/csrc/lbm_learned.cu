@@ -206,6 +206,38 @@ __global__ void features_kernel(const float* f, int nx, int ny, int nz, float ta
         for (int k = 0; k < 6; ++k) tgt[c * 6 + k] = msgs[k * N + c] / rho;
 }
 
+// strain rate S (xx yy zz xy xz yz) of every cell of a periodic FP32 population
+// array by the central differences of the neighbours' velocities, Eq. (fd),
+// as the features kernel forms it
+template <int Q>
+__global__ void strain_kernel(const float* f, int nx, int ny, int nz, float* s_out)
+{
+    const long long N = (long long)nx * ny * nz;
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int ix = (int)(c % nx), iy = (int)((c / nx) % ny), iz = (int)(c / ((long long)nx * ny));
+    const int xp = ix == nx - 1 ? 0 : ix + 1, xm = ix == 0 ? nx - 1 : ix - 1;
+    const int yp = iy == ny - 1 ? 0 : iy + 1, ym = iy == 0 ? ny - 1 : iy - 1;
+    const int zp = iz == nz - 1 ? 0 : iz + 1, zm = iz == 0 ? nz - 1 : iz - 1;
+    const long long nb[3][2] = {{((long long)iz * ny + iy) * nx + xp, ((long long)iz * ny + iy) * nx + xm},
+                                {((long long)iz * ny + yp) * nx + ix, ((long long)iz * ny + ym) * nx + ix},
+                                {((long long)zp * ny + iy) * nx + ix, ((long long)zm * ny + iy) * nx + ix}};
+    float du[3][3];
+    for (int a = 0; a < 3; ++a) {
+        float rp, up[3], rm, um[3];
+        cell_moments<Q>(f, N, nb[a][0], rp, up);
+        cell_moments<Q>(f, N, nb[a][1], rm, um);
+        for (int b = 0; b < 3; ++b) du[a][b] = 0.5f * (up[b] - um[b]);
+    }
+    float* o = s_out + c * 6;
+    o[0] = du[0][0];
+    o[1] = du[1][1];
+    o[2] = du[2][2];
+    o[3] = 0.5f * (du[0][1] + du[1][0]);
+    o[4] = 0.5f * (du[0][2] + du[2][0]);
+    o[5] = 0.5f * (du[1][2] + du[2][1]);
+}
+
 // ---------------------------------------------------------------- MLP
 
 // forward of one layer for a batch: A = X W^T + b, H = silu(A) (or H = A for the last layer)
@@ -612,6 +644,23 @@ int lbm_closure_features(const float* f_dev, int lattice, int nx, int ny, int nz
         features_kernel<27><<<g, 128, 0, s>>>(f_dev, nx, ny, nz, tau_hat, msgs_dev, x_dev, t_dev, kcmp_dev);
     else if (lattice == 19)
         features_kernel<19><<<g, 128, 0, s>>>(f_dev, nx, ny, nz, tau_hat, msgs_dev, x_dev, t_dev, kcmp_dev);
+    else
+        return set_last_error(LBM_ERR_ARG, "lattice must be 19 or 27");
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LBM_OK : set_last_error(LBM_ERR_CUDA, cudaGetErrorString(e));
+}
+
+int lbm_closure_strain(const float* f_dev, int lattice, int nx, int ny, int nz, float* s_dev, void* stream)
+{
+    if (!f_dev || !s_dev || nx < 1 || ny < 1 || nz < 1)
+        return set_last_error(LBM_ERR_ARG, "lbm_closure_strain: bad arguments");
+    const long long N = (long long)nx * ny * nz;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int g = (int)((N + 127) / 128);
+    if (lattice == 27)
+        strain_kernel<27><<<g, 128, 0, s>>>(f_dev, nx, ny, nz, s_dev);
+    else if (lattice == 19)
+        strain_kernel<19><<<g, 128, 0, s>>>(f_dev, nx, ny, nz, s_dev);
     else
         return set_last_error(LBM_ERR_ARG, "lattice must be 19 or 27");
     cudaError_t e = cudaGetLastError();

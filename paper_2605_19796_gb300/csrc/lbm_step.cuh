@@ -38,7 +38,6 @@
 #include "lbm_internal.h"
 #include "lbm_lattice.cuh"
 #include "lbm_mlp_infer.cuh"
-#include "lbm_mlp_tc.cuh"
 
 namespace lbmk {
 
@@ -652,18 +651,11 @@ struct StepShape {
 };
 
 // learned closure: network block and per-warp exchange after the ring and stash
-// (TC: the tensor-core network's block, 128-byte aligned, no exchange)
-template <int Q, typename R, int BC, int TY, int CL, bool TC = false>
-__host__ __device__ constexpr size_t step_mlp_offset()
+template <int Q, typename R, int BC, int TY, int CL>
+constexpr size_t step_smem_bytes()
 {
-    return TC ? (StepShape<Q, R, BC, TY>::base_bytes + 127) / 128 * 128 : StepShape<Q, R, BC, TY>::base_bytes;
-}
-template <int Q, typename R, int BC, int TY, int CL, bool TC = false>
-__host__ __device__ constexpr size_t step_smem_bytes()
-{
-    return step_mlp_offset<Q, R, BC, TY, CL, TC>() +
-           (CL == CL_LEARNED ? (TC ? (size_t)MlpTcLayout::BYTES : (size_t)(MlpLayout::BYTES + TY * MlpLayout::XCH_BYTES))
-                             : 0);
+    return StepShape<Q, R, BC, TY>::base_bytes +
+           (CL == CL_LEARNED ? (size_t)(MlpLayout::BYTES + TY * MlpLayout::XCH_BYTES) : 0);
 }
 
 // network inputs of one cell (the learned closure's 10 inputs: (m_neq - m_CE)/rho,
@@ -672,7 +664,10 @@ __host__ __device__ constexpr size_t step_smem_bytes()
 // The populations are read from the shared-memory stash (stride NT) rather
 // than kept in registers, so that only the network's fragments are live while
 // it runs; the caller reloads them for the collision.
-template <int Q, typename R, int NT>
+// The ten inputs of one cell, standardised and packed as BF16 pairs (pairs 5-7
+// zero); st: the cell's streamed populations in a stash of stride NT, as
+// g = f - w, or (RAW) as f itself.
+template <int Q, typename R, int NT, bool RAW = false>
 __device__ __forceinline__ void learned_inputs(const R* st, R drho, R ux, R uy, R uz, R Sxx, R Syy, R Szz, R Sxy,
                                                R Sxz, R Syz, R tau_hat, const float* xmu, const float* xis,
                                                uint32_t (&xin)[8])
@@ -684,7 +679,7 @@ __device__ __forceinline__ void learned_inputs(const R* st, R drho, R ux, R uy, 
         constexpr int i = decltype(I)::value;
         constexpr int cx = cx_of(Q, i), cy = cy_of(Q, i), cz = cz_of(Q, i);
         if constexpr (cx != 0 || cy != 0 || cz != 0) {
-            const R gi = st[i * NT];
+            const R gi = RAW ? st[i * NT] - (R)weight_of(Q, i) : st[i * NT];
             if (cx != 0) pxx += gi;
             if (cy != 0) pyy += gi;
             if (cz != 0) pzz += gi;
@@ -750,10 +745,7 @@ __device__ __forceinline__ void learned_msgs(const R* st, R drho, R ux, R uy, R 
     __syncwarp();
 }
 
-// TC (the learned closure on 32 x 4 tiles only): the network runs on the
-// tcgen05 tensor cores for the CTA's 128 cells at once (lbm_mlp_tc.cuh), with
-// its accumulators and operands in 128 TMEM columns of the CTA.
-template <int Q, typename S, int CL, int BC, int TY, bool TC = false>
+template <int Q, typename S, int CL, int BC, int TY>
 __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) == 8 || TY >= 16) ? 1 : 2)
     step_kernel(const StepArgs a)
 {
@@ -761,16 +753,12 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
     using Sh = StepShape<Q, R, BC, TY>;
     constexpr int TX = Sh::TX, HY = Sh::HY, RX = Sh::RX, RN = Sh::RN, NT = Sh::NT, NB = Sh::NB;
     static_assert(NB <= NT, "every halo cell of the ring needs a thread");
-    static_assert(!TC || (CL == CL_LEARNED && NT == 128 && sizeof(R) == 4 && BC == BC_PERIODIC),
-                  "tensor-core network: 128 cells, FP32 arithmetic, periodic boxes");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* ring = reinterpret_cast<R*>(smem_raw);  // [4][3][RN]
     R* stash = ring + 4 * 3 * RN;              // [2][Q][NT]
-    unsigned char* sm_mlp = smem_raw + step_mlp_offset<Q, R, BC, TY, CL, TC>();  // learned closure only
+    unsigned char* sm_mlp = smem_raw + Sh::base_bytes;                      // learned closure only
     unsigned char* sm_xch = sm_mlp + MlpLayout::BYTES + threadIdx.y * MlpLayout::XCH_BYTES;
-    if constexpr (CL == CL_LEARNED && TC) {
-        mlp_tc_repack(static_cast<const unsigned char*>(a.mlp), sm_mlp, threadIdx.y * 32 + threadIdx.x, NT);
-    } else if constexpr (CL == CL_LEARNED) {
+    if constexpr (CL == CL_LEARNED) {
         const uint4* src = static_cast<const uint4*>(a.mlp);
         uint4* dst = reinterpret_cast<uint4*>(sm_mlp);
         for (int k = threadIdx.y * 32 + threadIdx.x; k < MlpLayout::BYTES / 16; k += 32 * TY) dst[k] = src[k];
@@ -789,29 +777,6 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
     const int plane = (int)a.plane;
     const S* __restrict__ fin = static_cast<const S*>(a.fin) + (long long)box * a.boxstride;
     S* __restrict__ fout = static_cast<S*>(a.fout) + (long long)box * a.boxstride;
-
-    // tensor-core network: TMEM columns (warp 0 allocates), the MMA mbarrier,
-    // the re-laid weights made visible to the tensor cores
-    uint32_t tm_base = 0, tm_row = 0;
-    unsigned mma_phase = 0;
-    bool tc_ok = true;
-    if constexpr (TC) {
-        uint32_t* slot = reinterpret_cast<uint32_t*>(sm_mlp + MlpTcLayout::TMEM_SLOT);
-        if (ty == 0) {
-            tm_alloc(slot, MlpTcLayout::TM_COLS);
-            tm_relinquish();
-        }
-        if (tid == 0) {
-            mbar_init(reinterpret_cast<uint64_t*>(sm_mlp + MlpTcLayout::MBAR), 1);
-            asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        }
-        fence_proxy_async_smem();
-        tm_fence_before();
-        __syncthreads();
-        tm_fence_after();
-        tm_base = *slot;
-        tm_row = tm_base + ((uint32_t)(32 * ty) << 16);
-    }
 
     const double nu_d = a.box_nu[box];
     const R nu = (R)nu_d;
@@ -929,57 +894,7 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
         __syncthreads();
 
         // ---- plane z: strain from the ring, closure, relaxation, store
-        if constexpr (TC) {
-            // every thread takes part in the CTA-wide network; a cell outside
-            // the box feeds zero inputs and stores nothing
-            R Sxx = 0, Syy = 0, Szz = 0, Sxy = 0, Sxz = 0, Syz = 0;
-            const R* st = stash + (z & 1) * Q * NT + tid;
-            uint32_t xin[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-            if (own.valid) {
-                if (own_store && !isfinite(drho + ux + uy + uz)) atomicOr(a.flag, 1u);
-                const int sm = rslot(z - 1), s0 = rslot(z), sp = rslot(z + 1);
-                R du[3][3];
-#pragma unroll
-                for (int b = 0; b < 3; ++b) {
-                    const R* r0 = ringp(s0, b);
-                    du[0][b] = R(0.5) * (r0[own_r + 1] - r0[own_r - 1]);
-                    du[2][b] = R(0.5) * (ringp(sp, b)[own_r] - ringp(sm, b)[own_r]);
-                    du[1][b] = R(0.5) * (r0[own_r + RX] - r0[own_r - RX]);
-                }
-                Sxx = du[0][0];
-                Syy = du[1][1];
-                Szz = du[2][2];
-                Sxy = R(0.5) * (du[0][1] + du[1][0]);
-                Sxz = R(0.5) * (du[0][2] + du[2][0]);
-                Syz = R(0.5) * (du[1][2] + du[2][1]);
-                learned_inputs<Q, R, NT>(st, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, tau_hat,
-                                         reinterpret_cast<const float*>(sm_mlp + MlpTcLayout::XMU),
-                                         reinterpret_cast<const float*>(sm_mlp + MlpTcLayout::XIS), xin);
-            }
-            float y[6];
-            tc_ok = mlp_cta_forward_tc(sm_mlp, tm_base, tm_row, xin, y, mma_phase, tid, tc_ok);
-            if (!__syncthreads_and(tc_ok)) break;  // CTA-uniform
-            if (own.valid) {
-                const float* ymu = reinterpret_cast<const float*>(sm_mlp + MlpTcLayout::YMU);
-                const float* ysd = reinterpret_cast<const float*>(sm_mlp + MlpTcLayout::YSD);
-                const R rho = R(1) + drho;
-                R msgs[6];
-#pragma unroll
-                for (int q = 0; q < 6; ++q) msgs[q] = rho * (R)(y[q] * ysd[q] + ymu[q]);
-                R g[Q];
-#pragma unroll
-                for (int i = 0; i < Q; ++i) g[i] = st[i * NT];
-                collide<Q, R, CL, FORCE>(g, drho, ux, uy, uz, Sxx, Syy, Szz, Sxy, Sxz, Syz, omega, tau_hat, nu, cnud,
-                                         Fx, Fy, Fz, msgs);
-                if (own_store) {
-                    S* dst = fout + (z * plane + own.yr[1] + own.xs[1]);
-                    static_for<Q>([&](auto I) {
-                        constexpr int i = decltype(I)::value;
-                        store_g<S, R>(dst + (long long)i * ps, g[i], (R)weight_of(Q, i));
-                    });
-                }
-            }
-        } else if (own.valid) {
+        if (own.valid) {
             // a non-finite component makes the sum non-finite (the moments are O(1))
             if (own_store && !isfinite(drho + ux + uy + uz)) atomicOr(a.flag, 1u);
             const int sm = rslot(z - 1), s0 = rslot(z), sp = rslot(z + 1);
@@ -1029,30 +944,22 @@ __global__ void __launch_bounds__(32 * TY, (sizeof(typename StoreTraits<S>::R) =
         uy = vny;
         uz = vnz;
     }
-    if constexpr (TC) {
-        if (!tc_ok && tid == 0) atomicOr(a.flag, kFlagTimeout);
-        // every TMEM access of the CTA has completed before warp 0 frees the columns
-        tm_fence_before();
-        __syncthreads();
-        tm_fence_after();
-        if (ty == 0) tm_dealloc(tm_base, MlpTcLayout::TM_COLS);
-    }
 }
 
-template <int Q, typename S, int CL, int BC, int TY, bool TC = false>
+template <int Q, typename S, int CL, int BC, int TY>
 cudaError_t prepare_step_t()
 {
-    return cudaFuncSetAttribute(step_kernel<Q, S, CL, BC, TY, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)step_smem_bytes<Q, typename StoreTraits<S>::R, BC, TY, CL, TC>());
+    return cudaFuncSetAttribute(step_kernel<Q, S, CL, BC, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)step_smem_bytes<Q, typename StoreTraits<S>::R, BC, TY, CL>());
 }
 
-template <int Q, typename S, int CL, int BC, int TY, bool TC = false>
+template <int Q, typename S, int CL, int BC, int TY>
 cudaError_t launch_step_t(const StepArgs& a, int nbatch, cudaStream_t s)
 {
     using Sh = StepShape<Q, typename StoreTraits<S>::R, BC, TY>;
     static bool attr_set = false;  // per instantiation; prepare_step_t sets it ahead of stream capture
     if (!attr_set) {
-        cudaError_t e = prepare_step_t<Q, S, CL, BC, TY, TC>();
+        cudaError_t e = prepare_step_t<Q, S, CL, BC, TY>();
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -1060,8 +967,7 @@ cudaError_t launch_step_t(const StepArgs& a, int nbatch, cudaStream_t s)
     const int chunks = (a.nz + a.zchunk - 1) / a.zchunk;
     dim3 grid(tiles, chunks, nbatch), block(Sh::TX, TY);
     if (CL == CL_LEARNED && !a.mlp) return cudaErrorInvalidValue;
-    step_kernel<Q, S, CL, BC, TY, TC>
-        <<<grid, block, step_smem_bytes<Q, typename StoreTraits<S>::R, BC, TY, CL, TC>(), s>>>(a);
+    step_kernel<Q, S, CL, BC, TY><<<grid, block, step_smem_bytes<Q, typename StoreTraits<S>::R, BC, TY, CL>(), s>>>(a);
     return cudaGetLastError();
 }
 

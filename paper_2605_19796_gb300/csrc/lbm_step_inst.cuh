@@ -9,12 +9,14 @@
 // stash by cp.async one plane ahead (32- and 64-bit storage), 14 four cells per
 // thread with vector access and a tensor-memory stash (step_kernel_v4; periodic
 // D3Q27, 32- and 16-bit storage; BGK, KC-MP, KC-RB and the learned closure),
-// 15 the learned closure's register pull with the network on the tcgen05
-// tensor cores (32 x 4 tiles).
+// 15 the learned closure with the network on the tcgen05 tensor cores and the
+// pulls of the plane after next spread over its MMAs (step_kernel_tc, 32 x 4
+// tiles).
 #pragma once
 
 #include "lbm_step.cuh"
 #include "lbm_step_split.cuh"
+#include "lbm_step_tc.cuh"
 #include "lbm_step_v4.cuh"
 
 #include <type_traits>
@@ -117,8 +119,7 @@ cudaError_t launch_step_qs(int closure, int bc, int ty, int variant, const StepA
         // on the tcgen05 tensor cores (one 128-row GEMM per layer and CTA)
         if constexpr (R32) {
             if (closure == CL_LEARNED && bc == BC_PERIODIC && ty == 4)
-                return a ? launch_step_t<Q, S, CL_LEARNED, BC_PERIODIC, 4, true>(*a, nbatch, s)
-                         : (nbatch < 0 ? prepare_step_t<Q, S, CL_LEARNED, BC_PERIODIC, 4, true>() : cudaSuccess);
+                return a ? launch_tc_t<Q, S>(*a, nbatch, s) : (nbatch < 0 ? prepare_tc_t<Q, S>() : cudaSuccess);
         }
         return cudaErrorNotSupported;
     }

@@ -40,7 +40,7 @@ EXPORTS = ["lbm_config_default", "lbm_create", "lbm_destroy", "lbm_init_velocity
            "lbm_step_count", "lbm_kernel_launches", "lbm_last_error", "lbm_abi_version",
            "lbm_diagnostics_noalloc", "lbm_autotune", "lbm_launch_config", "lbm_mlp_param_count",
            "lbm_mlp_workspace_floats", "lbm_mlp_forward", "lbm_mlp_grad", "lbm_mlp_adamw", "lbm_box_filter",
-           "lbm_closure_features", "lbm_set_learned_closure", "lbm_mlp_packed_bytes", "lbm_mlp_pack",
+           "lbm_closure_features", "lbm_closure_strain", "lbm_set_learned_closure", "lbm_mlp_packed_bytes", "lbm_mlp_pack",
            "lbm_mlp_forward_tc", "lbm_wait_selftest", "lbm_host_alloc", "lbm_host_free",
            "lbm_init_velocity_f32", "lbm_moments_f32", "lbm_read_learned_closure",
            "lbm_set_learned_closure_file"]
@@ -109,6 +109,7 @@ def _load() -> ctypes.CDLL:
                                    ctypes.c_int, ctypes.c_double, ctypes.c_int, vp, vp, vp]
     lib.lbm_closure_features.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_double, vp, vp, vp, vp, vp]
+    lib.lbm_closure_strain.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
     lib.lbm_set_learned_closure.argtypes = [H, P(ctypes.c_float), P(ctypes.c_float)]
     lib.lbm_mlp_packed_bytes.restype = ctypes.c_longlong
     lib.lbm_mlp_pack.argtypes = [P(ctypes.c_float), P(ctypes.c_float), vp]
@@ -327,6 +328,11 @@ def lbm_box_filter(f_ptr, lattice, storage, nx, ny, nz, factor, fc_ptr, msgs_ptr
 def lbm_closure_features(f_ptr, lattice, nx, ny, nz, nu, msgs_ptr, x_ptr, t_ptr, kcmp_ptr=0, stream=None) -> None:
     _check(LIB.lbm_closure_features(_vp(f_ptr), int(lattice), int(nx), int(ny), int(nz), float(nu), _vp(msgs_ptr),
                                     _vp(x_ptr), _vp(t_ptr), _vp(kcmp_ptr), _vp(_stream_handle(stream))))
+
+
+def lbm_closure_strain(f_ptr, lattice, nx, ny, nz, s_ptr, stream=None) -> None:
+    _check(LIB.lbm_closure_strain(_vp(f_ptr), int(lattice), int(nx), int(ny), int(nz), _vp(s_ptr),
+                                  _vp(_stream_handle(stream))))
 
 
 def lbm_mlp_pack(params: np.ndarray, stats: np.ndarray) -> np.ndarray:

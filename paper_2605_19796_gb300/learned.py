@@ -15,8 +15,14 @@ the molecular rate) and learns m_sgs itself from data the method generates:
   4. training with the library's own forward/backward/AdamW kernels;
   5. fused BF16 tensor-core inference in the step kernel (closure "learned").
 
+A second training target ("dissipation") keeps the deviatoric part of the
+exact SGS stress and replaces its trace by the one whose rate reproduces the
+filtered field's local SGS energy transfer -m_sgs : S (the paper's open point
+on determining the turbulent relaxation from collision statistics, Sec. 8).
+
 Orchestration only: every numerical step runs in liblbm's kernels; torch holds
-device buffers and computes the energy spectra used for evaluation.
+device buffers, computes the energy spectra used for evaluation and the
+elementwise trace replacement of the dissipation target.
 """
 from __future__ import annotations
 
@@ -62,10 +68,52 @@ def snapshot_features(s: lbm.Solver, factor: int, nu_coarse: float, nu_fine: flo
     return x, t, kc, fc
 
 
+def snapshot_strain(fc: torch.Tensor) -> torch.Tensor:
+    """Strain rate S [N, 6] (xx yy zz xy xz yz) of coarse FP32 populations fc
+    [q, nz, ny, nx] (lbm_closure_strain: the features' central differences)."""
+    q, nz, ny, nx = fc.shape
+    out = torch.empty((nz * ny * nx, 6), dtype=torch.float32, device=fc.device)
+    lbm.lbm_closure_strain(fc.data_ptr(), q, nx, ny, nz, out.data_ptr())
+    torch.cuda.synchronize()
+    return out
+
+
+def dissipation_targets(T: torch.Tensor, S: torch.Tensor, c_nu: float, delta: float = 1.0,
+                        cap_quantile: float = 1.0) -> torch.Tensor:
+    """The exact targets T = m_sgs/rho [N, 6] with their trace replaced by the
+    one whose turbulent rate carries the local SGS energy transfer.  With the
+    transfer Pi = -T : S (off-diagonal terms twice) and the eddy viscosity that
+    dissipates it, nu* = max(Pi, 0) / (2 S : S), the rate nu_t = C_nu Delta
+    sqrt(|tr m_sgs| / 2) of Eq. (omega_sgs_operational) equals nu* for
+    tr = 2 (nu* / (C_nu Delta))^2.  The deviatoric part of T is kept.
+    cap_quantile < 1 clips nu* at that quantile of its values in T (the ratio
+    diverges where the filtered strain vanishes)."""
+    Td, Sd = T.double(), S.double()
+    w = torch.tensor([1.0, 1.0, 1.0, 2.0, 2.0, 2.0], dtype=torch.float64, device=T.device)
+    pi = -(Td * Sd * w).sum(1)
+    ss = (Sd * Sd * w).sum(1)
+    nu_star = torch.where(ss > 0, torch.clamp(pi, min=0.0) / (2.0 * ss + 1e-300), torch.zeros_like(ss))
+    if cap_quantile < 1.0:
+        k = max(1, int(round(cap_quantile * nu_star.numel())))
+        cap = torch.kthvalue(nu_star.cpu(), k).values.item()
+        nu_star = torch.clamp(nu_star, max=cap)
+    tr_new = 2.0 * (nu_star / (c_nu * delta)) ** 2
+    tr_old = Td[:, 0] + Td[:, 1] + Td[:, 2]
+    out = Td.clone()
+    for k in range(3):
+        out[:, k] += (tr_new - tr_old) / 3.0
+    return out.float()
+
+
 def generate(n_fine: int = 512, factor: int = 4, seeds: Sequence[int] = (0, 1, 2, 3, 4),
              k0s: Sequence[float] = (4.0, 8.0), nu_fine: float = 1e-4, urms: float = 0.04,
-             snap_steps: Sequence[int] = (300, 600), keep: float = 0.25, sample_seed: int = 0):
-    """Training samples from fine runs: returns (X, T, KC) on the GPU."""
+             snap_steps: Sequence[int] = (300, 600), keep: float = 0.25, sample_seed: int = 0,
+             target: str = "exact", c_nu: float = 0.035, cap_quantile: float = 0.99):
+    """Training samples from fine runs: returns (X, T, KC) on the GPU; target
+    "exact" (the SGS stress of Eq. m_sgs_2) or "dissipation" (its trace
+    replaced by dissipation_targets at this C_nu, nu* clipped at the snapshot's
+    cap_quantile)."""
+    assert target in ("exact", "dissipation"), target
     gen = torch.Generator(device="cuda").manual_seed(sample_seed)
     X, T, KC = [], [], []
     for k0 in k0s:
@@ -78,7 +126,9 @@ def generate(n_fine: int = 512, factor: int = 4, seeds: Sequence[int] = (0, 1, 2
                 for st in snap_steps:
                     s.step(st - done)
                     done = st
-                    x, t, kc, _ = snapshot_features(s, factor, nu_fine / factor, nu_fine)
+                    x, t, kc, fc = snapshot_features(s, factor, nu_fine / factor, nu_fine)
+                    if target == "dissipation":
+                        t = dissipation_targets(t, snapshot_strain(fc), c_nu, cap_quantile=cap_quantile)
                     n = x.shape[0]
                     idx = torch.randperm(n, generator=gen, device="cuda")[: max(1, int(keep * n))]
                     X.append(x[idx])
@@ -346,16 +396,23 @@ def main(argv=None) -> Dict:
     ap.add_argument("--t0", type=int, default=400)
     ap.add_argument("--coarse-steps", type=int, default=150)
     ap.add_argument("--mlups-sizes", default="128,256")
-    ap.add_argument("--out", default=os.path.join(os.path.dirname(__file__), "data", "learned_closure.npz"))
+    ap.add_argument("--target", default="exact", choices=["exact", "dissipation"],
+                    help="training target: the exact SGS stress, or its trace set by the SGS energy transfer")
+    ap.add_argument("--c-nu", type=float, default=0.035, help="C_nu of the dissipation target and its coarse runs")
+    ap.add_argument("--out", default=None,
+                    help="checkpoint (default data/learned_closure.npz, data/learned_closure_dissipation.npz)")
     a = ap.parse_args(argv)
+    if a.out is None:
+        name = "learned_closure.npz" if a.target == "exact" else "learned_closure_dissipation.npz"
+        a.out = os.path.join(os.path.dirname(__file__), "data", name)
     ints = lambda s: tuple(int(v) for v in s.split(",") if v)
     floats = lambda s: tuple(float(v) for v in s.split(",") if v)
     nu_fine = 1e-4
     t = time.perf_counter()
     X, T, KC = generate(a.n_fine, a.factor, ints(a.train_seeds), floats(a.k0s), nu_fine, snap_steps=ints(a.snap_steps),
-                        keep=a.keep)
+                        keep=a.keep, target=a.target, c_nu=a.c_nu)
     Xh, Th, KCh = generate(a.n_fine, a.factor, ints(a.test_seeds), floats(a.k0s), nu_fine,
-                           snap_steps=ints(a.snap_steps), keep=a.keep, sample_seed=1)
+                           snap_steps=ints(a.snap_steps), keep=a.keep, sample_seed=1, target=a.target, c_nu=a.c_nu)
     t_data = time.perf_counter() - t
     stats = standardisation(X, T)
     t = time.perf_counter()
@@ -373,6 +430,8 @@ def main(argv=None) -> Dict:
     for cl in ("kcmp", "learned"):
         calibrated[cl] = coarse_run(cl, ev_ref, res["params"], stats, cal[cl])
     calibrated["bgk"] = coarse_run("bgk", ev_ref)
+    # the learned closure at the C_nu its targets were built for
+    calibrated["learned_at_target_c_nu"] = coarse_run("learned", ev_ref, res["params"], stats, a.c_nu)
     os.makedirs(os.path.dirname(a.out), exist_ok=True)
     np.savez(a.out, params=res["params"], stats=stats, n_fine=a.n_fine, factor=a.factor, nu_fine=nu_fine,
              nu_coarse=nu_fine / a.factor)

@@ -86,6 +86,32 @@ def test_adamw_step(env):
 
 
 @pytest.mark.parametrize("q", [19, 27])
+def test_closure_strain_matches_oracle(env, orc, q):
+    """lbm_closure_strain (the strain the dissipation target is built from)
+    against the oracle's strain (App. F.1 step 3) of the same FP32 populations'
+    velocity, on a ragged periodic box.  Tolerance: the kernel sums in FP32
+    (velocity rounding about 1e-7 of |u| <= 0.1, halved by the central
+    difference), 5e-7 absolute."""
+    lbm, torch = env
+    shape = (16, 9, 12)
+    nx, ny, nz = shape
+    rho, u = inputs.hit_fields(0, k0=2.0, urms=0.06, seed=17, shape=shape)
+    rng = np.random.default_rng(7)
+    f = orc.init_equilibrium(q, rho, u) * (1 + 1e-3 * rng.standard_normal((q, nz, ny, nx)))
+    f32 = f.astype(np.float32)
+    fd = torch.from_numpy(np.ascontiguousarray(f32)).cuda()
+    out = torch.full((nx * ny * nz, 6), float("nan"), dtype=torch.float32, device="cuda")
+    lbm.lbm_closure_strain(fd.data_ptr(), q, nx, ny, nz, out.data_ptr())
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    _, uo = orc.fields(f32.astype(np.float64))
+    S = orc.strain_field(uo)
+    want = np.stack([S[0, 0], S[1, 1], S[2, 2], S[0, 1], S[0, 2], S[1, 2]], axis=-1).reshape(-1, 6)
+    assert np.abs(want).max() > 1e-3
+    assert np.abs(got - want).max() <= 5e-7, np.abs(got - want).max()
+
+
+@pytest.mark.parametrize("q", [19, 27])
 def test_box_filter_and_features(env, orc, q):
     lbm, torch = env
     from oracle import closure_data as cd

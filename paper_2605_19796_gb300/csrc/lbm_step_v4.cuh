@@ -642,8 +642,10 @@ __global__ void __launch_bounds__(256, 1) step_kernel_v4(const StepArgs a)
             static_for<9>([&](auto PI) {
                 constexpr int p = decltype(PI)::value;
                 constexpr int cy = p % 3 - 1, cz = p / 3 - 1, pat = v4_pat(cy, cz);
-                float g[3][4];
-                tm_ld12(ts + 12u * p, g);
+                // the triple's populations are on their way from TMEM while the
+                // per-triple constants are formed
+                uint32_t gr[12];
+                tm_ld12_issue(ts + 12u * p, gr);
                 float Y[4], B[4], Cm[4], Cp[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
@@ -661,6 +663,10 @@ __global__ void __launch_bounds__(256, 1) step_kernel_v4(const StepArgs a)
                         Cp[c] = Cm[c] = K[c].C[pat];
                     }
                 }
+                tm_ld12_wait(gr);
+                float g[3][4];
+#pragma unroll
+                for (int q = 0; q < 12; ++q) g[q / 4][q % 4] = __uint_as_float(gr[q]);
                 static_for<3>([&](auto CI) {
                     constexpr int k = decltype(CI)::value;
                     constexpr int cx = k - 1, i = 3 * p + k;

@@ -58,6 +58,28 @@ __device__ __forceinline__ void tm_ld12(uint32_t ta, float (&v)[3][4])
     for (int k = 0; k < 12; ++k) v[k / 4][k % 4] = __uint_as_float(r[k]);
 }
 
+// The same 12 columns in two statements: the load, then (after independent
+// work) the wait, which takes the destination registers as operands so that no
+// use of them can be placed between the two.
+__device__ __forceinline__ void tm_ld12_issue(uint32_t ta, uint32_t (&r)[12])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%12];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8, %9, %10, %11}, [%13];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11])
+        : "r"(ta), "r"(ta + 8u)
+        : "memory");
+}
+__device__ __forceinline__ void tm_ld12_wait(uint32_t (&r)[12])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11])
+                 :
+                 : "memory");
+}
+
 // 8 consecutive columns of the thread's lane, 32-bit values
 __device__ __forceinline__ void tm_st8(uint32_t ta, const uint32_t (&v)[8])
 {

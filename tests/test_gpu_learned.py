@@ -530,3 +530,66 @@ def test_learned_closure_pipeline(env):
     print("a posteriori:", post)
     for cl in ("kcmp", "learned", "bgk"):
         assert np.isfinite(post[cl]["E_k"]) and post[cl]["E_k"] > 0
+
+
+def test_learned_closure_gain_a_posteriori(env):
+    """What the trained network gains over the method without it, a posteriori
+    (reduced case: fine 128^3 KC-MP runs, seeds 0 and 1, box-filtered by 4 to
+    32^3; 40 coarse steps from the filtered state at fine step 150, evaluation
+    seed 7; C_nu calibrated per closure on seed 0 so that the coarse run
+    dissipates as the filtered fine run, bisection in [1e-3, 0.5]).  Measured
+    on a GB300 (spectrum = E(k) relative L2 error over shells 1..15,
+    dissipation against the filtered fine run's 5.82e-6):
+
+      BGK                              6.77 %   -27 %
+      KC-MP, C_nu = 0.035              4.91 %   +21 %
+      KC-MP, calibrated 0.023          4.94 %    +6 %
+      learned (exact m_sgs), 0.035     6.71 %   -27 %
+      learned (exact m_sgs), cal. 0.5  6.03 %   -18 %
+      learned (dissipation target),
+        cal. 0.5                       5.22 %   -12 %
+
+    The outcome asserted: the network trained on the exact SGS stress gains
+    nothing at the paper's C_nu (it dissipates as BGK, within 3 %: its trace is
+    small at this resolution, so the rate stays clipped) and stays behind
+    calibrated KC-MP in spectrum and dissipation even at the largest C_nu; the
+    dissipation-carrying target (trace from the local SGS transfer, nu* clipped
+    at its 90th percentile) recovers part of the missing dissipation and of the
+    spectrum error but still loses to calibrated KC-MP.  The analytic closure
+    is the fallback and the judge, as intended."""
+    lbm, torch = env
+    from paper_2605_19796_gb300 import learned
+
+    n_fine, factor, nu_f, c_nu = 128, 4, 1e-4, 0.035
+    cal_ref = learned.filtered_reference(n_fine, factor, 4.0, 0, nu_f, 0.04, 150, 40)
+    ev_ref = learned.filtered_reference(n_fine, factor, 4.0, 7, nu_f, 0.04, 150, 40)
+    target_diss = ev_ref["dissipation"]
+    res = {}
+    nets = {}
+    for target in ("exact", "dissipation"):
+        X, T, KC = learned.generate(n_fine, factor, seeds=(0, 1), k0s=(4.0,), snap_steps=(150, 300), keep=1.0,
+                                    target=target, c_nu=c_nu, cap_quantile=0.9)
+        stats = learned.standardisation(X, T)
+        tr = learned.train(X, T, stats, iters=1500, batch=4096, lr=2e-3)
+        nets[target] = (tr["params"], stats)
+        cn = learned.calibrate_c_nu("learned", cal_ref, tr["params"], stats)
+        res[target + "_cal"] = learned.coarse_run("learned", ev_ref, tr["params"], stats, cn)
+        res[target + "_cal"]["c_nu"] = cn
+    res["exact_default"] = learned.coarse_run("learned", ev_ref, *nets["exact"], c_nu)
+    ck = learned.calibrate_c_nu("kcmp", cal_ref)
+    res["kcmp_cal"] = learned.coarse_run("kcmp", ev_ref, c_nu=ck)
+    res["kcmp_cal"]["c_nu"] = ck
+    res["bgk"] = learned.coarse_run("bgk", ev_ref)
+    print({k: v for k, v in res.items()}, "filtered fine dissipation", target_diss)
+    derr = {k: abs(v["dissipation"] - target_diss) / target_diss for k, v in res.items()}
+    spec = {k: v["spectrum_rel_l2"] for k, v in res.items()}
+    assert all(np.isfinite(list(spec.values())))
+    # the exact-target network at the paper's C_nu dissipates as BGK
+    assert abs(res["exact_default"]["dissipation"] - res["bgk"]["dissipation"]) <= 0.03 * res["bgk"]["dissipation"]
+    # calibrated KC-MP wins on both measures against either network
+    for t in ("exact_cal", "dissipation_cal"):
+        assert spec["kcmp_cal"] < spec[t], (t, spec)
+        assert derr["kcmp_cal"] < derr[t], (t, derr)
+    # the dissipation target moves the network towards the filtered run
+    assert res["dissipation_cal"]["dissipation"] > res["exact_cal"]["dissipation"]
+    assert spec["dissipation_cal"] < spec["exact_cal"]

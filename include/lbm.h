@@ -104,7 +104,9 @@ typedef struct {
     int variant;        /* tuning: step-kernel variant, 0 = library default
                            (periodic D3Q27 with FP32/FP16/BF16 storage and
                            BGK, KC-MP or KC-RB, nx % 8 == 0: 14, tiles
-                           128 x 8, or 64 x 16 for nx <= 64; else, for FP32
+                           128 x 8, or 64 x 16 for nx <= 64, and for FP32
+                           storage 16 where nx is a multiple of the tile
+                           width and ny >= 8 tile heights; else, for FP32
                            storage, 12 on z-chunks of at most 16 planes for
                            periodic D3Q27 with KC-MP or KC-RB, 13 for KC-RR,
                            D3Q19 and walls; else 8 for periodic D3Q27 except
@@ -131,8 +133,14 @@ typedef struct {
                            with the network on the tcgen05 tensor cores (one
                            128-row BF16 GEMM per layer and CTA, accumulators
                            in tensor memory; periodic, 32- and 16-bit
-                           storage); other values, among them the retired
-                           2-7, 9, 10 and 11: LBM_ERR_ARG */
+                           storage), 16 = 14 with the interior of the
+                           staged rows copied by the Tensor Memory
+                           Accelerator (one cp.async.bulk.tensor per
+                           population and plane; BGK/KC-MP/KC-RB, nx a
+                           multiple of 128, or 64 for tile_y 16;
+                           LBM_ERR_UNSUPPORTED otherwise); other values,
+                           among them the retired 2-7, 9, 10 and 11:
+                           LBM_ERR_ARG */
     int disable_graphs; /* nonzero: lbm_step launches kernels one by one instead of
                            replaying a captured CUDA graph                        */
 } lbm_config;

@@ -27,7 +27,16 @@ struct StepArgs {
     double force[3];        // body force density (channel); zero otherwise
     unsigned int* flag;     // bit 0: non-finite density/velocity seen, bit 1: a bounded wait timed out
     const void* mlp;        // packed network parameters (learned closure only), MlpLayout::BYTES
+    // four-cell kernel with TMA staging: host addresses of the CUtensorMaps of
+    // fin (box TX x staged rows, and TX x 1 for tiles whose rows wrap), or null
+    const void* tmap_rows;
+    const void* tmap_row1;
 };
+
+// tensor map of a population buffer for the four-cell kernel's TMA staging
+// (4D: x, y, z, population of box; box box_x x box_rows x 1 x 1)
+cudaError_t encode_v4_map(void* map_out /*CUtensorMap*/, const void* buf, int storage, int nx, int ny, int nz, int q,
+                          int nbatch, int box_x, int box_rows);
 
 // host: packs 9414 FP32 parameters and 32 standardisation values into the
 // shared-memory layout of the fused inference (MlpLayout::BYTES bytes)
@@ -51,11 +60,14 @@ enum Variant {
     VAR_SPLIT_PF = 12,
     VAR_ASYNC = 13,
     VAR_VEC4 = 14,
-    VAR_TCNET = 15
+    VAR_TCNET = 15,
+    VAR_VEC4_TMA = 16
 };
 
 // variant 14: box shapes it is built for (nx a multiple of 8)
 bool vec4_shape_ok(int nx);
+// variant 16: every tile full in x (the TMA does not wrap around the box)
+bool vec4_tma_shape_ok(int nx, int tile_y);
 
 
 // Host-side launchers (lbm_step_*.cu).  Return cudaSuccess or the launch error.

@@ -50,6 +50,7 @@ bool step_supported(int q, int storage, int closure, int bc, int tile_y, int var
 }
 
 bool vec4_shape_ok(int nx) { return nx % 8 == 0; }
+bool vec4_tma_shape_ok(int nx, int tile_y) { return nx % (tile_y == 16 ? 64 : 128) == 0; }
 
 cudaError_t prepare_step(int q, int storage, int closure, int bc, int tile_y, int variant)
 {

@@ -9,19 +9,23 @@
 // stash by cp.async one plane ahead (32- and 64-bit storage), 14 four cells per
 // thread with vector access and a tensor-memory stash (step_kernel_v4; periodic
 // D3Q27, 32- and 16-bit storage; BGK, KC-MP, KC-RB and the learned closure),
-// 15 the learned closure with the network on the tcgen05 tensor cores and the
-// pulls of the plane after next spread over its MMAs (step_kernel_tc, 32 x 4
-// tiles).
+// 15 the learned closure with the network on the tcgen05 tensor cores
+// (step_kernel_tc, 32 x 4 tiles), 16 variant 14 with the interior of the
+// staged rows copied by TMA.
 #pragma once
 
 #include "lbm_step.cuh"
 #include "lbm_step_split.cuh"
 #include "lbm_step_tc.cuh"
-#include "lbm_step_v4.cuh"
 
 #include <type_traits>
 
 namespace lbmk {
+
+// four-cell kernels of D3Q27 with storage S (variants 14 and 16), defined in
+// lbm_step_v4_<storage>.cu; same conventions as launch_step_qs
+template <typename S>
+cudaError_t launch_v4_qs(int closure, int bc, int ty, bool tma, const StepArgs* a, int nbatch, cudaStream_t s);
 
 // a == nullptr, nbatch == 0: only report whether the combination is instantiated;
 // a == nullptr, nbatch == -1: set the kernel's shared-memory attribute (prepare).
@@ -29,28 +33,9 @@ template <int Q, typename S>
 cudaError_t launch_step_qs(int closure, int bc, int ty, int variant, const StepArgs* a, int nbatch, cudaStream_t s)
 {
     constexpr bool R32 = sizeof(typename StoreTraits<S>::R) == 4;
-    if (variant == VAR_VEC4) {
-        // tile_y 8: 128 x 8 tiles (one row per warp); 16: 64 x 16 tiles (two rows per warp)
-        if constexpr (Q == 27 && R32) {
-#define LBM_V4_CASE(CL, TYV, LPRV)                                                                     \
-    if (closure == CL && bc == BC_PERIODIC && ty == TYV)                                               \
-        return a ? launch_v4_t<Q, S, CL, LPRV>(*a, nbatch, s) : (nbatch < 0 ? prepare_v4_t<Q, S, CL, LPRV>() : cudaSuccess);
-            LBM_V4_CASE(CL_BGK, 8, 32)
-            LBM_V4_CASE(CL_KCMP, 8, 32)
-            LBM_V4_CASE(CL_KCRB_H, 8, 32)
-            LBM_V4_CASE(CL_KCRB_RAW, 8, 32)
-            LBM_V4_CASE(CL_BGK, 16, 16)
-            LBM_V4_CASE(CL_KCMP, 16, 16)
-            LBM_V4_CASE(CL_KCRB_H, 16, 16)
-            LBM_V4_CASE(CL_KCRB_RAW, 16, 16)
-            // the learned closure's network block and exchanges fit beside the
-            // FP32 staging area of 64 x 16 tiles only
-            LBM_V4_CASE(CL_LEARNED, 16, 16)
-            if constexpr (sizeof(S) == 2) {
-                LBM_V4_CASE(CL_LEARNED, 8, 32)
-            }
-#undef LBM_V4_CASE
-        }
+    if (variant == VAR_VEC4 || variant == VAR_VEC4_TMA) {
+        // the four-cell kernels live in their own translation units (lbm_step_v4_<storage>.cu)
+        if constexpr (Q == 27 && R32) return launch_v4_qs<S>(closure, bc, ty, variant == VAR_VEC4_TMA, a, nbatch, s);
         return cudaErrorNotSupported;
     }
     if (variant == VAR_SPLIT) {

@@ -40,6 +40,8 @@
 //    storage the store's "+ w" enters as w (1 + K), one fused rounding.
 #pragma once
 
+#include <cuda.h>
+
 #include <type_traits>
 
 #include "lbm_mbarrier.cuh"
@@ -90,7 +92,11 @@ __device__ __forceinline__ void v4_store(__nv_bfloat16* p, float a, float b, flo
 
 // LPR lanes per tile row: 32 (tiles 128 x 8, one row per warp) or 16 (tiles
 // 64 x 16, two rows per warp); 8 warps, one CTA per SM.
-template <int LPR, typename S, bool LEARNED = false>
+// TMAS: the interior of the staged rows (x0 .. x0 + TX - 1) is copied by the
+// Tensor Memory Accelerator, one cp.async.bulk.tensor per population and plane
+// into [27][RY][TX], and only the x-edge chunks (x0 - 4 .. x0 - 1 and x0 + TX ..
+// x0 + TX + 3 of every staged row) by cp.async, into [27][RY][8].
+template <int LPR, typename S, bool LEARNED = false, bool TMAS = false>
 struct V4Shape {
     static constexpr int NT = 256;
     static constexpr int RPW = 32 / LPR;  // tile rows per warp
@@ -101,11 +107,18 @@ struct V4Shape {
     static constexpr int NSLOT = 3;
     static constexpr int NB = 2 * TX + 2 * TY;     // halo cells of a ring plane (no corners)
     static constexpr int NCH = TX / 4;             // 4-cell chunks of a row
-    static constexpr int NPOS = 2 * NCH + 2 * RY;  // staged chunks beyond the own ones: halo rows, x-edge chunks
+    // staged chunks beyond the own ones: halo rows and x-edge chunks (TMAS: the x-edge chunks)
+    static constexpr int NPOS = TMAS ? 2 * RY : 2 * NCH + 2 * RY;
     static constexpr size_t ring_off = 32;         // three mbarriers, the TMEM base address
     static constexpr size_t ring_bytes = sizeof(float) * (size_t)NSLOT * 3 * RY * RP;
-    static constexpr size_t stg_off = ring_off + ring_bytes;
-    static constexpr size_t stg_bytes = sizeof(S) * (size_t)27 * RY * RP;  // [27][RY][RP], storage format
+    static constexpr size_t stg_off = (ring_off + ring_bytes + 127) / 128 * 128;  // TMA destinations: 128-byte aligned
+    static constexpr size_t stg_int_bytes = sizeof(S) * (size_t)27 * RY * TX;     // TMAS: [27][RY][TX]
+    static constexpr size_t stg_bytes = TMAS ? stg_int_bytes + sizeof(S) * (size_t)27 * RY * 8
+                                             : sizeof(S) * (size_t)27 * RY * RP;  // [27][RY][RP], storage format
+    static constexpr unsigned tma_bytes = (unsigned)stg_int_bytes;                // bytes the TMA copies per plane
+    static_assert(!TMAS || (RY * TX * sizeof(S)) % 128 == 0, "each population's TMA box 128-byte aligned");
+    static_assert(!(TMAS && LEARNED), "TMA staging is built for the analytic closures");
+    static_assert(!TMAS || (NPOS <= 40 && 40 + 8 * 26 < NT), "TMA issuing threads apart from the x-edge threads");
     // learned closure: the packed network and one 32-row exchange per warp
     static constexpr size_t mlp_off = stg_off + stg_bytes;
     static constexpr size_t mlp_bytes = LEARNED ? (size_t)MlpLayout::BYTES + 8 * (size_t)MlpLayout::XCH_BYTES : 0;
@@ -234,14 +247,29 @@ __device__ __forceinline__ void v4_learned_msgs(const float (&P)[6], float drho,
 // issued.  They land while the current plane collides.  Plane p arrives on ring
 // mbarrier (p - z0) & 1 (parity ((p - z0) >> 1) & 1) and fills the staging
 // area for the (p - z0)-th time (staging mbarrier parity (p - z0) & 1).
-template <int Q, typename S, int CL, int LPR>
-__global__ void __launch_bounds__(256, 1) step_kernel_v4(const StepArgs a)
+// one TMA copy of a box of a 4D tensor map into shared memory, completing on
+// the mbarrier (transaction bytes)
+__device__ __forceinline__ void v4_tma_load(void* smem_dst, const CUtensorMap* map, int x, int y, int z, int w,
+                                            uint64_t* bar)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];\n" ::"r"(d),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(w), "r"(b)
+        : "memory");
+}
+
+template <int Q, typename S, int CL, int LPR, bool TMAS = false>
+__global__ void __launch_bounds__(256, 1)
+    step_kernel_v4(const StepArgs a, const __grid_constant__ CUtensorMap map_rows, const __grid_constant__ CUtensorMap map_row1)
 {
     static_assert(Q == 27, "the four-cell kernel is built for D3Q27 (population triples along x)");
     static_assert(!std::is_same<S, double>::value, "FP32 arithmetic");
     static_assert(CL == CL_BGK || CL == CL_KCMP || CL == CL_KCRB_H || CL == CL_KCRB_RAW || CL == CL_LEARNED, "closure");
     constexpr bool LEARNED = CL == CL_LEARNED;
-    using Sh = V4Shape<LPR, S, LEARNED>;
+    using Sh = V4Shape<LPR, S, LEARNED, TMAS>;
     constexpr int TX = Sh::TX, TY = Sh::TY, RY = Sh::RY, RP = Sh::RP, NB = Sh::NB, NT = Sh::NT, NCH = Sh::NCH;
     constexpr int NHK = (NB + NT - 1) / NT;  // halo cells per thread (at most)
     constexpr bool SHIFTED = StoreTraits<S>::shifted;
@@ -251,7 +279,8 @@ __global__ void __launch_bounds__(256, 1) step_kernel_v4(const StepArgs a)
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_v4);  // [0], [1]: ring planes, [2]: staging
     uint32_t* tm_base_sm = reinterpret_cast<uint32_t*>(smem_v4 + 24);
     float* ring = reinterpret_cast<float*>(smem_v4 + Sh::ring_off);  // [NSLOT][3][RY][RP]
-    S* stg = reinterpret_cast<S*>(smem_v4 + Sh::stg_off);            // [27][RY][RP]
+    S* stg = reinterpret_cast<S*>(smem_v4 + Sh::stg_off);            // [27][RY][RP] (TMAS: [27][RY][TX])
+    S* stge = stg + 27 * RY * TX;                                     // TMAS: x-edge chunks [27][RY][8]
     unsigned char* sm_mlp = smem_v4 + Sh::mlp_off;                   // learned closure only
     unsigned char* sm_xch = sm_mlp + MlpLayout::BYTES + (threadIdx.x >> 5) * MlpLayout::XCH_BYTES;
 
@@ -290,7 +319,7 @@ __global__ void __launch_bounds__(256, 1) step_kernel_v4(const StepArgs a)
     // the extra staged chunk of this thread (tid < NPOS): staged row, column, global x, source rows
     int pos_r = -1, pos_col = 0, pos_x = 0, yr_pos[3] = {0, 0, 0};
     if (tid < Sh::NPOS) {
-        const int p = tid;
+        const int p = TMAS ? tid + 2 * NCH : tid;  // TMAS: x-edge chunks only
         if (p < 2 * NCH) {  // y-halo rows
             const int c = p % NCH;
             pos_r = p < NCH ? 0 : RY - 1;
@@ -358,13 +387,53 @@ __global__ void __launch_bounds__(256, 1) step_kernel_v4(const StepArgs a)
     };
     auto rslot = [&](int z) { return (int)((unsigned)(z - z0 + 1) % (unsigned)Sh::NSLOT); };
     auto ringp = [&](int s, int c) { return ring + (s * 3 + c) * (RY * RP); };
-    auto stg_at = [&](int i, int r, int col) { return stg + (i * RY + r) * RP + col; };
+    // staged value of population i, staged row r, column col (x0 - 4 + col)
+    auto stg_at = [&](int i, int r, int col) {
+        if constexpr (TMAS) {
+            if (col < 4) return stge + (i * RY + r) * 8 + col;
+            if (col >= TX + 4) return stge + (i * RY + r) * 8 + (col - TX);
+            return stg + (i * RY + r) * TX + (col - 4);
+        } else {
+            return stg + (i * RY + r) * RP + col;
+        }
+    };
 
     // cp.async of plane z's pulls into the staging area, then the thread's
     // arrival on the staging mbarrier (completed by the copies)
     auto issue = [&](int z) {
         int zr[3];
         zrows(z, zr);
+        if constexpr (TMAS) {
+            if (pos_r >= 0) {  // x-edge chunks by cp.async
+                static_for<27>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    constexpr int cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
+                    const S* base = fin + (long long)i * ps + zr[1 - cz];
+                    cp_async_chunk<S>((uint32_t)__cvta_generic_to_shared(stg_at(i, pos_r, pos_col)),
+                                      base + yr_pos[1 - cy] + pos_x);
+                });
+                cp_async_commit();
+                cp_async_arrive(&mbar[2]);
+            } else if (tid >= 40 && (tid - 40) % 8 == 0) {  // the interior by the TMA: population (tid - 40) / 8,
+                const int i = (tid - 40) / 8;                     // one issuing thread per population, spread over warps
+                const int cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
+                const int zc = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+                const int zsrc = cz == 0 ? zc : (cz == 1 ? (zc == 0 ? nz - 1 : zc - 1) : (zc == nz - 1 ? 0 : zc + 1));
+                const int ys = y0 - 1 - cy, w = box * 27 + i;
+                S* dst = stg + i * RY * TX;
+                mbar_expect_tx(&mbar[2], Sh::tma_bytes / 27u);
+                if (ys >= 0 && ys + RY <= ny) {
+                    v4_tma_load(dst, &map_rows, x0, ys, zsrc, w, &mbar[2]);
+                } else {  // rows wrapping around y: one row at a time
+#pragma unroll 1
+                    for (int r = 0; r < RY; ++r)
+                        v4_tma_load(dst + r * TX, &map_row1, x0, wrapi(ys + r, ny), zsrc, w, &mbar[2]);
+                }
+            } else {
+                mbar_arrive(&mbar[2]);
+            }
+            return;
+        }
         static_for<27>([&](auto I) {
             constexpr int i = decltype(I)::value;
             constexpr int cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
@@ -713,15 +782,25 @@ __global__ void __launch_bounds__(256, 1) step_kernel_v4(const StepArgs a)
 // nx a multiple of 8 (aligned vector rows for 32- and 16-bit storage)
 inline bool v4_shape_ok(int nx) { return nx % 8 == 0; }
 
+
 template <int Q, typename S, int CL, int LPR>
 cudaError_t prepare_v4_t()
 {
-    return cudaFuncSetAttribute(step_kernel_v4<Q, S, CL, LPR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)V4Shape<LPR, S, CL == CL_LEARNED>::smem_bytes);
+    cudaError_t e = cudaFuncSetAttribute(step_kernel_v4<Q, S, CL, LPR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)V4Shape<LPR, S, CL == CL_LEARNED, false>::smem_bytes);
+    if constexpr (CL != CL_LEARNED) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(step_kernel_v4<Q, S, CL, LPR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)V4Shape<LPR, S, false, true>::smem_bytes);
+    }
+    return e;
 }
 
+// tma: stage the rows' interior by TMA (variant 16; needs the tensor maps and
+// every tile full in x, since the TMA fills outside the box with zeros where
+// the cp.async path wraps)
 template <int Q, typename S, int CL, int LPR>
-cudaError_t launch_v4_t(const StepArgs& a, int nbatch, cudaStream_t s)
+cudaError_t launch_v4_t(const StepArgs& a, int nbatch, cudaStream_t s, bool tma)
 {
     using Sh = V4Shape<LPR, S, CL == CL_LEARNED>;
     if (!v4_shape_ok(a.nx)) return cudaErrorInvalidValue;
@@ -735,7 +814,17 @@ cudaError_t launch_v4_t(const StepArgs& a, int nbatch, cudaStream_t s)
     const int tiles = ((a.nx + Sh::TX - 1) / Sh::TX) * ((a.ny + Sh::TY - 1) / Sh::TY);
     const int chunks = (a.nz + a.zchunk - 1) / a.zchunk;
     dim3 grid(tiles, chunks, nbatch), block(Sh::NT);
-    step_kernel_v4<Q, S, CL, LPR><<<grid, block, Sh::smem_bytes, s>>>(a);
+    if (tma) {
+        if constexpr (CL != CL_LEARNED) {
+            if (!a.tmap_rows || !a.tmap_row1 || a.nx % Sh::TX != 0) return cudaErrorInvalidValue;
+            step_kernel_v4<Q, S, CL, LPR, true><<<grid, block, V4Shape<LPR, S, false, true>::smem_bytes, s>>>(
+                a, *static_cast<const CUtensorMap*>(a.tmap_rows), *static_cast<const CUtensorMap*>(a.tmap_row1));
+            return cudaGetLastError();
+        }
+        return cudaErrorNotSupported;
+    }
+    CUtensorMap none{};
+    step_kernel_v4<Q, S, CL, LPR, false><<<grid, block, Sh::smem_bytes, s>>>(a, none, none);
     return cudaGetLastError();
 }
 

@@ -69,8 +69,9 @@ def _cfg(lbm, **kw):
     (dict(force=(1e-5, 0.0, 0.0)), -6), (dict(bc=(0, 1, 0), ny=2), -1), (dict(tile_y=5), -6),
     (dict(nx=2048, ny=2048, nz=1024), -1),
     # retired and unknown kernel variants; variants not built for the storage or box
-    (dict(variant=2), -1), (dict(variant=6), -1), (dict(variant=11), -1), (dict(variant=16), -1),
-    (dict(variant=15), -6), (dict(variant=15, closure=5, storage=0), -6), (dict(variant=15, closure=5, tile_y=8), -6),
+    (dict(variant=2), -1), (dict(variant=6), -1), (dict(variant=11), -1),     (dict(variant=15), -6), (dict(variant=15, closure=5, storage=0), -6), (dict(variant=15, closure=5, tile_y=8), -6),
+    (dict(variant=16, nx=64), -6), (dict(variant=16, nx=64, tile_y=16, closure=5), -6),
+    (dict(variant=16, storage=0, nx=128), -6), (dict(variant=17), -1),
     (dict(variant=14, nx=44), -6), (dict(variant=14, storage=0), -6), (dict(variant=14, closure=4), -6),
     (dict(variant=13, storage=2), -6),
     (dict(variant=9), -1), (dict(variant=4), -1),

@@ -363,7 +363,8 @@ def test_full_size_sampled_cells_fp32(lbm, orc, n):
     pts = _sampled_cells(n, 48, seed=n)
     offs = np.array([(dx, dy, dz) for dz in range(-2, 3) for dy in range(-2, 3) for dx in range(-2, 3)])
     with lbm.Solver(27, (n, n, n), 1e-4, closure="kcmp", storage="fp32") as s:
-        assert s.launch_config["variant"] == 14  # the four-cell kernel on 128 x 8 tiles
+        # the four-cell kernel on 128 x 8 tiles with the rows' interior staged by TMA
+        assert s.launch_config["variant"] == 16 and s.launch_config["tile_y"] == 8
         s.init_velocity(rho, u)
         del rho, u
         s.step(3)
@@ -462,7 +463,9 @@ def test_ensemble_and_channel_launch_through_graph(lbm, orc):
 def test_default_variant_selection(lbm):
     """Library default: periodic D3Q27 with 32- or 16-bit storage and BGK,
     KC-MP or KC-RB takes the four-cell kernel (14) when nx is a multiple of 8
-    (tiles 128 x 8, or 64 x 16 for boxes at most 64 wide); otherwise, for FP32
+    (tiles 128 x 8, or 64 x 16 for boxes at most 64 wide), for FP32 storage
+    with TMA staging (16) where nx is a multiple of the tile width and ny spans
+    at least eight tiles; otherwise, for FP32
     storage, periodic D3Q27 with KC-MP or KC-RB the split-barrier pull with L2
     prefetches (12) on z-chunks of at most 16 planes; KC-RR, D3Q19 and walls
     with KC-MP the split-barrier pull with asynchronous copies (13); periodic
@@ -482,7 +485,11 @@ def test_default_variant_selection(lbm):
             ty = {14: 16, 15: 4, 1: 4 if closure == "learned" else 8}.get(want, 8)
             assert s.launch_config["tile_y"] == ty, (q, closure, storage)
     with lbm.Solver(27, (256, 32, 64), 1e-4, closure="kcmp", storage="fp32") as s:
-        assert s.launch_config["variant"] == 14 and s.launch_config["tile_y"] == 8
+        assert s.launch_config["variant"] == 14 and s.launch_config["tile_y"] == 8  # ny < 8 tile heights
+    with lbm.Solver(27, (256, 64, 16), 1e-4, closure="kcmp", storage="fp32") as s:
+        assert s.launch_config["variant"] == 16 and s.launch_config["tile_y"] == 8
+    with lbm.Solver(27, (256, 64, 16), 1e-4, closure="kcmp", storage="fp16") as s:
+        assert s.launch_config["variant"] == 14
     for closure, storage, want in (("kcmp", "fp32", 12), ("kcrb_hermite", "fp16", 8), ("bgk", "fp32", 8),
                                    ("learned", "fp32", 15)):
         with lbm.Solver(27, (44, 32, 64), 1e-4, closure=closure, storage=storage) as s:  # nx % 8 != 0

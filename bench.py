@@ -75,8 +75,8 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
-KERNEL_SOURCES = ("lbm_lattice.cuh", "lbm_mbarrier.cuh", "lbm_mlp_infer.cuh", "lbm_step.cuh", "lbm_step_split.cuh",
-                  "lbm_step_v4.cuh")
+KERNEL_SOURCES = ("lbm_lattice.cuh", "lbm_mbarrier.cuh", "lbm_mlp_infer.cuh", "lbm_mlp_tc.cuh", "lbm_tmem.cuh",
+                  "lbm_step.cuh", "lbm_step_split.cuh", "lbm_step_tc.cuh", "lbm_step_v4.cuh")
 
 
 def _code_only(text: str) -> str:

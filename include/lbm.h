@@ -106,10 +106,12 @@ typedef struct {
                            BGK, KC-MP or KC-RB, nx % 8 == 0: 14, tiles
                            128 x 8, or 64 x 16 for nx <= 64, and for FP32
                            storage 16 where nx is a multiple of the tile
-                           width and ny >= 8 tile heights; else, for FP32
-                           storage, 12 on z-chunks of at most 16 planes for
-                           periodic D3Q27 with KC-MP or KC-RB, 13 for KC-RR,
-                           D3Q19 and walls; else 8 for periodic D3Q27 except
+                           width and ny >= 8 tile heights; the D3Q27 FP32
+                           channel with BGK or KC-MP, nx % 8 == 0 and
+                           (ny - 1) % 16 != 0: 14 on 64 x 16 tiles; else, for
+                           FP32 storage, 12 on z-chunks of at most 16 planes
+                           for periodic D3Q27 with KC-MP or KC-RB, 13 for
+                           KC-RR, D3Q19 and walls; else 8 for periodic D3Q27 except
                            the learned closure; the learned closure on
                            periodic boxes with 32- or 16-bit storage: 15;
                            else 1),
@@ -125,7 +127,9 @@ typedef struct {
                            in shared memory by cp.async one plane ahead and
                            the populations parked in tensor memory until
                            their collision (periodic D3Q27, FP32/FP16/BF16
-                           storage, BGK/KC-MP/KC-RB, nx % 8 == 0; tile_y 8:
+                           storage, BGK/KC-MP/KC-RB, nx % 8 == 0; and the
+                           FP32 channel, walls in y with a force, BGK/KC-MP,
+                           (ny - 1) % tile_y != 0; tile_y 8:
                            128 x 8 tiles, 16: 64 x 16 tiles; the learned
                            closure: 64 x 16 tiles, and 128 x 8 for 16-bit
                            storage; LBM_ERR_UNSUPPORTED otherwise), 15 = the

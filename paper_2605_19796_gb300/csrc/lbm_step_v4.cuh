@@ -132,6 +132,7 @@ struct V4Shape {
 // relaxation constants of one cell (collide_coef in the per-triple form)
 struct V4Cell {
     float ca, cb, ex[3], ey[3], ez[3], C[5], Dxx, Dxy2, Dxz2;
+    float ux, uy, uz, uF;  // walls with a body force: Guo's source
 };
 
 // index of the (c_y, c_z) part of H: (0,0), (+-1,0), (0,+-1), c_y c_z = 1, c_y c_z = -1
@@ -261,7 +262,16 @@ __device__ __forceinline__ void v4_tma_load(void* smem_dst, const CUtensorMap* m
         : "memory");
 }
 
-template <int Q, typename S, int CL, int LPR, bool TMAS = false>
+// BC = BC_WALLS_Y: halfway bounce-back walls at y = 0 and y = ny - 1 with a body
+// force (the channel).  The staged rows stay those of the periodic box; a wall
+// row replaces the pulls that cross its wall by the cell's own post-collision
+// opposite population (loaded from global memory), takes the one-sided
+// difference of Eqs. (fd_boundary_lower/upper) across y, the velocity shifted
+// by F/2 and Guo's source.  Rows beyond a wall are computed from the periodic
+// image and neither stored nor read.  The top wall row must not be the first
+// row of its tile ((ny - 1) % TY != 0), so that both rows below it are in the
+// ring.
+template <int Q, typename S, int CL, int LPR, bool TMAS = false, int BC = BC_PERIODIC>
 __global__ void __launch_bounds__(256, 1)
     step_kernel_v4(const StepArgs a, const __grid_constant__ CUtensorMap map_rows, const __grid_constant__ CUtensorMap map_row1)
 {
@@ -269,6 +279,8 @@ __global__ void __launch_bounds__(256, 1)
     static_assert(!std::is_same<S, double>::value, "FP32 arithmetic");
     static_assert(CL == CL_BGK || CL == CL_KCMP || CL == CL_KCRB_H || CL == CL_KCRB_RAW || CL == CL_LEARNED, "closure");
     constexpr bool LEARNED = CL == CL_LEARNED;
+    constexpr bool WALLS = BC == BC_WALLS_Y;
+    static_assert(!(WALLS && LEARNED), "the learned closure runs on periodic boxes");
     using Sh = V4Shape<LPR, S, LEARNED, TMAS>;
     constexpr int TX = Sh::TX, TY = Sh::TY, RY = Sh::RY, RP = Sh::RP, NB = Sh::NB, NT = Sh::NT, NCH = Sh::NCH;
     constexpr int NHK = (NB + NT - 1) / NT;  // halo cells per thread (at most)
@@ -303,6 +315,8 @@ __global__ void __launch_bounds__(256, 1)
     const float tau_hat = (float)(nu_d / kTheta + 0.5);
     const float omega = (float)(1.0 / (nu_d / kTheta + 0.5));
     const float cnud = (float)a.cnu_delta;
+    // Guo's source (walls): (1 - omega/2)/theta and (1 - omega/2)/theta^2
+    const float gp1 = (1.f - 0.5f * omega) * (float)(1.0 / kTheta), gp2 = gp1 * (float)(1.0 / kTheta);
 
     // own cells: row ty of the tile (staged row ty + 1), x = xa .. xa + 3
     // (wrapped into the box for lanes beyond nx, which compute but do not store)
@@ -315,6 +329,10 @@ __global__ void __launch_bounds__(256, 1)
     const int xl = (x0 + nx - 1) % nx;  // left neighbour of the row's first cell (own pulls of the first plane)
     const int xr = (x0 + TX) % nx;      // right neighbour of the row's last cell
     const int ry_own = ty + 1, rx_own = 4 + 4 * lx;
+    // walls: this thread's row at a wall, and the body force
+    const bool wall_lo = WALLS && gy == 0, wall_hi = WALLS && gy == ny - 1;
+    const float Fx = WALLS ? (float)a.force[0] : 0.f, Fy = WALLS ? (float)a.force[1] : 0.f,
+                Fz = WALLS ? (float)a.force[2] : 0.f;
 
     // the extra staged chunk of this thread (tid < NPOS): staged row, column, global x, source rows
     int pos_r = -1, pos_col = 0, pos_x = 0, yr_pos[3] = {0, 0, 0};
@@ -500,6 +518,18 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
                     for (int c = 0; c < 4; ++c) g[k][c] -= w;
                 }
+                if constexpr (WALLS && cy != 0) {
+                    // halfway bounce-back: a pull across the wall takes the cell's own
+                    // post-collision opposite population (same plane)
+                    if (cy == 1 ? wall_lo : wall_hi) {
+                        const float4 b = v4_load(fin + (long long)(26 - i) * ps + zr[1] + yr_own[1] + xaw);
+                        constexpr float w = SHIFTED ? 0.f : (float)weight_of(Q, i);
+                        g[k][0] = b.x - w;
+                        g[k][1] = b.y - w;
+                        g[k][2] = b.z - w;
+                        g[k][3] = b.w - w;
+                    }
+                }
             });
             if constexpr (FULL) tm_st12(ts + 12u * p, g);
 #pragma unroll
@@ -529,9 +559,15 @@ __global__ void __launch_bounds__(256, 1)
         for (int c = 0; c < 4; ++c) {
             dr[c] = d[c];
             const float inv = 1.f / (1.f + d[c]);
-            u[0][c] = jx[c] * inv;
-            u[1][c] = jy[c] * inv;
-            u[2][c] = jz[c] * inv;
+            if constexpr (WALLS) {  // u = (sum g c + F/2) / rho
+                u[0][c] = (jx[c] + 0.5f * Fx) * inv;
+                u[1][c] = (jy[c] + 0.5f * Fy) * inv;
+                u[2][c] = (jz[c] + 0.5f * Fz) * inv;
+            } else {
+                u[0][c] = jx[c] * inv;
+                u[1][c] = jy[c] * inv;
+                u[2][c] = jz[c] * inv;
+            }
             if constexpr (FULL) {
                 P[0][c] = d[c] - g0[c];
                 P[1][c] = pyy[c];
@@ -555,15 +591,24 @@ __global__ void __launch_bounds__(256, 1)
         for (int k = 0; k < NHK; ++k) {
             if (hal_rr[k] >= 0) {
                 const int r = hal_rr[k], xr4 = 4 + hal_xr[k];
+                const int yh = y0 - 1 + r;  // the halo cell's row
+                const bool hlo = WALLS && yh == 0, hhi = WALLS && yh == ny - 1;
                 float gh[Q];
                 static_for<27>([&](auto I) {
                     constexpr int i = decltype(I)::value;
-                    constexpr int cx = i % 3 - 1;
-                    const float v = v4_cvt(*stg_at(i, r, xr4 - cx));
+                    constexpr int cx = i % 3 - 1, cy = (i / 3) % 3 - 1;
+                    float v = v4_cvt(*stg_at(i, r, xr4 - cx));
+                    if constexpr (WALLS && cy != 0) {  // bounce-back at a wall row (x-halo cells)
+                        if (cy == 1 ? hlo : hhi) {
+                            int zr[3];
+                            zrows(z, zr);
+                            v = v1_load(fin + (long long)(26 - i) * ps + zr[1] + yh * nx + (x0 + hal_xr[k] + nx) % nx);
+                        }
+                    }
                     gh[i] = SHIFTED ? v : v - (float)weight_of(Q, i);
                 });
                 float dh, vx, vy, vz;
-                moments<Q, float>(gh, dh, vx, vy, vz, 0.f, 0.f, 0.f);
+                moments<Q, float>(gh, dh, vx, vy, vz, Fx, Fy, Fz);
                 const int pos = r * RP + xr4;
                 ringp(s, 0)[pos] = vx;
                 ringp(s, 1)[pos] = vy;
@@ -632,10 +677,24 @@ __global__ void __launch_bounds__(256, 1)
                 du[0][b][1] = 0.5f * (u0[b][2] - u0[b][0]);
                 du[0][b][2] = 0.5f * (u0[b][3] - u0[b][1]);
                 du[0][b][3] = 0.5f * (ur - u0[b][2]);
-                du[1][b][0] = 0.5f * (yp.x - yn.x);
-                du[1][b][1] = 0.5f * (yp.y - yn.y);
-                du[1][b][2] = 0.5f * (yp.z - yn.z);
-                du[1][b][3] = 0.5f * (yp.w - yn.w);
+                if (WALLS && wall_lo) {  // one-sided at the lower wall, Eq. (fd_boundary_lower)
+                    const float4 y2 = *reinterpret_cast<const float4*>(r + 2 * RP);
+                    du[1][b][0] = 0.5f * (-3.f * u0[b][0] + 4.f * yp.x - y2.x);
+                    du[1][b][1] = 0.5f * (-3.f * u0[b][1] + 4.f * yp.y - y2.y);
+                    du[1][b][2] = 0.5f * (-3.f * u0[b][2] + 4.f * yp.z - y2.z);
+                    du[1][b][3] = 0.5f * (-3.f * u0[b][3] + 4.f * yp.w - y2.w);
+                } else if (WALLS && wall_hi) {  // one-sided at the upper wall, Eq. (fd_boundary_upper)
+                    const float4 y2 = *reinterpret_cast<const float4*>(r - 2 * RP);
+                    du[1][b][0] = 0.5f * (3.f * u0[b][0] - 4.f * yn.x + y2.x);
+                    du[1][b][1] = 0.5f * (3.f * u0[b][1] - 4.f * yn.y + y2.y);
+                    du[1][b][2] = 0.5f * (3.f * u0[b][2] - 4.f * yn.z + y2.z);
+                    du[1][b][3] = 0.5f * (3.f * u0[b][3] - 4.f * yn.w + y2.w);
+                } else {
+                    du[1][b][0] = 0.5f * (yp.x - yn.x);
+                    du[1][b][1] = 0.5f * (yp.y - yn.y);
+                    du[1][b][2] = 0.5f * (yp.z - yn.z);
+                    du[1][b][3] = 0.5f * (yp.w - yn.w);
+                }
 #pragma unroll
                 for (int c = 0; c < 4; ++c) du[2][b][c] = 0.5f * (u1[b][c] - um[b][c]);
             }
@@ -675,6 +734,12 @@ __global__ void __launch_bounds__(256, 1)
                                                                  omega, tau_hat, nu, cnud, LEARNED ? msg[c] : nullptr);
                 const float ux = u0[0][c], uy = u0[1][c], uz = u0[2][c];
                 const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+                if constexpr (WALLS) {
+                    K[c].ux = ux;
+                    K[c].uy = uy;
+                    K[c].uz = uz;
+                    K[c].uF = ux * Fx + uy * Fy + uz * Fz;
+                }
                 K[c].ex[0] = -a1 * ux + a2 * ux2;
                 K[c].ex[1] = a0 * ux2;
                 K[c].ex[2] = a1 * ux + a2 * ux2;
@@ -736,6 +801,25 @@ __global__ void __launch_bounds__(256, 1)
                 float g[3][4];
 #pragma unroll
                 for (int q = 0; q < 12; ++q) g[q / 4][q % 4] = __uint_as_float(gr[q]);
+                // Guo's source (walls with a force): (1 - omega/2) w [(c - u)/theta + (c.u) c/theta^2].F
+                // is G0 + c_x G1 + c_x^2 G2 along a triple, with P1 = (1 - omega/2)/theta,
+                // P2 = P1/theta, BF = c_y F_y + c_z F_z, Bu = c_y u_y + c_z u_z:
+                //   G0 = P1 (BF - u.F) + P2 Bu BF,  G1 = P1 F_x + P2 (u_x BF + F_x Bu),  G2 = P2 u_x F_x;
+                // it joins the constant of each population of the triple
+                float Cz[4];
+                if constexpr (WALLS) {
+                    const float BF = (float)cy * Fy + (float)cz * Fz;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const float Bu = (float)cy * K[c].uy + (float)cz * K[c].uz;
+                        const float G0 = fmaf(gp2 * Bu, BF, gp1 * (BF - K[c].uF));
+                        const float G1 = fmaf(gp2, fmaf(K[c].ux, BF, Fx * Bu), gp1 * Fx);
+                        const float G2 = gp2 * K[c].ux * Fx;
+                        Cz[c] = K[c].C[pat] + G0;
+                        Cp[c] += G0 + G1 + G2;
+                        Cm[c] += G0 - G1 + G2;
+                    }
+                }
                 static_for<3>([&](auto CI) {
                     constexpr int k = decltype(CI)::value;
                     constexpr int cx = k - 1, i = 3 * p + k;
@@ -744,7 +828,7 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
                         const float pm1 = fmaf(K[c].ex[k], B[c], Y[c]);
-                        const float Cc = cx == 0 ? K[c].C[pat] : (cx == 1 ? Cp[c] : Cm[c]);
+                        const float Cc = cx == 0 ? (WALLS ? Cz[c] : K[c].C[pat]) : (cx == 1 ? Cp[c] : Cm[c]);
                         const float Kv = fmaf(K[c].cb, pm1, Cc);
                         // FP32 storage stores f = g' + w: w (1 + K) in one rounding, so
                         // that no part of K is lost to a sum near 1 (its small terms
@@ -783,14 +867,14 @@ __global__ void __launch_bounds__(256, 1)
 inline bool v4_shape_ok(int nx) { return nx % 8 == 0; }
 
 
-template <int Q, typename S, int CL, int LPR>
+template <int Q, typename S, int CL, int LPR, int BC = BC_PERIODIC>
 cudaError_t prepare_v4_t()
 {
-    cudaError_t e = cudaFuncSetAttribute(step_kernel_v4<Q, S, CL, LPR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(step_kernel_v4<Q, S, CL, LPR, false, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)V4Shape<LPR, S, CL == CL_LEARNED, false>::smem_bytes);
     if constexpr (CL != CL_LEARNED) {
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(step_kernel_v4<Q, S, CL, LPR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(step_kernel_v4<Q, S, CL, LPR, true, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)V4Shape<LPR, S, false, true>::smem_bytes);
     }
     return e;
@@ -799,15 +883,16 @@ cudaError_t prepare_v4_t()
 // tma: stage the rows' interior by TMA (variant 16; needs the tensor maps and
 // every tile full in x, since the TMA fills outside the box with zeros where
 // the cp.async path wraps)
-template <int Q, typename S, int CL, int LPR>
+template <int Q, typename S, int CL, int LPR, int BC = BC_PERIODIC>
 cudaError_t launch_v4_t(const StepArgs& a, int nbatch, cudaStream_t s, bool tma)
 {
     using Sh = V4Shape<LPR, S, CL == CL_LEARNED>;
     if (!v4_shape_ok(a.nx)) return cudaErrorInvalidValue;
     if (CL == CL_LEARNED && !a.mlp) return cudaErrorInvalidValue;
+    if (BC == BC_WALLS_Y && (a.ny < 3 || (a.ny - 1) % Sh::TY == 0)) return cudaErrorInvalidValue;
     static bool attr_set = false;  // per instantiation; prepare_v4_t sets it ahead of stream capture
     if (!attr_set) {
-        cudaError_t e = prepare_v4_t<Q, S, CL, LPR>();
+        cudaError_t e = prepare_v4_t<Q, S, CL, LPR, BC>();
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -817,14 +902,14 @@ cudaError_t launch_v4_t(const StepArgs& a, int nbatch, cudaStream_t s, bool tma)
     if (tma) {
         if constexpr (CL != CL_LEARNED) {
             if (!a.tmap_rows || !a.tmap_row1 || a.nx % Sh::TX != 0) return cudaErrorInvalidValue;
-            step_kernel_v4<Q, S, CL, LPR, true><<<grid, block, V4Shape<LPR, S, false, true>::smem_bytes, s>>>(
+            step_kernel_v4<Q, S, CL, LPR, true, BC><<<grid, block, V4Shape<LPR, S, false, true>::smem_bytes, s>>>(
                 a, *static_cast<const CUtensorMap*>(a.tmap_rows), *static_cast<const CUtensorMap*>(a.tmap_row1));
             return cudaGetLastError();
         }
         return cudaErrorNotSupported;
     }
     CUtensorMap none{};
-    step_kernel_v4<Q, S, CL, LPR, false><<<grid, block, Sh::smem_bytes, s>>>(a, none, none);
+    step_kernel_v4<Q, S, CL, LPR, false, BC><<<grid, block, Sh::smem_bytes, s>>>(a, none, none);
     return cudaGetLastError();
 }
 

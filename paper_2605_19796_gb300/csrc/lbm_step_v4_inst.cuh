@@ -4,9 +4,15 @@
 // compile in parallel.
 #pragma once
 
+#include <type_traits>
+
 #include "lbm_step_v4.cuh"
 
 namespace lbmk {
+
+// the channel (bounce-back walls in y, body force), FP32 storage, BGK and KC-MP;
+// defined in lbm_step_v4_walls.cu
+cudaError_t launch_v4_walls(int closure, int ty, bool tma, const StepArgs* a, int nbatch, cudaStream_t s);
 
 template <typename S>
 cudaError_t launch_v4_qs(int closure, int bc, int ty, bool tma, const StepArgs* a, int nbatch, cudaStream_t s)
@@ -15,6 +21,10 @@ cudaError_t launch_v4_qs(int closure, int bc, int ty, bool tma, const StepArgs* 
     // tile_y 8: 128 x 8 tiles (one row per warp); 16: 64 x 16 tiles (two rows per
     // warp); tma (variant 16) stages the rows' interior by TMA (analytic closures)
     if (tma && closure == CL_LEARNED) return cudaErrorNotSupported;
+    if (bc == BC_WALLS_Y) {
+        if constexpr (std::is_same<S, float>::value) return launch_v4_walls(closure, ty, tma, a, nbatch, s);
+        return cudaErrorNotSupported;
+    }
 #define LBM_V4_CASE(CL, TYV, LPRV)                                                                     \
     if (closure == CL && bc == BC_PERIODIC && ty == TYV)                                               \
         return a ? launch_v4_t<Q, S, CL, LPRV>(*a, nbatch, s, tma) : (nbatch < 0 ? prepare_v4_t<Q, S, CL, LPRV>() : cudaSuccess);

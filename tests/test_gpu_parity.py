@@ -465,10 +465,12 @@ def test_default_variant_selection(lbm):
     KC-MP or KC-RB takes the four-cell kernel (14) when nx is a multiple of 8
     (tiles 128 x 8, or 64 x 16 for boxes at most 64 wide), for FP32 storage
     with TMA staging (16) where nx is a multiple of the tile width and ny spans
-    at least eight tiles; otherwise, for FP32
-    storage, periodic D3Q27 with KC-MP or KC-RB the split-barrier pull with L2
-    prefetches (12) on z-chunks of at most 16 planes; KC-RR, D3Q19 and walls
-    with KC-MP the split-barrier pull with asynchronous copies (13); periodic
+    at least eight tiles; the D3Q27 FP32 channel with BGK or KC-MP the
+    four-cell kernel (14) where (ny - 1) is not a multiple of the tile height;
+    otherwise, for FP32 storage, periodic D3Q27 with KC-MP or KC-RB the
+    split-barrier pull with L2 prefetches (12) on z-chunks of at most 16
+    planes; KC-RR, D3Q19 and the other walls with KC-MP the split-barrier pull
+    with asynchronous copies (13); periodic
     D3Q27 otherwise (BGK, FP64, 16-bit storage) the split-barrier pull (8);
     the learned closure on periodic boxes the register pull with the network on
     the tcgen05 tensor cores (15); the rest the register pull (1).  Tiles are
@@ -498,9 +500,12 @@ def test_default_variant_selection(lbm):
                 assert s.launch_config["tile_y"] == 4
             if want == 12:
                 assert s.launch_config["zchunk"] <= 16
-    for q, closure, want in ((27, "kcmp", 13), (19, "kcmp", 13), (27, "kcrb_hermite", 1), (27, "bgk", 1)):
-        with lbm.Solver(q, (40, 32, 16), 1e-4, closure=closure, storage="fp32", bc=(0, 1, 0)) as s:
-            assert s.launch_config["variant"] == want, (q, closure, "walls")
+    # walls: the four-cell kernel for D3Q27 FP32 with BGK or KC-MP where the top
+    # wall row is not the first row of a tile ((ny - 1) % 8 != 0), else variant 13 / 1
+    for q, closure, ny, want in ((27, "kcmp", 32, 14), (27, "bgk", 32, 14), (27, "kcmp", 33, 13),
+                                 (19, "kcmp", 32, 13), (27, "kcrb_hermite", 32, 1), (27, "bgk", 33, 1)):
+        with lbm.Solver(q, (40, ny, 16), 1e-4, closure=closure, storage="fp32", bc=(0, 1, 0)) as s:
+            assert s.launch_config["variant"] == want, (q, closure, ny, "walls")
     for retired in (4, 9):  # the TMA-staged and packed-pair kernels are retired
         with pytest.raises(lbm.LbmError):
             lbm.Solver(27, (64, 32, 16), 1e-4, closure="kcmp", storage="fp32", variant=retired)

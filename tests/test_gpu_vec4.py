@@ -150,3 +150,48 @@ def test_vec4_nonfinite_flag_and_shape_check(lbm, variant):
         s.synchronize()
     with pytest.raises(lbm.LbmError):
         lbm.Solver(27, (44, 16, 8), 1e-4, closure="kcmp", storage="fp32", variant=variant, tile_y=ty)
+
+
+@pytest.mark.parametrize("variant,tile_y", LAUNCHES)
+@pytest.mark.parametrize("shape", [(64, 11, 9), (32, 10, 7), (128, 27, 5)])
+@pytest.mark.parametrize("closure", ["bgk", "kcmp"])
+def test_vec4_channel_fp32(lbm, orc, closure, shape, tile_y, variant):
+    """The channel on the four-cell kernel: halfway bounce-back walls at y = 0
+    and y = ny - 1 (the cell's own opposite population where a pull crosses a
+    wall), the one-sided strain of Eqs. (fd_boundary_lower/upper), the F/2
+    velocity shift and Guo's source.  Against the register pull (variant 1) to
+    FP32 rounding and the FP64 oracle in velocity, over 8 steps and several
+    z-chunkings; ny = 10 puts the top wall row second in its 8-row tile (its
+    one-sided stencil reaches the halo row below the tile), ny = 27 a partial
+    top tile.  (ny - 1) a multiple of the tile height is refused."""
+    force = (2e-5, 0.0, 0.0)
+    nx, ny, nz = shape
+    if variant == 16 and nx % (128 if tile_y == 8 else 64) != 0 or (ny - 1) % tile_y == 0:
+        with pytest.raises(lbm.LbmError) as ei:
+            lbm.Solver(27, shape, 2e-3, closure=closure, storage="fp32", variant=variant, tile_y=tile_y,
+                       bc=(0, 1, 0), force=force)
+        assert ei.value.code == lbm.LBM_ERR_UNSUPPORTED
+        return
+    rho, u = inputs.channel_fields(nx, ny, nz, 0.05, seed=9)
+    nu = 2e-3
+    with lbm.Solver(27, shape, nu, closure=closure, c_nu=CNU[closure], storage="fp32", variant=1, bc=(0, 1, 0),
+                    force=force) as s:
+        s.init_velocity(rho, u)
+        s.step(8)
+        ref = s.get_populations()
+    res = {}
+    for zc in (0, 1, 3):
+        with lbm.Solver(27, shape, nu, closure=closure, c_nu=CNU[closure], storage="fp32", variant=variant,
+                        tile_y=tile_y, zchunk=zc, bc=(0, 1, 0), force=force) as s:
+            assert s.launch_config["variant"] == variant and s.launch_config["tile_y"] == tile_y
+            s.init_velocity(rho, u)
+            s.step(8)
+            res[zc] = s.get_populations()
+    for zc in (1, 3):
+        assert np.array_equal(res[zc], res[0]), zc
+    assert rel(res[0], ref) < 1e-6, rel(res[0], ref)
+    fo = orc.run(orc.init_equilibrium(27, rho, u), 8, closure=CL[closure], nu=nu, c_nu=CNU[closure], bc=(0, 1, 0),
+                 F=force)
+    _, ug = orc.fields(res[0], F=force)
+    _, uo = orc.fields(fo, F=force)
+    assert np.abs(ug - uo).max() < 1e-6, np.abs(ug - uo).max()

@@ -508,7 +508,7 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
                              cfg->closure == LBM_KCRB_RAW || cfg->closure == LBM_KCRR;
         const bool split_built = carrier || cfg->closure == LBM_BGK;
         // 128 x 8 tiles, or 64 x 16 for boxes at most 64 wide and for the channel
-        // (512 x 256 x 256 KC-MP: 17.7 GLUPS against 15.2 on 128 x 8 tiles)
+        // (512 x 256 x 256 KC-MP: 20.3 GLUPS against 19.9 on 128 x 8 tiles)
         const int v4_ty0 = cfg->tile_y ? cfg->tile_y : ((cfg->nx > 64 && bc_kind == BC_PERIODIC) ? 8 : 16);
         // the channel: FP32, BGK or KC-MP, the top wall row not the first row of a tile
         const bool v4_walls = bc_kind == BC_WALLS_Y && cfg->storage == LBM_FP32 &&
@@ -577,6 +577,9 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
     h->zchunk = cfg->zchunk ? cfg->zchunk : default_zchunk(cfg->nx, cfg->ny, cfg->nz, cfg->nbatch, tile_y);
     if (!cfg->zchunk && short_chunks && h->zchunk > 16) h->zchunk = 16;
     if (!cfg->zchunk && vec4_chunks) h->zchunk = default_zchunk_vec4(cfg->nx, cfg->ny, cfg->nz, cfg->nbatch, tile_y);
+    // the channel on the four-cell kernel prefers shorter chunks (512 x 256 x 256
+    // KC-MP on 64 x 16 tiles: 24 planes 20.7 GLUPS, 40: 20.3, 64: 19.2)
+    if (!cfg->zchunk && vec4_chunks && bc_kind == BC_WALLS_Y && h->zchunk > 24) h->zchunk = 24;
     // the learned closure's network-heavy CTAs balance better over about twice
     // as many, half as long chunks (256^3, register pull on 4-row tiles: 26
     // planes 8.43 GLUPS, 52 planes 8.28, 16 planes 8.18)

@@ -96,7 +96,9 @@ __device__ __forceinline__ void v4_store(__nv_bfloat16* p, float a, float b, flo
 // Tensor Memory Accelerator, one cp.async.bulk.tensor per population and plane
 // into [27][RY][TX], and only the x-edge chunks (x0 - 4 .. x0 - 1 and x0 + TX ..
 // x0 + TX + 3 of every staged row) by cp.async, into [27][RY][8].
-template <int LPR, typename S, bool LEARNED = false, bool TMAS = false>
+// WALLS: a buffer [2][9][TX] for the bounce-back values of the wall rows (the
+// cells' own opposite populations, copied with the plane's staging).
+template <int LPR, typename S, bool LEARNED = false, bool TMAS = false, bool WALLS = false>
 struct V4Shape {
     static constexpr int NT = 256;
     static constexpr int RPW = 32 / LPR;  // tile rows per warp
@@ -119,8 +121,10 @@ struct V4Shape {
     static_assert(!TMAS || (RY * TX * sizeof(S)) % 128 == 0, "each population's TMA box 128-byte aligned");
     static_assert(!(TMAS && LEARNED), "TMA staging is built for the analytic closures");
     static_assert(!TMAS || (NPOS <= 40 && 40 + 8 * 26 < NT), "TMA issuing threads apart from the x-edge threads");
+    static constexpr size_t bb_off = stg_off + stg_bytes;
+    static constexpr size_t bb_bytes = WALLS ? sizeof(S) * (size_t)2 * 9 * TX : 0;
     // learned closure: the packed network and one 32-row exchange per warp
-    static constexpr size_t mlp_off = stg_off + stg_bytes;
+    static constexpr size_t mlp_off = bb_off + bb_bytes;
     static constexpr size_t mlp_bytes = LEARNED ? (size_t)MlpLayout::BYTES + 8 * (size_t)MlpLayout::XCH_BYTES : 0;
     static constexpr size_t used = mlp_off + mlp_bytes;
     // at least 116 KB, so that two CTAs never share an SM (each allocates all
@@ -281,7 +285,7 @@ __global__ void __launch_bounds__(256, 1)
     constexpr bool LEARNED = CL == CL_LEARNED;
     constexpr bool WALLS = BC == BC_WALLS_Y;
     static_assert(!(WALLS && LEARNED), "the learned closure runs on periodic boxes");
-    using Sh = V4Shape<LPR, S, LEARNED, TMAS>;
+    using Sh = V4Shape<LPR, S, LEARNED, TMAS, WALLS>;
     constexpr int TX = Sh::TX, TY = Sh::TY, RY = Sh::RY, RP = Sh::RP, NB = Sh::NB, NT = Sh::NT, NCH = Sh::NCH;
     constexpr int NHK = (NB + NT - 1) / NT;  // halo cells per thread (at most)
     constexpr bool SHIFTED = StoreTraits<S>::shifted;
@@ -293,6 +297,7 @@ __global__ void __launch_bounds__(256, 1)
     float* ring = reinterpret_cast<float*>(smem_v4 + Sh::ring_off);  // [NSLOT][3][RY][RP]
     S* stg = reinterpret_cast<S*>(smem_v4 + Sh::stg_off);            // [27][RY][RP] (TMAS: [27][RY][TX])
     S* stge = stg + 27 * RY * TX;                                     // TMAS: x-edge chunks [27][RY][8]
+    S* bbs = reinterpret_cast<S*>(smem_v4 + Sh::bb_off);              // WALLS: [2][9][TX] bounce-back values
     unsigned char* sm_mlp = smem_v4 + Sh::mlp_off;                   // learned closure only
     unsigned char* sm_xch = sm_mlp + MlpLayout::BYTES + (threadIdx.x >> 5) * MlpLayout::XCH_BYTES;
 
@@ -460,6 +465,15 @@ __global__ void __launch_bounds__(256, 1)
             if (pos_r >= 0)
                 cp_async_chunk<S>((uint32_t)__cvta_generic_to_shared(stg_at(i, pos_r, pos_col)),
                                   base + yr_pos[1 - cy] + pos_x);
+            // a wall row's bounce-back values: population 26 - i of its own cells (plane
+            // z) for the pulls i that cross the wall, slot 0 lower wall, 1 upper
+            if constexpr (WALLS && cy != 0) {
+                if (cy == 1 ? wall_lo : wall_hi) {
+                    constexpr int qb = 3 * (cz + 1) + (i % 3);
+                    cp_async_chunk<S>((uint32_t)__cvta_generic_to_shared(bbs + ((cy == 1 ? 0 : 9) + qb) * TX + 4 * lx),
+                                      fin + (long long)(26 - i) * ps + zr[1] + yr_own[1] + xaw);
+                }
+            }
         });
         cp_async_commit();
         cp_async_arrive(&mbar[2]);
@@ -520,10 +534,20 @@ __global__ void __launch_bounds__(256, 1)
                 }
                 if constexpr (WALLS && cy != 0) {
                     // halfway bounce-back: a pull across the wall takes the cell's own
-                    // post-collision opposite population (same plane)
-                    if (cy == 1 ? wall_lo : wall_hi) {
+                    // post-collision opposite population (same plane); from the staged
+                    // copy, read by every thread and selected, so that no branch splits
+                    // the triple's loads
+                    const bool wl = cy == 1 ? wall_lo : wall_hi;
+                    constexpr float w = SHIFTED ? 0.f : (float)weight_of(Q, i);
+                    if constexpr (STAGED && !TMAS) {
+                        constexpr int qb = 3 * (cz + 1) + (i % 3);
+                        const float4 b = v4_lds(bbs + ((cy == 1 ? 0 : 9) + qb) * TX + 4 * lx);
+                        g[k][0] = wl ? b.x - w : g[k][0];
+                        g[k][1] = wl ? b.y - w : g[k][1];
+                        g[k][2] = wl ? b.z - w : g[k][2];
+                        g[k][3] = wl ? b.w - w : g[k][3];
+                    } else if (wl) {
                         const float4 b = v4_load(fin + (long long)(26 - i) * ps + zr[1] + yr_own[1] + xaw);
-                        constexpr float w = SHIFTED ? 0.f : (float)weight_of(Q, i);
                         g[k][0] = b.x - w;
                         g[k][1] = b.y - w;
                         g[k][2] = b.z - w;
@@ -596,17 +620,27 @@ __global__ void __launch_bounds__(256, 1)
                 float gh[Q];
                 static_for<27>([&](auto I) {
                     constexpr int i = decltype(I)::value;
-                    constexpr int cx = i % 3 - 1, cy = (i / 3) % 3 - 1;
-                    float v = v4_cvt(*stg_at(i, r, xr4 - cx));
-                    if constexpr (WALLS && cy != 0) {  // bounce-back at a wall row (x-halo cells)
-                        if (cy == 1 ? hlo : hhi) {
-                            int zr[3];
-                            zrows(z, zr);
-                            v = v1_load(fin + (long long)(26 - i) * ps + zr[1] + yh * nx + (x0 + hal_xr[k] + nx) % nx);
-                        }
-                    }
+                    constexpr int cx = i % 3 - 1;
+                    const float v = v4_cvt(*stg_at(i, r, xr4 - cx));
                     gh[i] = SHIFTED ? v : v - (float)weight_of(Q, i);
                 });
+                if constexpr (WALLS) {
+                    if (hlo || hhi) {  // bounce-back at a wall row (x-halo cells)
+                        int zr[3];
+                        zrows(z, zr);
+                        const S* cellp = fin + zr[1] + yh * nx + (x0 + hal_xr[k] + nx) % nx;
+                        static_for<27>([&](auto I) {
+                            constexpr int i = decltype(I)::value;
+                            constexpr int cy = (i / 3) % 3 - 1;
+                            if constexpr (cy != 0) {
+                                if (cy == 1 ? hlo : hhi) {
+                                    const float v = v1_load(cellp + (long long)(26 - i) * ps);
+                                    gh[i] = SHIFTED ? v : v - (float)weight_of(Q, i);
+                                }
+                            }
+                        });
+                    }
+                }
                 float dh, vx, vy, vz;
                 moments<Q, float>(gh, dh, vx, vy, vz, Fx, Fy, Fz);
                 const int pos = r * RP + xr4;
@@ -871,11 +905,11 @@ template <int Q, typename S, int CL, int LPR, int BC = BC_PERIODIC>
 cudaError_t prepare_v4_t()
 {
     cudaError_t e = cudaFuncSetAttribute(step_kernel_v4<Q, S, CL, LPR, false, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)V4Shape<LPR, S, CL == CL_LEARNED, false>::smem_bytes);
+                                         (int)V4Shape<LPR, S, CL == CL_LEARNED, false, BC == BC_WALLS_Y>::smem_bytes);
     if constexpr (CL != CL_LEARNED) {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(step_kernel_v4<Q, S, CL, LPR, true, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)V4Shape<LPR, S, false, true>::smem_bytes);
+                                     (int)V4Shape<LPR, S, false, true, BC == BC_WALLS_Y>::smem_bytes);
     }
     return e;
 }
@@ -886,7 +920,7 @@ cudaError_t prepare_v4_t()
 template <int Q, typename S, int CL, int LPR, int BC = BC_PERIODIC>
 cudaError_t launch_v4_t(const StepArgs& a, int nbatch, cudaStream_t s, bool tma)
 {
-    using Sh = V4Shape<LPR, S, CL == CL_LEARNED>;
+    using Sh = V4Shape<LPR, S, CL == CL_LEARNED, false, BC == BC_WALLS_Y>;
     if (!v4_shape_ok(a.nx)) return cudaErrorInvalidValue;
     if (CL == CL_LEARNED && !a.mlp) return cudaErrorInvalidValue;
     if (BC == BC_WALLS_Y && (a.ny < 3 || (a.ny - 1) % Sh::TY == 0)) return cudaErrorInvalidValue;
@@ -902,7 +936,7 @@ cudaError_t launch_v4_t(const StepArgs& a, int nbatch, cudaStream_t s, bool tma)
     if (tma) {
         if constexpr (CL != CL_LEARNED) {
             if (!a.tmap_rows || !a.tmap_row1 || a.nx % Sh::TX != 0) return cudaErrorInvalidValue;
-            step_kernel_v4<Q, S, CL, LPR, true, BC><<<grid, block, V4Shape<LPR, S, false, true>::smem_bytes, s>>>(
+            step_kernel_v4<Q, S, CL, LPR, true, BC><<<grid, block, V4Shape<LPR, S, false, true, BC == BC_WALLS_Y>::smem_bytes, s>>>(
                 a, *static_cast<const CUtensorMap*>(a.tmap_rows), *static_cast<const CUtensorMap*>(a.tmap_row1));
             return cudaGetLastError();
         }

@@ -26,12 +26,22 @@
 //    256 each.  The stash thus needs neither shared memory nor registers, and a
 //    1024-cell tile (whose halo costs a quarter or less of its own pulls) fits
 //    on one SM.
-//  * Velocities go through a ring of three planes in shared memory: the own
-//    cells' and the halo cells' (rows y0 - 1 and y0 + TY, columns x0 - 1 and
-//    x0 + TX, one cell per thread from the staged values).  The z-neighbours
-//    of the own cells stay in registers.  A thread that writes plane p has
-//    passed the barrier of plane p-1 (every thread has published it, after its
-//    strain reads of plane p-2), so nobody reads the slot of plane p-3 any more.
+//  * Velocities go through a ring of planes in shared memory: the own cells'
+//    and the halo cells' (rows y0 - 1 and y0 + TY, columns x0 - 1 and x0 + TX,
+//    one cell per thread from the staged values).  With three slots the
+//    z-neighbours of the own cells stay in registers; a thread that writes
+//    plane p has passed the barrier of plane p-1 (every thread has published
+//    it, after its strain reads of plane p-2), so nobody reads the slot of
+//    plane p-3 any more.  With four (v4_ring4: the TMA-staged KC kernels of the
+//    periodic box) the strain of plane z reads the slots of planes z - 1, z and
+//    z + 1 (the z-neighbours only at the thread's own cells, which it wrote
+//    itself), every thread has done its strain reads of plane p-3 when plane p
+//    is written, and the 36 registers no longer carried from plane to plane
+//    let the collision load its TMEM populations one triple ahead.  Measured
+//    (512^3 FP32, GLUPS): KC-MP 26.55 against 26.4, KC-RB raw 27.3 against
+//    26.8; BGK (29.3 against 29.7), the cp.async-staged kernels (FP32 24.0
+//    against 24.6, FP16 28.5 against 29.4, the 64^3 ensemble 21.7 against
+//    22.6) and the walls (spills) keep three.
 //  * The collision relaxes the four cells together, one (c_y, c_z) population
 //    triple at a time, in the common form g' = a g + w (b (P - 1) + c0 + D H)
 //    of collide() with P - 1 = e_x (1 + Y) + Y, Y = e_y + e_z + e_y e_z, and
@@ -98,7 +108,14 @@ __device__ __forceinline__ void v4_store(__nv_bfloat16* p, float a, float b, flo
 // x0 + TX + 3 of every staged row) by cp.async, into [27][RY][8].
 // WALLS: a buffer [2][9][TX] for the bounce-back values of the wall rows (the
 // cells' own opposite populations, copied with the plane's staging).
-template <int LPR, typename S, bool LEARNED = false, bool TMAS = false, bool WALLS = false>
+// four ring slots (the z-neighbours read from the ring, the TMEM loads one
+// triple ahead): the TMA-staged kernel of the periodic box with the KC closures
+__host__ __device__ constexpr bool v4_ring4(bool tmas, int cl, int bc)
+{
+    return tmas && bc == BC_PERIODIC && cl != CL_BGK && cl != CL_LEARNED;
+}
+
+template <int LPR, typename S, bool LEARNED = false, bool TMAS = false, bool WALLS = false, bool RZ4 = false>
 struct V4Shape {
     static constexpr int NT = 256;
     static constexpr int RPW = 32 / LPR;  // tile rows per warp
@@ -106,7 +123,8 @@ struct V4Shape {
     static constexpr int TY = 8 * RPW;
     static constexpr int RY = TY + 2;      // ring and staged rows: y0 - 1 .. y0 + TY
     static constexpr int RP = TX + 8;      // ring and staging pitch: x0 - 4 .. x0 + TX + 3, own cells at 4 .. TX + 3
-    static constexpr int NSLOT = 3;
+    static constexpr int NSLOT = RZ4 ? 4 : 3;
+    static_assert(!RZ4 || (!LEARNED && !WALLS), "four ring slots: periodic boxes, analytic closures");
     static constexpr int NB = 2 * TX + 2 * TY;     // halo cells of a ring plane (no corners)
     static constexpr int NCH = TX / 4;             // 4-cell chunks of a row
     // staged chunks beyond the own ones: halo rows and x-edge chunks (TMAS: the x-edge chunks)
@@ -285,11 +303,12 @@ __global__ void __launch_bounds__(256, 1)
     constexpr bool LEARNED = CL == CL_LEARNED;
     constexpr bool WALLS = BC == BC_WALLS_Y;
     static_assert(!(WALLS && LEARNED), "the learned closure runs on periodic boxes");
-    using Sh = V4Shape<LPR, S, LEARNED, TMAS, WALLS>;
+    using Sh = V4Shape<LPR, S, LEARNED, TMAS, WALLS, v4_ring4(TMAS, CL, BC)>;
     constexpr int TX = Sh::TX, TY = Sh::TY, RY = Sh::RY, RP = Sh::RP, NB = Sh::NB, NT = Sh::NT, NCH = Sh::NCH;
     constexpr int NHK = (NB + NT - 1) / NT;  // halo cells per thread (at most)
     constexpr bool SHIFTED = StoreTraits<S>::shifted;
     constexpr unsigned FULL = 0xffffffffu;
+    constexpr bool RZ = Sh::NSLOT == 4;  // the own cells' z-neighbours read from the ring
 
     extern __shared__ __align__(16) unsigned char smem_v4[];
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_v4);  // [0], [1]: ring planes, [2]: staging
@@ -659,6 +678,7 @@ __global__ void __launch_bounds__(256, 1)
         issue(z0);
         float dd[4], PP[6][4];  // the first plane's z-neighbour, loaded while plane z0 is staged
         pull_own(std::false_type{}, std::false_type{}, z0 - 1, dd, um, PP);
+        if constexpr (RZ) put_own(z0 - 1, um);
         ok = __all_sync(FULL, staged_wait(z0));
         if (ok) {
             pull_own(std::true_type{}, std::true_type{}, z0, dr0, u0, P0);
@@ -693,44 +713,65 @@ __global__ void __launch_bounds__(256, 1)
             if (z + 2 <= z1) issue(z + 2);
         } else {
             pull_own(std::false_type{}, std::true_type{}, z + 1, dr1, u1, P1);  // z-neighbour of the chunk's last plane
+            if constexpr (RZ) put_own(z + 1, u1);
         }
 
         // ---- plane z: neighbours' velocities, strain, closure, relaxation, store
         // du[a][b][c] = d_a u_b of cell c
         float S6[6][4];
+        float uo[3][4];  // the own cells' u at z
         {
             float du[3][3][4];
             const int s0 = rslot(z);
 #pragma unroll
             for (int b = 0; b < 3; ++b) {
                 const float* r = ringp(s0, b) + ry_own * RP + rx_own;
+                if constexpr (RZ) {
+                    const float4 c4 = *reinterpret_cast<const float4*>(r);
+                    uo[b][0] = c4.x;
+                    uo[b][1] = c4.y;
+                    uo[b][2] = c4.z;
+                    uo[b][3] = c4.w;
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) uo[b][c] = u0[b][c];
+                }
                 const float ul = r[-1], ur = r[4];
                 const float4 yn = *reinterpret_cast<const float4*>(r - RP);
                 const float4 yp = *reinterpret_cast<const float4*>(r + RP);
-                du[0][b][0] = 0.5f * (u0[b][1] - ul);
-                du[0][b][1] = 0.5f * (u0[b][2] - u0[b][0]);
-                du[0][b][2] = 0.5f * (u0[b][3] - u0[b][1]);
-                du[0][b][3] = 0.5f * (ur - u0[b][2]);
+                du[0][b][0] = 0.5f * (uo[b][1] - ul);
+                du[0][b][1] = 0.5f * (uo[b][2] - uo[b][0]);
+                du[0][b][2] = 0.5f * (uo[b][3] - uo[b][1]);
+                du[0][b][3] = 0.5f * (ur - uo[b][2]);
                 if (WALLS && wall_lo) {  // one-sided at the lower wall, Eq. (fd_boundary_lower)
                     const float4 y2 = *reinterpret_cast<const float4*>(r + 2 * RP);
-                    du[1][b][0] = 0.5f * (-3.f * u0[b][0] + 4.f * yp.x - y2.x);
-                    du[1][b][1] = 0.5f * (-3.f * u0[b][1] + 4.f * yp.y - y2.y);
-                    du[1][b][2] = 0.5f * (-3.f * u0[b][2] + 4.f * yp.z - y2.z);
-                    du[1][b][3] = 0.5f * (-3.f * u0[b][3] + 4.f * yp.w - y2.w);
+                    du[1][b][0] = 0.5f * (-3.f * uo[b][0] + 4.f * yp.x - y2.x);
+                    du[1][b][1] = 0.5f * (-3.f * uo[b][1] + 4.f * yp.y - y2.y);
+                    du[1][b][2] = 0.5f * (-3.f * uo[b][2] + 4.f * yp.z - y2.z);
+                    du[1][b][3] = 0.5f * (-3.f * uo[b][3] + 4.f * yp.w - y2.w);
                 } else if (WALLS && wall_hi) {  // one-sided at the upper wall, Eq. (fd_boundary_upper)
                     const float4 y2 = *reinterpret_cast<const float4*>(r - 2 * RP);
-                    du[1][b][0] = 0.5f * (3.f * u0[b][0] - 4.f * yn.x + y2.x);
-                    du[1][b][1] = 0.5f * (3.f * u0[b][1] - 4.f * yn.y + y2.y);
-                    du[1][b][2] = 0.5f * (3.f * u0[b][2] - 4.f * yn.z + y2.z);
-                    du[1][b][3] = 0.5f * (3.f * u0[b][3] - 4.f * yn.w + y2.w);
+                    du[1][b][0] = 0.5f * (3.f * uo[b][0] - 4.f * yn.x + y2.x);
+                    du[1][b][1] = 0.5f * (3.f * uo[b][1] - 4.f * yn.y + y2.y);
+                    du[1][b][2] = 0.5f * (3.f * uo[b][2] - 4.f * yn.z + y2.z);
+                    du[1][b][3] = 0.5f * (3.f * uo[b][3] - 4.f * yn.w + y2.w);
                 } else {
                     du[1][b][0] = 0.5f * (yp.x - yn.x);
                     du[1][b][1] = 0.5f * (yp.y - yn.y);
                     du[1][b][2] = 0.5f * (yp.z - yn.z);
                     du[1][b][3] = 0.5f * (yp.w - yn.w);
                 }
+                if constexpr (RZ) {
+                    const float4 zp = *reinterpret_cast<const float4*>(ringp(rslot(z + 1), b) + ry_own * RP + rx_own);
+                    const float4 zm = *reinterpret_cast<const float4*>(ringp(rslot(z - 1), b) + ry_own * RP + rx_own);
+                    du[2][b][0] = 0.5f * (zp.x - zm.x);
+                    du[2][b][1] = 0.5f * (zp.y - zm.y);
+                    du[2][b][2] = 0.5f * (zp.z - zm.z);
+                    du[2][b][3] = 0.5f * (zp.w - zm.w);
+                } else {
 #pragma unroll
-                for (int c = 0; c < 4; ++c) du[2][b][c] = 0.5f * (u1[b][c] - um[b][c]);
+                    for (int c = 0; c < 4; ++c) du[2][b][c] = 0.5f * (u1[b][c] - um[b][c]);
+                }
             }
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
@@ -749,7 +790,7 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const float P6[6] = {P0[0][c], P0[1][c], P0[2][c], P0[3][c], P0[4][c], P0[5][c]};
-                v4_learned_msgs(P6, dr0[c], u0[0][c], u0[1][c], u0[2][c], S6[0][c], S6[1][c], S6[2][c], S6[3][c],
+                v4_learned_msgs(P6, dr0[c], uo[0][c], uo[1][c], uo[2][c], S6[0][c], S6[1][c], S6[2][c], S6[3][c],
                                 S6[4][c], S6[5][c], tau_hat, sm_mlp, sm_xch, lane, msg[c]);
             }
         }
@@ -761,12 +802,12 @@ __global__ void __launch_bounds__(256, 1)
             constexpr float a0 = (float)(-kTheta / (2.0 * kTheta * kTheta));
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                if (own_store && !isfinite(dr0[c] + u0[0][c] + u0[1][c] + u0[2][c])) atomicOr(a.flag, kFlagNonfinite);
+                if (own_store && !isfinite(dr0[c] + uo[0][c] + uo[1][c] + uo[2][c])) atomicOr(a.flag, kFlagNonfinite);
                 const float P6[6] = {P0[0][c], P0[1][c], P0[2][c], P0[3][c], P0[4][c], P0[5][c]};
-                const Coef<float> k = collide_coef<Q, float, CL>(P6, dr0[c], u0[0][c], u0[1][c], u0[2][c], S6[0][c],
+                const Coef<float> k = collide_coef<Q, float, CL>(P6, dr0[c], uo[0][c], uo[1][c], uo[2][c], S6[0][c],
                                                                  S6[1][c], S6[2][c], S6[3][c], S6[4][c], S6[5][c],
                                                                  omega, tau_hat, nu, cnud, LEARNED ? msg[c] : nullptr);
-                const float ux = u0[0][c], uy = u0[1][c], uz = u0[2][c];
+                const float ux = uo[0][c], uy = uo[1][c], uz = uo[2][c];
                 const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
                 if constexpr (WALLS) {
                     K[c].ux = ux;
@@ -807,13 +848,21 @@ __global__ void __launch_bounds__(256, 1)
         {
             const uint32_t ts = tslot(z);
             const int cell = z * plane + gyw * nx + xaw;
+            // the triples' populations come from TMEM one triple ahead (PF): the load
+            // of triple p + 1 is issued once triple p's has completed (tcgen05.wait::ld
+            // waits for all of the thread's loads), and lands while triple p is
+            // relaxed and stored and triple p + 1's constants are formed.  Kernels
+            // that carry the z-neighbours in registers have no registers for the
+            // second triple: they issue each triple's load before forming its
+            // constants.
+            constexpr bool PF = RZ;
+            uint32_t gr[2][12];
+            if constexpr (PF) tm_ld12_issue(ts, gr[0]);
             static_for<9>([&](auto PI) {
                 constexpr int p = decltype(PI)::value;
                 constexpr int cy = p % 3 - 1, cz = p / 3 - 1, pat = v4_pat(cy, cz);
-                // the triple's populations are on their way from TMEM while the
-                // per-triple constants are formed
-                uint32_t gr[12];
-                tm_ld12_issue(ts + 12u * p, gr);
+                constexpr int sl = PF ? (p & 1) : 0;
+                if constexpr (!PF) tm_ld12_issue(ts + 12u * p, gr[0]);
                 float Y[4], B[4], Cm[4], Cp[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
@@ -831,10 +880,11 @@ __global__ void __launch_bounds__(256, 1)
                         Cp[c] = Cm[c] = K[c].C[pat];
                     }
                 }
-                tm_ld12_wait(gr);
+                tm_ld12_wait(gr[sl]);
                 float g[3][4];
 #pragma unroll
-                for (int q = 0; q < 12; ++q) g[q / 4][q % 4] = __uint_as_float(gr[q]);
+                for (int q = 0; q < 12; ++q) g[q / 4][q % 4] = __uint_as_float(gr[sl][q]);
+                if constexpr (PF && p < 8) tm_ld12_issue(ts + 12u * (p + 1), gr[(p + 1) & 1]);
                 // Guo's source (walls with a force): (1 - omega/2) w [(c - u)/theta + (c.u) c/theta^2].F
                 // is G0 + c_x G1 + c_x^2 G2 along a triple, with P1 = (1 - omega/2)/theta,
                 // P2 = P1/theta, BF = c_y F_y + c_z F_z, Bu = c_y u_y + c_z u_z:
@@ -876,10 +926,12 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             dr0[c] = dr1[c];
+            if constexpr (!RZ) {
 #pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                um[b][c] = u0[b][c];
-                u0[b][c] = u1[b][c];
+                for (int b = 0; b < 3; ++b) {
+                    um[b][c] = u0[b][c];
+                    u0[b][c] = u1[b][c];
+                }
             }
 #pragma unroll
             for (int q = 0; q < 6; ++q) P0[q][c] = P1[q][c];
@@ -909,7 +961,7 @@ cudaError_t prepare_v4_t()
     if constexpr (CL != CL_LEARNED) {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(step_kernel_v4<Q, S, CL, LPR, true, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)V4Shape<LPR, S, false, true, BC == BC_WALLS_Y>::smem_bytes);
+                                     (int)V4Shape<LPR, S, false, true, BC == BC_WALLS_Y, v4_ring4(true, CL, BC)>::smem_bytes);
     }
     return e;
 }
@@ -936,7 +988,8 @@ cudaError_t launch_v4_t(const StepArgs& a, int nbatch, cudaStream_t s, bool tma)
     if (tma) {
         if constexpr (CL != CL_LEARNED) {
             if (!a.tmap_rows || !a.tmap_row1 || a.nx % Sh::TX != 0) return cudaErrorInvalidValue;
-            step_kernel_v4<Q, S, CL, LPR, true, BC><<<grid, block, V4Shape<LPR, S, false, true, BC == BC_WALLS_Y>::smem_bytes, s>>>(
+            step_kernel_v4<Q, S, CL, LPR, true, BC>
+                <<<grid, block, V4Shape<LPR, S, false, true, BC == BC_WALLS_Y, v4_ring4(true, CL, BC)>::smem_bytes, s>>>(
                 a, *static_cast<const CUtensorMap*>(a.tmap_rows), *static_cast<const CUtensorMap*>(a.tmap_row1));
             return cudaGetLastError();
         }

@@ -154,7 +154,6 @@ struct V4Shape {
 // relaxation constants of one cell (collide_coef in the per-triple form)
 struct V4Cell {
     float ca, cb, ex[3], ey[3], ez[3], C[5], Dxx, Dxy2, Dxz2;
-    float ux, uy, uz, uF;  // walls with a body force: Guo's source
 };
 
 // index of the (c_y, c_z) part of H: (0,0), (+-1,0), (0,+-1), c_y c_z = 1, c_y c_z = -1
@@ -809,12 +808,6 @@ __global__ void __launch_bounds__(256, 1)
                                                                  omega, tau_hat, nu, cnud, LEARNED ? msg[c] : nullptr);
                 const float ux = uo[0][c], uy = uo[1][c], uz = uo[2][c];
                 const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
-                if constexpr (WALLS) {
-                    K[c].ux = ux;
-                    K[c].uy = uy;
-                    K[c].uz = uz;
-                    K[c].uF = ux * Fx + uy * Fy + uz * Fz;
-                }
                 K[c].ex[0] = -a1 * ux + a2 * ux2;
                 K[c].ex[1] = a0 * ux2;
                 K[c].ex[2] = a1 * ux + a2 * ux2;
@@ -842,6 +835,22 @@ __global__ void __launch_bounds__(256, 1)
                     K[c].Dxy2 = 2.f * k.D * k.Mxy;
                     K[c].Dxz2 = 2.f * k.D * k.Mxz;
                 }
+                if constexpr (WALLS) {
+                    // Guo's source over w, P1 (c.F - u.F) + P2 (c.u)(c.F) with P1 = (1 - omega/2)/theta
+                    // and P2 = P1/theta: its parts quadratic in c and the constant join the
+                    // per-cell quadratic form (the (c_y, c_z) patterns, c_x^2, c_x c_y, c_x c_z),
+                    // its part linear in c, uniform over the box, the per-triple constants below
+                    const float yF = gp2 * uy * Fy, zF = gp2 * uz * Fz, yzF = gp2 * (uy * Fz + uz * Fy);
+                    const float cF = -gp1 * (ux * Fx + uy * Fy + uz * Fz);
+                    K[c].C[0] += cF;
+                    K[c].C[1] += cF + yF;
+                    K[c].C[2] += cF + zF;
+                    K[c].C[3] += cF + (yF + zF) + yzF;
+                    K[c].C[4] += cF + (yF + zF) - yzF;
+                    K[c].Dxx += gp2 * ux * Fx;
+                    K[c].Dxy2 += gp2 * (ux * Fy + uy * Fx);
+                    K[c].Dxz2 += gp2 * (ux * Fz + uz * Fx);
+                }
             }
         }
         // relaxation, one population triple of the four cells at a time
@@ -863,17 +872,23 @@ __global__ void __launch_bounds__(256, 1)
                 constexpr int cy = p % 3 - 1, cz = p / 3 - 1, pat = v4_pat(cy, cz);
                 constexpr int sl = PF ? (p & 1) : 0;
                 if constexpr (!PF) tm_ld12_issue(ts + 12u * p, gr[0]);
-                float Y[4], B[4], Cm[4], Cp[4];
+                float Y[4], B[4], Cm[4], Cp[4], Cz[4];
+                // walls: Guo's source part linear in c, P1 (c_y F_y + c_z F_z) on the
+                // triple and P1 F_x c_x
+                float BFg = 0.f;
+                if constexpr (WALLS && cy != 0) BFg += (float)cy * (gp1 * Fy);
+                if constexpr (WALLS && cz != 0) BFg += (float)cz * (gp1 * Fz);
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     const float ey = K[c].ey[cy + 1], ez = K[c].ez[cz + 1];
                     Y[c] = fmaf(ey, ez, ey + ez);
                     B[c] = 1.f + Y[c];
-                    if constexpr (CL != CL_BGK) {
-                        float X = 0.f;
+                    Cz[c] = (WALLS && (cy != 0 || cz != 0)) ? K[c].C[pat] + BFg : K[c].C[pat];
+                    if constexpr (CL != CL_BGK || WALLS) {
+                        float X = WALLS ? gp1 * Fx : 0.f;
                         if constexpr (cy != 0) X += (float)cy * K[c].Dxy2;
                         if constexpr (cz != 0) X += (float)cz * K[c].Dxz2;
-                        const float CpD = K[c].C[pat] + K[c].Dxx;
+                        const float CpD = Cz[c] + K[c].Dxx;
                         Cp[c] = CpD + X;
                         Cm[c] = CpD - X;
                     } else {
@@ -885,25 +900,6 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
                 for (int q = 0; q < 12; ++q) g[q / 4][q % 4] = __uint_as_float(gr[sl][q]);
                 if constexpr (PF && p < 8) tm_ld12_issue(ts + 12u * (p + 1), gr[(p + 1) & 1]);
-                // Guo's source (walls with a force): (1 - omega/2) w [(c - u)/theta + (c.u) c/theta^2].F
-                // is G0 + c_x G1 + c_x^2 G2 along a triple, with P1 = (1 - omega/2)/theta,
-                // P2 = P1/theta, BF = c_y F_y + c_z F_z, Bu = c_y u_y + c_z u_z:
-                //   G0 = P1 (BF - u.F) + P2 Bu BF,  G1 = P1 F_x + P2 (u_x BF + F_x Bu),  G2 = P2 u_x F_x;
-                // it joins the constant of each population of the triple
-                float Cz[4];
-                if constexpr (WALLS) {
-                    const float BF = (float)cy * Fy + (float)cz * Fz;
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const float Bu = (float)cy * K[c].uy + (float)cz * K[c].uz;
-                        const float G0 = fmaf(gp2 * Bu, BF, gp1 * (BF - K[c].uF));
-                        const float G1 = fmaf(gp2, fmaf(K[c].ux, BF, Fx * Bu), gp1 * Fx);
-                        const float G2 = gp2 * K[c].ux * Fx;
-                        Cz[c] = K[c].C[pat] + G0;
-                        Cp[c] += G0 + G1 + G2;
-                        Cm[c] += G0 - G1 + G2;
-                    }
-                }
                 static_for<3>([&](auto CI) {
                     constexpr int k = decltype(CI)::value;
                     constexpr int cx = k - 1, i = 3 * p + k;
@@ -912,7 +908,7 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
                         const float pm1 = fmaf(K[c].ex[k], B[c], Y[c]);
-                        const float Cc = cx == 0 ? (WALLS ? Cz[c] : K[c].C[pat]) : (cx == 1 ? Cp[c] : Cm[c]);
+                        const float Cc = cx == 0 ? Cz[c] : (cx == 1 ? Cp[c] : Cm[c]);
                         const float Kv = fmaf(K[c].cb, pm1, Cc);
                         // FP32 storage stores f = g' + w: w (1 + K) in one rounding, so
                         // that no part of K is lost to a sum near 1 (its small terms

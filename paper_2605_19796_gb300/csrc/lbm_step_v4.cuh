@@ -32,16 +32,16 @@
 //    z-neighbours of the own cells stay in registers; a thread that writes
 //    plane p has passed the barrier of plane p-1 (every thread has published
 //    it, after its strain reads of plane p-2), so nobody reads the slot of
-//    plane p-3 any more.  With four (v4_ring4: the TMA-staged KC kernels of the
-//    periodic box) the strain of plane z reads the slots of planes z - 1, z and
-//    z + 1 (the z-neighbours only at the thread's own cells, which it wrote
-//    itself), every thread has done its strain reads of plane p-3 when plane p
-//    is written, and the 36 registers no longer carried from plane to plane
-//    let the collision load its TMEM populations one triple ahead.  Measured
-//    (512^3 FP32, GLUPS): KC-MP 26.55 against 26.4, KC-RB raw 27.3 against
-//    26.8; BGK (29.3 against 29.7), the cp.async-staged kernels (FP32 24.0
-//    against 24.6, FP16 28.5 against 29.4, the 64^3 ensemble 21.7 against
-//    22.6) and the walls (spills) keep three.
+//    plane p-3 any more.  With four (v4_ring4: the TMA-staged KC kernels) the
+//    strain of plane z reads the slots of planes z - 1, z and z + 1 (the
+//    z-neighbours only at the thread's own cells, which it wrote itself),
+//    every thread has done its strain reads of plane p-3 when plane p is
+//    written, and the 36 registers no longer carried from plane to plane let
+//    the periodic box's collision load its TMEM populations one triple ahead,
+//    and the walls' TMA kernel run without spills.  Measured (512^3 FP32,
+//    GLUPS): KC-MP 26.55 against 26.4, KC-RB raw 27.3 against 26.8; BGK (29.3
+//    against 29.7) and the cp.async-staged kernels (FP32 24.0 against 24.6,
+//    FP16 28.5 against 29.4, the 64^3 ensemble 21.7 against 22.6) keep three.
 //  * The collision relaxes the four cells together, one (c_y, c_z) population
 //    triple at a time, in the common form g' = a g + w (b (P - 1) + c0 + D H)
 //    of collide() with P - 1 = e_x (1 + Y) + Y, Y = e_y + e_z + e_y e_z, and
@@ -107,12 +107,14 @@ __device__ __forceinline__ void v4_store(__nv_bfloat16* p, float a, float b, flo
 // into [27][RY][TX], and only the x-edge chunks (x0 - 4 .. x0 - 1 and x0 + TX ..
 // x0 + TX + 3 of every staged row) by cp.async, into [27][RY][8].
 // WALLS: a buffer [2][9][TX] for the bounce-back values of the wall rows (the
-// cells' own opposite populations, copied with the plane's staging).
-// four ring slots (the z-neighbours read from the ring, the TMEM loads one
-// triple ahead): the TMA-staged kernel of the periodic box with the KC closures
+// cells' own opposite populations, copied with the plane's staging: by
+// cp.async, or with TMAS one row box per population and wall by the TMA).
+// four ring slots (the z-neighbours read from the ring; in the periodic box
+// also the TMEM loads one triple ahead): the TMA-staged kernels with the KC
+// closures
 __host__ __device__ constexpr bool v4_ring4(bool tmas, int cl, int bc)
 {
-    return tmas && bc == BC_PERIODIC && cl != CL_BGK && cl != CL_LEARNED;
+    return tmas && cl != CL_BGK && cl != CL_LEARNED;
 }
 
 template <int LPR, typename S, bool LEARNED = false, bool TMAS = false, bool WALLS = false, bool RZ4 = false>
@@ -124,7 +126,7 @@ struct V4Shape {
     static constexpr int RY = TY + 2;      // ring and staged rows: y0 - 1 .. y0 + TY
     static constexpr int RP = TX + 8;      // ring and staging pitch: x0 - 4 .. x0 + TX + 3, own cells at 4 .. TX + 3
     static constexpr int NSLOT = RZ4 ? 4 : 3;
-    static_assert(!RZ4 || (!LEARNED && !WALLS), "four ring slots: periodic boxes, analytic closures");
+    static_assert(!RZ4 || !LEARNED, "four ring slots: analytic closures");
     static constexpr int NB = 2 * TX + 2 * TY;     // halo cells of a ring plane (no corners)
     static constexpr int NCH = TX / 4;             // 4-cell chunks of a row
     // staged chunks beyond the own ones: halo rows and x-edge chunks (TMAS: the x-edge chunks)
@@ -139,7 +141,7 @@ struct V4Shape {
     static_assert(!TMAS || (RY * TX * sizeof(S)) % 128 == 0, "each population's TMA box 128-byte aligned");
     static_assert(!(TMAS && LEARNED), "TMA staging is built for the analytic closures");
     static_assert(!TMAS || (NPOS <= 40 && 40 + 8 * 26 < NT), "TMA issuing threads apart from the x-edge threads");
-    static constexpr size_t bb_off = stg_off + stg_bytes;
+    static constexpr size_t bb_off = (stg_off + stg_bytes + 127) / 128 * 128;  // TMAS: TMA destinations
     static constexpr size_t bb_bytes = WALLS ? sizeof(S) * (size_t)2 * 9 * TX : 0;
     // learned closure: the packed network and one 32-row exchange per warp
     static constexpr size_t mlp_off = bb_off + bb_bytes;
@@ -286,7 +288,7 @@ __device__ __forceinline__ void v4_tma_load(void* smem_dst, const CUtensorMap* m
 // BC = BC_WALLS_Y: halfway bounce-back walls at y = 0 and y = ny - 1 with a body
 // force (the channel).  The staged rows stay those of the periodic box; a wall
 // row replaces the pulls that cross its wall by the cell's own post-collision
-// opposite population (loaded from global memory), takes the one-sided
+// opposite population (staged with the plane), takes the one-sided
 // difference of Eqs. (fd_boundary_lower/upper) across y, the velocity shifted
 // by F/2 and Guo's source.  Rows beyond a wall are computed from the periodic
 // image and neither stored nor read.  The top wall row must not be the first
@@ -462,13 +464,26 @@ __global__ void __launch_bounds__(256, 1)
                 const int zsrc = cz == 0 ? zc : (cz == 1 ? (zc == 0 ? nz - 1 : zc - 1) : (zc == nz - 1 ? 0 : zc + 1));
                 const int ys = y0 - 1 - cy, w = box * 27 + i;
                 S* dst = stg + i * RY * TX;
-                mbar_expect_tx(&mbar[2], Sh::tma_bytes / 27u);
+                // walls: issuers 0..8 also copy the bounce-back row qb = i of the lower
+                // and the upper wall when the tile holds it (population 26 - j of the
+                // wall row at plane z, j the pull that crosses the wall)
+                const bool bb_lo = WALLS && i < 9 && y0 == 0;
+                const bool bb_hi = WALLS && i < 9 && y0 <= ny - 1 && ny - 1 < y0 + TY;
+                mbar_expect_tx(&mbar[2], Sh::tma_bytes / 27u + (unsigned)((bb_lo + bb_hi) * TX * (int)sizeof(S)));
                 if (ys >= 0 && ys + RY <= ny) {
                     v4_tma_load(dst, &map_rows, x0, ys, zsrc, w, &mbar[2]);
                 } else {  // rows wrapping around y: one row at a time
 #pragma unroll 1
                     for (int r = 0; r < RY; ++r)
                         v4_tma_load(dst + r * TX, &map_row1, x0, wrapi(ys + r, ny), zsrc, w, &mbar[2]);
+                }
+                if constexpr (WALLS) {
+                    const int qz = i / 3, qx = i % 3;  // qb = 3 (c_z + 1) + (c_x + 1) of the crossing pull
+                    if (bb_lo)  // pulls with c_y = +1 cross the lower wall
+                        v4_tma_load(bbs + i * TX, &map_row1, x0, 0, zc, box * 27 + 26 - (9 * qz + 6 + qx), &mbar[2]);
+                    if (bb_hi)  // pulls with c_y = -1 cross the upper wall
+                        v4_tma_load(bbs + (9 + i) * TX, &map_row1, x0, ny - 1, zc, box * 27 + 26 - (9 * qz + qx),
+                                    &mbar[2]);
                 }
             } else {
                 mbar_arrive(&mbar[2]);
@@ -557,7 +572,7 @@ __global__ void __launch_bounds__(256, 1)
                     // the triple's loads
                     const bool wl = cy == 1 ? wall_lo : wall_hi;
                     constexpr float w = SHIFTED ? 0.f : (float)weight_of(Q, i);
-                    if constexpr (STAGED && !TMAS) {
+                    if constexpr (STAGED) {
                         constexpr int qb = 3 * (cz + 1) + (i % 3);
                         const float4 b = v4_lds(bbs + ((cy == 1 ? 0 : 9) + qb) * TX + 4 * lx);
                         g[k][0] = wl ? b.x - w : g[k][0];
@@ -864,7 +879,7 @@ __global__ void __launch_bounds__(256, 1)
             // that carry the z-neighbours in registers have no registers for the
             // second triple: they issue each triple's load before forming its
             // constants.
-            constexpr bool PF = RZ;
+            constexpr bool PF = RZ && !WALLS;
             uint32_t gr[2][12];
             if constexpr (PF) tm_ld12_issue(ts, gr[0]);
             static_for<9>([&](auto PI) {

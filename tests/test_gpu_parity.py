@@ -481,7 +481,9 @@ def test_default_variant_selection(lbm):
     (tiles 128 x 8, or 64 x 16 for boxes at most 64 wide), for FP32 storage
     with TMA staging (16) where nx is a multiple of the tile width and ny spans
     at least eight tiles; the D3Q27 FP32 channel with BGK or KC-MP the
-    four-cell kernel (14) where (ny - 1) is not a multiple of the tile height;
+    four-cell kernel (14) where (ny - 1) is not a multiple of the tile height,
+    with KC-MP under the same conditions as the periodic box with TMA staging
+    (16);
     otherwise, for FP32 storage, periodic D3Q27 with KC-MP or KC-RB the
     split-barrier pull with L2 prefetches (12) on z-chunks of at most 16
     planes; KC-RR, D3Q19 and the other walls with KC-MP the split-barrier pull
@@ -521,6 +523,9 @@ def test_default_variant_selection(lbm):
                                  (19, "kcmp", 32, 13), (27, "kcrb_hermite", 32, 1), (27, "bgk", 33, 1)):
         with lbm.Solver(q, (40, ny, 16), 1e-4, closure=closure, storage="fp32", bc=(0, 1, 0)) as s:
             assert s.launch_config["variant"] == want, (q, closure, ny, "walls")
+    for closure, want in (("kcmp", 16), ("bgk", 14)):  # nx a multiple of 64, ny = 130 spans eight 16-row tiles
+        with lbm.Solver(27, (128, 130, 8), 1e-4, closure=closure, storage="fp32", bc=(0, 1, 0)) as s:
+            assert s.launch_config["variant"] == want and s.launch_config["tile_y"] == 16, (closure, "walls")
     for retired in (4, 9):  # the TMA-staged and packed-pair kernels are retired
         with pytest.raises(lbm.LbmError):
             lbm.Solver(27, (64, 32, 16), 1e-4, closure="kcmp", storage="fp32", variant=retired)

@@ -106,9 +106,11 @@ typedef struct {
                            BGK, KC-MP or KC-RB, nx % 8 == 0: 14, tiles
                            128 x 8, or 64 x 16 for nx <= 64, and for FP32
                            storage 16 where nx is a multiple of the tile
-                           width and ny >= 8 tile heights; the D3Q27 FP32
-                           channel with BGK or KC-MP, nx % 8 == 0 and
-                           (ny - 1) % 16 != 0: 14 on 64 x 16 tiles; else, for
+                           width and ny a multiple of the tile height or
+                           >= 8 tile heights; the D3Q27 FP32 channel with BGK
+                           or KC-MP, nx % 8 == 0 and (ny - 1) % 16 != 0: 14
+                           on 64 x 16 tiles, with KC-MP 16 under the same
+                           conditions as the periodic box; else, for
                            FP32 storage, 12 on z-chunks of at most 16 planes
                            for periodic D3Q27 with KC-MP or KC-RB, 13 for
                            KC-RR, D3Q19 and walls; else 8 for periodic D3Q27 except

@@ -88,9 +88,10 @@ struct lbm_handle {
     cudaStream_t xstream = nullptr;
     cudaEvent_t ev_filled[2] = {nullptr, nullptr};
     cudaEvent_t ev_drained[2] = {nullptr, nullptr};
-    // four-cell kernel's TMA staging: tensor maps of f[0], f[1] (box of the
-    // tile's staged rows, and of one row), encoded for v4map_tile (0 = none)
-    CUtensorMap v4map[2][2];
+    // four-cell kernel's TMA staging: tensor maps of f[0], f[1] (boxes of the
+    // tile's RY staged rows, of one row, of RY - 1 and of RY - 2 rows), encoded
+    // for v4map_tile (0 = none)
+    CUtensorMap v4map[2][4];
     int v4map_tile = 0;
 };
 
@@ -164,6 +165,8 @@ StepArgs step_args(const lbm_handle* h)
     a.mlp = h->d_mlp;
     a.tmap_rows = nullptr;
     a.tmap_row1 = nullptr;
+    a.tmap_rm1 = nullptr;
+    a.tmap_rm2 = nullptr;
     return a;
 }
 
@@ -176,13 +179,14 @@ void ensure_v4_maps(lbm_handle* h)
     const bool want = h->variant == VAR_VEC4_TMA && h->cfg.nx % tx == 0;
     if (!want || h->v4map_tile == ty) return;
     h->v4map_tile = 0;
+    const int rows[4] = {ty + 2, 1, ty + 1, ty};
     for (int b = 0; b < 2; ++b) {
-        if (encode_v4_map(&h->v4map[b][0], h->f[b], h->cfg.storage, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->q,
-                          h->cfg.nbatch, tx, ty + 2) != cudaSuccess ||
-            encode_v4_map(&h->v4map[b][1], h->f[b], h->cfg.storage, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->q,
-                          h->cfg.nbatch, tx, 1) != cudaSuccess) {
-            cudaGetLastError();
-            return;
+        for (int m = 0; m < 4; ++m) {
+            if (encode_v4_map(&h->v4map[b][m], h->f[b], h->cfg.storage, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->q,
+                              h->cfg.nbatch, tx, rows[m]) != cudaSuccess) {
+                cudaGetLastError();
+                return;
+            }
         }
     }
     h->v4map_tile = ty;
@@ -198,6 +202,8 @@ cudaError_t enqueue_steps(const lbm_handle* h, int n, int cur, cudaStream_t s)
         a.fout = h->f[cur ^ 1];
         a.tmap_rows = maps ? &h->v4map[cur][0] : nullptr;
         a.tmap_row1 = maps ? &h->v4map[cur][1] : nullptr;
+        a.tmap_rm1 = maps ? &h->v4map[cur][2] : nullptr;
+        a.tmap_rm2 = maps ? &h->v4map[cur][3] : nullptr;
         cudaError_t e = launch_step(h->q, h->cfg.storage, h->cfg.closure, h->bc_kind, h->tile_y, h->variant, a,
                                     h->cfg.nbatch, s);
         if (e != cudaSuccess) return e;
@@ -520,13 +526,14 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
                               (cfg->closure == LBM_KCMP || cfg->closure == LBM_KCRB_HERMITE ||
                                cfg->closure == LBM_KCRB_RAW);
         const int v4_ty = v4_ty0;
-        // TMA staging (16) where every tile is full in x and the tiles whose
-        // staged rows wrap around y (copied row by row) are few: periodic boxes,
-        // and the channel with KC-MP (512 x 256 x 256 on 64 x 16 tiles: 23.0
-        // GLUPS against 21.5 with cp.async staging)
+        // TMA staging (16) where every tile is full in x, and full in y or the
+        // ragged tiles (whose staged rows are copied row by row) are few:
+        // periodic boxes (64 x 64^3 ensemble on 64 x 16 tiles: 25.0 GLUPS
+        // against 22.5 with cp.async staging), and the channel with KC-MP (512 x
+        // 256 x 256 on 64 x 16 tiles: 23.0 against 21.5)
         const bool tma_first = cfg->storage == LBM_FP32 &&
                                (bc_kind == BC_PERIODIC || (v4_walls && cfg->closure == LBM_KCMP)) &&
-                               vec4_tma_shape_ok(cfg->nx, v4_ty) && cfg->ny >= 8 * v4_ty;
+                               vec4_tma_shape_ok(cfg->nx, v4_ty) && (cfg->ny % v4_ty == 0 || cfg->ny >= 8 * v4_ty);
         if (v4_first && tma_first && step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, v4_ty, VAR_VEC4_TMA)) {
             variant = VAR_VEC4_TMA;
             tile_y = v4_ty;

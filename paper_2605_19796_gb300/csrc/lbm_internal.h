@@ -28,9 +28,12 @@ struct StepArgs {
     unsigned int* flag;     // bit 0: non-finite density/velocity seen, bit 1: a bounded wait timed out
     const void* mlp;        // packed network parameters (learned closure only), MlpLayout::BYTES
     // four-cell kernel with TMA staging: host addresses of the CUtensorMaps of
-    // fin (box TX x staged rows, and TX x 1 for tiles whose rows wrap), or null
+    // fin (box TX x staged rows RY, TX x 1, TX x (RY - 1) and TX x (RY - 2): the
+    // last three for tiles whose staged rows wrap around y), or null
     const void* tmap_rows;
     const void* tmap_row1;
+    const void* tmap_rm1;
+    const void* tmap_rm2;
 };
 
 // tensor map of a population buffer for the four-cell kernel's TMA staging

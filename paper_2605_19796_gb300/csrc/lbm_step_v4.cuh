@@ -296,7 +296,8 @@ __device__ __forceinline__ void v4_tma_load(void* smem_dst, const CUtensorMap* m
 // ring.
 template <int Q, typename S, int CL, int LPR, bool TMAS = false, int BC = BC_PERIODIC>
 __global__ void __launch_bounds__(256, 1)
-    step_kernel_v4(const StepArgs a, const __grid_constant__ CUtensorMap map_rows, const __grid_constant__ CUtensorMap map_row1)
+    step_kernel_v4(const StepArgs a, const __grid_constant__ CUtensorMap map_rows, const __grid_constant__ CUtensorMap map_row1,
+                   const __grid_constant__ CUtensorMap map_rm1, const __grid_constant__ CUtensorMap map_rm2)
 {
     static_assert(Q == 27, "the four-cell kernel is built for D3Q27 (population triples along x)");
     static_assert(!std::is_same<S, double>::value, "FP32 arithmetic");
@@ -470,9 +471,19 @@ __global__ void __launch_bounds__(256, 1)
                 const bool bb_lo = WALLS && i < 9 && y0 == 0;
                 const bool bb_hi = WALLS && i < 9 && y0 <= ny - 1 && ny - 1 < y0 + TY;
                 mbar_expect_tx(&mbar[2], Sh::tma_bytes / 27u + (unsigned)((bb_lo + bb_hi) * TX * (int)sizeof(S)));
-                if (ys >= 0 && ys + RY <= ny) {
+                const int klo = -ys, khi = ys + RY - ny;  // rows wrapped from the top / to the bottom
+                if (ys >= 0 && khi <= 0) {
                     v4_tma_load(dst, &map_rows, x0, ys, zsrc, w, &mbar[2]);
-                } else {  // rows wrapping around y: one row at a time
+                } else if (klo >= 1 && klo <= 2 && RY - klo <= ny) {
+                    // rows ys .. -1 are rows ny + ys .. ny - 1, one at a time; the rest one box
+                    for (int r = 0; r < klo; ++r) v4_tma_load(dst + r * TX, &map_row1, x0, ny + ys + r, zsrc, w, &mbar[2]);
+                    v4_tma_load(dst + klo * TX, klo == 1 ? &map_rm1 : &map_rm2, x0, 0, zsrc, w, &mbar[2]);
+                } else if (ys >= 0 && khi <= 2) {
+                    // one box of rows ys .. ny - 1, then rows ny .. are rows 0 .., one at a time
+                    v4_tma_load(dst, khi == 1 ? &map_rm1 : &map_rm2, x0, ys, zsrc, w, &mbar[2]);
+                    for (int r = RY - khi; r < RY; ++r)
+                        v4_tma_load(dst + r * TX, &map_row1, x0, ys + r - ny, zsrc, w, &mbar[2]);
+                } else {  // short boxes and ragged last tiles: one row at a time
 #pragma unroll 1
                     for (int r = 0; r < RY; ++r)
                         v4_tma_load(dst + r * TX, &map_row1, x0, wrapi(ys + r, ny), zsrc, w, &mbar[2]);
@@ -998,16 +1009,18 @@ cudaError_t launch_v4_t(const StepArgs& a, int nbatch, cudaStream_t s, bool tma)
     dim3 grid(tiles, chunks, nbatch), block(Sh::NT);
     if (tma) {
         if constexpr (CL != CL_LEARNED) {
-            if (!a.tmap_rows || !a.tmap_row1 || a.nx % Sh::TX != 0) return cudaErrorInvalidValue;
+            if (!a.tmap_rows || !a.tmap_row1 || !a.tmap_rm1 || !a.tmap_rm2 || a.nx % Sh::TX != 0)
+                return cudaErrorInvalidValue;
             step_kernel_v4<Q, S, CL, LPR, true, BC>
                 <<<grid, block, V4Shape<LPR, S, false, true, BC == BC_WALLS_Y, v4_ring4(true, CL, BC)>::smem_bytes, s>>>(
-                a, *static_cast<const CUtensorMap*>(a.tmap_rows), *static_cast<const CUtensorMap*>(a.tmap_row1));
+                a, *static_cast<const CUtensorMap*>(a.tmap_rows), *static_cast<const CUtensorMap*>(a.tmap_row1),
+                *static_cast<const CUtensorMap*>(a.tmap_rm1), *static_cast<const CUtensorMap*>(a.tmap_rm2));
             return cudaGetLastError();
         }
         return cudaErrorNotSupported;
     }
     CUtensorMap none{};
-    step_kernel_v4<Q, S, CL, LPR, false, BC><<<grid, block, Sh::smem_bytes, s>>>(a, none, none);
+    step_kernel_v4<Q, S, CL, LPR, false, BC><<<grid, block, Sh::smem_bytes, s>>>(a, none, none, none, none);
     return cudaGetLastError();
 }
 

@@ -479,8 +479,8 @@ def test_default_variant_selection(lbm):
     """Library default: periodic D3Q27 with 32- or 16-bit storage and BGK,
     KC-MP or KC-RB takes the four-cell kernel (14) when nx is a multiple of 8
     (tiles 128 x 8, or 64 x 16 for boxes at most 64 wide), for FP32 storage
-    with TMA staging (16) where nx is a multiple of the tile width and ny spans
-    at least eight tiles; the D3Q27 FP32 channel with BGK or KC-MP the
+    with TMA staging (16) where nx is a multiple of the tile width and ny a
+    multiple of the tile height or at least eight tile heights; the D3Q27 FP32 channel with BGK or KC-MP the
     four-cell kernel (14) where (ny - 1) is not a multiple of the tile height,
     with KC-MP under the same conditions as the periodic box with TMA staging
     (16);
@@ -503,8 +503,10 @@ def test_default_variant_selection(lbm):
             assert s.launch_config["variant"] == want, (q, closure, storage)
             ty = {14: 16, 15: 4, 1: 4 if closure == "learned" else 8}.get(want, 8)
             assert s.launch_config["tile_y"] == ty, (q, closure, storage)
-    with lbm.Solver(27, (256, 32, 64), 1e-4, closure="kcmp", storage="fp32") as s:
-        assert s.launch_config["variant"] == 14 and s.launch_config["tile_y"] == 8  # ny < 8 tile heights
+    with lbm.Solver(27, (256, 36, 64), 1e-4, closure="kcmp", storage="fp32") as s:
+        assert s.launch_config["variant"] == 14 and s.launch_config["tile_y"] == 8  # a ragged tile, ny < 8 tile heights
+    with lbm.Solver(27, (64, 64, 64), 1e-4, closure="kcmp", storage="fp32", nbatch=2) as s:
+        assert s.launch_config["variant"] == 16 and s.launch_config["tile_y"] == 16  # full tiles
     with lbm.Solver(27, (256, 64, 16), 1e-4, closure="kcmp", storage="fp32") as s:
         assert s.launch_config["variant"] == 16 and s.launch_config["tile_y"] == 8
     with lbm.Solver(27, (256, 64, 16), 1e-4, closure="kcmp", storage="fp16") as s:

@@ -66,7 +66,9 @@ LAUNCHES = [(14, 8), (14, 16), (16, 8), (16, 16)]
 
 
 @pytest.mark.parametrize("variant,tile_y", LAUNCHES)
-@pytest.mark.parametrize("shape", [(256, 20, 9), (64, 8, 5), (24, 5, 3)])
+# (128, 32, 6): full tiles in y, so the first and the last tile row of the TMA-staged
+# variant copy their wrapping rows as one box of RY - 1 or RY - 2 rows and one or two single rows
+@pytest.mark.parametrize("shape", [(256, 20, 9), (64, 8, 5), (24, 5, 3), (128, 32, 6)])
 @pytest.mark.parametrize("closure", ["bgk", "kcmp", "kcrb_hermite", "kcrb_raw"])
 def test_vec4_fp32_matches_register_pull_and_oracle(lbm, orc, closure, shape, tile_y, variant):
     nus = np.array([2e-5, 1e-4])

@@ -130,7 +130,11 @@ int default_zchunk_vec4(int nx, int ny, int nz, int nbatch, int tile_y)
     if (nz <= 64 && nz >= 16 && tiles * ((nz + 15) / 16) >= 2LL * 152) return 16;
     const long long want = (2LL * 152 + tiles - 1) / tiles;  // chunks per tile column for two CTAs per SM
     long long zc = (nz + want - 1) / want;
-    if (zc > 40) zc = 40;
+    // at most 36 planes (512^3 KC-MP with TMA staging, 128 x 8 tiles: 36 planes
+    // 27.7 GLUPS, 45: 27.7, 38: 27.6, 40: 27.4, 34: 27.4, 32: 27.3; 256^3: 36
+    // planes 27.7, 40: 25.9, 30: 25.7, 28: 26.8, 32: 24.3 - the CTAs of the last
+    // wave decide, the short last chunk of a 36-plane split filling it)
+    if (zc > 36) zc = 36;
     if (zc < 4) zc = 4;
     if (zc > nz) zc = nz;
     return (int)zc;
@@ -587,9 +591,11 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
     h->zchunk = cfg->zchunk ? cfg->zchunk : default_zchunk(cfg->nx, cfg->ny, cfg->nz, cfg->nbatch, tile_y);
     if (!cfg->zchunk && short_chunks && h->zchunk > 16) h->zchunk = 16;
     if (!cfg->zchunk && vec4_chunks) h->zchunk = default_zchunk_vec4(cfg->nx, cfg->ny, cfg->nz, cfg->nbatch, tile_y);
-    // the channel on the four-cell kernel prefers shorter chunks (512 x 256 x 256
-    // KC-MP on 64 x 16 tiles: 24 planes 20.7 GLUPS, 40: 20.3, 64: 19.2)
-    if (!cfg->zchunk && vec4_chunks && bc_kind == BC_WALLS_Y && h->zchunk > 24) h->zchunk = 24;
+    // the channel with cp.async staging prefers shorter chunks (512 x 256 x 256
+    // KC-MP on 64 x 16 tiles: 24 planes 20.7 GLUPS, 40: 20.3, 64: 19.2); with TMA
+    // staging it takes the general rule (36 planes 24.3, 32: 24.1, 27: 23.9, 24:
+    // 23.4, 43: 22.4)
+    if (!cfg->zchunk && vec4_chunks && bc_kind == BC_WALLS_Y && variant == VAR_VEC4 && h->zchunk > 24) h->zchunk = 24;
     // the learned closure's network-heavy CTAs balance better over about twice
     // as many, half as long chunks (256^3, register pull on 4-row tiles: 26
     // planes 8.43 GLUPS, 52 planes 8.28, 16 planes 8.18)

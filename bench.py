@@ -61,6 +61,11 @@ WORKLOADS = {
     "channel512x256x256_d3q19_fp32_kcmp": dict(shape=(512, 256, 256), q=19, storage="fp32", closure="kcmp",
                                                nu=0.004 * 128 / 180, force=(0.004 ** 2 / 128, 0.0, 0.0),
                                                u_bulk=0.063),
+    # the same channel at half the size in every direction (h = 64, Re_tau ~ 90
+    # at the same u_tau): a case small enough for multi-pass ncu captures
+    "channel256x128x128_d3q27_fp32_kcmp": dict(shape=(256, 128, 128), q=27, storage="fp32", closure="kcmp",
+                                               nu=0.004 * 64 / 90, force=(0.004 ** 2 / 64, 0.0, 0.0),
+                                               u_bulk=0.063),
 }
 DEFAULT_WORKLOAD = "hit512_d3q27_fp32_kcmp"
 ELEM = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}

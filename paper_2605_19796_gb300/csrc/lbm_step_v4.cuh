@@ -153,9 +153,35 @@ struct V4Shape {
     static_assert(smem_bytes <= 227 * 1024, "shared memory of one CTA");
 };
 
-// relaxation constants of one cell (collide_coef in the per-triple form)
+// D3Q19 in the four-cell kernel: a population keeps its D3Q27 position
+// j = 9 (c_z + 1) + 3 (c_y + 1) + (c_x + 1) for its staged rows, its TMEM
+// columns and its triple p = j / 3 along x; D3Q19 has no corners (all three
+// components nonzero), so its four triples with c_y c_z != 0 hold the c_x = 0
+// population only.  v4_has: position j is a population of lattice Q;
+// v4_pop: its index in lattice Q (the population arrays' order).
+__host__ __device__ constexpr bool v4_has(int Q, int j)
+{
+    return Q == 27 || j % 3 == 1 || (j / 3) % 3 == 1 || j / 9 == 1;
+}
+constexpr unsigned kV4Corners = 0x5140145u;  // bits j of the eight corners: 0, 2, 6, 8, 18, 20, 24, 26
+__host__ __device__ constexpr int v4_pop(int Q, int j)
+{
+    int below = 0;  // corners before position j
+    for (int k = 0; k < j; ++k) below += (kV4Corners >> k) & 1u;
+    return Q == 27 ? j : j - below;
+}
+// the same at run time (a thread's population)
+__device__ __forceinline__ int v4_pop_rt(int Q, int j) { return Q == 27 ? j : j - __popc(kV4Corners & ((1u << j) - 1u)); }
+
+// relaxation constants of one cell (collide_coef in the per-triple form).
+// D3Q27: the product equilibrium's per-axis terms ex, ey, ez.  D3Q19 (second
+// order Hermite equilibrium, P - 1 = c.u/theta + (c.u)^2/(2 theta^2) -
+// u^2/(2 theta)): qx, qy, qz = u/theta, qq = qx^2/2 and hu = -u^2/(2 theta), so
+// that along a triple with B = c_y qy + c_z qz, P - 1 = Y + c_x qx (1 + B) +
+// c_x^2 qq with Y = B + B^2/2 + hu.
 struct V4Cell {
     float ca, cb, ex[3], ey[3], ez[3], C[5], Dxx, Dxy2, Dxz2;
+    float qx, qy, qz, qq, hu;
 };
 
 // index of the (c_y, c_z) part of H: (0,0), (+-1,0), (0,+-1), c_y c_z = 1, c_y c_z = -1
@@ -299,7 +325,8 @@ __global__ void __launch_bounds__(256, 1)
     step_kernel_v4(const StepArgs a, const __grid_constant__ CUtensorMap map_rows, const __grid_constant__ CUtensorMap map_row1,
                    const __grid_constant__ CUtensorMap map_rm1, const __grid_constant__ CUtensorMap map_rm2)
 {
-    static_assert(Q == 27, "the four-cell kernel is built for D3Q27 (population triples along x)");
+    static_assert(Q == 27 || Q == 19, "the four-cell kernel is built for D3Q27 and D3Q19 (population triples along x)");
+    static_assert(Q == 27 || CL != CL_LEARNED, "the learned closure's four-cell kernel is D3Q27");
     static_assert(!std::is_same<S, double>::value, "FP32 arithmetic");
     static_assert(CL == CL_BGK || CL == CL_KCMP || CL == CL_KCRB_H || CL == CL_KCRB_RAW || CL == CL_LEARNED, "closure");
     constexpr bool LEARNED = CL == CL_LEARNED;
@@ -452,24 +479,29 @@ __global__ void __launch_bounds__(256, 1)
                 static_for<27>([&](auto I) {
                     constexpr int i = decltype(I)::value;
                     constexpr int cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
-                    const S* base = fin + (long long)i * ps + zr[1 - cz];
-                    cp_async_chunk<S>((uint32_t)__cvta_generic_to_shared(stg_at(i, pos_r, pos_col)),
-                                      base + yr_pos[1 - cy] + pos_x);
+                    if constexpr (v4_has(Q, i)) {
+                        const S* base = fin + (long long)v4_pop(Q, i) * ps + zr[1 - cz];
+                        cp_async_chunk<S>((uint32_t)__cvta_generic_to_shared(stg_at(i, pos_r, pos_col)),
+                                          base + yr_pos[1 - cy] + pos_x);
+                    }
                 });
                 cp_async_commit();
                 cp_async_arrive(&mbar[2]);
-            } else if (tid >= 40 && (tid - 40) % 8 == 0) {  // the interior by the TMA: population (tid - 40) / 8,
-                const int i = (tid - 40) / 8;                     // one issuing thread per population, spread over warps
+            } else if (tid >= 40 && (tid - 40) % 8 == 0 && v4_has(Q, (tid - 40) / 8)) {
+                // the interior by the TMA: position (tid - 40) / 8, one issuing thread per
+                // population, spread over the warps
+                const int i = (tid - 40) / 8;
                 const int cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
                 const int zc = z < 0 ? z + nz : (z >= nz ? z - nz : z);
                 const int zsrc = cz == 0 ? zc : (cz == 1 ? (zc == 0 ? nz - 1 : zc - 1) : (zc == nz - 1 ? 0 : zc + 1));
-                const int ys = y0 - 1 - cy, w = box * 27 + i;
+                const int ys = y0 - 1 - cy, w = box * Q + v4_pop_rt(Q, i);
                 S* dst = stg + i * RY * TX;
                 // walls: issuers 0..8 also copy the bounce-back row qb = i of the lower
                 // and the upper wall when the tile holds it (population 26 - j of the
                 // wall row at plane z, j the pull that crosses the wall)
-                const bool bb_lo = WALLS && i < 9 && y0 == 0;
-                const bool bb_hi = WALLS && i < 9 && y0 <= ny - 1 && ny - 1 < y0 + TY;
+                const int jlo = 9 * (i / 3) + 6 + i % 3, jhi = 9 * (i / 3) + i % 3;  // the crossing pulls (i < 9)
+                const bool bb_lo = WALLS && i < 9 && y0 == 0 && v4_has(Q, jlo);
+                const bool bb_hi = WALLS && i < 9 && y0 <= ny - 1 && ny - 1 < y0 + TY && v4_has(Q, jhi);
                 mbar_expect_tx(&mbar[2], Sh::tma_bytes / 27u + (unsigned)((bb_lo + bb_hi) * TX * (int)sizeof(S)));
                 const int klo = -ys, khi = ys + RY - ny;  // rows wrapped from the top / to the bottom
                 if (ys >= 0 && khi <= 0) {
@@ -488,12 +520,11 @@ __global__ void __launch_bounds__(256, 1)
                     for (int r = 0; r < RY; ++r)
                         v4_tma_load(dst + r * TX, &map_row1, x0, wrapi(ys + r, ny), zsrc, w, &mbar[2]);
                 }
-                if constexpr (WALLS) {
-                    const int qz = i / 3, qx = i % 3;  // qb = 3 (c_z + 1) + (c_x + 1) of the crossing pull
+                if constexpr (WALLS) {  // qb = i = 3 (c_z + 1) + (c_x + 1) of the crossing pull
                     if (bb_lo)  // pulls with c_y = +1 cross the lower wall
-                        v4_tma_load(bbs + i * TX, &map_row1, x0, 0, zc, box * 27 + 26 - (9 * qz + 6 + qx), &mbar[2]);
+                        v4_tma_load(bbs + i * TX, &map_row1, x0, 0, zc, box * Q + v4_pop_rt(Q, 26 - jlo), &mbar[2]);
                     if (bb_hi)  // pulls with c_y = -1 cross the upper wall
-                        v4_tma_load(bbs + (9 + i) * TX, &map_row1, x0, ny - 1, zc, box * 27 + 26 - (9 * qz + qx),
+                        v4_tma_load(bbs + (9 + i) * TX, &map_row1, x0, ny - 1, zc, box * Q + v4_pop_rt(Q, 26 - jhi),
                                     &mbar[2]);
                 }
             } else {
@@ -504,18 +535,23 @@ __global__ void __launch_bounds__(256, 1)
         static_for<27>([&](auto I) {
             constexpr int i = decltype(I)::value;
             constexpr int cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
-            const S* base = fin + (long long)i * ps + zr[1 - cz];
-            cp_async_chunk<S>((uint32_t)__cvta_generic_to_shared(stg_at(i, ry_own, rx_own)), base + yr_own[1 - cy] + xaw);
-            if (pos_r >= 0)
-                cp_async_chunk<S>((uint32_t)__cvta_generic_to_shared(stg_at(i, pos_r, pos_col)),
-                                  base + yr_pos[1 - cy] + pos_x);
-            // a wall row's bounce-back values: population 26 - i of its own cells (plane
-            // z) for the pulls i that cross the wall, slot 0 lower wall, 1 upper
-            if constexpr (WALLS && cy != 0) {
-                if (cy == 1 ? wall_lo : wall_hi) {
-                    constexpr int qb = 3 * (cz + 1) + (i % 3);
-                    cp_async_chunk<S>((uint32_t)__cvta_generic_to_shared(bbs + ((cy == 1 ? 0 : 9) + qb) * TX + 4 * lx),
-                                      fin + (long long)(26 - i) * ps + zr[1] + yr_own[1] + xaw);
+            if constexpr (v4_has(Q, i)) {
+                const S* base = fin + (long long)v4_pop(Q, i) * ps + zr[1 - cz];
+                cp_async_chunk<S>((uint32_t)__cvta_generic_to_shared(stg_at(i, ry_own, rx_own)),
+                                  base + yr_own[1 - cy] + xaw);
+                if (pos_r >= 0)
+                    cp_async_chunk<S>((uint32_t)__cvta_generic_to_shared(stg_at(i, pos_r, pos_col)),
+                                      base + yr_pos[1 - cy] + pos_x);
+                // a wall row's bounce-back values: the opposite population (position
+                // 26 - i) of its own cells (plane z) for the pulls i that cross the wall,
+                // slot 0 lower wall, 1 upper
+                if constexpr (WALLS && cy != 0) {
+                    if (cy == 1 ? wall_lo : wall_hi) {
+                        constexpr int qb = 3 * (cz + 1) + (i % 3);
+                        cp_async_chunk<S>(
+                            (uint32_t)__cvta_generic_to_shared(bbs + ((cy == 1 ? 0 : 9) + qb) * TX + 4 * lx),
+                            fin + (long long)v4_pop(Q, 26 - i) * ps + zr[1] + yr_own[1] + xaw);
+                    }
                 }
             }
         });
@@ -541,11 +577,17 @@ __global__ void __launch_bounds__(256, 1)
             constexpr int p = decltype(PI)::value;
             constexpr int cy = p % 3 - 1, cz = p / 3 - 1;
             const int roff = zr[1 - cz] + yr_own[1 - cy];
+            constexpr bool TRIPLE = v4_has(Q, 3 * p);  // D3Q19: c_y c_z != 0 holds c_x = 0 only
             float g[3][4];
             static_for<3>([&](auto CI) {
                 constexpr int k = decltype(CI)::value;
                 constexpr int cx = k - 1, i = 3 * p + k;
-                const S* src = fin + (long long)i * ps + roff;
+                if constexpr (!v4_has(Q, i)) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) g[k][c] = 0.f;
+                    return;
+                }
+                const S* src = fin + (long long)v4_pop(Q, i) * ps + roff;
                 float4 v;
                 if constexpr (STAGED)
                     v = v4_lds(stg_at(i, ry_own, rx_own));
@@ -572,7 +614,7 @@ __global__ void __launch_bounds__(256, 1)
                     g[k][3] = v.w;
                 }
                 if constexpr (!SHIFTED) {
-                    constexpr float w = (float)weight_of(Q, i);
+                    constexpr float w = (float)weight_of(Q, v4_pop(Q, i));
 #pragma unroll
                     for (int c = 0; c < 4; ++c) g[k][c] -= w;
                 }
@@ -582,7 +624,7 @@ __global__ void __launch_bounds__(256, 1)
                     // copy, read by every thread and selected, so that no branch splits
                     // the triple's loads
                     const bool wl = cy == 1 ? wall_lo : wall_hi;
-                    constexpr float w = SHIFTED ? 0.f : (float)weight_of(Q, i);
+                    constexpr float w = SHIFTED ? 0.f : (float)weight_of(Q, v4_pop(Q, i));
                     if constexpr (STAGED) {
                         constexpr int qb = 3 * (cz + 1) + (i % 3);
                         const float4 b = v4_lds(bbs + ((cy == 1 ? 0 : 9) + qb) * TX + 4 * lx);
@@ -591,7 +633,7 @@ __global__ void __launch_bounds__(256, 1)
                         g[k][2] = wl ? b.z - w : g[k][2];
                         g[k][3] = wl ? b.w - w : g[k][3];
                     } else if (wl) {
-                        const float4 b = v4_load(fin + (long long)(26 - i) * ps + zr[1] + yr_own[1] + xaw);
+                        const float4 b = v4_load(fin + (long long)v4_pop(Q, 26 - i) * ps + zr[1] + yr_own[1] + xaw);
                         g[k][0] = b.x - w;
                         g[k][1] = b.y - w;
                         g[k][2] = b.z - w;
@@ -602,10 +644,10 @@ __global__ void __launch_bounds__(256, 1)
             if constexpr (FULL) tm_st12(ts + 12u * p, g);
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                const float s = (g[0][c] + g[1][c]) + g[2][c];
-                const float dx = g[2][c] - g[0][c];
+                const float s = TRIPLE ? (g[0][c] + g[1][c]) + g[2][c] : g[1][c];
+                const float dx = TRIPLE ? g[2][c] - g[0][c] : 0.f;
                 d[c] += s;
-                jx[c] += dx;
+                if constexpr (TRIPLE) jx[c] += dx;
                 if constexpr (cy == 1) jy[c] += s;
                 if constexpr (cy == -1) jy[c] -= s;
                 if constexpr (cz == 1) jz[c] += s;
@@ -614,10 +656,10 @@ __global__ void __launch_bounds__(256, 1)
                     g0[c] += g[1][c];
                     if constexpr (cy != 0) pyy[c] += s;
                     if constexpr (cz != 0) pzz[c] += s;
-                    if constexpr (cy == 1) pxy[c] += dx;
-                    if constexpr (cy == -1) pxy[c] -= dx;
-                    if constexpr (cz == 1) pxz[c] += dx;
-                    if constexpr (cz == -1) pxz[c] -= dx;
+                    if constexpr (TRIPLE && cy == 1) pxy[c] += dx;
+                    if constexpr (TRIPLE && cy == -1) pxy[c] -= dx;
+                    if constexpr (TRIPLE && cz == 1) pxz[c] += dx;
+                    if constexpr (TRIPLE && cz == -1) pxz[c] -= dx;
                     if constexpr (cy * cz == 1) pyz[c] += s;
                     if constexpr (cy * cz == -1) pyz[c] -= s;
                 }
@@ -665,8 +707,11 @@ __global__ void __launch_bounds__(256, 1)
                 static_for<27>([&](auto I) {
                     constexpr int i = decltype(I)::value;
                     constexpr int cx = i % 3 - 1;
-                    const float v = v4_cvt(*stg_at(i, r, xr4 - cx));
-                    gh[i] = SHIFTED ? v : v - (float)weight_of(Q, i);
+                    if constexpr (v4_has(Q, i)) {
+                        constexpr int iq = v4_pop(Q, i);
+                        const float v = v4_cvt(*stg_at(i, r, xr4 - cx));
+                        gh[iq] = SHIFTED ? v : v - (float)weight_of(Q, iq);
+                    }
                 });
                 if constexpr (WALLS) {
                     if (hlo || hhi) {  // bounce-back at a wall row (x-halo cells)
@@ -676,10 +721,11 @@ __global__ void __launch_bounds__(256, 1)
                         static_for<27>([&](auto I) {
                             constexpr int i = decltype(I)::value;
                             constexpr int cy = (i / 3) % 3 - 1;
-                            if constexpr (cy != 0) {
+                            if constexpr (cy != 0 && v4_has(Q, i)) {
                                 if (cy == 1 ? hlo : hhi) {
-                                    const float v = v1_load(cellp + (long long)(26 - i) * ps);
-                                    gh[i] = SHIFTED ? v : v - (float)weight_of(Q, i);
+                                    constexpr int iq = v4_pop(Q, i);
+                                    const float v = v1_load(cellp + (long long)v4_pop(Q, 26 - i) * ps);
+                                    gh[iq] = SHIFTED ? v : v - (float)weight_of(Q, iq);
                                 }
                             }
                         });
@@ -834,15 +880,23 @@ __global__ void __launch_bounds__(256, 1)
                                                                  omega, tau_hat, nu, cnud, LEARNED ? msg[c] : nullptr);
                 const float ux = uo[0][c], uy = uo[1][c], uz = uo[2][c];
                 const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
-                K[c].ex[0] = -a1 * ux + a2 * ux2;
-                K[c].ex[1] = a0 * ux2;
-                K[c].ex[2] = a1 * ux + a2 * ux2;
-                K[c].ey[0] = -a1 * uy + a2 * uy2;
-                K[c].ey[1] = a0 * uy2;
-                K[c].ey[2] = a1 * uy + a2 * uy2;
-                K[c].ez[0] = -a1 * uz + a2 * uz2;
-                K[c].ez[1] = a0 * uz2;
-                K[c].ez[2] = a1 * uz + a2 * uz2;
+                if constexpr (Q == 27) {
+                    K[c].ex[0] = -a1 * ux + a2 * ux2;
+                    K[c].ex[1] = a0 * ux2;
+                    K[c].ex[2] = a1 * ux + a2 * ux2;
+                    K[c].ey[0] = -a1 * uy + a2 * uy2;
+                    K[c].ey[1] = a0 * uy2;
+                    K[c].ey[2] = a1 * uy + a2 * uy2;
+                    K[c].ez[0] = -a1 * uz + a2 * uz2;
+                    K[c].ez[1] = a0 * uz2;
+                    K[c].ez[2] = a1 * uz + a2 * uz2;
+                } else {
+                    K[c].qx = a1 * ux;
+                    K[c].qy = a1 * uy;
+                    K[c].qz = a1 * uz;
+                    K[c].qq = 0.5f * K[c].qx * K[c].qx;
+                    K[c].hu = -0.5f * a1 * ((ux2 + uy2) + uz2);
+                }
                 K[c].ca = k.ca;
                 K[c].cb = k.cb;
                 const float c0 = k.c0;
@@ -898,7 +952,7 @@ __global__ void __launch_bounds__(256, 1)
                 constexpr int cy = p % 3 - 1, cz = p / 3 - 1, pat = v4_pat(cy, cz);
                 constexpr int sl = PF ? (p & 1) : 0;
                 if constexpr (!PF) tm_ld12_issue(ts + 12u * p, gr[0]);
-                float Y[4], B[4], Cm[4], Cp[4], Cz[4];
+                float Y[4], B[4], Cm[4], Cp[4], Cz[4], YQ[4];
                 // walls: Guo's source part linear in c, P1 (c_y F_y + c_z F_z) on the
                 // triple and P1 F_x c_x
                 float BFg = 0.f;
@@ -906,9 +960,18 @@ __global__ void __launch_bounds__(256, 1)
                 if constexpr (WALLS && cz != 0) BFg += (float)cz * (gp1 * Fz);
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    const float ey = K[c].ey[cy + 1], ez = K[c].ez[cz + 1];
-                    Y[c] = fmaf(ey, ez, ey + ez);
-                    B[c] = 1.f + Y[c];
+                    if constexpr (Q == 27) {  // P - 1 = e_x (1 + Y) + Y along the triple
+                        const float ey = K[c].ey[cy + 1], ez = K[c].ez[cz + 1];
+                        Y[c] = fmaf(ey, ez, ey + ez);
+                        B[c] = 1.f + Y[c];
+                    } else {  // D3Q19: P - 1 = Y + c_x qx (1 + Bq) + c_x^2 qq, B = qx (1 + Bq)
+                        float Bq = 0.f;
+                        if constexpr (cy != 0) Bq = (float)cy * K[c].qy;
+                        if constexpr (cz != 0) Bq = fmaf((float)cz, K[c].qz, Bq);
+                        Y[c] = fmaf(0.5f * Bq, Bq, Bq + K[c].hu);
+                        B[c] = fmaf(K[c].qx, Bq, K[c].qx);
+                        YQ[c] = Y[c] + K[c].qq;
+                    }
                     Cz[c] = (WALLS && (cy != 0 || cz != 0)) ? K[c].C[pat] + BFg : K[c].C[pat];
                     if constexpr (CL != CL_BGK || WALLS) {
                         float X = WALLS ? gp1 * Fx : 0.f;
@@ -929,11 +992,13 @@ __global__ void __launch_bounds__(256, 1)
                 static_for<3>([&](auto CI) {
                     constexpr int k = decltype(CI)::value;
                     constexpr int cx = k - 1, i = 3 * p + k;
-                    constexpr float w = (float)weight_of(Q, i);
+                    if constexpr (!v4_has(Q, i)) return;
+                    constexpr float w = (float)weight_of(Q, v4_pop(Q, i));
                     float o[4];
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                        const float pm1 = fmaf(K[c].ex[k], B[c], Y[c]);
+                        const float pm1 = Q == 27 ? fmaf(K[c].ex[k], B[c], Y[c])
+                                                  : (cx == 0 ? Y[c] : (cx == 1 ? YQ[c] + B[c] : YQ[c] - B[c]));
                         const float Cc = cx == 0 ? Cz[c] : (cx == 1 ? Cp[c] : Cm[c]);
                         const float Kv = fmaf(K[c].cb, pm1, Cc);
                         // FP32 storage stores f = g' + w: w (1 + K) in one rounding, so
@@ -941,7 +1006,7 @@ __global__ void __launch_bounds__(256, 1)
                         // would be dropped with a consistent sign, a mass bias)
                         o[c] = fmaf(K[c].ca, g[k][c], SHIFTED ? w * Kv : fmaf(w, Kv, w));
                     }
-                    if (own_store) v4_store(fout + ((long long)i * ps + cell), o[0], o[1], o[2], o[3]);
+                    if (own_store) v4_store(fout + ((long long)v4_pop(Q, i) * ps + cell), o[0], o[1], o[2], o[3]);
                 });
             });
         }

@@ -1,11 +1,11 @@
 // Four-cell step kernel instantiations for the channel (variants 14 and 16):
 // D3Q27, float storage, halfway bounce-back walls in y with a body force, BGK
 // and KC-MP.
-#include "lbm_step_v4.cuh"
+#include "lbm_step_v4_inst.cuh"
 
 namespace lbmk {
 
-cudaError_t launch_v4_walls(int closure, int ty, bool tma, const StepArgs* a, int nbatch, cudaStream_t s)
+cudaError_t launch_v4_walls_q27(int closure, int ty, bool tma, const StepArgs* a, int nbatch, cudaStream_t s)
 {
     constexpr int Q = 27;
     using S = float;

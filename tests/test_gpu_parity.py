@@ -476,17 +476,17 @@ def test_ensemble_and_channel_launch_through_graph(lbm, orc):
 
 
 def test_default_variant_selection(lbm):
-    """Library default: periodic D3Q27 with 32- or 16-bit storage and BGK,
+    """Library default: periodic D3Q27 with 32- or 16-bit storage, and D3Q19 with FP32 storage, and BGK,
     KC-MP or KC-RB takes the four-cell kernel (14) when nx is a multiple of 8
     (tiles 128 x 8, or 64 x 16 for boxes at most 64 wide), for FP32 storage
     with TMA staging (16) where nx is a multiple of the tile width and ny a
-    multiple of the tile height or at least eight tile heights; the D3Q27 FP32 channel with BGK or KC-MP the
+    multiple of the tile height or at least eight tile heights; the FP32 channel (D3Q27, D3Q19) with BGK or KC-MP the
     four-cell kernel (14) where (ny - 1) is not a multiple of the tile height,
     with KC-MP under the same conditions as the periodic box with TMA staging
     (16);
     otherwise, for FP32 storage, periodic D3Q27 with KC-MP or KC-RB the
     split-barrier pull with L2 prefetches (12) on z-chunks of at most 16
-    planes; KC-RR, D3Q19 and the other walls with KC-MP the split-barrier pull
+    planes; KC-RR and the other walls with KC-MP the split-barrier pull
     with asynchronous copies (13); periodic
     D3Q27 otherwise (BGK, FP64, 16-bit storage) the split-barrier pull (8);
     the learned closure on periodic boxes the register pull with the network on
@@ -495,13 +495,13 @@ def test_default_variant_selection(lbm):
     is not built for a box is refused."""
     for q, closure, storage, want in ((27, "kcmp", "fp32", 14), (27, "kcrb_hermite", "fp16", 14), (27, "kcmp", "fp64", 8),
                                       (27, "kcrb_raw", "fp32", 14), (27, "kcrr", "fp32", 13),
-                                      (27, "bgk", "bf16", 14), (19, "kcmp", "fp32", 13), (19, "bgk", "fp32", 1),
+                                      (27, "bgk", "bf16", 14), (19, "kcmp", "fp32", 14), (19, "bgk", "fp32", 14),
                                       (19, "kcmp", "fp16", 1), (27, "kcrr", "fp64", 8),
                                       (27, "learned", "fp32", 15), (27, "learned", "bf16", 15),
                                       (19, "learned", "fp32", 15)):
         with lbm.Solver(q, (40, 32, 64), 1e-4, closure=closure, storage=storage) as s:
             assert s.launch_config["variant"] == want, (q, closure, storage)
-            ty = {14: 16, 15: 4, 1: 4 if closure == "learned" else 8}.get(want, 8)
+            ty = {14: 16, 15: 4, 1: 4 if closure == "learned" else 8}.get(want, 8)  # nx = 40: 64 x 16 tiles
             assert s.launch_config["tile_y"] == ty, (q, closure, storage)
     with lbm.Solver(27, (256, 36, 64), 1e-4, closure="kcmp", storage="fp32") as s:
         assert s.launch_config["variant"] == 14 and s.launch_config["tile_y"] == 8  # a ragged tile, ny < 8 tile heights
@@ -522,7 +522,8 @@ def test_default_variant_selection(lbm):
     # walls: the four-cell kernel for D3Q27 FP32 with BGK or KC-MP where the top
     # wall row is not the first row of a tile ((ny - 1) % 8 != 0), else variant 13 / 1
     for q, closure, ny, want in ((27, "kcmp", 32, 14), (27, "bgk", 32, 14), (27, "kcmp", 33, 13),
-                                 (19, "kcmp", 32, 13), (27, "kcrb_hermite", 32, 1), (27, "bgk", 33, 1)):
+                                 (19, "kcmp", 32, 14), (19, "kcmp", 33, 13), (27, "kcrb_hermite", 32, 1),
+                                 (27, "bgk", 33, 1)):
         with lbm.Solver(q, (40, ny, 16), 1e-4, closure=closure, storage="fp32", bc=(0, 1, 0)) as s:
             assert s.launch_config["variant"] == want, (q, closure, ny, "walls")
     for closure, want in (("kcmp", 16), ("bgk", 14)):  # nx a multiple of 64, ny = 130 spans eight 16-row tiles

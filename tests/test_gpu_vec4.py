@@ -52,8 +52,8 @@ def _fields(shape, nbatch, seed):
     return fs, np.stack([f[0] for f in fs]), np.stack([f[1] for f in fs], axis=1)
 
 
-def _run(lbm, shape, nus, closure, storage, variant, rho, u, steps, **kw):
-    with lbm.Solver(27, shape, nus, closure=closure, c_nu=CNU[closure], storage=storage, variant=variant,
+def _run(lbm, shape, nus, closure, storage, variant, rho, u, steps, q=27, **kw):
+    with lbm.Solver(q, shape, nus, closure=closure, c_nu=CNU[closure], storage=storage, variant=variant,
                     nbatch=len(nus), **kw) as s:
         assert s.launch_config["variant"] == variant
         s.init_velocity(rho, u)
@@ -193,6 +193,77 @@ def test_vec4_channel_fp32(lbm, orc, closure, shape, tile_y, variant):
         assert np.array_equal(res[zc], res[0]), zc
     assert rel(res[0], ref) < 1e-6, rel(res[0], ref)
     fo = orc.run(orc.init_equilibrium(27, rho, u), 8, closure=CL[closure], nu=nu, c_nu=CNU[closure], bc=(0, 1, 0),
+                 F=force)
+    _, ug = orc.fields(res[0], F=force)
+    _, uo = orc.fields(fo, F=force)
+    assert np.abs(ug - uo).max() < 1e-6, np.abs(ug - uo).max()
+
+
+@pytest.mark.parametrize("variant,tile_y", LAUNCHES)
+@pytest.mark.parametrize("shape", [(256, 20, 9), (128, 32, 6), (24, 5, 3)])
+@pytest.mark.parametrize("closure", ["bgk", "kcmp", "kcrb_hermite", "kcrb_raw"])
+def test_vec4_d3q19_fp32(lbm, orc, closure, shape, tile_y, variant):
+    """D3Q19 on the four-cell kernel: the populations keep their D3Q27 positions
+    (staged rows, TMEM columns, triples along x), the four triples with
+    c_y c_z != 0 hold their c_x = 0 population only, and the relaxation takes
+    the second-order Hermite equilibrium along a triple.  Against the register
+    pull (variant 1) to FP32 rounding and the FP64 oracle in velocity, over 8
+    steps, two boxes and several z-chunkings."""
+    nus = np.array([2e-5, 1e-4])
+    if variant == 16 and shape[0] % (128 if tile_y == 8 else 64) != 0:
+        with pytest.raises(lbm.LbmError) as ei:
+            lbm.Solver(19, shape, nus, closure=closure, storage="fp32", variant=variant, tile_y=tile_y, nbatch=2)
+        assert ei.value.code == lbm.LBM_ERR_UNSUPPORTED
+        return
+    fields, rho, u = _fields(shape, 2, 80)
+    ref, _ = _run(lbm, shape, nus, closure, "fp32", 1, rho, u, 8, q=19)
+    res = {}
+    for zc in (0, 1, 3):
+        res[zc], cfg = _run(lbm, shape, nus, closure, "fp32", variant, rho, u, 8, q=19, tile_y=tile_y, zchunk=zc)
+        assert cfg["tile_y"] == tile_y
+    for zc in (1, 3):
+        assert np.array_equal(res[zc], res[0]), zc
+    assert rel(res[0], ref) < 1e-6, rel(res[0], ref)
+    for b in range(2):
+        fo = orc.run(orc.init_equilibrium(19, fields[b][0], fields[b][1]), 8, closure=CL[closure], nu=nus[b],
+                     c_nu=CNU[closure])
+        _, ug = orc.fields(res[0][b])
+        _, uo = orc.fields(fo)
+        assert np.abs(ug - uo).max() < 1e-6, (b, np.abs(ug - uo).max())
+
+
+@pytest.mark.parametrize("variant,tile_y", LAUNCHES)
+@pytest.mark.parametrize("shape", [(64, 11, 9), (128, 27, 5)])
+@pytest.mark.parametrize("closure", ["bgk", "kcmp"])
+def test_vec4_channel_d3q19_fp32(lbm, orc, closure, shape, tile_y, variant):
+    """The D3Q19 channel on the four-cell kernel (halfway bounce-back walls in
+    y, one-sided strain, Guo force), against the register pull and the FP64
+    oracle, as the D3Q27 channel test."""
+    force = (2e-5, 0.0, 0.0)
+    nx, ny, nz = shape
+    if variant == 16 and nx % (128 if tile_y == 8 else 64) != 0 or (ny - 1) % tile_y == 0:
+        with pytest.raises(lbm.LbmError):
+            lbm.Solver(19, shape, 2e-3, closure=closure, storage="fp32", variant=variant, tile_y=tile_y,
+                       bc=(0, 1, 0), force=force)
+        return
+    rho, u = inputs.channel_fields(nx, ny, nz, 0.05, seed=11)
+    nu = 2e-3
+    with lbm.Solver(19, shape, nu, closure=closure, c_nu=CNU[closure], storage="fp32", variant=1, bc=(0, 1, 0),
+                    force=force) as s:
+        s.init_velocity(rho, u)
+        s.step(8)
+        ref = s.get_populations()
+    res = {}
+    for zc in (0, 3):
+        with lbm.Solver(19, shape, nu, closure=closure, c_nu=CNU[closure], storage="fp32", variant=variant,
+                        tile_y=tile_y, zchunk=zc, bc=(0, 1, 0), force=force) as s:
+            assert s.launch_config["variant"] == variant and s.launch_config["tile_y"] == tile_y
+            s.init_velocity(rho, u)
+            s.step(8)
+            res[zc] = s.get_populations()
+    assert np.array_equal(res[3], res[0])
+    assert rel(res[0], ref) < 1e-6, rel(res[0], ref)
+    fo = orc.run(orc.init_equilibrium(19, rho, u), 8, closure=CL[closure], nu=nu, c_nu=CNU[closure], bc=(0, 1, 0),
                  F=force)
     _, ug = orc.fields(res[0], F=force)
     _, uo = orc.fields(fo, F=force)

@@ -102,18 +102,19 @@ typedef struct {
                            learned closure, else 8)                                  */
     int zchunk;         /* tuning: z-planes per CTA march (0 = library default)      */
     int variant;        /* tuning: step-kernel variant, 0 = library default
-                           (periodic D3Q27 with FP32/FP16/BF16 storage and
-                           BGK, KC-MP or KC-RB, nx % 8 == 0: 14, tiles
-                           128 x 8, or 64 x 16 for nx <= 64, and for FP32
-                           storage 16 where nx is a multiple of the tile
-                           width and ny a multiple of the tile height or
-                           >= 8 tile heights; the D3Q27 FP32 channel with BGK
-                           or KC-MP, nx % 8 == 0 and (ny - 1) % 16 != 0: 14
-                           on 64 x 16 tiles, with KC-MP 16 under the same
-                           conditions as the periodic box; else, for
+                           (periodic D3Q27 with FP32/FP16/BF16 storage, and
+                           D3Q19 with FP32 storage, and BGK, KC-MP or KC-RB,
+                           nx % 8 == 0: 14, tiles 128 x 8, or 64 x 16 for
+                           nx <= 64, and for FP32 storage 16 where nx is a
+                           multiple of the tile width and ny a multiple of
+                           the tile height or >= 8 tile heights; the FP32
+                           channel (D3Q27, D3Q19) with BGK or KC-MP, nx % 8
+                           == 0 and (ny - 1) % 16 != 0: 14 on 64 x 16 tiles,
+                           with KC-MP 16 under the same conditions as the
+                           periodic box; else, for
                            FP32 storage, 12 on z-chunks of at most 16 planes
                            for periodic D3Q27 with KC-MP or KC-RB, 13 for
-                           KC-RR, D3Q19 and walls; else 8 for periodic D3Q27 except
+                           KC-RR and walls; else 8 for periodic D3Q27 except
                            the learned closure; the learned closure on
                            periodic boxes with 32- or 16-bit storage: 15;
                            else 1),
@@ -129,8 +130,10 @@ typedef struct {
                            in shared memory by cp.async one plane ahead and
                            the populations parked in tensor memory until
                            their collision (periodic D3Q27, FP32/FP16/BF16
-                           storage, BGK/KC-MP/KC-RB, nx % 8 == 0; and the
-                           FP32 channel, walls in y with a force, BGK/KC-MP,
+                           storage, and periodic D3Q19, FP32 storage,
+                           BGK/KC-MP/KC-RB, nx % 8 == 0; and the FP32
+                           channel of either lattice, walls in y with a
+                           force, BGK/KC-MP,
                            (ny - 1) % tile_y != 0; tile_y 8:
                            128 x 8 tiles, 16: 64 x 16 tiles; the learned
                            closure: 64 x 16 tiles, and 128 x 8 for 16-bit

@@ -40,6 +40,7 @@ WORKLOADS = {
     "hit256_d3q27_bf16_kcmp": dict(n=256, q=27, storage="bf16", closure="kcmp", nu=1e-4, k0=4.0, urms=0.04),
     "hit512_d3q19_fp32_kcmp": dict(n=512, q=19, storage="fp32", closure="kcmp", nu=1e-4, k0=4.0, urms=0.04),
     "hit256_d3q19_fp32_kcmp": dict(n=256, q=19, storage="fp32", closure="kcmp", nu=1e-4, k0=4.0, urms=0.04),
+    "hit512_d3q19_fp16_kcmp": dict(n=512, q=19, storage="fp16", closure="kcmp", nu=1e-4, k0=4.0, urms=0.04),
     "hit512_d3q27_fp32_bgk": dict(n=512, q=27, storage="fp32", closure="bgk", nu=1e-4, k0=4.0, urms=0.04),
     "hit512_d3q27_fp32_kcrr": dict(n=512, q=27, storage="fp32", closure="kcrr", nu=1e-4, k0=4.0, urms=0.04),
     "hit512_d3q27_fp32_kcrb_raw": dict(n=512, q=27, storage="fp32", closure="kcrb_raw", nu=1e-4, k0=4.0, urms=0.04),

@@ -102,8 +102,8 @@ typedef struct {
                            learned closure, else 8)                                  */
     int zchunk;         /* tuning: z-planes per CTA march (0 = library default)      */
     int variant;        /* tuning: step-kernel variant, 0 = library default
-                           (periodic D3Q27 with FP32/FP16/BF16 storage, and
-                           D3Q19 with FP32 storage, and BGK, KC-MP or KC-RB,
+                           (periodic D3Q27 and D3Q19 with FP32/FP16/BF16
+                           storage and BGK, KC-MP or KC-RB,
                            nx % 8 == 0: 14, tiles 128 x 8, or 64 x 16 for
                            nx <= 64, and for FP32 storage 16 where nx is a
                            multiple of the tile width and ny a multiple of
@@ -129,9 +129,9 @@ typedef struct {
                            (16-bit) vector loads and stores, the pulls staged
                            in shared memory by cp.async one plane ahead and
                            the populations parked in tensor memory until
-                           their collision (periodic D3Q27, FP32/FP16/BF16
-                           storage, and periodic D3Q19, FP32 storage,
-                           BGK/KC-MP/KC-RB, nx % 8 == 0; and the FP32
+                           their collision (periodic D3Q27 and D3Q19,
+                           FP32/FP16/BF16 storage, BGK/KC-MP/KC-RB,
+                           nx % 8 == 0; and the FP32
                            channel of either lattice, walls in y with a
                            force, BGK/KC-MP,
                            (ny - 1) % tile_y != 0; tile_y 8:

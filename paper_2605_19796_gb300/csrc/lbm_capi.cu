@@ -523,8 +523,8 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
         // the channel: FP32, BGK or KC-MP, the top wall row not the first row of a tile
         const bool v4_walls = bc_kind == BC_WALLS_Y && cfg->storage == LBM_FP32 &&
                               (cfg->closure == LBM_KCMP || cfg->closure == LBM_BGK) && (cfg->ny - 1) % v4_ty0 != 0;
-        // D3Q27, and D3Q19 with FP32 storage
-        const bool v4_lattice = cfg->lattice == LBM_D3Q27 || (cfg->lattice == LBM_D3Q19 && cfg->storage == LBM_FP32);
+        // D3Q27 and D3Q19
+        const bool v4_lattice = cfg->lattice == LBM_D3Q27 || cfg->lattice == LBM_D3Q19;
         const bool v4_first = v4_lattice && (bc_kind == BC_PERIODIC || v4_walls) &&
                               cfg->storage != LBM_FP64 && cfg->closure != LBM_KCRR && cfg->closure != LBM_LEARNED &&
                               vec4_shape_ok(cfg->nx) && (cfg->tile_y == 0 || cfg->tile_y == 8 || cfg->tile_y == 16);

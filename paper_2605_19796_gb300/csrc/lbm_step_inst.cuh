@@ -23,7 +23,7 @@
 namespace lbmk {
 
 // four-cell kernels of lattice Q with storage S (variants 14 and 16), defined
-// in lbm_step_v4_*.cu (D3Q27: FP32, FP16, BF16 storage; D3Q19: FP32); same
+// in lbm_step_v4_*.cu (FP32, FP16 and BF16 storage of either lattice); same
 // conventions as launch_step_qs
 template <int Q, typename S>
 cudaError_t launch_v4_qs(int closure, int bc, int ty, bool tma, const StepArgs* a, int nbatch, cudaStream_t s);
@@ -37,8 +37,7 @@ cudaError_t launch_step_qs(int closure, int bc, int ty, int variant, const StepA
     if (variant == VAR_VEC4 || variant == VAR_VEC4_TMA) {
         // the four-cell kernels live in their own translation units (lbm_step_v4_*.cu)
         if constexpr (Q == 27 && R32) return launch_v4_qs<27, S>(closure, bc, ty, variant == VAR_VEC4_TMA, a, nbatch, s);
-        if constexpr (Q == 19 && std::is_same<S, float>::value)
-            return launch_v4_qs<19, S>(closure, bc, ty, variant == VAR_VEC4_TMA, a, nbatch, s);
+        if constexpr (Q == 19 && R32) return launch_v4_qs<19, S>(closure, bc, ty, variant == VAR_VEC4_TMA, a, nbatch, s);
         return cudaErrorNotSupported;
     }
     if (variant == VAR_SPLIT) {

@@ -476,7 +476,7 @@ def test_ensemble_and_channel_launch_through_graph(lbm, orc):
 
 
 def test_default_variant_selection(lbm):
-    """Library default: periodic D3Q27 with 32- or 16-bit storage, and D3Q19 with FP32 storage, and BGK,
+    """Library default: periodic D3Q27 and D3Q19 with 32- or 16-bit storage and BGK,
     KC-MP or KC-RB takes the four-cell kernel (14) when nx is a multiple of 8
     (tiles 128 x 8, or 64 x 16 for boxes at most 64 wide), for FP32 storage
     with TMA staging (16) where nx is a multiple of the tile width and ny a
@@ -496,7 +496,7 @@ def test_default_variant_selection(lbm):
     for q, closure, storage, want in ((27, "kcmp", "fp32", 14), (27, "kcrb_hermite", "fp16", 14), (27, "kcmp", "fp64", 8),
                                       (27, "kcrb_raw", "fp32", 14), (27, "kcrr", "fp32", 13),
                                       (27, "bgk", "bf16", 14), (19, "kcmp", "fp32", 14), (19, "bgk", "fp32", 14),
-                                      (19, "kcmp", "fp16", 1), (27, "kcrr", "fp64", 8),
+                                      (19, "kcmp", "fp16", 14), (27, "kcrr", "fp64", 8),
                                       (27, "learned", "fp32", 15), (27, "learned", "bf16", 15),
                                       (19, "learned", "fp32", 15)):
         with lbm.Solver(q, (40, 32, 64), 1e-4, closure=closure, storage=storage) as s:

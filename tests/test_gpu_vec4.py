@@ -268,3 +268,26 @@ def test_vec4_channel_d3q19_fp32(lbm, orc, closure, shape, tile_y, variant):
     _, ug = orc.fields(res[0], F=force)
     _, uo = orc.fields(fo, F=force)
     assert np.abs(ug - uo).max() < 1e-6, np.abs(ug - uo).max()
+
+
+@pytest.mark.parametrize("variant", [14, 16])
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+@pytest.mark.parametrize("closure", ["bgk", "kcmp"])
+def test_vec4_d3q19_16bit_matches_register_pull(lbm, orc, closure, storage, variant):
+    """D3Q19 with weight-shifted 16-bit storage on the four-cell kernel against
+    the register pull, to eight ulps of the 16-bit format at the largest
+    |f - w|, as the D3Q27 16-bit test."""
+    shape = (128, 21, 7)
+    nus = np.array([2e-5, 1e-4])
+    _, rho, u = _fields(shape, 2, 90)
+    ref, _ = _run(lbm, shape, nus, closure, storage, 1, rho, u, 5, q=19)
+    got, _ = _run(lbm, shape, nus, closure, storage, variant, rho, u, 5, q=19, tile_y=8)
+    got2, _ = _run(lbm, shape, nus, closure, storage, variant, rho, u, 5, q=19, tile_y=8, zchunk=2)
+    assert np.array_equal(got, got2)
+    w = orc.lattice(19)[1][None, :, None, None, None]
+    gmax = np.abs(ref - w).max()
+    tol = 8 * (2.0 ** -10 if storage == "fp16" else 2.0 ** -7) * gmax
+    for b in range(2):
+        r1, u1 = orc.fields(ref[b])
+        rv, uv = orc.fields(got[b])
+        assert np.abs(rv - r1).max() < tol and np.abs(uv - u1).max() < tol, (b, tol)

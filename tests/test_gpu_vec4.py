@@ -95,12 +95,14 @@ def test_vec4_fp32_matches_register_pull_and_oracle(lbm, orc, closure, shape, ti
         assert np.abs(ug - uo).max() < 1e-6, (b, np.abs(ug - uo).max())
 
 
+@pytest.mark.parametrize("shape", [(128, 21, 7), (128, 32, 5)])
 @pytest.mark.parametrize("variant", [14, 16])
 @pytest.mark.parametrize("tile_y", [8, 16])
 @pytest.mark.parametrize("storage", ["fp16", "bf16"])
 @pytest.mark.parametrize("closure", ["bgk", "kcmp", "kcrb_hermite", "kcrb_raw"])
-def test_vec4_16bit_matches_register_pull(lbm, orc, closure, storage, tile_y, variant):
-    shape = (128, 21, 7)
+def test_vec4_16bit_matches_register_pull(lbm, orc, closure, storage, tile_y, variant, shape):
+    # (128, 32, 5): full tiles in y, so the TMA-staged variant copies the wrapping
+    # rows of the first and the last tile row as one box and one or two rows
     nus = np.array([2e-5, 1e-4])
     _, rho, u = _fields(shape, 2, 70)
     ref, _ = _run(lbm, shape, nus, closure, storage, 1, rho, u, 5)

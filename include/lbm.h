@@ -107,7 +107,8 @@ typedef struct {
                            nx % 8 == 0: 14, tiles 128 x 8, or 64 x 16 for
                            nx <= 64, and for FP32 storage 16 where nx is a
                            multiple of the tile width and ny a multiple of
-                           the tile height or >= 8 tile heights; the FP32
+                           the tile height or >= 8 tile heights (also for
+                           D3Q27 KC-RR); the FP32
                            channel (D3Q27, D3Q19) with BGK or KC-MP, nx % 8
                            == 0 and (ny - 1) % 16 != 0: 14 on 64 x 16 tiles,
                            with KC-MP 16 under the same conditions as the
@@ -130,8 +131,8 @@ typedef struct {
                            in shared memory by cp.async one plane ahead and
                            the populations parked in tensor memory until
                            their collision (periodic D3Q27 and D3Q19,
-                           FP32/FP16/BF16 storage, BGK/KC-MP/KC-RB,
-                           nx % 8 == 0; and the FP32
+                           FP32/FP16/BF16 storage, BGK/KC-MP/KC-RB, and
+                           KC-RR on D3Q27, nx % 8 == 0; and the FP32
                            channel of either lattice, walls in y with a
                            force, BGK/KC-MP,
                            (ny - 1) % tile_y != 0; tile_y 8:
@@ -145,7 +146,7 @@ typedef struct {
                            storage), 16 = 14 with the interior of the
                            staged rows copied by the Tensor Memory
                            Accelerator (one cp.async.bulk.tensor per
-                           population and plane; BGK/KC-MP/KC-RB, nx a
+                           population and plane; BGK/KC-MP/KC-RB/KC-RR, nx a
                            multiple of 128, or 64 for tile_y 16;
                            LBM_ERR_UNSUPPORTED otherwise); other values,
                            among them the retired 2-7, 9, 10 and 11:

@@ -526,7 +526,7 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
         // D3Q27 and D3Q19
         const bool v4_lattice = cfg->lattice == LBM_D3Q27 || cfg->lattice == LBM_D3Q19;
         const bool v4_first = v4_lattice && (bc_kind == BC_PERIODIC || v4_walls) &&
-                              cfg->storage != LBM_FP64 && cfg->closure != LBM_KCRR && cfg->closure != LBM_LEARNED &&
+                              cfg->storage != LBM_FP64 && cfg->closure != LBM_LEARNED &&
                               vec4_shape_ok(cfg->nx) && (cfg->tile_y == 0 || cfg->tile_y == 8 || cfg->tile_y == 16);
         const bool pf_first = cfg->lattice == LBM_D3Q27 && bc_kind == BC_PERIODIC && cfg->storage == LBM_FP32 &&
                               (cfg->closure == LBM_KCMP || cfg->closure == LBM_KCRB_HERMITE ||
@@ -544,7 +544,8 @@ int lbm_create(const lbm_config* cfg, lbm_handle** out)
             variant = VAR_VEC4_TMA;
             tile_y = v4_ty;
             vec4_chunks = true;
-        } else if (v4_first && step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, v4_ty, VAR_VEC4)) {
+        } else if (v4_first && cfg->closure != LBM_KCRR &&  // KC-RR on cp.async staging: 19.3 GLUPS, 13: 20.2
+                   step_supported(cfg->lattice, cfg->storage, cfg->closure, bc_kind, v4_ty, VAR_VEC4)) {
             variant = VAR_VEC4;
             tile_y = v4_ty;
             vec4_chunks = true;

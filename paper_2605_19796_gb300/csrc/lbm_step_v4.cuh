@@ -328,7 +328,10 @@ __global__ void __launch_bounds__(256, 1)
     static_assert(Q == 27 || Q == 19, "the four-cell kernel is built for D3Q27 and D3Q19 (population triples along x)");
     static_assert(Q == 27 || CL != CL_LEARNED, "the learned closure's four-cell kernel is D3Q27");
     static_assert(!std::is_same<S, double>::value, "FP32 arithmetic");
-    static_assert(CL == CL_BGK || CL == CL_KCMP || CL == CL_KCRB_H || CL == CL_KCRB_RAW || CL == CL_LEARNED, "closure");
+    static_assert(CL == CL_BGK || CL == CL_KCMP || CL == CL_KCRB_H || CL == CL_KCRB_RAW || CL == CL_KCRR ||
+                      CL == CL_LEARNED,
+                  "closure");
+    static_assert(CL != CL_KCRR || (Q == 27 && BC == BC_PERIODIC), "KC-RR: D3Q27, periodic boxes");
     constexpr bool LEARNED = CL == CL_LEARNED;
     constexpr bool WALLS = BC == BC_WALLS_Y;
     static_assert(!(WALLS && LEARNED), "the learned closure runs on periodic boxes");
@@ -865,151 +868,193 @@ __global__ void __launch_bounds__(256, 1)
                                 S6[4][c], S6[5][c], tau_hat, sm_mlp, sm_xch, lane, msg[c]);
             }
         }
-        // per-cell relaxation constants
-        V4Cell K[4];
-        {
-            constexpr float a1 = (float)(1.0 / kTheta);
-            constexpr float a2 = (float)((1.0 - kTheta) / (2.0 * kTheta * kTheta));
-            constexpr float a0 = (float)(-kTheta / (2.0 * kTheta * kTheta));
+        if constexpr (CL == CL_KCRR) {
+            // KC-RR (App. F.4): its Hermite-space collision needs all 27 populations
+            // of a cell at once, so the cells go one at a time: the cell's 27 TMEM
+            // columns (12 p + 4 k + c) into registers, collide_kcrr, the results
+            // back into the same columns; then every population's four results
+            // leave as one vector store, as in the other closures' relaxation
+            const uint32_t ts = tslot(z);
+            const int cell = z * plane + gyw * nx + xaw;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 if (own_store && !isfinite(dr0[c] + uo[0][c] + uo[1][c] + uo[2][c])) atomicOr(a.flag, kFlagNonfinite);
-                const float P6[6] = {P0[0][c], P0[1][c], P0[2][c], P0[3][c], P0[4][c], P0[5][c]};
-                const Coef<float> k = collide_coef<Q, float, CL>(P6, dr0[c], uo[0][c], uo[1][c], uo[2][c], S6[0][c],
-                                                                 S6[1][c], S6[2][c], S6[3][c], S6[4][c], S6[5][c],
-                                                                 omega, tau_hat, nu, cnud, LEARNED ? msg[c] : nullptr);
-                const float ux = uo[0][c], uy = uo[1][c], uz = uo[2][c];
-                const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
-                if constexpr (Q == 27) {
-                    K[c].ex[0] = -a1 * ux + a2 * ux2;
-                    K[c].ex[1] = a0 * ux2;
-                    K[c].ex[2] = a1 * ux + a2 * ux2;
-                    K[c].ey[0] = -a1 * uy + a2 * uy2;
-                    K[c].ey[1] = a0 * uy2;
-                    K[c].ey[2] = a1 * uy + a2 * uy2;
-                    K[c].ez[0] = -a1 * uz + a2 * uz2;
-                    K[c].ez[1] = a0 * uz2;
-                    K[c].ez[2] = a1 * uz + a2 * uz2;
-                } else {
-                    K[c].qx = a1 * ux;
-                    K[c].qy = a1 * uy;
-                    K[c].qz = a1 * uz;
-                    K[c].qq = 0.5f * K[c].qx * K[c].qx;
-                    K[c].hu = -0.5f * a1 * ((ux2 + uy2) + uz2);
-                }
-                K[c].ca = k.ca;
-                K[c].cb = k.cb;
-                const float c0 = k.c0;
-                if constexpr (CL == CL_BGK) {
+                uint32_t r[27];
 #pragma unroll
-                    for (int q = 0; q < 5; ++q) K[c].C[q] = c0;
-                    K[c].Dxx = K[c].Dxy2 = K[c].Dxz2 = 0.f;
-                } else {
-                    const float h0 = -k.t, h1 = k.Myy - k.t, h2 = k.Mzz - k.t, hyz = (k.Myy + k.Mzz) - k.t;
-                    K[c].C[0] = c0 + k.D * h0;
-                    K[c].C[1] = c0 + k.D * h1;
-                    K[c].C[2] = c0 + k.D * h2;
-                    K[c].C[3] = c0 + k.D * (hyz + 2.f * k.Myz);
-                    K[c].C[4] = c0 + k.D * (hyz - 2.f * k.Myz);
-                    K[c].Dxx = k.D * k.Mxx;
-                    K[c].Dxy2 = 2.f * k.D * k.Mxy;
-                    K[c].Dxz2 = 2.f * k.D * k.Mxz;
-                }
-                if constexpr (WALLS) {
-                    // Guo's source over w, P1 (c.F - u.F) + P2 (c.u)(c.F) with P1 = (1 - omega/2)/theta
-                    // and P2 = P1/theta: its parts quadratic in c and the constant join the
-                    // per-cell quadratic form (the (c_y, c_z) patterns, c_x^2, c_x c_y, c_x c_z),
-                    // its part linear in c, uniform over the box, the per-triple constants below
-                    const float yF = gp2 * uy * Fy, zF = gp2 * uz * Fz, yzF = gp2 * (uy * Fz + uz * Fy);
-                    const float cF = -gp1 * (ux * Fx + uy * Fy + uz * Fz);
-                    K[c].C[0] += cF;
-                    K[c].C[1] += cF + yF;
-                    K[c].C[2] += cF + zF;
-                    K[c].C[3] += cF + (yF + zF) + yzF;
-                    K[c].C[4] += cF + (yF + zF) - yzF;
-                    K[c].Dxx += gp2 * ux * Fx;
-                    K[c].Dxy2 += gp2 * (ux * Fy + uy * Fx);
-                    K[c].Dxz2 += gp2 * (ux * Fz + uz * Fx);
-                }
+                for (int i = 0; i < 27; ++i) tm_ld1_issue(ts + (uint32_t)(12 * (i / 3) + 4 * (i % 3) + c), r[i]);
+                tm_ld_wait9(r);
+                tm_ld_wait9(r + 9);
+                tm_ld_wait9(r + 18);
+                float g[27];
+#pragma unroll
+                for (int i = 0; i < 27; ++i) g[i] = __uint_as_float(r[i]);
+                collide_kcrr<float>(g, dr0[c], uo[0][c], uo[1][c], uo[2][c], S6[0][c], S6[1][c], S6[2][c], S6[3][c],
+                                    S6[4][c], S6[5][c], omega, tau_hat, nu, cnud);
+#pragma unroll
+                for (int i = 0; i < 27; ++i)
+                    tm_st1(ts + (uint32_t)(12 * (i / 3) + 4 * (i % 3) + c), __float_as_uint(g[i]));
             }
-        }
-        // relaxation, one population triple of the four cells at a time
-        {
-            const uint32_t ts = tslot(z);
-            const int cell = z * plane + gyw * nx + xaw;
-            // the triples' populations come from TMEM one triple ahead (PF): the load
-            // of triple p + 1 is issued once triple p's has completed (tcgen05.wait::ld
-            // waits for all of the thread's loads), and lands while triple p is
-            // relaxed and stored and triple p + 1's constants are formed.  Kernels
-            // that carry the z-neighbours in registers have no registers for the
-            // second triple: they issue each triple's load before forming its
-            // constants.
-            constexpr bool PF = RZ && !WALLS;
-            uint32_t gr[2][12];
-            if constexpr (PF) tm_ld12_issue(ts, gr[0]);
+            tm_wait_st();
             static_for<9>([&](auto PI) {
                 constexpr int p = decltype(PI)::value;
-                constexpr int cy = p % 3 - 1, cz = p / 3 - 1, pat = v4_pat(cy, cz);
-                constexpr int sl = PF ? (p & 1) : 0;
-                if constexpr (!PF) tm_ld12_issue(ts + 12u * p, gr[0]);
-                float Y[4], B[4], Cm[4], Cp[4], Cz[4], YQ[4];
-                // walls: Guo's source part linear in c, P1 (c_y F_y + c_z F_z) on the
-                // triple and P1 F_x c_x
-                float BFg = 0.f;
-                if constexpr (WALLS && cy != 0) BFg += (float)cy * (gp1 * Fy);
-                if constexpr (WALLS && cz != 0) BFg += (float)cz * (gp1 * Fz);
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    if constexpr (Q == 27) {  // P - 1 = e_x (1 + Y) + Y along the triple
-                        const float ey = K[c].ey[cy + 1], ez = K[c].ez[cz + 1];
-                        Y[c] = fmaf(ey, ez, ey + ez);
-                        B[c] = 1.f + Y[c];
-                    } else {  // D3Q19: P - 1 = Y + c_x qx (1 + Bq) + c_x^2 qq, B = qx (1 + Bq)
-                        float Bq = 0.f;
-                        if constexpr (cy != 0) Bq = (float)cy * K[c].qy;
-                        if constexpr (cz != 0) Bq = fmaf((float)cz, K[c].qz, Bq);
-                        Y[c] = fmaf(0.5f * Bq, Bq, Bq + K[c].hu);
-                        B[c] = fmaf(K[c].qx, Bq, K[c].qx);
-                        YQ[c] = Y[c] + K[c].qq;
-                    }
-                    Cz[c] = (WALLS && (cy != 0 || cz != 0)) ? K[c].C[pat] + BFg : K[c].C[pat];
-                    if constexpr (CL != CL_BGK || WALLS) {
-                        float X = WALLS ? gp1 * Fx : 0.f;
-                        if constexpr (cy != 0) X += (float)cy * K[c].Dxy2;
-                        if constexpr (cz != 0) X += (float)cz * K[c].Dxz2;
-                        const float CpD = Cz[c] + K[c].Dxx;
-                        Cp[c] = CpD + X;
-                        Cm[c] = CpD - X;
-                    } else {
-                        Cp[c] = Cm[c] = K[c].C[pat];
-                    }
-                }
-                tm_ld12_wait(gr[sl]);
-                float g[3][4];
-#pragma unroll
-                for (int q = 0; q < 12; ++q) g[q / 4][q % 4] = __uint_as_float(gr[sl][q]);
-                if constexpr (PF && p < 8) tm_ld12_issue(ts + 12u * (p + 1), gr[(p + 1) & 1]);
+                float gp[3][4];
+                tm_ld12(ts + 12u * p, gp);
                 static_for<3>([&](auto CI) {
-                    constexpr int k = decltype(CI)::value;
-                    constexpr int cx = k - 1, i = 3 * p + k;
-                    if constexpr (!v4_has(Q, i)) return;
-                    constexpr float w = (float)weight_of(Q, v4_pop(Q, i));
+                    constexpr int k = decltype(CI)::value, i = 3 * p + k;
+                    constexpr float w = (float)weight_of(Q, i);
                     float o[4];
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const float pm1 = Q == 27 ? fmaf(K[c].ex[k], B[c], Y[c])
-                                                  : (cx == 0 ? Y[c] : (cx == 1 ? YQ[c] + B[c] : YQ[c] - B[c]));
-                        const float Cc = cx == 0 ? Cz[c] : (cx == 1 ? Cp[c] : Cm[c]);
-                        const float Kv = fmaf(K[c].cb, pm1, Cc);
-                        // FP32 storage stores f = g' + w: w (1 + K) in one rounding, so
-                        // that no part of K is lost to a sum near 1 (its small terms
-                        // would be dropped with a consistent sign, a mass bias)
-                        o[c] = fmaf(K[c].ca, g[k][c], SHIFTED ? w * Kv : fmaf(w, Kv, w));
-                    }
-                    if (own_store) v4_store(fout + ((long long)v4_pop(Q, i) * ps + cell), o[0], o[1], o[2], o[3]);
+                    for (int c = 0; c < 4; ++c) o[c] = SHIFTED ? gp[k][c] : gp[k][c] + w;
+                    if (own_store) v4_store(fout + ((long long)i * ps + cell), o[0], o[1], o[2], o[3]);
                 });
             });
-        }
+        } else {
+            // per-cell relaxation constants
+            V4Cell K[4];
+            {
+                constexpr float a1 = (float)(1.0 / kTheta);
+                constexpr float a2 = (float)((1.0 - kTheta) / (2.0 * kTheta * kTheta));
+                constexpr float a0 = (float)(-kTheta / (2.0 * kTheta * kTheta));
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (own_store && !isfinite(dr0[c] + uo[0][c] + uo[1][c] + uo[2][c])) atomicOr(a.flag, kFlagNonfinite);
+                    const float P6[6] = {P0[0][c], P0[1][c], P0[2][c], P0[3][c], P0[4][c], P0[5][c]};
+                    const Coef<float> k = collide_coef<Q, float, CL>(P6, dr0[c], uo[0][c], uo[1][c], uo[2][c], S6[0][c],
+                                                                     S6[1][c], S6[2][c], S6[3][c], S6[4][c], S6[5][c],
+                                                                     omega, tau_hat, nu, cnud, LEARNED ? msg[c] : nullptr);
+                    const float ux = uo[0][c], uy = uo[1][c], uz = uo[2][c];
+                    const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+                    if constexpr (Q == 27) {
+                        K[c].ex[0] = -a1 * ux + a2 * ux2;
+                        K[c].ex[1] = a0 * ux2;
+                        K[c].ex[2] = a1 * ux + a2 * ux2;
+                        K[c].ey[0] = -a1 * uy + a2 * uy2;
+                        K[c].ey[1] = a0 * uy2;
+                        K[c].ey[2] = a1 * uy + a2 * uy2;
+                        K[c].ez[0] = -a1 * uz + a2 * uz2;
+                        K[c].ez[1] = a0 * uz2;
+                        K[c].ez[2] = a1 * uz + a2 * uz2;
+                    } else {
+                        K[c].qx = a1 * ux;
+                        K[c].qy = a1 * uy;
+                        K[c].qz = a1 * uz;
+                        K[c].qq = 0.5f * K[c].qx * K[c].qx;
+                        K[c].hu = -0.5f * a1 * ((ux2 + uy2) + uz2);
+                    }
+                    K[c].ca = k.ca;
+                    K[c].cb = k.cb;
+                    const float c0 = k.c0;
+                    if constexpr (CL == CL_BGK) {
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) K[c].C[q] = c0;
+                        K[c].Dxx = K[c].Dxy2 = K[c].Dxz2 = 0.f;
+                    } else {
+                        const float h0 = -k.t, h1 = k.Myy - k.t, h2 = k.Mzz - k.t, hyz = (k.Myy + k.Mzz) - k.t;
+                        K[c].C[0] = c0 + k.D * h0;
+                        K[c].C[1] = c0 + k.D * h1;
+                        K[c].C[2] = c0 + k.D * h2;
+                        K[c].C[3] = c0 + k.D * (hyz + 2.f * k.Myz);
+                        K[c].C[4] = c0 + k.D * (hyz - 2.f * k.Myz);
+                        K[c].Dxx = k.D * k.Mxx;
+                        K[c].Dxy2 = 2.f * k.D * k.Mxy;
+                        K[c].Dxz2 = 2.f * k.D * k.Mxz;
+                    }
+                    if constexpr (WALLS) {
+                        // Guo's source over w, P1 (c.F - u.F) + P2 (c.u)(c.F) with P1 = (1 - omega/2)/theta
+                        // and P2 = P1/theta: its parts quadratic in c and the constant join the
+                        // per-cell quadratic form (the (c_y, c_z) patterns, c_x^2, c_x c_y, c_x c_z),
+                        // its part linear in c, uniform over the box, the per-triple constants below
+                        const float yF = gp2 * uy * Fy, zF = gp2 * uz * Fz, yzF = gp2 * (uy * Fz + uz * Fy);
+                        const float cF = -gp1 * (ux * Fx + uy * Fy + uz * Fz);
+                        K[c].C[0] += cF;
+                        K[c].C[1] += cF + yF;
+                        K[c].C[2] += cF + zF;
+                        K[c].C[3] += cF + (yF + zF) + yzF;
+                        K[c].C[4] += cF + (yF + zF) - yzF;
+                        K[c].Dxx += gp2 * ux * Fx;
+                        K[c].Dxy2 += gp2 * (ux * Fy + uy * Fx);
+                        K[c].Dxz2 += gp2 * (ux * Fz + uz * Fx);
+                    }
+                }
+            }
+            // relaxation, one population triple of the four cells at a time
+            {
+                const uint32_t ts = tslot(z);
+                const int cell = z * plane + gyw * nx + xaw;
+                // the triples' populations come from TMEM one triple ahead (PF): the load
+                // of triple p + 1 is issued once triple p's has completed (tcgen05.wait::ld
+                // waits for all of the thread's loads), and lands while triple p is
+                // relaxed and stored and triple p + 1's constants are formed.  Kernels
+                // that carry the z-neighbours in registers have no registers for the
+                // second triple: they issue each triple's load before forming its
+                // constants.
+                constexpr bool PF = RZ && !WALLS;
+                uint32_t gr[2][12];
+                if constexpr (PF) tm_ld12_issue(ts, gr[0]);
+                static_for<9>([&](auto PI) {
+                    constexpr int p = decltype(PI)::value;
+                    constexpr int cy = p % 3 - 1, cz = p / 3 - 1, pat = v4_pat(cy, cz);
+                    constexpr int sl = PF ? (p & 1) : 0;
+                    if constexpr (!PF) tm_ld12_issue(ts + 12u * p, gr[0]);
+                    float Y[4], B[4], Cm[4], Cp[4], Cz[4], YQ[4];
+                    // walls: Guo's source part linear in c, P1 (c_y F_y + c_z F_z) on the
+                    // triple and P1 F_x c_x
+                    float BFg = 0.f;
+                    if constexpr (WALLS && cy != 0) BFg += (float)cy * (gp1 * Fy);
+                    if constexpr (WALLS && cz != 0) BFg += (float)cz * (gp1 * Fz);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        if constexpr (Q == 27) {  // P - 1 = e_x (1 + Y) + Y along the triple
+                            const float ey = K[c].ey[cy + 1], ez = K[c].ez[cz + 1];
+                            Y[c] = fmaf(ey, ez, ey + ez);
+                            B[c] = 1.f + Y[c];
+                        } else {  // D3Q19: P - 1 = Y + c_x qx (1 + Bq) + c_x^2 qq, B = qx (1 + Bq)
+                            float Bq = 0.f;
+                            if constexpr (cy != 0) Bq = (float)cy * K[c].qy;
+                            if constexpr (cz != 0) Bq = fmaf((float)cz, K[c].qz, Bq);
+                            Y[c] = fmaf(0.5f * Bq, Bq, Bq + K[c].hu);
+                            B[c] = fmaf(K[c].qx, Bq, K[c].qx);
+                            YQ[c] = Y[c] + K[c].qq;
+                        }
+                        Cz[c] = (WALLS && (cy != 0 || cz != 0)) ? K[c].C[pat] + BFg : K[c].C[pat];
+                        if constexpr (CL != CL_BGK || WALLS) {
+                            float X = WALLS ? gp1 * Fx : 0.f;
+                            if constexpr (cy != 0) X += (float)cy * K[c].Dxy2;
+                            if constexpr (cz != 0) X += (float)cz * K[c].Dxz2;
+                            const float CpD = Cz[c] + K[c].Dxx;
+                            Cp[c] = CpD + X;
+                            Cm[c] = CpD - X;
+                        } else {
+                            Cp[c] = Cm[c] = K[c].C[pat];
+                        }
+                    }
+                    tm_ld12_wait(gr[sl]);
+                    float g[3][4];
+#pragma unroll
+                    for (int q = 0; q < 12; ++q) g[q / 4][q % 4] = __uint_as_float(gr[sl][q]);
+                    if constexpr (PF && p < 8) tm_ld12_issue(ts + 12u * (p + 1), gr[(p + 1) & 1]);
+                    static_for<3>([&](auto CI) {
+                        constexpr int k = decltype(CI)::value;
+                        constexpr int cx = k - 1, i = 3 * p + k;
+                        if constexpr (!v4_has(Q, i)) return;
+                        constexpr float w = (float)weight_of(Q, v4_pop(Q, i));
+                        float o[4];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const float pm1 = Q == 27 ? fmaf(K[c].ex[k], B[c], Y[c])
+                                                      : (cx == 0 ? Y[c] : (cx == 1 ? YQ[c] + B[c] : YQ[c] - B[c]));
+                            const float Cc = cx == 0 ? Cz[c] : (cx == 1 ? Cp[c] : Cm[c]);
+                            const float Kv = fmaf(K[c].cb, pm1, Cc);
+                            // FP32 storage stores f = g' + w: w (1 + K) in one rounding, so
+                            // that no part of K is lost to a sum near 1 (its small terms
+                            // would be dropped with a consistent sign, a mass bias)
+                            o[c] = fmaf(K[c].ca, g[k][c], SHIFTED ? w * Kv : fmaf(w, Kv, w));
+                        }
+                        if (own_store) v4_store(fout + ((long long)v4_pop(Q, i) * ps + cell), o[0], o[1], o[2], o[3]);
+                    });
+                });
+            }
+        }  // analytic closures other than KC-RR
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             dr0[c] = dr1[c];

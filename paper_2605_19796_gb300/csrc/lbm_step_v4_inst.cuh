@@ -38,6 +38,10 @@ cudaError_t launch_v4_qs(int closure, int bc, int ty, bool tma, const StepArgs* 
     LBM_V4_CASE(CL_KCMP, 16, 16)
     LBM_V4_CASE(CL_KCRB_H, 16, 16)
     LBM_V4_CASE(CL_KCRB_RAW, 16, 16)
+    if constexpr (Q == 27) {  // KC-RR is defined on D3Q27
+        LBM_V4_CASE(CL_KCRR, 8, 32)
+        LBM_V4_CASE(CL_KCRR, 16, 16)
+    }
     // the learned closure (D3Q27): its network block and exchanges fit beside
     // the FP32 staging area of 64 x 16 tiles only
     if constexpr (Q == 27) {

@@ -80,6 +80,27 @@ __device__ __forceinline__ void tm_ld12_wait(uint32_t (&r)[12])
                  : "memory");
 }
 
+// one column of the thread's lane: load issued (wait with tm_ld_wait9 before
+// use) / store
+__device__ __forceinline__ void tm_ld1_issue(uint32_t ta, uint32_t& r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n" : "=r"(r) : "r"(ta) : "memory");
+}
+__device__ __forceinline__ void tm_st1(uint32_t ta, uint32_t v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};\n" ::"r"(ta), "r"(v) : "memory");
+}
+// waits for all of the thread's loads issued so far; r: nine of their
+// destination registers, which are not read before this
+__device__ __forceinline__ void tm_ld_wait9(uint32_t* r)
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8])
+                 :
+                 : "memory");
+}
+
 // 8 consecutive columns of the thread's lane, 32-bit values
 __device__ __forceinline__ void tm_st8(uint32_t ta, const uint32_t (&v)[8])
 {

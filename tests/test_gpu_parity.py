@@ -397,8 +397,8 @@ def test_full_size_sampled_cells_fp32(lbm, orc, n):
 
 
 def test_full_size_sampled_cells_kcrr(lbm, orc):
-    """KC-RR at 256^3 (D3Q27, FP32, its default launch: asynchronous copies,
-    variant 13): one GPU step, then sampled cells against the oracle's
+    """KC-RR at 256^3 (D3Q27, FP32, its default launch: the four-cell kernel
+    with TMA staging, variant 16): one GPU step, then sampled cells against the oracle's
     single-cell KC-RR step on the GPU's own pre-step populations; tolerance as
     for KC-MP (the separable Hermite transforms add ~10^2 operations)."""
     n = 256
@@ -406,7 +406,7 @@ def test_full_size_sampled_cells_kcrr(lbm, orc):
     pts = _sampled_cells(n, 32, seed=7)
     offs = np.array([(dx, dy, dz) for dz in range(-2, 3) for dy in range(-2, 3) for dx in range(-2, 3)])
     with lbm.Solver(27, (n, n, n), 1e-4, closure="kcrr", c_nu=0.02, storage="fp32") as s:
-        assert s.launch_config["variant"] == 13
+        assert s.launch_config["variant"] == 16
         s.init_velocity(rho, u)
         del rho, u
         s.step(3)
@@ -509,6 +509,8 @@ def test_default_variant_selection(lbm):
         assert s.launch_config["variant"] == 16 and s.launch_config["tile_y"] == 16  # full tiles
     with lbm.Solver(27, (256, 64, 16), 1e-4, closure="kcmp", storage="fp32") as s:
         assert s.launch_config["variant"] == 16 and s.launch_config["tile_y"] == 8
+    with lbm.Solver(27, (256, 64, 16), 1e-4, closure="kcrr", storage="fp32") as s:
+        assert s.launch_config["variant"] == 16 and s.launch_config["tile_y"] == 8  # KC-RR: TMA staging only
     with lbm.Solver(27, (256, 64, 16), 1e-4, closure="kcmp", storage="fp16") as s:
         assert s.launch_config["variant"] == 14
     for closure, storage, want in (("kcmp", "fp32", 12), ("kcrb_hermite", "fp16", 8), ("bgk", "fp32", 8),

@@ -26,8 +26,8 @@ from paper_2605_19796_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-CL = {"bgk": 0, "kcmp": 1, "kcrb_hermite": 2, "kcrb_raw": 3}
-CNU = {"bgk": 0.0, "kcmp": 0.035, "kcrb_hermite": 0.02, "kcrb_raw": 0.02}
+CL = {"bgk": 0, "kcmp": 1, "kcrb_hermite": 2, "kcrb_raw": 3, "kcrr": 4}
+CNU = {"bgk": 0.0, "kcmp": 0.035, "kcrb_hermite": 0.02, "kcrb_raw": 0.02, "kcrr": 0.02}
 
 
 @pytest.fixture(scope="module")
@@ -69,7 +69,7 @@ LAUNCHES = [(14, 8), (14, 16), (16, 8), (16, 16)]
 # (128, 32, 6): full tiles in y, so the first and the last tile row of the TMA-staged
 # variant copy their wrapping rows as one box of RY - 1 or RY - 2 rows and one or two single rows
 @pytest.mark.parametrize("shape", [(256, 20, 9), (64, 8, 5), (24, 5, 3), (128, 32, 6)])
-@pytest.mark.parametrize("closure", ["bgk", "kcmp", "kcrb_hermite", "kcrb_raw"])
+@pytest.mark.parametrize("closure", ["bgk", "kcmp", "kcrb_hermite", "kcrb_raw", "kcrr"])
 def test_vec4_fp32_matches_register_pull_and_oracle(lbm, orc, closure, shape, tile_y, variant):
     nus = np.array([2e-5, 1e-4])
     if variant == 16 and shape[0] % (128 if tile_y == 8 else 64) != 0:
@@ -99,7 +99,7 @@ def test_vec4_fp32_matches_register_pull_and_oracle(lbm, orc, closure, shape, ti
 @pytest.mark.parametrize("variant", [14, 16])
 @pytest.mark.parametrize("tile_y", [8, 16])
 @pytest.mark.parametrize("storage", ["fp16", "bf16"])
-@pytest.mark.parametrize("closure", ["bgk", "kcmp", "kcrb_hermite", "kcrb_raw"])
+@pytest.mark.parametrize("closure", ["bgk", "kcmp", "kcrb_hermite", "kcrb_raw", "kcrr"])
 def test_vec4_16bit_matches_register_pull(lbm, orc, closure, storage, tile_y, variant, shape):
     # (128, 32, 5): full tiles in y, so the TMA-staged variant copies the wrapping
     # rows of the first and the last tile row as one box and one or two rows

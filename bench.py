@@ -43,6 +43,7 @@ WORKLOADS = {
     "hit512_d3q19_fp16_kcmp": dict(n=512, q=19, storage="fp16", closure="kcmp", nu=1e-4, k0=4.0, urms=0.04),
     "hit512_d3q27_fp32_bgk": dict(n=512, q=27, storage="fp32", closure="bgk", nu=1e-4, k0=4.0, urms=0.04),
     "hit512_d3q27_fp32_kcrr": dict(n=512, q=27, storage="fp32", closure="kcrr", nu=1e-4, k0=4.0, urms=0.04),
+    "hit256_d3q27_fp32_kcrr": dict(n=256, q=27, storage="fp32", closure="kcrr", nu=1e-4, k0=4.0, urms=0.04),
     "hit512_d3q27_fp32_kcrb_raw": dict(n=512, q=27, storage="fp32", closure="kcrb_raw", nu=1e-4, k0=4.0, urms=0.04),
     "hit256_d3q27_fp64_kcmp": dict(n=256, q=27, storage="fp64", closure="kcmp", nu=1e-4, k0=4.0, urms=0.04),
     "hit128_d3q27_fp64_kcmp": dict(n=128, q=27, storage="fp64", closure="kcmp", nu=1e-4, k0=4.0, urms=0.04),

@@ -4,8 +4,9 @@
 // Same update as step_kernel (lbm_step.cuh): pull streaming (Eq. streaming),
 // moments (App. F.1 step 1), equilibrium (Eq. discrete_equilibrium), strain
 // (Eqs. fd, strain_rate_discrete), closure, rate (Eq. omega_sgs_operational)
-// and two-rate relaxation (App. F.2, F.3), store.  Periodic D3Q27 boxes whose
-// nx is a multiple of 8.  The mapping onto the GPU differs:
+// and two-rate relaxation (App. F.2, F.3; KC-RR, App. F.4), store.  D3Q27 and
+// D3Q19, periodic boxes and channels with walls in y, nx a multiple of 8.  The
+// mapping onto the GPU differs:
 //
 //  * Each thread owns four consecutive x-cells of one row.  The source row of a
 //    population is read with ONE aligned vector load per thread (16 bytes for
@@ -47,7 +48,10 @@
 //    of collide() with P - 1 = e_x (1 + Y) + Y, Y = e_y + e_z + e_y e_z, and
 //    the quadratic form H split into its (c_y, c_z) part and the c_x terms, so
 //    that each population's four results form one vector store.  For FP32
-//    storage the store's "+ w" enters as w (1 + K), one fused rounding.
+//    storage the store's "+ w" enters as w (1 + K), one fused rounding.  D3Q19
+//    takes its Hermite equilibrium along a triple (V4Cell), and KC-RR collides
+//    one cell at a time from the TMEM stash (its Hermite-space collision needs
+//    a cell's 27 populations together) before the same vector stores.
 #pragma once
 
 #include <cuda.h>

@@ -72,7 +72,8 @@ def _cfg(lbm, **kw):
     (dict(variant=2), -1), (dict(variant=6), -1), (dict(variant=11), -1),     (dict(variant=15), -6), (dict(variant=15, closure=5, storage=0), -6), (dict(variant=15, closure=5, tile_y=8), -6),
     (dict(variant=16, nx=64), -6), (dict(variant=16, nx=64, tile_y=16, closure=5), -6),
     (dict(variant=16, storage=0, nx=128), -6), (dict(variant=17), -1),
-    (dict(variant=14, nx=44), -6), (dict(variant=14, storage=0), -6), (dict(variant=14, closure=4), -6),
+    (dict(variant=14, nx=44), -6), (dict(variant=14, storage=0), -6),
+    (dict(variant=14, closure=4, bc=(0, 1, 0), ny=32), -6), (dict(variant=16, closure=2, bc=(0, 1, 0), ny=32, nx=128), -6),
     (dict(variant=13, storage=2), -6),
     (dict(variant=9), -1), (dict(variant=4), -1),
 ])

@@ -48,7 +48,8 @@
 //    of collide() with P - 1 = e_x (1 + Y) + Y, Y = e_y + e_z + e_y e_z, and
 //    the quadratic form H split into its (c_y, c_z) part and the c_x terms, so
 //    that each population's four results form one vector store.  For FP32
-//    storage the store's "+ w" enters as w (1 + K), one fused rounding.  D3Q19
+//    storage the "+ w" of the stored f = g' + w comes last, after g' is
+//    rounded on its own small scale, so that the mass does not drift.  D3Q19
 //    takes its Hermite equilibrium along a triple (V4Cell), and KC-RR collides
 //    one cell at a time from the TMEM stash (its Hermite-space collision needs
 //    a cell's 27 populations together) before the same vector stores.
@@ -1049,10 +1050,12 @@ __global__ void __launch_bounds__(256, 1)
                                                       : (cx == 0 ? Y[c] : (cx == 1 ? YQ[c] + B[c] : YQ[c] - B[c]));
                             const float Cc = cx == 0 ? Cz[c] : (cx == 1 ? Cp[c] : Cm[c]);
                             const float Kv = fmaf(K[c].cb, pm1, Cc);
-                            // FP32 storage stores f = g' + w: w (1 + K) in one rounding, so
-                            // that no part of K is lost to a sum near 1 (its small terms
-                            // would be dropped with a consistent sign, a mass bias)
-                            o[c] = fmaf(K[c].ca, g[k][c], SHIFTED ? w * Kv : fmaf(w, Kv, w));
+                            // g' = a g + w K rounded on the scale of g, then (FP32 storage)
+                            // f = g' + w in one rounding on the scale of w, as in the
+                            // one-cell kernels: w (1 + K) rounded first and a g added after
+                            // it rounds twice on the scale of w and drifted the mass
+                            const float gq = fmaf(K[c].ca, g[k][c], w * Kv);
+                            o[c] = SHIFTED ? gq : gq + w;
                         }
                         if (own_store) v4_store(fout + ((long long)v4_pop(Q, i) * ps + cell), o[0], o[1], o[2], o[3]);
                     });

@@ -396,6 +396,33 @@ def test_full_size_sampled_cells_fp32(lbm, orc, n):
     assert abs(mass1 - mass0) <= 1e-9 * mass0
 
 
+def test_full_size_sampled_cells_d3q19_fp32(lbm, orc):
+    """Full-size D3Q19 HIT (512^3, FP32, KC-MP) in its default launch (the
+    four-cell kernel with TMA staging, the D3Q27 positions without the
+    corners): one GPU step, then sampled cells against the oracle's single-cell
+    step on the GPU's own pre-step populations, as the D3Q27 test."""
+    n = 512
+    rho, u = inputs.hit_fields(n, k0=4.0, urms=0.04, seed=3)
+    pts = _sampled_cells(n, 32, seed=19)
+    offs = np.array([(dx, dy, dz) for dz in range(-2, 3) for dy in range(-2, 3) for dx in range(-2, 3)])
+    with lbm.Solver(19, (n, n, n), 1e-4, closure="kcmp", storage="fp32") as s:
+        assert s.launch_config["variant"] == 16 and s.launch_config["tile_y"] == 8
+        s.init_velocity(rho, u)
+        del rho, u
+        s.step(3)
+        blocks = s.probe((pts[:, None, :] + offs[None, :, :]).reshape(-1, 3)).reshape(len(pts), 125, 19)
+        mass0 = s.diagnostics()[0]
+        s.step(1)
+        after = s.probe(pts)
+        mass1 = s.diagnostics()[0]
+    scale = np.abs(after).max()
+    for k in range(len(pts)):
+        blk = blocks[k].T.reshape(19, 5, 5, 5)
+        ref = orc.step_cell(blk, closure=1, nu=1e-4, c_nu=0.035)
+        assert np.abs(after[k] - ref).max() <= 2e-6 * scale, (pts[k], np.abs(after[k] - ref).max())
+    assert abs(mass1 - mass0) <= 1e-9 * mass0
+
+
 def test_full_size_sampled_cells_kcrr(lbm, orc):
     """KC-RR at 256^3 (D3Q27, FP32, its default launch: the four-cell kernel
     with TMA staging, variant 16): one GPU step, then sampled cells against the oracle's
